@@ -1,0 +1,556 @@
+/*
+ * Plain FP64 CPU oracle for the Keldysh loop bubble of the single-impurity Anderson
+ * model (KeldyshQFT paper, arXiv:2405.20996).
+ *
+ * TEST INFRASTRUCTURE.  Only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark may load this code.  It shares no source with the CUDA library.
+ *
+ * What it computes (one output point at a time, no blocking or reordering):
+ *
+ *   B_r(w, v, v')^{alpha} = c_r * sum_j  w_j/(2 pi i) * J(x_j)
+ *        * sum_{beta} Gamma1^{...}(w, v, v''_j) Pi_r^{beta}(w, v''_j) Gamma2^{...}(w, v''_j, v')
+ *
+ *   - the bubble Gamma1 o Pi_r o Gamma2 of two vertices in channel r (Sec. II.E.1,
+ *     "bubble_function"), with the propagator pair Pi = G G or Pi-dot = G S + S G
+ *     (Sec. II.D.5, "Bubble");
+ *   - the v'' integral taken by a fixed composite 5-point Gauss-Lobatto rule in the
+ *     auxiliary variable x of the frequency grid v = A tan(pi x / 2)
+ *     (Sec. II.G.4 and II.G.5; x covers [-1, 1] including v = +-inf, where the
+ *     integrand times the Jacobian is replaced by its limit);
+ *   - vertices stored as asymptotic classes K1, K2, K2', K3 per channel and read out
+ *     by multilinear interpolation in x ("linear_on_aux", Sec. II.G.7) with zero
+ *     values at x = +-1;
+ *   - the output split into classes by which parts of the two vertices are used
+ *     (Sec. II.D.1: parts whose external legs do / do not meet at one bare vertex).
+ *
+ * Conventions (readings of the paper where it defers to its companion paper):
+ *   Keldysh: 1 = classical, 2 = quantum; G^{1|1} = G^K, G^{1|2} = G^R, G^{2|1} = G^A,
+ *   G^{2|2} = 0.  Bare vertex (parquet approximation R = Gamma_0, Sec. I.B):
+ *   Gamma_0^{up,down} = +U/2 on components with an odd number of quantum indices.
+ *   Channel variables: a: w = v1'-v2, v = (v1'+v2)/2, v' = (v1+v2')/2;
+ *   p: w = v1'+v2', v = (v1'-v2')/2, v' = (v1-v2)/2; t: w = v2'-v2, v = (v1'+v1)/2,
+ *   v' = (v2'+v2)/2.  Spin: only the up-down component is stored; the up-up component
+ *   is Gamma(1'2'|12) - Gamma(1'2'|21) (SU(2) + crossing, Sec. II.G.3).
+ *   Bubbles (antisymmetric diagram rules, Eq. (1a-c) of Sec. III.B with c_a = 1,
+ *   c_p = 1/2 x 2 equal spin terms = 1, c_t = -1):
+ *     a: sum G1^{a1' b4'|b3 a2} G^{b3|b3'}(v''+w/2) G^{b4|b4'}(v''-w/2) G2^{b3' a2'|a1 b4}
+ *     p: sum G1^{a1' a2'|b3 b4} G^{b3|b3'}(w/2+v'') G^{b4|b4'}(w/2-v'') G2^{b3' b4'|a1 a2}
+ *     t: -sum [G1uu G2ud + G1ud G2uu], G1^{a1' b3'|a1 b4}(w,v,v'') G^{b3|b3'}(v''+w/2)
+ *         G^{b4|b4'}(v''-w/2) G2^{b4' a2'|b3 a2}(w,v'',v')
+ *   Measure dv''/(2 pi i).
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef double complex cplx;
+
+#define PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------------------
+ * Frequency grid (Sec. II.G.4): N points x_i = -1 + 2(i+1)/(N+1), v_i = A tan(pi x_i/2).
+ * The extended node list X_k = -1 + 2(k+1)/(N+1), k = -1..N adds x = -1 and x = +1,
+ * where every vertex class takes the value 0.
+ * ------------------------------------------------------------------------------------ */
+static double nu_to_x(double nu, double A) {
+    if (isinf(nu)) return nu > 0 ? 1.0 : -1.0;
+    return (2.0 / PI) * atan(nu / A);
+}
+
+/* Linear interpolation stencil in x: up to two real nodes with weights. Returns the
+ * number of contributing real nodes (0, 1 or 2). */
+static int stencil(double nu, int n, double A, int idx[2], double wt[2]) {
+    if (!isfinite(nu)) return 0;               /* value at x = +-1 is zero */
+    double x = nu_to_x(nu, A);
+    double d = 2.0 / (n + 1);
+    int k = (int)floor((x + 1.0) / d) - 1;     /* X_k <= x < X_{k+1} */
+    if (k < -1) k = -1;
+    if (k > n - 1) k = n - 1;
+    double Xk = -1.0 + 2.0 * (k + 1) / (n + 1);
+    double t = (x - Xk) / d;
+    int m = 0;
+    if (k >= 0 && k <= n - 1) { idx[m] = k; wt[m] = 1.0 - t; ++m; }
+    if (k + 1 >= 0 && k + 1 <= n - 1) { idx[m] = k + 1; wt[m] = t; ++m; }
+    return m;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Vertex object: bare part plus, per channel, the four asymptotic classes (Sec. II.D.1).
+ * ------------------------------------------------------------------------------------ */
+typedef struct {
+    int n1, n2w, n2v, n3w, n3v;   /* class grids (shared by the three channels) */
+    double A;                      /* grid scale */
+    double U;                      /* bare vertex strength; used only if has_R */
+    int has_R;
+    const cplx *K1[3], *K2[3], *K2p[3], *K3[3];   /* NULL = class absent */
+} ovtx;
+
+/* Component index of (a1', a2' | a1, a2), each given as 0 (classical) / 1 (quantum). */
+static inline int kidx(int b1p, int b2p, int b1, int b2) { return 8 * b1p + 4 * b2p + 2 * b1 + b2; }
+
+static int popc4(int c) { return (c & 1) + ((c >> 1) & 1) + ((c >> 2) & 1) + ((c >> 3) & 1); }
+
+/* Bare vertex, up-down component, 16 Keldysh components (Sec. I.B, PA R = Gamma_0). */
+static void bare_vertex(const ovtx *V, cplx out[16]) {
+    for (int c = 0; c < 16; ++c) out[c] = (V->has_R && (popc4(c) & 1)) ? 0.5 * V->U : 0.0;
+}
+
+/* Add f * class(w, v, v') of channel ch into out (16 comps). k: 0 K1, 1 K2, 2 K2', 3 K3. */
+static void add_class(const ovtx *V, int ch, int k, double w, double v, double vp, double f, cplx out[16]) {
+    int iw[2], iv[2], ip[2];
+    double ww[2], wv[2], wp[2];
+    if (k == 0) {
+        const cplx *D = V->K1[ch];
+        if (!D) return;
+        int mw = stencil(w, V->n1, V->A, iw, ww);
+        for (int a = 0; a < mw; ++a)
+            for (int c = 0; c < 16; ++c) out[c] += f * ww[a] * D[(size_t)iw[a] * 16 + c];
+    } else if (k == 1 || k == 2) {
+        const cplx *D = (k == 1) ? V->K2[ch] : V->K2p[ch];
+        if (!D) return;
+        double u = (k == 1) ? v : vp;
+        int mw = stencil(w, V->n2w, V->A, iw, ww);
+        int mv = stencil(u, V->n2v, V->A, iv, wv);
+        for (int a = 0; a < mw; ++a)
+            for (int b = 0; b < mv; ++b) {
+                const cplx *p = D + ((size_t)iw[a] * V->n2v + iv[b]) * 16;
+                double g = f * ww[a] * wv[b];
+                for (int c = 0; c < 16; ++c) out[c] += g * p[c];
+            }
+    } else {
+        const cplx *D = V->K3[ch];
+        if (!D) return;
+        int mw = stencil(w, V->n3w, V->A, iw, ww);
+        int mv = stencil(v, V->n3v, V->A, iv, wv);
+        int mp = stencil(vp, V->n3v, V->A, ip, wp);
+        for (int a = 0; a < mw; ++a)
+            for (int b = 0; b < mv; ++b)
+                for (int e = 0; e < mp; ++e) {
+                    const cplx *p = D + (((size_t)iw[a] * V->n3v + iv[b]) * V->n3v + ip[e]) * 16;
+                    double g = f * ww[a] * wv[b] * wp[e];
+                    for (int c = 0; c < 16; ++c) out[c] += g * p[c];
+                }
+    }
+}
+
+/* Leg frequencies (v1', v2', v1, v2) from channel variables, and back. */
+static void legs_from(int r, double w, double v, double vp, double L[4]) {
+    if (r == 0) { L[0] = v + w / 2; L[3] = v - w / 2; L[2] = vp + w / 2; L[1] = vp - w / 2; }
+    else if (r == 1) { L[0] = w / 2 + v; L[1] = w / 2 - v; L[2] = w / 2 + vp; L[3] = w / 2 - vp; }
+    else { L[1] = vp + w / 2; L[3] = vp - w / 2; L[0] = v - w / 2; L[2] = v + w / 2; }
+}
+static void chan_from(int r, const double L[4], double *w, double *v, double *vp) {
+    if (r == 0) { *w = L[0] - L[3]; *v = (L[0] + L[3]) / 2; *vp = (L[2] + L[1]) / 2; }
+    else if (r == 1) { *w = L[0] + L[1]; *v = (L[0] - L[1]) / 2; *vp = (L[2] - L[3]) / 2; }
+    else { *w = L[1] - L[3]; *v = (L[0] + L[2]) / 2; *vp = (L[1] + L[3]) / 2; }
+}
+
+/* Parts of the up-down vertex relative to channel r, evaluated at r-variables
+ * (w, v, vp) (v or vp may be +-inf): R, own classes k = 0..3, and the sum of the
+ * two other channels (evaluated at the converted frequencies). */
+typedef struct { cplx R[16]; cplx own[4][16]; cplx other[16]; } vparts;
+
+static void parts_ud(const ovtx *V, int r, double w, double v, double vp, int want_own, int want_other,
+                     vparts *P) {
+    memset(P, 0, sizeof(*P));
+    bare_vertex(V, P->R);
+    if (want_own)
+        for (int k = 0; k < 4; ++k) add_class(V, r, k, w, v, vp, 1.0, P->own[k]);
+    if (want_other) {
+        double L[4];
+        legs_from(r, w, v, vp, L);
+        for (int c = 0; c < 3; ++c) {
+            if (c == r) continue;
+            double wc, vc, pc;
+            chan_from(c, L, &wc, &vc, &pc);
+            for (int k = 0; k < 4; ++k) add_class(V, c, k, wc, vc, pc, 1.0, P->other);
+        }
+    }
+}
+
+/* Parts of the up-up vertex, Gamma_uu(1'2'|12) = Gamma_ud(1'2'|12) - Gamma_ud(1'2'|21),
+ * split relative to channel r.  Exchanging legs 1 and 2 maps channel a <-> t, p -> p, so
+ * the own-channel classes of the exchanged term come from channel sigma(r). */
+static void parts_uu(const ovtx *V, int r, double w, double v, double vp, int want_own, int want_other,
+                     vparts *P) {
+    vparts D;
+    parts_ud(V, r, w, v, vp, want_own, want_other, &D);
+    *P = D;
+    double L[4], S[4];
+    legs_from(r, w, v, vp, L);
+    S[0] = L[0]; S[1] = L[1]; S[2] = L[3]; S[3] = L[2];         /* legs 1 <-> 2 */
+    int sr = (r == 0) ? 2 : (r == 2) ? 0 : 1;
+    cplx R[16], own[4][16], oth[16];
+    memset(own, 0, sizeof(own));
+    memset(oth, 0, sizeof(oth));
+    bare_vertex(V, R);
+    for (int c = 0; c < 3; ++c) {
+        double wc, vc, pc;
+        if (c == sr) {
+            if (!want_own) continue;
+            /* sigma(r)-variables of the exchanged legs, written out exactly so that an
+             * infinite v or v' needs no cancellation: a <-> t: (w, v, v') -> (-w, v, v');
+             * p: (w, v, v') -> (w, v, -v') */
+            if (r == 1) { wc = w; vc = v; pc = -vp; }
+            else { wc = -w; vc = v; pc = vp; }
+            for (int k = 0; k < 4; ++k) add_class(V, c, k, wc, vc, pc, 1.0, own[k]);
+        } else {
+            if (!want_other) continue;
+            chan_from(c, S, &wc, &vc, &pc);
+            for (int k = 0; k < 4; ++k) add_class(V, c, k, wc, vc, pc, 1.0, oth);
+        }
+    }
+    /* component of the exchanged term: (a1' a2' | a2 a1) */
+    for (int cc = 0; cc < 16; ++cc) {
+        int b1p = (cc >> 3) & 1, b2p = (cc >> 2) & 1, b1 = (cc >> 1) & 1, b2 = cc & 1;
+        int sw = kidx(b1p, b2p, b2, b1);
+        P->R[cc] -= R[sw];
+        for (int k = 0; k < 4; ++k) P->own[k][cc] -= own[k][sw];
+        P->other[cc] -= oth[sw];
+    }
+}
+
+/* Selection of vertex parts (Sec. II.D.1).  For the left vertex Gamma1(w, v, v''):
+ *   SEL_ZERO = R + K1_r + K2'_r   (independent of the external v)
+ *   SEL_NU   = K2_r + K3_r + other channels
+ * for the right vertex Gamma2(w, v'', v'):
+ *   SEL_ZERO = R + K1_r + K2_r    (independent of the external v')
+ *   SEL_NU   = K2'_r + K3_r + other channels
+ * SEL_FULL = everything. */
+enum { SEL_ZERO = 0, SEL_NU = 1, SEL_FULL = 2 };
+
+static void vertex_select(const ovtx *V, int r, int spin_uu, int side_right, int sel, double w, double v,
+                          double vp, cplx out[16]) {
+    vparts P;
+    int want_other = (sel != SEL_ZERO);
+    if (spin_uu) parts_uu(V, r, w, v, vp, 1, want_other, &P);
+    else parts_ud(V, r, w, v, vp, 1, want_other, &P);
+    /* class that does not depend on the external argument of this side */
+    int k_ext_free = side_right ? 1 : 2;   /* right: K2_r(w, v''); left: K2'_r(w, v'') */
+    int k_ext_dep = side_right ? 2 : 1;
+    for (int c = 0; c < 16; ++c) {
+        cplx zero = P.R[c] + P.own[0][c] + P.own[k_ext_free][c];
+        cplx nu = P.own[k_ext_dep][c] + P.own[3][c] + P.other[c];
+        out[c] = (sel == SEL_ZERO) ? zero : (sel == SEL_NU) ? nu : zero + nu;
+    }
+}
+
+/* ------------------------------------------------------------------------------------
+ * Propagators (Sec. II.D.4, III.C.3): G^R = 1 / (v - eps + i Delta - Sigma^R(v)),
+ * G^A = (G^R)*, G^K = G^R [Sigma^K - 2 i Delta tanh(v/2T)] G^A.  Single-scale
+ * propagator of the hybridisation flow: S = d/dDelta G at fixed Sigma, S^R = -i (G^R)^2.
+ * Sigma tables (optional) are interpolated linearly in x with zero at x = +-1.
+ * ------------------------------------------------------------------------------------ */
+typedef struct {
+    double Delta, T, eps, A_sig;
+    int n_sig;                    /* 0: Sigma = 0 */
+    const cplx *sigR, *sigK;
+} oprop;
+
+static double tanh_ft(double v, double T) {
+    if (T <= 0.0) return v > 0 ? 1.0 : (v < 0 ? -1.0 : 0.0);
+    return tanh(v / (2.0 * T));
+}
+
+/* 2x2 Keldysh matrices M[a][a'] (a, a' = 0 classical, 1 quantum). which: 0 = G, 1 = S */
+static void prop_matrix(const oprop *P, int which, double v, cplx M[2][2]) {
+    cplx sR = 0, sK = 0;
+    if (P->n_sig > 0) {
+        int id[2];
+        double wt[2];
+        int m = stencil(v, P->n_sig, P->A_sig, id, wt);
+        for (int a = 0; a < m; ++a) { sR += wt[a] * P->sigR[id[a]]; if (P->sigK) sK += wt[a] * P->sigK[id[a]]; }
+    }
+    cplx GR = 1.0 / (v - P->eps + I * P->Delta - sR);
+    cplx GA = conj(GR);
+    double th = tanh_ft(v, P->T);
+    cplx mid = sK - 2.0 * I * P->Delta * th;
+    if (which == 0) {
+        M[0][0] = GR * mid * GA;
+        M[0][1] = GR;
+        M[1][0] = GA;
+        M[1][1] = 0;
+    } else {
+        cplx SR = -I * GR * GR;
+        cplx SA = conj(SR);
+        M[0][0] = SR * mid * GA + GR * (-2.0 * I * th) * GA + GR * mid * SA;
+        M[0][1] = SR;
+        M[1][0] = SA;
+        M[1][1] = 0;
+    }
+}
+
+/* lim_{v->+-inf} v * P(v): G -> [[0,1],[1,0]], S -> 0 */
+static void prop_asym(int which, cplx M[2][2]) {
+    M[0][0] = 0; M[1][1] = 0;
+    M[0][1] = M[1][0] = (which == 0) ? 1.0 : 0.0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Bubble integrand: 16 output components at one node.
+ * x_node in [-1, 1]; returns J(x) * F(v(x)) (or its limit at x = +-1), without the
+ * 1/(2 pi i), the weight and the channel prefactor.
+ * pi_kind: 0 = G G, 1 = G S + S G.
+ * ------------------------------------------------------------------------------------ */
+typedef struct {
+    const ovtx *V1, *V2;
+    const oprop *P;
+    int pi_kind, r, lsel, rsel;
+    double w, v, vp;
+} bctx;
+
+/* Pi^{b3 b3' b4 b4'} = P1^{b3|b3'}(arg3) P2^{b4|b4'}(arg4) summed over the pair kinds. */
+static void pi_matrix(const bctx *B, double nupp, int at_inf, double sgn_inf, cplx Pi[2][2][2][2]) {
+    double w = B->w;
+    double a3, a4, s3, s4;
+    if (B->r == 1) { a3 = w / 2 + nupp; a4 = w / 2 - nupp; s3 = 1; s4 = -1; }
+    else { a3 = nupp + w / 2; a4 = nupp - w / 2; s3 = 1; s4 = 1; }
+    cplx G3[2][2], G4[2][2], S3[2][2], S4[2][2];
+    if (at_inf) {
+        /* lim v''^2 P(a3) P(a4) = s3 s4 * asym * asym (independent of the sign of v'') */
+        (void)sgn_inf;
+        prop_asym(0, G3); prop_asym(0, G4); prop_asym(1, S3); prop_asym(1, S4);
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) {
+                G3[i][j] *= s3; S3[i][j] *= s3; G4[i][j] *= s4; S4[i][j] *= s4;
+            }
+    } else {
+        prop_matrix(B->P, 0, a3, G3);
+        prop_matrix(B->P, 0, a4, G4);
+        if (B->pi_kind == 1) { prop_matrix(B->P, 1, a3, S3); prop_matrix(B->P, 1, a4, S4); }
+    }
+    for (int b3 = 0; b3 < 2; ++b3)
+        for (int b3p = 0; b3p < 2; ++b3p)
+            for (int b4 = 0; b4 < 2; ++b4)
+                for (int b4p = 0; b4p < 2; ++b4p) {
+                    cplx val = G3[b3][b3p] * G4[b4][b4p];
+                    if (B->pi_kind == 1) val = G3[b3][b3p] * S4[b4][b4p] + S3[b3][b3p] * G4[b4][b4p];
+                    Pi[b3][b3p][b4][b4p] = val;
+                }
+}
+
+static void contract(int r, const cplx L[16], const cplx Pi[2][2][2][2], const cplx R[16], cplx F[16]) {
+    for (int o = 0; o < 16; ++o) {
+        int a1p = (o >> 3) & 1, a2p = (o >> 2) & 1, a1 = (o >> 1) & 1, a2 = o & 1;
+        cplx s = 0;
+        for (int b3 = 0; b3 < 2; ++b3)
+            for (int b3p = 0; b3p < 2; ++b3p)
+                for (int b4 = 0; b4 < 2; ++b4)
+                    for (int b4p = 0; b4p < 2; ++b4p) {
+                        int li, ri;
+                        if (r == 0) { li = kidx(a1p, b4p, b3, a2); ri = kidx(b3p, a2p, a1, b4); }
+                        else if (r == 1) { li = kidx(a1p, a2p, b3, b4); ri = kidx(b3p, b4p, a1, a2); }
+                        else { li = kidx(a1p, b3p, a1, b4); ri = kidx(b4p, a2p, b3, a2); }
+                        s += L[li] * Pi[b3][b3p][b4][b4p] * R[ri];
+                    }
+        F[o] += s;
+    }
+}
+
+static void integrand_x(const bctx *B, double x, cplx F[16]) {
+    const ovtx *V1 = B->V1, *V2 = B->V2;
+    double A = V1->A;
+    int at_inf = (x <= -1.0 || x >= 1.0);
+    double nupp, jac;
+    if (at_inf) {
+        nupp = (x > 0) ? INFINITY : -INFINITY;
+        jac = PI / (2.0 * A);     /* J(x) / v''^2 at x = +-1 */
+    } else {
+        double tn = tan(PI * x / 2);
+        nupp = A * tn;
+        jac = A * PI / 2 * (1.0 + tn * tn);
+    }
+    cplx Pi[2][2][2][2];
+    pi_matrix(B, nupp, at_inf, x, Pi);
+    for (int c = 0; c < 16; ++c) F[c] = 0;
+    cplx L[16], R[16];
+    if (B->r != 2) {
+        vertex_select(V1, B->r, 0, 0, B->lsel, B->w, B->v, nupp, L);
+        vertex_select(V2, B->r, 0, 1, B->rsel, B->w, nupp, B->vp, R);
+        contract(B->r, L, Pi, R, F);
+    } else {
+        cplx Lu[16], Ru[16];
+        vertex_select(V1, 2, 1, 0, B->lsel, B->w, B->v, nupp, Lu);
+        vertex_select(V2, 2, 0, 1, B->rsel, B->w, nupp, B->vp, R);
+        contract(2, Lu, Pi, R, F);
+        vertex_select(V1, 2, 0, 0, B->lsel, B->w, B->v, nupp, L);
+        vertex_select(V2, 2, 1, 1, B->rsel, B->w, nupp, B->vp, Ru);
+        contract(2, L, Pi, Ru, F);
+    }
+    for (int c = 0; c < 16; ++c) F[c] *= jac;
+}
+
+static double chan_prefactor(int r) { return r == 2 ? -1.0 : 1.0; }
+
+/* ------------------------------------------------------------------------------------
+ * Composite 5-point Gauss-Lobatto rule on [-1, 1] with P = (Nq-1)/4 panels
+ * (nodes 0, +-sqrt(3/7), +-1 of each panel; weights 32/45, 49/90, 1/10).
+ * ------------------------------------------------------------------------------------ */
+int og_gl5_rule(int Nq, double *x, double *wt) {
+    if (Nq < 5 || (Nq - 1) % 4 != 0) return -1;
+    int P = (Nq - 1) / 4;
+    double h = 2.0 / P;
+    double t[5] = {-1.0, -sqrt(3.0 / 7.0), 0.0, sqrt(3.0 / 7.0), 1.0};
+    double u[5] = {1.0 / 10, 49.0 / 90, 32.0 / 45, 49.0 / 90, 1.0 / 10};
+    for (int j = 0; j < Nq; ++j) wt[j] = 0.0;
+    for (int p = 0; p < P; ++p) {
+        double xl = -1.0 + p * h;
+        for (int q = 0; q < 5; ++q) {
+            int j = 4 * p + q;
+            x[j] = (q == 4 && p == P - 1) ? 1.0 : (q == 0 && p == 0) ? -1.0 : xl + (t[q] + 1.0) * h / 2;
+            wt[j] += u[q] * h / 2;
+        }
+    }
+    return 0;
+}
+
+/* One output point with the fixed rule. */
+static void bubble_point_fixed(const bctx *B, int Nq, const double *xq, const double *wq, cplx out[16]) {
+    cplx acc[16], F[16];
+    for (int c = 0; c < 16; ++c) acc[c] = 0;
+    for (int j = 0; j < Nq; ++j) {
+        integrand_x(B, xq[j], F);
+        for (int c = 0; c < 16; ++c) acc[c] += wq[j] * F[c];
+    }
+    double cr = chan_prefactor(B->r);
+    for (int c = 0; c < 16; ++c) out[c] = cr * acc[c] / (2.0 * PI * I);
+}
+
+/* Public: bubble at npts points (w, v, vp) = freqs[3i..3i+2]; out[16 i + c]. */
+int og_bubble_points(const ovtx *V1, const ovtx *V2, const oprop *P, int pi_kind, int r, int lsel, int rsel,
+                     int Nq, int npts, const double *freqs, cplx *out, int nthreads) {
+    if (r < 0 || r > 2 || Nq < 5 || (Nq - 1) % 4) return -1;
+    double *xq = malloc(sizeof(double) * Nq), *wq = malloc(sizeof(double) * Nq);
+    if (!xq || !wq) { free(xq); free(wq); return -2; }
+    og_gl5_rule(Nq, xq, wq);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int i = 0; i < npts; ++i) {
+        bctx B = {V1, V2, P, pi_kind, r, lsel, rsel, freqs[3 * i], freqs[3 * i + 1], freqs[3 * i + 2]};
+        bubble_point_fixed(&B, Nq, xq, wq, out + (size_t)16 * i);
+    }
+    free(xq);
+    free(wq);
+    return 0;
+}
+
+/* Raw integrand J(x) F(v(x)) at given x nodes for one point (for quadrature tests). */
+int og_integrand(const ovtx *V1, const ovtx *V2, const oprop *P, int pi_kind, int r, int lsel, int rsel,
+                 double w, double v, double vp, int nx, const double *xs, cplx *out) {
+    bctx B = {V1, V2, P, pi_kind, r, lsel, rsel, w, v, vp};
+    for (int i = 0; i < nx; ++i) integrand_x(&B, xs[i], out + (size_t)16 * i);
+    return 0;
+}
+
+/* Full vertex (up-down or up-up) at channel-r variables, for tests. */
+int og_vertex_eval(const ovtx *V, int r, int spin_uu, int side_right, int sel, int npts, const double *freqs,
+                   cplx *out) {
+    for (int i = 0; i < npts; ++i)
+        vertex_select(V, r, spin_uu, side_right, sel, freqs[3 * i], freqs[3 * i + 1], freqs[3 * i + 2],
+                      out + (size_t)16 * i);
+    return 0;
+}
+
+/* Propagator matrices at frequencies (for tests): out[4 i + 2 a + a'] */
+int og_prop_eval(const oprop *P, int which, int n, const double *v, cplx *out) {
+    for (int i = 0; i < n; ++i) {
+        cplx M[2][2];
+        prop_matrix(P, which, v[i], M);
+        out[4 * i + 0] = M[0][0]; out[4 * i + 1] = M[0][1];
+        out[4 * i + 2] = M[1][0]; out[4 * i + 3] = M[1][1];
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Adaptive Gauss-Lobatto integrator (Sec. II.G.5): GL4 and its 7-point Kronrod
+ * extension on each interval; the 13-point extension gives the error scale I_s once
+ * for the whole interval; an interval is accepted when |I7 - I4| < eps |I_s|, else it
+ * is split at the 7 nodes.  Vector integrand (16 comps), max-norm.
+ * Nodes/weights on [-1, 1] are passed in (derived by the caller from the paper's
+ * printed nodes).
+ * ------------------------------------------------------------------------------------ */
+typedef struct {
+    const bctx *B;
+    double x7[7], w4[7], w7[7];   /* 7 nodes on [-1,1]; GL4 weights (0 at the Kronrod nodes) */
+    double eps, Is;
+    int depth_max, evals, fail;
+} adapt_t;
+
+static double vnorm(const cplx *a) {
+    double m = 0;
+    for (int c = 0; c < 16; ++c) { double q = cabs(a[c]); if (q > m) m = q; }
+    return m;
+}
+
+static void adapt_rec(adapt_t *S, double a, double b, const cplx fa[16], const cplx fb[16], int depth,
+                      cplx out[16]) {
+    double m = 0.5 * (a + b), h = 0.5 * (b - a);
+    cplx f[7][16];
+    memcpy(f[0], fa, sizeof(cplx) * 16);
+    memcpy(f[6], fb, sizeof(cplx) * 16);
+    for (int q = 1; q < 6; ++q) { integrand_x(S->B, m + h * S->x7[q], f[q]); S->evals++; }
+    cplx I4[16], I7[16], d[16];
+    for (int c = 0; c < 16; ++c) {
+        I4[c] = 0; I7[c] = 0;
+        for (int q = 0; q < 7; ++q) { I4[c] += S->w4[q] * f[q][c]; I7[c] += S->w7[q] * f[q][c]; }
+        I4[c] *= h; I7[c] *= h;
+        d[c] = I7[c] - I4[c];
+    }
+    if (vnorm(d) <= S->eps * S->Is || depth >= S->depth_max || b - a < 1e-14) {
+        if (depth >= S->depth_max && vnorm(d) > S->eps * S->Is) S->fail = 1;
+        memcpy(out, I7, sizeof(cplx) * 16);
+        return;
+    }
+    for (int c = 0; c < 16; ++c) out[c] = 0;
+    for (int q = 0; q < 6; ++q) {
+        cplx part[16];
+        adapt_rec(S, m + h * S->x7[q], m + h * S->x7[q + 1], f[q], f[q + 1], depth + 1, part);
+        for (int c = 0; c < 16; ++c) out[c] += part[c];
+    }
+}
+
+/* x7: the 7 GLK7 nodes, w4/w7: GL4 (zeros at Kronrod nodes) and GLK7 weights,
+ * x13/w13: the 13-point rule used once for I_s.  Returns number of integrand calls,
+ * negative if some interval hit the depth limit. */
+int og_bubble_points_adaptive(const ovtx *V1, const ovtx *V2, const oprop *P, int pi_kind, int r, int lsel,
+                              int rsel, int npts, const double *freqs, const double *x7, const double *w4,
+                              const double *w7, const double *x13, const double *w13, double eps,
+                              int depth_max, cplx *out, int nthreads) {
+    long total = 0;
+    int failed = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : total) reduction(| : failed)
+#endif
+    for (int i = 0; i < npts; ++i) {
+        bctx B = {V1, V2, P, pi_kind, r, lsel, rsel, freqs[3 * i], freqs[3 * i + 1], freqs[3 * i + 2]};
+        adapt_t S;
+        S.B = &B;
+        memcpy(S.x7, x7, sizeof(S.x7));
+        memcpy(S.w4, w4, sizeof(S.w4));
+        memcpy(S.w7, w7, sizeof(S.w7));
+        S.eps = eps; S.depth_max = depth_max; S.evals = 0; S.fail = 0;
+        cplx f13[13][16], I13[16];
+        for (int q = 0; q < 13; ++q) { integrand_x(&B, x13[q], f13[q]); S.evals++; }
+        for (int c = 0; c < 16; ++c) {
+            I13[c] = 0;
+            for (int q = 0; q < 13; ++q) I13[c] += w13[q] * f13[q][c];
+        }
+        S.Is = vnorm(I13);
+        if (S.Is == 0) S.Is = 1e-300;
+        cplx res[16];
+        adapt_rec(&S, -1.0, 1.0, f13[0], f13[12], 0, res);
+        double cr = chan_prefactor(r);
+        for (int c = 0; c < 16; ++c) out[(size_t)16 * i + c] = cr * res[c] / (2.0 * PI * I);
+        total += S.evals;
+        failed |= S.fail;
+    }
+    return failed ? -(int)(total > 0x7fffffff ? 0x7fffffff : total) : (int)(total > 0x7fffffff ? 0x7fffffff : total);
+}
