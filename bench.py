@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Benchmark: delivered bubble points/s of the one-loop Keldysh bubble in all three
+channels on the mixed-precision workload (K1 401, K2 101x101, K3 51^3, 4001
+Gauss-Lobatto nodes, complex64 vertex storage; U/Delta = 2, T = 0.05).
+
+One step = one bubble B_r(Gamma, Gamma) (Pi = G G) for r = a, p, t, every class
+(K1, K2, K2', K3) of each channel, from the seeded SIAM-shaped vertex resident in HBM.
+A delivered point is one (w, v, v') x one of the 16 Keldysh components of one class of
+one channel: 7,365,792 per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64] [--impl reference]
+
+Under torchrun (N > 1) every rank runs its own independent parameter point (weak
+scaling, no data-path collective); value = points of all ranks / max-over-ranks time.
+--impl reference times the FP64 CPU oracle (the reference arm of this method) on a
+bounded sample of the same workload.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+GRIDS = dict(n1=401, n2w=101, n2v=101, n3w=51, n3v=51)
+NQ, U, DELTA, T = 4001, 2.0, 1.0, 0.05
+WORKLOAD = "one-loop bubble a,p,t; K1 401, K2 101x101, K3 51^3, 16 Keldysh comps, Nq 4001, c64 vertex"
+METRIC = "bubble points/s (w.v.v'.Keldysh) at <=1e-6 rel err vs plain FP64 GPU"
+
+
+def class_points(g):
+    return {"K1": g["n1"] * 16, "K2": g["n2w"] * g["n2v"] * 16, "K2p": g["n2w"] * g["n2v"] * 16,
+            "K3": g["n3w"] * g["n3v"] ** 2 * 16}
+
+
+POINTS_PER_STEP = 3 * sum(class_points(GRIDS).values())
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+# FP64 FMA pipe: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (max SM clock);
+# measured 1.20 TFLOP/s with a register-resident FMA loop on this GPU model.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# --------------------------------------------------------------------------------------
+def oracle_rate(budget_s=12.0, seed=0):
+    """Oracle points/s on a stratified sample of the workload (all channels and classes,
+    sample sizes scaled to roughly budget_s of CPU time); returns (rate, description)."""
+    import seeded as S
+    from oracle import oracle as O
+    ch = S.seeded_vertex(GRIDS, U, seed=seed)
+    c64 = {c: tuple(a.astype(np.complex64).astype(np.complex128) for a in v) for c, v in ch.items()}
+    V = O.Vertex(GRIDS, U=U, has_R=True, channels=c64)
+    P = O.Prop(Delta=DELTA, T=T)
+    rng = np.random.default_rng(seed)
+    shapes = {"K1": (GRIDS["n1"],), "K2": (GRIDS["n2w"], GRIDS["n2v"]), "K2p": (GRIDS["n2w"], GRIDS["n2v"]),
+              "K3": (GRIDS["n3w"], GRIDS["n3v"], GRIDS["n3v"])}
+    cores = os.cpu_count() or 1
+    # calibrate on a few K3 points
+    idx = [tuple(int(rng.integers(0, n)) for n in shapes["K3"]) for _ in range(max(4, cores))]
+    t0 = time.perf_counter()
+    O.bubble_class(V, V, P, 0, "K3", NQ, idx=idx)
+    per_pt = (time.perf_counter() - t0) / len(idx)
+    n_k3 = int(max(cores, min(4096, budget_s / 3 / 1.6 / max(per_pt, 1e-6))))
+    n_small = max(cores, n_k3 // 4)
+    est, sampled, elapsed = 0.0, 0, 0.0
+    for r in range(3):
+        for cls, n in (("K1", n_small), ("K2", n_small), ("K2p", n_small), ("K3", n_k3)):
+            idx = [tuple(int(rng.integers(0, m)) for m in shapes[cls]) for _ in range(n)]
+            t0 = time.perf_counter()
+            O.bubble_class(V, V, P, r, cls, NQ, idx=idx)
+            dt = time.perf_counter() - t0
+            elapsed += dt
+            sampled += n
+            est += dt / n * int(np.prod(shapes[cls]))
+    rate = POINTS_PER_STEP / est
+    desc = ("stratified random sample of %d output points (%d per K3, %d per K1/K2/K2' class, 3 channels), "
+            "%.1f s CPU wall; whole-step time extrapolated per class" % (sampled, n_k3, n_small, elapsed))
+    return rate, cores, desc, elapsed
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    times = []
+    for _ in range(args.warmup):
+        oracle_rate(budget_s=3.0)
+    vals = []
+    for _ in range(args.steps):
+        rate, cores, desc, el = oracle_rate(budget_s=args.ref_budget)
+        vals.append(rate)
+        times.append(el)
+    v = float(np.median(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "points/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * POINTS_PER_STEP / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "points_per_step": POINTS_PER_STEP},
+            "cpu_baseline": {"value": v, "unit": "points/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------------------
+def contraction_flops(prec):
+    """Useful (complex-as-real) flops of the contractions per step by kernel family."""
+    g = GRIDS
+    out = {}
+    for r in range(3):
+        ns = 2 if r == 2 else 1
+        K = 4 * ns * NQ
+        for cls, nw, nL, nR in (("K1", g["n1"], 1, 1), ("K2", g["n2w"], g["n2v"], 1),
+                                ("K2p", g["n2w"], 1, g["n2v"]), ("K3", g["n3w"], g["n3v"], g["n3v"])):
+            out[(r, cls)] = 8.0 * nw * (4 * nL) * (4 * nR) * K
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64"])
+    ap.add_argument("--ref-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import seeded as S
+    from paper_2405_20996_gb300 import kb
+    from paper_2405_20996_gb300.engine import Engine
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    prec = args.precision
+    if prec == "auto":
+        prec = "mixed"
+    ch = S.seeded_vertex(GRIDS, U, seed=1000 + rank)        # each rank: its own parameter point
+    eng = Engine(GRIDS, NQ, device=local)
+    eng.set_model(DELTA, T)
+    eng.set_vertex(0, U=U, has_R=True, channels=ch, dtype=torch.complex64)
+    out_dt = torch.complex64 if prec == "mixed" else torch.complex128
+    eng.alloc_out(1, dtype=out_dt)
+    try:
+        eng.bubble(0, 0, 0, 1, precision=prec, class_mask=1)
+        torch.cuda.synchronize()
+    except kb.KBError as e:
+        if prec == "mixed" and e.status == kb.KB_ERR_UNSUPPORTED:
+            prec = "fp64"
+            out_dt = torch.complex128
+            eng.alloc_out(1, dtype=out_dt)
+        else:
+            raise
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for r in range(3):
+            eng.bubble(r, 0, 0, 1, precision=prec, stream=stream)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # 256 MB > 129 MB L2
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed before each, events on the launching stream ----
+    kb.kb_profile_enable(eng.ctx, True)
+    n0 = eng.launches()
+    clk = ClockSampler(local) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop() if clk else None
+    launches = eng.launches() - n0
+    prof = kb.kb_profile_read(eng.ctx)
+    kb.kb_profile_enable(eng.ctx, False)
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    ms_step = ms_max / args.steps
+    value = ws * POINTS_PER_STEP / (ms_step / 1e3)
+
+    # ---- end to end through the public API: pinned host inputs -> device -> bubbles -> host ----
+    host_in = {k: v.to("cpu").pin_memory() for k, v in eng.tensors[0].items()}
+    host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in eng.tensors[1].items()}
+    h2d = sum(v.numel() * v.element_size() for v in host_in.values())
+    d2h = sum(v.numel() * v.element_size() for v in host_out.values())
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k, v in host_in.items():
+            eng.tensors[0][k].copy_(v, non_blocking=True)
+        step()
+        for k, v in host_out.items():
+            v.copy_(eng.tensors[1][k], non_blocking=True)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    te = torch.tensor([sum(e2e_ms) / len(e2e_ms)], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_val = ws * POINTS_PER_STEP / (float(te.item()) / 1e3)
+
+    # ---- roofline of the dominant kernel (its CUDA-event time over the timed region) ----
+    hbm, bf16, src = peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    name, (dms, dcnt) = dom
+    share = dms / max(sum(v[0] for v in prof.values()), 1e-30)
+    fl = contraction_flops(prec)
+    roof = None
+    if name in ("k_zgemm_f64", "k_zgemm_skinny_f64"):
+        sel = [k for k in fl if (k[1] in ("K3", "K2p")) == (name == "k_zgemm_f64")]
+        work = sum(fl[k] for k in sel) * args.steps
+        ach = work / (dms / 1e3) / 1e12
+        roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "share": share,
+                "note": "FP64 FMA pipe peak derived from 152 SMs x 2 DFMA/clk x 2.07 GHz"}
+    else:
+        roof = {"kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None, "share": share}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, cores, desc, _ = oracle_rate(budget_s=args.ref_budget)
+        cpu = {"value": rate, "unit": "points/s", "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if prec == "mixed" else "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "precision": prec, "points_per_step": POINTS_PER_STEP,
+                           "l2": "flushed (256 MB write) before every timed step", "parallelism": "weak: one "
+                           "independent parameter point per GPU"},
+                "e2e": {"value": e2e_val, "unit": "points/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+                "kernels_ms": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
+                "peaks_source": src}
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,133 @@
+/*
+ * kb.h — C ABI of the GB300 Keldysh loop-bubble library (libkb.so).
+ *
+ * The library evaluates the loop bubble of the single-impurity Anderson model in the
+ * Keldysh formalism (KeldyshQFT paper, arXiv:2405.20996, Sec. II.E.1 "bubble_function"):
+ *
+ *     B_r(w, v, v') = c_r ∫ dv''/(2πi) Γ1(w, v, v'') Π_r(w, v'') Γ2(w, v'', v'),
+ *
+ * in the channels r = a, p, t (c_a = 1, c_p = 1/2 × 2 equal spin terms, c_t = −1 with the
+ * up-up/up-down spin sum), for all 16 Keldysh components, with the propagator pair
+ * Π = G G or Π-dot = G S + S G (Sec. II.D.5).  The v'' integral is the fixed composite
+ * 5-point Gauss-Lobatto rule in the grid's auxiliary variable x (Sec. II.G.4–II.G.5);
+ * vertices are the asymptotic classes K1, K2, K2', K3 per channel (Sec. II.D.1) read by
+ * linear interpolation in x (Sec. II.G.7).  Loop parts of the multiloop flow (Sec. III.C:
+ * one-loop Γ∘Π-dot∘Γ, left γ-dot∘Π∘Γ, right Γ∘Π∘γ-dot, central Γ∘Π∘(left part)) and the
+ * parquet Bethe–Salpeter step (Sec. III.B) are bubbles of different vertex slots and
+ * propagator pairs.
+ *
+ * Conventions: every vertex array holds the up-down spin component with the 16 Keldysh
+ * components innermost, ordered (a1' a2' | a1 a2) lexicographically with 1 = classical,
+ * 2 = quantum, component index c = 8 b1' + 4 b2' + 2 b1 + b2 (b = a − 1); complex numbers
+ * are interleaved (re, im).  Class layouts (row-major):
+ *     K1 [n1][16], K2 [n2w][n2v][16] (w, v), K2' [n2w][n2v][16] (w, v'),
+ *     K3 [n3w][n3v][n3v][16] (w, v, v').
+ * Grids: N points v_i = A tan(π x_i / 2), x_i = −1 + 2(i+1)/(N+1), the same map for every
+ * axis; classes read as 0 at x = ±1 (v = ±∞).
+ *
+ * Memory: all vertex pointers are DEVICE pointers owned by the caller, who keeps them
+ * alive and unmodified until the work of the next kb_bubble on the given stream is done.
+ * The library owns its context, its device tables and its workspace.
+ * Errors: every call returns a kb_status and never aborts; kb_last_error() describes the
+ * last failure.  Calls are asynchronous on the given cudaStream_t (NULL = legacy default
+ * stream).  There is no CPU fallback: without a CUDA device kb_create fails.
+ */
+#ifndef KB_H
+#define KB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kb_ctx kb_ctx;
+
+typedef enum {
+    KB_OK = 0,
+    KB_ERR_ARG = 1,          /* invalid argument (range, null, size mismatch) */
+    KB_ERR_STATE = 2,        /* call order violated (e.g. bubble before set_grids) */
+    KB_ERR_CUDA = 3,         /* a CUDA runtime call failed; see kb_last_error */
+    KB_ERR_OOM = 4,          /* device allocation failed */
+    KB_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+    KB_ERR_UNSUPPORTED = 6   /* combination not built (e.g. precision on this device) */
+} kb_status;
+
+enum { KB_CH_A = 0, KB_CH_P = 1, KB_CH_T = 2 };
+enum { KB_K1 = 0, KB_K2 = 1, KB_K2P = 2, KB_K3 = 3 };
+#define KB_MASK_ALL 0xFu
+enum { KB_PI_GG = 0, KB_PI_GS_SG = 1 };           /* Π = G G,  Π-dot = G S + S G */
+enum { KB_DT_C128 = 0, KB_DT_C64 = 1 };           /* complex double / complex float */
+enum { KB_PREC_FP64 = 0, KB_PREC_MIXED = 1 };     /* plain FP64 / FP32 gather + 3xTF32 tensor-core contraction */
+#define KB_MAX_SLOTS 16
+
+/* Frequency grids of the vertex classes and the quadrature (Sec. II.G.4, II.G.5).
+ * nq must be 4P + 1 (P panels of the composite 5-point Gauss-Lobatto rule). */
+typedef struct {
+    int n1;          /* K1 bosonic points */
+    int n2w, n2v;    /* K2 / K2' bosonic and fermionic points */
+    int n3w, n3v;    /* K3 bosonic and fermionic points */
+    int nq;          /* quadrature nodes on x in [-1, 1], endpoints included */
+    double A;        /* grid scale (v = A tan(pi x / 2)) */
+} kb_grid_desc;
+
+/* Create a context on CUDA device `device`.  Fails with KB_ERR_CUDA if there is none. */
+kb_status kb_create(kb_ctx **ctx, int device);
+kb_status kb_destroy(kb_ctx *ctx);
+
+/* Set the class grids and the quadrature (Sec. II.G.4–5).  Invalidates nothing owned by
+ * the caller; must precede kb_bubble. */
+kb_status kb_set_grids(kb_ctx *ctx, const kb_grid_desc *g);
+
+/* Model (Sec. I.A, III.A.1): flat hybridisation Δ, temperature T (T = 0 allowed), and the
+ * effective level eps (0 for the symmetric model with the Hartree shift absorbed).
+ * G^R(v) = 1/(v − eps + iΔ − Σ^R(v)), G^K = G^R [Σ^K − 2iΔ tanh(v/2T)] G^A, and the
+ * hybridisation-flow single-scale propagator S = ∂G/∂Δ at fixed Σ (Sec. III.C.3). */
+kb_status kb_set_model(kb_ctx *ctx, double Delta, double T, double eps);
+
+/* Optional dynamic self-energy (Sec. II.D.2): n_sig points on a tan grid of scale A_sig,
+ * interleaved complex double HOST arrays (copied); Σ reads 0 at x = ±1.  sigR == NULL
+ * resets Σ = 0.  sigK may be NULL (Σ^K = 0). */
+kb_status kb_set_self_energy(kb_ctx *ctx, int n_sig, double A_sig, const double *sigR, const double *sigK);
+
+/* Vertex slot `slot` (0 .. KB_MAX_SLOTS-1): the bare part R = Γ0 of the parquet
+ * approximation (Sec. I.B: +U/2 on components with an odd number of quantum indices)
+ * when has_R != 0, and no classes.  Classes are attached with kb_set_vertex_class. */
+kb_status kb_set_vertex(kb_ctx *ctx, int slot, int has_R, double U);
+
+/* Attach class `cls` of channel `channel` of slot `slot`: DEVICE pointer in the layout
+ * above, dtype KB_DT_C128 or KB_DT_C64 (all classes of a slot need not share a dtype).
+ * ptr == NULL detaches (the class reads as zero). */
+kb_status kb_set_vertex_class(kb_ctx *ctx, int slot, int channel, int cls, void *dev_ptr, int dtype);
+
+/* The bubble of channel `channel` with Γ1 = slot_left, Γ2 = slot_right and propagator pair
+ * pi_kind, written into the classes (class_mask bits 1 << KB_K1 .. 1 << KB_K3) of channel
+ * `channel` of slot out_slot:  out ← alpha · B + beta · out  (the paper adds, Sec. II.E.1;
+ * beta = 1 reproduces that).  Γ1 is the vertex carrying the external v (for t: the vertex on
+ * the external legs 1', 1).  precision: KB_PREC_FP64 (plain, every step in FP64) or
+ * KB_PREC_MIXED (FP32 gather, 3xTF32 tensor-core contraction with FP32 accumulation;
+ * propagators, Π and the tail in FP64).  The out slot's classes must be attached and must
+ * not alias the inputs. */
+kb_status kb_bubble(kb_ctx *ctx, int channel, int slot_left, int slot_right, int out_slot, int pi_kind,
+                    unsigned class_mask, double alpha, double beta, int precision, void *stream);
+
+/* Bytes of device workspace the library currently holds (grows on demand). */
+kb_status kb_workspace_bytes(kb_ctx *ctx, unsigned long long *bytes);
+
+/* Number of kernel launches issued by this context since creation (for accounting). */
+kb_status kb_launch_count(kb_ctx *ctx, unsigned long long *count);
+
+/* Kernel timing: when enabled, every kernel launch of this context is bracketed by CUDA
+ * events on its stream.  kb_profile_read aggregates the records per kernel name (after
+ * synchronising the device): index i in [0, n) where n is returned in *count when name is
+ * NULL; otherwise *name (static string), *ms (total device time) and *launches of entry i.
+ * Enabling clears earlier records. */
+kb_status kb_profile_enable(kb_ctx *ctx, int on);
+kb_status kb_profile_read(kb_ctx *ctx, int index, const char **name, double *ms, unsigned long long *launches,
+                          int *count);
+
+/* Human-readable description of the last error on this context (never NULL). */
+const char *kb_last_error(kb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KB_H */

@@ -1,0 +1,141 @@
+// Device helpers shared by the FP64 and mixed-precision kernels: complex FP64 arithmetic,
+// propagators (Sec. II.D.4, III.C.3), the x-grid stencil (Sec. II.G.4, II.G.7), channel
+// frequency maps (Sec. II.D.1) and the Pi table (Sec. II.D.5).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "kb_internal.h"
+
+namespace kb {
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cinv(double2 a) {
+    double d = a.x * a.x + a.y * a.y;
+    return make_double2(a.x / d, -a.y / d);
+}
+// z += a * b
+__device__ __forceinline__ void cfma(double2& z, double2 a, double2 b) {
+    z.x = fma(a.x, b.x, fma(-a.y, b.y, z.x));
+    z.y = fma(a.x, b.y, fma(a.y, b.x, z.y));
+}
+
+constexpr double KB_PI = 3.14159265358979323846;
+
+// Linear stencil in x on an n-point grid with zero-valued virtual nodes at x = -1 and x = 1.
+// Returns the lower node k in [-1, n-1] and the weight t of node k+1; non-finite v gives
+// k = -2 (the class contributes nothing).
+__device__ __forceinline__ int xstencil(double v, int n, double A, double& t) {
+    if (!isfinite(v)) return -2;
+    double x = (2.0 / KB_PI) * atan(v / A);
+    double s = (x + 1.0) * (0.5 * (n + 1));   // position in units of the spacing, X_k at s = k + 1
+    double fk = floor(s);
+    int k = (int)fk - 1;
+    if (k < -1) k = -1;
+    if (k > n - 1) k = n - 1;
+    double Xk = -1.0 + 2.0 * (k + 1) / (n + 1);
+    t = (x - Xk) * (0.5 * (n + 1));
+    return k;
+}
+
+// legs (v1', v2', v1, v2) from channel variables (w, v, vp) and back (Sec. II.D.1)
+__device__ __forceinline__ void legs_of(int r, double w, double v, double vp, double L[4]) {
+    if (r == KB_CH_A) { L[0] = v + 0.5 * w; L[3] = v - 0.5 * w; L[2] = vp + 0.5 * w; L[1] = vp - 0.5 * w; }
+    else if (r == KB_CH_P) { L[0] = 0.5 * w + v; L[1] = 0.5 * w - v; L[2] = 0.5 * w + vp; L[3] = 0.5 * w - vp; }
+    else { L[1] = vp + 0.5 * w; L[3] = vp - 0.5 * w; L[0] = v - 0.5 * w; L[2] = v + 0.5 * w; }
+}
+__device__ __forceinline__ void vars_of(int c, const double L[4], double& w, double& v, double& vp) {
+    if (c == KB_CH_A) { w = L[0] - L[3]; v = 0.5 * (L[0] + L[3]); vp = 0.5 * (L[2] + L[1]); }
+    else if (c == KB_CH_P) { w = L[0] + L[1]; v = 0.5 * (L[0] - L[1]); vp = 0.5 * (L[2] - L[3]); }
+    else { w = L[1] - L[3]; v = 0.5 * (L[0] + L[2]); vp = 0.5 * (L[1] + L[3]); }
+}
+
+__device__ __forceinline__ double tanh_T(double v, double T) {
+    if (T <= 0.0) return v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0);
+    return tanh(v / (2.0 * T));
+}
+
+// 2x2 Keldysh matrix of G (which = 0) or S (which = 1) at frequency v; index [a][a'],
+// 0 = classical, 1 = quantum: [[K, R], [A, 0]].
+__device__ inline void prop2x2(const Model& m, int which, double v, double2 P[2][2]) {
+    double2 sR = make_double2(0, 0), sK = make_double2(0, 0);
+    if (m.n_sig > 0) {
+        double t;
+        int k = xstencil(v, m.n_sig, m.A_sig, t);
+        if (k >= 0) { sR = cadd(sR, cscale(m.sigR[k], 1.0 - t)); sK = cadd(sK, cscale(m.sigK[k], 1.0 - t)); }
+        if (k >= -1 && k + 1 <= m.n_sig - 1) {
+            sR = cadd(sR, cscale(m.sigR[k + 1], t));
+            sK = cadd(sK, cscale(m.sigK[k + 1], t));
+        }
+    }
+    double2 GR = cinv(make_double2(v - m.eps - sR.x, m.Delta - sR.y));
+    double2 GA = cconj(GR);
+    double th = tanh_T(v, m.T);
+    double2 mid = make_double2(sK.x, sK.y - 2.0 * m.Delta * th);
+    if (which == 0) {
+        P[0][0] = cmul(cmul(GR, mid), GA);
+        P[0][1] = GR;
+        P[1][0] = GA;
+    } else {
+        double2 SR = cmul(make_double2(0.0, -1.0), cmul(GR, GR));
+        double2 SA = cconj(SR);
+        double2 t1 = cmul(cmul(SR, mid), GA);
+        double2 t2 = cmul(cmul(GR, make_double2(0.0, -2.0 * th)), GA);
+        double2 t3 = cmul(cmul(GR, mid), SA);
+        P[0][0] = cadd(cadd(t1, t2), t3);
+        P[0][1] = SR;
+        P[1][0] = SA;
+    }
+    P[1][1] = make_double2(0, 0);
+}
+
+// Pi table entry (all 16 [B][D]) for node j at bosonic w, scaled by
+// c_r * w_j * J_j / (2 pi i); at x_j = +-1 the limit of J * P(arg3) * P(arg4) is used:
+// J / v''^2 -> pi / (2A), v'' * G -> [[0, 1], [1, 0]] times the sign of v'' in the
+// argument, v'' * S -> 0 (Sec. II.G.6 tail reading).
+__device__ inline void pi_entry(const Model& m, const ChannelMaps& M, int r, int pi_kind, double A, double w,
+                                double xj, double wj, double2 out[16]) {
+    double cr = (r == KB_CH_T) ? -1.0 : 1.0;
+    double2 P3[2][2], P4[2][2], S3[2][2], S4[2][2];
+    double scale;
+    if (xj <= -1.0 || xj >= 1.0) {
+        double s3 = 1.0, s4 = (r == KB_CH_P) ? -1.0 : 1.0;
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                double g = (a != b) ? 1.0 : 0.0;
+                P3[a][b] = make_double2(g * s3, 0);
+                P4[a][b] = make_double2(g * s4, 0);
+                S3[a][b] = S4[a][b] = make_double2(0, 0);
+            }
+        scale = KB_PI / (2.0 * A);
+    } else {
+        double tn = tan(0.5 * KB_PI * xj);
+        double vpp = A * tn;
+        double a3, a4;
+        if (r == KB_CH_P) { a3 = 0.5 * w + vpp; a4 = 0.5 * w - vpp; }
+        else { a3 = vpp + 0.5 * w; a4 = vpp - 0.5 * w; }
+        prop2x2(m, 0, a3, P3);
+        prop2x2(m, 0, a4, P4);
+        if (pi_kind == KB_PI_GS_SG) { prop2x2(m, 1, a3, S3); prop2x2(m, 1, a4, S4); }
+        scale = 0.5 * A * KB_PI * (1.0 + tn * tn);
+    }
+    // c_r * w_j * scale / (2 pi i) = -i * (c_r w_j scale / 2 pi)
+    double f = cr * wj * scale / (2.0 * KB_PI);
+    for (int B = 0; B < 4; ++B)
+        for (int D = 0; D < 4; ++D) {
+            const int* q = M.piq[B][D];
+            double2 v;
+            if (pi_kind == KB_PI_GS_SG)
+                v = cadd(cmul(P3[q[0]][q[1]], S4[q[2]][q[3]]), cmul(S3[q[0]][q[1]], P4[q[2]][q[3]]));
+            else
+                v = cmul(P3[q[0]][q[1]], P4[q[2]][q[3]]);
+            out[4 * B + D] = make_double2(f * v.y, -f * v.x);   // times -i f
+        }
+}
+
+}  // namespace kb

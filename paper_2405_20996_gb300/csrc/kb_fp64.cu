@@ -1,0 +1,376 @@
+// Plain FP64 path: every step (propagators, Pi, vertex gather, contraction, scatter) in
+// double precision.  Structure per output class and chunk of bosonic frequencies:
+//   k_pi_table      Pi_r(w, v''_j) 4x4, times c_r w_j J_j / (2 pi i)          (rows a2, a3, a6)
+//   k_gather_f64    left tile  L[w][(v, A)][(s, j, B)]                         (row a4)
+//                   right tile R'[w][(v', C)][(s, j, B)] = sum_D Pi[B][D] R[D][C]
+//   k_zgemm_f64     G[w][(v, A)][(v', C)] = sum_k L[..][k] R'[..][k]           (row a5)
+//   k_scatter       out[w][v][v'][c(A, C)] = alpha G + beta out                 (row a7)
+#include <algorithm>
+#include <cstdio>
+
+#include "kb_dev.cuh"
+
+namespace kb {
+
+// ------------------------------------------------------------------------------------
+// Vertex evaluation in FP64 (16 Keldysh components at once)
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ double2 ld_c(const void* p, int dt, size_t i) {
+    if (dt == KB_DT_C128) return reinterpret_cast<const double2*>(p)[i];
+    float2 f = reinterpret_cast<const float2*>(p)[i];
+    return make_double2(f.x, f.y);
+}
+
+// acc[o] += f * class(c, k)(w, v, vp)[src(o)], src(o) = o or o with (a1 <-> a2) when swap12
+__device__ void acc_class_f64(const VertexDev& V, const Grids& G, int c, int k, double w, double v, double vp,
+                              double f, bool swap12, double2 acc[16]) {
+    const void* D = V.cls[c][k];
+    if (!D) return;
+    int dt = V.dt[c][k];
+    int nw, nv;
+    if (k == 0) { nw = G.n1; nv = 1; }
+    else if (k < 3) { nw = G.n2w; nv = G.n2v; }
+    else { nw = G.n3w; nv = G.n3v; }
+    double tw, tv = 0, tp = 0;
+    int kw = xstencil(w, nw, G.A, tw);
+    if (kw == -2) return;
+    int kv = 0, kp = 0;
+    if (k == 1 || k == 3) { kv = xstencil(v, nv, G.A, tv); if (kv == -2) return; }
+    if (k == 2) { kv = xstencil(vp, nv, G.A, tv); if (kv == -2) return; }
+    if (k == 3) { kp = xstencil(vp, nv, G.A, tp); if (kp == -2) return; }
+    int nb_v = (k == 0) ? 1 : 2, nb_p = (k == 3) ? 2 : 1;
+    for (int a = 0; a < 2; ++a) {
+        int iw = kw + a;
+        if (iw < 0 || iw > nw - 1) continue;
+        double fw = a ? tw : 1.0 - tw;
+        for (int b = 0; b < nb_v; ++b) {
+            int iv = kv + b;
+            double fv = 1.0;
+            if (k != 0) { if (iv < 0 || iv > nv - 1) continue; fv = b ? tv : 1.0 - tv; }
+            for (int e = 0; e < nb_p; ++e) {
+                int ip = kp + e;
+                double fp = 1.0;
+                if (k == 3) { if (ip < 0 || ip > nv - 1) continue; fp = e ? tp : 1.0 - tp; }
+                size_t base;
+                if (k == 0) base = (size_t)iw * 16;
+                else if (k < 3) base = ((size_t)iw * nv + iv) * 16;
+                else base = (((size_t)iw * nv + iv) * nv + ip) * 16;
+                double g = f * fw * fv * fp;
+#pragma unroll
+                for (int o = 0; o < 16; ++o) {
+                    int src = swap12 ? ((o & 12) | ((o & 1) << 1) | ((o >> 1) & 1)) : o;
+                    double2 val = ld_c(D, dt, base + src);
+                    acc[o].x = fma(g, val.x, acc[o].x);
+                    acc[o].y = fma(g, val.y, acc[o].y);
+                }
+            }
+        }
+    }
+}
+
+// Part of Gamma (spin up-down, or up-up when uu) relative to channel r at r-variables
+// (w, v, vp): zero part (R + K1_r + [K2'_r left | K2_r right]) or v-part
+// ([K2_r left | K2'_r right] + K3_r + the other channels at converted frequencies).
+// up-up: Gamma(1'2'|12) - Gamma(1'2'|21); exchanging legs 1, 2 maps a <-> t, p -> p with
+// own-channel variables (w, v, vp) -> (-w, v, vp) (a, t) or (w, v, -vp) (p).
+__device__ void vertex_part_f64(const VertexDev& V, const Grids& G, int r, bool uu, bool right, bool nupart,
+                                double w, double v, double vp, double2 out[16]) {
+#pragma unroll
+    for (int o = 0; o < 16; ++o) out[o] = make_double2(0, 0);
+    if (!nupart && !uu && V.has_R) {
+#pragma unroll
+        for (int o = 0; o < 16; ++o) out[o].x = (__popc(o) & 1) ? V.halfU : 0.0;
+    }
+    int k_free = right ? 1 : 2, k_dep = right ? 2 : 1;
+    int ka = nupart ? k_dep : 0, kb2 = nupart ? 3 : k_free;
+    int sr = (r == KB_CH_A) ? KB_CH_T : (r == KB_CH_T ? KB_CH_A : KB_CH_P);
+    double xw = (r == KB_CH_P) ? w : -w, xvp = (r == KB_CH_P) ? -vp : vp;
+    for (int q = 0; q < 2; ++q) {
+        int k = q ? kb2 : ka;
+        acc_class_f64(V, G, r, k, w, v, vp, 1.0, false, out);
+        if (uu) acc_class_f64(V, G, sr, k, xw, v, xvp, -1.0, true, out);
+    }
+    if (nupart) {
+        double L[4];
+        legs_of(r, w, v, vp, L);
+        for (int c = 0; c < 3; ++c) {
+            if (c == r) continue;
+            double wc, vc, pc;
+            vars_of(c, L, wc, vc, pc);
+            for (int k = 0; k < 4; ++k) acc_class_f64(V, G, c, k, wc, vc, pc, 1.0, false, out);
+        }
+        if (uu) {
+            double S[4] = {L[0], L[1], L[3], L[2]};
+            for (int c = 0; c < 3; ++c) {
+                if (c == sr) continue;
+                double wc, vc, pc;
+                vars_of(c, S, wc, vc, pc);
+                for (int k = 0; k < 4; ++k) acc_class_f64(V, G, c, k, wc, vc, pc, -1.0, true, out);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Kernels
+// ------------------------------------------------------------------------------------
+struct ClassJob {
+    int r, pi_kind, ns;          // channel, pair kind, spin terms (2 for t)
+    int nq;
+    int nw_chunk, w0;            // bosonic indices [w0, w0 + nw_chunk) of the class grid
+    int nw_grid;                 // size of the class's bosonic grid
+    int nL, nR;                  // external fermionic points of the left / right tile (1 = zero part)
+    int nvL_grid, nvR_grid;      // grid sizes of those axes
+    bool L_nu, R_nu;             // which part each side uses
+};
+
+__constant__ ChannelMaps c_maps[3];
+
+__device__ __forceinline__ double grid_freq(int i, int n, double A) {
+    return A * tan(0.5 * KB_PI * (-1.0 + 2.0 * (i + 1) / (double)(n + 1)));
+}
+
+// Pi[wl][j][16]
+__global__ void k_pi_table(Model m, ClassJob J, double A, const double* __restrict__ xq,
+                           const double* __restrict__ wq, double2* __restrict__ Pi) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int wl = blockIdx.y;
+    if (j >= J.nq || wl >= J.nw_chunk) return;
+    double w = grid_freq(J.w0 + wl, J.nw_grid, A);
+    double2 e[16];
+    pi_entry(m, c_maps[J.r], J.r, J.pi_kind, A, w, xq[j], wq[j], e);
+    double2* o = Pi + ((size_t)wl * J.nq + j) * 16;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) o[i] = e[i];
+}
+
+// One thread per (w, external v, s, j).  Writes the 4x4 block of the tile.
+template <bool RIGHT>
+__global__ void k_gather_f64(VertexDev V, Grids G, ClassJob J, const double* __restrict__ xq,
+                             const double2* __restrict__ Pi, double2* __restrict__ tile) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int s = blockIdx.y % J.ns;
+    int vi = blockIdx.y / J.ns;
+    int wl = blockIdx.z;
+    int nrow = RIGHT ? J.nR : J.nL;
+    if (j >= J.nq || vi >= nrow) return;
+    const ChannelMaps& M = c_maps[J.r];
+    bool nupart = RIGHT ? J.R_nu : J.L_nu;
+    int nvg = RIGHT ? J.nvR_grid : J.nvL_grid;
+    double w = grid_freq(J.w0 + wl, J.nw_grid, G.A);
+    double vext = nupart ? grid_freq(vi, nvg, G.A) : 0.0;
+    double xj = xq[j];
+    double vpp = (xj <= -1.0) ? -INFINITY : (xj >= 1.0 ? INFINITY : G.A * tan(0.5 * KB_PI * xj));
+    // spin of this term: t channel left s=0 up-up, s=1 up-down; right s=0 up-down, s=1 up-up
+    bool uu = (J.r == KB_CH_T) && (RIGHT ? (s == 1) : (s == 0));
+    double2 g[16];
+    if (RIGHT) vertex_part_f64(V, G, J.r, uu, true, nupart, w, vpp, vext, g);
+    else vertex_part_f64(V, G, J.r, uu, false, nupart, w, vext, vpp, g);
+    size_t K = (size_t)4 * J.ns * J.nq;
+    size_t kcol = ((size_t)s * J.nq + j) * 4;
+    size_t rowbase = ((size_t)wl * 4 * nrow + (size_t)vi * 4);
+    if (!RIGHT) {
+        for (int A = 0; A < 4; ++A) {
+            double2* dst = tile + (rowbase + A) * K + kcol;
+            for (int B = 0; B < 4; ++B) dst[B] = g[M.cL[A][B]];
+        }
+    } else {
+        const double2* P = Pi + ((size_t)wl * J.nq + j) * 16;
+        double2 pm[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) pm[i] = P[i];
+        for (int C = 0; C < 4; ++C) {
+            double2* dst = tile + (rowbase + C) * K + kcol;
+            for (int B = 0; B < 4; ++B) {
+                double2 acc = make_double2(0, 0);
+#pragma unroll
+                for (int D = 0; D < 4; ++D) cfma(acc, pm[4 * B + D], g[M.cR[D][C]]);
+                dst[B] = acc;
+            }
+        }
+    }
+}
+
+// Batched complex GEMM G[b][m][n] = sum_k A[b][m][k] * B[b][n][k] (both K-contiguous).
+// 32x32 output tile, 256 threads, each 2x2 outputs; K chunks of 16 through shared memory.
+__global__ void __launch_bounds__(256) k_zgemm_f64(const double2* __restrict__ Am, const double2* __restrict__ Bm,
+                                                   double2* __restrict__ Cm, int M, int N, int K) {
+    __shared__ double2 sA[16][33], sB[16][33];
+    int b = blockIdx.z;
+    int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+    const double2* A = Am + (size_t)b * M * K;
+    const double2* B = Bm + (size_t)b * N * K;
+    int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    double2 acc[2][2] = {};
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int i = threadIdx.x; i < 32 * 16; i += 256) {
+            int row = i / 16, kk = i % 16;
+            int gm = m0 + row, gn = n0 + row, gk = k0 + kk;
+            sA[kk][row] = (gm < M && gk < K) ? A[(size_t)gm * K + gk] : make_double2(0, 0);
+            sB[kk][row] = (gn < N && gk < K) ? B[(size_t)gn * K + gk] : make_double2(0, 0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            double2 a0 = sA[kk][ty], a1 = sA[kk][ty + 16];
+            double2 b0 = sB[kk][tx], b1 = sB[kk][tx + 16];
+            cfma(acc[0][0], a0, b0);
+            cfma(acc[0][1], a0, b1);
+            cfma(acc[1][0], a1, b0);
+            cfma(acc[1][1], a1, b1);
+        }
+        __syncthreads();
+    }
+    for (int i = 0; i < 2; ++i)
+        for (int jj = 0; jj < 2; ++jj) {
+            int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * jj;
+            if (gm < M && gn < N) Cm[((size_t)b * M + gm) * N + gn] = acc[i][jj];
+        }
+}
+
+// Skinny GEMM for N <= 4 (zero-part right tile): one warp per row m.
+__global__ void k_zgemm_skinny_f64(const double2* __restrict__ Am, const double2* __restrict__ Bm,
+                                   double2* __restrict__ Cm, int M, int N, int K, int batch) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= M * batch) return;
+    int b = warp / M, m = warp % M;
+    const double2* a = Am + ((size_t)b * M + m) * K;
+    const double2* B = Bm + (size_t)b * N * K;
+    double2 acc[4] = {};
+    for (int k = lane; k < K; k += 32) {
+        double2 av = a[k];
+        for (int n = 0; n < N; ++n) cfma(acc[n], av, B[(size_t)n * K + k]);
+    }
+    for (int n = 0; n < N; ++n)
+        for (int o = 16; o > 0; o >>= 1) {
+            acc[n].x += __shfl_xor_sync(0xffffffffu, acc[n].x, o);
+            acc[n].y += __shfl_xor_sync(0xffffffffu, acc[n].y, o);
+        }
+    if (lane == 0)
+        for (int n = 0; n < N; ++n) Cm[((size_t)b * M + m) * N + n] = acc[n];
+}
+
+// out class array <- alpha * G + beta * out; G[wl][(vL, A)][(vR, C)]
+__global__ void k_scatter(ClassJob J, int cls, const double2* __restrict__ Gm, void* out, int dt, double alpha,
+                          double beta) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)J.nw_chunk * J.nL * J.nR * 16;
+    if (idx >= total) return;
+    int o = idx % 16;
+    size_t rest = idx / 16;
+    int vR = rest % J.nR;
+    rest /= J.nR;
+    int vL = rest % J.nL;
+    int wl = rest / J.nL;
+    // find (A, C) with cO[A][C] == o
+    const ChannelMaps& M = c_maps[J.r];
+    int A = 0, C = 0;
+    for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 4; ++c)
+            if (M.cO[a][c] == o) { A = a; C = c; }
+    int Mrows = 4 * J.nL, Ncols = 4 * J.nR;
+    double2 gv = Gm[((size_t)wl * Mrows + 4 * vL + A) * Ncols + 4 * vR + C];
+    // output element index in the class layout
+    size_t w = J.w0 + wl, e;
+    if (cls == KB_K1) e = w * 16 + o;
+    else if (cls == KB_K2) e = (w * J.nL + vL) * 16 + o;
+    else if (cls == KB_K2P) e = (w * J.nR + vR) * 16 + o;
+    else e = ((w * J.nL + vL) * J.nR + vR) * 16 + o;
+    if (dt == KB_DT_C128) {
+        double2* p = reinterpret_cast<double2*>(out) + e;
+        double2 old = beta != 0.0 ? *p : make_double2(0, 0);
+        *p = make_double2(alpha * gv.x + beta * old.x, alpha * gv.y + beta * old.y);
+    } else {
+        float2* p = reinterpret_cast<float2*>(out) + e;
+        float2 old = beta != 0.0 ? *p : make_float2(0, 0);
+        *p = make_float2((float)(alpha * gv.x + beta * old.x), (float)(alpha * gv.y + beta * old.y));
+    }
+}
+
+}  // namespace kb
+
+using namespace kb;
+
+static bool g_maps_uploaded[64] = {};
+
+static kb_status upload_maps(kb_ctx* ctx) {
+    if (g_maps_uploaded[ctx->device]) return KB_OK;
+    ChannelMaps h[3] = {channel_maps(0), channel_maps(1), channel_maps(2)};
+    KB_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_maps, h, sizeof(h)));
+    g_maps_uploaded[ctx->device] = true;
+    return KB_OK;
+}
+
+// Shapes of one output class: rows of the left tile, rows of the right tile, grids.
+void class_shape(const Grids& g, int cls, int& nw, int& nL, int& nR, int& nvg) {
+    if (cls == KB_K1) { nw = g.n1; nL = 1; nR = 1; nvg = 1; }
+    else if (cls == KB_K2) { nw = g.n2w; nL = g.n2v; nR = 1; nvg = g.n2v; }
+    else if (cls == KB_K2P) { nw = g.n2w; nL = 1; nR = g.n2v; nvg = g.n2v; }
+    else { nw = g.n3w; nL = g.n3v; nR = g.n3v; nvg = g.n3v; }
+}
+
+kb_status kb_bubble_fp64(kb_ctx* ctx, int r, int sl, int sr, int so, int pi_kind, unsigned mask, double alpha,
+                         double beta, cudaStream_t st) {
+    kb_status s = upload_maps(ctx);
+    if (s != KB_OK) return s;
+    const Grids& g = ctx->g;
+    int ns = (r == KB_CH_T) ? 2 : 1;
+    size_t K = (size_t)4 * ns * g.nq;
+    for (int cls = 0; cls < 4; ++cls) {
+        if (!((mask >> cls) & 1)) continue;
+        int nw, nL, nR, nvg;
+        class_shape(g, cls, nw, nL, nR, nvg);
+        size_t per_w = (size_t)g.nq * 16 * sizeof(double2) + (size_t)4 * nL * K * sizeof(double2) +
+                       (size_t)4 * nR * K * sizeof(double2) + (size_t)16 * nL * nR * sizeof(double2);
+        int chunk = (int)std::max<size_t>(1, std::min<size_t>(nw, ctx->ws_limit / per_w));
+        s = kb_ensure_workspace(ctx, per_w * chunk);
+        if (s != KB_OK) return s;
+        char* base = static_cast<char*>(ctx->ws.ptr);
+        double2* Pi = reinterpret_cast<double2*>(base);
+        double2* Lt = Pi + (size_t)chunk * g.nq * 16;
+        double2* Rt = Lt + (size_t)chunk * 4 * nL * K;
+        double2* Gm = Rt + (size_t)chunk * 4 * nR * K;
+        for (int w0 = 0; w0 < nw; w0 += chunk) {
+            ClassJob J;
+            J.r = r; J.pi_kind = pi_kind; J.ns = ns; J.nq = g.nq;
+            J.nw_chunk = std::min(chunk, nw - w0); J.w0 = w0; J.nw_grid = nw;
+            J.nL = nL; J.nR = nR; J.nvL_grid = nvg; J.nvR_grid = nvg;
+            J.L_nu = (cls == KB_K2 || cls == KB_K3);
+            J.R_nu = (cls == KB_K2P || cls == KB_K3);
+            {
+                KB_LAUNCH(ctx, st, "k_pi_table");
+                dim3 bp((g.nq + 127) / 128, J.nw_chunk);
+                k_pi_table<<<bp, 128, 0, st>>>(ctx->m, J, g.A, ctx->d_xq, ctx->d_wq, Pi);
+            }
+            {
+                KB_LAUNCH(ctx, st, "k_gather_f64_left");
+                dim3 bl((g.nq + 127) / 128, nL * ns, J.nw_chunk);
+                k_gather_f64<false><<<bl, 128, 0, st>>>(ctx->slots[sl], g, J, ctx->d_xq, Pi, Lt);
+            }
+            {
+                KB_LAUNCH(ctx, st, "k_gather_f64_right");
+                dim3 br((g.nq + 127) / 128, nR * ns, J.nw_chunk);
+                k_gather_f64<true><<<br, 128, 0, st>>>(ctx->slots[sr], g, J, ctx->d_xq, Pi, Rt);
+            }
+            int Mr = 4 * nL, Nc = 4 * nR;
+            if (Nc <= 4) {
+                KB_LAUNCH(ctx, st, "k_zgemm_skinny_f64");
+                int warps = Mr * J.nw_chunk;
+                k_zgemm_skinny_f64<<<(warps * 32 + 255) / 256, 256, 0, st>>>(Lt, Rt, Gm, Mr, Nc, (int)K, J.nw_chunk);
+            } else {
+                KB_LAUNCH(ctx, st, "k_zgemm_f64");
+                dim3 bg((Nc + 31) / 32, (Mr + 31) / 32, J.nw_chunk);
+                k_zgemm_f64<<<bg, 256, 0, st>>>(Lt, Rt, Gm, Mr, Nc, (int)K);
+            }
+            {
+                KB_LAUNCH(ctx, st, "k_scatter");
+                size_t tot = (size_t)J.nw_chunk * nL * nR * 16;
+                k_scatter<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+                    J, cls, Gm, const_cast<void*>(ctx->slots[so].cls[r][cls]), ctx->slots[so].dt[r][cls], alpha, beta);
+            }
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) { ctx->err = std::string("fp64 launch: ") + cudaGetErrorString(e); return KB_ERR_CUDA; }
+        }
+    }
+    return KB_OK;
+}

@@ -1,0 +1,113 @@
+// Internal types shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/kb.h"
+
+namespace kb {
+
+// Class grids and quadrature size; every axis uses v = A tan(pi x / 2) with
+// x_i = -1 + 2 (i + 1) / (N + 1) (Sec. II.G.4).
+struct Grids {
+    int n1, n2w, n2v, n3w, n3v, nq;
+    double A;
+};
+
+// One vertex slot as the kernels see it: bare part and per channel/class pointers.
+struct VertexDev {
+    const void* cls[3][4];   // [channel][K1, K2, K2', K3], nullptr = absent
+    int dt[3][4];            // KB_DT_C128 / KB_DT_C64
+    int has_R;
+    double halfU;            // U / 2
+};
+
+// Propagator model (Sec. III.A.1, III.C.3).
+struct Model {
+    double Delta, T, eps;
+    int n_sig;
+    double A_sig;
+    const double2* sigR;     // device, n_sig entries or nullptr
+    const double2* sigK;
+};
+
+// Keldysh index maps of channel r (matrix form of the 16-component contraction):
+//   left tile  L[A][B] = Gamma1^{cL[A][B]},  right tile R[D][C] = Gamma2^{cR[D][C]},
+//   output     B[A][C] -> component cO[A][C];
+//   Pi[B][D] = P^{b3|b3'}(arg3) P^{b4|b4'}(arg4) with (b3, b3', b4, b4') = piq[B][D].
+struct ChannelMaps {
+    int cL[4][4], cR[4][4], cO[4][4];
+    int piq[4][4][4];
+};
+ChannelMaps channel_maps(int r);
+
+// Workspace / bookkeeping owned by a context.
+struct Workspace {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace kb
+
+struct kb_prof_rec {
+    const char* name;
+    cudaEvent_t a, b;
+};
+
+struct kb_ctx {
+    int device = 0;
+    bool grids_set = false, model_set = false;
+    kb::Grids g{};
+    kb::Model m{};
+    double* d_xq = nullptr;   // quadrature nodes x_j (device, nq)
+    double* d_wq = nullptr;   // weights w_j (device, nq)
+    double2* d_sig = nullptr; // Sigma tables (2 * n_sig)
+    kb::VertexDev slots[KB_MAX_SLOTS];
+    bool slot_set[KB_MAX_SLOTS];
+    kb::Workspace ws;
+    unsigned long long launches = 0;
+    std::string err;
+    size_t ws_limit = 0;
+    bool prof_on = false;
+    std::vector<kb_prof_rec> prof;
+};
+
+// Bracket a launch with timing events when profiling is on.
+struct KbProfScope {
+    kb_ctx* c;
+    cudaStream_t s;
+    kb_prof_rec rec{};
+    KbProfScope(kb_ctx* ctx, cudaStream_t st, const char* name) : c(ctx), s(st) {
+        ++c->launches;
+        if (!c->prof_on) return;
+        rec.name = name;
+        cudaEventCreate(&rec.a);
+        cudaEventCreate(&rec.b);
+        cudaEventRecord(rec.a, s);
+    }
+    ~KbProfScope() {
+        if (!c->prof_on) return;
+        cudaEventRecord(rec.b, s);
+        c->prof.push_back(rec);
+    }
+};
+#define KB_LAUNCH(ctx, st, name) KbProfScope kb_prof_scope_##__LINE__(ctx, st, name)
+
+// error helper
+#define KB_CUDA_TRY(ctx, call)                                                              \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                \
+            return e_ == cudaErrorMemoryAllocation ? KB_ERR_OOM : KB_ERR_CUDA;              \
+        }                                                                                   \
+    } while (0)
+
+// launchers implemented in kb_fp64.cu / kb_mixed.cu
+kb_status kb_bubble_fp64(kb_ctx* ctx, int r, int sl, int sr, int so, int pi_kind, unsigned mask, double alpha,
+                         double beta, cudaStream_t st);
+kb_status kb_bubble_mixed(kb_ctx* ctx, int r, int sl, int sr, int so, int pi_kind, unsigned mask, double alpha,
+                          double beta, cudaStream_t st);
+kb_status kb_ensure_workspace(kb_ctx* ctx, size_t bytes);

@@ -1,0 +1,78 @@
+"""PyTorch-facing helper around the C ABI: owns the device tensors of the vertex slots
+(PyTorch is used for device memory and streams only) and calls kb_bubble."""
+
+import torch
+
+from . import kb
+
+CLASS_NAMES = ("K1", "K2", "K2p", "K3")
+DT = {torch.complex128: kb.KB_DT_C128, torch.complex64: kb.KB_DT_C64}
+PREC = {"fp64": kb.KB_PREC_FP64, "mixed": kb.KB_PREC_MIXED}
+
+
+class Engine:
+    def __init__(self, grids, nq, A=5.0, device=0):
+        self.device = torch.device("cuda", device)
+        self.grids = dict(grids)
+        self.nq, self.A = nq, A
+        self.ctx = kb.kb_create(device)
+        g = self.grids
+        kb.kb_set_grids(self.ctx, g["n1"], g["n2w"], g["n2v"], g["n3w"], g["n3v"], nq, A)
+        self.tensors = {}
+
+    def close(self):
+        if self.ctx is not None:
+            kb.kb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def class_shapes(self):
+        g = self.grids
+        return {"K1": (g["n1"], 16), "K2": (g["n2w"], g["n2v"], 16), "K2p": (g["n2w"], g["n2v"], 16),
+                "K3": (g["n3w"], g["n3v"], g["n3v"], 16)}
+
+    def set_model(self, Delta, T, eps=0.0):
+        kb.kb_set_model(self.ctx, Delta, T, eps)
+
+    def set_self_energy(self, sigR=None, sigK=None, A_sig=5.0):
+        kb.kb_set_self_energy(self.ctx, sigR, sigK, A_sig)
+
+    def set_vertex(self, slot, U=0.0, has_R=False, channels=None, dtype=torch.complex128):
+        """channels: {channel: (K1, K2, K2p, K3)} arrays (numpy or torch; None = absent)."""
+        kb.kb_set_vertex(self.ctx, slot, has_R, U)
+        self.tensors[slot] = {}
+        for ch, classes in (channels or {}).items():
+            for k, arr in enumerate(classes):
+                if arr is None:
+                    continue
+                t = torch.as_tensor(arr).to(device=self.device, dtype=dtype).contiguous()
+                self.attach(slot, ch, k, t)
+
+    def attach(self, slot, ch, k, t):
+        assert t.is_cuda and t.is_contiguous() and t.dtype in DT
+        self.tensors.setdefault(slot, {})[(ch, k)] = t
+        kb.kb_set_vertex_class(self.ctx, slot, ch, k, t.data_ptr(), DT[t.dtype])
+
+    def alloc_out(self, slot, channels=(0, 1, 2), dtype=torch.complex128, classes=(0, 1, 2, 3)):
+        kb.kb_set_vertex(self.ctx, slot, False, 0.0)
+        self.tensors[slot] = {}
+        sh = self.class_shapes()
+        for ch in channels:
+            for k in classes:
+                self.attach(slot, ch, k, torch.zeros(sh[CLASS_NAMES[k]], dtype=dtype, device=self.device))
+
+    def out(self, slot, ch):
+        return {CLASS_NAMES[k]: t for (c, k), t in self.tensors[slot].items() if c == ch}
+
+    def bubble(self, channel, left, right, out, pi_kind=kb.KB_PI_GG, class_mask=kb.KB_MASK_ALL, alpha=1.0,
+               beta=0.0, precision="fp64", stream=None):
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        kb.kb_bubble(self.ctx, channel, left, right, out, pi_kind, class_mask, alpha, beta, PREC[precision], st)
+
+    def launches(self):
+        return kb.kb_launch_count(self.ctx)

@@ -1,0 +1,157 @@
+"""Thin ctypes binding of libkb (include/kb.h): the same entry points, argument
+marshalling only.  Every step of the bubble runs in the library's CUDA kernels; there is
+no CPU fallback — if libkb.so cannot be built or loaded, importing the functions fails.
+"""
+
+import ctypes as C
+import os
+import re
+
+from . import build as _build
+
+KB_OK, KB_ERR_ARG, KB_ERR_STATE, KB_ERR_CUDA, KB_ERR_OOM, KB_ERR_TIMEOUT, KB_ERR_UNSUPPORTED = range(7)
+KB_CH_A, KB_CH_P, KB_CH_T = 0, 1, 2
+KB_K1, KB_K2, KB_K2P, KB_K3 = 0, 1, 2, 3
+KB_MASK_ALL = 0xF
+KB_PI_GG, KB_PI_GS_SG = 0, 1
+KB_DT_C128, KB_DT_C64 = 0, 1
+KB_PREC_FP64, KB_PREC_MIXED = 0, 1
+KB_MAX_SLOTS = 16
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "kb.h")
+
+
+class kb_grid_desc(C.Structure):
+    _fields_ = [("n1", C.c_int), ("n2w", C.c_int), ("n2v", C.c_int), ("n3w", C.c_int), ("n3v", C.c_int),
+                ("nq", C.c_int), ("A", C.c_double)]
+
+
+class KBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("kb status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+_SIGS = {
+    "kb_create": [C.POINTER(C.c_void_p), C.c_int],
+    "kb_destroy": [C.c_void_p],
+    "kb_set_grids": [C.c_void_p, C.POINTER(kb_grid_desc)],
+    "kb_set_model": [C.c_void_p, C.c_double, C.c_double, C.c_double],
+    "kb_set_self_energy": [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p],
+    "kb_set_vertex": [C.c_void_p, C.c_int, C.c_int, C.c_double],
+    "kb_set_vertex_class": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int],
+    "kb_bubble": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_double, C.c_double,
+                  C.c_int, C.c_void_p],
+    "kb_workspace_bytes": [C.c_void_p, C.POINTER(C.c_ulonglong)],
+    "kb_launch_count": [C.c_void_p, C.POINTER(C.c_ulonglong)],
+    "kb_profile_enable": [C.c_void_p, C.c_int],
+    "kb_profile_read": [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
+                        C.POINTER(C.c_ulonglong), C.POINTER(C.c_int)],
+}
+
+
+def lib(path=None):
+    """Load libkb.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        p = path or _build.build()
+        L = C.CDLL(p)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.kb_last_error.argtypes = [C.c_void_p]
+        L.kb_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    """Entry points declared in include/kb.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:kb_status|const char \*)\s*(kb_\w+)\s*\(", txt, re.M)))
+
+
+def _check(ctx, st):
+    if st != KB_OK:
+        msg = lib().kb_last_error(ctx).decode() if ctx else ""
+        raise KBError(st, msg)
+
+
+# ---- same-name wrappers --------------------------------------------------------------
+def kb_create(device=0):
+    ctx = C.c_void_p()
+    st = lib().kb_create(C.byref(ctx), device)
+    if st != KB_OK:
+        raise KBError(st, "kb_create failed (no CUDA device %d?)" % device)
+    return ctx
+
+
+def kb_destroy(ctx):
+    _check(None, lib().kb_destroy(ctx))
+
+
+def kb_set_grids(ctx, n1, n2w, n2v, n3w, n3v, nq, A=5.0):
+    g = kb_grid_desc(n1, n2w, n2v, n3w, n3v, nq, A)
+    _check(ctx, lib().kb_set_grids(ctx, C.byref(g)))
+
+
+def kb_set_model(ctx, Delta, T, eps=0.0):
+    _check(ctx, lib().kb_set_model(ctx, Delta, T, eps))
+
+
+def kb_set_self_energy(ctx, sigR=None, sigK=None, A_sig=5.0):
+    import numpy as np
+    if sigR is None:
+        _check(ctx, lib().kb_set_self_energy(ctx, 0, A_sig, None, None))
+        return
+    r = np.ascontiguousarray(np.asarray(sigR, dtype=np.complex128))
+    k = None if sigK is None else np.ascontiguousarray(np.asarray(sigK, dtype=np.complex128))
+    _check(ctx, lib().kb_set_self_energy(ctx, len(r), A_sig, r.ctypes.data, None if k is None else k.ctypes.data))
+
+
+def kb_set_vertex(ctx, slot, has_R, U=0.0):
+    _check(ctx, lib().kb_set_vertex(ctx, slot, int(bool(has_R)), float(U)))
+
+
+def kb_set_vertex_class(ctx, slot, channel, cls, dev_ptr, dtype):
+    _check(ctx, lib().kb_set_vertex_class(ctx, slot, channel, cls, dev_ptr, dtype))
+
+
+def kb_bubble(ctx, channel, slot_left, slot_right, out_slot, pi_kind=KB_PI_GG, class_mask=KB_MASK_ALL,
+              alpha=1.0, beta=0.0, precision=KB_PREC_FP64, stream=0):
+    _check(ctx, lib().kb_bubble(ctx, channel, slot_left, slot_right, out_slot, pi_kind, class_mask, alpha, beta,
+                                precision, stream))
+
+
+def kb_workspace_bytes(ctx):
+    v = C.c_ulonglong()
+    _check(ctx, lib().kb_workspace_bytes(ctx, C.byref(v)))
+    return v.value
+
+
+def kb_launch_count(ctx):
+    v = C.c_ulonglong()
+    _check(ctx, lib().kb_launch_count(ctx, C.byref(v)))
+    return v.value
+
+
+def kb_last_error(ctx):
+    return lib().kb_last_error(ctx).decode()
+
+
+def kb_profile_enable(ctx, on=True):
+    _check(ctx, lib().kb_profile_enable(ctx, int(bool(on))))
+
+
+def kb_profile_read(ctx):
+    """{kernel name: (total ms, launches)} of the records since profiling was enabled."""
+    n = C.c_int()
+    _check(ctx, lib().kb_profile_read(ctx, 0, None, None, None, C.byref(n)))
+    out = {}
+    for i in range(n.value):
+        nm, ms, cnt = C.c_char_p(), C.c_double(), C.c_ulonglong()
+        _check(ctx, lib().kb_profile_read(ctx, i, C.byref(nm), C.byref(ms), C.byref(cnt), None))
+        out[nm.value.decode()] = (ms.value, cnt.value)
+    return out
