@@ -93,6 +93,15 @@ kb_status kb_set_self_energy(kb_ctx *ctx, int n_sig, double A_sig, const double 
  * when has_R != 0, and no classes.  Classes are attached with kb_set_vertex_class. */
 kb_status kb_set_vertex(kb_ctx *ctx, int slot, int has_R, double U);
 
+/* Channels that are part of the vertex in slot `slot` (bit 1 << KB_CH_x; default all
+ * three after kb_set_vertex).  The up-up spin component needed by the t channel is built
+ * channel by channel (SU(2) + crossing, Sec. II.G.3): gamma_c^uu(1'2'|12) =
+ * gamma_c^ud(1'2'|12) - gamma_sigma(c)^ud(1'2'|21), sigma: a <-> t, p -> p, so the data of
+ * an excluded channel is still read as the crossing partner of an included one.  Use it
+ * for the multiloop corrections, whose vertex is the sum over the channels other than r
+ * (Sec. III.C). */
+kb_status kb_set_vertex_channels(kb_ctx *ctx, int slot, unsigned mask);
+
 /* Attach class `cls` of channel `channel` of slot `slot`: DEVICE pointer in the layout
  * above, dtype KB_DT_C128 or KB_DT_C64 (all classes of a slot need not share a dtype).
  * ptr == NULL detaches (the class reads as zero). */

@@ -86,7 +86,8 @@ typedef struct {
     double A;                      /* grid scale */
     double U;                      /* bare vertex strength; used only if has_R */
     int has_R;
-    const cplx *K1[3], *K2[3], *K2p[3], *K3[3];   /* NULL = class absent */
+    int mask;                      /* channels included in the vertex (bit c); see parts_uu */
+    const cplx *K1[3], *K2[3], *K2p[3], *K3[3];   /* NULL = class absent (reads 0) */
 } ovtx;
 
 /* Component index of (a1', a2' | a1, a2), each given as 0 (classical) / 1 (quantum). */
@@ -150,21 +151,20 @@ static void chan_from(int r, const double L[4], double *w, double *v, double *vp
 }
 
 /* Parts of the up-down vertex relative to channel r, evaluated at r-variables
- * (w, v, vp) (v or vp may be +-inf): R, own classes k = 0..3, and the sum of the
- * two other channels (evaluated at the converted frequencies). */
+ * (w, v, vp) (v or vp may be +-inf): R, own classes k = 0..3 (if r is included), and the
+ * sum of the other included channels (evaluated at the converted frequencies). */
 typedef struct { cplx R[16]; cplx own[4][16]; cplx other[16]; } vparts;
 
-static void parts_ud(const ovtx *V, int r, double w, double v, double vp, int want_own, int want_other,
-                     vparts *P) {
+static void parts_ud(const ovtx *V, int r, double w, double v, double vp, int want_other, vparts *P) {
     memset(P, 0, sizeof(*P));
     bare_vertex(V, P->R);
-    if (want_own)
+    if ((V->mask >> r) & 1)
         for (int k = 0; k < 4; ++k) add_class(V, r, k, w, v, vp, 1.0, P->own[k]);
     if (want_other) {
         double L[4];
         legs_from(r, w, v, vp, L);
         for (int c = 0; c < 3; ++c) {
-            if (c == r) continue;
+            if (c == r || !((V->mask >> c) & 1)) continue;
             double wc, vc, pc;
             chan_from(c, L, &wc, &vc, &pc);
             for (int k = 0; k < 4; ++k) add_class(V, c, k, wc, vc, pc, 1.0, P->other);
@@ -172,36 +172,38 @@ static void parts_ud(const ovtx *V, int r, double w, double v, double vp, int wa
     }
 }
 
-/* Parts of the up-up vertex, Gamma_uu(1'2'|12) = Gamma_ud(1'2'|12) - Gamma_ud(1'2'|21),
- * split relative to channel r.  Exchanging legs 1 and 2 maps channel a <-> t, p -> p, so
- * the own-channel classes of the exchanged term come from channel sigma(r). */
-static void parts_uu(const ovtx *V, int r, double w, double v, double vp, int want_own, int want_other,
-                     vparts *P) {
-    vparts D;
-    parts_ud(V, r, w, v, vp, want_own, want_other, &D);
-    *P = D;
+/* Parts of the up-up vertex split relative to channel r (used by the t-channel bubble).
+ * For the full vertex Gamma_uu(1'2'|12) = Gamma_ud(1'2'|12) - Gamma_ud(1'2'|21).  Channel by
+ * channel, exchanging legs 1 and 2 turns a-reducible diagrams into t-reducible ones and
+ * keeps p-reducible ones, so the r-reducible up-up part is
+ *     gamma_c^uu(1'2'|12) = gamma_c^ud(1'2'|12) - gamma_{sigma(c)}^ud(1'2'|21),
+ * sigma: a <-> t, p -> p.  A vertex that includes only some channels (e.g. the sum over
+ * the channels other than r in a multiloop correction) takes the exchanged term from the
+ * partner channel's data, whether or not the partner itself is included. */
+static void parts_uu(const ovtx *V, int r, double w, double v, double vp, int want_other, vparts *P) {
+    parts_ud(V, r, w, v, vp, want_other, P);
     double L[4], S[4];
     legs_from(r, w, v, vp, L);
     S[0] = L[0]; S[1] = L[1]; S[2] = L[3]; S[3] = L[2];         /* legs 1 <-> 2 */
-    int sr = (r == 0) ? 2 : (r == 2) ? 0 : 1;
     cplx R[16], own[4][16], oth[16];
     memset(own, 0, sizeof(own));
     memset(oth, 0, sizeof(oth));
     bare_vertex(V, R);
     for (int c = 0; c < 3; ++c) {
+        if (!((V->mask >> c) & 1)) continue;
+        int sc = (c == 0) ? 2 : (c == 2) ? 0 : 1;
         double wc, vc, pc;
-        if (c == sr) {
-            if (!want_own) continue;
+        if (c == r) {
             /* sigma(r)-variables of the exchanged legs, written out exactly so that an
              * infinite v or v' needs no cancellation: a <-> t: (w, v, v') -> (-w, v, v');
              * p: (w, v, v') -> (w, v, -v') */
             if (r == 1) { wc = w; vc = v; pc = -vp; }
             else { wc = -w; vc = v; pc = vp; }
-            for (int k = 0; k < 4; ++k) add_class(V, c, k, wc, vc, pc, 1.0, own[k]);
+            for (int k = 0; k < 4; ++k) add_class(V, sc, k, wc, vc, pc, 1.0, own[k]);
         } else {
             if (!want_other) continue;
-            chan_from(c, S, &wc, &vc, &pc);
-            for (int k = 0; k < 4; ++k) add_class(V, c, k, wc, vc, pc, 1.0, oth);
+            chan_from(sc, S, &wc, &vc, &pc);
+            for (int k = 0; k < 4; ++k) add_class(V, sc, k, wc, vc, pc, 1.0, oth);
         }
     }
     /* component of the exchanged term: (a1' a2' | a2 a1) */
@@ -227,8 +229,8 @@ static void vertex_select(const ovtx *V, int r, int spin_uu, int side_right, int
                           double vp, cplx out[16]) {
     vparts P;
     int want_other = (sel != SEL_ZERO);
-    if (spin_uu) parts_uu(V, r, w, v, vp, 1, want_other, &P);
-    else parts_ud(V, r, w, v, vp, 1, want_other, &P);
+    if (spin_uu) parts_uu(V, r, w, v, vp, want_other, &P);
+    else parts_ud(V, r, w, v, vp, want_other, &P);
     /* class that does not depend on the external argument of this side */
     int k_ext_free = side_right ? 1 : 2;   /* right: K2_r(w, v''); left: K2'_r(w, v'') */
     int k_ext_dep = side_right ? 2 : 1;

@@ -55,7 +55,7 @@ def lib():
 
 class _OVtx(C.Structure):
     _fields_ = [("n1", C.c_int), ("n2w", C.c_int), ("n2v", C.c_int), ("n3w", C.c_int), ("n3v", C.c_int),
-                ("A", C.c_double), ("U", C.c_double), ("has_R", C.c_int),
+                ("A", C.c_double), ("U", C.c_double), ("has_R", C.c_int), ("mask", C.c_int),
                 ("K1", C.c_void_p * 3), ("K2", C.c_void_p * 3), ("K2p", C.c_void_p * 3), ("K3", C.c_void_p * 3)]
 
 
@@ -71,9 +71,11 @@ def grid(n, A=5.0):
 
 
 class Vertex:
-    """Bare part (U, on/off) plus per-channel classes (K1, K2, K2p, K3) as complex128."""
+    """Bare part (U, on/off) plus per-channel classes (K1, K2, K2p, K3) as complex128.
+    include: channels that are part of the vertex (default all three); data of an
+    excluded channel is used only as the crossing partner of the up-up component."""
 
-    def __init__(self, grids, U=0.0, has_R=False, channels=None, A=5.0):
+    def __init__(self, grids, U=0.0, has_R=False, channels=None, A=5.0, include=(0, 1, 2)):
         self.grids = dict(grids)
         self.A, self.U, self.has_R = A, float(U), bool(has_R)
         self.ch = {}
@@ -83,6 +85,7 @@ class Vertex:
         g = self.grids
         s.n1, s.n2w, s.n2v, s.n3w, s.n3v = g["n1"], g["n2w"], g["n2v"], g["n3w"], g["n3v"]
         s.A, s.U, s.has_R = A, self.U, int(self.has_R)
+        s.mask = sum(1 << c for c in include)
         for c in range(3):
             cl = self.ch.get(c, (None,) * 4)
             for k, name in enumerate(("K1", "K2", "K2p", "K3")):

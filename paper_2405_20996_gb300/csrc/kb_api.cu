@@ -188,8 +188,19 @@ kb_status kb_set_vertex(kb_ctx* ctx, int slot, int has_R, double U) {
     }
     std::memset(&ctx->slots[slot], 0, sizeof(kb::VertexDev));
     ctx->slots[slot].has_R = has_R ? 1 : 0;
+    ctx->slots[slot].mask = 7;
     ctx->slots[slot].halfU = 0.5 * U;
     ctx->slot_set[slot] = true;
+    return KB_OK;
+}
+
+kb_status kb_set_vertex_channels(kb_ctx* ctx, int slot, unsigned mask) {
+    if (!ctx || slot < 0 || slot >= KB_MAX_SLOTS || mask > 7) {
+        if (ctx) ctx->err = "kb_set_vertex_channels: bad slot or mask";
+        return KB_ERR_ARG;
+    }
+    if (!ctx->slot_set[slot]) { ctx->err = "kb_set_vertex_channels: call kb_set_vertex first"; return KB_ERR_STATE; }
+    ctx->slots[slot].mask = (int)mask;
     return KB_OK;
 }
 

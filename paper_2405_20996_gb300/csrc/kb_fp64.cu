@@ -70,9 +70,10 @@ __device__ void acc_class_f64(const VertexDev& V, const Grids& G, int c, int k, 
 
 // Part of Gamma (spin up-down, or up-up when uu) relative to channel r at r-variables
 // (w, v, vp): zero part (R + K1_r + [K2'_r left | K2_r right]) or v-part
-// ([K2_r left | K2'_r right] + K3_r + the other channels at converted frequencies).
-// up-up: Gamma(1'2'|12) - Gamma(1'2'|21); exchanging legs 1, 2 maps a <-> t, p -> p with
-// own-channel variables (w, v, vp) -> (-w, v, vp) (a, t) or (w, v, -vp) (p).
+// ([K2_r left | K2'_r right] + K3_r + the other included channels at converted
+// frequencies).  Up-up, channel by channel: gamma_c^uu(1'2'|12) = gamma_c^ud(1'2'|12) -
+// gamma_{sigma(c)}^ud(1'2'|21) with sigma: a <-> t, p -> p; the exchanged own-channel term
+// is read at (w, v, vp) -> (-w, v, vp) (a, t) or (w, v, -vp) (p).
 __device__ void vertex_part_f64(const VertexDev& V, const Grids& G, int r, bool uu, bool right, bool nupart,
                                 double w, double v, double vp, double2 out[16]) {
 #pragma unroll
@@ -83,29 +84,28 @@ __device__ void vertex_part_f64(const VertexDev& V, const Grids& G, int r, bool 
     }
     int k_free = right ? 1 : 2, k_dep = right ? 2 : 1;
     int ka = nupart ? k_dep : 0, kb2 = nupart ? 3 : k_free;
-    int sr = (r == KB_CH_A) ? KB_CH_T : (r == KB_CH_T ? KB_CH_A : KB_CH_P);
-    double xw = (r == KB_CH_P) ? w : -w, xvp = (r == KB_CH_P) ? -vp : vp;
-    for (int q = 0; q < 2; ++q) {
-        int k = q ? kb2 : ka;
-        acc_class_f64(V, G, r, k, w, v, vp, 1.0, false, out);
-        if (uu) acc_class_f64(V, G, sr, k, xw, v, xvp, -1.0, true, out);
+    if ((V.mask >> r) & 1) {
+        int sr = (r == KB_CH_A) ? KB_CH_T : (r == KB_CH_T ? KB_CH_A : KB_CH_P);
+        double xw = (r == KB_CH_P) ? w : -w, xvp = (r == KB_CH_P) ? -vp : vp;
+        for (int q = 0; q < 2; ++q) {
+            int k = q ? kb2 : ka;
+            acc_class_f64(V, G, r, k, w, v, vp, 1.0, false, out);
+            if (uu) acc_class_f64(V, G, sr, k, xw, v, xvp, -1.0, true, out);
+        }
     }
     if (nupart) {
         double L[4];
         legs_of(r, w, v, vp, L);
+        double S[4] = {L[0], L[1], L[3], L[2]};
         for (int c = 0; c < 3; ++c) {
-            if (c == r) continue;
+            if (c == r || !((V.mask >> c) & 1)) continue;
             double wc, vc, pc;
             vars_of(c, L, wc, vc, pc);
             for (int k = 0; k < 4; ++k) acc_class_f64(V, G, c, k, wc, vc, pc, 1.0, false, out);
-        }
-        if (uu) {
-            double S[4] = {L[0], L[1], L[3], L[2]};
-            for (int c = 0; c < 3; ++c) {
-                if (c == sr) continue;
-                double wc, vc, pc;
-                vars_of(c, S, wc, vc, pc);
-                for (int k = 0; k < 4; ++k) acc_class_f64(V, G, c, k, wc, vc, pc, -1.0, true, out);
+            if (uu) {
+                int sc = (c == KB_CH_A) ? KB_CH_T : (c == KB_CH_T ? KB_CH_A : KB_CH_P);
+                vars_of(sc, S, wc, vc, pc);
+                for (int k = 0; k < 4; ++k) acc_class_f64(V, G, sc, k, wc, vc, pc, -1.0, true, out);
             }
         }
     }

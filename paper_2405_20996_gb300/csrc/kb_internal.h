@@ -21,6 +21,8 @@ struct VertexDev {
     const void* cls[3][4];   // [channel][K1, K2, K2', K3], nullptr = absent
     int dt[3][4];            // KB_DT_C128 / KB_DT_C64
     int has_R;
+    int mask;                // channels included (bit c); excluded channels serve only as
+                             // crossing partners of the up-up component
     double halfU;            // U / 2
 };
 

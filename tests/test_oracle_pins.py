@@ -419,3 +419,23 @@ def test_quadrature_convergence_smooth_integrand():
          for n in (101, 401, 1601, 3201)]
     assert e[0] > e[1] > e[2] > e[3]
     assert e[3] < 1e-5 and e[2] < 1e-3
+
+
+@pytest.mark.parametrize("r", [0, 1, 2])
+def test_multiloop_left_part_has_no_k1_k2p(r):
+    """Multiloop left correction gamma-dot_rbar o Pi o Gamma (Sec. III.C): its left vertex
+    is the sum over the channels other than r, so no part of it is r-reducible with bare
+    legs on the left: the output has no K1 and no K2' class.  In the t channel this needs
+    the up-up component built channel by channel (crossing partner a <-> t)."""
+    g = G_TINY
+    dot = S.seeded_vertex(g, 0.5, seed=4)
+    inc = tuple(c for c in range(3) if c != r)
+    Vd = O.Vertex(g, channels=dot, include=inc)
+    V = O.Vertex(g, U=1.0, has_R=True, channels=S.seeded_vertex(g, 1.0, seed=5))
+    P = O.Prop(Delta=1.0, T=0.1)
+    B = O.bubble_all(Vd, V, P, r, 101, pi_kind=O.PI_GG)
+    assert np.abs(B["K1"]).max() == 0.0 and np.abs(B["K2p"]).max() == 0.0
+    assert np.abs(B["K2"]).max() > 0 and np.abs(B["K3"]).max() > 0
+    # right correction Gamma o Pi o gamma-dot_rbar: no K1 and no K2
+    B = O.bubble_all(V, Vd, P, r, 101)
+    assert np.abs(B["K1"]).max() == 0.0 and np.abs(B["K2"]).max() == 0.0

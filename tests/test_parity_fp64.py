@@ -23,7 +23,7 @@ def engine_for(cfg):
 def run_gpu(e, ch_in, r, U, pi_kind=0, dtype=torch.complex128, left=None, right=None, has_R=True):
     e.set_vertex(0, U=U, has_R=has_R, channels=ch_in, dtype=dtype)
     if left is not None:
-        e.set_vertex(1, U=U, has_R=left[1], channels=left[0], dtype=dtype)
+        e.set_vertex(1, U=U, has_R=left[1], channels=left[0], dtype=dtype, include=left[2])
     e.alloc_out(2, channels=(r,))
     e.bubble(r, 1 if left is not None else 0, 0, 2, pi_kind=pi_kind)
     torch.cuda.synchronize()
@@ -64,7 +64,8 @@ def test_pi_dot_sigma_table_and_loop_part_slots(r):
     cfg = dict(RAGGED, T=0.07)
     g = cfg["grids"]
     ch = seeded_inputs(cfg, seed=3)
-    dot = {c: v for c, v in S.seeded_vertex(g, 0.5, seed=4).items() if c != r}
+    dot = S.seeded_vertex(g, 0.5, seed=4)
+    inc = tuple(c for c in range(3) if c != r)        # gamma-dot of the channels other than r
     sg = O.grid(33)
     sR = S.seeded_sigma(33, seed=9)
     sK = 2j * np.tanh(sg / (2 * cfg["T"])) * sR.imag
@@ -72,10 +73,10 @@ def test_pi_dot_sigma_table_and_loop_part_slots(r):
     e.set_self_energy(sR, sK)
     ch32 = {c: tuple(a.astype(np.complex64) for a in v) for c, v in ch.items()}
     dot32 = {c: tuple(a.astype(np.complex64) for a in v) for c, v in dot.items()}
-    got = run_gpu(e, ch32, r, cfg["U"], pi_kind=1, dtype=torch.complex64, left=(dot32, False))
+    got = run_gpu(e, ch32, r, cfg["U"], pi_kind=1, dtype=torch.complex64, left=(dot32, False, inc))
     cast = lambda d: {c: tuple(a.astype(np.complex64).astype(np.complex128) for a in v) for c, v in d.items()}
     V = oracle_vertex(cfg, cast(ch))
-    Vd = O.Vertex(g, U=cfg["U"], has_R=False, channels=cast(dot))
+    Vd = O.Vertex(g, U=cfg["U"], has_R=False, channels=cast(dot), include=inc)
     P = O.Prop(Delta=cfg["Delta"], T=cfg["T"], sigR=sR, sigK=sK)
     ref = O.bubble_all(Vd, V, P, r, cfg["nq"], pi_kind=O.PI_GS)
     assert np.abs(ref["K1"]).max() == 0.0 and np.abs(ref["K2p"]).max() == 0.0   # L part: no K1, K2'
