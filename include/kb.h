@@ -48,7 +48,8 @@ typedef enum {
     KB_ERR_CUDA = 3,         /* a CUDA runtime call failed; see kb_last_error */
     KB_ERR_OOM = 4,          /* device allocation failed */
     KB_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
-    KB_ERR_UNSUPPORTED = 6   /* combination not built (e.g. precision on this device) */
+    KB_ERR_UNSUPPORTED = 6,  /* combination not built (e.g. precision on this device) */
+    KB_ERR_TOO_LARGE = 7     /* problem does not fit the fixed scratch of kb_bubble_fp64_noalloc */
 } kb_status;
 
 enum { KB_CH_A = 0, KB_CH_P = 1, KB_CH_T = 2 };
@@ -132,6 +133,46 @@ kb_status kb_launch_count(kb_ctx *ctx, unsigned long long *count);
 kb_status kb_profile_enable(kb_ctx *ctx, int on);
 kb_status kb_profile_read(kb_ctx *ctx, int index, const char **name, double *ms, unsigned long long *launches,
                           int *count);
+
+/* ---------------------------------------------------------------------------------------
+ * Allocation-free entry point.
+ *
+ * For callers that cannot call cudaMalloc — code running where the device memory is owned
+ * by someone else (a fixed memory pool, a host program that pre-reserves all memory), or
+ * code that must not trigger an allocation (and the implicit synchronisation it can cause)
+ * in the middle of its own work.  This function evaluates ONE output class of the plain
+ * FP64 bubble (the same kernels as kb_bubble with KB_PREC_FP64) and allocates nothing: its
+ * intermediate buffers (quadrature table, Pi table, vertex tiles, contraction result) live
+ * in a fixed device array of KB_NOALLOC_SCRATCH_BYTES that is part of the library image,
+ * so every GPU that loads libkb holds that array until the process exits.  The paper has no
+ * counterpart of this call; it is a deployment convenience.
+ *
+ * No context is used.  The caller passes the grids, the model (Sigma = 0: G^R = 1/(v - eps
+ * + i Delta)), the two vertices as device pointers in the layout above, and the device
+ * output array of class `cls` of channel `channel` (out <- alpha B + beta out).
+ * The first call on a device looks up the array's device address (and uploads the small
+ * index tables); make that first call before any stream capture.  All calls share the one
+ * array, and each call overwrites every scratch element it reads, so no call depends on an
+ * earlier one; calls whose work overlaps on the GPU (different streams, or different host
+ * threads, without ordering between them) race on the array and must be serialised by the
+ * caller.  The work runs in bosonic-frequency chunks that fit the array; a problem whose
+ * single bosonic frequency does not fit (roughly (8 n_v nq (2 for t)) * 16 bytes for the
+ * vertex tiles) returns KB_ERR_TOO_LARGE without launching anything.
+ * --------------------------------------------------------------------------------------- */
+#define KB_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+typedef struct {
+    int has_R;              /* include the bare vertex R = Gamma0 */
+    double U;               /* its strength */
+    unsigned channels;      /* included channels (bits), as kb_set_vertex_channels */
+    const void *cls[3][4];  /* device pointers [channel][K1, K2, K2', K3], NULL = absent */
+    int dtype[3][4];        /* KB_DT_C128 / KB_DT_C64 */
+} kb_vertex_desc;
+
+kb_status kb_bubble_fp64_noalloc(const kb_grid_desc *g, double Delta, double T, double eps,
+                                 const kb_vertex_desc *left, const kb_vertex_desc *right, int channel,
+                                 int pi_kind, int cls, void *out, int out_dtype, double alpha, double beta,
+                                 void *stream);
 
 /* Human-readable description of the last error on this context (never NULL). */
 const char *kb_last_error(kb_ctx *ctx);

@@ -6,6 +6,7 @@
 //   k_zgemm_f64     G[w][(v, A)][(v', C)] = sum_k L[..][k] R'[..][k]           (row a5)
 //   k_scatter       out[w][v][v'][c(A, C)] = alpha G + beta out                 (row a7)
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 
 #include "kb_dev.cuh"
@@ -373,4 +374,111 @@ kb_status kb_bubble_fp64(kb_ctx* ctx, int r, int sl, int sr, int so, int pi_kind
         }
     }
     return KB_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free entry point (kb_bubble_fp64_noalloc in include/kb.h).  The scratch of the
+// FP64 class pipeline lives in this fixed device array instead of a cudaMalloc'ed
+// workspace.  Host code must not pass the array's name to a kernel (on the host it is only
+// a stand-in); its device address is looked up once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_kb_noalloc_scratch[KB_NOALLOC_SCRATCH_BYTES];
+
+namespace kb {
+// Composite 5-point Gauss-Lobatto nodes and weights on [-1, 1] (same rule as kb_set_grids).
+__global__ void k_gl5_table(int nq, double* __restrict__ x, double* __restrict__ w) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nq) return;
+    int P = (nq - 1) / 4, p = j / 4, q = j % 4;
+    double h = 2.0 / P;
+    const double t[4] = {-1.0, -0.65465367070797714380, 0.0, 0.65465367070797714380};   // sqrt(3/7)
+    const double u[4] = {0.1, 49.0 / 90.0, 32.0 / 45.0, 49.0 / 90.0};
+    if (j == nq - 1) { x[j] = 1.0; w[j] = 0.05 * h; return; }
+    x[j] = (j == 0) ? -1.0 : -1.0 + p * h + (t[q] + 1.0) * 0.5 * h;
+    w[j] = u[q] * 0.5 * h * ((q == 0 && p > 0) ? 2.0 : 1.0);
+}
+}  // namespace kb
+
+static void* g_noalloc_ptr[64] = {};
+static bool g_noalloc_ready[64] = {};
+
+static kb_status noalloc_setup(int dev) {
+    if (dev < 0 || dev >= 64) return KB_ERR_ARG;
+    if (g_noalloc_ready[dev]) return KB_OK;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_kb_noalloc_scratch) != cudaSuccess || !p) return KB_ERR_CUDA;
+    ChannelMaps h[3] = {channel_maps(0), channel_maps(1), channel_maps(2)};
+    if (cudaMemcpyToSymbol(c_maps, h, sizeof(h)) != cudaSuccess) return KB_ERR_CUDA;
+    g_noalloc_ptr[dev] = p;
+    g_noalloc_ready[dev] = true;
+    return KB_OK;
+}
+
+extern "C" kb_status kb_bubble_fp64_noalloc(const kb_grid_desc* gd, double Delta, double T, double eps,
+                                            const kb_vertex_desc* left, const kb_vertex_desc* right, int r,
+                                            int pi_kind, int cls, void* out, int out_dtype, double alpha,
+                                            double beta, void* stream) {
+    if (!gd || !left || !right || !out || r < 0 || r > 2 || cls < 0 || cls > 3 ||
+        (pi_kind != KB_PI_GG && pi_kind != KB_PI_GS_SG) || (out_dtype != KB_DT_C128 && out_dtype != KB_DT_C64) ||
+        !(Delta > 0) || !(T >= 0) || !std::isfinite(eps) || !std::isfinite(alpha) || !std::isfinite(beta) ||
+        gd->n1 < 1 || gd->n2w < 1 || gd->n2v < 1 || gd->n3w < 1 || gd->n3v < 1 || gd->nq < 5 ||
+        (gd->nq - 1) % 4 || !(gd->A > 0) || left->channels > 7 || right->channels > 7)
+        return KB_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return KB_ERR_CUDA;
+    kb_status s = noalloc_setup(dev);
+    if (s != KB_OK) return s;
+    Grids g{gd->n1, gd->n2w, gd->n2v, gd->n3w, gd->n3v, gd->nq, gd->A};
+    Model m{Delta, T, eps, 0, 1.0, nullptr, nullptr};
+    VertexDev V[2];
+    const kb_vertex_desc* D[2] = {left, right};
+    for (int i = 0; i < 2; ++i) {
+        V[i].has_R = D[i]->has_R ? 1 : 0;
+        V[i].mask = (int)D[i]->channels;
+        V[i].halfU = 0.5 * D[i]->U;
+        for (int c = 0; c < 3; ++c)
+            for (int k = 0; k < 4; ++k) {
+                V[i].cls[c][k] = D[i]->cls[c][k];
+                V[i].dt[c][k] = D[i]->dtype[c][k];
+                if (V[i].dt[c][k] != KB_DT_C128 && V[i].dt[c][k] != KB_DT_C64) return KB_ERR_ARG;
+            }
+    }
+    int ns = (r == KB_CH_T) ? 2 : 1;
+    size_t K = (size_t)4 * ns * g.nq;
+    int nw, nL, nR, nvg;
+    class_shape(g, cls, nw, nL, nR, nvg);
+    size_t table = 2 * sizeof(double) * ((g.nq + 31) / 32 * 32);
+    size_t per_w = (size_t)g.nq * 16 * sizeof(double2) + (size_t)4 * nL * K * sizeof(double2) +
+                   (size_t)4 * nR * K * sizeof(double2) + (size_t)16 * nL * nR * sizeof(double2);
+    if (table + per_w > KB_NOALLOC_SCRATCH_BYTES) return KB_ERR_TOO_LARGE;
+    int chunk = (int)std::min<size_t>(nw, (KB_NOALLOC_SCRATCH_BYTES - table) / per_w);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char* base = static_cast<char*>(g_noalloc_ptr[dev]);
+    double* xq = reinterpret_cast<double*>(base);
+    double* wq = xq + (g.nq + 31) / 32 * 32;
+    double2* Pi = reinterpret_cast<double2*>(base + table);
+    double2* Lt = Pi + (size_t)chunk * g.nq * 16;
+    double2* Rt = Lt + (size_t)chunk * 4 * nL * K;
+    double2* Gm = Rt + (size_t)chunk * 4 * nR * K;
+    k_gl5_table<<<(g.nq + 127) / 128, 128, 0, st>>>(g.nq, xq, wq);
+    for (int w0 = 0; w0 < nw; w0 += chunk) {
+        ClassJob J;
+        J.r = r; J.pi_kind = pi_kind; J.ns = ns; J.nq = g.nq;
+        J.nw_chunk = std::min(chunk, nw - w0); J.w0 = w0; J.nw_grid = nw;
+        J.nL = nL; J.nR = nR; J.nvL_grid = nvg; J.nvR_grid = nvg;
+        J.L_nu = (cls == KB_K2 || cls == KB_K3);
+        J.R_nu = (cls == KB_K2P || cls == KB_K3);
+        k_pi_table<<<dim3((g.nq + 127) / 128, J.nw_chunk), 128, 0, st>>>(m, J, g.A, xq, wq, Pi);
+        k_gather_f64<false><<<dim3((g.nq + 127) / 128, nL * ns, J.nw_chunk), 128, 0, st>>>(V[0], g, J, xq, Pi, Lt);
+        k_gather_f64<true><<<dim3((g.nq + 127) / 128, nR * ns, J.nw_chunk), 128, 0, st>>>(V[1], g, J, xq, Pi, Rt);
+        int Mr = 4 * nL, Nc = 4 * nR;
+        if (Nc <= 4)
+            k_zgemm_skinny_f64<<<(Mr * J.nw_chunk * 32 + 255) / 256, 256, 0, st>>>(Lt, Rt, Gm, Mr, Nc, (int)K,
+                                                                                    J.nw_chunk);
+        else
+            k_zgemm_f64<<<dim3((Nc + 31) / 32, (Mr + 31) / 32, J.nw_chunk), 256, 0, st>>>(Lt, Rt, Gm, Mr, Nc, (int)K);
+        size_t tot = (size_t)J.nw_chunk * nL * nR * 16;
+        k_scatter<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(J, cls, Gm, out, out_dtype, alpha, beta);
+    }
+    return cudaGetLastError() == cudaSuccess ? KB_OK : KB_ERR_CUDA;
 }

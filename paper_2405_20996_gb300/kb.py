@@ -32,6 +32,14 @@ class KBError(RuntimeError):
         self.status = status
 
 
+class kb_vertex_desc(C.Structure):
+    _fields_ = [("has_R", C.c_int), ("U", C.c_double), ("channels", C.c_uint),
+                ("cls", (C.c_void_p * 4) * 3), ("dtype", (C.c_int * 4) * 3)]
+
+
+KB_ERR_TOO_LARGE = 7
+KB_NOALLOC_SCRATCH_BYTES = 32 << 20
+
 _lib = None
 _SIGS = {
     "kb_create": [C.POINTER(C.c_void_p), C.c_int],
@@ -46,6 +54,9 @@ _SIGS = {
                   C.c_int, C.c_void_p],
     "kb_workspace_bytes": [C.c_void_p, C.POINTER(C.c_ulonglong)],
     "kb_launch_count": [C.c_void_p, C.POINTER(C.c_ulonglong)],
+    "kb_bubble_fp64_noalloc": [C.POINTER(kb_grid_desc), C.c_double, C.c_double, C.c_double,
+                               C.POINTER(kb_vertex_desc), C.POINTER(kb_vertex_desc), C.c_int, C.c_int, C.c_int,
+                               C.c_void_p, C.c_int, C.c_double, C.c_double, C.c_void_p],
     "kb_profile_enable": [C.c_void_p, C.c_int],
     "kb_profile_read": [C.c_void_p, C.c_int, C.POINTER(C.c_char_p), C.POINTER(C.c_double),
                         C.POINTER(C.c_ulonglong), C.POINTER(C.c_int)],
@@ -160,3 +171,10 @@ def kb_profile_read(ctx):
         _check(ctx, lib().kb_profile_read(ctx, i, C.byref(nm), C.byref(ms), C.byref(cnt), None))
         out[nm.value.decode()] = (ms.value, cnt.value)
     return out
+
+
+def kb_bubble_fp64_noalloc(grid, Delta, T, eps, left, right, channel, pi_kind, cls, out_ptr, out_dtype, alpha=1.0,
+                           beta=0.0, stream=0):
+    """Allocation-free FP64 bubble of one class (see include/kb.h); returns the status."""
+    return lib().kb_bubble_fp64_noalloc(C.byref(grid), Delta, T, eps, C.byref(left), C.byref(right), channel,
+                                        pi_kind, cls, out_ptr, out_dtype, alpha, beta, stream)
