@@ -119,6 +119,11 @@ kb_status kb_set_vertex_class(kb_ctx *ctx, int slot, int channel, int cls, void 
 kb_status kb_bubble(kb_ctx *ctx, int channel, int slot_left, int slot_right, int out_slot, int pi_kind,
                     unsigned class_mask, double alpha, double beta, int precision, void *stream);
 
+/* Synchronise the context's device and report device-side failures since the last check:
+ * KB_ERR_TIMEOUT if a bounded wait inside a tensor-core kernel gave up (that kernel's output
+ * is then incomplete), KB_ERR_CUDA for a CUDA error.  Clears the timeout flag. */
+kb_status kb_check_device(kb_ctx *ctx);
+
 /* Bytes of device workspace the library currently holds (grows on demand). */
 kb_status kb_workspace_bytes(kb_ctx *ctx, unsigned long long *bytes);
 

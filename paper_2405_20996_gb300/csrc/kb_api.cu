@@ -90,6 +90,8 @@ static void prof_clear(kb_ctx* ctx) {
     ctx->prof.clear();
 }
 
+int kb_tc_take_status();
+
 extern "C" {
 
 kb_status kb_create(kb_ctx** out, int device) {
@@ -252,6 +254,16 @@ kb_status kb_bubble(kb_ctx* ctx, int channel, int sl, int sr, int so, int pi_kin
     if (precision == KB_PREC_MIXED) return kb_bubble_mixed(ctx, channel, sl, sr, so, pi_kind, mask, alpha, beta, st);
     ctx->err = "kb_bubble: unknown precision";
     return KB_ERR_ARG;
+}
+
+kb_status kb_check_device(kb_ctx* ctx) {
+    if (!ctx) return KB_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    KB_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    int v = kb_tc_take_status();
+    if (v < 0) { ctx->err = "kb_check_device: status read failed"; return KB_ERR_CUDA; }
+    if (v) { ctx->err = "a bounded device-side wait gave up (tensor-core contraction)"; return KB_ERR_TIMEOUT; }
+    return KB_OK;
 }
 
 kb_status kb_workspace_bytes(kb_ctx* ctx, unsigned long long* bytes) {

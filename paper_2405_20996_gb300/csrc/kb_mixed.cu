@@ -1,7 +1,599 @@
-// Mixed-precision path (FP32 gather, 3xTF32 tcgen05 contraction); filled in later.
-#include "kb_internal.h"
+// Mixed-precision path: propagators, Pi and the high-frequency tail in FP64; vertex gather
+// in FP32 with double-float frequency arithmetic (kb_mixed.cuh); contractions with FP32
+// products.  Per channel r:
+//   k_mx_tables   double-float node tables of the class grids and the quadrature
+//   k_mx_prep     per (w, node) on the K2 grid: N_s = Pi R0_s and M_s = L0_s Pi (4x4,
+//                 FP64 then FP32); on the K3 grid: Pi in FP32 for folding the right tile
+//   k_mx_k1       K1(w) = sum_j L0 Pi R0, one CTA per w
+//   k_mx_sumj     column sums over j of N_s, M_s (for the v-independent own class)
+//   k_mx_k2<R>    K2 (K2') = sum_j [v-part of Gamma1] N  (M [v'-part of Gamma2]), gather
+//                 fused with the contraction, no tile in memory
+//   k_mx_tile3<R> K3 tiles: left L[(v,A)][(s,j,B)], right R' = Pi R, as four FP32 planes
+//                 (re hi, re lo, im hi, im lo; hi = TF32-rounded value, lo = remainder)
+//   K3 contraction: tcgen05 3xTF32 (kb_tc.cu) or the SIMT reference k_mx_cgemm
+//   k_mx_scatter3 out <- alpha B + beta out for K3
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
 
-kb_status kb_bubble_mixed(kb_ctx* ctx, int, int, int, int, int, unsigned, double, double, cudaStream_t) {
-    ctx->err = "mixed precision path not built yet";
-    return KB_ERR_UNSUPPORTED;
+#include "kb_mixed.cuh"
+
+namespace kb {
+
+// ------------------------------------------------------------------------------------
+// tables
+// ------------------------------------------------------------------------------------
+__global__ void k_mx_tables(int n1, int n2w, int n2v, int n3w, int n3v, int nq, double A, const double* __restrict__ xq,
+                            df* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int sizes[6] = {n1, n2w, n2v, n3w, n3v, nq};
+    int off = 0;
+    for (int g = 0; g < 6; ++g) {
+        if (i < off + sizes[g]) {
+            int k = i - off;
+            double x = (g < 5) ? -1.0 + 2.0 * (k + 1) / (double)(sizes[g] + 1) : xq[k];
+            df v;
+            if (x <= -1.0) v = {-INFINITY, 0.f};
+            else if (x >= 1.0) v = {INFINITY, 0.f};
+            else v = df_make(A * tan(0.5 * KB_PI * x));
+            out[i] = v;
+            return;
+        }
+        off += sizes[g];
+    }
+}
+
+struct MixedJob {
+    int r, pi_kind, ns, nq;
+    ChannelMaps M;
+    double alpha, beta;
+};
+
+__device__ __forceinline__ double2 c64to128(float2 a) { return make_double2(a.x, a.y); }
+
+// Zero part of a vertex as seen by the K1/K2 tables (own channel only, FP32 gather).
+// left: R + K1_r + K2'_r(w, v''); right: R + K1_r + K2_r(w, v'').
+template <int r>
+__device__ __forceinline__ void zero_part(const VertexF& V, const DfGrids& G, bool uu, bool right, df w, df vpp,
+                                          float2 out[16]) {
+    df zero = {0.f, 0.f};
+    if (right) vertex_part_f32<r>(V, G, uu, true, 1 | 2 | 4, w, vpp, zero, out);
+    else vertex_part_f32<r>(V, G, uu, false, 1 | 2 | 4, w, zero, vpp, out);
+}
+
+// Per (w in K2 grid, j): N_s = Pi R0_s, M_s = L0_s Pi;  Nt/Mt layout [w][s][j][16] float2.
+// Right spin order s: 0 up-down, 1 up-up (t); left: 0 up-up, 1 up-down (t).
+template <int R>
+__global__ void __launch_bounds__(128) k_mx_prep_k2(VertexF VL, VertexF VR, DfGrids G, Model m, MixedJob J, const double* __restrict__ xq,
+                             const double* __restrict__ wq, const df* __restrict__ wgrid, float2* __restrict__ Nt,
+                             float2* __restrict__ Mt) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int wi = blockIdx.y;
+    if (j >= J.nq) return;
+    const df* qn = G.n3v + G.N3v;   // quadrature nodes follow the K3 fermionic grid in the table
+    df w = wgrid[wi], vpp = qn[j];
+    double2 Pi[16];
+    pi_entry(m, J.M, J.r, J.pi_kind, G.A, (double)w.h + (double)w.l, xq[j], wq[j], Pi);
+    constexpr int NS = (R == KB_CH_T) ? 2 : 1;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        float2 R0[16], L0[16];
+        bool uuR = (R == KB_CH_T) && s == 1, uuL = (R == KB_CH_T) && s == 0;
+        zero_part<R>(VR, G, uuR, true, w, vpp, R0);
+        zero_part<R>(VL, G, uuL, false, w, vpp, L0);
+        float2* n = Nt + (((size_t)wi * J.ns + s) * J.nq + j) * 16;
+        float2* mm = Mt + (((size_t)wi * J.ns + s) * J.nq + j) * 16;
+#pragma unroll
+        for (int X = 0; X < 4; ++X)
+#pragma unroll
+            for (int Y = 0; Y < 4; ++Y) {
+                double2 an = make_double2(0, 0), am = make_double2(0, 0);
+#pragma unroll
+                for (int Z = 0; Z < 4; ++Z) {
+                    cfma(an, Pi[4 * X + Z], c64to128(R0[cmap<R>(Z, Y)]));   // N[B=X][C=Y] = sum_D Pi[B][D] R0[D][C]
+                    cfma(am, c64to128(L0[cmap<R>(X, Z)]), Pi[4 * Z + Y]);   // M[A=X][D=Y] = sum_B L0[A][B] Pi[B][D]
+                }
+                n[4 * X + Y] = make_float2((float)an.x, (float)an.y);
+                mm[4 * X + Y] = make_float2((float)am.x, (float)am.y);
+            }
+    }
+}
+
+// Pi on the K3 bosonic grid, FP64 -> FP32: Pt[w][j][16]
+__global__ void k_mx_pi3(DfGrids G, Model m, MixedJob J, const double* __restrict__ xq, const double* __restrict__ wq,
+                         float2* __restrict__ Pt) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    int wi = blockIdx.y;
+    if (j >= J.nq) return;
+    df w = G.n3w[wi];
+    double2 Pi[16];
+    pi_entry(m, J.M, J.r, J.pi_kind, G.A, (double)w.h + (double)w.l, xq[j], wq[j], Pi);
+    float2* o = Pt + ((size_t)wi * J.nq + j) * 16;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) o[i] = make_float2((float)Pi[i].x, (float)Pi[i].y);
+}
+
+// Block-wide sum of 16 complex numbers per thread into FP64 (result valid in thread 0).
+template <int NT>
+__device__ __forceinline__ void block_sum16(const float2 v[16], double2 res[16], double* sh) {
+    // sh: NT/32 * 32 doubles
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 0; o < 16; ++o) {
+        double x = v[o].x, y = v[o].y;
+        for (int d = 16; d > 0; d >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, d);
+            y += __shfl_xor_sync(0xffffffffu, y, d);
+        }
+        if (lane == 0) { sh[wid * 32 + 2 * o] = x; sh[wid * 32 + 2 * o + 1] = y; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int o = 0; o < 16; ++o) {
+            double x = 0, y = 0;
+            for (int wv = 0; wv < NT / 32; ++wv) { x += sh[wv * 32 + 2 * o]; y += sh[wv * 32 + 2 * o + 1]; }
+            res[o] = make_double2(x, y);
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void store_out(void* out, int dt, size_t e, double2 v, double alpha, double beta) {
+    if (dt == KB_DT_C128) {
+        double2* p = reinterpret_cast<double2*>(out) + e;
+        double2 o = beta != 0.0 ? *p : make_double2(0, 0);
+        *p = make_double2(alpha * v.x + beta * o.x, alpha * v.y + beta * o.y);
+    } else {
+        float2* p = reinterpret_cast<float2*>(out) + e;
+        float2 o = beta != 0.0 ? *p : make_float2(0, 0);
+        *p = make_float2((float)(alpha * v.x + beta * o.x), (float)(alpha * v.y + beta * o.y));
+    }
+}
+
+// K1(w) = sum_j sum_s L0_s Pi R0_s : one CTA (128 threads) per w of the K1 grid.
+template <int R>
+__global__ void __launch_bounds__(128) k_mx_k1(VertexF VL, VertexF VR, DfGrids G, Model m, MixedJob J,
+                                               const double* __restrict__ xq, const double* __restrict__ wq, void* out,
+                                               int odt) {
+    __shared__ double sh[4 * 32];
+    int wi = blockIdx.x;
+    const df* qn = G.n3v + G.N3v;
+    df w = G.n1[wi];
+    float2 acc[16];
+    for (int o = 0; o < 16; ++o) acc[o] = make_float2(0, 0);
+    for (int j = threadIdx.x; j < J.nq; j += blockDim.x) {
+        double2 Pi[16];
+        pi_entry(m, J.M, J.r, J.pi_kind, G.A, (double)w.h + (double)w.l, xq[j], wq[j], Pi);
+        constexpr int NS = (R == KB_CH_T) ? 2 : 1;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            float2 R0[16], L0[16];
+            zero_part<R>(VR, G, (R == KB_CH_T) && s == 1, true, w, qn[j], R0);
+            zero_part<R>(VL, G, (R == KB_CH_T) && s == 0, false, w, qn[j], L0);
+#pragma unroll
+            for (int B = 0; B < 4; ++B)
+#pragma unroll
+                for (int C = 0; C < 4; ++C) {
+                    double2 n = make_double2(0, 0);
+#pragma unroll
+                    for (int D = 0; D < 4; ++D) cfma(n, Pi[4 * B + D], c64to128(R0[cmap<R>(D, C)]));
+                    float2 nf = make_float2((float)n.x, (float)n.y);
+#pragma unroll
+                    for (int A = 0; A < 4; ++A) {
+                        float2 l = L0[cmap<R>(A, B)];
+                        float2& a = acc[4 * A + C];
+                        a.x = fmaf(l.x, nf.x, fmaf(-l.y, nf.y, a.x));
+                        a.y = fmaf(l.x, nf.y, fmaf(l.y, nf.x, a.y));
+                    }
+                }
+        }
+    }
+    double2 res[16];
+    block_sum16<128>(acc, res, sh);
+    if (threadIdx.x == 0)
+        for (int A = 0; A < 4; ++A)
+            for (int C = 0; C < 4; ++C) store_out(out, odt, (size_t)wi * 16 + J.M.cO[A][C], res[4 * A + C], J.alpha, J.beta);
+}
+
+// Column sums over j of the K2-grid tables: S[t][w][s][16], t = 0 (N) or 1 (M).
+__global__ void k_mx_sumj(const float2* __restrict__ Nt, const float2* __restrict__ Mt, int nq, int ns,
+                          double2* __restrict__ S) {
+    __shared__ double sh[4 * 32];
+    int wi = blockIdx.x, s = blockIdx.y, t = blockIdx.z;
+    const float2* T = (t == 0 ? Nt : Mt) + ((size_t)wi * ns + s) * nq * 16;
+    float2 acc[16];
+    for (int o = 0; o < 16; ++o) acc[o] = make_float2(0, 0);
+    for (int j = threadIdx.x; j < nq; j += blockDim.x)
+        for (int o = 0; o < 16; ++o) { acc[o].x += T[(size_t)j * 16 + o].x; acc[o].y += T[(size_t)j * 16 + o].y; }
+    double2 res[16];
+    block_sum16<128>(acc, res, sh);
+    if (threadIdx.x == 0) {
+        double2* o = S + (((size_t)t * gridDim.x + wi) * ns + s) * 16;
+        for (int i = 0; i < 16; ++i) o[i] = res[i];
+    }
+}
+
+// K2 (RIGHT = false): out(w, v)[A][C] = sum_j sum_s sum_B L_s(w, v, v''_j)[A][B] N_s(w, j)[B][C]
+//   with L the v-dependent part of Gamma1 without its own K2 class, plus
+//   K2own_s(w, v)[A][B] * SN_s(w)[B][C]  (the own K2 class does not depend on v'').
+// K2' (RIGHT = true): out(w, v')[A][C] = sum_j sum_s sum_D M_s(w, j)[A][D] R_s(w, v''_j, v')[D][C]
+//   + SM_s(w)[A][D] * K2'own_s(w, v')[D][C].
+// One CTA (128 threads) per (w, v); the endpoint nodes contribute only through the own
+// class and are skipped in the loop.
+template <bool RIGHT, int R>
+__global__ void __launch_bounds__(128, 3) k_mx_k2(VertexF V, DfGrids G, MixedJob J, const float2* __restrict__ Tab,
+                                               const double2* __restrict__ Ssum, void* out, int odt) {
+    __shared__ double sh[4 * 32];
+    int wi = blockIdx.y, vi = blockIdx.x;
+    const df* qn = G.n3v + G.N3v;
+    df w = G.n2w[wi], ve = G.n2v[vi];
+    float2 acc[16];
+    for (int o = 0; o < 16; ++o) acc[o] = make_float2(0, 0);
+    constexpr int NS = (R == KB_CH_T) ? 2 : 1;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        bool uu = (R == KB_CH_T) && (RIGHT ? s == 1 : s == 0);
+        const float2* T = Tab + (((size_t)wi * NS + s) * J.nq) * 16;
+        for (int j = 1 + threadIdx.x; j < J.nq - 1; j += blockDim.x) {
+            float2 g[16];
+            if (RIGHT) vertex_part_f32<R>(V, G, uu, true, 16 | 32, w, qn[j], ve, g);
+            else vertex_part_f32<R>(V, G, uu, false, 16 | 32, w, ve, qn[j], g);
+            const float4* tp = reinterpret_cast<const float4*>(T + (size_t)j * 16);
+            if (!RIGHT) {
+                // acc[A][C] += sum_B g(A,B) N[B][C], one row B of N at a time
+#pragma unroll
+                for (int B = 0; B < 4; ++B) {
+                    float4 u = __ldg(tp + 2 * B), v = __ldg(tp + 2 * B + 1);
+                    float2 nb[4] = {make_float2(u.x, u.y), make_float2(u.z, u.w), make_float2(v.x, v.y),
+                                    make_float2(v.z, v.w)};
+#pragma unroll
+                    for (int A = 0; A < 4; ++A) {
+                        float2 x = g[cmap<R>(A, B)];
+#pragma unroll
+                        for (int C = 0; C < 4; ++C) {
+                            float2& a = acc[4 * A + C];
+                            a.x = fmaf(x.x, nb[C].x, fmaf(-x.y, nb[C].y, a.x));
+                            a.y = fmaf(x.x, nb[C].y, fmaf(x.y, nb[C].x, a.y));
+                        }
+                    }
+                }
+            } else {
+                // acc[A][C] += sum_D M[A][D] g(D,C), one row A of M at a time
+#pragma unroll
+                for (int A = 0; A < 4; ++A) {
+                    float4 u = __ldg(tp + 2 * A), v = __ldg(tp + 2 * A + 1);
+                    float2 ma[4] = {make_float2(u.x, u.y), make_float2(u.z, u.w), make_float2(v.x, v.y),
+                                    make_float2(v.z, v.w)};
+#pragma unroll
+                    for (int D = 0; D < 4; ++D)
+#pragma unroll
+                        for (int C = 0; C < 4; ++C) {
+                            float2 y = g[cmap<R>(D, C)];
+                            float2& a = acc[4 * A + C];
+                            a.x = fmaf(ma[D].x, y.x, fmaf(-ma[D].y, y.y, a.x));
+                            a.y = fmaf(ma[D].x, y.y, fmaf(ma[D].y, y.x, a.y));
+                        }
+                }
+            }
+        }
+    }
+    double2 res[16];
+    block_sum16<128>(acc, res, sh);
+    if (threadIdx.x == 0) {
+        df zero = {0.f, 0.f};
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            bool uu = (R == KB_CH_T) && (RIGHT ? s == 1 : s == 0);
+            float2 g[16];
+            if (RIGHT) vertex_part_f32<R>(V, G, uu, true, 8, w, zero, ve, g);
+            else vertex_part_f32<R>(V, G, uu, false, 8, w, ve, zero, g);
+            const double2* S = Ssum + (((size_t)(RIGHT ? 1 : 0) * G.N2w + wi) * NS + s) * 16;
+#pragma unroll
+            for (int A = 0; A < 4; ++A)
+#pragma unroll
+                for (int C = 0; C < 4; ++C)
+#pragma unroll
+                    for (int B = 0; B < 4; ++B) {
+                        if (!RIGHT) cfma(res[4 * A + C], c64to128(g[cmap<R>(A, B)]), S[4 * B + C]);
+                        else cfma(res[4 * A + C], S[4 * A + B], c64to128(g[cmap<R>(B, C)]));
+                    }
+        }
+#pragma unroll
+        for (int A = 0; A < 4; ++A)
+#pragma unroll
+            for (int C = 0; C < 4; ++C)
+                store_out(out, odt, ((size_t)wi * G.N2v + vi) * 16 + cmap<R>(A, C), res[4 * A + C], J.alpha, J.beta);
+    }
+}
+
+// TF32 split of an FP32 value: hi rounded to the 10-bit TF32 mantissa, lo = x - hi
+// (exact in FP32).
+__device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
+    uint32_t u;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+    hi = __uint_as_float(u);
+    lo = x - hi;
+}
+
+// K3 tiles.  Left: row (v, A), col k = (s*nq + j)*4 + B, value Gamma1_s^{cL[A][B]}(w, v, v''_j)
+// (v-dependent part incl. the own K2 class).  Right: row (v', C), same k, value
+// sum_D Pi[B][D] Gamma2_s^{cR[D][C]}(w, v''_j, v').  Four planes per tile:
+// [plane][row][k], plane = 2*(re 0 / im 1) + (hi 0 / lo 1), each plane rows x K floats.
+template <bool RIGHT, int R>
+__global__ void __launch_bounds__(128, 4) k_mx_tile3(VertexF V, DfGrids G, MixedJob J, int w0, const float2* __restrict__ Pt,
+                                                  float* __restrict__ tile) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int NS = (R == KB_CH_T) ? 2 : 1;
+    int s = blockIdx.y % NS, vi = blockIdx.y / NS, wl = blockIdx.z;
+    if (j >= J.nq) return;
+    const df* qn = G.n3v + G.N3v;
+    df w = G.n3w[w0 + wl], ve = G.n3v[vi];
+    bool uu = (R == KB_CH_T) && (RIGHT ? s == 1 : s == 0);
+    float2 g[16];
+    if (RIGHT) vertex_part_f32<R>(V, G, uu, true, 8 | 16 | 32, w, qn[j], ve, g);
+    else vertex_part_f32<R>(V, G, uu, false, 8 | 16 | 32, w, ve, qn[j], g);
+    size_t rows = (size_t)4 * G.N3v, K = (size_t)4 * NS * J.nq;
+    size_t plane = rows * K;
+    float* base = tile + (size_t)wl * 4 * plane;
+    size_t col = ((size_t)s * J.nq + j) * 4;
+    float2 val[16];
+    if (!RIGHT) {
+#pragma unroll
+        for (int A = 0; A < 4; ++A)
+#pragma unroll
+            for (int B = 0; B < 4; ++B) val[4 * A + B] = g[cmap<R>(A, B)];
+    } else {
+        const float2* P = Pt + ((size_t)(w0 + wl) * J.nq + j) * 16;
+#pragma unroll
+        for (int C = 0; C < 4; ++C)
+#pragma unroll
+            for (int B = 0; B < 4; ++B) {
+                float2 a = make_float2(0, 0);
+#pragma unroll
+                for (int D = 0; D < 4; ++D) {
+                    float2 p = P[4 * B + D], x = g[cmap<R>(D, C)];
+                    a.x = fmaf(p.x, x.x, fmaf(-p.y, x.y, a.x));
+                    a.y = fmaf(p.x, x.y, fmaf(p.y, x.x, a.y));
+                }
+                val[4 * C + B] = a;
+            }
+    }
+#pragma unroll
+    for (int X = 0; X < 4; ++X) {
+        size_t row = (size_t)vi * 4 + X;
+        float4 rh, rl, ih, il;
+        float* f[4] = {&rh.x, &rh.y, &rh.z, &rh.w};
+        float* fl[4] = {&rl.x, &rl.y, &rl.z, &rl.w};
+        float* gi[4] = {&ih.x, &ih.y, &ih.z, &ih.w};
+        float* gl[4] = {&il.x, &il.y, &il.z, &il.w};
+#pragma unroll
+        for (int B = 0; B < 4; ++B) {
+            tf32_split(val[4 * X + B].x, *f[B], *fl[B]);
+            tf32_split(val[4 * X + B].y, *gi[B], *gl[B]);
+        }
+        *reinterpret_cast<float4*>(base + 0 * plane + row * K + col) = rh;
+        *reinterpret_cast<float4*>(base + 1 * plane + row * K + col) = rl;
+        *reinterpret_cast<float4*>(base + 2 * plane + row * K + col) = ih;
+        *reinterpret_cast<float4*>(base + 3 * plane + row * K + col) = il;
+    }
+}
+
+// SIMT reference contraction of the K3 tiles (hi + lo recombined, FP32 products, FP32
+// partial sums over chunks of 64 k, FP64 across chunks).  C[b][m][n] (double2).
+__global__ void __launch_bounds__(256) k_mx_cgemm(const float* __restrict__ At, const float* __restrict__ Bt,
+                                                  double2* __restrict__ Cm, int M, int N, int K) {
+    __shared__ float2 sA[16][65], sB[16][65];
+    int b = blockIdx.z, m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+    size_t pa = (size_t)M * K, pb = (size_t)N * K;
+    const float* A = At + (size_t)b * 4 * pa;
+    const float* B = Bt + (size_t)b * 4 * pb;
+    int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    float2 acc[4][4];
+    double2 tot[4][4];
+    for (int i = 0; i < 4; ++i)
+        for (int jj = 0; jj < 4; ++jj) { acc[i][jj] = make_float2(0, 0); tot[i][jj] = make_double2(0, 0); }
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        for (int i = threadIdx.x; i < 64 * 16; i += 256) {
+            int row = i / 16, kk = i % 16, gk = k0 + kk;
+            int gm = m0 + row, gn = n0 + row;
+            float2 a = make_float2(0, 0), bb = make_float2(0, 0);
+            if (gm < M && gk < K) {
+                size_t o = (size_t)gm * K + gk;
+                a = make_float2(A[o] + A[pa + o], A[2 * pa + o] + A[3 * pa + o]);
+            }
+            if (gn < N && gk < K) {
+                size_t o = (size_t)gn * K + gk;
+                bb = make_float2(B[o] + B[pb + o], B[2 * pb + o] + B[3 * pb + o]);
+            }
+            sA[kk][row] = a;
+            sB[kk][row] = bb;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float2 av[4], bv[4];
+            for (int i = 0; i < 4; ++i) { av[i] = sA[kk][ty + 16 * i]; bv[i] = sB[kk][tx + 16 * i]; }
+            for (int i = 0; i < 4; ++i)
+                for (int jj = 0; jj < 4; ++jj) {
+                    float2& c = acc[i][jj];
+                    c.x = fmaf(av[i].x, bv[jj].x, fmaf(-av[i].y, bv[jj].y, c.x));
+                    c.y = fmaf(av[i].x, bv[jj].y, fmaf(av[i].y, bv[jj].x, c.y));
+                }
+        }
+        __syncthreads();
+        if (((k0 / 16) & 3) == 3 || k0 + 16 >= K)
+            for (int i = 0; i < 4; ++i)
+                for (int jj = 0; jj < 4; ++jj) {
+                    tot[i][jj].x += acc[i][jj].x; tot[i][jj].y += acc[i][jj].y;
+                    acc[i][jj] = make_float2(0, 0);
+                }
+    }
+    for (int i = 0; i < 4; ++i)
+        for (int jj = 0; jj < 4; ++jj) {
+            int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * jj;
+            if (gm < M && gn < N) Cm[((size_t)b * M + gm) * N + gn] = tot[i][jj];
+        }
+}
+
+// out K3 <- alpha C + beta out, C[wl][(v, A)][(v', C)]
+__global__ void k_mx_scatter3(MixedJob J, int w0, int nwc, int nv, const double2* __restrict__ Cm, void* out, int odt) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)nwc * nv * nv * 16;
+    if (idx >= total) return;
+    int o = idx % 16;
+    size_t rest = idx / 16;
+    int vR = rest % nv;
+    rest /= nv;
+    int vL = rest % nv;
+    int wl = (int)(rest / nv);
+    int A = 0, C = 0;
+    for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 4; ++c)
+            if (J.M.cO[a][c] == o) { A = a; C = c; }
+    int Mr = 4 * nv;
+    double2 gv = Cm[((size_t)wl * Mr + 4 * vL + A) * Mr + 4 * vR + C];
+    store_out(out, odt, (((size_t)(w0 + wl) * nv + vL) * nv + vR) * 16 + o, gv, J.alpha, J.beta);
+}
+
+}  // namespace kb
+
+using namespace kb;
+
+// tcgen05 contraction of the K3 tiles (kb_tc.cu); returns false if not launched.
+bool kb_tc_k3(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
+              void* scratch, size_t scratch_bytes, cudaStream_t st);
+
+static VertexF to_vf(const VertexDev& V, kb_ctx* ctx, bool& ok) {
+    VertexF F;
+    ok = true;
+    for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < 4; ++k) {
+            F.cls[c][k] = reinterpret_cast<const float2*>(V.cls[c][k]);
+            if (V.cls[c][k] && V.dt[c][k] != KB_DT_C64) ok = false;
+            if (V.cls[c][k] && (reinterpret_cast<uintptr_t>(V.cls[c][k]) & 15)) ok = false;
+        }
+    F.has_R = V.has_R;
+    F.mask = V.mask;
+    F.halfU = (float)V.halfU;
+    if (!ok) ctx->err = "mixed precision needs complex64 classes aligned to 16 bytes";
+    return F;
+}
+
+template <int r>
+static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, unsigned mask, double alpha, double beta,
+                            cudaStream_t st) {
+    const Grids& g = ctx->g;
+    bool ok1, ok2;
+    VertexF VL = to_vf(ctx->slots[sl], ctx, ok1), VR = to_vf(ctx->slots[sr], ctx, ok2);
+    if (!ok1 || !ok2) return KB_ERR_ARG;
+    const VertexDev& VO = ctx->slots[so];
+    MixedJob J;
+    J.r = r; J.pi_kind = pi_kind; J.ns = (r == KB_CH_T) ? 2 : 1; J.nq = g.nq;
+    J.M = channel_maps(r); J.alpha = alpha; J.beta = beta;
+    int ns = J.ns;
+    // workspace layout
+    size_t ntab = (size_t)g.n1 + g.n2w + g.n2v + g.n3w + g.n3v + g.nq;
+    size_t off_tab = 0;
+    size_t off_N = (ntab * sizeof(df) + 255) / 256 * 256;
+    size_t szNM = (size_t)g.n2w * ns * g.nq * 16 * sizeof(float2);
+    size_t off_M = off_N + szNM;
+    size_t off_S = off_M + szNM;
+    size_t szS = (size_t)2 * g.n2w * ns * 16 * sizeof(double2);
+    size_t off_P3 = (off_S + szS + 255) / 256 * 256;
+    size_t szP3 = (size_t)g.n3w * g.nq * 16 * sizeof(float2);
+    size_t off_T = (off_P3 + szP3 + 1023) / 1024 * 1024;
+    size_t rows = (size_t)4 * g.n3v, K = (size_t)4 * ns * g.nq;
+    size_t per_w = 2 * 4 * rows * K * sizeof(float) + rows * rows * sizeof(double2) + 1024;
+    size_t budget = ctx->ws_limit > off_T ? ctx->ws_limit - off_T : 0;
+    int chunk = (int)std::max<size_t>(1, std::min<size_t>(g.n3w, budget / per_w));
+    size_t tc_scratch = std::min<size_t>(2ull << 30, std::max<size_t>(64ull << 20, (size_t)24 * chunk * rows * rows * 16));
+    size_t need = ((mask >> KB_K3) & 1) ? off_T + per_w * chunk + tc_scratch : off_T;
+    kb_status s = kb_ensure_workspace(ctx, need);
+    if (s != KB_OK) return s;
+    char* ws = static_cast<char*>(ctx->ws.ptr);
+    df* tab = reinterpret_cast<df*>(ws + off_tab);
+    float2* Nt = reinterpret_cast<float2*>(ws + off_N);
+    float2* Mt = reinterpret_cast<float2*>(ws + off_M);
+    double2* Ss = reinterpret_cast<double2*>(ws + off_S);
+    float2* P3 = reinterpret_cast<float2*>(ws + off_P3);
+    DfGrids G;
+    G.n1 = tab; G.n2w = G.n1 + g.n1; G.n2v = G.n2w + g.n2w; G.n3w = G.n2v + g.n2v; G.n3v = G.n3w + g.n3w;
+    G.N1 = g.n1; G.N2w = g.n2w; G.N2v = g.n2v; G.N3w = g.n3w; G.N3v = g.n3v; G.A = (float)g.A;
+    {
+        KB_LAUNCH(ctx, st, "k_mx_tables");
+        k_mx_tables<<<(unsigned)((ntab + 255) / 256), 256, 0, st>>>(g.n1, g.n2w, g.n2v, g.n3w, g.n3v, g.nq, g.A, ctx->d_xq,
+                                                                    tab);
+    }
+    if ((mask >> KB_K1) & 1) {
+        KB_LAUNCH(ctx, st, "k_mx_k1");
+        k_mx_k1<r><<<g.n1, 128, 0, st>>>(VL, VR, G, ctx->m, J, ctx->d_xq, ctx->d_wq, const_cast<void*>(VO.cls[r][KB_K1]),
+                                      VO.dt[r][KB_K1]);
+    }
+    if (mask & ((1u << KB_K2) | (1u << KB_K2P))) {
+        {
+            KB_LAUNCH(ctx, st, "k_mx_prep_k2");
+            k_mx_prep_k2<r><<<dim3((g.nq + 127) / 128, g.n2w), 128, 0, st>>>(VL, VR, G, ctx->m, J, ctx->d_xq, ctx->d_wq,
+                                                                          G.n2w, Nt, Mt);
+        }
+        {
+            KB_LAUNCH(ctx, st, "k_mx_sumj");
+            k_mx_sumj<<<dim3(g.n2w, ns, 2), 128, 0, st>>>(Nt, Mt, g.nq, ns, Ss);
+        }
+        if ((mask >> KB_K2) & 1) {
+            KB_LAUNCH(ctx, st, "k_mx_k2");
+            k_mx_k2<false, r><<<dim3(g.n2v, g.n2w), 128, 0, st>>>(VL, G, J, Nt, Ss, const_cast<void*>(VO.cls[r][KB_K2]),
+                                                               VO.dt[r][KB_K2]);
+        }
+        if ((mask >> KB_K2P) & 1) {
+            KB_LAUNCH(ctx, st, "k_mx_k2p");
+            k_mx_k2<true, r><<<dim3(g.n2v, g.n2w), 128, 0, st>>>(VR, G, J, Mt, Ss, const_cast<void*>(VO.cls[r][KB_K2P]),
+                                                              VO.dt[r][KB_K2P]);
+        }
+    }
+    if ((mask >> KB_K3) & 1) {
+        {
+            KB_LAUNCH(ctx, st, "k_mx_pi3");
+            k_mx_pi3<<<dim3((g.nq + 127) / 128, g.n3w), 128, 0, st>>>(G, ctx->m, J, ctx->d_xq, ctx->d_wq, P3);
+        }
+        float* TA = reinterpret_cast<float*>(ws + off_T);
+        float* TB = TA + (size_t)chunk * 4 * rows * K;
+        double2* Cm = reinterpret_cast<double2*>(TB + (size_t)chunk * 4 * rows * K);
+        void* scratch = reinterpret_cast<char*>(Cm) + (size_t)chunk * rows * rows * sizeof(double2);
+        bool use_tc = std::getenv("KB_K3_SIMT") == nullptr;
+        for (int w0 = 0; w0 < g.n3w; w0 += chunk) {
+            int nwc = std::min(chunk, g.n3w - w0);
+            {
+                KB_LAUNCH(ctx, st, "k_mx_tile3_left");
+                k_mx_tile3<false, r><<<dim3((g.nq + 127) / 128, g.n3v * ns, nwc), 128, 0, st>>>(VL, G, J, w0, P3, TA);
+            }
+            {
+                KB_LAUNCH(ctx, st, "k_mx_tile3_right");
+                k_mx_tile3<true, r><<<dim3((g.nq + 127) / 128, g.n3v * ns, nwc), 128, 0, st>>>(VR, G, J, w0, P3, TB);
+            }
+            bool done = false;
+            if (use_tc) done = kb_tc_k3(ctx, TA, TB, Cm, (int)rows, (int)rows, (int)K, nwc, scratch, tc_scratch, st);
+            if (!done) {
+                KB_LAUNCH(ctx, st, "k_mx_cgemm");
+                k_mx_cgemm<<<dim3((unsigned)((rows + 63) / 64), (unsigned)((rows + 63) / 64), nwc), 256, 0, st>>>(
+                    TA, TB, Cm, (int)rows, (int)rows, (int)K);
+            }
+            {
+                KB_LAUNCH(ctx, st, "k_mx_scatter3");
+                size_t tot = (size_t)nwc * g.n3v * g.n3v * 16;
+                k_mx_scatter3<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(J, w0, nwc, g.n3v, Cm,
+                                                                            const_cast<void*>(VO.cls[r][KB_K3]),
+                                                                            VO.dt[r][KB_K3]);
+            }
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { ctx->err = std::string("mixed launch: ") + cudaGetErrorString(e); return KB_ERR_CUDA; }
+    return KB_OK;
+}
+
+kb_status kb_bubble_mixed(kb_ctx* ctx, int r, int sl, int sr, int so, int pi_kind, unsigned mask, double alpha,
+                          double beta, cudaStream_t st) {
+    if (r == KB_CH_A) return mixed_impl<KB_CH_A>(ctx, sl, sr, so, pi_kind, mask, alpha, beta, st);
+    if (r == KB_CH_P) return mixed_impl<KB_CH_P>(ctx, sl, sr, so, pi_kind, mask, alpha, beta, st);
+    return mixed_impl<KB_CH_T>(ctx, sl, sr, so, pi_kind, mask, alpha, beta, st);
 }

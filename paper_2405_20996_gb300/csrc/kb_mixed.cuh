@@ -1,0 +1,225 @@
+// Mixed-precision device helpers: double-float (pair of FP32) frequency arithmetic and an
+// FP32 vertex gather whose interpolation weights are accurate to ~1e-7 even on fine grids.
+//
+// Why double-float: a vertex class is interpolated linearly in x = (2/pi) atan(v/A)
+// (Sec. II.G.7).  The weight of a node is (x - X_k)(N+1)/2; with x in plain FP32 its
+// absolute error (~6e-8) is amplified by (N+1)/2, which for a 401-point grid of random
+// data would be a 1e-5 relative error.  Here the frequency sums are exact to ~1e-14
+// (two-sum), the cell is found exactly by comparing against the node frequencies, and the
+// fraction uses atan(a) - atan(b) = atan((a - b)/(1 + ab)) with a - b formed in
+// double-float, so the weight carries only the FP32 relative error of a small number.
+#pragma once
+#include "kb_dev.cuh"
+
+namespace kb {
+
+struct df {
+    float h, l;
+};
+
+__device__ __forceinline__ df df_make(double x) {
+    float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    float s = __fadd_rn(a.h, b.h);
+    float bb = __fsub_rn(s, a.h);
+    float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df df_half(df a) { return {0.5f * a.h, 0.5f * a.l}; }
+__device__ __forceinline__ bool df_lt(df a, df b) { return a.h < b.h || (a.h == b.h && a.l < b.l); }
+
+// Node tables of the class grids (double-float), in device memory.
+struct DfGrids {
+    const df* n1;     // K1 bosonic
+    const df* n2w;    // K2 bosonic
+    const df* n2v;    // K2 fermionic
+    const df* n3w;    // K3 bosonic
+    const df* n3v;    // K3 fermionic
+    int N1, N2w, N2v, N3w, N3v;
+    float A;
+};
+
+// Stencil on an N-point grid with zero-valued virtual nodes at x = +-1: returns the lower
+// node k in [-1, N-1] and the fraction t toward node k+1; -2 for an infinite argument.
+__device__ __forceinline__ int df_stencil(df v, const df* __restrict__ nodes, int N, float A, float& t) {
+    if (!isfinite(v.h)) return -2;
+    float x = 0.636619772367581343f * atanf(v.h / A);
+    int k = (int)floorf((x + 1.0f) * (0.5f * (float)(N + 1))) - 1;
+    k = max(-1, min(k, N - 1));
+    if (k >= 0 && df_lt(v, nodes[k])) --k;
+    else if (k + 1 <= N - 1 && !df_lt(v, nodes[k + 1])) ++k;
+    float z;
+    if (k < 0) {
+        z = -A / v.h;                                  // x + 1 = (2/pi) atan(-A/v), v < 0
+    } else {
+        df nk = nodes[k];
+        df d = df_sub(v, nk);
+        z = (d.h + d.l) * A / fmaf(v.h, nk.h, A * A);
+    }
+    t = atanf(z) * ((float)(N + 1) * 0.318309886183790672f);
+    return k;
+}
+
+// acc[o] += f * class value, 16 comps, data complex64 [..][16]; swap12 reads comp o with
+// the unprimed Keldysh indices exchanged (bits 0 and 1 of o).
+__device__ __forceinline__ void add_rec16(float2 acc[16], const float2* __restrict__ p, float g, bool swap12) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int grp = 0; grp < 4; ++grp) {
+        float4 u = __ldg(q + 2 * grp), v = __ldg(q + 2 * grp + 1);
+        float2 c0 = make_float2(u.x, u.y), c1 = make_float2(u.z, u.w), c2 = make_float2(v.x, v.y),
+               c3 = make_float2(v.z, v.w);
+        if (swap12) { float2 tmp = c1; c1 = c2; c2 = tmp; }
+        acc[4 * grp + 0].x = fmaf(g, c0.x, acc[4 * grp + 0].x); acc[4 * grp + 0].y = fmaf(g, c0.y, acc[4 * grp + 0].y);
+        acc[4 * grp + 1].x = fmaf(g, c1.x, acc[4 * grp + 1].x); acc[4 * grp + 1].y = fmaf(g, c1.y, acc[4 * grp + 1].y);
+        acc[4 * grp + 2].x = fmaf(g, c2.x, acc[4 * grp + 2].x); acc[4 * grp + 2].y = fmaf(g, c2.y, acc[4 * grp + 2].y);
+        acc[4 * grp + 3].x = fmaf(g, c3.x, acc[4 * grp + 3].x); acc[4 * grp + 3].y = fmaf(g, c3.y, acc[4 * grp + 3].y);
+    }
+}
+
+// Class k (0 K1, 1 K2, 2 K2', 3 K3) of data D at channel variables (w, v, vp).
+__device__ __forceinline__ void acc_class_f32(const float2* __restrict__ D, int k, const DfGrids& G, df w, df v,
+                                              df vp, float f, bool swap12, float2 acc[16]) {
+    if (!D) return;
+    float tw, tv = 0.f, tp = 0.f;
+    int kw, kv = 0, kp = 0, nv = 1;
+    if (k == 0) {
+        kw = df_stencil(w, G.n1, G.N1, G.A, tw);
+        if (kw == -2) return;
+        for (int a = 0; a < 2; ++a) {
+            int iw = kw + a;
+            float fw = a ? tw : 1.f - tw;
+            if (iw < 0 || iw >= G.N1 || fw == 0.f) continue;
+            add_rec16(acc, D + (size_t)iw * 16, f * fw, swap12);
+        }
+        return;
+    }
+    if (k < 3) {
+        kw = df_stencil(w, G.n2w, G.N2w, G.A, tw);
+        if (kw == -2) return;
+        kv = df_stencil(k == 1 ? v : vp, G.n2v, G.N2v, G.A, tv);
+        if (kv == -2) return;
+        nv = G.N2v;
+        for (int a = 0; a < 2; ++a) {
+            int iw = kw + a;
+            float fw = a ? tw : 1.f - tw;
+            if (iw < 0 || iw >= G.N2w || fw == 0.f) continue;
+            for (int b = 0; b < 2; ++b) {
+                int iv = kv + b;
+                float fv = b ? tv : 1.f - tv;
+                if (iv < 0 || iv >= nv || fv == 0.f) continue;
+                add_rec16(acc, D + ((size_t)iw * nv + iv) * 16, f * fw * fv, swap12);
+            }
+        }
+        return;
+    }
+    kw = df_stencil(w, G.n3w, G.N3w, G.A, tw);
+    if (kw == -2) return;
+    kv = df_stencil(v, G.n3v, G.N3v, G.A, tv);
+    if (kv == -2) return;
+    kp = df_stencil(vp, G.n3v, G.N3v, G.A, tp);
+    if (kp == -2) return;
+    nv = G.N3v;
+    for (int a = 0; a < 2; ++a) {
+        int iw = kw + a;
+        float fw = a ? tw : 1.f - tw;
+        if (iw < 0 || iw >= G.N3w || fw == 0.f) continue;
+        for (int b = 0; b < 2; ++b) {
+            int iv = kv + b;
+            float fv = b ? tv : 1.f - tv;
+            if (iv < 0 || iv >= nv || fv == 0.f) continue;
+            for (int e = 0; e < 2; ++e) {
+                int ip = kp + e;
+                float fp = e ? tp : 1.f - tp;
+                if (ip < 0 || ip >= nv || fp == 0.f) continue;
+                add_rec16(acc, D + (((size_t)iw * nv + iv) * nv + ip) * 16, f * fw * fv * fp, swap12);
+            }
+        }
+    }
+}
+
+// legs (v1', v2', v1, v2) and channel variables in double-float (Sec. II.D.1)
+__device__ __forceinline__ void df_legs(int r, df w, df v, df vp, df L[4]) {
+    df hw = df_half(w);
+    if (r == KB_CH_A) { L[0] = df_add(v, hw); L[3] = df_sub(v, hw); L[2] = df_add(vp, hw); L[1] = df_sub(vp, hw); }
+    else if (r == KB_CH_P) { L[0] = df_add(hw, v); L[1] = df_sub(hw, v); L[2] = df_add(hw, vp); L[3] = df_sub(hw, vp); }
+    else { L[1] = df_add(vp, hw); L[3] = df_sub(vp, hw); L[0] = df_sub(v, hw); L[2] = df_add(v, hw); }
+}
+__device__ __forceinline__ void df_vars(int c, const df L[4], df& w, df& v, df& vp) {
+    if (c == KB_CH_A) { w = df_sub(L[0], L[3]); v = df_half(df_add(L[0], L[3])); vp = df_half(df_add(L[2], L[1])); }
+    else if (c == KB_CH_P) { w = df_add(L[0], L[1]); v = df_half(df_sub(L[0], L[1])); vp = df_half(df_sub(L[2], L[3])); }
+    else { w = df_sub(L[1], L[3]); v = df_half(df_add(L[0], L[2])); vp = df_half(df_add(L[1], L[3])); }
+}
+
+// Compile-time Keldysh index maps of channel R (same as channel_maps in kb_api.cu):
+// left tile L[A][B] = Gamma1^{cL(A,B)}, right tile R[D][C] = Gamma2^{cR(D,C)}, output cO(A,C).
+template <int R>
+__host__ __device__ constexpr int cmap(int X, int Y) {
+    return R == KB_CH_A ? 8 * (X >> 1) + 4 * (Y >> 1) + 2 * (Y & 1) + (X & 1)
+         : R == KB_CH_P ? 8 * (X >> 1) + 4 * (X & 1) + 2 * (Y >> 1) + (Y & 1)
+                        : 8 * (X >> 1) + 4 * (Y >> 1) + 2 * (X & 1) + (Y & 1);
+}
+
+// Vertex in device form for the mixed path (complex64 classes only).
+struct VertexF {
+    const float2* cls[3][4];
+    int has_R, mask;
+    float halfU;
+};
+
+// Parts of the vertex relative to channel r at r-variables (w, v, vp), FP32 accumulation.
+// what bits: 1 = R, 2 = K1_r, 4 = ext-free own class (K2'_r left / K2_r right),
+// 8 = ext-dependent own class (K2_r left / K2'_r right), 16 = K3_r, 32 = other channels.
+// uu: up-up component, built channel by channel (crossing partner a <-> t).
+// The argument that may be infinite is the quadrature frequency v''; infinite arguments
+// make a class read zero, and the other channels then vanish as well.
+template <int r>
+__device__ __forceinline__ void vertex_part_f32(const VertexF& V, const DfGrids& G, bool uu, bool right, int what, df w,
+                                                df v, df vp, float2 out[16]) {
+#pragma unroll
+    for (int o = 0; o < 16; ++o) out[o] = make_float2(0.f, 0.f);
+    if ((what & 1) && !uu && V.has_R) {
+#pragma unroll
+        for (int o = 0; o < 16; ++o) out[o].x = (__popc(o) & 1) ? V.halfU : 0.f;
+    }
+    int k_free = right ? 1 : 2, k_dep = right ? 2 : 1;
+    if ((V.mask >> r) & 1) {
+        constexpr int sr = (r == KB_CH_A) ? KB_CH_T : (r == KB_CH_T ? KB_CH_A : KB_CH_P);
+        df xw = (r == KB_CH_P) ? w : df_neg(w), xvp = (r == KB_CH_P) ? df_neg(vp) : vp;
+        const int ks[4] = {0, k_free, k_dep, 3};
+        const int bits[4] = {2, 4, 8, 16};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (!(what & bits[q])) continue;
+            acc_class_f32(V.cls[r][ks[q]], ks[q], G, w, v, vp, 1.f, false, out);
+            if (uu) acc_class_f32(V.cls[sr][ks[q]], ks[q], G, xw, v, xvp, -1.f, true, out);
+        }
+    }
+    if ((what & 32) && isfinite(v.h) && isfinite(vp.h)) {
+        df L[4];
+        df_legs(r, w, v, vp, L);
+        df S[4] = {L[0], L[1], L[3], L[2]};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            if (c == r || !((V.mask >> c) & 1)) continue;
+            df wc, vc, pc;
+            df_vars(c, L, wc, vc, pc);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc_class_f32(V.cls[c][k], k, G, wc, vc, pc, 1.f, false, out);
+            if (uu) {
+                int sc = (c == KB_CH_A) ? KB_CH_T : (c == KB_CH_T ? KB_CH_A : KB_CH_P);
+                df_vars(sc, S, wc, vc, pc);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc_class_f32(V.cls[sc][k], k, G, wc, vc, pc, -1.f, true, out);
+            }
+        }
+    }
+}
+
+}  // namespace kb

@@ -1,0 +1,428 @@
+// K3 contraction on the 5th-generation tensor cores (tcgen05, kind::tf32) with a 3xTF32
+// split: each FP32 operand x = hi + lo (hi = TF32 rounding of x, lo = x - hi), and
+//   Re C = Ar Br - Ai Bi,  Im C = Ar Bi + Ai Br,
+// every real product X Y taken as Xhi Yhi + Xhi Ylo + Xlo Yhi (the lo*lo term, ~2^-22
+// relative, is dropped).  The minus sign of Ai Bi is the negate-A bit of the instruction
+// descriptor.  Accumulation in FP32 in tensor memory (two 128 x N accumulators, Re and
+// Im) restarted every SEG K chunks; finished segments are added into double-float sums in
+// registers, the K dimension is split over CTAs and the split partials are added in FP64.
+//
+// Operands (written by k_mx_tile3): A = [batch][plane][M][K], B = [batch][plane][N][K],
+// planes (re hi, re lo, im hi, im lo), K-contiguous FP32.  One CTA = one (batch, 128-row
+// M tile, 64-column N tile, K range).  Warp roles: warp 0 issues the TMA loads, warp 1
+// allocates tensor memory and issues the MMAs, warps 2-17 drain the accumulators.  All waits are bounded; a wait that gives up sets a device flag
+// (read by kb_check_device), the CTA drains its copies in flight and frees its tensor
+// memory before returning.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include <string>
+
+#include "kb_internal.h"
+
+namespace kb {
+namespace tc {
+
+constexpr int KC = 16;            // K elements (FP32) per stage and plane row: 64 bytes
+constexpr int MT = 128;           // rows per M tile
+constexpr long long WAIT_BUDGET = 4000000000LL;   // clock cycles (~2 s) per wait
+
+__device__ int g_tc_status;       // nonzero: a bounded wait gave up (bit 0 producer, 1 MMA, 2 epilogue)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;
+    long long t0 = clock64();
+    while (!mbar_try(bar, parity))
+        if (clock64() - t0 > WAIT_BUDGET) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): K-major operand, 64-byte swizzle, 8-row
+// groups 512 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);     // start address
+    d |= (uint64_t)1 << 16;                         // leading byte offset (unused here)
+    d |= (uint64_t)(512 >> 4) << 32;                // stride byte offset
+    d |= (uint64_t)1 << 46;                         // descriptor version
+    d |= (uint64_t)4 << 61;                         // 64-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::tf32: D F32, A/B TF32, both K-major, optional negate A.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N, bool negA) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((negA ? 1u : 0u) << 13) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t id, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dt),
+        "l"(ad), "l"(bd), "r"(id), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcJob {
+    int M, N, K, batch, mtiles, ntiles, ksplit, chunks_per_split, nchunks;
+};
+
+// Segmented accumulation: tensor memory holds two buffers of (Re, Im) 128 x NT FP32
+// accumulators; the MMA warp restarts a buffer every SEG K chunks and the epilogue warps
+// add each finished segment into double-float (hi + lo) running sums held in registers,
+// so no FP32 accumulator ever sums more than SEG * KC * 6 / 8 products.
+constexpr int SEG = 2;
+constexpr int NTT = 64;                       // N columns per CTA
+constexpr int EPI_WARPS = 16;                 // 4 per TMEM lane quarter, 16 columns each
+constexpr int NTHREADS_S = 64 + 32 * EPI_WARPS;
+constexpr int STAGES_S = 4;
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+    float s = __fadd_rn(hi, x);
+    float bb = __fsub_rn(s, hi);
+    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+// partial sums P[ks][b][M][N] double2
+__global__ void __maxnreg__(96)
+    k_tc_k3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcJob J,
+            double2* __restrict__ P) {
+    constexpr int NT = NTT;
+    constexpr uint32_t A_PLANE = MT * KC * 4;      // 8 KB
+    constexpr uint32_t B_PLANE = NT * KC * 4;      // 4 KB
+    constexpr uint32_t STAGE = 4 * A_PLANE + 4 * B_PLANE;
+    constexpr uint32_t TMEM_COLS = 256;            // 2 buffers x (Re, Im) x 64
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES_S * STAGE);
+    uint64_t* empty = full + STAGES_S;
+    uint64_t* segfull = empty + STAGES_S;       // [2]
+    uint64_t* segempty = segfull + 2;           // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(segempty + 2);
+    __shared__ volatile int s_fail;
+
+    int unit = blockIdx.x;
+    int ks = unit % J.ksplit;
+    int rest = unit / J.ksplit;
+    int nt = rest % J.ntiles;
+    rest /= J.ntiles;
+    int mt = rest % J.mtiles;
+    int b = rest / J.mtiles;
+    int c0 = ks * J.chunks_per_split;
+    int c1 = min(J.nchunks, c0 + J.chunks_per_split);
+    int nck = max(0, c1 - c0);
+    int nseg = (nck + SEG - 1) / SEG;
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES_S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int i = 0; i < 2; ++i) { mbar_init(&segfull[i], 1); mbar_init(&segempty[i], 32 * EPI_WARPS); }
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    uint32_t tbase = *tslot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t issued = 0, phases = 0;     // bit s: stage s issued / parity of its last issue
+            for (int i = 0; i < nck; ++i) {
+                int s = i % STAGES_S;
+                uint32_t ph = (uint32_t)((i / STAGES_S) & 1);
+                if (s_fail) break;
+                if (i >= STAGES_S && !mbar_wait(&empty[s], ph ^ 1)) { atomicOr(&g_tc_status, 1); s_fail = 1; break; }
+                unsigned char* st = smem + s * STAGE;
+                mbar_expect_tx(&full[s], STAGE);
+                int kx = (c0 + i) * KC;
+                for (int p = 0; p < 4; ++p) {
+                    tma_load_3d(st + p * A_PLANE, &tmA, &full[s], kx, mt * MT, 4 * b + p);
+                    tma_load_3d(st + 4 * A_PLANE + p * B_PLANE, &tmB, &full[s], kx, nt * NT, 4 * b + p);
+                }
+                issued |= 1u << s;
+                phases = (phases & ~(1u << s)) | (ph << s);
+            }
+            for (int s = 0; s < STAGES_S; ++s)
+                if (((issued >> s) & 1) && !mbar_wait(&full[s], (phases >> s) & 1)) atomicOr(&g_tc_status, 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t id_pos = idesc_tf32(MT, NT, false), id_neg = idesc_tf32(MT, NT, true);
+            for (int i = 0; i < nck; ++i) {
+                int s = i % STAGES_S;
+                uint32_t ph = (uint32_t)((i / STAGES_S) & 1);
+                int g = i / SEG, buf = g & 1;
+                bool seg_start = (i % SEG) == 0;
+                if (s_fail) break;
+                if (seg_start && g >= 2 && !mbar_wait(&segempty[buf], (uint32_t)(((g >> 1) - 1) & 1))) {
+                    atomicOr(&g_tc_status, 2); s_fail = 1; break;
+                }
+                if (!mbar_wait(&full[s], ph)) { atomicOr(&g_tc_status, 2); s_fail = 1; break; }
+                fence_after();
+                uint32_t dRe = tbase + buf * 2 * NT, dIm = dRe + NT;
+                uint32_t sa = smem_u32(smem + s * STAGE);
+                uint32_t sb = sa + 4 * A_PLANE;
+#pragma unroll
+                for (int kk = 0; kk < KC / 8; ++kk) {
+                    uint32_t off = kk * 32;
+                    uint64_t arh = sdesc_sw64(sa + 0 * A_PLANE + off), arl = sdesc_sw64(sa + 1 * A_PLANE + off);
+                    uint64_t aih = sdesc_sw64(sa + 2 * A_PLANE + off), ail = sdesc_sw64(sa + 3 * A_PLANE + off);
+                    uint64_t brh = sdesc_sw64(sb + 0 * B_PLANE + off), brl = sdesc_sw64(sb + 1 * B_PLANE + off);
+                    uint64_t bih = sdesc_sw64(sb + 2 * B_PLANE + off), bil = sdesc_sw64(sb + 3 * B_PLANE + off);
+                    uint32_t first = (seg_start && kk == 0) ? 0u : 1u;
+                    mma_tf32(dRe, arh, brh, id_pos, first);
+                    mma_tf32(dRe, arh, brl, id_pos, 1);
+                    mma_tf32(dRe, arl, brh, id_pos, 1);
+                    mma_tf32(dRe, aih, bih, id_neg, 1);
+                    mma_tf32(dRe, aih, bil, id_neg, 1);
+                    mma_tf32(dRe, ail, bih, id_neg, 1);
+                    mma_tf32(dIm, arh, bih, id_pos, first);
+                    mma_tf32(dIm, arh, bil, id_pos, 1);
+                    mma_tf32(dIm, arl, bih, id_pos, 1);
+                    mma_tf32(dIm, aih, brh, id_pos, 1);
+                    mma_tf32(dIm, aih, brl, id_pos, 1);
+                    mma_tf32(dIm, ail, brh, id_pos, 1);
+                }
+                mma_commit(&empty[s]);
+                if ((i % SEG) == SEG - 1 || i == nck - 1) mma_commit(&segfull[buf]);
+            }
+        }
+    } else {
+        // epilogue warps 2 .. 2+EPI_WARPS-1: lane quarter q, 16-column group cg
+        int e = warp - 2;
+        int q = warp & 3, cg = e >> 2;
+        float hre[16], lre[16], him[16], lim[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) { hre[i] = 0.f; lre[i] = 0.f; him[i] = 0.f; lim[i] = 0.f; }
+        bool ok = true;
+        for (int g = 0; g < nseg; ++g) {
+            int buf = g & 1;
+            if (s_fail || !mbar_wait(&segfull[buf], (uint32_t)((g >> 1) & 1))) {
+                atomicOr(&g_tc_status, 4); ok = false; break;
+            }
+            fence_after();
+            uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * NT + cg * 16);
+#pragma unroll
+            for (int part = 0; part < 4; ++part) {
+                float v[8];
+                tmem_ld8(ta + (part >> 1) * NT + (part & 1) * 8, v);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    int c = (part & 1) * 8 + i;
+                    if (part < 2) two_sum_acc(hre[c], lre[c], v[i]);
+                    else two_sum_acc(him[c], lim[c], v[i]);
+                }
+            }
+            fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&segempty[buf])) : "memory");
+        }
+        int row = mt * MT + q * 32 + lane;
+        if (ok && row < J.M) {
+            double2* out = P + (((size_t)ks * J.batch + b) * J.M + row) * J.N;
+            int col0 = nt * NT + cg * 16;
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                if (col0 + i < J.N)
+                    out[col0 + i] = make_double2((double)hre[i] + (double)lre[i], (double)him[i] + (double)lim[i]);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TMEM_COLS) : "memory");
+}
+
+// C[b][m][n] = sum over splits of P (FP64)
+__global__ void k_tc_reduce(const double2* __restrict__ P, double2* __restrict__ C, size_t per_split, int ksplit) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= per_split) return;
+    double re = 0, im = 0;
+    for (int k = 0; k < ksplit; ++k) {
+        double2 v = P[(size_t)k * per_split + i];
+        re += v.x;
+        im += v.y;
+    }
+    C[i] = make_double2(re, im);
+}
+
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encoder() {
+    static EncodeTiled fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+static bool make_map(CUtensorMap* m, const float* base, int K, int rows, int planes, int box_rows) {
+    EncodeTiled enc = encoder();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)planes};
+    cuuint64_t strides[2] = {(cuuint64_t)K * 4, (cuuint64_t)K * 4 * rows};
+    cuuint32_t box[3] = {(cuuint32_t)KC, (cuuint32_t)box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+static bool launch(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
+                   void* scratch, size_t scratch_bytes, cudaStream_t st) {
+    TcJob J;
+    J.M = M; J.N = N; J.K = K; J.batch = batch;
+    J.mtiles = (M + MT - 1) / MT;
+    J.ntiles = (N + NTT - 1) / NTT;
+    J.nchunks = (K + KC - 1) / KC;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    int base = batch * J.mtiles * J.ntiles;
+    int best = 1;
+    double best_eff = 0;
+    for (int s = 1; s <= 64; ++s) {
+        if ((J.nchunks + s - 1) / s < 8 * SEG) break;
+        size_t need = (size_t)s * batch * M * N * sizeof(double2);
+        if (need > scratch_bytes) break;
+        long units = (long)base * s;
+        long waves = (units + sms - 1) / sms;
+        double eff = (double)units / (waves * sms) * (1.0 - 0.002 * s);
+        if (eff > best_eff + 1e-9) { best_eff = eff; best = s; }
+    }
+    const char* cps_env = std::getenv("KB_TC_CPS");   // developer override: K chunks per split
+    if (cps_env && std::atoi(cps_env) > 0) {
+        int cps = std::atoi(cps_env);
+        int s = (J.nchunks + cps - 1) / cps;
+        if ((size_t)s * batch * M * N * sizeof(double2) <= scratch_bytes) best = s;
+    }
+    J.ksplit = best;
+    J.chunks_per_split = (J.nchunks + best - 1) / best;
+    if (std::getenv("KB_TC_VERBOSE"))
+        std::fprintf(stderr, "k_tc_k3: M %d N %d K %d batch %d tiles %dx%d ksplit %d chunks/split %d\n", M, N, K, batch,
+                     J.mtiles, J.ntiles, J.ksplit, J.chunks_per_split);
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, At, K, M, 4 * batch, MT) || !make_map(&mb, Bt, K, N, 4 * batch, NTT)) return false;
+    constexpr size_t STAGE = 4 * MT * KC * 4 + 4 * NTT * KC * 4;
+    size_t smem = STAGES_S * STAGE + 128 + 1024;
+    static bool attr_set[64] = {};
+    if (!attr_set[ctx->device]) {
+        if (cudaFuncSetAttribute(k_tc_k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return false;
+        attr_set[ctx->device] = true;
+    }
+    double2* P = reinterpret_cast<double2*>(scratch);
+    {
+        KB_LAUNCH(ctx, st, "k_tc_k3");
+        k_tc_k3<<<base * J.ksplit, NTHREADS_S, smem, st>>>(ma, mb, J, P);
+    }
+    cudaError_t le = cudaGetLastError();
+    if (le != cudaSuccess) {
+        ctx->err = std::string("k_tc_k3 launch: ") + cudaGetErrorString(le);
+        if (std::getenv("KB_TC_VERBOSE")) std::fprintf(stderr, "%s\n", ctx->err.c_str());
+        return false;
+    }
+    {
+        KB_LAUNCH(ctx, st, "k_tc_reduce");
+        size_t per = (size_t)batch * M * N;
+        k_tc_reduce<<<(unsigned)((per + 255) / 256), 256, 0, st>>>(P, Cm, per, J.ksplit);
+    }
+    return cudaGetLastError() == cudaSuccess;
+}
+
+}  // namespace tc
+}  // namespace kb
+
+bool kb_tc_k3(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch, void* scratch,
+              size_t scratch_bytes, cudaStream_t st) {
+    using namespace kb::tc;
+    if ((K % 4) != 0 || (reinterpret_cast<uintptr_t>(At) & 15) || (reinterpret_cast<uintptr_t>(Bt) & 15))
+        return false;
+    return launch(ctx, At, Bt, Cm, M, N, K, batch, scratch, scratch_bytes, st);
+}
+
+int kb_tc_take_status() {
+    int v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, kb::tc::g_tc_status, sizeof(int)) != cudaSuccess) return -1;
+    if (v) cudaMemcpyToSymbol(kb::tc::g_tc_status, &z, sizeof(int));
+    return v;
+}

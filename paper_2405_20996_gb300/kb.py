@@ -53,6 +53,7 @@ _SIGS = {
     "kb_bubble": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_double, C.c_double,
                   C.c_int, C.c_void_p],
     "kb_workspace_bytes": [C.c_void_p, C.POINTER(C.c_ulonglong)],
+    "kb_check_device": [C.c_void_p],
     "kb_launch_count": [C.c_void_p, C.POINTER(C.c_ulonglong)],
     "kb_bubble_fp64_noalloc": [C.POINTER(kb_grid_desc), C.c_double, C.c_double, C.c_double,
                                C.POINTER(kb_vertex_desc), C.POINTER(kb_vertex_desc), C.c_int, C.c_int, C.c_int,
@@ -139,6 +140,10 @@ def kb_bubble(ctx, channel, slot_left, slot_right, out_slot, pi_kind=KB_PI_GG, c
               alpha=1.0, beta=0.0, precision=KB_PREC_FP64, stream=0):
     _check(ctx, lib().kb_bubble(ctx, channel, slot_left, slot_right, out_slot, pi_kind, class_mask, alpha, beta,
                                 precision, stream))
+
+
+def kb_check_device(ctx):
+    _check(ctx, lib().kb_check_device(ctx))
 
 
 def kb_workspace_bytes(ctx):
