@@ -214,7 +214,8 @@ def main():
     ch = S.seeded_vertex(GRIDS, U, seed=1000 + rank)        # each rank: its own parameter point
     eng = Engine(GRIDS, NQ, device=local)
     eng.set_model(DELTA, T)
-    eng.set_vertex(0, U=U, has_R=True, channels=ch, dtype=torch.complex64)
+    # the seeded vertex is conjugation- and crossing-symmetric by construction
+    eng.set_vertex(0, U=U, has_R=True, channels=ch, dtype=torch.complex64, symmetric=True)
     out_dt = torch.complex64 if prec == "mixed" else torch.complex128
     eng.alloc_out(1, dtype=out_dt)
     try:

@@ -103,6 +103,16 @@ kb_status kb_set_vertex(kb_ctx *ctx, int slot, int has_R, double U);
  * (Sec. III.C). */
 kb_status kb_set_vertex_channels(kb_ctx *ctx, int slot, unsigned mask);
 
+/* Declare that the vertex in slot `slot` obeys complex conjugation and crossing symmetry
+ * (Sec. II.G.3; in channel variables, conjugation: a,p (w,v,v') -> (w,v',v), t -> (-w,v,v')
+ * with Keldysh (a1'a2'|a1a2) -> (a1a2|a1'a2'), conj and sign (-1)^(1+sum a); crossing:
+ * a,t (w,v,v') -> (-w,v',v), p -> (w,-v,-v') with (a1'a2'|a1a2) -> (a2'a1'|a2a1)).  A bubble
+ * of such a vertex with itself (slot_left == slot_right, beta == 0) then computes only the
+ * independent part of the output (K2 for w >= 0 in a and t, for v >= 0 in p; K1 and K3 for
+ * w >= 0 in a and t; the right K3 tile from the left one) and fills the rest by the same
+ * symmetries.  The caller vouches for the symmetry; nothing checks it. */
+kb_status kb_set_vertex_symmetric(kb_ctx *ctx, int slot, int symmetric);
+
 /* Attach class `cls` of channel `channel` of slot `slot`: DEVICE pointer in the layout
  * above, dtype KB_DT_C128 or KB_DT_C64 (all classes of a slot need not share a dtype).
  * ptr == NULL detaches (the class reads as zero). */

@@ -206,6 +206,16 @@ kb_status kb_set_vertex_channels(kb_ctx* ctx, int slot, unsigned mask) {
     return KB_OK;
 }
 
+kb_status kb_set_vertex_symmetric(kb_ctx* ctx, int slot, int symmetric) {
+    if (!ctx || slot < 0 || slot >= KB_MAX_SLOTS) {
+        if (ctx) ctx->err = "kb_set_vertex_symmetric: bad slot";
+        return KB_ERR_ARG;
+    }
+    if (!ctx->slot_set[slot]) { ctx->err = "kb_set_vertex_symmetric: call kb_set_vertex first"; return KB_ERR_STATE; }
+    ctx->slots[slot].symmetric = symmetric ? 1 : 0;
+    return KB_OK;
+}
+
 kb_status kb_set_vertex_class(kb_ctx* ctx, int slot, int channel, int cls, void* ptr, int dtype) {
     if (!ctx || slot < 0 || slot >= KB_MAX_SLOTS || channel < 0 || channel > 2 || cls < 0 || cls > 3 ||
         (dtype != KB_DT_C128 && dtype != KB_DT_C64)) {

@@ -24,6 +24,7 @@ struct VertexDev {
     int mask;                // channels included (bit c); excluded channels serve only as
                              // crossing partners of the up-up component
     double halfU;            // U / 2
+    int symmetric;           // declared conjugation + crossing symmetric
 };
 
 // Propagator model (Sec. III.A.1, III.C.3).

@@ -154,9 +154,9 @@ __device__ __forceinline__ void store_out(void* out, int dt, size_t e, double2 v
 template <int R>
 __global__ void __launch_bounds__(128) k_mx_k1(VertexF VL, VertexF VR, DfGrids G, Model m, MixedJob J,
                                                const double* __restrict__ xq, const double* __restrict__ wq, void* out,
-                                               int odt) {
+                                               int odt, int w_off) {
     __shared__ double sh[4 * 32];
-    int wi = blockIdx.x;
+    int wi = w_off + blockIdx.x;
     const df* qn = G.n3v + G.N3v;
     df w = G.n1[wi];
     float2 acc[16];
@@ -222,9 +222,10 @@ __global__ void k_mx_sumj(const float2* __restrict__ Nt, const float2* __restric
 // class and are skipped in the loop.
 template <bool RIGHT, int R>
 __global__ void __launch_bounds__(128, 3) k_mx_k2(VertexF V, DfGrids G, MixedJob J, const float2* __restrict__ Tab,
-                                               const double2* __restrict__ Ssum, void* out, int odt) {
+                                               const double2* __restrict__ Ssum, void* out, int odt, int w_off,
+                                               int v_off) {
     __shared__ double sh[4 * 32];
-    int wi = blockIdx.y, vi = blockIdx.x;
+    int wi = w_off + blockIdx.y, vi = v_off + blockIdx.x;
     const df* qn = G.n3v + G.N3v;
     df w = G.n2w[wi], ve = G.n2v[vi];
     float2 acc[16];
@@ -319,11 +320,43 @@ __device__ __forceinline__ void tf32_split(float x, float& hi, float& lo) {
 // (v-dependent part incl. the own K2 class).  Right: row (v', C), same k, value
 // sum_D Pi[B][D] Gamma2_s^{cR[D][C]}(w, v''_j, v').  Four planes per tile:
 // [plane][row][k], plane = 2*(re 0 / im 1) + (hi 0 / lo 1), each plane rows x K floats.
-template <bool RIGHT, int R>
-__global__ void __launch_bounds__(128, 4) k_mx_tile3(VertexF V, DfGrids G, MixedJob J, int w0, const float2* __restrict__ Pt,
-                                                  float* __restrict__ tile) {
+// Keldysh component permutations of the symmetry images (c = 8 b1' + 4 b2' + 2 b1 + b2):
+// conjugation (a1'a2'|a1a2) -> (a1a2|a1'a2'); crossing -> (a2'a1'|a2a1); the conjugation sign
+// is (-1)^(1 + number of quantum indices + 4).
+__host__ __device__ constexpr int perm_c(int c) { return ((c & 3) << 2) | (c >> 2); }
+__host__ __device__ constexpr int perm_x(int c) {
+    return (((c >> 2) & 1) << 3) | (((c >> 3) & 1) << 2) | ((c & 1) << 1) | ((c >> 1) & 1);
+}
+__host__ __device__ constexpr int popc4c(int c) { return (c & 1) + ((c >> 1) & 1) + ((c >> 2) & 1) + ((c >> 3) & 1); }
+__host__ __device__ constexpr float sign_c(int c) { return (popc4c(c) & 1) ? 1.f : -1.f; }
+
+__device__ __forceinline__ void write_planes(float* base, size_t plane, size_t row, size_t K, size_t col,
+                                             const float2 v[4]) {
+    float4 rh, rl, ih, il;
+    tf32_split(v[0].x, rh.x, rl.x); tf32_split(v[1].x, rh.y, rl.y);
+    tf32_split(v[2].x, rh.z, rl.z); tf32_split(v[3].x, rh.w, rl.w);
+    tf32_split(v[0].y, ih.x, il.x); tf32_split(v[1].y, ih.y, il.y);
+    tf32_split(v[2].y, ih.z, il.z); tf32_split(v[3].y, ih.w, il.w);
+    *reinterpret_cast<float4*>(base + 0 * plane + row * K + col) = rh;
+    *reinterpret_cast<float4*>(base + 1 * plane + row * K + col) = rl;
+    *reinterpret_cast<float4*>(base + 2 * plane + row * K + col) = ih;
+    *reinterpret_cast<float4*>(base + 3 * plane + row * K + col) = il;
+}
+
+// K3 tiles.  Left: row (v, A), col k = (s*nq + j)*4 + B, value Gamma1_s^{cL[A][B]}(w, v, v''_j)
+// (v-dependent part incl. the own K2 class).  Right: row (v', C), same k, value
+// sum_D Pi[B][D] Gamma2_s^{cR[D][C]}(w, v''_j, v').  Four planes per tile:
+// [plane][row][k], plane = 2*(re 0 / im 1) + (hi 0 / lo 1), each plane rows x K floats.
+// MODE 0: left tile, 1: right tile, 2: both from one gather of the left record, the right
+// record being its symmetry image at the same w (a, p: conjugation; t: conjugation after
+// crossing, with the spin terms up-down <-> up-down, up-up <-> up-up).
+template <int MODE, int R>
+__global__ void __launch_bounds__(128, 4) k_mx_tile3(VertexF V, DfGrids G, MixedJob J, int w0, int wt0,
+                                                  const float2* __restrict__ Pt, float* __restrict__ tile,
+                                                  float* __restrict__ tileR) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     constexpr int NS = (R == KB_CH_T) ? 2 : 1;
+    constexpr bool RIGHT = (MODE == 1);
     int s = blockIdx.y % NS, vi = blockIdx.y / NS, wl = blockIdx.z;
     if (j >= J.nq) return;
     const df* qn = G.n3v + G.N3v;
@@ -334,47 +367,92 @@ __global__ void __launch_bounds__(128, 4) k_mx_tile3(VertexF V, DfGrids G, Mixed
     else vertex_part_f32<R>(V, G, uu, false, 8 | 16 | 32, w, ve, qn[j], g);
     size_t rows = (size_t)4 * G.N3v, K = (size_t)4 * NS * J.nq;
     size_t plane = rows * K;
-    float* base = tile + (size_t)wl * 4 * plane;
-    size_t col = ((size_t)s * J.nq + j) * 4;
-    float2 val[16];
-    if (!RIGHT) {
+    const float2* P = Pt + ((size_t)(w0 + wl) * J.nq + j) * 16;
+    if (MODE != 1) {
+        float* base = tile + (size_t)(wt0 + wl) * 4 * plane;
+        size_t col = ((size_t)s * J.nq + j) * 4;
 #pragma unroll
-        for (int A = 0; A < 4; ++A)
+        for (int A = 0; A < 4; ++A) {
+            float2 v[4] = {g[cmap<R>(A, 0)], g[cmap<R>(A, 1)], g[cmap<R>(A, 2)], g[cmap<R>(A, 3)]};
+            write_planes(base, plane, (size_t)vi * 4 + A, K, col, v);
+        }
+    }
+    if (MODE != 0) {
+        float2 h[16];
+        int sr = s;
+        if (MODE == 2) {
+            // right record Gamma2^c(w, v'', v' = v) = sign(c) conj(Gamma1^{pi(c)}(w, v, v''))
 #pragma unroll
-            for (int B = 0; B < 4; ++B) val[4 * A + B] = g[cmap<R>(A, B)];
-    } else {
-        const float2* P = Pt + ((size_t)(w0 + wl) * J.nq + j) * 16;
+            for (int c = 0; c < 16; ++c) {
+                constexpr int dummy = 0;
+                (void)dummy;
+                int pc = (R == KB_CH_T) ? perm_x(perm_c(c)) : perm_c(c);
+                float sg = sign_c(c);
+                h[c] = make_float2(sg * g[pc].x, -sg * g[pc].y);
+            }
+            if (R == KB_CH_T) sr = 1 - s;      // left up-up (0) <-> right up-up (1)
+        } else {
 #pragma unroll
-        for (int C = 0; C < 4; ++C)
+            for (int c = 0; c < 16; ++c) h[c] = g[c];
+        }
+        float* base = (MODE == 2 ? tileR : tile) + (size_t)(wt0 + wl) * 4 * plane;
+        size_t col = ((size_t)sr * J.nq + j) * 4;
+#pragma unroll
+        for (int C = 0; C < 4; ++C) {
+            float2 v[4];
 #pragma unroll
             for (int B = 0; B < 4; ++B) {
                 float2 a = make_float2(0, 0);
 #pragma unroll
                 for (int D = 0; D < 4; ++D) {
-                    float2 p = P[4 * B + D], x = g[cmap<R>(D, C)];
+                    float2 p = P[4 * B + D], x = h[cmap<R>(D, C)];
                     a.x = fmaf(p.x, x.x, fmaf(-p.y, x.y, a.x));
                     a.y = fmaf(p.x, x.y, fmaf(p.y, x.x, a.y));
                 }
-                val[4 * C + B] = a;
+                v[B] = a;
             }
-    }
-#pragma unroll
-    for (int X = 0; X < 4; ++X) {
-        size_t row = (size_t)vi * 4 + X;
-        float4 rh, rl, ih, il;
-        float* f[4] = {&rh.x, &rh.y, &rh.z, &rh.w};
-        float* fl[4] = {&rl.x, &rl.y, &rl.z, &rl.w};
-        float* gi[4] = {&ih.x, &ih.y, &ih.z, &ih.w};
-        float* gl[4] = {&il.x, &il.y, &il.z, &il.w};
-#pragma unroll
-        for (int B = 0; B < 4; ++B) {
-            tf32_split(val[4 * X + B].x, *f[B], *fl[B]);
-            tf32_split(val[4 * X + B].y, *gi[B], *gl[B]);
+            write_planes(base, plane, (size_t)vi * 4 + C, K, col, v);
         }
-        *reinterpret_cast<float4*>(base + 0 * plane + row * K + col) = rh;
-        *reinterpret_cast<float4*>(base + 1 * plane + row * K + col) = rl;
-        *reinterpret_cast<float4*>(base + 2 * plane + row * K + col) = ih;
-        *reinterpret_cast<float4*>(base + 3 * plane + row * K + col) = il;
+    }
+}
+
+// Symmetry fill: out[dst] = image of out[src] for the output classes of a bubble of a
+// symmetric vertex with itself (see kb_set_vertex_symmetric).  kind: 0 conjugation after
+// crossing (a: w -> -w), 1 conjugation (t: w -> -w), 2 crossing (p: v -> -v), 3 conjugation
+// with v <-> v' (a, p: K2' from K2), 4 conjugation after crossing at the same w (t: K2'
+// from K2).  Elements: class layout [w][v][v'][16] with nv2/nv3 = 1 where absent.
+__global__ void k_mx_symfill(void* outp, const void* srcp, int dt, int kind, int nw, int nv, int nvp, int w_cnt,
+                             int v_cnt) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)w_cnt * v_cnt * nvp * 16;
+    if (idx >= total) return;
+    int c = idx % 16;
+    size_t rest = idx / 16;
+    int ip = rest % nvp;
+    rest /= nvp;
+    int iv = rest % v_cnt;
+    int iw = (int)(rest / v_cnt);
+    // destination indices and source indices
+    int dw = iw, dv = iv, dp = ip, sw = iw, sv = iv, sp = ip;
+    int pc;
+    bool cj;
+    float sg = 1.f;
+    if (kind == 0 || kind == 1) { sw = nw - 1 - iw; }
+    if (kind == 2) { sv = nv - 1 - iv; sp = nvp - 1 - ip; }
+    if (kind == 0) { pc = perm_x(perm_c(c)); cj = true; }
+    else if (kind == 1) { pc = perm_c(c); cj = true; }
+    else if (kind == 2) { pc = perm_x(c); cj = false; }
+    else if (kind == 3) { pc = perm_c(c); cj = true; }
+    else { pc = perm_x(perm_c(c)); cj = true; }
+    if (cj) sg = sign_c(c);
+    size_t de = (((size_t)dw * nv + dv) * nvp + dp) * 16 + c;
+    size_t se = (((size_t)sw * nv + sv) * nvp + sp) * 16 + pc;
+    if (dt == KB_DT_C128) {
+        double2 v = reinterpret_cast<const double2*>(srcp)[se];
+        reinterpret_cast<double2*>(outp)[de] = make_double2(sg * v.x, cj ? -sg * v.y : sg * v.y);
+    } else {
+        float2 v = reinterpret_cast<const float2*>(srcp)[se];
+        reinterpret_cast<float2*>(outp)[de] = make_float2(sg * v.x, cj ? -sg * v.y : sg * v.y);
     }
 }
 
@@ -487,6 +565,9 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
     VertexF VL = to_vf(ctx->slots[sl], ctx, ok1), VR = to_vf(ctx->slots[sr], ctx, ok2);
     if (!ok1 || !ok2) return KB_ERR_ARG;
     const VertexDev& VO = ctx->slots[so];
+    // a bubble of a declared-symmetric vertex with itself: compute the independent part only
+    const bool sym = (sl == sr) && ctx->slots[sl].symmetric && beta == 0.0 &&
+                     (!((mask >> KB_K2P) & 1) || ((mask >> KB_K2) & 1)) && std::getenv("KB_NO_SYMMETRY") == nullptr;
     MixedJob J;
     J.r = r; J.pi_kind = pi_kind; J.ns = (r == KB_CH_T) ? 2 : 1; J.nq = g.nq;
     J.M = channel_maps(r); J.alpha = alpha; J.beta = beta;
@@ -526,8 +607,9 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
     }
     if ((mask >> KB_K1) & 1) {
         KB_LAUNCH(ctx, st, "k_mx_k1");
-        k_mx_k1<r><<<g.n1, 128, 0, st>>>(VL, VR, G, ctx->m, J, ctx->d_xq, ctx->d_wq, const_cast<void*>(VO.cls[r][KB_K1]),
-                                      VO.dt[r][KB_K1]);
+        int w_off = (sym && r != KB_CH_P) ? g.n1 / 2 : 0;
+        k_mx_k1<r><<<g.n1 - w_off, 128, 0, st>>>(VL, VR, G, ctx->m, J, ctx->d_xq, ctx->d_wq,
+                                              const_cast<void*>(VO.cls[r][KB_K1]), VO.dt[r][KB_K1], w_off);
     }
     if (mask & ((1u << KB_K2) | (1u << KB_K2P))) {
         {
@@ -541,13 +623,14 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
         }
         if ((mask >> KB_K2) & 1) {
             KB_LAUNCH(ctx, st, "k_mx_k2");
-            k_mx_k2<false, r><<<dim3(g.n2v, g.n2w), 128, 0, st>>>(VL, G, J, Nt, Ss, const_cast<void*>(VO.cls[r][KB_K2]),
-                                                               VO.dt[r][KB_K2]);
+            int w_off = (sym && r != KB_CH_P) ? g.n2w / 2 : 0, v_off = (sym && r == KB_CH_P) ? g.n2v / 2 : 0;
+            k_mx_k2<false, r><<<dim3(g.n2v - v_off, g.n2w - w_off), 128, 0, st>>>(
+                VL, G, J, Nt, Ss, const_cast<void*>(VO.cls[r][KB_K2]), VO.dt[r][KB_K2], w_off, v_off);
         }
-        if ((mask >> KB_K2P) & 1) {
+        if (!sym && ((mask >> KB_K2P) & 1)) {
             KB_LAUNCH(ctx, st, "k_mx_k2p");
             k_mx_k2<true, r><<<dim3(g.n2v, g.n2w), 128, 0, st>>>(VR, G, J, Mt, Ss, const_cast<void*>(VO.cls[r][KB_K2P]),
-                                                              VO.dt[r][KB_K2P]);
+                                                              VO.dt[r][KB_K2P], 0, 0);
         }
     }
     if ((mask >> KB_K3) & 1) {
@@ -560,15 +643,23 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
         double2* Cm = reinterpret_cast<double2*>(TB + (size_t)chunk * 4 * rows * K);
         void* scratch = reinterpret_cast<char*>(Cm) + (size_t)chunk * rows * rows * sizeof(double2);
         bool use_tc = std::getenv("KB_K3_SIMT") == nullptr;
-        for (int w0 = 0; w0 < g.n3w; w0 += chunk) {
+        int w3_lo = (sym && r != KB_CH_P) ? g.n3w / 2 : 0;
+        for (int w0 = w3_lo; w0 < g.n3w; w0 += chunk) {
             int nwc = std::min(chunk, g.n3w - w0);
-            {
-                KB_LAUNCH(ctx, st, "k_mx_tile3_left");
-                k_mx_tile3<false, r><<<dim3((g.nq + 127) / 128, g.n3v * ns, nwc), 128, 0, st>>>(VL, G, J, w0, P3, TA);
-            }
-            {
-                KB_LAUNCH(ctx, st, "k_mx_tile3_right");
-                k_mx_tile3<true, r><<<dim3((g.nq + 127) / 128, g.n3v * ns, nwc), 128, 0, st>>>(VR, G, J, w0, P3, TB);
+            if (sym) {
+                KB_LAUNCH(ctx, st, "k_mx_tile3_both");
+                k_mx_tile3<2, r><<<dim3((g.nq + 127) / 128, g.n3v * ns, nwc), 128, 0, st>>>(VL, G, J, w0, 0, P3, TA, TB);
+            } else {
+                {
+                    KB_LAUNCH(ctx, st, "k_mx_tile3_left");
+                    k_mx_tile3<0, r><<<dim3((g.nq + 127) / 128, g.n3v * ns, nwc), 128, 0, st>>>(VL, G, J, w0, 0, P3, TA,
+                                                                                               nullptr);
+                }
+                {
+                    KB_LAUNCH(ctx, st, "k_mx_tile3_right");
+                    k_mx_tile3<1, r><<<dim3((g.nq + 127) / 128, g.n3v * ns, nwc), 128, 0, st>>>(VR, G, J, w0, 0, P3, TB,
+                                                                                               nullptr);
+                }
             }
             bool done = false;
             if (use_tc) done = kb_tc_k3(ctx, TA, TB, Cm, (int)rows, (int)rows, (int)K, nwc, scratch, tc_scratch, st);
@@ -584,6 +675,26 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
                                                                             const_cast<void*>(VO.cls[r][KB_K3]),
                                                                             VO.dt[r][KB_K3]);
             }
+        }
+    }
+    if (sym) {
+        auto fill = [&](int dst_cls, int src_cls, int kind, int nw, int nv, int nvp, int wc, int vc) {
+            KB_LAUNCH(ctx, st, "k_mx_symfill");
+            size_t tot = (size_t)wc * vc * nvp * 16;
+            if (tot == 0) return;
+            k_mx_symfill<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(const_cast<void*>(VO.cls[r][dst_cls]),
+                                                                        VO.cls[r][src_cls], VO.dt[r][dst_cls], kind, nw,
+                                                                        nv, nvp, wc, vc);
+        };
+        int kw = (r == KB_CH_A) ? 0 : 1;                 // w -> -w image: a conj-after-crossing, t conj
+        if (r != KB_CH_P) {
+            if ((mask >> KB_K1) & 1) fill(KB_K1, KB_K1, kw, g.n1, 1, 1, g.n1 / 2, 1);
+            if ((mask >> KB_K3) & 1) fill(KB_K3, KB_K3, kw, g.n3w, g.n3v, g.n3v, g.n3w / 2, g.n3v);
+        }
+        if ((mask >> KB_K2) & 1) {
+            if (r != KB_CH_P) fill(KB_K2, KB_K2, kw, g.n2w, g.n2v, 1, g.n2w / 2, g.n2v);
+            else fill(KB_K2, KB_K2, 2, g.n2w, g.n2v, 1, g.n2w, g.n2v / 2);
+            if ((mask >> KB_K2P) & 1) fill(KB_K2P, KB_K2, r == KB_CH_T ? 4 : 3, g.n2w, g.n2v, 1, g.n2w, g.n2v);
         }
     }
     cudaError_t e = cudaGetLastError();

@@ -42,11 +42,14 @@ class Engine:
     def set_self_energy(self, sigR=None, sigK=None, A_sig=5.0):
         kb.kb_set_self_energy(self.ctx, sigR, sigK, A_sig)
 
-    def set_vertex(self, slot, U=0.0, has_R=False, channels=None, dtype=torch.complex128, include=(0, 1, 2)):
+    def set_vertex(self, slot, U=0.0, has_R=False, channels=None, dtype=torch.complex128, include=(0, 1, 2),
+                   symmetric=False):
         """channels: {channel: (K1, K2, K2p, K3)} arrays (numpy or torch; None = absent);
-        include: channels that are part of the vertex (others: crossing partners only)."""
+        include: channels that are part of the vertex (others: crossing partners only);
+        symmetric: the caller vouches for conjugation + crossing symmetry."""
         kb.kb_set_vertex(self.ctx, slot, has_R, U)
         kb.kb_set_vertex_channels(self.ctx, slot, sum(1 << c for c in include))
+        kb.kb_set_vertex_symmetric(self.ctx, slot, symmetric)
         self.tensors[slot] = {}
         for ch, classes in (channels or {}).items():
             for k, arr in enumerate(classes):

@@ -49,6 +49,7 @@ _SIGS = {
     "kb_set_self_energy": [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p],
     "kb_set_vertex": [C.c_void_p, C.c_int, C.c_int, C.c_double],
     "kb_set_vertex_channels": [C.c_void_p, C.c_int, C.c_uint],
+    "kb_set_vertex_symmetric": [C.c_void_p, C.c_int, C.c_int],
     "kb_set_vertex_class": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int],
     "kb_bubble": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_double, C.c_double,
                   C.c_int, C.c_void_p],
@@ -130,6 +131,10 @@ def kb_set_vertex(ctx, slot, has_R, U=0.0):
 
 def kb_set_vertex_channels(ctx, slot, mask):
     _check(ctx, lib().kb_set_vertex_channels(ctx, slot, mask))
+
+
+def kb_set_vertex_symmetric(ctx, slot, symmetric=True):
+    _check(ctx, lib().kb_set_vertex_symmetric(ctx, slot, int(bool(symmetric))))
 
 
 def kb_set_vertex_class(ctx, slot, channel, cls, dev_ptr, dtype):

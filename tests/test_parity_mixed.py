@@ -24,14 +24,15 @@ def c64_as_128(ch):
     return {c: tuple(a.astype(np.complex64).astype(np.complex128) for a in v) for c, v in ch.items()}
 
 
-def gpu_bubble(cfg, ch, r, precision, pi_kind=0, left=None, sigma=None, out_dtype=torch.complex128, mask=0xF):
+def gpu_bubble(cfg, ch, r, precision, pi_kind=0, left=None, sigma=None, out_dtype=torch.complex128, mask=0xF,
+               symmetric=False):
     from paper_2405_20996_gb300 import kb
     from paper_2405_20996_gb300.engine import Engine
     e = Engine(cfg["grids"], cfg["nq"])
     e.set_model(cfg["Delta"], cfg["T"])
     if sigma is not None:
         e.set_self_energy(*sigma)
-    e.set_vertex(0, U=cfg["U"], has_R=True, channels=c64(ch), dtype=torch.complex64)
+    e.set_vertex(0, U=cfg["U"], has_R=True, channels=c64(ch), dtype=torch.complex64, symmetric=symmetric)
     sl = 0
     if left is not None:
         e.set_vertex(1, U=cfg["U"], has_R=False, channels=c64(left[0]), dtype=torch.complex64, include=left[1])
@@ -88,7 +89,7 @@ def test_mixed_full_size_vs_fp64_gpu_and_oracle_samples():
     P = O.Prop(Delta=cfg["Delta"], T=cfg["T"])
     shapes = {"K1": (401,), "K2": (101, 101), "K2p": (101, 101), "K3": (51, 51, 51)}
     for r in range(3):
-        mx = gpu_bubble(cfg, ch, r, "mixed")
+        mx = gpu_bubble(cfg, ch, r, "mixed", symmetric=True)
         fp = gpu_bubble(cfg, ch, r, "fp64")
         for k in CLS:
             assert rel_err(mx[k], fp[k]) <= TOL, (r, k, rel_err(mx[k], fp[k]))
@@ -114,3 +115,22 @@ def test_tensor_core_contraction_matches_simt_reference():
         os.environ.pop("KB_K3_SIMT", None)
     assert rel_err(tc["K3"], simt["K3"]) <= TOL
     assert np.abs(tc["K3"] - simt["K3"]).max() > 0      # the two contractions are distinct code
+
+
+EVEN = dict(grids=dict(n1=36, n2w=12, n2v=10, n3w=8, n3v=10), nq=161, U=1.2, Delta=1.0, T=0.15)
+
+
+@pytest.mark.parametrize("cfg", [RAGGED, EVEN], ids=["odd", "even"])
+@pytest.mark.parametrize("r", [0, 1, 2])
+def test_symmetric_mode_matches_full_and_oracle(cfg, r):
+    """Kernel (d): for a conjugation- and crossing-symmetric vertex bubbled with itself only
+    the independent part is computed and the rest filled by symmetry; the result equals
+    the full computation and the oracle (odd and even grid sizes)."""
+    ch = seeded_inputs(cfg, seed=51)
+    sym = gpu_bubble(cfg, ch, r, "mixed", symmetric=True)
+    full = gpu_bubble(cfg, ch, r, "mixed", symmetric=False)
+    V = oracle_vertex(cfg, c64_as_128(ch))
+    ref = O.bubble_all(V, V, O.Prop(Delta=cfg["Delta"], T=cfg["T"]), r, cfg["nq"])
+    for k in CLS:
+        assert rel_err(sym[k], full[k]) <= TOL, (r, k, rel_err(sym[k], full[k]))
+        assert rel_err(sym[k], ref[k]) <= TOL, (r, k, rel_err(sym[k], ref[k]))
