@@ -218,71 +218,60 @@ __global__ void k_mx_sumj(const float2* __restrict__ Nt, const float2* __restric
 //   K2own_s(w, v)[A][B] * SN_s(w)[B][C]  (the own K2 class does not depend on v'').
 // K2' (RIGHT = true): out(w, v')[A][C] = sum_j sum_s sum_D M_s(w, j)[A][D] R_s(w, v''_j, v')[D][C]
 //   + SM_s(w)[A][D] * K2'own_s(w, v')[D][C].
-// One CTA (128 threads) per (w, v); the endpoint nodes contribute only through the own
-// class and are skipped in the loop.
+// One CTA (128 threads) per (w, v).  Per tile of 128 nodes every thread gathers one record
+// into shared memory; then the 4x4 contraction runs with one output component per thread
+// (16 components x 8 record groups), so the gather carries no output accumulators.  The
+// endpoint nodes contribute only through the own class and are skipped in the tiles.
 template <bool RIGHT, int R>
-__global__ void __launch_bounds__(128, 3) k_mx_k2(VertexF V, DfGrids G, MixedJob J, const float2* __restrict__ Tab,
+__global__ void __launch_bounds__(128, 4) k_mx_k2(VertexF V, DfGrids G, MixedJob J, const float2* __restrict__ Tab,
                                                const double2* __restrict__ Ssum, void* out, int odt, int w_off,
                                                int v_off) {
-    __shared__ double sh[4 * 32];
+    __shared__ float2 rec[128][17];
+    __shared__ float2 red[8][16];
     int wi = w_off + blockIdx.y, vi = v_off + blockIdx.x;
     const df* qn = G.n3v + G.N3v;
     df w = G.n2w[wi], ve = G.n2v[vi];
-    float2 acc[16];
-    for (int o = 0; o < 16; ++o) acc[o] = make_float2(0, 0);
+    const int tid = threadIdx.x, o = tid & 15, q = tid >> 4;
+    const int A = o >> 2, C = o & 3;
+    float2 acc = make_float2(0.f, 0.f);
     constexpr int NS = (R == KB_CH_T) ? 2 : 1;
-#pragma unroll
+#pragma unroll 1
     for (int s = 0; s < NS; ++s) {
         bool uu = (R == KB_CH_T) && (RIGHT ? s == 1 : s == 0);
         const float2* T = Tab + (((size_t)wi * NS + s) * J.nq) * 16;
-        for (int j = 1 + threadIdx.x; j < J.nq - 1; j += blockDim.x) {
+#pragma unroll 1
+        for (int j0 = 1; j0 < J.nq - 1; j0 += 128) {
+            int j = j0 + tid;
             float2 g[16];
-            if (RIGHT) vertex_part_f32<R>(V, G, uu, true, 16 | 32, w, qn[j], ve, g);
-            else vertex_part_f32<R>(V, G, uu, false, 16 | 32, w, ve, qn[j], g);
-            const float4* tp = reinterpret_cast<const float4*>(T + (size_t)j * 16);
-            if (!RIGHT) {
-                // acc[A][C] += sum_B g(A,B) N[B][C], one row B of N at a time
-#pragma unroll
-                for (int B = 0; B < 4; ++B) {
-                    float4 u = __ldg(tp + 2 * B), v = __ldg(tp + 2 * B + 1);
-                    float2 nb[4] = {make_float2(u.x, u.y), make_float2(u.z, u.w), make_float2(v.x, v.y),
-                                    make_float2(v.z, v.w)};
-#pragma unroll
-                    for (int A = 0; A < 4; ++A) {
-                        float2 x = g[cmap<R>(A, B)];
-#pragma unroll
-                        for (int C = 0; C < 4; ++C) {
-                            float2& a = acc[4 * A + C];
-                            a.x = fmaf(x.x, nb[C].x, fmaf(-x.y, nb[C].y, a.x));
-                            a.y = fmaf(x.x, nb[C].y, fmaf(x.y, nb[C].x, a.y));
-                        }
-                    }
-                }
+            if (j < J.nq - 1) {
+                if (RIGHT) vertex_part_f32<R>(V, G, uu, true, 16 | 32, w, qn[j], ve, g);
+                else vertex_part_f32<R>(V, G, uu, false, 16 | 32, w, ve, qn[j], g);
             } else {
-                // acc[A][C] += sum_D M[A][D] g(D,C), one row A of M at a time
 #pragma unroll
-                for (int A = 0; A < 4; ++A) {
-                    float4 u = __ldg(tp + 2 * A), v = __ldg(tp + 2 * A + 1);
-                    float2 ma[4] = {make_float2(u.x, u.y), make_float2(u.z, u.w), make_float2(v.x, v.y),
-                                    make_float2(v.z, v.w)};
+                for (int c = 0; c < 16; ++c) g[c] = make_float2(0.f, 0.f);
+            }
 #pragma unroll
-                    for (int D = 0; D < 4; ++D)
+            for (int c = 0; c < 16; ++c) rec[tid][c] = g[c];
+            __syncthreads();
+            int nrec = min(128, J.nq - 1 - j0);
+#pragma unroll 1
+            for (int rr = q; rr < nrec; rr += 8) {
+                const float2* t = T + (size_t)(j0 + rr) * 16;
+                if (!RIGHT) {
 #pragma unroll
-                        for (int C = 0; C < 4; ++C) {
-                            float2 y = g[cmap<R>(D, C)];
-                            float2& a = acc[4 * A + C];
-                            a.x = fmaf(ma[D].x, y.x, fmaf(-ma[D].y, y.y, a.x));
-                            a.y = fmaf(ma[D].x, y.y, fmaf(ma[D].y, y.x, a.y));
-                        }
+                    for (int B = 0; B < 4; ++B) cmac2(acc, rec[rr][cmap<R>(A, B)], __ldg(t + 4 * B + C));
+                } else {
+#pragma unroll
+                    for (int D = 0; D < 4; ++D) cmac2(acc, __ldg(t + 4 * A + D), rec[rr][cmap<R>(D, C)]);
                 }
             }
+            __syncthreads();
         }
     }
-    double2 res[16];
-    block_sum16<128>(acc, res, sh);
-    if (threadIdx.x == 0) {
+    // own ext-dependent class: own(w, v) * sum_j N(w, j) (or sum_j M(w, j) * own(w, v'))
+    if (q == 0) {
         df zero = {0.f, 0.f};
-#pragma unroll
+#pragma unroll 1
         for (int s = 0; s < NS; ++s) {
             bool uu = (R == KB_CH_T) && (RIGHT ? s == 1 : s == 0);
             float2 g[16];
@@ -290,20 +279,24 @@ __global__ void __launch_bounds__(128, 3) k_mx_k2(VertexF V, DfGrids G, MixedJob
             else vertex_part_f32<R>(V, G, uu, false, 8, w, ve, zero, g);
             const double2* S = Ssum + (((size_t)(RIGHT ? 1 : 0) * G.N2w + wi) * NS + s) * 16;
 #pragma unroll
-            for (int A = 0; A < 4; ++A)
-#pragma unroll
-                for (int C = 0; C < 4; ++C)
-#pragma unroll
-                    for (int B = 0; B < 4; ++B) {
-                        if (!RIGHT) cfma(res[4 * A + C], c64to128(g[cmap<R>(A, B)]), S[4 * B + C]);
-                        else cfma(res[4 * A + C], S[4 * A + B], c64to128(g[cmap<R>(B, C)]));
-                    }
+            for (int B = 0; B < 4; ++B) {
+                if (!RIGHT) {
+                    double2 sv = S[4 * B + C];
+                    cmac2(acc, g[cmap<R>(A, B)], make_float2((float)sv.x, (float)sv.y));
+                } else {
+                    double2 sv = S[4 * A + B];
+                    cmac2(acc, make_float2((float)sv.x, (float)sv.y), g[cmap<R>(B, C)]);
+                }
+            }
         }
+    }
+    red[q][o] = acc;
+    __syncthreads();
+    if (q == 0) {
+        double re = 0, im = 0;
 #pragma unroll
-        for (int A = 0; A < 4; ++A)
-#pragma unroll
-            for (int C = 0; C < 4; ++C)
-                store_out(out, odt, ((size_t)wi * G.N2v + vi) * 16 + cmap<R>(A, C), res[4 * A + C], J.alpha, J.beta);
+        for (int k = 0; k < 8; ++k) { re += red[k][o].x; im += red[k][o].y; }
+        store_out(out, odt, ((size_t)wi * G.N2v + vi) * 16 + cmap<R>(A, C), make_double2(re, im), J.alpha, J.beta);
     }
 }
 

@@ -45,6 +45,27 @@ struct DfGrids {
     float A;
 };
 
+// Approximate x = (2/pi) atan(v/A) of a frequency; shared by all grids that read it.
+__device__ __forceinline__ float x_of(df v, float A) { return 0.636619772367581343f * atanf(v.h / A); }
+
+// Stencil from a precomputed approximate x (see df_stencil below for the method).
+__device__ __forceinline__ int stencil_x(df v, float x, const df* __restrict__ nodes, int N, float A, float& t) {
+    int k = (int)floorf((x + 1.0f) * (0.5f * (float)(N + 1))) - 1;
+    k = max(-1, min(k, N - 1));
+    if (k >= 0 && df_lt(v, nodes[k])) --k;
+    else if (k + 1 <= N - 1 && !df_lt(v, nodes[k + 1])) ++k;
+    float z;
+    if (k < 0) {
+        z = -A / v.h;
+    } else {
+        df nk = nodes[k];
+        df d = df_sub(v, nk);
+        z = (d.h + d.l) * A / fmaf(v.h, nk.h, A * A);
+    }
+    t = atanf(z) * ((float)(N + 1) * 0.318309886183790672f);
+    return k;
+}
+
 // Stencil on an N-point grid with zero-valued virtual nodes at x = +-1: returns the lower
 // node k in [-1, N-1] and the fraction t toward node k+1; -2 for an infinite argument.
 __device__ __forceinline__ int df_stencil(df v, const df* __restrict__ nodes, int N, float A, float& t) {
@@ -70,17 +91,24 @@ __device__ __forceinline__ int df_stencil(df v, const df* __restrict__ nodes, in
 // the unprimed Keldysh indices exchanged (bits 0 and 1 of o).
 __device__ __forceinline__ void add_rec16(float2 acc[16], const float2* __restrict__ p, float g, bool swap12) {
     const float4* q = reinterpret_cast<const float4*>(p);
+    const float2 gg = make_float2(g, g);
 #pragma unroll
     for (int grp = 0; grp < 4; ++grp) {
         float4 u = __ldg(q + 2 * grp), v = __ldg(q + 2 * grp + 1);
         float2 c0 = make_float2(u.x, u.y), c1 = make_float2(u.z, u.w), c2 = make_float2(v.x, v.y),
                c3 = make_float2(v.z, v.w);
         if (swap12) { float2 tmp = c1; c1 = c2; c2 = tmp; }
-        acc[4 * grp + 0].x = fmaf(g, c0.x, acc[4 * grp + 0].x); acc[4 * grp + 0].y = fmaf(g, c0.y, acc[4 * grp + 0].y);
-        acc[4 * grp + 1].x = fmaf(g, c1.x, acc[4 * grp + 1].x); acc[4 * grp + 1].y = fmaf(g, c1.y, acc[4 * grp + 1].y);
-        acc[4 * grp + 2].x = fmaf(g, c2.x, acc[4 * grp + 2].x); acc[4 * grp + 2].y = fmaf(g, c2.y, acc[4 * grp + 2].y);
-        acc[4 * grp + 3].x = fmaf(g, c3.x, acc[4 * grp + 3].x); acc[4 * grp + 3].y = fmaf(g, c3.y, acc[4 * grp + 3].y);
+        acc[4 * grp + 0] = __ffma2_rn(gg, c0, acc[4 * grp + 0]);
+        acc[4 * grp + 1] = __ffma2_rn(gg, c1, acc[4 * grp + 1]);
+        acc[4 * grp + 2] = __ffma2_rn(gg, c2, acc[4 * grp + 2]);
+        acc[4 * grp + 3] = __ffma2_rn(gg, c3, acc[4 * grp + 3]);
     }
+}
+
+// acc += x * y (complex), two packed FMAs
+__device__ __forceinline__ void cmac2(float2& acc, float2 x, float2 y) {
+    acc = __ffma2_rn(make_float2(x.x, x.x), y, acc);
+    acc = __ffma2_rn(make_float2(-x.y, x.y), make_float2(y.y, y.x), acc);
 }
 
 // Class k (0 K1, 1 K2, 2 K2', 3 K3) of data D at channel variables (w, v, vp).
@@ -173,12 +201,84 @@ struct VertexF {
     float halfU;
 };
 
+// Corners of one class: nd dimensions with lower nodes kk[d], fractions tt[d] and sizes N[d]
+// (row-major data, 16 complex components per record); the corner code exists once.
+__device__ __forceinline__ void corners(const float2* __restrict__ D, int nd, int k0, int k1, int k2, float t0,
+                                        float t1, float t2, int N0, int N1, int N2, float f, bool swap12,
+                                        float2 acc[16]) {
+    int kk[3] = {k0, k1, k2}, N[3] = {N0, N1, N2};
+    float tt[3] = {t0, t1, t2};
+    int st[3] = {1, 1, 1};
+    if (nd == 2) st[0] = N[1];
+    if (nd == 3) { st[1] = N[2]; st[0] = N[1] * N[2]; }
+    int base = kk[0] * st[0] + (nd >= 2 ? kk[1] * st[1] : 0) + (nd == 3 ? kk[2] * st[2] : 0);
+    int ncorner = 1 << nd;
+#pragma unroll 1
+    for (int c = 0; c < ncorner; ++c) {
+        float wgt = f;
+        int off = base;
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (d < nd) {
+                bool bt = (c >> d) & 1;
+                ok = ok && (bt ? (kk[d] + 1 < N[d]) : (kk[d] >= 0));
+                wgt *= bt ? tt[d] : 1.f - tt[d];
+                off += bt ? st[d] : 0;
+            }
+        }
+        if (!ok || wgt == 0.f) continue;
+        add_rec16(acc, D + (size_t)off * 16, wgt, swap12);
+    }
+}
+
+// Stencils of one channel's classes at (w, v, vp): K1 on the K1 grid, K2/K2' on the K2
+// grids, K3 on the K3 grids; flags say which classes contribute.
+struct Sten7 {
+    int kw1, kw2, kw3, kv2, kv3, kp2, kp3;
+    float tw1, tw2, tw3, tv2, tv3, tp2, tp3;
+    bool u0, u1, u2, u3;
+};
+
+__device__ __forceinline__ Sten7 stencils7(const VertexF& V, int ch, unsigned classes, const DfGrids& G, df gw, df gv,
+                                           df gp) {
+    Sten7 S;
+    const bool fw = isfinite(gw.h), fv = isfinite(gv.h), fp = isfinite(gp.h);
+    const float xw = fw ? x_of(gw, G.A) : 0.f, xv = fv ? x_of(gv, G.A) : 0.f, xp = fp ? x_of(gp, G.A) : 0.f;
+    S.u0 = (classes & 1) && V.cls[ch][0] && fw;
+    S.u1 = (classes & 2) && V.cls[ch][1] && fw && fv;
+    S.u2 = (classes & 4) && V.cls[ch][2] && fw && fp;
+    S.u3 = (classes & 8) && V.cls[ch][3] && fw && fv && fp;
+    S.tw1 = S.tw2 = S.tw3 = S.tv2 = S.tv3 = S.tp2 = S.tp3 = 0.f;
+    S.kw1 = S.kw2 = S.kw3 = S.kv2 = S.kv3 = S.kp2 = S.kp3 = 0;
+    if (S.u0) S.kw1 = stencil_x(gw, xw, G.n1, G.N1, G.A, S.tw1);
+    if (S.u1 || S.u2) S.kw2 = stencil_x(gw, xw, G.n2w, G.N2w, G.A, S.tw2);
+    if (S.u1) S.kv2 = stencil_x(gv, xv, G.n2v, G.N2v, G.A, S.tv2);
+    if (S.u2) S.kp2 = stencil_x(gp, xp, G.n2v, G.N2v, G.A, S.tp2);
+    if (S.u3) {
+        S.kw3 = stencil_x(gw, xw, G.n3w, G.N3w, G.A, S.tw3);
+        S.kv3 = stencil_x(gv, xv, G.n3v, G.N3v, G.A, S.tv3);
+        S.kp3 = stencil_x(gp, xp, G.n3v, G.N3v, G.A, S.tp3);
+    }
+    return S;
+}
+
+__device__ __forceinline__ void apply7(const VertexF& V, int ch, const Sten7& S, const DfGrids& G, float f, bool sw,
+                                       float2 out[16]) {
+    if (S.u0) corners(V.cls[ch][0], 1, S.kw1, 0, 0, S.tw1, 0.f, 0.f, G.N1, 1, 1, f, sw, out);
+    if (S.u1) corners(V.cls[ch][1], 2, S.kw2, S.kv2, 0, S.tw2, S.tv2, 0.f, G.N2w, G.N2v, 1, f, sw, out);
+    if (S.u2) corners(V.cls[ch][2], 2, S.kw2, S.kp2, 0, S.tw2, S.tp2, 0.f, G.N2w, G.N2v, 1, f, sw, out);
+    if (S.u3) corners(V.cls[ch][3], 3, S.kw3, S.kv3, S.kp3, S.tw3, S.tv3, S.tp3, G.N3w, G.N3v, G.N3v, f, sw, out);
+}
+
 // Parts of the vertex relative to channel r at r-variables (w, v, vp), FP32 accumulation.
 // what bits: 1 = R, 2 = K1_r, 4 = ext-free own class (K2'_r left / K2_r right),
 // 8 = ext-dependent own class (K2_r left / K2'_r right), 16 = K3_r, 32 = other channels.
 // uu: up-up component, built channel by channel (crossing partner a <-> t).
 // The argument that may be infinite is the quadrature frequency v''; infinite arguments
 // make a class read zero, and the other channels then vanish as well.
+// All stencils of a group of lookups are computed before its corner loads so that the
+// independent stencil computations overlap.
 template <int r>
 __device__ __forceinline__ void vertex_part_f32(const VertexF& V, const DfGrids& G, bool uu, bool right, int what, df w,
                                                 df v, df vp, float2 out[16]) {
@@ -189,36 +289,51 @@ __device__ __forceinline__ void vertex_part_f32(const VertexF& V, const DfGrids&
         for (int o = 0; o < 16; ++o) out[o].x = (__popc(o) & 1) ? V.halfU : 0.f;
     }
     int k_free = right ? 1 : 2, k_dep = right ? 2 : 1;
-    if ((V.mask >> r) & 1) {
-        constexpr int sr = (r == KB_CH_A) ? KB_CH_T : (r == KB_CH_T ? KB_CH_A : KB_CH_P);
-        df xw = (r == KB_CH_P) ? w : df_neg(w), xvp = (r == KB_CH_P) ? df_neg(vp) : vp;
-        const int ks[4] = {0, k_free, k_dep, 3};
-        const int bits[4] = {2, 4, 8, 16};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (!(what & bits[q])) continue;
-            acc_class_f32(V.cls[r][ks[q]], ks[q], G, w, v, vp, 1.f, false, out);
-            if (uu) acc_class_f32(V.cls[sr][ks[q]], ks[q], G, xw, v, xvp, -1.f, true, out);
-        }
-    }
-    if ((what & 32) && isfinite(v.h) && isfinite(vp.h)) {
-        df L[4];
-        df_legs(r, w, v, vp, L);
-        df S[4] = {L[0], L[1], L[3], L[2]};
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            if (c == r || !((V.mask >> c) & 1)) continue;
-            df wc, vc, pc;
-            df_vars(c, L, wc, vc, pc);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc_class_f32(V.cls[c][k], k, G, wc, vc, pc, 1.f, false, out);
-            if (uu) {
-                int sc = (c == KB_CH_A) ? KB_CH_T : (c == KB_CH_T ? KB_CH_A : KB_CH_P);
-                df_vars(sc, S, wc, vc, pc);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) acc_class_f32(V.cls[sc][k], k, G, wc, vc, pc, -1.f, true, out);
+    unsigned own = 0;
+    if (what & 2) own |= 1u << 0;
+    if (what & 4) own |= 1u << k_free;
+    if (what & 8) own |= 1u << k_dep;
+    if (what & 16) own |= 1u << 3;
+    if (!((V.mask >> r) & 1)) own = 0;
+    bool cross = (what & 32) && isfinite(v.h) && isfinite(vp.h);
+    constexpr int sr = (r == KB_CH_A) ? KB_CH_T : (r == KB_CH_T ? KB_CH_A : KB_CH_P);
+    // lookup groups: 0 own direct, 1 own exchanged (uu), 2/3 other channels direct,
+    // 4/5 their exchanged partners (uu)
+#pragma unroll 1
+    for (int grp = 0; grp < 6; ++grp) {
+        int ch;
+        unsigned classes;
+        float f = 1.f;
+        bool sw = false;
+        df gw, gv, gp;
+        if (grp == 0) {
+            if (!own) continue;
+            ch = r; classes = own; gw = w; gv = v; gp = vp;
+        } else if (grp == 1) {
+            if (!own || !uu) continue;
+            ch = sr; classes = own; f = -1.f; sw = true;
+            gw = (r == KB_CH_P) ? w : df_neg(w); gv = v; gp = (r == KB_CH_P) ? df_neg(vp) : vp;
+        } else {
+            if (!cross) continue;
+            int c = (grp & 1) ? ((r == 2) ? 1 : 2) : ((r == 0) ? 1 : 0);   // the two channels != r
+            if (!((V.mask >> c) & 1)) continue;
+            df L[4];
+            df_legs(r, w, v, vp, L);
+            classes = 15;
+            if (grp < 4) {
+                ch = c;
+                df_vars(c, L, gw, gv, gp);
+            } else {
+                if (!uu) continue;
+                ch = (c == KB_CH_A) ? KB_CH_T : (c == KB_CH_T ? KB_CH_A : KB_CH_P);
+                df S4[4] = {L[0], L[1], L[3], L[2]};
+                df_vars(ch, S4, gw, gv, gp);
+                f = -1.f;
+                sw = true;
             }
         }
+        Sten7 S = stencils7(V, ch, classes, G, gw, gv, gp);
+        apply7(V, ch, S, G, f, sw, out);
     }
 }
 
