@@ -54,6 +54,63 @@ def peaks():
 # FP64 FMA pipe: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (max SM clock);
 # measured 1.20 TFLOP/s with a register-resident FMA loop on this GPU model.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP32 pipe: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz; measured 70 TFLOP/s.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# TF32 tensor peak: measured dense bf16 (MEASURED_PEAKS.json) x the nominal tf32/bf16 ratio
+# (1.1 / 2.25 PFLOP/s dense).
+TF32_OVER_BF16 = 1.1 / 2.25
+
+
+def mixed_kernel_work():
+    """Algorithmic work per step of the symmetric mixed path, by kernel (flops).
+    Gather kernels: every interpolation corner adds 16 complex values times a real weight
+    (64 flops); a record (one (w, v, node) of one spin term) has nominally 44 corners in
+    the up-down component (own K3 8 + two other channels x (K1 2 + K2 4 + K2' 4 + K3 8))
+    and 88 in the up-up one (each lookup also at the exchanged legs); the fused K2 kernel
+    adds the 4x4x4 complex contraction (512 flops), the K3 tile kernel the Pi fold of the
+    right record (512 flops) and the own K2 class (4 corners).
+    K3 contraction: 8 M N K useful flops per bosonic frequency (M = N = 4 n3v, K = 4 ns nq);
+    the 3xTF32 split issues three times that on the tensor pipe."""
+    g = GRIDS
+    nq = NQ
+    half = lambda n: n - n // 2
+    w = {}
+    # k_mx_k2 (K2 only; K2' is filled by symmetry)
+    rec_a = half(g["n2w"]) * g["n2v"] * (nq - 2)
+    rec_p = g["n2w"] * half(g["n2v"]) * (nq - 2)
+    rec_t = half(g["n2w"]) * g["n2v"] * (nq - 2)
+    w["k_mx_k2"] = (rec_a + rec_p) * (44 * 64 + 512) + rec_t * ((44 + 88) * 64 + 2 * 512)
+    # k_mx_tile3_both
+    r3a = half(g["n3w"]) * g["n3v"] * nq
+    r3p = g["n3w"] * g["n3v"] * nq
+    r3t = half(g["n3w"]) * g["n3v"] * nq
+    w["k_mx_tile3_both"] = (r3a + r3p) * (48 * 64 + 512) + r3t * ((48 + 96) * 64 + 2 * 512)
+    # k_tc_k3 (useful)
+    M = 4 * g["n3v"]
+    tc = 0.0
+    for r, nw in ((0, half(g["n3w"])), (1, g["n3w"]), (2, half(g["n3w"]))):
+        ns = 2 if r == 2 else 1
+        tc += 8.0 * M * M * (4 * ns * nq) * nw
+    w["k_tc_k3"] = tc
+    return w
+
+
+def roofline_entry(name, ms_total, steps, work, bf16_peak, traffic=None):
+    if name not in work or ms_total <= 0:
+        return None
+    flops = work[name] * steps
+    if name == "k_tc_k3":
+        peak = bf16_peak * TF32_OVER_BF16
+        issued = 3.0 * flops / (ms_total / 1e3) / 1e12
+        return {"kernel": name, "bound": "tensor", "achieved": issued, "peak": peak, "unit": "TFLOP/s",
+                "frac": issued / peak, "traffic": traffic,
+                "note": "issued TF32 flops (3 MMAs per useful product); useful = achieved / 3; peak = measured "
+                        "bf16 x nominal tf32/bf16 ratio"}
+    ach = flops / (ms_total / 1e3) / 1e12
+    return {"kernel": name, "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP32_PEAK_TFLOPS, "traffic": traffic,
+            "note": "algorithmic interpolation + contraction flops (see mixed_kernel_work); peak = FP32 pipe "
+                    "152 SMs x 128 lanes x 2 x 2.07 GHz"}
 
 
 class ClockSampler:
@@ -307,8 +364,19 @@ def main():
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "share": share,
                 "note": "FP64 FMA pipe peak derived from 152 SMs x 2 DFMA/clk x 2.07 GHz"}
     else:
-        roof = {"kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
-                "traffic": None, "share": share}
+        work = mixed_kernel_work() if prec == "mixed" else {}
+        roof = roofline_entry(name, dms, args.steps, work, bf16) or {
+            "kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None}
+        roof["share"] = share
+        others = []
+        for k in ("k_mx_tile3_both", "k_tc_k3"):
+            if k in prof and k != name:
+                e = roofline_entry(k, prof[k][0], args.steps, work, bf16)
+                if e:
+                    e["share"] = prof[k][0] / max(sum(v[0] for v in prof.values()), 1e-30)
+                    others.append(e)
+        roof["others"] = others
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

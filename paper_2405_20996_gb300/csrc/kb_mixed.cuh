@@ -212,23 +212,56 @@ __device__ __forceinline__ void corners(const float2* __restrict__ D, int nd, in
     if (nd == 2) st[0] = N[1];
     if (nd == 3) { st[1] = N[2]; st[0] = N[1] * N[2]; }
     int base = kk[0] * st[0] + (nd >= 2 ? kk[1] * st[1] : 0) + (nd == 3 ? kk[2] * st[2] : 0);
-    int ncorner = 1 << nd;
+    int ncorner = 1 << nd;   // even
+    // two corners per iteration: both records are loaded before either is applied
 #pragma unroll 1
-    for (int c = 0; c < ncorner; ++c) {
-        float wgt = f;
-        int off = base;
-        bool ok = true;
+    for (int c = 0; c < ncorner; c += 2) {
+        float wg[2];
+        int off[2];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            if (d < nd) {
-                bool bt = (c >> d) & 1;
-                ok = ok && (bt ? (kk[d] + 1 < N[d]) : (kk[d] >= 0));
-                wgt *= bt ? tt[d] : 1.f - tt[d];
-                off += bt ? st[d] : 0;
+        for (int e = 0; e < 2; ++e) {
+            int cc = c + e;
+            float wgt = f;
+            int of = base;
+            bool ok = true;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (d < nd) {
+                    bool bt = (cc >> d) & 1;
+                    ok = ok && (bt ? (kk[d] + 1 < N[d]) : (kk[d] >= 0));
+                    wgt *= bt ? tt[d] : 1.f - tt[d];
+                    of += bt ? st[d] : 0;
+                }
             }
+            bool use = ok && wgt != 0.f;
+            wg[e] = use ? wgt : 0.f;
+            off[e] = use ? of : -1;
         }
-        if (!ok || wgt == 0.f) continue;
-        add_rec16(acc, D + (size_t)off * 16, wgt, swap12);
+        float4 u0[8], u1[8];
+        const float4* q0 = reinterpret_cast<const float4*>(D + (size_t)max(off[0], 0) * 16);
+        const float4* q1 = reinterpret_cast<const float4*>(D + (size_t)max(off[1], 0) * 16);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) u0[i] = off[0] >= 0 ? __ldg(q0 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) u1[i] = off[1] >= 0 ? __ldg(q1 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float2 g0 = make_float2(wg[0], wg[0]), g1 = make_float2(wg[1], wg[1]);
+#pragma unroll
+        for (int grp = 0; grp < 4; ++grp) {
+            float2 a0 = make_float2(u0[2 * grp].x, u0[2 * grp].y), a1 = make_float2(u0[2 * grp].z, u0[2 * grp].w);
+            float2 a2 = make_float2(u0[2 * grp + 1].x, u0[2 * grp + 1].y);
+            float2 a3 = make_float2(u0[2 * grp + 1].z, u0[2 * grp + 1].w);
+            float2 b0 = make_float2(u1[2 * grp].x, u1[2 * grp].y), b1 = make_float2(u1[2 * grp].z, u1[2 * grp].w);
+            float2 b2 = make_float2(u1[2 * grp + 1].x, u1[2 * grp + 1].y);
+            float2 b3 = make_float2(u1[2 * grp + 1].z, u1[2 * grp + 1].w);
+            if (swap12) {
+                float2 t0 = a1; a1 = a2; a2 = t0;
+                float2 t1 = b1; b1 = b2; b2 = t1;
+            }
+            acc[4 * grp + 0] = __ffma2_rn(g1, b0, __ffma2_rn(g0, a0, acc[4 * grp + 0]));
+            acc[4 * grp + 1] = __ffma2_rn(g1, b1, __ffma2_rn(g0, a1, acc[4 * grp + 1]));
+            acc[4 * grp + 2] = __ffma2_rn(g1, b2, __ffma2_rn(g0, a2, acc[4 * grp + 2]));
+            acc[4 * grp + 3] = __ffma2_rn(g1, b3, __ffma2_rn(g0, a3, acc[4 * grp + 3]));
+        }
     }
 }
 
