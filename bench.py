@@ -9,6 +9,10 @@ A delivered point is one (w, v, v') x one of the 16 Keldysh components of one cl
 one channel: 7,365,792 per step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64] [--impl reference]
+                 [--channels apt] [--no-e2e] [--no-cpu-baseline]
+
+--channels and --no-e2e narrow a run to one channel's kernels for profiling captures; the
+default line is the three-channel step.
 
 Under torchrun (N > 1) every rank runs its own independent parameter point (weak
 scaling, no data-path collective); value = points of all ranks / max-over-ranks time.
@@ -61,7 +65,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 TF32_OVER_BF16 = 1.1 / 2.25
 
 
-def mixed_kernel_work():
+def mixed_kernel_work(channels=(0, 1, 2)):
     """Algorithmic work per step of the symmetric mixed path, by kernel (flops).
     Gather kernels: every interpolation corner adds 16 complex values times a real weight
     (64 flops); a record (one (w, v, node) of one spin term) has nominally 44 corners in
@@ -79,16 +83,20 @@ def mixed_kernel_work():
     rec_a = half(g["n2w"]) * g["n2v"] * (nq - 2)
     rec_p = g["n2w"] * half(g["n2v"]) * (nq - 2)
     rec_t = half(g["n2w"]) * g["n2v"] * (nq - 2)
-    w["k_mx_k2"] = (rec_a + rec_p) * (44 * 64 + 512) + rec_t * ((44 + 88) * 64 + 2 * 512)
+    w["k_mx_k2"] = ((0 in channels) * rec_a + (1 in channels) * rec_p) * (44 * 64 + 512) + \
+        (2 in channels) * rec_t * ((44 + 88) * 64 + 2 * 512)
     # k_mx_tile3_both
     r3a = half(g["n3w"]) * g["n3v"] * nq
     r3p = g["n3w"] * g["n3v"] * nq
     r3t = half(g["n3w"]) * g["n3v"] * nq
-    w["k_mx_tile3_both"] = (r3a + r3p) * (48 * 64 + 512) + r3t * ((48 + 96) * 64 + 2 * 512)
+    w["k_mx_tile3_both"] = ((0 in channels) * r3a + (1 in channels) * r3p) * (48 * 64 + 512) + \
+        (2 in channels) * r3t * ((48 + 96) * 64 + 2 * 512)
     # k_tc_k3 (useful)
     M = 4 * g["n3v"]
     tc = 0.0
     for r, nw in ((0, half(g["n3w"])), (1, g["n3w"]), (2, half(g["n3w"]))):
+        if r not in channels:
+            continue
         ns = 2 if r == 2 else 1
         tc += 8.0 * M * M * (4 * ns * nq) * nw
     w["k_tc_k3"] = tc
@@ -248,7 +256,12 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64"])
     ap.add_argument("--ref-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--channels", default="apt", help="subset of a, p, t (profiling captures)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling captures)")
     args = ap.parse_args()
+    chans = tuple(sorted({"apt".index(c) for c in args.channels}))
+    if not chans:
+        ap.error("--channels needs at least one of a, p, t")
     if args.impl == "reference":
         return run_reference(args)
 
@@ -287,8 +300,10 @@ def main():
             raise
     stream = torch.cuda.current_stream(dev)
 
+    points = POINTS_PER_STEP * len(chans) // 3
+
     def step():
-        for r in range(3):
+        for r in chans:
             eng.bubble(r, 0, 0, 1, precision=prec, stream=stream)
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # 256 MB > 129 MB L2
@@ -324,30 +339,33 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
     ms_step = ms_max / args.steps
-    value = ws * POINTS_PER_STEP / (ms_step / 1e3)
+    value = ws * points / (ms_step / 1e3)
 
     # ---- end to end through the public API: pinned host inputs -> device -> bubbles -> host ----
-    host_in = {k: v.to("cpu").pin_memory() for k, v in eng.tensors[0].items()}
-    host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in eng.tensors[1].items()}
-    h2d = sum(v.numel() * v.element_size() for v in host_in.values())
-    d2h = sum(v.numel() * v.element_size() for v in host_out.values())
-    e2e_ms = []
-    for it in range(args.warmup + args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for k, v in host_in.items():
-            eng.tensors[0][k].copy_(v, non_blocking=True)
-        step()
-        for k, v in host_out.items():
-            v.copy_(eng.tensors[1][k], non_blocking=True)
-        torch.cuda.synchronize()
-        if it >= args.warmup:
-            e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    te = torch.tensor([sum(e2e_ms) / len(e2e_ms)], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_val = ws * POINTS_PER_STEP / (float(te.item()) / 1e3)
+    e2e = None
+    if not args.no_e2e:
+        host_in = {k: v.to("cpu").pin_memory() for k, v in eng.tensors[0].items()}
+        host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in eng.tensors[1].items()}
+        h2d = sum(v.numel() * v.element_size() for v in host_in.values())
+        d2h = sum(v.numel() * v.element_size() for v in host_out.values())
+        e2e_ms = []
+        for it in range(args.warmup + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k, v in host_in.items():
+                eng.tensors[0][k].copy_(v, non_blocking=True)
+            step()
+            for k, v in host_out.items():
+                v.copy_(eng.tensors[1][k], non_blocking=True)
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        te = torch.tensor([sum(e2e_ms) / len(e2e_ms)], dtype=torch.float64, device=dev)
+        if dist:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_val = ws * points / (float(te.item()) / 1e3)
+        e2e = {"value": e2e_val, "unit": "points/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # ---- roofline of the dominant kernel (its CUDA-event time over the timed region) ----
     hbm, bf16, src = peaks()
@@ -364,7 +382,7 @@ def main():
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "share": share,
                 "note": "FP64 FMA pipe peak derived from 152 SMs x 2 DFMA/clk x 2.07 GHz"}
     else:
-        work = mixed_kernel_work() if prec == "mixed" else {}
+        work = mixed_kernel_work(chans) if prec == "mixed" else {}
         roof = roofline_entry(name, dms, args.steps, work, bf16) or {
             "kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
             "traffic": None}
@@ -379,7 +397,7 @@ def main():
         roof["others"] = others
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and len(chans) == 3:
         rate, cores, desc, _ = oracle_rate(budget_s=args.ref_budget)
         cpu = {"value": rate, "unit": "points/s", "cores": cores, "kind": "oracle", "sample": desc}
 
@@ -387,10 +405,11 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if prec == "mixed" else "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "precision": prec, "points_per_step": POINTS_PER_STEP,
+                "config": {"workload": WORKLOAD if len(chans) == 3 else WORKLOAD.replace("a,p,t", args.channels),
+                           "precision": prec, "points_per_step": points,
                            "l2": "flushed (256 MB write) before every timed step", "parallelism": "weak: one "
                            "independent parameter point per GPU"},
-                "e2e": {"value": e2e_val, "unit": "points/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "e2e": e2e,
                 "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
                 "kernels_ms": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
                 "peaks_source": src}
