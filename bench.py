@@ -162,6 +162,19 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def weak_scaling_value(points_per_rank, ms_local, dist=None, device="cpu"):
+    """Whole-job throughput of a weak-scaling run: every rank processes points_per_rank
+    points per step; the job's step time is the maximum of the ranks' times.  Returns
+    (points/s over all ranks, max step time in ms)."""
+    import torch
+    ws = dist.get_world_size() if dist is not None else 1
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ws * points_per_rank / (ms_max / 1e3), ms_max
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -334,12 +347,7 @@ def main():
     prof = kb.kb_profile_read(eng.ctx)
     kb.kb_profile_enable(eng.ctx, False)
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    ms_step = ms_max / args.steps
-    value = ws * points / (ms_step / 1e3)
+    value, ms_step = weak_scaling_value(points, ms / args.steps, dist, dev)
 
     # ---- end to end through the public API: pinned host inputs -> device -> bubbles -> host ----
     e2e = None
@@ -361,10 +369,7 @@ def main():
             torch.cuda.synchronize()
             if it >= args.warmup:
                 e2e_ms.append(1e3 * (time.perf_counter() - t0))
-        te = torch.tensor([sum(e2e_ms) / len(e2e_ms)], dtype=torch.float64, device=dev)
-        if dist:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e_val = ws * points / (float(te.item()) / 1e3)
+        e2e_val, _ = weak_scaling_value(points, sum(e2e_ms) / len(e2e_ms), dist, dev)
         e2e = {"value": e2e_val, "unit": "points/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # ---- roofline of the dominant kernel (its CUDA-event time over the timed region) ----
