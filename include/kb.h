@@ -129,6 +129,36 @@ kb_status kb_set_vertex_class(kb_ctx *ctx, int slot, int channel, int cls, void 
 kb_status kb_bubble(kb_ctx *ctx, int channel, int slot_left, int slot_right, int out_slot, int pi_kind,
                     unsigned class_mask, double alpha, double beta, int precision, void *stream);
 
+/* Vector-jacobian product (adjoint) of kb_bubble (the differentiation pattern of the
+ * method: gradients of a scalar loss through B_r, e.g. for Newton-Krylov solves of the
+ * parquet equations, Sec. III.B).
+ *
+ * Convention: gradients of a real loss L on the real embedding (real and imaginary parts
+ * as independent reals), bar(z) = dL/dRe z + i dL/dIm z, PyTorch's convention for complex
+ * tensors.  The classes (class_mask) of channel `channel` of slot gout_slot hold
+ * bar(out) for out = alpha B_r(Γ_left, Γ_right; Π) (+ beta out, which does not involve the
+ * vertices).  The call ACCUMULATES:
+ *   grad_left_slot  (or -1): classes += alpha J_left^H  bar(out), J_left = dB/d(stored
+ *                    classes of slot_left) — every attached class of every channel of the
+ *                    gradient slot receives its share (interpolation corners, channel
+ *                    conversion and the up-up crossing partners of the forward);
+ *   grad_right_slot (or -1): the same for slot_right (the two may be the same slot, then
+ *                    both contributions add, as for B(Γ, Γ));
+ *   grad_GR_K1/K2/K3 (device, complex128, or NULL): the gradient with respect to G^R at the
+ *                    propagator samples of the output classes on that bosonic grid:
+ *                    [w][node][side], w on the K1 (n1), K2 (n2w; K2 and K2' add) or K3
+ *                    (n3w) grid, side 0 the propagator at v''+w/2 (a, t) or w/2+v'' (p),
+ *                    side 1 at v''-w/2 or w/2-v''; G^A = (G^R)* and G^K = tanh(v/2T)(G^R -
+ *                    G^A) are taken as functions of G^R (equilibrium FDR, Sec. II.D.4).
+ *                    Needs pi_kind KB_PI_GG and no self-energy table (else
+ *                    KB_ERR_UNSUPPORTED); the tail nodes (v'' = ±inf) carry no G dependence.
+ * Gradient classes must be complex128 and must not alias any input.  The bare part
+ * R = Γ0 is a fixed parameter (no gradient).  precision: KB_PREC_FP64 only (others return
+ * KB_ERR_UNSUPPORTED). */
+kb_status kb_bubble_vjp(kb_ctx *ctx, int channel, int slot_left, int slot_right, int gout_slot, int pi_kind,
+                        unsigned class_mask, double alpha, int grad_left_slot, int grad_right_slot,
+                        void *grad_GR_K1, void *grad_GR_K2, void *grad_GR_K3, int precision, void *stream);
+
 /* Synchronise the context's device and report device-side failures since the last check:
  * KB_ERR_TIMEOUT if a bounded wait inside a tensor-core kernel gave up (that kernel's output
  * is then incomplete), KB_ERR_CUDA for a CUDA error.  Clears the timeout flag. */

@@ -305,12 +305,20 @@ typedef struct {
     double w, v, vp;
 } bctx;
 
+/* Arguments of the two propagators of the bubble in channel r (Sec. II.D.5):
+ * a, t: v'' + w/2 and v'' - w/2; p: w/2 + v'' and w/2 - v''. */
+static void prop_args(int r, double w, double nupp, double *a3, double *a4) {
+    if (r == 1) { *a3 = w / 2 + nupp; *a4 = w / 2 - nupp; }
+    else { *a3 = nupp + w / 2; *a4 = nupp - w / 2; }
+}
+
 /* Pi^{b3 b3' b4 b4'} = P1^{b3|b3'}(arg3) P2^{b4|b4'}(arg4) summed over the pair kinds. */
 static void pi_matrix(const bctx *B, double nupp, int at_inf, double sgn_inf, cplx Pi[2][2][2][2]) {
     double w = B->w;
     double a3, a4, s3, s4;
-    if (B->r == 1) { a3 = w / 2 + nupp; a4 = w / 2 - nupp; s3 = 1; s4 = -1; }
-    else { a3 = nupp + w / 2; a4 = nupp - w / 2; s3 = 1; s4 = 1; }
+    prop_args(B->r, w, nupp, &a3, &a4);
+    s3 = 1;
+    s4 = (B->r == 1) ? -1 : 1;
     cplx G3[2][2], G4[2][2], S3[2][2], S4[2][2];
     if (at_inf) {
         /* lim v''^2 P(a3) P(a4) = s3 s4 * asym * asym (independent of the sign of v'') */
@@ -335,18 +343,24 @@ static void pi_matrix(const bctx *B, double nupp, int at_inf, double sgn_inf, cp
                 }
 }
 
+/* Components of the left and right vertex that meet output component o and internal
+ * indices (b3, b3', b4, b4') in channel r (leg routing of the bubble, see the header). */
+static void contract_idx(int r, int o, int b3, int b3p, int b4, int b4p, int *li, int *ri) {
+    int a1p = (o >> 3) & 1, a2p = (o >> 2) & 1, a1 = (o >> 1) & 1, a2 = o & 1;
+    if (r == 0) { *li = kidx(a1p, b4p, b3, a2); *ri = kidx(b3p, a2p, a1, b4); }
+    else if (r == 1) { *li = kidx(a1p, a2p, b3, b4); *ri = kidx(b3p, b4p, a1, a2); }
+    else { *li = kidx(a1p, b3p, a1, b4); *ri = kidx(b4p, a2p, b3, a2); }
+}
+
 static void contract(int r, const cplx L[16], const cplx Pi[2][2][2][2], const cplx R[16], cplx F[16]) {
     for (int o = 0; o < 16; ++o) {
-        int a1p = (o >> 3) & 1, a2p = (o >> 2) & 1, a1 = (o >> 1) & 1, a2 = o & 1;
         cplx s = 0;
         for (int b3 = 0; b3 < 2; ++b3)
             for (int b3p = 0; b3p < 2; ++b3p)
                 for (int b4 = 0; b4 < 2; ++b4)
                     for (int b4p = 0; b4p < 2; ++b4p) {
                         int li, ri;
-                        if (r == 0) { li = kidx(a1p, b4p, b3, a2); ri = kidx(b3p, a2p, a1, b4); }
-                        else if (r == 1) { li = kidx(a1p, a2p, b3, b4); ri = kidx(b3p, b4p, a1, a2); }
-                        else { li = kidx(a1p, b3p, a1, b4); ri = kidx(b4p, a2p, b3, a2); }
+                        contract_idx(r, o, b3, b3p, b4, b4p, &li, &ri);
                         s += L[li] * Pi[b3][b3p][b4][b4p] * R[ri];
                     }
         F[o] += s;
@@ -555,4 +569,267 @@ int og_bubble_points_adaptive(const ovtx *V1, const ovtx *V2, const oprop *P, in
         failed |= S.fail;
     }
     return failed ? -(int)(total > 0x7fffffff ? 0x7fffffff : total) : (int)(total > 0x7fffffff ? 0x7fffffff : total);
+}
+
+/* ------------------------------------------------------------------------------------
+ * Adjoint of the bubble (vector-Jacobian product).
+ *
+ * Convention: gradients of a real loss L on the real embedding (real and imaginary parts
+ * as independent reals), bar(z) = dL/dRe z + i dL/dIm z.  B depends linearly
+ * (holomorphically) on the stored class values of either vertex, so the gradient with
+ * respect to a stored value e is sum over outputs o of conj(dB_o/de) bar(B_o).
+ * With respect to the retarded propagator at one sample frequency, the advanced and
+ * Keldysh components are functions of it in equilibrium without a self-energy table:
+ * G^A = (G^R)*, G^K = tanh(v/2T) (G^R - G^A) (the FDR, Sec. II.D.4), so
+ *     bar(G^R) = bar(G^{1|2}) + conj(bar(G^{2|1})) + th (bar(G^{1|1}) - conj(bar(G^{1|1}))).
+ * The bare part R = Gamma_0 is a fixed parameter and gets no gradient.
+ * ------------------------------------------------------------------------------------ */
+typedef struct { cplx *K1[3], *K2[3], *K2p[3], *K3[3]; } ograd;   /* vertex shapes; NULL = not wanted */
+
+static size_t cls_elems(const ovtx *V, int k) {
+    if (k == 0) return (size_t)V->n1 * 16;
+    if (k < 3) return (size_t)V->n2w * V->n2v * 16;
+    return (size_t)V->n3w * V->n3v * V->n3v * 16;
+}
+
+static cplx **grad_slot(ograd *G, int c, int k) {
+    return k == 0 ? &G->K1[c] : k == 1 ? &G->K2[c] : k == 2 ? &G->K2p[c] : &G->K3[c];
+}
+
+/* Transpose of add_class: grad(class)[corner] += f * weight * bar. */
+static void add_class_adj(const ovtx *V, ograd *Gd, int ch, int k, double w, double v, double vp, double f,
+                          const cplx bar[16]) {
+    cplx *D = *grad_slot(Gd, ch, k);
+    if (!D) return;
+    int iw[2], iv[2], ip[2];
+    double ww[2], wv[2], wp[2];
+    if (k == 0) {
+        int mw = stencil(w, V->n1, V->A, iw, ww);
+        for (int a = 0; a < mw; ++a)
+            for (int c = 0; c < 16; ++c) D[(size_t)iw[a] * 16 + c] += f * ww[a] * bar[c];
+    } else if (k == 1 || k == 2) {
+        double u = (k == 1) ? v : vp;
+        int mw = stencil(w, V->n2w, V->A, iw, ww);
+        int mv = stencil(u, V->n2v, V->A, iv, wv);
+        for (int a = 0; a < mw; ++a)
+            for (int b = 0; b < mv; ++b) {
+                cplx *p = D + ((size_t)iw[a] * V->n2v + iv[b]) * 16;
+                double g = f * ww[a] * wv[b];
+                for (int c = 0; c < 16; ++c) p[c] += g * bar[c];
+            }
+    } else {
+        int mw = stencil(w, V->n3w, V->A, iw, ww);
+        int mv = stencil(v, V->n3v, V->A, iv, wv);
+        int mp = stencil(vp, V->n3v, V->A, ip, wp);
+        for (int a = 0; a < mw; ++a)
+            for (int b = 0; b < mv; ++b)
+                for (int e = 0; e < mp; ++e) {
+                    cplx *p = D + (((size_t)iw[a] * V->n3v + iv[b]) * V->n3v + ip[e]) * 16;
+                    double g = f * ww[a] * wv[b] * wp[e];
+                    for (int c = 0; c < 16; ++c) p[c] += g * bar[c];
+                }
+    }
+}
+
+/* Transpose of vertex_select: bar holds the gradient of the 16 selected components. */
+static void vertex_select_adj(const ovtx *V, ograd *Gd, int r, int spin_uu, int side_right, int sel, double w,
+                              double v, double vp, const cplx bar[16]) {
+    int k_ext_free = side_right ? 1 : 2;
+    int k_ext_dep = side_right ? 2 : 1;
+    int want_other = (sel != SEL_ZERO);
+    cplx bown[4][16], both[16];
+    memset(bown, 0, sizeof(bown));
+    memset(both, 0, sizeof(both));
+    for (int c = 0; c < 16; ++c) {
+        if (sel != SEL_NU) { bown[0][c] += bar[c]; bown[k_ext_free][c] += bar[c]; }
+        if (sel != SEL_ZERO) { bown[k_ext_dep][c] += bar[c]; bown[3][c] += bar[c]; both[c] += bar[c]; }
+    }
+    /* direct (up-down) term of parts_ud */
+    if ((V->mask >> r) & 1)
+        for (int k = 0; k < 4; ++k) add_class_adj(V, Gd, r, k, w, v, vp, 1.0, bown[k]);
+    double L[4];
+    legs_from(r, w, v, vp, L);
+    if (want_other)
+        for (int c = 0; c < 3; ++c) {
+            if (c == r || !((V->mask >> c) & 1)) continue;
+            double wc, vc, pc;
+            chan_from(c, L, &wc, &vc, &pc);
+            for (int k = 0; k < 4; ++k) add_class_adj(V, Gd, c, k, wc, vc, pc, 1.0, both);
+        }
+    if (!spin_uu) return;
+    /* exchanged term of parts_uu: X[cc] -= X'[sw(cc)], so bar(X')[sw(cc)] = -bar(X)[cc] */
+    cplx sown[4][16], soth[16];
+    for (int cc = 0; cc < 16; ++cc) {
+        int b1p = (cc >> 3) & 1, b2p = (cc >> 2) & 1, b1 = (cc >> 1) & 1, b2 = cc & 1;
+        int sw = kidx(b1p, b2p, b2, b1);
+        for (int k = 0; k < 4; ++k) sown[k][sw] = -bown[k][cc];
+        soth[sw] = -both[cc];
+    }
+    double S[4];
+    S[0] = L[0]; S[1] = L[1]; S[2] = L[3]; S[3] = L[2];
+    for (int c = 0; c < 3; ++c) {
+        if (!((V->mask >> c) & 1)) continue;
+        int sc = (c == 0) ? 2 : (c == 2) ? 0 : 1;
+        double wc, vc, pc;
+        if (c == r) {
+            if (r == 1) { wc = w; vc = v; pc = -vp; }
+            else { wc = -w; vc = v; pc = vp; }
+            for (int k = 0; k < 4; ++k) add_class_adj(V, Gd, sc, k, wc, vc, pc, 1.0, sown[k]);
+        } else {
+            if (!want_other) continue;
+            chan_from(sc, S, &wc, &vc, &pc);
+            for (int k = 0; k < 4; ++k) add_class_adj(V, Gd, sc, k, wc, vc, pc, 1.0, soth);
+        }
+    }
+}
+
+/* Adjoint of one output point: bar holds bar(B_o) for its 16 components. gGR (or NULL)
+ * is this point's bosonic row of the propagator-gradient table, [j][side] with side 0 the
+ * propagator at arg3 and side 1 the one at arg4 (prop_args). */
+static void bubble_point_vjp(const bctx *B, int Nq, const double *xq, const double *wq, const cplx gbar[16],
+                             ograd *G1, ograd *G2, cplx *gGR) {
+    const ovtx *V1 = B->V1, *V2 = B->V2;
+    double A = V1->A, cr = chan_prefactor(B->r);
+    int nterm = (B->r == 2) ? 2 : 1;
+    for (int j = 0; j < Nq; ++j) {
+        double x = xq[j];
+        int at_inf = (x <= -1.0 || x >= 1.0);
+        double nupp, jac;
+        if (at_inf) {
+            nupp = (x > 0) ? INFINITY : -INFINITY;
+            jac = PI / (2.0 * A);
+        } else {
+            double tn = tan(PI * x / 2);
+            nupp = A * tn;
+            jac = A * PI / 2 * (1.0 + tn * tn);
+        }
+        cplx sj = cr * wq[j] * jac / (2.0 * PI * I);
+        cplx Pi[2][2][2][2];
+        pi_matrix(B, nupp, at_inf, x, Pi);
+        cplx bPi[2][2][2][2];
+        memset(bPi, 0, sizeof(bPi));
+        for (int term = 0; term < nterm; ++term) {
+            /* a, p: (ud, ud); t: term 0 = (uu, ud), term 1 = (ud, uu) */
+            int uuL = (B->r == 2) && term == 0, uuR = (B->r == 2) && term == 1;
+            cplx L[16], R[16], bL[16], bR[16];
+            vertex_select(V1, B->r, uuL, 0, B->lsel, B->w, B->v, nupp, L);
+            vertex_select(V2, B->r, uuR, 1, B->rsel, B->w, nupp, B->vp, R);
+            memset(bL, 0, sizeof(bL));
+            memset(bR, 0, sizeof(bR));
+            for (int o = 0; o < 16; ++o)
+                for (int b3 = 0; b3 < 2; ++b3)
+                    for (int b3p = 0; b3p < 2; ++b3p)
+                        for (int b4 = 0; b4 < 2; ++b4)
+                            for (int b4p = 0; b4p < 2; ++b4p) {
+                                int li, ri;
+                                contract_idx(B->r, o, b3, b3p, b4, b4p, &li, &ri);
+                                cplx p = Pi[b3][b3p][b4][b4p];
+                                bL[li] += conj(sj * p * R[ri]) * gbar[o];
+                                bR[ri] += conj(sj * L[li] * p) * gbar[o];
+                                bPi[b3][b3p][b4][b4p] += conj(sj * L[li] * R[ri]) * gbar[o];
+                            }
+            if (G1) vertex_select_adj(V1, G1, B->r, uuL, 0, B->lsel, B->w, B->v, nupp, bL);
+            if (G2) vertex_select_adj(V2, G2, B->r, uuR, 1, B->rsel, B->w, nupp, B->vp, bR);
+        }
+        if (!gGR || at_inf || B->pi_kind != 0) continue;
+        /* Pi = G(a3) (x) G(a4); then G^A = (G^R)*, G^K = th (G^R - G^A) */
+        double a3, a4;
+        prop_args(B->r, B->w, nupp, &a3, &a4);
+        cplx G3[2][2], G4[2][2], bG3[2][2], bG4[2][2];
+        prop_matrix(B->P, 0, a3, G3);
+        prop_matrix(B->P, 0, a4, G4);
+        memset(bG3, 0, sizeof(bG3));
+        memset(bG4, 0, sizeof(bG4));
+        for (int b3 = 0; b3 < 2; ++b3)
+            for (int b3p = 0; b3p < 2; ++b3p)
+                for (int b4 = 0; b4 < 2; ++b4)
+                    for (int b4p = 0; b4p < 2; ++b4p) {
+                        bG3[b3][b3p] += conj(G4[b4][b4p]) * bPi[b3][b3p][b4][b4p];
+                        bG4[b4][b4p] += conj(G3[b3][b3p]) * bPi[b3][b3p][b4][b4p];
+                    }
+        double th3 = tanh_ft(a3, B->P->T), th4 = tanh_ft(a4, B->P->T);
+        gGR[2 * j + 0] += bG3[0][1] + conj(bG3[1][0]) + th3 * (bG3[0][0] - conj(bG3[0][0]));
+        gGR[2 * j + 1] += bG4[0][1] + conj(bG4[1][0]) + th4 * (bG4[0][0] - conj(bG4[0][0]));
+    }
+}
+
+/* Private copy of the wanted gradient arrays (zeroed); returns the buffer or NULL. */
+static cplx *grad_private(const ovtx *V, const ograd *src, ograd *dst) {
+    size_t tot = 0;
+    for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < 4; ++k)
+            if (*grad_slot((ograd *)src, c, k)) tot += cls_elems(V, k);
+    cplx *buf = calloc(tot > 0 ? tot : 1, sizeof(cplx));
+    if (!buf) return NULL;
+    size_t off = 0;
+    for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < 4; ++k) {
+            if (*grad_slot((ograd *)src, c, k)) { *grad_slot(dst, c, k) = buf + off; off += cls_elems(V, k); }
+            else *grad_slot(dst, c, k) = NULL;
+        }
+    return buf;
+}
+
+static void grad_accumulate(const ovtx *V, const ograd *priv, ograd *dst) {
+    for (int c = 0; c < 3; ++c)
+        for (int k = 0; k < 4; ++k) {
+            cplx *d = *grad_slot(dst, c, k), *p = *grad_slot((ograd *)priv, c, k);
+            if (!d || !p) continue;
+            size_t n = cls_elems(V, k);
+            for (size_t i = 0; i < n; ++i) d[i] += p[i];
+        }
+}
+
+/* Public: VJP at npts output points (w, v, vp) = freqs[3i..3i+2] with gradients
+ * gbar[16 i + c].  G1, G2 (either may be NULL) receive += the gradients with respect to
+ * the stored classes of V1 and V2; gGR (or NULL; n_gr entries) receives += the gradient
+ * with respect to G^R at the samples [iw[i]][j][side].  pi_kind must be 0 (G G) and P
+ * must have no self-energy table when gGR is given. */
+int og_bubble_vjp_points(const ovtx *V1, const ovtx *V2, const oprop *P, int pi_kind, int r, int lsel, int rsel,
+                         int Nq, int npts, const double *freqs, const cplx *gbar, const int *iw, ograd *G1,
+                         ograd *G2, cplx *gGR, int n_gr, int nthreads) {
+    if (r < 0 || r > 2 || Nq < 5 || (Nq - 1) % 4) return -1;
+    if (gGR && (pi_kind != 0 || P->n_sig > 0 || !iw)) return -3;
+    double *xq = malloc(sizeof(double) * Nq), *wq = malloc(sizeof(double) * Nq);
+    if (!xq || !wq) { free(xq); free(wq); return -2; }
+    og_gl5_rule(Nq, xq, wq);
+    int fail = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        ograd p1, p2;
+        cplx *b1 = G1 ? grad_private(V1, G1, &p1) : NULL;
+        cplx *b2 = G2 ? grad_private(V2, G2, &p2) : NULL;
+        cplx *pg = gGR ? calloc((size_t)n_gr, sizeof(cplx)) : NULL;
+        int ok = (!G1 || b1) && (!G2 || b2) && (!gGR || pg);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int i = 0; i < npts; ++i) {
+            if (!ok) continue;
+            if (gGR && ((size_t)iw[i] + 1) * Nq * 2 > (size_t)n_gr) { ok = 0; continue; }
+            bctx B = {V1, V2, P, pi_kind, r, lsel, rsel, freqs[3 * i], freqs[3 * i + 1], freqs[3 * i + 2]};
+            bubble_point_vjp(&B, Nq, xq, wq, gbar + (size_t)16 * i, G1 ? &p1 : NULL, G2 ? &p2 : NULL,
+                             gGR ? pg + (size_t)iw[i] * Nq * 2 : NULL);
+        }
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+        {
+            if (!ok) fail = 1;
+            else {
+                if (G1) grad_accumulate(V1, &p1, G1);
+                if (G2) grad_accumulate(V2, &p2, G2);
+                if (gGR) for (int i = 0; i < n_gr; ++i) gGR[i] += pg[i];
+            }
+        }
+        free(b1);
+        free(b2);
+        free(pg);
+    }
+    free(xq);
+    free(wq);
+    return fail ? -2 : 0;
 }

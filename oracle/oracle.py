@@ -178,6 +178,70 @@ def bubble_all(V1, V2, P, r, Nq, pi_kind=PI_GG, classes=("K1", "K2", "K2p", "K3"
     return {c: bubble_class(V1, V2, P, r, c, Nq, pi_kind, nthreads=nthreads) for c in classes}
 
 
+class _OGrad(C.Structure):
+    _fields_ = [("K1", C.c_void_p * 3), ("K2", C.c_void_p * 3), ("K2p", C.c_void_p * 3), ("K3", C.c_void_p * 3)]
+
+
+CLASSES = ("K1", "K2", "K2p", "K3")
+
+
+def zero_grads(grids):
+    """Gradient arrays of every class of every channel (complex128, zeros)."""
+    return {c: [np.zeros(class_shape(grids, k), dtype=np.complex128) for k in CLASSES] for c in range(3)}
+
+
+def _ograd(gr):
+    s = _OGrad()
+    for c in range(3):
+        for k, name in enumerate(CLASSES):
+            getattr(s, name)[c] = gr[c][k].ctypes.data
+    return s
+
+
+def class_omega_index(grids, cls, idx=None):
+    """Bosonic index (on the class's own w grid) of each output point of a class."""
+    shp = class_shape(grids, cls)[:-1]
+    if idx is None:
+        return np.repeat(np.arange(shp[0]), int(np.prod(shp[1:])) if len(shp) > 1 else 1).astype(np.int32)
+    return np.array([t[0] for t in idx], dtype=np.int32)
+
+
+def bubble_vjp(V1, V2, P, r, cls, Nq, gbar, pi_kind=PI_GG, want_left=True, want_right=True, want_gr=False,
+               idx=None, nthreads=0):
+    """Vector-Jacobian product of one output class of B_r (real-embedding convention:
+    bar(z) = dL/dRe z + i dL/dIm z for a real loss L).  gbar has the class's shape (or
+    (len(idx), 16)).  Returns (grad_left, grad_right, grad_GR): gradient dicts
+    channel -> [K1, K2, K2p, K3] with the vertex's shapes (None if not wanted), and the
+    gradient with respect to G^R at the samples [w index][node][side] (side 0: the
+    propagator at v''+w/2 (a, t) or w/2+v'' (p); side 1: at v''-w/2 or w/2-v'')."""
+    ls, rs = CLASS_SEL[cls]
+    f = class_freqs(V1.grids, cls, V1.A, idx)
+    gb = np.ascontiguousarray(np.asarray(gbar, dtype=np.complex128).reshape(-1, 16))
+    if len(gb) != len(f):
+        raise ValueError("gbar does not match the class's points")
+    iw = np.ascontiguousarray(class_omega_index(V1.grids, cls, idx))
+    gl = zero_grads(V1.grids) if want_left else None
+    gr = zero_grads(V2.grids) if want_right else None
+    ggr = None
+    n_gr = 0
+    if want_gr:
+        nw = class_shape(V1.grids, cls)[0]
+        ggr = np.zeros((nw, Nq, 2), dtype=np.complex128)
+        n_gr = ggr.size
+    sl = _ograd(gl) if gl is not None else None
+    sr = _ograd(gr) if gr is not None else None
+    rc = lib().og_bubble_vjp_points(V1.ptr(), V2.ptr(), P.ptr(), C.c_int(pi_kind), C.c_int(r), C.c_int(ls),
+                                    C.c_int(rs), C.c_int(Nq), C.c_int(len(f)), _dptr(f),
+                                    gb.ctypes.data_as(C.c_void_p), iw.ctypes.data_as(C.c_void_p),
+                                    C.byref(sl) if sl is not None else None,
+                                    C.byref(sr) if sr is not None else None,
+                                    ggr.ctypes.data_as(C.c_void_p) if ggr is not None else None, C.c_int(n_gr),
+                                    C.c_int(nthreads))
+    if rc != 0:
+        raise RuntimeError("og_bubble_vjp_points failed: %d" % rc)
+    return gl, gr, ggr
+
+
 def integrand(V1, V2, P, r, lsel, rsel, w, v, vp, xs, pi_kind=PI_GG):
     xs = np.ascontiguousarray(xs, dtype=np.float64)
     out = np.zeros((len(xs), 16), dtype=np.complex128)

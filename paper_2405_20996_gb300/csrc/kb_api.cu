@@ -266,6 +266,63 @@ kb_status kb_bubble(kb_ctx* ctx, int channel, int sl, int sr, int so, int pi_kin
     return KB_ERR_ARG;
 }
 
+kb_status kb_bubble_vjp(kb_ctx* ctx, int channel, int sl, int sr, int sgo, int pi_kind, unsigned mask, double alpha,
+                        int sgl, int sgr, void* grad_GR_K1, void* grad_GR_K2, void* grad_GR_K3, int precision,
+                        void* stream) {
+    if (!ctx) return KB_ERR_ARG;
+    if (!ctx->grids_set || !ctx->model_set) { ctx->err = "kb_bubble_vjp: set grids and model first"; return KB_ERR_STATE; }
+    auto slot_ok = [](int s) { return s >= 0 && s < KB_MAX_SLOTS; };
+    if (channel < 0 || channel > 2 || !slot_ok(sl) || !slot_ok(sr) || !slot_ok(sgo) || (sgl != -1 && !slot_ok(sgl)) ||
+        (sgr != -1 && !slot_ok(sgr)) || (pi_kind != KB_PI_GG && pi_kind != KB_PI_GS_SG) || (mask & ~KB_MASK_ALL) ||
+        !std::isfinite(alpha)) {
+        ctx->err = "kb_bubble_vjp: argument out of range";
+        return KB_ERR_ARG;
+    }
+    if (!ctx->slot_set[sl] || !ctx->slot_set[sr] || !ctx->slot_set[sgo] || (sgl >= 0 && !ctx->slot_set[sgl]) ||
+        (sgr >= 0 && !ctx->slot_set[sgr])) {
+        ctx->err = "kb_bubble_vjp: slot not set";
+        return KB_ERR_STATE;
+    }
+    for (int k = 0; k < 4; ++k)
+        if (((mask >> k) & 1) && !ctx->slots[sgo].cls[channel][k]) {
+            ctx->err = "kb_bubble_vjp: output-gradient class not attached";
+            return KB_ERR_STATE;
+        }
+    for (int gs : {sgl, sgr}) {
+        if (gs < 0) continue;
+        for (int c = 0; c < 3; ++c)
+            for (int k = 0; k < 4; ++k) {
+                const void* p = ctx->slots[gs].cls[c][k];
+                if (!p) continue;
+                if (ctx->slots[gs].dt[c][k] != KB_DT_C128) {
+                    ctx->err = "kb_bubble_vjp: gradient classes must be complex128";
+                    return KB_ERR_ARG;
+                }
+                for (int q = 0; q < 4; ++q)
+                    for (int cc = 0; cc < 3; ++cc)
+                        if (p == ctx->slots[sl].cls[cc][q] || p == ctx->slots[sr].cls[cc][q] ||
+                            p == ctx->slots[sgo].cls[cc][q]) {
+                            ctx->err = "kb_bubble_vjp: a gradient class aliases an input";
+                            return KB_ERR_ARG;
+                        }
+            }
+    }
+    void* tabs[3] = {grad_GR_K1, grad_GR_K2, grad_GR_K3};
+    bool any_gr = grad_GR_K1 || grad_GR_K2 || grad_GR_K3;
+    if (any_gr && (pi_kind != KB_PI_GG || ctx->m.n_sig > 0)) {
+        ctx->err = "kb_bubble_vjp: the G^R gradient needs pi_kind GG and no self-energy table (FDR form of G^K)";
+        return KB_ERR_UNSUPPORTED;
+    }
+    if (precision != KB_PREC_FP64) {
+        ctx->err = "kb_bubble_vjp: only KB_PREC_FP64 is built";
+        return KB_ERR_UNSUPPORTED;
+    }
+    if (mask == 0 || (sgl < 0 && sgr < 0 && !any_gr)) return KB_OK;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) { ctx->err = "cudaSetDevice failed"; return KB_ERR_CUDA; }
+    return kb_bubble_vjp_fp64(ctx, channel, sl, sr, sgo, pi_kind, mask, alpha, sgl, sgr, any_gr ? tabs : nullptr,
+                              reinterpret_cast<cudaStream_t>(stream));
+}
+
 kb_status kb_check_device(kb_ctx* ctx) {
     if (!ctx) return KB_ERR_ARG;
     cudaSetDevice(ctx->device);

@@ -113,4 +113,6 @@ kb_status kb_bubble_fp64(kb_ctx* ctx, int r, int sl, int sr, int so, int pi_kind
                          double beta, cudaStream_t st);
 kb_status kb_bubble_mixed(kb_ctx* ctx, int r, int sl, int sr, int so, int pi_kind, unsigned mask, double alpha,
                           double beta, cudaStream_t st);
+kb_status kb_bubble_vjp_fp64(kb_ctx* ctx, int r, int sl, int sr, int sgo, int pi_kind, unsigned mask, double alpha,
+                             int sgl, int sgr, void* const gGR[3], cudaStream_t st);
 kb_status kb_ensure_workspace(kb_ctx* ctx, size_t bytes);

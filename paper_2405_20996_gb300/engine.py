@@ -79,5 +79,26 @@ class Engine:
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
         kb.kb_bubble(self.ctx, channel, left, right, out, pi_kind, class_mask, alpha, beta, PREC[precision], st)
 
+    def bubble_vjp(self, channel, left, right, gout, pi_kind=kb.KB_PI_GG, class_mask=kb.KB_MASK_ALL, alpha=1.0,
+                   grad_left=-1, grad_right=-1, grad_gr=None, precision="fp64", stream=None):
+        """Accumulate the vector-jacobian product of bubble(...) into the gradient slots
+        grad_left / grad_right (-1 = not wanted) and, if grad_gr is a dict
+        {"K1", "K2", "K3"} -> complex128 device tensors [nw][nq][2], the G^R gradient."""
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        tabs = [None, None, None]
+        for i, name in enumerate(("K1", "K2", "K3")):
+            t = (grad_gr or {}).get(name)
+            if t is not None:
+                assert t.is_cuda and t.is_contiguous() and t.dtype == torch.complex128
+                tabs[i] = t.data_ptr()
+        kb.kb_bubble_vjp(self.ctx, channel, left, right, gout, pi_kind, class_mask, alpha, grad_left, grad_right,
+                         *tabs, PREC[precision], st)
+
+    def gr_tables(self):
+        """Zeroed G^R gradient tables [nw][nq][2] for the K1, K2 and K3 bosonic grids."""
+        g = self.grids
+        return {name: torch.zeros((nw, self.nq, 2), dtype=torch.complex128, device=self.device)
+                for name, nw in (("K1", g["n1"]), ("K2", g["n2w"]), ("K3", g["n3w"]))}
+
     def launches(self):
         return kb.kb_launch_count(self.ctx)

@@ -53,6 +53,8 @@ _SIGS = {
     "kb_set_vertex_class": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int],
     "kb_bubble": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_double, C.c_double,
                   C.c_int, C.c_void_p],
+    "kb_bubble_vjp": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_double, C.c_int,
+                      C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
     "kb_workspace_bytes": [C.c_void_p, C.POINTER(C.c_ulonglong)],
     "kb_check_device": [C.c_void_p],
     "kb_launch_count": [C.c_void_p, C.POINTER(C.c_ulonglong)],
@@ -145,6 +147,14 @@ def kb_bubble(ctx, channel, slot_left, slot_right, out_slot, pi_kind=KB_PI_GG, c
               alpha=1.0, beta=0.0, precision=KB_PREC_FP64, stream=0):
     _check(ctx, lib().kb_bubble(ctx, channel, slot_left, slot_right, out_slot, pi_kind, class_mask, alpha, beta,
                                 precision, stream))
+
+
+def kb_bubble_vjp(ctx, channel, slot_left, slot_right, gout_slot, pi_kind=KB_PI_GG, class_mask=KB_MASK_ALL,
+                  alpha=1.0, grad_left_slot=-1, grad_right_slot=-1, grad_GR_K1=None, grad_GR_K2=None,
+                  grad_GR_K3=None, precision=KB_PREC_FP64, stream=0):
+    _check(ctx, lib().kb_bubble_vjp(ctx, channel, slot_left, slot_right, gout_slot, pi_kind, class_mask, alpha,
+                                    grad_left_slot, grad_right_slot, grad_GR_K1, grad_GR_K2, grad_GR_K3,
+                                    precision, stream))
 
 
 def kb_check_device(ctx):
