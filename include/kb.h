@@ -159,6 +159,46 @@ kb_status kb_bubble_vjp(kb_ctx *ctx, int channel, int slot_left, int slot_right,
                         unsigned class_mask, double alpha, int grad_left_slot, int grad_right_slot,
                         void *grad_GR_K1, void *grad_GR_K2, void *grad_GR_K3, int precision, void *stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Step graphs (batching): a list of bubbles of one or several contexts — several
+ * parameter points, each with its own grids, model and vertices, the loop parts of a
+ * multiloop step (Sec. III.C: one-loop, left, right and central parts are bubbles with
+ * different slots and propagator pairs) and the three channels — captured once into a
+ * CUDA graph and replayed with one launch per step.
+ *
+ * kb_graph_create sizes every context's workspace for its bubbles, does the one-time
+ * device setup, and captures the bubbles (each as kb_bubble would run it) without running
+ * them.  Bubbles of the same context run in list order; bubbles of different contexts
+ * are independent branches of the graph and may overlap on the GPU, so they must not
+ * write an array another branch reads or writes.  The graph holds the device pointers
+ * and parameters in force at creation: later kb_set_* calls do not change it; the caller
+ * keeps the contexts and every attached array alive until kb_graph_destroy.  All contexts
+ * must be on one device.  On failure nothing is kept and the message is in
+ * kb_last_error of the context of the failing (or the first) descriptor.
+ * kb_graph_launch enqueues one replay on `stream` (asynchronous, like kb_bubble);
+ * kb_graph_kernel_count gives the kernels one replay runs.
+ * --------------------------------------------------------------------------------------- */
+typedef struct kb_graph kb_graph;
+
+typedef struct {
+    kb_ctx *ctx;
+    int channel, slot_left, slot_right, out_slot, pi_kind;
+    unsigned class_mask;
+    double alpha, beta;
+    int precision;
+} kb_bubble_desc;
+
+kb_status kb_graph_create(kb_graph **graph, const kb_bubble_desc *bubbles, int n);
+kb_status kb_graph_launch(kb_graph *graph, void *stream);
+kb_status kb_graph_kernel_count(kb_graph *graph, unsigned long long *count);
+kb_status kb_graph_destroy(kb_graph *graph);
+
+/* Device workspace limit of a context in bytes (default 4 GiB, or the KB_WORKSPACE_MB
+ * environment variable at kb_create).  Larger limits let the K3 contraction batch more
+ * bosonic frequencies per launch; smaller ones bound memory when many contexts coexist.
+ * Takes effect at the next call that sizes the workspace. */
+kb_status kb_set_workspace_limit(kb_ctx *ctx, unsigned long long bytes);
+
 /* Synchronise the context's device and report device-side failures since the last check:
  * KB_ERR_TIMEOUT if a bounded wait inside a tensor-core kernel gave up (that kernel's output
  * is then incomplete), KB_ERR_CUDA for a CUDA error.  Clears the timeout flag. */

@@ -131,6 +131,32 @@ void class_shape(const Grids& g, int cls, int& nw, int& nL, int& nR, int& nvg) {
     else { nw = g.n3w; nL = g.n3v; nR = g.n3v; nvg = g.n3v; }
 }
 
+// Bytes per bosonic frequency of the FP64 class pipeline (Pi table, both tiles, product)
+// and the frequencies processed per chunk within the context's workspace limit.
+static void fp64_chunking(const kb_ctx* ctx, int r, int cls, size_t& per_w, int& chunk) {
+    const Grids& g = ctx->g;
+    size_t K = (size_t)4 * ((r == KB_CH_T) ? 2 : 1) * g.nq;
+    int nw, nL, nR, nvg;
+    class_shape(g, cls, nw, nL, nR, nvg);
+    per_w = (size_t)g.nq * 16 * sizeof(double2) + (size_t)4 * nL * K * sizeof(double2) +
+            (size_t)4 * nR * K * sizeof(double2) + (size_t)16 * nL * nR * sizeof(double2);
+    chunk = (int)std::max<size_t>(1, std::min<size_t>(nw, ctx->ws_limit / per_w));
+}
+
+size_t kb_fp64_workspace_need(const kb_ctx* ctx, int r, unsigned mask) {
+    size_t need = 0;
+    for (int cls = 0; cls < 4; ++cls)
+        if ((mask >> cls) & 1) {
+            size_t per_w;
+            int chunk;
+            fp64_chunking(ctx, r, cls, per_w, chunk);
+            need = std::max(need, per_w * chunk);
+        }
+    return need;
+}
+
+kb_status kb_fp64_prepare(kb_ctx* ctx) { return upload_maps(ctx); }
+
 kb_status kb_bubble_fp64(kb_ctx* ctx, int r, int sl, int sr, int so, int pi_kind, unsigned mask, double alpha,
                          double beta, cudaStream_t st) {
     kb_status s = upload_maps(ctx);
@@ -142,9 +168,9 @@ kb_status kb_bubble_fp64(kb_ctx* ctx, int r, int sl, int sr, int so, int pi_kind
         if (!((mask >> cls) & 1)) continue;
         int nw, nL, nR, nvg;
         class_shape(g, cls, nw, nL, nR, nvg);
-        size_t per_w = (size_t)g.nq * 16 * sizeof(double2) + (size_t)4 * nL * K * sizeof(double2) +
-                       (size_t)4 * nR * K * sizeof(double2) + (size_t)16 * nL * nR * sizeof(double2);
-        int chunk = (int)std::max<size_t>(1, std::min<size_t>(nw, ctx->ws_limit / per_w));
+        size_t per_w;
+        int chunk;
+        fp64_chunking(ctx, r, cls, per_w, chunk);
         s = kb_ensure_workspace(ctx, per_w * chunk);
         if (s != KB_OK) return s;
         char* base = static_cast<char*>(ctx->ws.ptr);

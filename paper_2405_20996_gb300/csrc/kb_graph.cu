@@ -1,0 +1,176 @@
+// Step graphs: a list of bubbles — of one or several contexts (parameter points with their
+// own grids and models), loop parts and channels — captured once into a CUDA graph and
+// replayed as one launch per step.  Bubbles of one context run in list order (they share
+// its workspace); the bubbles of different contexts run on separate branches of the graph
+// and may overlap on the GPU.
+#include <algorithm>
+#include <cstdio>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "kb_internal.h"
+
+struct kb_graph {
+    int device = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<std::pair<kb_ctx*, unsigned long long>> launches;   // kernels per replay, per context
+    unsigned long long kernels = 0;
+};
+
+namespace {
+
+struct Branch {
+    kb_ctx* ctx;
+    cudaStream_t st = nullptr;
+    cudaEvent_t done = nullptr;
+    size_t need = 0;
+    unsigned long long launches0 = 0;
+};
+
+kb_status fail(kb_ctx* ctx, const std::string& msg, kb_status s) {
+    if (ctx) ctx->err = msg;
+    return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
+    if (!out) return KB_ERR_ARG;
+    *out = nullptr;
+    if (!d || n < 1) return KB_ERR_ARG;
+    kb_ctx* c0 = d[0].ctx;
+    if (!c0) return KB_ERR_ARG;
+    std::vector<Branch> br;
+    std::map<kb_ctx*, size_t> index;
+    for (int i = 0; i < n; ++i) {
+        kb_ctx* c = d[i].ctx;
+        if (!c) return fail(c0, "kb_graph_create: null context in descriptor", KB_ERR_ARG);
+        if (c->device != c0->device) return fail(c0, "kb_graph_create: contexts on different devices", KB_ERR_ARG);
+        if (!c->grids_set || !c->model_set) return fail(c, "kb_graph_create: set grids and model first", KB_ERR_STATE);
+        if (d[i].channel < 0 || d[i].channel > 2 || (d[i].class_mask & ~KB_MASK_ALL) ||
+            (d[i].precision != KB_PREC_FP64 && d[i].precision != KB_PREC_MIXED))
+            return fail(c, "kb_graph_create: descriptor out of range", KB_ERR_ARG);
+        if (!index.count(c)) { index[c] = br.size(); br.push_back(Branch{c}); }
+        Branch& b = br[index[c]];
+        size_t need = d[i].precision == KB_PREC_FP64 ? kb_fp64_workspace_need(c, d[i].channel, d[i].class_mask)
+                                                     : kb_mixed_workspace_need(c, d[i].channel, d[i].class_mask);
+        b.need = std::max(b.need, need);
+    }
+    if (cudaSetDevice(c0->device) != cudaSuccess) return fail(c0, "cudaSetDevice failed", KB_ERR_CUDA);
+    // everything that allocates, synchronises or copies happens before the capture
+    for (auto& b : br) {
+        kb_status s = kb_ensure_workspace(b.ctx, b.need);
+        if (s != KB_OK) return s;
+        s = kb_fp64_prepare(b.ctx);
+        if (s != KB_OK) return s;
+    }
+    bool any_mixed = false;
+    for (int i = 0; i < n; ++i) any_mixed |= d[i].precision == KB_PREC_MIXED;
+    if (any_mixed && !kb_tc_prepare(c0->device))
+        return fail(c0, "kb_graph_create: tensor-core kernel setup failed", KB_ERR_CUDA);
+
+    cudaStream_t s0 = nullptr;
+    cudaEvent_t fork = nullptr;
+    kb_status st = KB_OK;
+    auto cleanup = [&]() {
+        for (auto& b : br) {
+            if (b.st) cudaStreamDestroy(b.st);
+            if (b.done) cudaEventDestroy(b.done);
+        }
+        if (fork) cudaEventDestroy(fork);
+        if (s0) cudaStreamDestroy(s0);
+    };
+    if (cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) {
+        cleanup();
+        return fail(c0, "kb_graph_create: stream/event creation failed", KB_ERR_CUDA);
+    }
+    for (auto& b : br)
+        if (cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess) {
+            cleanup();
+            return fail(c0, "kb_graph_create: stream/event creation failed", KB_ERR_CUDA);
+        }
+    std::vector<bool> prof(br.size());
+    for (size_t i = 0; i < br.size(); ++i) {
+        prof[i] = br[i].ctx->prof_on;
+        br[i].ctx->prof_on = false;   // no timing events inside a graph
+        br[i].launches0 = br[i].ctx->launches;
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        st = fail(c0, "kb_graph_create: cudaStreamBeginCapture failed", KB_ERR_CUDA);
+    } else {
+        cudaEventRecord(fork, s0);
+        for (auto& b : br) cudaStreamWaitEvent(b.st, fork, 0);
+        for (int i = 0; i < n && st == KB_OK; ++i) {
+            const kb_bubble_desc& x = d[i];
+            st = kb_bubble(x.ctx, x.channel, x.slot_left, x.slot_right, x.out_slot, x.pi_kind, x.class_mask, x.alpha,
+                           x.beta, x.precision, br[index[x.ctx]].st);
+        }
+        for (auto& b : br) {
+            cudaEventRecord(b.done, b.st);
+            cudaStreamWaitEvent(s0, b.done, 0);
+        }
+        cudaError_t e = cudaStreamEndCapture(s0, &graph);
+        if (st == KB_OK && e != cudaSuccess)
+            st = fail(c0, std::string("kb_graph_create: capture failed: ") + cudaGetErrorString(e), KB_ERR_CUDA);
+    }
+    kb_graph* g = nullptr;
+    if (st == KB_OK) {
+        g = new (std::nothrow) kb_graph();
+        if (!g) st = KB_ERR_OOM;
+    }
+    for (size_t i = 0; i < br.size(); ++i) {
+        unsigned long long k = br[i].ctx->launches - br[i].launches0;
+        br[i].ctx->launches = br[i].launches0;   // captured, not run
+        br[i].ctx->prof_on = prof[i];
+        if (g) { g->launches.push_back({br[i].ctx, k}); g->kernels += k; }
+    }
+    if (st == KB_OK) {
+        cudaError_t e = cudaGraphInstantiate(&g->exec, graph, 0);
+        if (e != cudaSuccess) {
+            st = fail(c0, std::string("kb_graph_create: instantiate failed: ") + cudaGetErrorString(e), KB_ERR_CUDA);
+        }
+    }
+    cudaGetLastError();
+    cleanup();
+    if (st != KB_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        delete g;
+        return st;
+    }
+    g->graph = graph;
+    g->device = c0->device;
+    *out = g;
+    return KB_OK;
+}
+
+kb_status kb_graph_launch(kb_graph* g, void* stream) {
+    if (!g || !g->exec) return KB_ERR_ARG;
+    if (cudaSetDevice(g->device) != cudaSuccess) return KB_ERR_CUDA;
+    if (cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return KB_ERR_CUDA;
+    for (auto& p : g->launches) p.first->launches += p.second;
+    return KB_OK;
+}
+
+kb_status kb_graph_kernel_count(kb_graph* g, unsigned long long* count) {
+    if (!g || !count) return KB_ERR_ARG;
+    *count = g->kernels;
+    return KB_OK;
+}
+
+kb_status kb_graph_destroy(kb_graph* g) {
+    if (!g) return KB_ERR_ARG;
+    cudaSetDevice(g->device);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return KB_OK;
+}
+
+}  // extern "C"

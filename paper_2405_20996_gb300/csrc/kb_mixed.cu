@@ -550,6 +550,39 @@ static VertexF to_vf(const VertexDev& V, kb_ctx* ctx, bool& ok) {
     return F;
 }
 
+// Workspace layout of one mixed-precision bubble of channel r (byte offsets into the
+// context's workspace) and the bytes it needs.
+struct MixedLayout {
+    size_t off_tab, off_N, off_M, off_S, off_P3, off_T, rows, K, per_w, tc_scratch, need;
+    int chunk;
+};
+
+static MixedLayout mixed_layout(const kb_ctx* ctx, int r, unsigned mask) {
+    const Grids& g = ctx->g;
+    int ns = (r == KB_CH_T) ? 2 : 1;
+    MixedLayout L;
+    size_t ntab = (size_t)g.n1 + g.n2w + g.n2v + g.n3w + g.n3v + g.nq;
+    L.off_tab = 0;
+    L.off_N = (ntab * sizeof(df) + 255) / 256 * 256;
+    size_t szNM = (size_t)g.n2w * ns * g.nq * 16 * sizeof(float2);
+    L.off_M = L.off_N + szNM;
+    L.off_S = L.off_M + szNM;
+    size_t szS = (size_t)2 * g.n2w * ns * 16 * sizeof(double2);
+    L.off_P3 = (L.off_S + szS + 255) / 256 * 256;
+    size_t szP3 = (size_t)g.n3w * g.nq * 16 * sizeof(float2);
+    L.off_T = (L.off_P3 + szP3 + 1023) / 1024 * 1024;
+    L.rows = (size_t)4 * g.n3v;
+    L.K = (size_t)4 * ns * g.nq;
+    L.per_w = 2 * 4 * L.rows * L.K * sizeof(float) + L.rows * L.rows * sizeof(double2) + 1024;
+    size_t budget = ctx->ws_limit > L.off_T ? ctx->ws_limit - L.off_T : 0;
+    L.chunk = (int)std::max<size_t>(1, std::min<size_t>(g.n3w, budget / L.per_w));
+    L.tc_scratch = std::min<size_t>(2ull << 30, std::max<size_t>(64ull << 20, (size_t)24 * L.chunk * L.rows * L.rows * 16));
+    L.need = ((mask >> KB_K3) & 1) ? L.off_T + L.per_w * L.chunk + L.tc_scratch : L.off_T;
+    return L;
+}
+
+size_t kb_mixed_workspace_need(const kb_ctx* ctx, int r, unsigned mask) { return mixed_layout(ctx, r, mask).need; }
+
 template <int r>
 static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, unsigned mask, double alpha, double beta,
                             cudaStream_t st) {
@@ -565,24 +598,12 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
     J.r = r; J.pi_kind = pi_kind; J.ns = (r == KB_CH_T) ? 2 : 1; J.nq = g.nq;
     J.M = channel_maps(r); J.alpha = alpha; J.beta = beta;
     int ns = J.ns;
-    // workspace layout
-    size_t ntab = (size_t)g.n1 + g.n2w + g.n2v + g.n3w + g.n3v + g.nq;
-    size_t off_tab = 0;
-    size_t off_N = (ntab * sizeof(df) + 255) / 256 * 256;
-    size_t szNM = (size_t)g.n2w * ns * g.nq * 16 * sizeof(float2);
-    size_t off_M = off_N + szNM;
-    size_t off_S = off_M + szNM;
-    size_t szS = (size_t)2 * g.n2w * ns * 16 * sizeof(double2);
-    size_t off_P3 = (off_S + szS + 255) / 256 * 256;
-    size_t szP3 = (size_t)g.n3w * g.nq * 16 * sizeof(float2);
-    size_t off_T = (off_P3 + szP3 + 1023) / 1024 * 1024;
-    size_t rows = (size_t)4 * g.n3v, K = (size_t)4 * ns * g.nq;
-    size_t per_w = 2 * 4 * rows * K * sizeof(float) + rows * rows * sizeof(double2) + 1024;
-    size_t budget = ctx->ws_limit > off_T ? ctx->ws_limit - off_T : 0;
-    int chunk = (int)std::max<size_t>(1, std::min<size_t>(g.n3w, budget / per_w));
-    size_t tc_scratch = std::min<size_t>(2ull << 30, std::max<size_t>(64ull << 20, (size_t)24 * chunk * rows * rows * 16));
-    size_t need = ((mask >> KB_K3) & 1) ? off_T + per_w * chunk + tc_scratch : off_T;
-    kb_status s = kb_ensure_workspace(ctx, need);
+    const MixedLayout Lo = mixed_layout(ctx, r, mask);
+    const size_t off_tab = Lo.off_tab, off_N = Lo.off_N, off_M = Lo.off_M, off_S = Lo.off_S, off_P3 = Lo.off_P3,
+                 off_T = Lo.off_T, rows = Lo.rows, K = Lo.K, tc_scratch = Lo.tc_scratch;
+    const int chunk = Lo.chunk;
+    const size_t ntab = (size_t)g.n1 + g.n2w + g.n2v + g.n3w + g.n3v + g.nq;
+    kb_status s = kb_ensure_workspace(ctx, Lo.need);
     if (s != KB_OK) return s;
     char* ws = static_cast<char*>(ctx->ws.ptr);
     df* tab = reinterpret_cast<df*>(ws + off_tab);

@@ -348,6 +348,25 @@ static bool make_map(CUtensorMap* m, const float* base, int K, int rows, int pla
     return r == CUDA_SUCCESS;
 }
 
+static size_t tc_smem_bytes() {
+    constexpr size_t STAGE = 4 * MT * KC * 4 + 4 * NTT * KC * 4;
+    return STAGES_S * STAGE + 128 + 1024;
+}
+
+// One-time per device: opt the kernel in to its dynamic shared memory (not a stream
+// operation, so it is done before any capture) and resolve the tensor-map encoder.
+static bool tc_prepare(int device) {
+    static bool attr_set[64] = {};
+    if (device < 0 || device >= 64) return false;
+    if (!attr_set[device]) {
+        if (cudaFuncSetAttribute(k_tc_k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes()) !=
+            cudaSuccess)
+            return false;
+        attr_set[device] = true;
+    }
+    return encoder() != nullptr;
+}
+
 static bool launch(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
                    void* scratch, size_t scratch_bytes, cudaStream_t st) {
     TcJob J;
@@ -382,14 +401,8 @@ static bool launch(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, i
                      J.mtiles, J.ntiles, J.ksplit, J.chunks_per_split);
     CUtensorMap ma, mb;
     if (!make_map(&ma, At, K, M, 4 * batch, MT) || !make_map(&mb, Bt, K, N, 4 * batch, NTT)) return false;
-    constexpr size_t STAGE = 4 * MT * KC * 4 + 4 * NTT * KC * 4;
-    size_t smem = STAGES_S * STAGE + 128 + 1024;
-    static bool attr_set[64] = {};
-    if (!attr_set[ctx->device]) {
-        if (cudaFuncSetAttribute(k_tc_k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return false;
-        attr_set[ctx->device] = true;
-    }
+    size_t smem = tc_smem_bytes();
+    if (!tc_prepare(ctx->device)) return false;
     double2* P = reinterpret_cast<double2*>(scratch);
     {
         KB_LAUNCH(ctx, st, "k_tc_k3");
@@ -419,6 +432,8 @@ bool kb_tc_k3(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M,
         return false;
     return launch(ctx, At, Bt, Cm, M, N, K, batch, scratch, scratch_bytes, st);
 }
+
+bool kb_tc_prepare(int device) { return kb::tc::tc_prepare(device); }
 
 int kb_tc_take_status() {
     int v = 0, z = 0;

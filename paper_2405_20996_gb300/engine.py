@@ -100,5 +100,52 @@ class Engine:
         return {name: torch.zeros((nw, self.nq, 2), dtype=torch.complex128, device=self.device)
                 for name, nw in (("K1", g["n1"]), ("K2", g["n2w"]), ("K3", g["n3w"]))}
 
+    def desc(self, channel, left, right, out, pi_kind=kb.KB_PI_GG, class_mask=kb.KB_MASK_ALL, alpha=1.0, beta=0.0,
+             precision="fp64"):
+        """Descriptor of one bubble of this engine for a StepGraph."""
+        return kb.kb_bubble_desc(self.ctx, channel, left, right, out, pi_kind, class_mask, alpha, beta,
+                                 PREC[precision])
+
+    def share_slot(self, slot, other, other_slot, U=0.0, has_R=False, include=(0, 1, 2), symmetric=False):
+        """Attach the device tensors of another engine's slot to a slot of this engine
+        (no copy), e.g. one vertex read by several contexts."""
+        kb.kb_set_vertex(self.ctx, slot, has_R, U)
+        kb.kb_set_vertex_channels(self.ctx, slot, sum(1 << c for c in include))
+        kb.kb_set_vertex_symmetric(self.ctx, slot, symmetric)
+        self.tensors[slot] = {}
+        for (ch, k), t in other.tensors[other_slot].items():
+            self.attach(slot, ch, k, t)
+
+    def set_workspace_limit(self, nbytes):
+        kb.kb_set_workspace_limit(self.ctx, nbytes)
+
     def launches(self):
         return kb.kb_launch_count(self.ctx)
+
+
+class StepGraph:
+    """Bubbles of one or several engines captured into one CUDA graph (kb_graph_create);
+    launch() replays them as one step.  Bubbles of different engines may overlap."""
+
+    def __init__(self, descs, device=None):
+        self.descs = list(descs)
+        self.device = device
+        self.g = kb.kb_graph_create(self.descs)
+
+    def launch(self, stream=None):
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        kb.kb_graph_launch(self.g, st)
+
+    def kernels(self):
+        return kb.kb_graph_kernel_count(self.g)
+
+    def close(self):
+        if self.g is not None:
+            kb.kb_graph_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

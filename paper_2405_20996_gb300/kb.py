@@ -37,6 +37,12 @@ class kb_vertex_desc(C.Structure):
                 ("cls", (C.c_void_p * 4) * 3), ("dtype", (C.c_int * 4) * 3)]
 
 
+class kb_bubble_desc(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("channel", C.c_int), ("slot_left", C.c_int), ("slot_right", C.c_int),
+                ("out_slot", C.c_int), ("pi_kind", C.c_int), ("class_mask", C.c_uint), ("alpha", C.c_double),
+                ("beta", C.c_double), ("precision", C.c_int)]
+
+
 KB_ERR_TOO_LARGE = 7
 KB_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -55,6 +61,11 @@ _SIGS = {
                   C.c_int, C.c_void_p],
     "kb_bubble_vjp": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_double, C.c_int,
                       C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
+    "kb_graph_create": [C.POINTER(C.c_void_p), C.POINTER(kb_bubble_desc), C.c_int],
+    "kb_graph_launch": [C.c_void_p, C.c_void_p],
+    "kb_graph_kernel_count": [C.c_void_p, C.POINTER(C.c_ulonglong)],
+    "kb_graph_destroy": [C.c_void_p],
+    "kb_set_workspace_limit": [C.c_void_p, C.c_ulonglong],
     "kb_workspace_bytes": [C.c_void_p, C.POINTER(C.c_ulonglong)],
     "kb_check_device": [C.c_void_p],
     "kb_launch_count": [C.c_void_p, C.POINTER(C.c_ulonglong)],
@@ -155,6 +166,34 @@ def kb_bubble_vjp(ctx, channel, slot_left, slot_right, gout_slot, pi_kind=KB_PI_
     _check(ctx, lib().kb_bubble_vjp(ctx, channel, slot_left, slot_right, gout_slot, pi_kind, class_mask, alpha,
                                     grad_left_slot, grad_right_slot, grad_GR_K1, grad_GR_K2, grad_GR_K3,
                                     precision, stream))
+
+
+def kb_graph_create(descs):
+    """descs: sequence of kb_bubble_desc; returns the graph handle."""
+    arr = (kb_bubble_desc * len(descs))(*descs)
+    g = C.c_void_p()
+    st = lib().kb_graph_create(C.byref(g), arr, len(descs))
+    if st != KB_OK:
+        raise KBError(st, lib().kb_last_error(descs[0].ctx).decode() if len(descs) else "")
+    return g
+
+
+def kb_graph_launch(graph, stream=0):
+    _check(None, lib().kb_graph_launch(graph, stream))
+
+
+def kb_graph_kernel_count(graph):
+    v = C.c_ulonglong()
+    _check(None, lib().kb_graph_kernel_count(graph, C.byref(v)))
+    return v.value
+
+
+def kb_graph_destroy(graph):
+    _check(None, lib().kb_graph_destroy(graph))
+
+
+def kb_set_workspace_limit(ctx, nbytes):
+    _check(ctx, lib().kb_set_workspace_limit(ctx, int(nbytes)))
 
 
 def kb_check_device(ctx):

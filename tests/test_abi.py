@@ -28,3 +28,15 @@ def test_null_context_arguments_rejected():
     assert L.kb_bubble(None, 0, 0, 0, 0, 0, 15, 1.0, 0.0, 0, None) == kb.KB_ERR_ARG
     assert L.kb_set_model(None, 1.0, 0.1, 0.0) == kb.KB_ERR_ARG
     assert L.kb_last_error(None) == b"null context"
+
+
+def test_null_arguments_of_vjp_and_graph_rejected():
+    L = kb.lib()
+    assert L.kb_bubble_vjp(None, 0, 0, 0, 0, 0, 15, 1.0, -1, -1, None, None, None, 0, None) == kb.KB_ERR_ARG
+    g = ctypes.c_void_p()
+    assert L.kb_graph_create(ctypes.byref(g), None, 0) == kb.KB_ERR_ARG and not g.value
+    d = (kb.kb_bubble_desc * 1)()
+    assert L.kb_graph_create(ctypes.byref(g), d, 1) == kb.KB_ERR_ARG      # null context
+    assert L.kb_graph_launch(None, None) == kb.KB_ERR_ARG
+    assert L.kb_graph_destroy(None) == kb.KB_ERR_ARG
+    assert L.kb_set_workspace_limit(None, 1 << 30) == kb.KB_ERR_ARG
