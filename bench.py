@@ -69,8 +69,9 @@ def mixed_kernel_work(channels=(0, 1, 2)):
     """Algorithmic work per step of the symmetric mixed path, by kernel (flops).
     Gather kernels: every interpolation corner adds 16 complex values times a real weight
     (64 flops); a record (one (w, v, node) of one spin term) has nominally 44 corners in
-    the up-down component (own K3 8 + two other channels x (K1 2 + K2 4 + K2' 4 + K3 8))
-    and 88 in the up-up one (each lookup also at the exchanged legs); the fused K2 kernel
+    the up-down component (own K3 8 + two other channels x (K1 2 + K2 4 + K2' 4 + K3 8));
+    the up-up one adds the exchanged term (each lookup again at the exchanged legs: 44 more),
+    so a t record, which needs both spin components, has 88; the fused K2 kernel
     adds the 4x4x4 complex contraction (512 flops), the K3 tile kernel the Pi fold of the
     right record (512 flops) and the own K2 class (4 corners).
     K3 contraction: 8 M N K useful flops per bosonic frequency (M = N = 4 n3v, K = 4 ns nq);
@@ -84,13 +85,13 @@ def mixed_kernel_work(channels=(0, 1, 2)):
     rec_p = g["n2w"] * half(g["n2v"]) * (nq - 2)
     rec_t = half(g["n2w"]) * g["n2v"] * (nq - 2)
     w["k_mx_k2"] = ((0 in channels) * rec_a + (1 in channels) * rec_p) * (44 * 64 + 512) + \
-        (2 in channels) * rec_t * ((44 + 88) * 64 + 2 * 512)
+        (2 in channels) * rec_t * ((44 + 44) * 64 + 2 * 512)
     # k_mx_tile3_both
     r3a = half(g["n3w"]) * g["n3v"] * nq
     r3p = g["n3w"] * g["n3v"] * nq
     r3t = half(g["n3w"]) * g["n3v"] * nq
     w["k_mx_tile3_both"] = ((0 in channels) * r3a + (1 in channels) * r3p) * (48 * 64 + 512) + \
-        (2 in channels) * r3t * ((48 + 96) * 64 + 2 * 512)
+        (2 in channels) * r3t * ((48 + 48) * 64 + 2 * 512)
     # k_tc_k3 (useful)
     M = 4 * g["n3v"]
     tc = 0.0

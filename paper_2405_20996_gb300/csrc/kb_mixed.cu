@@ -58,8 +58,9 @@ template <int r>
 __device__ __forceinline__ void zero_part(const VertexF& V, const DfGrids& G, bool uu, bool right, df w, df vpp,
                                           float2 out[16]) {
     df zero = {0.f, 0.f};
-    if (right) vertex_part_f32<r>(V, G, uu, true, 1 | 2 | 4, w, vpp, zero, out);
-    else vertex_part_f32<r>(V, G, uu, false, 1 | 2 | 4, w, zero, vpp, out);
+    const int parts = uu ? PARTS_UU : PARTS_UD;
+    if (right) vertex_part_f32<r>(V, G, parts, true, 1 | 2 | 4, w, vpp, zero, out);
+    else vertex_part_f32<r>(V, G, parts, false, 1 | 2 | 4, w, zero, vpp, out);
 }
 
 // Per (w in K2 grid, j): N_s = Pi R0_s, M_s = L0_s Pi;  Nt/Mt layout [w][s][j][16] float2.
@@ -73,8 +74,13 @@ __global__ void __launch_bounds__(128) k_mx_prep_k2(VertexF VL, VertexF VR, DfGr
     if (j >= J.nq) return;
     const df* qn = G.n3v + G.N3v;   // quadrature nodes follow the K3 fermionic grid in the table
     df w = wgrid[wi], vpp = qn[j];
-    double2 Pi[16];
-    pi_entry(m, J.M, J.r, J.pi_kind, G.A, (double)w.h + (double)w.l, xq[j], wq[j], Pi);
+    float2 Pf[16];
+    {
+        double2 Pi[16];
+        pi_entry(m, J.M, J.r, J.pi_kind, G.A, (double)w.h + (double)w.l, xq[j], wq[j], Pi);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) Pf[i] = make_float2((float)Pi[i].x, (float)Pi[i].y);
+    }
     constexpr int NS = (R == KB_CH_T) ? 2 : 1;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
@@ -88,14 +94,14 @@ __global__ void __launch_bounds__(128) k_mx_prep_k2(VertexF VL, VertexF VR, DfGr
         for (int X = 0; X < 4; ++X)
 #pragma unroll
             for (int Y = 0; Y < 4; ++Y) {
-                double2 an = make_double2(0, 0), am = make_double2(0, 0);
+                float2 an = make_float2(0.f, 0.f), am = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int Z = 0; Z < 4; ++Z) {
-                    cfma(an, Pi[4 * X + Z], c64to128(R0[cmap<R>(Z, Y)]));   // N[B=X][C=Y] = sum_D Pi[B][D] R0[D][C]
-                    cfma(am, c64to128(L0[cmap<R>(X, Z)]), Pi[4 * Z + Y]);   // M[A=X][D=Y] = sum_B L0[A][B] Pi[B][D]
+                    cmac2(an, Pf[4 * X + Z], R0[cmap<R>(Z, Y)]);   // N[B=X][C=Y] = sum_D Pi[B][D] R0[D][C]
+                    cmac2(am, L0[cmap<R>(X, Z)], Pf[4 * Z + Y]);   // M[A=X][D=Y] = sum_B L0[A][B] Pi[B][D]
                 }
-                n[4 * X + Y] = make_float2((float)an.x, (float)an.y);
-                mm[4 * X + Y] = make_float2((float)am.x, (float)am.y);
+                n[4 * X + Y] = an;
+                mm[4 * X + Y] = am;
             }
     }
 }
@@ -150,20 +156,31 @@ __device__ __forceinline__ void store_out(void* out, int dt, size_t e, double2 v
     }
 }
 
-// K1(w) = sum_j sum_s L0_s Pi R0_s : one CTA (128 threads) per w of the K1 grid.
+// K1(w) = sum_j sum_s L0_s Pi R0_s.  Grid (w of the K1 grid, node slice): each CTA of 128
+// threads sums its slice of the nodes and writes an FP64 partial; k_mx_k1_fin adds the
+// slices in order and stores.
+constexpr int K1_SLICES = 8;
+
 template <int R>
 __global__ void __launch_bounds__(128) k_mx_k1(VertexF VL, VertexF VR, DfGrids G, Model m, MixedJob J,
-                                               const double* __restrict__ xq, const double* __restrict__ wq, void* out,
-                                               int odt, int w_off) {
+                                               const double* __restrict__ xq, const double* __restrict__ wq,
+                                               double2* __restrict__ part, int w_off) {
     __shared__ double sh[4 * 32];
-    int wi = w_off + blockIdx.x;
+    int wi = w_off + blockIdx.x, sl = blockIdx.y;
     const df* qn = G.n3v + G.N3v;
     df w = G.n1[wi];
+    const int per = (J.nq + K1_SLICES - 1) / K1_SLICES;
+    const int jb = sl * per, je = min(J.nq, jb + per);
     float2 acc[16];
     for (int o = 0; o < 16; ++o) acc[o] = make_float2(0, 0);
-    for (int j = threadIdx.x; j < J.nq; j += blockDim.x) {
-        double2 Pi[16];
-        pi_entry(m, J.M, J.r, J.pi_kind, G.A, (double)w.h + (double)w.l, xq[j], wq[j], Pi);
+    for (int j = jb + threadIdx.x; j < je; j += blockDim.x) {
+        float2 Pf[16];
+        {
+            double2 Pi[16];
+            pi_entry(m, J.M, J.r, J.pi_kind, G.A, (double)w.h + (double)w.l, xq[j], wq[j], Pi);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) Pf[i] = make_float2((float)Pi[i].x, (float)Pi[i].y);
+        }
         constexpr int NS = (R == KB_CH_T) ? 2 : 1;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
@@ -174,25 +191,31 @@ __global__ void __launch_bounds__(128) k_mx_k1(VertexF VL, VertexF VR, DfGrids G
             for (int B = 0; B < 4; ++B)
 #pragma unroll
                 for (int C = 0; C < 4; ++C) {
-                    double2 n = make_double2(0, 0);
+                    float2 nf = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int D = 0; D < 4; ++D) cfma(n, Pi[4 * B + D], c64to128(R0[cmap<R>(D, C)]));
-                    float2 nf = make_float2((float)n.x, (float)n.y);
+                    for (int D = 0; D < 4; ++D) cmac2(nf, Pf[4 * B + D], R0[cmap<R>(D, C)]);
 #pragma unroll
-                    for (int A = 0; A < 4; ++A) {
-                        float2 l = L0[cmap<R>(A, B)];
-                        float2& a = acc[4 * A + C];
-                        a.x = fmaf(l.x, nf.x, fmaf(-l.y, nf.y, a.x));
-                        a.y = fmaf(l.x, nf.y, fmaf(l.y, nf.x, a.y));
-                    }
+                    for (int A = 0; A < 4; ++A) cmac2(acc[4 * A + C], L0[cmap<R>(A, B)], nf);
                 }
         }
     }
     double2 res[16];
     block_sum16<128>(acc, res, sh);
     if (threadIdx.x == 0)
-        for (int A = 0; A < 4; ++A)
-            for (int C = 0; C < 4; ++C) store_out(out, odt, (size_t)wi * 16 + J.M.cO[A][C], res[4 * A + C], J.alpha, J.beta);
+        for (int o = 0; o < 16; ++o) part[((size_t)blockIdx.x * K1_SLICES + sl) * 16 + o] = res[o];
+}
+
+__global__ void k_mx_k1_fin(MixedJob J, const double2* __restrict__ part, void* out, int odt, int w_off, int nw) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nw * 16) return;
+    int wl = i / 16, o = i % 16, A = o / 4, C = o % 4;
+    double x = 0, y = 0;
+    for (int sl = 0; sl < K1_SLICES; ++sl) {
+        double2 p = part[((size_t)wl * K1_SLICES + sl) * 16 + o];
+        x += p.x;
+        y += p.y;
+    }
+    store_out(out, odt, (size_t)(w_off + wl) * 16 + J.M.cO[A][C], make_double2(x, y), J.alpha, J.beta);
 }
 
 // Column sums over j of the K2-grid tables: S[t][w][s][16], t = 0 (N) or 1 (M).
@@ -226,7 +249,11 @@ template <bool RIGHT, int R>
 __global__ void __launch_bounds__(128, 4) k_mx_k2(VertexF V, DfGrids G, MixedJob J, const float2* __restrict__ Tab,
                                                const double2* __restrict__ Ssum, void* out, int odt, int w_off,
                                                int v_off) {
-    __shared__ float2 rec[128][17];
+    constexpr int NS = (R == KB_CH_T) ? 2 : 1;
+    // records of the quadrature nodes of one chunk: [0] up-down, [1] up-up (t only; the
+    // up-up record is the up-down one plus the exchanged term, so the direct lookups are
+    // done once for both spin terms)
+    __shared__ float2 rec[NS][128][17];
     __shared__ float2 red[8][16];
     int wi = w_off + blockIdx.y, vi = v_off + blockIdx.x;
     const df* qn = G.n3v + G.N3v;
@@ -234,50 +261,76 @@ __global__ void __launch_bounds__(128, 4) k_mx_k2(VertexF V, DfGrids G, MixedJob
     const int tid = threadIdx.x, o = tid & 15, q = tid >> 4;
     const int A = o >> 2, C = o & 3;
     float2 acc = make_float2(0.f, 0.f);
-    constexpr int NS = (R == KB_CH_T) ? 2 : 1;
+    // spin term s uses up-up on the left for s = 0 and on the right for s = 1 (t channel)
+    const float2* T0 = Tab + ((size_t)wi * NS) * J.nq * 16;
+    const float2* T1 = T0 + (size_t)J.nq * 16;
 #pragma unroll 1
-    for (int s = 0; s < NS; ++s) {
-        bool uu = (R == KB_CH_T) && (RIGHT ? s == 1 : s == 0);
-        const float2* T = Tab + (((size_t)wi * NS + s) * J.nq) * 16;
-#pragma unroll 1
-        for (int j0 = 1; j0 < J.nq - 1; j0 += 128) {
-            int j = j0 + tid;
-            float2 g[16];
-            if (j < J.nq - 1) {
-                if (RIGHT) vertex_part_f32<R>(V, G, uu, true, 16 | 32, w, qn[j], ve, g);
-                else vertex_part_f32<R>(V, G, uu, false, 16 | 32, w, ve, qn[j], g);
-            } else {
+    for (int j0 = 1; j0 < J.nq - 1; j0 += 128) {
+        int j = j0 + tid;
+        float2 g[16];
+        const bool valid = j < J.nq - 1;
+        if (valid) {
+            if (RIGHT) vertex_part_f32<R>(V, G, PARTS_UD, true, 16 | 32, w, qn[j], ve, g);
+            else vertex_part_f32<R>(V, G, PARTS_UD, false, 16 | 32, w, ve, qn[j], g);
+        } else {
 #pragma unroll
-                for (int c = 0; c < 16; ++c) g[c] = make_float2(0.f, 0.f);
+            for (int c = 0; c < 16; ++c) g[c] = make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) rec[0][tid][c] = g[c];
+        if (NS == 2) {
+            if (valid) {
+                if (RIGHT) vertex_part_f32<R>(V, G, PARTS_X, true, 16 | 32, w, qn[j], ve, g, true);
+                else vertex_part_f32<R>(V, G, PARTS_X, false, 16 | 32, w, ve, qn[j], g, true);
             }
 #pragma unroll
-            for (int c = 0; c < 16; ++c) rec[tid][c] = g[c];
-            __syncthreads();
-            int nrec = min(128, J.nq - 1 - j0);
+            for (int c = 0; c < 16; ++c) rec[NS - 1][tid][c] = g[c];
+        }
+        __syncthreads();
+        int nrec = min(128, J.nq - 1 - j0);
 #pragma unroll 1
-            for (int rr = q; rr < nrec; rr += 8) {
-                const float2* t = T + (size_t)(j0 + rr) * 16;
+        for (int rr = q; rr < nrec; rr += 8) {
+            const float2* t0 = T0 + (size_t)(j0 + rr) * 16;
+            if (NS == 1) {
                 if (!RIGHT) {
 #pragma unroll
-                    for (int B = 0; B < 4; ++B) cmac2(acc, rec[rr][cmap<R>(A, B)], __ldg(t + 4 * B + C));
+                    for (int B = 0; B < 4; ++B) cmac2(acc, rec[0][rr][cmap<R>(A, B)], __ldg(t0 + 4 * B + C));
                 } else {
 #pragma unroll
-                    for (int D = 0; D < 4; ++D) cmac2(acc, __ldg(t + 4 * A + D), rec[rr][cmap<R>(D, C)]);
+                    for (int D = 0; D < 4; ++D) cmac2(acc, __ldg(t0 + 4 * A + D), rec[0][rr][cmap<R>(D, C)]);
+                }
+            } else {
+                const float2* t1 = T1 + (size_t)(j0 + rr) * 16;
+                if (!RIGHT) {
+#pragma unroll
+                    for (int B = 0; B < 4; ++B) {
+                        cmac2(acc, rec[NS - 1][rr][cmap<R>(A, B)], __ldg(t0 + 4 * B + C));
+                        cmac2(acc, rec[0][rr][cmap<R>(A, B)], __ldg(t1 + 4 * B + C));
+                    }
+                } else {
+#pragma unroll
+                    for (int D = 0; D < 4; ++D) {
+                        cmac2(acc, __ldg(t0 + 4 * A + D), rec[0][rr][cmap<R>(D, C)]);
+                        cmac2(acc, __ldg(t1 + 4 * A + D), rec[NS - 1][rr][cmap<R>(D, C)]);
+                    }
                 }
             }
-            __syncthreads();
         }
+        __syncthreads();
     }
     // own ext-dependent class: own(w, v) * sum_j N(w, j) (or sum_j M(w, j) * own(w, v'))
     if (q == 0) {
         df zero = {0.f, 0.f};
+        float2 g[16];
 #pragma unroll 1
         for (int s = 0; s < NS; ++s) {
-            bool uu = (R == KB_CH_T) && (RIGHT ? s == 1 : s == 0);
-            float2 g[16];
-            if (RIGHT) vertex_part_f32<R>(V, G, uu, true, 8, w, zero, ve, g);
-            else vertex_part_f32<R>(V, G, uu, false, 8, w, ve, zero, g);
-            const double2* S = Ssum + (((size_t)(RIGHT ? 1 : 0) * G.N2w + wi) * NS + s) * 16;
+            // s = 0: up-down on both sides for a, p; for t the up-down record (left s = 1,
+            // right s = 0) comes first, then the exchanged term turns it into up-up
+            const int parts = (s == 0) ? PARTS_UD : PARTS_X;
+            if (RIGHT) vertex_part_f32<R>(V, G, parts, true, 8, w, zero, ve, g, s > 0);
+            else vertex_part_f32<R>(V, G, parts, false, 8, w, ve, zero, g, s > 0);
+            const int st = (NS == 1) ? 0 : (RIGHT ? s : 1 - s);
+            const double2* S = Ssum + (((size_t)(RIGHT ? 1 : 0) * G.N2w + wi) * NS + st) * 16;
 #pragma unroll
             for (int B = 0; B < 4; ++B) {
                 if (!RIGHT) {
@@ -350,64 +403,71 @@ __global__ void __launch_bounds__(128, 4) k_mx_tile3(VertexF V, DfGrids G, Mixed
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     constexpr int NS = (R == KB_CH_T) ? 2 : 1;
     constexpr bool RIGHT = (MODE == 1);
-    int s = blockIdx.y % NS, vi = blockIdx.y / NS, wl = blockIdx.z;
+    int vi = blockIdx.y, wl = blockIdx.z;
     if (j >= J.nq) return;
     const df* qn = G.n3v + G.N3v;
     df w = G.n3w[w0 + wl], ve = G.n3v[vi];
-    bool uu = (R == KB_CH_T) && (RIGHT ? s == 1 : s == 0);
-    float2 g[16];
-    if (RIGHT) vertex_part_f32<R>(V, G, uu, true, 8 | 16 | 32, w, qn[j], ve, g);
-    else vertex_part_f32<R>(V, G, uu, false, 8 | 16 | 32, w, ve, qn[j], g);
     size_t rows = (size_t)4 * G.N3v, K = (size_t)4 * NS * J.nq;
     size_t plane = rows * K;
     const float2* P = Pt + ((size_t)(w0 + wl) * J.nq + j) * 16;
-    if (MODE != 1) {
-        float* base = tile + (size_t)(wt0 + wl) * 4 * plane;
-        size_t col = ((size_t)s * J.nq + j) * 4;
+    float2 g[16];
+    // t channel: the up-down record first, then the exchanged term turns it into the
+    // up-up record (one set of direct lookups for both spin terms).  Spin index s of the
+    // tile columns: left s = 0 up-up, s = 1 up-down; right s = 0 up-down, s = 1 up-up.
+#pragma unroll 1
+    for (int pass = 0; pass < NS; ++pass) {
+        const int parts = pass == 0 ? PARTS_UD : PARTS_X;
+        if (RIGHT) vertex_part_f32<R>(V, G, parts, true, 8 | 16 | 32, w, qn[j], ve, g, pass > 0);
+        else vertex_part_f32<R>(V, G, parts, false, 8 | 16 | 32, w, ve, qn[j], g, pass > 0);
+        const bool uu = pass > 0;
+        const int s = (NS == 1) ? 0 : (RIGHT ? (uu ? 1 : 0) : (uu ? 0 : 1));
+        if (MODE != 1) {
+            float* base = tile + (size_t)(wt0 + wl) * 4 * plane;
+            size_t col = ((size_t)s * J.nq + j) * 4;
 #pragma unroll
-        for (int A = 0; A < 4; ++A) {
-            float2 v[4] = {g[cmap<R>(A, 0)], g[cmap<R>(A, 1)], g[cmap<R>(A, 2)], g[cmap<R>(A, 3)]};
-            write_planes(base, plane, (size_t)vi * 4 + A, K, col, v);
-        }
-    }
-    if (MODE != 0) {
-        float2 h[16];
-        int sr = s;
-        if (MODE == 2) {
-            // right record Gamma2^c(w, v'', v' = v) = sign(c) conj(Gamma1^{pi(c)}(w, v, v''))
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                constexpr int dummy = 0;
-                (void)dummy;
-                int pc = (R == KB_CH_T) ? perm_x(perm_c(c)) : perm_c(c);
-                float sg = sign_c(c);
-                h[c] = make_float2(sg * g[pc].x, -sg * g[pc].y);
+            for (int A = 0; A < 4; ++A) {
+                float2 v[4] = {g[cmap<R>(A, 0)], g[cmap<R>(A, 1)], g[cmap<R>(A, 2)], g[cmap<R>(A, 3)]};
+                write_planes(base, plane, (size_t)vi * 4 + A, K, col, v);
             }
-            if (R == KB_CH_T) sr = 1 - s;      // left up-up (0) <-> right up-up (1)
-        } else {
-#pragma unroll
-            for (int c = 0; c < 16; ++c) h[c] = g[c];
         }
-        float* base = (MODE == 2 ? tileR : tile) + (size_t)(wt0 + wl) * 4 * plane;
-        size_t col = ((size_t)sr * J.nq + j) * 4;
+        if (MODE != 0) {
+            float2 h[16];
+            int sr = s;
+            if (MODE == 2) {
+                // right record Gamma2^c(w, v'', v' = v) = sign(c) conj(Gamma1^{pi(c)}(w, v, v''))
 #pragma unroll
-        for (int C = 0; C < 4; ++C) {
-            float2 v[4];
-#pragma unroll
-            for (int B = 0; B < 4; ++B) {
-                float2 a = make_float2(0, 0);
-#pragma unroll
-                for (int D = 0; D < 4; ++D) {
-                    float2 p = P[4 * B + D], x = h[cmap<R>(D, C)];
-                    a.x = fmaf(p.x, x.x, fmaf(-p.y, x.y, a.x));
-                    a.y = fmaf(p.x, x.y, fmaf(p.y, x.x, a.y));
+                for (int c = 0; c < 16; ++c) {
+                    int pc = (R == KB_CH_T) ? perm_x(perm_c(c)) : perm_c(c);
+                    float sg = sign_c(c);
+                    h[c] = make_float2(sg * g[pc].x, -sg * g[pc].y);
                 }
-                v[B] = a;
+                if (R == KB_CH_T) sr = 1 - s;      // left up-up (0) <-> right up-up (1)
+            } else {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) h[c] = g[c];
             }
-            write_planes(base, plane, (size_t)vi * 4 + C, K, col, v);
+            float* base = (MODE == 2 ? tileR : tile) + (size_t)(wt0 + wl) * 4 * plane;
+            size_t col = ((size_t)sr * J.nq + j) * 4;
+#pragma unroll
+            for (int C = 0; C < 4; ++C) {
+                float2 v[4];
+#pragma unroll
+                for (int B = 0; B < 4; ++B) {
+                    float2 a = make_float2(0, 0);
+#pragma unroll
+                    for (int D = 0; D < 4; ++D) {
+                        float2 p = P[4 * B + D], x = h[cmap<R>(D, C)];
+                        a.x = fmaf(p.x, x.x, fmaf(-p.y, x.y, a.x));
+                        a.y = fmaf(p.x, x.y, fmaf(p.y, x.x, a.y));
+                    }
+                    v[B] = a;
+                }
+                write_planes(base, plane, (size_t)vi * 4 + C, K, col, v);
+            }
         }
     }
 }
+
 
 // Symmetry fill: out[dst] = image of out[src] for the output classes of a bubble of a
 // symmetric vertex with itself (see kb_set_vertex_symmetric).  kind: 0 conjugation after
@@ -553,7 +613,7 @@ static VertexF to_vf(const VertexDev& V, kb_ctx* ctx, bool& ok) {
 // Workspace layout of one mixed-precision bubble of channel r (byte offsets into the
 // context's workspace) and the bytes it needs.
 struct MixedLayout {
-    size_t off_tab, off_N, off_M, off_S, off_P3, off_T, rows, K, per_w, tc_scratch, need;
+    size_t off_tab, off_N, off_M, off_S, off_P3, off_K1, off_T, rows, K, per_w, tc_scratch, need;
     int chunk;
 };
 
@@ -570,7 +630,9 @@ static MixedLayout mixed_layout(const kb_ctx* ctx, int r, unsigned mask) {
     size_t szS = (size_t)2 * g.n2w * ns * 16 * sizeof(double2);
     L.off_P3 = (L.off_S + szS + 255) / 256 * 256;
     size_t szP3 = (size_t)g.n3w * g.nq * 16 * sizeof(float2);
-    L.off_T = (L.off_P3 + szP3 + 1023) / 1024 * 1024;
+    L.off_K1 = (L.off_P3 + szP3 + 255) / 256 * 256;
+    size_t szK1 = (size_t)g.n1 * K1_SLICES * 16 * sizeof(double2);
+    L.off_T = (L.off_K1 + szK1 + 1023) / 1024 * 1024;
     L.rows = (size_t)4 * g.n3v;
     L.K = (size_t)4 * ns * g.nq;
     L.per_w = 2 * 4 * L.rows * L.K * sizeof(float) + L.rows * L.rows * sizeof(double2) + 1024;
@@ -620,10 +682,19 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
                                                                     tab);
     }
     if ((mask >> KB_K1) & 1) {
-        KB_LAUNCH(ctx, st, "k_mx_k1");
         int w_off = (sym && r != KB_CH_P) ? g.n1 / 2 : 0;
-        k_mx_k1<r><<<g.n1 - w_off, 128, 0, st>>>(VL, VR, G, ctx->m, J, ctx->d_xq, ctx->d_wq,
-                                              const_cast<void*>(VO.cls[r][KB_K1]), VO.dt[r][KB_K1], w_off);
+        double2* part = reinterpret_cast<double2*>(ws + Lo.off_K1);
+        {
+            KB_LAUNCH(ctx, st, "k_mx_k1");
+            k_mx_k1<r><<<dim3(g.n1 - w_off, K1_SLICES), 128, 0, st>>>(VL, VR, G, ctx->m, J, ctx->d_xq, ctx->d_wq,
+                                                                     part, w_off);
+        }
+        {
+            KB_LAUNCH(ctx, st, "k_mx_k1_fin");
+            int tot = (g.n1 - w_off) * 16;
+            k_mx_k1_fin<<<(tot + 127) / 128, 128, 0, st>>>(J, part, const_cast<void*>(VO.cls[r][KB_K1]),
+                                                          VO.dt[r][KB_K1], w_off, g.n1 - w_off);
+        }
     }
     if (mask & ((1u << KB_K2) | (1u << KB_K2P))) {
         {
@@ -662,16 +733,16 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
             int nwc = std::min(chunk, g.n3w - w0);
             if (sym) {
                 KB_LAUNCH(ctx, st, "k_mx_tile3_both");
-                k_mx_tile3<2, r><<<dim3((g.nq + 127) / 128, g.n3v * ns, nwc), 128, 0, st>>>(VL, G, J, w0, 0, P3, TA, TB);
+                k_mx_tile3<2, r><<<dim3((g.nq + 127) / 128, g.n3v, nwc), 128, 0, st>>>(VL, G, J, w0, 0, P3, TA, TB);
             } else {
                 {
                     KB_LAUNCH(ctx, st, "k_mx_tile3_left");
-                    k_mx_tile3<0, r><<<dim3((g.nq + 127) / 128, g.n3v * ns, nwc), 128, 0, st>>>(VL, G, J, w0, 0, P3, TA,
+                    k_mx_tile3<0, r><<<dim3((g.nq + 127) / 128, g.n3v, nwc), 128, 0, st>>>(VL, G, J, w0, 0, P3, TA,
                                                                                                nullptr);
                 }
                 {
                     KB_LAUNCH(ctx, st, "k_mx_tile3_right");
-                    k_mx_tile3<1, r><<<dim3((g.nq + 127) / 128, g.n3v * ns, nwc), 128, 0, st>>>(VR, G, J, w0, 0, P3, TB,
+                    k_mx_tile3<1, r><<<dim3((g.nq + 127) / 128, g.n3v, nwc), 128, 0, st>>>(VR, G, J, w0, 0, P3, TB,
                                                                                                nullptr);
                 }
             }

@@ -307,19 +307,30 @@ __device__ __forceinline__ void apply7(const VertexF& V, int ch, const Sten7& S,
 // Parts of the vertex relative to channel r at r-variables (w, v, vp), FP32 accumulation.
 // what bits: 1 = R, 2 = K1_r, 4 = ext-free own class (K2'_r left / K2_r right),
 // 8 = ext-dependent own class (K2_r left / K2'_r right), 16 = K3_r, 32 = other channels.
-// uu: up-up component, built channel by channel (crossing partner a <-> t).
+// parts: PARTS_UD = the up-down component (direct lookups); PARTS_X = the exchanged term
+// of the up-up component alone, -gamma_{sigma(c)}^ud(1'2'|21) channel by channel
+// (crossing partner a <-> t, p -> p); PARTS_UU = both, the up-up component.  Since
+// up-up = up-down + exchanged term, a caller that needs both spin components evaluates
+// PARTS_UD once and then adds PARTS_X onto it (accumulate = true).
 // The argument that may be infinite is the quadrature frequency v''; infinite arguments
 // make a class read zero, and the other channels then vanish as well.
 // All stencils of a group of lookups are computed before its corner loads so that the
 // independent stencil computations overlap.
+constexpr int PARTS_UD = 1, PARTS_X = 2, PARTS_UU = 3;
+
 template <int r>
-__device__ __forceinline__ void vertex_part_f32(const VertexF& V, const DfGrids& G, bool uu, bool right, int what, df w,
-                                                df v, df vp, float2 out[16]) {
+__device__ __forceinline__ void vertex_part_f32(const VertexF& V, const DfGrids& G, int parts, bool right, int what,
+                                                df w, df v, df vp, float2 out[16], bool accumulate = false) {
+    const bool dir = parts & PARTS_UD, exch = parts & PARTS_X;
+    if (!accumulate) {
 #pragma unroll
-    for (int o = 0; o < 16; ++o) out[o] = make_float2(0.f, 0.f);
-    if ((what & 1) && !uu && V.has_R) {
+        for (int o = 0; o < 16; ++o) out[o] = make_float2(0.f, 0.f);
+    }
+    // the bare part is even under a1 <-> a2, so its up-up value R(12) - R(21) is zero
+    if ((what & 1) && V.has_R && dir != exch) {
+        const float u = dir ? V.halfU : -V.halfU;
 #pragma unroll
-        for (int o = 0; o < 16; ++o) out[o].x = (__popc(o) & 1) ? V.halfU : 0.f;
+        for (int o = 0; o < 16; ++o) out[o].x += (__popc(o) & 1) ? u : 0.f;
     }
     int k_free = right ? 1 : 2, k_dep = right ? 2 : 1;
     unsigned own = 0;
@@ -330,8 +341,8 @@ __device__ __forceinline__ void vertex_part_f32(const VertexF& V, const DfGrids&
     if (!((V.mask >> r) & 1)) own = 0;
     bool cross = (what & 32) && isfinite(v.h) && isfinite(vp.h);
     constexpr int sr = (r == KB_CH_A) ? KB_CH_T : (r == KB_CH_T ? KB_CH_A : KB_CH_P);
-    // lookup groups: 0 own direct, 1 own exchanged (uu), 2/3 other channels direct,
-    // 4/5 their exchanged partners (uu)
+    // lookup groups: 0 own direct, 1 own exchanged, 2/3 other channels direct,
+    // 4/5 their exchanged partners
 #pragma unroll 1
     for (int grp = 0; grp < 6; ++grp) {
         int ch;
@@ -340,14 +351,14 @@ __device__ __forceinline__ void vertex_part_f32(const VertexF& V, const DfGrids&
         bool sw = false;
         df gw, gv, gp;
         if (grp == 0) {
-            if (!own) continue;
+            if (!own || !dir) continue;
             ch = r; classes = own; gw = w; gv = v; gp = vp;
         } else if (grp == 1) {
-            if (!own || !uu) continue;
+            if (!own || !exch) continue;
             ch = sr; classes = own; f = -1.f; sw = true;
             gw = (r == KB_CH_P) ? w : df_neg(w); gv = v; gp = (r == KB_CH_P) ? df_neg(vp) : vp;
         } else {
-            if (!cross) continue;
+            if (!cross || (grp < 4 ? !dir : !exch)) continue;
             int c = (grp & 1) ? ((r == 2) ? 1 : 2) : ((r == 0) ? 1 : 0);   // the two channels != r
             if (!((V.mask >> c) & 1)) continue;
             df L[4];
@@ -357,7 +368,6 @@ __device__ __forceinline__ void vertex_part_f32(const VertexF& V, const DfGrids&
                 ch = c;
                 df_vars(c, L, gw, gv, gp);
             } else {
-                if (!uu) continue;
                 ch = (c == KB_CH_A) ? KB_CH_T : (c == KB_CH_T ? KB_CH_A : KB_CH_P);
                 df S4[4] = {L[0], L[1], L[3], L[2]};
                 df_vars(ch, S4, gw, gv, gp);
