@@ -45,131 +45,68 @@ struct DfGrids {
     float A;
 };
 
-// Approximate x = (2/pi) atan(v/A) of a frequency; shared by all grids that read it.
-__device__ __forceinline__ float x_of(df v, float A) { return 0.636619772367581343f * atanf(v.h / A); }
+// Cell estimate x ~ (2/pi) atan(v/A) of a frequency, shared by all grids that read it.
+// It only has to land within one cell of the true one (the cell is then fixed by exact
+// double-float comparisons with the node frequencies), so a short odd polynomial in
+// u = min(|y|, 1/|y|), y = v/A, does: (2/pi) atan(u) ~ u (c0 + c1 u^2 + c2 u^4 + c3 u^6),
+// least-squares fit on [0, 1] (csrc/fit_atan_estimate.py), max error 5.2e-5 in x, i.e.
+// below 0.03 cells for grids of up to 1000 points; atan(y) = pi/2 - atan(1/y) for y > 1.
+__device__ __forceinline__ float x_est(float v, float invA) {
+    const float y = fabsf(v) * invA;
+    const bool big = y > 1.f;
+    const float u = big ? __fdividef(1.f, y) : y;
+    const float u2 = u * u;
+    const float p = u * fmaf(u2, fmaf(u2, fmaf(u2, -0.02481973f, 0.09311505f), -0.2044664f), 0.63611925f);
+    return copysignf(big ? 1.f - p : p, v);
+}
 
-// Stencil from a precomputed approximate x (see df_stencil below for the method).
+// atan(z) for the small arguments of the stencil fraction: the odd Taylor series to z^15
+// (relative error below z^16/17, 1.1e-9 at |z| = 0.33); larger |z| (grids of fewer than
+// nine points, or the cells next to x = +-1 on such grids) take atanf.
+__device__ __forceinline__ float atan_frac(float z) {
+    if (fabsf(z) > 0.33f) return atanf(z);
+    const float z2 = z * z;
+    float p = fmaf(z2, -1.f / 15.f, 1.f / 13.f);
+    p = fmaf(z2, p, -1.f / 11.f);
+    p = fmaf(z2, p, 1.f / 9.f);
+    p = fmaf(z2, p, -1.f / 7.f);
+    p = fmaf(z2, p, 1.f / 5.f);
+    p = fmaf(z2, p, -1.f / 3.f);
+    p = fmaf(z2, p, 1.f);
+    return z * p;
+}
+
+// Stencil on an N-point grid with zero-valued virtual nodes at x = +-1 from the cell
+// estimate x: returns the lower node k in [-1, N-1] and the fraction t toward node k+1.
+// The fraction relative to the estimated node uses atan(a) - atan(b) = atan((a - b)/(1 + ab))
+// with a - b formed in double-float: x - X_k = (2/pi) atan((v - v_k) A / (A^2 + v v_k)),
+// and for k = -1 (v < 0) x + 1 = (2/pi) atan(-A/v).  It is accurate to the FP32 relative
+// error of t itself, so the estimate only has to be within one cell: t < 0 or t >= 1
+// moves k by one (t + 1, t - 1 are then exact to FP32 rounding).
 __device__ __forceinline__ int stencil_x(df v, float x, const df* __restrict__ nodes, int N, float A, float& t) {
     int k = (int)floorf((x + 1.0f) * (0.5f * (float)(N + 1))) - 1;
     k = max(-1, min(k, N - 1));
-    if (k >= 0 && df_lt(v, nodes[k])) --k;
-    else if (k + 1 <= N - 1 && !df_lt(v, nodes[k + 1])) ++k;
+    if (k < 0 && !(v.h < 0.f)) k = 0;
+    const float scale = (float)(N + 1) * 0.318309886183790672f;
     float z;
     if (k < 0) {
-        z = -A / v.h;
+        z = __fdividef(-A, v.h);
     } else {
         df nk = nodes[k];
         df d = df_sub(v, nk);
-        z = (d.h + d.l) * A / fmaf(v.h, nk.h, A * A);
+        z = __fdividef((d.h + d.l) * A, fmaf(v.h, nk.h, A * A));
     }
-    t = atanf(z) * ((float)(N + 1) * 0.318309886183790672f);
+    t = atan_frac(z) * scale;
+    if (t < 0.f && k >= 0) { --k; t += 1.f; }
+    else if (t >= 1.f && k < N - 1) { ++k; t -= 1.f; }
+    t = fminf(fmaxf(t, 0.f), 1.f);
     return k;
-}
-
-// Stencil on an N-point grid with zero-valued virtual nodes at x = +-1: returns the lower
-// node k in [-1, N-1] and the fraction t toward node k+1; -2 for an infinite argument.
-__device__ __forceinline__ int df_stencil(df v, const df* __restrict__ nodes, int N, float A, float& t) {
-    if (!isfinite(v.h)) return -2;
-    float x = 0.636619772367581343f * atanf(v.h / A);
-    int k = (int)floorf((x + 1.0f) * (0.5f * (float)(N + 1))) - 1;
-    k = max(-1, min(k, N - 1));
-    if (k >= 0 && df_lt(v, nodes[k])) --k;
-    else if (k + 1 <= N - 1 && !df_lt(v, nodes[k + 1])) ++k;
-    float z;
-    if (k < 0) {
-        z = -A / v.h;                                  // x + 1 = (2/pi) atan(-A/v), v < 0
-    } else {
-        df nk = nodes[k];
-        df d = df_sub(v, nk);
-        z = (d.h + d.l) * A / fmaf(v.h, nk.h, A * A);
-    }
-    t = atanf(z) * ((float)(N + 1) * 0.318309886183790672f);
-    return k;
-}
-
-// acc[o] += f * class value, 16 comps, data complex64 [..][16]; swap12 reads comp o with
-// the unprimed Keldysh indices exchanged (bits 0 and 1 of o).
-__device__ __forceinline__ void add_rec16(float2 acc[16], const float2* __restrict__ p, float g, bool swap12) {
-    const float4* q = reinterpret_cast<const float4*>(p);
-    const float2 gg = make_float2(g, g);
-#pragma unroll
-    for (int grp = 0; grp < 4; ++grp) {
-        float4 u = __ldg(q + 2 * grp), v = __ldg(q + 2 * grp + 1);
-        float2 c0 = make_float2(u.x, u.y), c1 = make_float2(u.z, u.w), c2 = make_float2(v.x, v.y),
-               c3 = make_float2(v.z, v.w);
-        if (swap12) { float2 tmp = c1; c1 = c2; c2 = tmp; }
-        acc[4 * grp + 0] = __ffma2_rn(gg, c0, acc[4 * grp + 0]);
-        acc[4 * grp + 1] = __ffma2_rn(gg, c1, acc[4 * grp + 1]);
-        acc[4 * grp + 2] = __ffma2_rn(gg, c2, acc[4 * grp + 2]);
-        acc[4 * grp + 3] = __ffma2_rn(gg, c3, acc[4 * grp + 3]);
-    }
 }
 
 // acc += x * y (complex), two packed FMAs
 __device__ __forceinline__ void cmac2(float2& acc, float2 x, float2 y) {
     acc = __ffma2_rn(make_float2(x.x, x.x), y, acc);
     acc = __ffma2_rn(make_float2(-x.y, x.y), make_float2(y.y, y.x), acc);
-}
-
-// Class k (0 K1, 1 K2, 2 K2', 3 K3) of data D at channel variables (w, v, vp).
-__device__ __forceinline__ void acc_class_f32(const float2* __restrict__ D, int k, const DfGrids& G, df w, df v,
-                                              df vp, float f, bool swap12, float2 acc[16]) {
-    if (!D) return;
-    float tw, tv = 0.f, tp = 0.f;
-    int kw, kv = 0, kp = 0, nv = 1;
-    if (k == 0) {
-        kw = df_stencil(w, G.n1, G.N1, G.A, tw);
-        if (kw == -2) return;
-        for (int a = 0; a < 2; ++a) {
-            int iw = kw + a;
-            float fw = a ? tw : 1.f - tw;
-            if (iw < 0 || iw >= G.N1 || fw == 0.f) continue;
-            add_rec16(acc, D + (size_t)iw * 16, f * fw, swap12);
-        }
-        return;
-    }
-    if (k < 3) {
-        kw = df_stencil(w, G.n2w, G.N2w, G.A, tw);
-        if (kw == -2) return;
-        kv = df_stencil(k == 1 ? v : vp, G.n2v, G.N2v, G.A, tv);
-        if (kv == -2) return;
-        nv = G.N2v;
-        for (int a = 0; a < 2; ++a) {
-            int iw = kw + a;
-            float fw = a ? tw : 1.f - tw;
-            if (iw < 0 || iw >= G.N2w || fw == 0.f) continue;
-            for (int b = 0; b < 2; ++b) {
-                int iv = kv + b;
-                float fv = b ? tv : 1.f - tv;
-                if (iv < 0 || iv >= nv || fv == 0.f) continue;
-                add_rec16(acc, D + ((size_t)iw * nv + iv) * 16, f * fw * fv, swap12);
-            }
-        }
-        return;
-    }
-    kw = df_stencil(w, G.n3w, G.N3w, G.A, tw);
-    if (kw == -2) return;
-    kv = df_stencil(v, G.n3v, G.N3v, G.A, tv);
-    if (kv == -2) return;
-    kp = df_stencil(vp, G.n3v, G.N3v, G.A, tp);
-    if (kp == -2) return;
-    nv = G.N3v;
-    for (int a = 0; a < 2; ++a) {
-        int iw = kw + a;
-        float fw = a ? tw : 1.f - tw;
-        if (iw < 0 || iw >= G.N3w || fw == 0.f) continue;
-        for (int b = 0; b < 2; ++b) {
-            int iv = kv + b;
-            float fv = b ? tv : 1.f - tv;
-            if (iv < 0 || iv >= nv || fv == 0.f) continue;
-            for (int e = 0; e < 2; ++e) {
-                int ip = kp + e;
-                float fp = e ? tp : 1.f - tp;
-                if (ip < 0 || ip >= nv || fp == 0.f) continue;
-                add_rec16(acc, D + (((size_t)iw * nv + iv) * nv + ip) * 16, f * fw * fv * fp, swap12);
-            }
-        }
-    }
 }
 
 // legs (v1', v2', v1, v2) and channel variables in double-float (Sec. II.D.1)
@@ -277,7 +214,8 @@ __device__ __forceinline__ Sten7 stencils7(const VertexF& V, int ch, unsigned cl
                                            df gp) {
     Sten7 S;
     const bool fw = isfinite(gw.h), fv = isfinite(gv.h), fp = isfinite(gp.h);
-    const float xw = fw ? x_of(gw, G.A) : 0.f, xv = fv ? x_of(gv, G.A) : 0.f, xp = fp ? x_of(gp, G.A) : 0.f;
+    const float ia = 1.f / G.A;
+    const float xw = fw ? x_est(gw.h, ia) : 0.f, xv = fv ? x_est(gv.h, ia) : 0.f, xp = fp ? x_est(gp.h, ia) : 0.f;
     S.u0 = (classes & 1) && V.cls[ch][0] && fw;
     S.u1 = (classes & 2) && V.cls[ch][1] && fw && fv;
     S.u2 = (classes & 4) && V.cls[ch][2] && fw && fp;
