@@ -273,16 +273,19 @@ __global__ void __maxnreg__(96)
             }
             fence_after();
             uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * NT + cg * 16);
+            // one 16-column load (and one wait) per part: the load latency is paid twice per
+            // segment, not once per 8 columns
+            {
+                float v[16];
+                tmem_ld16(ta, v);
 #pragma unroll
-            for (int part = 0; part < 4; ++part) {
-                float v[8];
-                tmem_ld8(ta + (part >> 1) * NT + (part & 1) * 8, v);
+                for (int c = 0; c < 16; ++c) two_sum_acc(hre[c], lre[c], v[c]);
+            }
+            {
+                float v[16];
+                tmem_ld16(ta + NT, v);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    int c = (part & 1) * 8 + i;
-                    if (part < 2) two_sum_acc(hre[c], lre[c], v[i]);
-                    else two_sum_acc(him[c], lim[c], v[i]);
-                }
+                for (int c = 0; c < 16; ++c) two_sum_acc(him[c], lim[c], v[c]);
             }
             fence_before();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&segempty[buf])) : "memory");
