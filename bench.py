@@ -104,9 +104,18 @@ def mixed_kernel_work(channels=(0, 1, 2)):
     return w
 
 
+# DRAM bytes (read + write) of one launch of each timed kernel, from ncu captures of the
+# a-channel bubble of this workload (dram__bytes_read.sum + dram__bytes_write.sum; the
+# commands are in profiles/).  The K3 kernels' traffic grows with the bosonic frequencies of
+# a launch; these are the figures of the captured launches (26 frequencies).
+NCU_TRAFFIC = {"k_mx_k2": 61.6e6, "k_mx_tile3_both": 2.985e9, "k_tc_k3": 3.458e9}
+
+
 def roofline_entry(name, ms_total, steps, work, bf16_peak, traffic=None):
     if name not in work or ms_total <= 0:
         return None
+    if traffic is None:
+        traffic = NCU_TRAFFIC.get(name)
     flops = work[name] * steps
     if name == "k_tc_k3":
         peak = bf16_peak * TF32_OVER_BF16
