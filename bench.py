@@ -73,7 +73,8 @@ def mixed_kernel_work(channels=(0, 1, 2)):
     the up-up one adds the exchanged term (each lookup again at the exchanged legs: 44 more),
     so a t record, which needs both spin components, has 88; the fused K2 kernel
     adds the 4x4x4 complex contraction (512 flops), the K3 tile kernel the Pi fold of the
-    right record (512 flops) and the own K2 class (4 corners).
+    right record (512 flops; p folds two, the record and its crossing image) and the own K2
+    class (4 corners).  Symmetric mode: a, t compute w >= 0, p computes v >= 0 of K2 and K3.
     K3 contraction: 8 M N K useful flops per bosonic frequency (M = N = 4 n3v, K = 4 ns nq);
     the 3xTF32 split issues three times that on the tensor pipe."""
     g = GRIDS
@@ -88,18 +89,19 @@ def mixed_kernel_work(channels=(0, 1, 2)):
         (2 in channels) * rec_t * ((44 + 44) * 64 + 2 * 512)
     # k_mx_tile3_both
     r3a = half(g["n3w"]) * g["n3v"] * nq
-    r3p = g["n3w"] * g["n3v"] * nq
+    r3p = g["n3w"] * half(g["n3v"]) * nq
     r3t = half(g["n3w"]) * g["n3v"] * nq
-    w["k_mx_tile3_both"] = ((0 in channels) * r3a + (1 in channels) * r3p) * (48 * 64 + 512) + \
+    w["k_mx_tile3_both"] = (0 in channels) * r3a * (48 * 64 + 512) + (1 in channels) * r3p * (48 * 64 + 2 * 512) + \
         (2 in channels) * r3t * ((48 + 48) * 64 + 2 * 512)
     # k_tc_k3 (useful)
-    M = 4 * g["n3v"]
+    N = 4 * g["n3v"]
     tc = 0.0
     for r, nw in ((0, half(g["n3w"])), (1, g["n3w"]), (2, half(g["n3w"]))):
         if r not in channels:
             continue
         ns = 2 if r == 2 else 1
-        tc += 8.0 * M * M * (4 * ns * nq) * nw
+        M = 4 * half(g["n3v"]) if r == 1 else N      # p: rows v >= 0, the rest by crossing
+        tc += 8.0 * M * N * (4 * ns * nq) * nw
     w["k_tc_k3"] = tc
     return w
 

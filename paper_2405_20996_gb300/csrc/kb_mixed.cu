@@ -396,20 +396,29 @@ __device__ __forceinline__ void write_planes(float* base, size_t plane, size_t r
 // MODE 0: left tile, 1: right tile, 2: both from one gather of the left record, the right
 // record being its symmetry image at the same w (a, p: conjugation; t: conjugation after
 // crossing, with the spin terms up-down <-> up-down, up-up <-> up-up).
+// Rows: the left tile holds v = vh .. N3v-1 (rowsL = 4 (N3v - vh) rows), the right tile all
+// v' (rowsR = 4 N3v rows).  vh > 0 (p channel, MODE 2): only the crossing-independent half
+// v >= 0 of the output is computed; the right tile rows v' < 0 then come from the same
+// records through crossing, Gamma2(w, -v'', -v) = X[Gamma2(w, v'', v)], written at the
+// mirrored node nq-1-j (the node set is symmetric under v'' -> -v'').
 template <int MODE, int R>
-__global__ void __launch_bounds__(128, 4) k_mx_tile3(VertexF V, DfGrids G, MixedJob J, int w0, int wt0,
-                                                  const float2* __restrict__ Pt, float* __restrict__ tile,
-                                                  float* __restrict__ tileR) {
+__global__ void __launch_bounds__(128, 4) k_mx_tile3(VertexF V, DfGrids G, MixedJob J, int w0, int wt0, int vh,
+                                                  int rowsL, int rowsR, const float2* __restrict__ Pt,
+                                                  float* __restrict__ tile, float* __restrict__ tileR) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     constexpr int NS = (R == KB_CH_T) ? 2 : 1;
     constexpr bool RIGHT = (MODE == 1);
-    int vi = blockIdx.y, wl = blockIdx.z;
+    int vi = vh + blockIdx.y, wl = blockIdx.z;
     if (j >= J.nq) return;
     const df* qn = G.n3v + G.N3v;
     df w = G.n3w[w0 + wl], ve = G.n3v[vi];
-    size_t rows = (size_t)4 * G.N3v, K = (size_t)4 * NS * J.nq;
-    size_t plane = rows * K;
+    const size_t K = (size_t)4 * NS * J.nq;
+    const size_t planeL = (size_t)rowsL * K, planeR = (size_t)rowsR * K;
     const float2* P = Pt + ((size_t)(w0 + wl) * J.nq + j) * 16;
+    const int vm = G.N3v - 1 - vi;                 // mirrored row of the crossing image
+    const bool mirror = (MODE == 2) && (R == KB_CH_P) && vh > 0 && vm != vi;
+    const int jm = J.nq - 1 - j;
+    const float2* Pm = Pt + ((size_t)(w0 + wl) * J.nq + jm) * 16;
     float2 g[16];
     // t channel: the up-down record first, then the exchanged term turns it into the
     // up-up record (one set of direct lookups for both spin terms).  Spin index s of the
@@ -422,12 +431,12 @@ __global__ void __launch_bounds__(128, 4) k_mx_tile3(VertexF V, DfGrids G, Mixed
         const bool uu = pass > 0;
         const int s = (NS == 1) ? 0 : (RIGHT ? (uu ? 1 : 0) : (uu ? 0 : 1));
         if (MODE != 1) {
-            float* base = tile + (size_t)(wt0 + wl) * 4 * plane;
+            float* base = tile + (size_t)(wt0 + wl) * 4 * planeL;
             size_t col = ((size_t)s * J.nq + j) * 4;
 #pragma unroll
             for (int A = 0; A < 4; ++A) {
                 float2 v[4] = {g[cmap<R>(A, 0)], g[cmap<R>(A, 1)], g[cmap<R>(A, 2)], g[cmap<R>(A, 3)]};
-                write_planes(base, plane, (size_t)vi * 4 + A, K, col, v);
+                write_planes(base, planeL, (size_t)(vi - vh) * 4 + A, K, col, v);
             }
         }
         if (MODE != 0) {
@@ -446,7 +455,7 @@ __global__ void __launch_bounds__(128, 4) k_mx_tile3(VertexF V, DfGrids G, Mixed
 #pragma unroll
                 for (int c = 0; c < 16; ++c) h[c] = g[c];
             }
-            float* base = (MODE == 2 ? tileR : tile) + (size_t)(wt0 + wl) * 4 * plane;
+            float* base = (MODE == 2 ? tileR : tile) + (size_t)(wt0 + wl) * 4 * planeR;
             size_t col = ((size_t)sr * J.nq + j) * 4;
 #pragma unroll
             for (int C = 0; C < 4; ++C) {
@@ -462,7 +471,27 @@ __global__ void __launch_bounds__(128, 4) k_mx_tile3(VertexF V, DfGrids G, Mixed
                     }
                     v[B] = a;
                 }
-                write_planes(base, plane, (size_t)vi * 4 + C, K, col, v);
+                write_planes(base, planeR, (size_t)vi * 4 + C, K, col, v);
+            }
+            if (mirror) {
+                // crossing image: component c of the mirrored record is component perm_x(c)
+                size_t colm = ((size_t)sr * J.nq + jm) * 4;
+#pragma unroll
+                for (int C = 0; C < 4; ++C) {
+                    float2 v[4];
+#pragma unroll
+                    for (int B = 0; B < 4; ++B) {
+                        float2 a = make_float2(0, 0);
+#pragma unroll
+                        for (int D = 0; D < 4; ++D) {
+                            float2 p = Pm[4 * B + D], x = h[perm_x(cmap<R>(D, C))];
+                            a.x = fmaf(p.x, x.x, fmaf(-p.y, x.y, a.x));
+                            a.y = fmaf(p.x, x.y, fmaf(p.y, x.x, a.y));
+                        }
+                        v[B] = a;
+                    }
+                    write_planes(base, planeR, (size_t)vm * 4 + C, K, colm, v);
+                }
             }
         }
     }
@@ -566,24 +595,26 @@ __global__ void __launch_bounds__(256) k_mx_cgemm(const float* __restrict__ At, 
         }
 }
 
-// out K3 <- alpha C + beta out, C[wl][(v, A)][(v', C)]
-__global__ void k_mx_scatter3(MixedJob J, int w0, int nwc, int nv, const double2* __restrict__ Cm, void* out, int odt) {
+// out K3 <- alpha C + beta out, C[wl][(v - vh, A)][(v', C)] for v = vh .. nv-1
+__global__ void k_mx_scatter3(MixedJob J, int w0, int nwc, int nv, int vh, const double2* __restrict__ Cm, void* out,
+                              int odt) {
+    const int nvL = nv - vh;
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    size_t total = (size_t)nwc * nv * nv * 16;
+    size_t total = (size_t)nwc * nvL * nv * 16;
     if (idx >= total) return;
     int o = idx % 16;
     size_t rest = idx / 16;
     int vR = rest % nv;
     rest /= nv;
-    int vL = rest % nv;
-    int wl = (int)(rest / nv);
+    int vL = rest % nvL;
+    int wl = (int)(rest / nvL);
     int A = 0, C = 0;
     for (int a = 0; a < 4; ++a)
         for (int c = 0; c < 4; ++c)
             if (J.M.cO[a][c] == o) { A = a; C = c; }
-    int Mr = 4 * nv;
-    double2 gv = Cm[((size_t)wl * Mr + 4 * vL + A) * Mr + 4 * vR + C];
-    store_out(out, odt, (((size_t)(w0 + wl) * nv + vL) * nv + vR) * 16 + o, gv, J.alpha, J.beta);
+    int Mr = 4 * nvL, Nc = 4 * nv;
+    double2 gv = Cm[((size_t)wl * Mr + 4 * vL + A) * Nc + 4 * vR + C];
+    store_out(out, odt, (((size_t)(w0 + wl) * nv + vh + vL) * nv + vR) * 16 + o, gv, J.alpha, J.beta);
 }
 
 }  // namespace kb
@@ -729,34 +760,38 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
         void* scratch = reinterpret_cast<char*>(Cm) + (size_t)chunk * rows * rows * sizeof(double2);
         bool use_tc = std::getenv("KB_K3_SIMT") == nullptr;
         int w3_lo = (sym && r != KB_CH_P) ? g.n3w / 2 : 0;
+        // p (symmetric): rows v >= 0 only, the rest by crossing (k_mx_tile3, symmetry fill)
+        const int vh3 = (sym && r == KB_CH_P) ? g.n3v / 2 : 0;
+        const int rowsL = 4 * (g.n3v - vh3), rowsR = (int)rows;
         for (int w0 = w3_lo; w0 < g.n3w; w0 += chunk) {
             int nwc = std::min(chunk, g.n3w - w0);
             if (sym) {
                 KB_LAUNCH(ctx, st, "k_mx_tile3_both");
-                k_mx_tile3<2, r><<<dim3((g.nq + 127) / 128, g.n3v, nwc), 128, 0, st>>>(VL, G, J, w0, 0, P3, TA, TB);
+                k_mx_tile3<2, r><<<dim3((g.nq + 127) / 128, g.n3v - vh3, nwc), 128, 0, st>>>(VL, G, J, w0, 0, vh3, rowsL,
+                                                                                           rowsR, P3, TA, TB);
             } else {
                 {
                     KB_LAUNCH(ctx, st, "k_mx_tile3_left");
-                    k_mx_tile3<0, r><<<dim3((g.nq + 127) / 128, g.n3v, nwc), 128, 0, st>>>(VL, G, J, w0, 0, P3, TA,
-                                                                                               nullptr);
+                    k_mx_tile3<0, r><<<dim3((g.nq + 127) / 128, g.n3v, nwc), 128, 0, st>>>(VL, G, J, w0, 0, 0, rowsL,
+                                                                                           rowsR, P3, TA, nullptr);
                 }
                 {
                     KB_LAUNCH(ctx, st, "k_mx_tile3_right");
-                    k_mx_tile3<1, r><<<dim3((g.nq + 127) / 128, g.n3v, nwc), 128, 0, st>>>(VR, G, J, w0, 0, P3, TB,
-                                                                                               nullptr);
+                    k_mx_tile3<1, r><<<dim3((g.nq + 127) / 128, g.n3v, nwc), 128, 0, st>>>(VR, G, J, w0, 0, 0, rowsL,
+                                                                                           rowsR, P3, TB, nullptr);
                 }
             }
             bool done = false;
-            if (use_tc) done = kb_tc_k3(ctx, TA, TB, Cm, (int)rows, (int)rows, (int)K, nwc, scratch, tc_scratch, st);
+            if (use_tc) done = kb_tc_k3(ctx, TA, TB, Cm, rowsL, rowsR, (int)K, nwc, scratch, tc_scratch, st);
             if (!done) {
                 KB_LAUNCH(ctx, st, "k_mx_cgemm");
-                k_mx_cgemm<<<dim3((unsigned)((rows + 63) / 64), (unsigned)((rows + 63) / 64), nwc), 256, 0, st>>>(
-                    TA, TB, Cm, (int)rows, (int)rows, (int)K);
+                k_mx_cgemm<<<dim3((unsigned)((rowsR + 63) / 64), (unsigned)((rowsL + 63) / 64), nwc), 256, 0, st>>>(
+                    TA, TB, Cm, rowsL, rowsR, (int)K);
             }
             {
                 KB_LAUNCH(ctx, st, "k_mx_scatter3");
-                size_t tot = (size_t)nwc * g.n3v * g.n3v * 16;
-                k_mx_scatter3<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(J, w0, nwc, g.n3v, Cm,
+                size_t tot = (size_t)nwc * (g.n3v - vh3) * g.n3v * 16;
+                k_mx_scatter3<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(J, w0, nwc, g.n3v, vh3, Cm,
                                                                             const_cast<void*>(VO.cls[r][KB_K3]),
                                                                             VO.dt[r][KB_K3]);
             }
@@ -776,6 +811,7 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
             if ((mask >> KB_K1) & 1) fill(KB_K1, KB_K1, kw, g.n1, 1, 1, g.n1 / 2, 1);
             if ((mask >> KB_K3) & 1) fill(KB_K3, KB_K3, kw, g.n3w, g.n3v, g.n3v, g.n3w / 2, g.n3v);
         }
+        if (r == KB_CH_P && ((mask >> KB_K3) & 1)) fill(KB_K3, KB_K3, 2, g.n3w, g.n3v, g.n3v, g.n3w, g.n3v / 2);
         if ((mask >> KB_K2) & 1) {
             if (r != KB_CH_P) fill(KB_K2, KB_K2, kw, g.n2w, g.n2v, 1, g.n2w / 2, g.n2v);
             else fill(KB_K2, KB_K2, 2, g.n2w, g.n2v, 1, g.n2w, g.n2v / 2);
