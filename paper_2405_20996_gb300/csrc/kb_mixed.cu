@@ -236,6 +236,50 @@ __global__ void k_mx_sumj(const float2* __restrict__ Nt, const float2* __restric
     }
 }
 
+// Node-weighted sums of a K2-grid table: Ntil[t][w][s][m][16] = sum_j phi_m(v''_j) T_t(w, s, j)
+// over the interior nodes, phi_m the linear hat function of K3 grid node m in x (the same
+// stencil as the gathers, so the weights agree exactly).  The own K3 class of a K2 record is
+// K3_r(w, v, v'') with (w, v) fixed per output point, a function of v'' alone, so
+//   sum_j K3_r(w, v, v''_j) T(w, j) = sum_m K3_r(w, v, X_m) Ntil(w, m):
+// the own K3 lookups leave the node loop of k_mx_k2.  t = 0: N table (left), 1: M (right).
+__device__ __forceinline__ int first_not_below(const df* __restrict__ qn, int lo, int hi, df x) {
+    // first j in [lo, hi] with qn[j] >= x (hi + 1 if none); qn increasing
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        if (df_lt(qn[mid], x)) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_mx_ntilde(const float2* __restrict__ Nt, const float2* __restrict__ Mt, DfGrids G, int nq, int ns,
+                            int t0, double2* __restrict__ out) {
+    // one thread per (grid node m, Keldysh component o) of one (w, s, table)
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int wi = blockIdx.y, s = blockIdx.z % ns, t = t0 + blockIdx.z / ns;
+    const int m = idx >> 4, o = idx & 15;
+    if (m >= G.N3v) return;
+    const float2* T = (t == 0 ? Nt : Mt) + ((size_t)wi * ns + s) * nq * 16 + o;
+    const df* qn = G.n3v + G.N3v;
+    const float ia = 1.f / G.A;
+    // nodes whose stencil can touch grid node m lie between X_{m-1} and X_{m+1}
+    int jl = (m == 0) ? 1 : first_not_below(qn, 1, nq - 2, G.n3v[m - 1]) - 1;
+    int jh = (m == G.N3v - 1) ? nq - 2 : first_not_below(qn, 1, nq - 2, G.n3v[m + 1]);
+    jl = max(jl, 1);
+    jh = min(jh, nq - 2);
+    double ax = 0.0, ay = 0.0;
+    for (int j = jl; j <= jh; ++j) {
+        float tt;
+        const int k = stencil_x(qn[j], x_est(qn[j].h, ia), G.n3v, G.N3v, G.A, tt);
+        const float ph = (k == m) ? 1.f - tt : ((k + 1 == m) ? tt : 0.f);
+        if (ph == 0.f) continue;
+        const float2 x = __ldg(T + (size_t)j * 16);
+        ax = fma((double)ph, (double)x.x, ax);
+        ay = fma((double)ph, (double)x.y, ay);
+    }
+    out[((((size_t)t * G.N2w + wi) * ns + s) * G.N3v + m) * 16 + o] = make_double2(ax, ay);
+}
+
 // K2 (RIGHT = false): out(w, v)[A][C] = sum_j sum_s sum_B L_s(w, v, v''_j)[A][B] N_s(w, j)[B][C]
 //   with L the v-dependent part of Gamma1 without its own K2 class, plus
 //   K2own_s(w, v)[A][B] * SN_s(w)[B][C]  (the own K2 class does not depend on v'').
@@ -247,8 +291,8 @@ __global__ void k_mx_sumj(const float2* __restrict__ Nt, const float2* __restric
 // endpoint nodes contribute only through the own class and are skipped in the tiles.
 template <bool RIGHT, int R>
 __global__ void __launch_bounds__(128, 4) k_mx_k2(VertexF V, DfGrids G, MixedJob J, const float2* __restrict__ Tab,
-                                               const double2* __restrict__ Ssum, void* out, int odt, int w_off,
-                                               int v_off) {
+                                               const double2* __restrict__ Ssum, const double2* __restrict__ Ntil,
+                                               void* out, int odt, int w_off, int v_off) {
     constexpr int NS = (R == KB_CH_T) ? 2 : 1;
     // records of the quadrature nodes of one chunk: [0] up-down, [1] up-up (t only; the
     // up-up record is the up-down one plus the exchanged term, so the direct lookups are
@@ -270,8 +314,8 @@ __global__ void __launch_bounds__(128, 4) k_mx_k2(VertexF V, DfGrids G, MixedJob
         float2 g[16];
         const bool valid = j < J.nq - 1;
         if (valid) {
-            if (RIGHT) vertex_part_f32<R>(V, G, PARTS_UD, true, 16 | 32, w, qn[j], ve, g);
-            else vertex_part_f32<R>(V, G, PARTS_UD, false, 16 | 32, w, ve, qn[j], g);
+            if (RIGHT) vertex_part_f32<R>(V, G, PARTS_UD, true, 32, w, qn[j], ve, g);
+            else vertex_part_f32<R>(V, G, PARTS_UD, false, 32, w, ve, qn[j], g);
         } else {
 #pragma unroll
             for (int c = 0; c < 16; ++c) g[c] = make_float2(0.f, 0.f);
@@ -280,8 +324,8 @@ __global__ void __launch_bounds__(128, 4) k_mx_k2(VertexF V, DfGrids G, MixedJob
         for (int c = 0; c < 16; ++c) rec[0][tid][c] = g[c];
         if (NS == 2) {
             if (valid) {
-                if (RIGHT) vertex_part_f32<R>(V, G, PARTS_X, true, 16 | 32, w, qn[j], ve, g, true);
-                else vertex_part_f32<R>(V, G, PARTS_X, false, 16 | 32, w, ve, qn[j], g, true);
+                if (RIGHT) vertex_part_f32<R>(V, G, PARTS_X, true, 32, w, qn[j], ve, g, true);
+                else vertex_part_f32<R>(V, G, PARTS_X, false, 32, w, ve, qn[j], g, true);
             }
 #pragma unroll
             for (int c = 0; c < 16; ++c) rec[NS - 1][tid][c] = g[c];
@@ -317,6 +361,62 @@ __global__ void __launch_bounds__(128, 4) k_mx_k2(VertexF V, DfGrids G, MixedJob
             }
         }
         __syncthreads();
+    }
+    // own K3 class through the node-weighted sums: records at the K3 grid nodes X_m,
+    // [0] up-down (pairs with N_0 + N_1, or N_0 for a, p), [1] the exchanged term of the
+    // t channel's up-up component (pairs with N_0 left, N_1 right)
+    {
+        const double2* Nb = Ntil + (((size_t)(RIGHT ? 1 : 0) * G.N2w + wi) * NS) * G.N3v * 16;
+#pragma unroll 1
+        for (int m0 = 0; m0 < G.N3v; m0 += 128) {
+            const int m = m0 + tid;
+            if (m < G.N3v) {
+                float2 g[16];
+                if (RIGHT) vertex_part_f32<R>(V, G, PARTS_UD, true, 16, w, G.n3v[m], ve, g);
+                else vertex_part_f32<R>(V, G, PARTS_UD, false, 16, w, ve, G.n3v[m], g);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) rec[0][tid][c] = g[c];
+                if (NS == 2) {
+                    if (RIGHT) vertex_part_f32<R>(V, G, PARTS_X, true, 16, w, G.n3v[m], ve, g);
+                    else vertex_part_f32<R>(V, G, PARTS_X, false, 16, w, ve, G.n3v[m], g);
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) rec[NS - 1][tid][c] = g[c];
+                }
+            }
+            __syncthreads();
+            const int nrec = min(128, G.N3v - m0);
+#pragma unroll 1
+            for (int rr = q; rr < nrec; rr += 8) {
+                const double2* n0 = Nb + (size_t)(m0 + rr) * 16;
+                const double2* n1 = n0 + (size_t)G.N3v * 16;
+                if (!RIGHT) {
+#pragma unroll
+                    for (int B = 0; B < 4; ++B) {
+                        double2 a = n0[4 * B + C];
+                        if (NS == 2) {
+                            double2 b = n1[4 * B + C];
+                            cmac2(acc, rec[0][rr][cmap<R>(A, B)], make_float2((float)(a.x + b.x), (float)(a.y + b.y)));
+                            cmac2(acc, rec[NS - 1][rr][cmap<R>(A, B)], make_float2((float)a.x, (float)a.y));
+                        } else {
+                            cmac2(acc, rec[0][rr][cmap<R>(A, B)], make_float2((float)a.x, (float)a.y));
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int D = 0; D < 4; ++D) {
+                        double2 a = n0[4 * A + D];
+                        if (NS == 2) {
+                            double2 b = n1[4 * A + D];
+                            cmac2(acc, make_float2((float)(a.x + b.x), (float)(a.y + b.y)), rec[0][rr][cmap<R>(D, C)]);
+                            cmac2(acc, make_float2((float)b.x, (float)b.y), rec[NS - 1][rr][cmap<R>(D, C)]);
+                        } else {
+                            cmac2(acc, make_float2((float)a.x, (float)a.y), rec[0][rr][cmap<R>(D, C)]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
     }
     // own ext-dependent class: own(w, v) * sum_j N(w, j) (or sum_j M(w, j) * own(w, v'))
     if (q == 0) {
@@ -644,7 +744,7 @@ static VertexF to_vf(const VertexDev& V, kb_ctx* ctx, bool& ok) {
 // Workspace layout of one mixed-precision bubble of channel r (byte offsets into the
 // context's workspace) and the bytes it needs.
 struct MixedLayout {
-    size_t off_tab, off_N, off_M, off_S, off_P3, off_K1, off_T, rows, K, per_w, tc_scratch, need;
+    size_t off_tab, off_N, off_M, off_S, off_P3, off_K1, off_NT, off_T, rows, K, per_w, tc_scratch, need;
     int chunk;
 };
 
@@ -663,7 +763,9 @@ static MixedLayout mixed_layout(const kb_ctx* ctx, int r, unsigned mask) {
     size_t szP3 = (size_t)g.n3w * g.nq * 16 * sizeof(float2);
     L.off_K1 = (L.off_P3 + szP3 + 255) / 256 * 256;
     size_t szK1 = (size_t)g.n1 * K1_SLICES * 16 * sizeof(double2);
-    L.off_T = (L.off_K1 + szK1 + 1023) / 1024 * 1024;
+    L.off_NT = (L.off_K1 + szK1 + 255) / 256 * 256;
+    size_t szNT = (size_t)2 * g.n2w * ns * g.n3v * 16 * sizeof(double2);
+    L.off_T = (L.off_NT + szNT + 1023) / 1024 * 1024;
     L.rows = (size_t)4 * g.n3v;
     L.K = (size_t)4 * ns * g.nq;
     L.per_w = 2 * 4 * L.rows * L.K * sizeof(float) + L.rows * L.rows * sizeof(double2) + 1024;
@@ -703,6 +805,7 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
     float2* Nt = reinterpret_cast<float2*>(ws + off_N);
     float2* Mt = reinterpret_cast<float2*>(ws + off_M);
     double2* Ss = reinterpret_cast<double2*>(ws + off_S);
+    double2* Ntl = reinterpret_cast<double2*>(ws + Lo.off_NT);
     float2* P3 = reinterpret_cast<float2*>(ws + off_P3);
     DfGrids G;
     G.n1 = tab; G.n2w = G.n1 + g.n1; G.n2v = G.n2w + g.n2w; G.n3w = G.n2v + g.n2v; G.n3v = G.n3w + g.n3w;
@@ -737,16 +840,25 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
             KB_LAUNCH(ctx, st, "k_mx_sumj");
             k_mx_sumj<<<dim3(g.n2w, ns, 2), 128, 0, st>>>(Nt, Mt, g.nq, ns, Ss);
         }
+        {
+            // left (N) table for K2; the right (M) table only when K2' is gathered
+            KB_LAUNCH(ctx, st, "k_mx_ntilde");
+            const int nt = (!sym && ((mask >> KB_K2P) & 1)) ? 2 : 1;
+            const int t0 = ((mask >> KB_K2) & 1) ? 0 : 1;
+            k_mx_ntilde<<<dim3((g.n3v * 16 + 127) / 128, g.n2w, ns * (t0 == 1 ? 1 : nt)), 128, 0, st>>>(
+                Nt, Mt, G, g.nq, ns, t0, Ntl);
+        }
         if ((mask >> KB_K2) & 1) {
             KB_LAUNCH(ctx, st, "k_mx_k2");
             int w_off = (sym && r != KB_CH_P) ? g.n2w / 2 : 0, v_off = (sym && r == KB_CH_P) ? g.n2v / 2 : 0;
             k_mx_k2<false, r><<<dim3(g.n2v - v_off, g.n2w - w_off), 128, 0, st>>>(
-                VL, G, J, Nt, Ss, const_cast<void*>(VO.cls[r][KB_K2]), VO.dt[r][KB_K2], w_off, v_off);
+                VL, G, J, Nt, Ss, Ntl, const_cast<void*>(VO.cls[r][KB_K2]), VO.dt[r][KB_K2], w_off, v_off);
         }
         if (!sym && ((mask >> KB_K2P) & 1)) {
             KB_LAUNCH(ctx, st, "k_mx_k2p");
-            k_mx_k2<true, r><<<dim3(g.n2v, g.n2w), 128, 0, st>>>(VR, G, J, Mt, Ss, const_cast<void*>(VO.cls[r][KB_K2P]),
-                                                              VO.dt[r][KB_K2P], 0, 0);
+            k_mx_k2<true, r><<<dim3(g.n2v, g.n2w), 128, 0, st>>>(VR, G, J, Mt, Ss, Ntl,
+                                                              const_cast<void*>(VO.cls[r][KB_K2P]), VO.dt[r][KB_K2P],
+                                                              0, 0);
         }
     }
     if ((mask >> KB_K3) & 1) {
