@@ -9,7 +9,7 @@ A delivered point is one (w, v, v') x one of the 16 Keldysh components of one cl
 one channel: 7,365,792 per step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64] [--impl reference]
-                 [--channels apt] [--no-e2e] [--no-cpu-baseline]
+                 [--channels apt] [--no-e2e] [--no-cpu-baseline] [--workload step|points32|vjp]
 
 --channels and --no-e2e narrow a run to one channel's kernels for profiling captures; the
 default line is the three-channel step.
@@ -274,6 +274,118 @@ def contraction_flops(prec):
     return out
 
 
+# --------------------------------------------------------------------------------------
+# Secondary workloads (not the default line): the batching and the adjoint paths
+# --------------------------------------------------------------------------------------
+def _timed(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / steps
+
+
+def run_points32(args):
+    """32 independent parameter points of uneven grid sizes (U/Delta ~ U[0.5, 3], T ~ log-
+    uniform in [0.005, 0.5], K3 n^3 with n in {21, 31, 41, 51, 61}, K2 (2n-1)^2, K1 5n-4,
+    Nq 4001), the one-loop bubble of all three channels of each, mixed precision: one step
+    graph with one branch per point, against the same bubbles launched eagerly."""
+    import torch
+    import seeded as S
+    from paper_2405_20996_gb300.engine import Engine, StepGraph
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(2024)
+    pts, points, sizes = [], 0, []
+    for i in range(32):
+        n = int(rng.choice([21, 31, 41, 51, 61]))
+        Ui = float(rng.uniform(0.5, 3.0))
+        Ti = float(10 ** rng.uniform(np.log10(0.005), np.log10(0.5)))
+        g = dict(n1=5 * n - 4, n2w=2 * n - 1, n2v=2 * n - 1, n3w=n, n3v=n)
+        e = Engine(g, NQ, device=0)
+        e.set_model(DELTA, Ti)
+        e.set_workspace_limit(2 << 30)
+        e.set_vertex(0, U=Ui, has_R=True, channels=S.seeded_vertex(g, Ui, seed=3000 + i), dtype=torch.complex64,
+                     symmetric=True)
+        e.alloc_out(1, dtype=torch.complex64)
+        pts.append(e)
+        sizes.append(n)
+        points += 3 * sum(class_points(g).values())
+    stream = torch.cuda.current_stream(dev)
+    graph = StepGraph([e.desc(r, 0, 0, 1, precision="mixed") for e in pts for r in range(3)], device=dev)
+    n0 = sum(e.launches() for e in pts)
+    ms_graph = _timed(lambda: graph.launch(stream), args.steps, args.warmup, stream)
+    launches = (sum(e.launches() for e in pts) - n0) // (args.steps + args.warmup)
+
+    def eager():
+        for e in pts:
+            for r in range(3):
+                e.bubble(r, 0, 0, 1, precision="mixed", stream=stream)
+
+    ms_eager = _timed(eager, args.steps, args.warmup, stream)
+    line = {"metric": METRIC, "value": points / (ms_graph / 1e3), "unit": "points/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "32 parameter points, K3 n^3 n in {21..61}, K2 (2n-1)^2, K1 5n-4, Nq 4001, a,p,t",
+                       "n3": sizes, "points_per_step": points, "launch": "one CUDA graph, one branch per point"},
+            "eager": {"value": points / (ms_eager / 1e3), "ms_per_step": ms_eager}, "gpu_launches": launches}
+    print(json.dumps(line))
+    return 0
+
+
+def run_vjp(args):
+    """Adjoint of the one-loop bubble of all three channels (K1 201, K2 81^2, K3 41^3,
+    Nq 4001, U/Delta = 2, T = 0.05): kb_bubble_vjp in FP64 with respect to the vertex (both
+    sides, one gradient slot) and G^R, beside the FP64 forward bubble.  Points: output
+    points whose gradient is pulled back per second."""
+    import torch
+    import seeded as S
+    from paper_2405_20996_gb300 import kb
+    from paper_2405_20996_gb300.engine import Engine
+    g = dict(n1=201, n2w=81, n2v=81, n3w=41, n3v=41)
+    dev = torch.device("cuda", 0)
+    e = Engine(g, NQ, device=0)
+    e.set_model(DELTA, T)
+    e.set_vertex(0, U=U, has_R=True, channels=S.seeded_vertex(g, U, seed=77))
+    e.alloc_out(1)
+    rng = np.random.default_rng(5)
+    for t in e.tensors[1].values():
+        t.copy_(torch.from_numpy(rng.standard_normal(t.shape) + 1j * rng.standard_normal(t.shape)))
+    e.alloc_out(2)                                  # gradient slot (complex128, zeroed)
+    e.alloc_out(3)                                  # forward output slot
+    tabs = e.gr_tables()
+    stream = torch.cuda.current_stream(dev)
+    points = 3 * sum(class_points(g).values())
+
+    def vjp():
+        for r in range(3):
+            e.bubble_vjp(r, 0, 0, 1, grad_left=2, grad_right=2, grad_gr=tabs, stream=stream)
+
+    def fwd():
+        for r in range(3):
+            e.bubble(r, 0, 0, 3, precision="fp64", stream=stream)
+
+    ms_vjp = _timed(vjp, args.steps, min(args.warmup, 1), stream)
+    ms_fwd = _timed(fwd, args.steps, min(args.warmup, 1), stream)
+    kb.kb_check_device(e.ctx)
+    line = {"metric": "adjoint bubble points/s (w.v.v'.Keldysh, vertex + G^R gradients)",
+            "value": points / (ms_vjp / 1e3), "unit": "points/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": min(args.warmup, 1), "ms_per_step": ms_vjp, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "VJP of the one-loop bubble a,p,t; K1 201, K2 81x81, K3 41^3, Nq 4001",
+                       "points_per_step": points},
+            "forward_fp64": {"value": points / (ms_fwd / 1e3), "ms_per_step": ms_fwd}}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -287,7 +399,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling captures)")
     ap.add_argument("--no-graph", action="store_true", help="eager launches instead of one step graph")
     ap.add_argument("--ws-gb", type=int, default=8, help="device workspace limit per context (GiB)")
+    ap.add_argument("--workload", default="step", choices=["step", "points32", "vjp"],
+                    help="step: the default three-channel line; points32 / vjp: the batching and adjoint paths")
     args = ap.parse_args()
+    if args.workload != "step" and args.impl == "ours":
+        return run_points32(args) if args.workload == "points32" else run_vjp(args)
     chans = tuple(sorted({"apt".index(c) for c in args.channels}))
     if not chans:
         ap.error("--channels needs at least one of a, p, t")
