@@ -179,11 +179,18 @@ __global__ void __launch_bounds__(256) k_zgemm_gen(const double2* __restrict__ A
 // One thread per (w, v, s, j) record of the left tile: bar(L) -> gradient slot.
 __global__ void k_vjp_left(VertexDev V, VertexDev Gd, Grids G, ClassJob J, const double* __restrict__ xq,
                            const double2* __restrict__ gL) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    int s = blockIdx.y % J.ns;
-    int vi = blockIdx.y / J.ns;
-    int wl = blockIdx.z;
-    if (j >= J.nq || vi >= J.nL) return;
+    // consecutive threads take different (v, s, w) of the same node: records that share
+    // interpolation corners (adjacent nodes) sit in different warps, so the atomic adds of
+    // one warp rarely collide on one address
+    const size_t inner = (size_t)J.nw_chunk * J.ns * J.nL;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= inner * J.nq) return;
+    const int j = (int)(idx / inner);
+    size_t rest = idx % inner;
+    const int vi = (int)(rest % J.nL);
+    rest /= J.nL;
+    const int s = (int)(rest % J.ns);
+    const int wl = (int)(rest / J.ns);
     const ChannelMaps& M = c_maps[J.r];
     double w = grid_freq(J.w0 + wl, J.nw_grid, G.A);
     double vext = J.L_nu ? grid_freq(vi, J.nvL_grid, G.A) : 0.0;
@@ -201,14 +208,31 @@ __global__ void k_vjp_left(VertexDev V, VertexDev Gd, Grids G, ClassJob J, const
 
 // One thread per (w, v', s, j) record of the right tile: bar(R') -> bar(R) -> gradient slot,
 // and (gPi != nullptr) bar(Pi)[w][j] += sum_C conj(R[D][C]) bar(R')[C][B].
+// Launched twice when both are wanted: for the vertex gradient (want_vertex, gPi null) with
+// consecutive threads on different (v, s, w) of one node, like k_vjp_left; for the Pi
+// gradient (gPi) with consecutive threads on consecutive nodes, whose Pi entries differ.
 __global__ void k_vjp_right(VertexDev V, VertexDev Gd, bool want_vertex, Grids G, ClassJob J,
                             const double* __restrict__ xq, const double2* __restrict__ Pi,
                             const double2* __restrict__ gRp, double2* __restrict__ gPi) {
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    int s = blockIdx.y % J.ns;
-    int vi = blockIdx.y / J.ns;
-    int wl = blockIdx.z;
-    if (j >= J.nq || vi >= J.nR) return;
+    const size_t inner = (size_t)J.nw_chunk * J.ns * J.nR;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= inner * J.nq) return;
+    int j, vi, s, wl;
+    if (gPi) {
+        j = (int)(idx % J.nq);
+        size_t rest = idx / J.nq;
+        vi = (int)(rest % J.nR);
+        rest /= J.nR;
+        s = (int)(rest % J.ns);
+        wl = (int)(rest / J.ns);
+    } else {
+        j = (int)(idx / inner);
+        size_t rest = idx % inner;
+        vi = (int)(rest % J.nR);
+        rest /= J.nR;
+        s = (int)(rest % J.ns);
+        wl = (int)(rest / J.ns);
+    }
     const ChannelMaps& M = c_maps[J.r];
     double w = grid_freq(J.w0 + wl, J.nw_grid, G.A);
     double vext = J.R_nu ? grid_freq(vi, J.nvR_grid, G.A) : 0.0;
@@ -370,8 +394,8 @@ kb_status kb_bubble_vjp_fp64(kb_ctx* ctx, int r, int sl, int sr, int sgo, int pi
                 }
                 {
                     KB_LAUNCH(ctx, st, "k_vjp_left");
-                    k_vjp_left<<<dim3((g.nq + 127) / 128, nL * ns, J.nw_chunk), 128, 0, st>>>(ctx->slots[sl], GL, g, J,
-                                                                                            ctx->d_xq, gL);
+                    size_t tot = (size_t)J.nw_chunk * ns * nL * g.nq;
+                    k_vjp_left<<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(ctx->slots[sl], GL, g, J, ctx->d_xq, gL);
                 }
             }
             if (want_r || want_gr) {
@@ -386,8 +410,13 @@ kb_status kb_bubble_vjp_fp64(kb_ctx* ctx, int r, int sl, int sr, int sgo, int pi
                     KB_CUDA_TRY(ctx, cudaMemsetAsync(gPi, 0, (size_t)J.nw_chunk * g.nq * 16 * sizeof(double2), st));
                 {
                     KB_LAUNCH(ctx, st, "k_vjp_right");
-                    k_vjp_right<<<dim3((g.nq + 127) / 128, nR * ns, J.nw_chunk), 128, 0, st>>>(
-                        ctx->slots[sr], GR, want_r, g, J, ctx->d_xq, Pi, gRp, gPi);
+                    size_t tot = (size_t)J.nw_chunk * ns * nR * g.nq;
+                    if (want_r)
+                        k_vjp_right<<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(ctx->slots[sr], GR, true, g, J,
+                                                                                 ctx->d_xq, Pi, gRp, nullptr);
+                    if (want_gr)
+                        k_vjp_right<<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(ctx->slots[sr], GR, false, g, J,
+                                                                                 ctx->d_xq, Pi, gRp, gPi);
                 }
                 if (want_gr) {
                     KB_LAUNCH(ctx, st, "k_vjp_gr");
