@@ -3,13 +3,16 @@
 //   Re C = Ar Br - Ai Bi,  Im C = Ar Bi + Ai Br,
 // every real product X Y taken as Xhi Yhi + Xhi Ylo + Xlo Yhi (the lo*lo term, ~2^-22
 // relative, is dropped).  The minus sign of Ai Bi is the negate-A bit of the instruction
-// descriptor.  Accumulation in FP32 in tensor memory (two 128 x N accumulators, Re and
-// Im) restarted every SEG K chunks; finished segments are added into double-float sums in
-// registers, the K dimension is split over CTAs and the split partials are added in FP64.
+// descriptor.  A CTA computes either the real or the imaginary part of a 128 x 128 output
+// tile (6 MMAs of N = 128 per k-step): the register file holds the compensated running
+// sums of 128 x 128 real values, and N = 128 halves the shared-memory operand reads per MMA
+// flop against complex 128 x 64 tiles.  Accumulation in FP32 in tensor memory restarted
+// every SEG K chunks; finished segments are added into compensated FP32 sums in registers,
+// the K dimension is split over CTAs and the split partials are added in FP64.
 //
 // Operands (written by k_mx_tile3): A = [batch][plane][M][K], B = [batch][plane][N][K],
 // planes (re hi, re lo, im hi, im lo), K-contiguous FP32.  One CTA = one (batch, 128-row
-// M tile, 64-column N tile, K range).  Warp roles: warp 0 issues the TMA loads, warp 1
+// M tile, 128-column N tile, part Re or Im, K range).  Warp roles: warp 0 issues the TMA loads, warp 1
 // allocates tensor memory and issues the MMAs, warps 2-17 drain the accumulators.  All waits are bounded; a wait that gives up sets a device flag
 // (read by kb_check_device), the CTA drains its copies in flight and frees its tensor
 // memory before returning.
@@ -129,22 +132,27 @@ struct TcJob {
     int M, N, K, batch, mtiles, ntiles, ksplit, chunks_per_split, nchunks;
 };
 
-// Segmented accumulation: tensor memory holds two buffers of (Re, Im) 128 x NT FP32
-// accumulators; the MMA warp restarts a buffer every SEG K chunks and the epilogue warps
-// add each finished segment into double-float (hi + lo) running sums held in registers,
-// so no FP32 accumulator ever sums more than SEG * KC * 6 / 8 products.
+// Segmented accumulation: tensor memory holds two buffers of one 128 x NT FP32
+// accumulator (the CTA's part); the MMA warp restarts a buffer every SEG K chunks and the
+// epilogue warps add each finished segment into compensated (Kahan) FP32 running sums held
+// in registers, so no plain FP32 accumulator ever sums more than SEG * KC * 6 / 8 products.
 constexpr int SEG = 2;
-constexpr int NTT = 64;                       // N columns per CTA
-constexpr int EPI_WARPS = 16;                 // 4 per TMEM lane quarter, 16 columns each
+constexpr int NTT = 128;                      // N columns per CTA
+constexpr int EPI_WARPS = 16;                 // 4 per TMEM lane quarter, 32 columns each
 constexpr int NTHREADS_S = 64 + 32 * EPI_WARPS;
-constexpr int STAGES_S = 4;
+constexpr int STAGES_S = 3;
 
-__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
-    float s = __fadd_rn(hi, x);
-    float bb = __fsub_rn(s, hi);
-    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
-    hi = s;
-    lo = __fadd_rn(lo, e);
+// Compensated (Kahan) summation of two columns at once with packed FP32 operations:
+// s is the running sum, n the negated compensation (the rounding error still to be added).
+// Each step: y = x + n, t = s + y, n = y - (t - s), s = t; the subtractions are FMAs with
+// -1, so every operation is one correctly rounded FP32 result.  The sum is s + n.
+__device__ __forceinline__ void kahan2(float2& s, float2& n, float2 x) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 y = __fadd2_rn(x, n);
+    const float2 t = __fadd2_rn(s, y);
+    const float2 d = __ffma2_rn(m1, s, t);
+    n = __ffma2_rn(m1, d, y);
+    s = t;
 }
 
 // partial sums P[ks][b][M][N] double2
@@ -153,9 +161,9 @@ __global__ void __maxnreg__(96)
             double2* __restrict__ P) {
     constexpr int NT = NTT;
     constexpr uint32_t A_PLANE = MT * KC * 4;      // 8 KB
-    constexpr uint32_t B_PLANE = NT * KC * 4;      // 4 KB
+    constexpr uint32_t B_PLANE = NT * KC * 4;      // 8 KB
     constexpr uint32_t STAGE = 4 * A_PLANE + 4 * B_PLANE;
-    constexpr uint32_t TMEM_COLS = 256;            // 2 buffers x (Re, Im) x 64
+    constexpr uint32_t TMEM_COLS = 256;            // 2 buffers x 128 columns
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES_S * STAGE);
@@ -168,6 +176,8 @@ __global__ void __maxnreg__(96)
     int unit = blockIdx.x;
     int ks = unit % J.ksplit;
     int rest = unit / J.ksplit;
+    const int part = rest & 1;                     // 0: real part, 1: imaginary part
+    rest >>= 1;
     int nt = rest % J.ntiles;
     rest /= J.ntiles;
     int mt = rest % J.mtiles;
@@ -230,7 +240,7 @@ __global__ void __maxnreg__(96)
                 }
                 if (!mbar_wait(&full[s], ph)) { atomicOr(&g_tc_status, 2); s_fail = 1; break; }
                 fence_after();
-                uint32_t dRe = tbase + buf * 2 * NT, dIm = dRe + NT;
+                const uint32_t dacc = tbase + buf * NT;
                 uint32_t sa = smem_u32(smem + s * STAGE);
                 uint32_t sb = sa + 4 * A_PLANE;
 #pragma unroll
@@ -241,30 +251,33 @@ __global__ void __maxnreg__(96)
                     uint64_t brh = sdesc_sw64(sb + 0 * B_PLANE + off), brl = sdesc_sw64(sb + 1 * B_PLANE + off);
                     uint64_t bih = sdesc_sw64(sb + 2 * B_PLANE + off), bil = sdesc_sw64(sb + 3 * B_PLANE + off);
                     uint32_t first = (seg_start && kk == 0) ? 0u : 1u;
-                    mma_tf32(dRe, arh, brh, id_pos, first);
-                    mma_tf32(dRe, arh, brl, id_pos, 1);
-                    mma_tf32(dRe, arl, brh, id_pos, 1);
-                    mma_tf32(dRe, aih, bih, id_neg, 1);
-                    mma_tf32(dRe, aih, bil, id_neg, 1);
-                    mma_tf32(dRe, ail, bih, id_neg, 1);
-                    mma_tf32(dIm, arh, bih, id_pos, first);
-                    mma_tf32(dIm, arh, bil, id_pos, 1);
-                    mma_tf32(dIm, arl, bih, id_pos, 1);
-                    mma_tf32(dIm, aih, brh, id_pos, 1);
-                    mma_tf32(dIm, aih, brl, id_pos, 1);
-                    mma_tf32(dIm, ail, brh, id_pos, 1);
+                    if (part == 0) {          // Re = Ar Br - Ai Bi
+                        mma_tf32(dacc, arh, brh, id_pos, first);
+                        mma_tf32(dacc, arh, brl, id_pos, 1);
+                        mma_tf32(dacc, arl, brh, id_pos, 1);
+                        mma_tf32(dacc, aih, bih, id_neg, 1);
+                        mma_tf32(dacc, aih, bil, id_neg, 1);
+                        mma_tf32(dacc, ail, bih, id_neg, 1);
+                    } else {                  // Im = Ar Bi + Ai Br
+                        mma_tf32(dacc, arh, bih, id_pos, first);
+                        mma_tf32(dacc, arh, bil, id_pos, 1);
+                        mma_tf32(dacc, arl, bih, id_pos, 1);
+                        mma_tf32(dacc, aih, brh, id_pos, 1);
+                        mma_tf32(dacc, aih, brl, id_pos, 1);
+                        mma_tf32(dacc, ail, brh, id_pos, 1);
+                    }
                 }
                 mma_commit(&empty[s]);
                 if ((i % SEG) == SEG - 1 || i == nck - 1) mma_commit(&segfull[buf]);
             }
         }
     } else {
-        // epilogue warps 2 .. 2+EPI_WARPS-1: lane quarter q, 16-column group cg
+        // epilogue warps 2 .. 2+EPI_WARPS-1: lane quarter q, 32-column group cg
         int e = warp - 2;
         int q = warp & 3, cg = e >> 2;
-        float hre[16], lre[16], him[16], lim[16];
+        float2 sm[16], ng[16];       // columns (2i, 2i+1): running sums and negated compensations
 #pragma unroll
-        for (int i = 0; i < 16; ++i) { hre[i] = 0.f; lre[i] = 0.f; him[i] = 0.f; lim[i] = 0.f; }
+        for (int i = 0; i < 16; ++i) { sm[i] = make_float2(0.f, 0.f); ng[i] = make_float2(0.f, 0.f); }
         bool ok = true;
         for (int g = 0; g < nseg; ++g) {
             int buf = g & 1;
@@ -272,32 +285,28 @@ __global__ void __maxnreg__(96)
                 atomicOr(&g_tc_status, 4); ok = false; break;
             }
             fence_after();
-            uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * NT + cg * 16);
-            // one 16-column load (and one wait) per part: the load latency is paid twice per
-            // segment, not once per 8 columns
-            {
-                float v[16];
-                tmem_ld16(ta, v);
+            uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * NT + cg * 32);
+            // two 16-column loads, one wait each
 #pragma unroll
-                for (int c = 0; c < 16; ++c) two_sum_acc(hre[c], lre[c], v[c]);
-            }
-            {
+            for (int h = 0; h < 2; ++h) {
                 float v[16];
-                tmem_ld16(ta + NT, v);
+                tmem_ld16(ta + 16 * h, v);
 #pragma unroll
-                for (int c = 0; c < 16; ++c) two_sum_acc(him[c], lim[c], v[c]);
+                for (int c = 0; c < 8; ++c) kahan2(sm[8 * h + c], ng[8 * h + c], make_float2(v[2 * c], v[2 * c + 1]));
             }
             fence_before();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&segempty[buf])) : "memory");
         }
         int row = mt * MT + q * 32 + lane;
         if (ok && row < J.M) {
-            double2* out = P + (((size_t)ks * J.batch + b) * J.M + row) * J.N;
-            int col0 = nt * NT + cg * 16;
+            // this CTA's part (.x real / .y imaginary) of the FP64 partial
+            double* out = reinterpret_cast<double*>(P + (((size_t)ks * J.batch + b) * J.M + row) * J.N) + part;
+            int col0 = nt * NT + cg * 32;
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
-                if (col0 + i < J.N)
-                    out[col0 + i] = make_double2((double)hre[i] + (double)lre[i], (double)him[i] + (double)lim[i]);
+            for (int i = 0; i < 16; ++i) {
+                if (col0 + 2 * i < J.N) out[2 * (col0 + 2 * i)] = (double)sm[i].x + (double)ng[i].x;
+                if (col0 + 2 * i + 1 < J.N) out[2 * (col0 + 2 * i + 1)] = (double)sm[i].y + (double)ng[i].y;
+            }
         }
     }
     fence_before();
@@ -379,7 +388,7 @@ static bool launch(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, i
     J.nchunks = (K + KC - 1) / KC;
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    int base = batch * J.mtiles * J.ntiles;
+    int base = batch * J.mtiles * J.ntiles * 2;     // x 2: real and imaginary part
     int best = 1;
     double best_eff = 0;
     for (int s = 1; s <= 64; ++s) {
