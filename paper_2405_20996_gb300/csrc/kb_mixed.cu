@@ -280,6 +280,15 @@ __global__ void k_mx_ntilde(const float2* __restrict__ Nt, const float2* __restr
     out[((((size_t)t * G.N2w + wi) * ns + s) * G.N3v + m) * 16 + o] = make_double2(ax, ay);
 }
 
+// Loads of the propagator-vertex tables in the contraction: each element is used by one
+// instruction (four lanes at once), so it is read without allocating in L1, which keeps L1
+// for the vertex records the gathers reuse.
+__device__ __forceinline__ float2 ld_stream(const float2* p) {
+    float2 v;
+    asm("ld.global.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+
 // K2 (RIGHT = false): out(w, v)[A][C] = sum_j sum_s sum_B L_s(w, v, v''_j)[A][B] N_s(w, j)[B][C]
 //   with L the v-dependent part of Gamma1 without its own K2 class, plus
 //   K2own_s(w, v)[A][B] * SN_s(w)[B][C]  (the own K2 class does not depend on v'').
@@ -338,24 +347,24 @@ __global__ void __launch_bounds__(128, 4) k_mx_k2(VertexF V, DfGrids G, MixedJob
             if (NS == 1) {
                 if (!RIGHT) {
 #pragma unroll
-                    for (int B = 0; B < 4; ++B) cmac2(acc, rec[0][rr][cmap<R>(A, B)], __ldg(t0 + 4 * B + C));
+                    for (int B = 0; B < 4; ++B) cmac2(acc, rec[0][rr][cmap<R>(A, B)], ld_stream(t0 + 4 * B + C));
                 } else {
 #pragma unroll
-                    for (int D = 0; D < 4; ++D) cmac2(acc, __ldg(t0 + 4 * A + D), rec[0][rr][cmap<R>(D, C)]);
+                    for (int D = 0; D < 4; ++D) cmac2(acc, ld_stream(t0 + 4 * A + D), rec[0][rr][cmap<R>(D, C)]);
                 }
             } else {
                 const float2* t1 = T1 + (size_t)(j0 + rr) * 16;
                 if (!RIGHT) {
 #pragma unroll
                     for (int B = 0; B < 4; ++B) {
-                        cmac2(acc, rec[NS - 1][rr][cmap<R>(A, B)], __ldg(t0 + 4 * B + C));
-                        cmac2(acc, rec[0][rr][cmap<R>(A, B)], __ldg(t1 + 4 * B + C));
+                        cmac2(acc, rec[NS - 1][rr][cmap<R>(A, B)], ld_stream(t0 + 4 * B + C));
+                        cmac2(acc, rec[0][rr][cmap<R>(A, B)], ld_stream(t1 + 4 * B + C));
                     }
                 } else {
 #pragma unroll
                     for (int D = 0; D < 4; ++D) {
-                        cmac2(acc, __ldg(t0 + 4 * A + D), rec[0][rr][cmap<R>(D, C)]);
-                        cmac2(acc, __ldg(t1 + 4 * A + D), rec[NS - 1][rr][cmap<R>(D, C)]);
+                        cmac2(acc, ld_stream(t0 + 4 * A + D), rec[0][rr][cmap<R>(D, C)]);
+                        cmac2(acc, ld_stream(t1 + 4 * A + D), rec[NS - 1][rr][cmap<R>(D, C)]);
                     }
                 }
             }
