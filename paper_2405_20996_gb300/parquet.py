@@ -1,0 +1,195 @@
+"""Parquet approximation solved with the library's bubble (Sec. III.B).
+
+The parquet approximation takes the totally irreducible vertex as the bare one, R = Γ0
+(strength U; Sec. II.B).  With the self-energy held fixed (the context's Σ table, or Σ = 0),
+the reducible vertices of the three channels solve the Bethe–Salpeter equations
+
+    γ_r = B_r(I_r, Γ),   I_r = Γ − γ_r,   Γ = R + γ_a + γ_p + γ_t,   r ∈ {a, p, t},
+
+where B_r carries the channel prefactor c_r (1, 1/2, −1) and γ_r is stored as its
+asymptotic classes K1, K2, K2', K3 (Sec. II.D.1).  I_r is the vertex slot of Γ with
+channel r left out of the slot's channel mask; the library still reads channel r's data
+as the crossing partner of the up-up component, as the vertex requires.
+
+Two solvers; every bubble goes through the library's plain FP64 path:
+
+- the damped fixed point γ ← (1 − m) γ + m B(γ) with mixing m, the scheme the paper
+  describes for its parquet solver, stopped on the relative maximum-norm change;
+- Newton–Krylov on F(γ) = γ − B(γ): each Newton step solves J δ = −F by restarted
+  GMRES.  B_r is bilinear in its two vertices, so the Jacobian product is
+      J v = v − Σ_r [B_r(V_I_r, Γ) + B_r(I_r, V)],   V = Σ_r v_r (no bare part),
+  two bubbles per channel; J^H comes from kb_bubble_vjp (`adjoint`).
+
+The state is one flat complex128 device vector holding the 12 class arrays; the vertex
+slots are views of it, so no data moves between a solver update and the next bubble.  The
+solvers' vector algebra (updates, norms, inner products) are PyTorch device operations;
+the GMRES Hessenberg least-squares problem (at most a few dozen unknowns) is solved on the
+host.
+"""
+
+import numpy as np
+import torch
+
+from . import kb
+from .engine import CLASS_NAMES, Engine
+
+# vertex slots of the engine context
+S_GAMMA = 0                 # Γ = R + γ_a + γ_p + γ_t
+S_I = (1, 2, 3)             # I_r = Γ − γ_r
+S_DELTA = 4                 # V = v_a + v_p + v_t (a tangent or adjoint direction, no R)
+S_DELTA_I = (5, 6, 7)       # V − v_r
+S_OUT = 8                   # bubble outputs, all channels
+S_GRAD = 9                  # adjoint accumulation, all channels
+
+
+class ParquetPA:
+    """Parquet-approximation solver of one parameter point (grids, Nq, U, Δ, T)."""
+
+    def __init__(self, grids, nq, U, Delta, T, A=5.0, eps=0.0, device=0):
+        self.e = Engine(grids, nq, A=A, device=device)
+        self.e.set_model(Delta, T, eps)
+        self.U = float(U)
+        self.dev = self.e.device
+        sh = self.e.class_shapes()
+        self.layout, off = [], 0
+        for ch in range(3):
+            for k, name in enumerate(CLASS_NAMES):
+                n = int(np.prod(sh[name]))
+                self.layout.append((ch, k, sh[name], off, n))
+                off += n
+        self.n = off
+        z = lambda: torch.zeros(self.n, dtype=torch.complex128, device=self.dev)
+        self.gamma, self.delta, self.out, self.grad = z(), z(), z(), z()
+        self._attach(S_GAMMA, self.gamma, True, 7)
+        self._attach(S_DELTA, self.delta, False, 7)
+        for r in range(3):
+            self._attach(S_I[r], self.gamma, True, 7 & ~(1 << r))
+            self._attach(S_DELTA_I[r], self.delta, False, 7 & ~(1 << r))
+        self._attach(S_OUT, self.out, False, 7)
+        self._attach(S_GRAD, self.grad, False, 7)
+        self.bubbles = 0
+
+    def close(self):
+        self.e.close()
+
+    def _attach(self, slot, buf, has_R, mask):
+        kb.kb_set_vertex(self.e.ctx, slot, has_R, self.U)
+        kb.kb_set_vertex_channels(self.e.ctx, slot, mask)
+        kb.kb_set_vertex_symmetric(self.e.ctx, slot, False)
+        self.e.tensors[slot] = {}
+        for ch, k, shape, off, n in self.layout:
+            self.e.attach(slot, ch, k, buf[off:off + n].view(shape))
+
+    def classes(self, buf, ch):
+        """{"K1", "K2", "K2p", "K3"} views of channel ch of a flat state vector."""
+        return {CLASS_NAMES[k]: buf[off:off + n].view(shape) for c, k, shape, off, n in self.layout if c == ch}
+
+    def channels(self, buf):
+        """{channel: (K1, K2, K2p, K3)} of a flat state vector (views)."""
+        return {ch: tuple(self.classes(buf, ch)[k] for k in CLASS_NAMES) for ch in range(3)}
+
+    # ---- the map and its derivatives ----------------------------------------------------
+    def bse(self, gamma):
+        """Right-hand sides B_r(I_r, Γ) of the three Bethe–Salpeter equations at γ."""
+        self.gamma.copy_(gamma)
+        for r in range(3):
+            self.e.bubble(r, S_I[r], S_GAMMA, S_OUT, precision="fp64")
+        self.bubbles += 3
+        return self.out.clone()
+
+    def residual(self, gamma):
+        return gamma - self.bse(gamma)
+
+    def jvp(self, gamma, v):
+        """J v at γ for F(γ) = γ − B(γ)."""
+        self.gamma.copy_(gamma)
+        self.delta.copy_(v)
+        for r in range(3):
+            self.e.bubble(r, S_DELTA_I[r], S_GAMMA, S_OUT, precision="fp64")
+            self.e.bubble(r, S_I[r], S_DELTA, S_OUT, beta=1.0, precision="fp64")
+        self.bubbles += 6
+        return v - self.out
+
+    def adjoint(self, gamma, u):
+        """J^H u at γ: u − Σ_r (dB_r/dγ)^H u_r through the adjoint kernels (complex-linear
+        map, so J^H is the conjugate transpose; gradients in PyTorch's convention)."""
+        self.gamma.copy_(gamma)
+        self.out.copy_(u)
+        self.grad.zero_()
+        for r in range(3):
+            self.e.bubble_vjp(r, S_I[r], S_GAMMA, S_OUT, grad_left=S_GRAD, grad_right=S_GRAD)
+        return u - self.grad
+
+    @staticmethod
+    def rel(diff, ref):
+        return float(diff.abs().max()) / max(float(ref.abs().max()), 1e-300)
+
+    # ---- solvers ------------------------------------------------------------------------
+    def fixed_point(self, mix=0.5, tol=1e-10, maxit=500, gamma0=None):
+        """Damped iteration; returns (γ, history of relative residuals)."""
+        g = torch.zeros_like(self.gamma) if gamma0 is None else gamma0.clone()
+        hist = []
+        for _ in range(maxit):
+            b = self.bse(g)
+            hist.append(self.rel(g - b, b))
+            if hist[-1] <= tol:
+                return b, hist
+            g = (1.0 - mix) * g + mix * b
+        return g, hist
+
+    def gmres(self, gamma, rhs, rtol, m=30, maxit=300):
+        """Restarted GMRES(m) for J x = rhs at γ (Arnoldi with modified Gram–Schmidt; the
+        small least-squares problem min ||β e1 − H y|| solved on the host each step).
+        Returns (x, number of Jacobian products, relative residual)."""
+        x = torch.zeros_like(rhs)
+        bnorm = float(torch.linalg.vector_norm(rhs))
+        if bnorm == 0.0:
+            return x, 0, 0.0
+        its, res = 0, 1.0
+        r = rhs.clone()
+        while its < maxit:
+            beta = float(torch.linalg.vector_norm(r))
+            res = beta / bnorm
+            if res <= rtol:
+                break
+            V = [r / beta]
+            H = np.zeros((m + 1, m), dtype=np.complex128)
+            y = None
+            for k in range(m):
+                w = self.jvp(gamma, V[k])
+                its += 1
+                for i in range(k + 1):
+                    h = torch.vdot(V[i], w)
+                    H[i, k] = complex(h)
+                    w = w - h * V[i]
+                hn = float(torch.linalg.vector_norm(w))
+                H[k + 1, k] = hn
+                e1 = np.zeros(k + 2, dtype=np.complex128)
+                e1[0] = beta
+                y = np.linalg.lstsq(H[:k + 2, :k + 1], e1, rcond=None)[0]
+                res = float(np.linalg.norm(e1 - H[:k + 2, :k + 1] @ y)) / bnorm
+                if res <= rtol or hn == 0.0 or its >= maxit:
+                    break
+                V.append(w / hn)
+            for i in range(len(y)):
+                x = x + complex(y[i]) * V[i]
+            if res <= rtol or its >= maxit:
+                break
+            r = rhs - self.jvp(gamma, x)
+        return x, its, res
+
+    def newton_krylov(self, tol=1e-10, maxit=30, gmres_m=30, gmres_maxit=300, gamma0=None):
+        """Inexact Newton; returns (γ, history of relative residuals, GMRES products per step)."""
+        g = torch.zeros_like(self.gamma) if gamma0 is None else gamma0.clone()
+        hist, lin = [], []
+        for _ in range(maxit):
+            b = self.bse(g)
+            F = g - b
+            hist.append(self.rel(F, b))
+            if hist[-1] <= tol:
+                return b, hist, lin
+            eta = min(1e-2, max(1e-4 * hist[-1], 1e-12))    # forcing term of the inexact Newton step
+            d, its, _ = self.gmres(g, -F, eta, gmres_m, gmres_maxit)
+            lin.append(its)
+            g = g + d
+        return g, hist, lin
