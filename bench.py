@@ -340,6 +340,112 @@ def run_points32(args):
     return 0
 
 
+ML_SIZES = {
+    # K1 201, K2 81^2, K3 41^3, Nq 4001, U/Delta = 2, T = 0.05
+    "multiloop": (dict(n1=201, n2w=81, n2v=81, n3w=41, n3v=41), 4001, 2.0, 0.05),
+    # the largest instance: K1 801, K2 201^2, K3 101^3, Nq 8001, U/Delta = 3, T = 0.01
+    "multiloop-large": (dict(n1=801, n2w=201, n2v=201, n3w=101, n3v=101), 8001, 3.0, 0.01),
+}
+
+
+def run_multiloop(args):
+    """Right-hand side of the six-loop flow for the vertex (Sec. III.C): per channel one
+    one-loop bubble with the single-scale pair, then left / central / right parts up to
+    l = 6 (15 bubbles per channel, 45 per step) plus the slot additions, mixed precision,
+    one step graph with the channels as parallel branches and a join between loop orders;
+    against the same entries launched eagerly on one stream."""
+    import torch
+    import seeded as S
+    from paper_2405_20996_gb300 import kb
+    from paper_2405_20996_gb300.multiloop import MultiloopStep
+    g, nq, Ui, Ti = ML_SIZES[args.workload]
+    dev = torch.device("cuda", 0)
+    ml = MultiloopStep(g, nq, Ui, DELTA, Ti, S.seeded_vertex(g, Ui, seed=4242), n_loops=6, precision="mixed")
+    for e in ml.e.values():
+        e.set_workspace_limit(args.ws_gb << 30)
+    stream = torch.cuda.current_stream(dev)
+    nb = ml.bubbles_per_step()
+    points = nb * sum(class_points(g).values())
+    graph = ml.build()
+
+    def launches():
+        return sum(e.launches() for e in ml.e.values())
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)     # 256 MB > 129 MB L2
+
+    def timed(fn, steps, warmup, clk=None):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        c = ClockSampler(0) if clk else None
+        evs = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / steps, (c.stop() if c else None)
+
+    n0 = launches()
+    ms_graph, clocks = timed(lambda: graph.launch(stream), args.steps, args.warmup, clk=True)
+    per_step = (launches() - n0) // (args.steps + args.warmup)
+    ms_eager, _ = timed(lambda: ml.run_eager(stream), args.steps, min(args.warmup, 1))
+    for e in ml.e.values():
+        kb.kb_profile_enable(e.ctx, True)
+    flush.zero_()
+    ml.run_eager(stream)
+    torch.cuda.synchronize()
+    prof = {}
+    for e in ml.e.values():
+        for k, (t, c) in kb.kb_profile_read(e.ctx).items():
+            p0 = prof.get(k, (0.0, 0))
+            prof[k] = (p0[0] + t, p0[1] + c)
+        kb.kb_profile_enable(e.ctx, False)
+    for e in ml.e.values():
+        kb.kb_check_device(e.ctx)
+    tot = max(sum(v[0] for v in prof.values()), 1e-30)
+    # K3 contraction work of one step (useful flops; 3xTF32 issues three times that): the
+    # one-loop bubble of the symmetric vertex computes the independent half (a, t: w >= 0;
+    # p: rows v >= 0), every other part the full K3 (M = N = 4 n3v, K = 4 ns nq per w)
+    half = lambda n: n - n // 2
+    tc_useful = 0.0
+    for x in ml.descs:
+        if x.op != kb.KB_OP_BUBBLE:
+            continue
+        r, ns = x.channel, (2 if x.channel == 2 else 1)
+        N = 4 * g["n3v"]
+        M, nw = N, g["n3w"]
+        if x.slot_left == x.slot_right:
+            M, nw = (4 * half(g["n3v"]), g["n3w"]) if r == 1 else (N, half(g["n3w"]))
+        tc_useful += 8.0 * M * N * 4 * ns * nq * nw
+    roof = None
+    if "k_tc_k3" in prof:
+        _, bf16, _ = peaks()
+        peak = bf16 * TF32_OVER_BF16
+        issued = 3.0 * tc_useful / (prof["k_tc_k3"][0] / 1e3) / 1e12
+        roof = {"kernel": "k_tc_k3", "bound": "tensor", "achieved": issued, "peak": peak, "unit": "TFLOP/s",
+                "frac": issued / peak, "traffic": None, "share": prof["k_tc_k3"][0] / tot,
+                "note": "issued TF32 flops of the step's K3 contractions / their CUDA-event time in one profiled "
+                        "eager step; peak = measured bf16 x nominal tf32/bf16 ratio"}
+    line = {"metric": METRIC, "value": points / (ms_graph / 1e3), "unit": "points/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "six-loop vertex flow step, a,p,t, K1 %d, K2 %dx%d, K3 %d^3, Nq %d, c64"
+                                   % (g["n1"], g["n2w"], g["n2v"], g["n3w"], nq),
+                       "bubbles_per_step": nb, "points_per_step": points, "U": Ui, "T": Ti,
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "launch": "one CUDA graph per step, channels as branches, a join per loop order"},
+            "eager": {"value": points / (ms_eager / 1e3), "ms_per_step": ms_eager}, "gpu_launches": per_step,
+            "roofline": roof, "clocks": clocks,
+            "kernels_ms": {k: round(v[0], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}}
+    print(json.dumps(line))
+    ml.close()
+    return 0
+
+
 def run_vjp(args):
     """Adjoint of the one-loop bubble of all three channels (K1 201, K2 81^2, K3 41^3,
     Nq 4001, U/Delta = 2, T = 0.05): kb_bubble_vjp in FP64 with respect to the vertex (both
@@ -389,7 +495,7 @@ def run_vjp(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64"])
@@ -399,10 +505,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling captures)")
     ap.add_argument("--no-graph", action="store_true", help="eager launches instead of one step graph")
     ap.add_argument("--ws-gb", type=int, default=8, help="device workspace limit per context (GiB)")
-    ap.add_argument("--workload", default="step", choices=["step", "points32", "vjp"],
-                    help="step: the default three-channel line; points32 / vjp: the batching and adjoint paths")
+    ap.add_argument("--workload", default="step", choices=["step", "points32", "vjp", "multiloop", "multiloop-large"],
+                    help="step: the default three-channel line; points32 / vjp / multiloop: the batching, "
+                         "adjoint and multiloop paths")
     args = ap.parse_args()
     if args.workload != "step" and args.impl == "ours":
+        if args.workload.startswith("multiloop"):
+            return run_multiloop(args)
         return run_points32(args) if args.workload == "points32" else run_vjp(args)
     chans = tuple(sorted({"apt".index(c) for c in args.channels}))
     if not chans:

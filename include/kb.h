@@ -124,8 +124,9 @@ kb_status kb_set_vertex_class(kb_ctx *ctx, int slot, int channel, int cls, void 
  * beta = 1 reproduces that).  Γ1 is the vertex carrying the external v (for t: the vertex on
  * the external legs 1', 1).  precision: KB_PREC_FP64 (plain, every step in FP64) or
  * KB_PREC_MIXED (FP32 gather, 3xTF32 tensor-core contraction with FP32 accumulation;
- * propagators, Π and the tail in FP64).  The out slot's classes must be attached and must
- * not alias the inputs. */
+ * propagators, Π and the tail in FP64; its input classes must be complex64 with 32-byte
+ * aligned pointers, as every cudaMalloc or PyTorch allocation is).  The out slot's classes
+ * must be attached and must not alias the inputs. */
 kb_status kb_bubble(kb_ctx *ctx, int channel, int slot_left, int slot_right, int out_slot, int pi_kind,
                     unsigned class_mask, double alpha, double beta, int precision, void *stream);
 
@@ -180,18 +181,38 @@ kb_status kb_bubble_vjp(kb_ctx *ctx, int channel, int slot_left, int slot_right,
  * --------------------------------------------------------------------------------------- */
 typedef struct kb_graph kb_graph;
 
+/* Entry kinds of a step graph (kb_bubble_desc.op; zero-initialise the descriptor):
+ *   KB_OP_BUBBLE  kb_bubble(ctx, channel, slot_left, slot_right, out_slot, pi_kind,
+ *                 class_mask, alpha, beta, precision);
+ *   KB_OP_ADD     kb_vertex_add(ctx, channel, slot_left, out_slot, class_mask, alpha);
+ *   KB_OP_JOIN    every later entry, on every branch, waits for every earlier entry of
+ *                 every branch (ctx may be NULL; the other fields are ignored) — the
+ *                 point where the next loop order of a multiloop step reads the
+ *                 derivatives of all channels of the previous one. */
+enum { KB_OP_BUBBLE = 0, KB_OP_ADD = 1, KB_OP_JOIN = 2 };
+
 typedef struct {
     kb_ctx *ctx;
     int channel, slot_left, slot_right, out_slot, pi_kind;
     unsigned class_mask;
     double alpha, beta;
     int precision;
+    int op;
 } kb_bubble_desc;
 
 kb_status kb_graph_create(kb_graph **graph, const kb_bubble_desc *bubbles, int n);
 kb_status kb_graph_launch(kb_graph *graph, void *stream);
 kb_status kb_graph_kernel_count(kb_graph *graph, unsigned long long *count);
 kb_status kb_graph_destroy(kb_graph *graph);
+
+/* Slot arithmetic: the classes (class_mask) of channel `channel` of slot_dst
+ * += alpha * those of slot_src, elementwise in the destination's precision (c64 or c128;
+ * the source may have either).  Absent source classes read zero; a destination class
+ * must be attached where the source has one, and must not be the same array.  Used
+ * between the bubbles of a multiloop step (Sec. III.C: the l-loop derivative of channel r
+ * is the sum of its left, central and right parts).  Asynchronous on `stream`. */
+kb_status kb_vertex_add(kb_ctx *ctx, int channel, int slot_src, int slot_dst, unsigned class_mask, double alpha,
+                        void *stream);
 
 /* Device workspace limit of a context in bytes (default 4 GiB, or the KB_WORKSPACE_MB
  * environment variable at kb_create).  Larger limits let the K3 contraction batch more

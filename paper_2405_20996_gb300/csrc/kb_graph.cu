@@ -2,7 +2,8 @@
 // own grids and models), loop parts and channels — captured once into a CUDA graph and
 // replayed as one launch per step.  Bubbles of one context run in list order (they share
 // its workspace); the bubbles of different contexts run on separate branches of the graph
-// and may overlap on the GPU.
+// and may overlap on the GPU.  Slot additions run in their context's branch; a join entry
+// makes every branch wait for all others (the next loop order of a multiloop step).
 #include <algorithm>
 #include <cstdio>
 #include <map>
@@ -42,19 +43,26 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
     if (!out) return KB_ERR_ARG;
     *out = nullptr;
     if (!d || n < 1) return KB_ERR_ARG;
-    kb_ctx* c0 = d[0].ctx;
+    kb_ctx* c0 = nullptr;
+    for (int i = 0; i < n && !c0; ++i)
+        if (d[i].op != KB_OP_JOIN) c0 = d[i].ctx;
     if (!c0) return KB_ERR_ARG;
     std::vector<Branch> br;
     std::map<kb_ctx*, size_t> index;
+    int joins = 0;
     for (int i = 0; i < n; ++i) {
+        if (d[i].op == KB_OP_JOIN) { ++joins; continue; }
         kb_ctx* c = d[i].ctx;
         if (!c) return fail(c0, "kb_graph_create: null context in descriptor", KB_ERR_ARG);
         if (c->device != c0->device) return fail(c0, "kb_graph_create: contexts on different devices", KB_ERR_ARG);
         if (!c->grids_set || !c->model_set) return fail(c, "kb_graph_create: set grids and model first", KB_ERR_STATE);
+        if (d[i].op != KB_OP_BUBBLE && d[i].op != KB_OP_ADD)
+            return fail(c, "kb_graph_create: unknown entry kind", KB_ERR_ARG);
         if (d[i].channel < 0 || d[i].channel > 2 || (d[i].class_mask & ~KB_MASK_ALL) ||
-            (d[i].precision != KB_PREC_FP64 && d[i].precision != KB_PREC_MIXED))
+            (d[i].op == KB_OP_BUBBLE && d[i].precision != KB_PREC_FP64 && d[i].precision != KB_PREC_MIXED))
             return fail(c, "kb_graph_create: descriptor out of range", KB_ERR_ARG);
         if (!index.count(c)) { index[c] = br.size(); br.push_back(Branch{c}); }
+        if (d[i].op != KB_OP_BUBBLE) continue;
         Branch& b = br[index[c]];
         size_t need = d[i].precision == KB_PREC_FP64 ? kb_fp64_workspace_need(c, d[i].channel, d[i].class_mask)
                                                      : kb_mixed_workspace_need(c, d[i].channel, d[i].class_mask);
@@ -69,18 +77,21 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
         if (s != KB_OK) return s;
     }
     bool any_mixed = false;
-    for (int i = 0; i < n; ++i) any_mixed |= d[i].precision == KB_PREC_MIXED;
+    for (int i = 0; i < n; ++i) any_mixed |= d[i].op == KB_OP_BUBBLE && d[i].precision == KB_PREC_MIXED;
     if (any_mixed && !kb_tc_prepare(c0->device))
         return fail(c0, "kb_graph_create: tensor-core kernel setup failed", KB_ERR_CUDA);
 
     cudaStream_t s0 = nullptr;
     cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join_ev((size_t)joins * br.size(), nullptr);
     kb_status st = KB_OK;
     auto cleanup = [&]() {
         for (auto& b : br) {
             if (b.st) cudaStreamDestroy(b.st);
             if (b.done) cudaEventDestroy(b.done);
         }
+        for (auto e : join_ev)
+            if (e) cudaEventDestroy(e);
         if (fork) cudaEventDestroy(fork);
         if (s0) cudaStreamDestroy(s0);
     };
@@ -92,6 +103,11 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
     for (auto& b : br)
         if (cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess) {
+            cleanup();
+            return fail(c0, "kb_graph_create: stream/event creation failed", KB_ERR_CUDA);
+        }
+    for (auto& e : join_ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
             cleanup();
             return fail(c0, "kb_graph_create: stream/event creation failed", KB_ERR_CUDA);
         }
@@ -107,10 +123,22 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
     } else {
         cudaEventRecord(fork, s0);
         for (auto& b : br) cudaStreamWaitEvent(b.st, fork, 0);
+        int jn = 0;
         for (int i = 0; i < n && st == KB_OK; ++i) {
             const kb_bubble_desc& x = d[i];
-            st = kb_bubble(x.ctx, x.channel, x.slot_left, x.slot_right, x.out_slot, x.pi_kind, x.class_mask, x.alpha,
-                           x.beta, x.precision, br[index[x.ctx]].st);
+            if (x.op == KB_OP_JOIN) {
+                cudaEvent_t* ev = &join_ev[(size_t)jn++ * br.size()];
+                for (size_t b = 0; b < br.size(); ++b) cudaEventRecord(ev[b], br[b].st);
+                for (size_t b = 0; b < br.size(); ++b)
+                    for (size_t o = 0; o < br.size(); ++o)
+                        if (o != b) cudaStreamWaitEvent(br[b].st, ev[o], 0);
+            } else if (x.op == KB_OP_ADD) {
+                st = kb_vertex_add_impl(x.ctx, x.channel, x.slot_left, x.out_slot, x.class_mask, x.alpha,
+                                        br[index[x.ctx]].st);
+            } else {
+                st = kb_bubble(x.ctx, x.channel, x.slot_left, x.slot_right, x.out_slot, x.pi_kind, x.class_mask,
+                               x.alpha, x.beta, x.precision, br[index[x.ctx]].st);
+            }
         }
         for (auto& b : br) {
             cudaEventRecord(b.done, b.st);

@@ -116,6 +116,9 @@ kb_status kb_bubble_mixed(kb_ctx* ctx, int r, int sl, int sr, int so, int pi_kin
 kb_status kb_bubble_vjp_fp64(kb_ctx* ctx, int r, int sl, int sr, int sgo, int pi_kind, unsigned mask, double alpha,
                              int sgl, int sgr, void* const gGR[3], cudaStream_t st);
 kb_status kb_ensure_workspace(kb_ctx* ctx, size_t bytes);
+// slot arithmetic (kb_ops.cu)
+kb_status kb_vertex_add_impl(kb_ctx* ctx, int channel, int src, int dst, unsigned mask, double alpha,
+                             cudaStream_t st);
 // workspace a bubble needs (so that a graph capture never grows it), and the one-time
 // device setup of each unit (constant tables, kernel attributes) done before a capture
 size_t kb_fp64_workspace_need(const kb_ctx* ctx, int r, unsigned mask);

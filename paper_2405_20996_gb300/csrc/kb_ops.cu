@@ -1,0 +1,97 @@
+// Vertex arithmetic between slots: the sums the multiloop step needs between its bubbles
+// (Sec. III.C: the l-loop derivative of channel r is the sum of its left, central and right
+// parts, and the left part is also the right vertex of the next order's central part, so it
+// is computed once into its own slot and added).
+#include <algorithm>
+#include <cstdio>
+#include <string>
+
+#include "kb_internal.h"
+
+namespace kb {
+namespace {
+
+template <typename TS, typename TD>
+__global__ void k_class_add(const TS* __restrict__ src, TD* __restrict__ dst, size_t n, double alpha) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double sx = (double)src[2 * i], sy = (double)src[2 * i + 1];
+        dst[2 * i] = (TD)((double)dst[2 * i] + alpha * sx);
+        dst[2 * i + 1] = (TD)((double)dst[2 * i + 1] + alpha * sy);
+    }
+}
+
+size_t class_points(const Grids& g, int k) {
+    switch (k) {
+        case 0: return (size_t)g.n1;
+        case 1:
+        case 2: return (size_t)g.n2w * g.n2v;
+        default: return (size_t)g.n3w * g.n3v * g.n3v;
+    }
+}
+
+}  // namespace
+}  // namespace kb
+
+using namespace kb;
+
+kb_status kb_vertex_add_impl(kb_ctx* ctx, int channel, int src, int dst, unsigned mask, double alpha,
+                             cudaStream_t st) {
+    if (!ctx) return KB_ERR_ARG;
+    if (channel < 0 || channel > 2 || src < 0 || src >= KB_MAX_SLOTS || dst < 0 || dst >= KB_MAX_SLOTS ||
+        (mask & ~KB_MASK_ALL)) {
+        ctx->err = "kb_vertex_add: argument out of range";
+        return KB_ERR_ARG;
+    }
+    if (!ctx->grids_set) {
+        ctx->err = "kb_vertex_add: set grids first";
+        return KB_ERR_STATE;
+    }
+    if (src == dst) {
+        ctx->err = "kb_vertex_add: source and destination are the same slot";
+        return KB_ERR_ARG;
+    }
+    const VertexDev& S = ctx->slots[src];
+    const VertexDev& D = ctx->slots[dst];
+    for (int k = 0; k < 4; ++k) {
+        if (!((mask >> k) & 1) || !S.cls[channel][k]) continue;   // absent source classes read zero
+        if (!D.cls[channel][k]) {
+            ctx->err = "kb_vertex_add: destination class not attached";
+            return KB_ERR_ARG;
+        }
+        if (S.cls[channel][k] == D.cls[channel][k]) {
+            ctx->err = "kb_vertex_add: source and destination class alias";
+            return KB_ERR_ARG;
+        }
+    }
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return KB_ERR_CUDA;
+    for (int k = 0; k < 4; ++k) {
+        if (!((mask >> k) & 1) || !S.cls[channel][k]) continue;
+        const size_t n = class_points(ctx->g, k) * 16;
+        const int threads = 256;
+        const int blocks = (int)std::min<size_t>((n + threads - 1) / threads, (size_t)152 * 8);
+        KB_LAUNCH(ctx, st, "k_class_add");
+        const bool s64 = S.dt[channel][k] == KB_DT_C64, d64 = D.dt[channel][k] == KB_DT_C64;
+        const void* sp = S.cls[channel][k];
+        void* dp = const_cast<void*>(D.cls[channel][k]);
+        if (s64 && d64)
+            k_class_add<float, float><<<blocks, threads, 0, st>>>((const float*)sp, (float*)dp, n, alpha);
+        else if (s64)
+            k_class_add<float, double><<<blocks, threads, 0, st>>>((const float*)sp, (double*)dp, n, alpha);
+        else if (d64)
+            k_class_add<double, float><<<blocks, threads, 0, st>>>((const double*)sp, (float*)dp, n, alpha);
+        else
+            k_class_add<double, double><<<blocks, threads, 0, st>>>((const double*)sp, (double*)dp, n, alpha);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            ctx->err = std::string("kb_vertex_add: ") + cudaGetErrorString(e);
+            return KB_ERR_CUDA;
+        }
+    }
+    return KB_OK;
+}
+
+extern "C" kb_status kb_vertex_add(kb_ctx* ctx, int channel, int slot_src, int slot_dst, unsigned class_mask,
+                                   double alpha, void* stream) {
+    return kb_vertex_add_impl(ctx, channel, slot_src, slot_dst, class_mask, alpha,
+                              reinterpret_cast<cudaStream_t>(stream));
+}

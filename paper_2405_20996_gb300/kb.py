@@ -40,9 +40,10 @@ class kb_vertex_desc(C.Structure):
 class kb_bubble_desc(C.Structure):
     _fields_ = [("ctx", C.c_void_p), ("channel", C.c_int), ("slot_left", C.c_int), ("slot_right", C.c_int),
                 ("out_slot", C.c_int), ("pi_kind", C.c_int), ("class_mask", C.c_uint), ("alpha", C.c_double),
-                ("beta", C.c_double), ("precision", C.c_int)]
+                ("beta", C.c_double), ("precision", C.c_int), ("op", C.c_int)]
 
 
+KB_OP_BUBBLE, KB_OP_ADD, KB_OP_JOIN = 0, 1, 2
 KB_ERR_TOO_LARGE = 7
 KB_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -61,6 +62,7 @@ _SIGS = {
                   C.c_int, C.c_void_p],
     "kb_bubble_vjp": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_double, C.c_int,
                       C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
+    "kb_vertex_add": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_double, C.c_void_p],
     "kb_graph_create": [C.POINTER(C.c_void_p), C.POINTER(kb_bubble_desc), C.c_int],
     "kb_graph_launch": [C.c_void_p, C.c_void_p],
     "kb_graph_kernel_count": [C.c_void_p, C.POINTER(C.c_ulonglong)],
@@ -168,13 +170,28 @@ def kb_bubble_vjp(ctx, channel, slot_left, slot_right, gout_slot, pi_kind=KB_PI_
                                     precision, stream))
 
 
+def kb_vertex_add(ctx, channel, slot_src, slot_dst, class_mask=KB_MASK_ALL, alpha=1.0, stream=0):
+    _check(ctx, lib().kb_vertex_add(ctx, channel, slot_src, slot_dst, class_mask, alpha, stream))
+
+
+def kb_add_desc(ctx, channel, slot_src, slot_dst, class_mask=KB_MASK_ALL, alpha=1.0):
+    """Step-graph entry: slot_dst += alpha * slot_src (classes of one channel)."""
+    return kb_bubble_desc(ctx, channel, slot_src, -1, slot_dst, 0, class_mask, alpha, 0.0, 0, KB_OP_ADD)
+
+
+def kb_join_desc():
+    """Step-graph entry: every later entry waits for all earlier ones (all branches)."""
+    return kb_bubble_desc(None, 0, -1, -1, -1, 0, 0, 0.0, 0.0, 0, KB_OP_JOIN)
+
+
 def kb_graph_create(descs):
     """descs: sequence of kb_bubble_desc; returns the graph handle."""
     arr = (kb_bubble_desc * len(descs))(*descs)
     g = C.c_void_p()
     st = lib().kb_graph_create(C.byref(g), arr, len(descs))
     if st != KB_OK:
-        raise KBError(st, lib().kb_last_error(descs[0].ctx).decode() if len(descs) else "")
+        ctx = next((d.ctx for d in descs if d.ctx), None)
+        raise KBError(st, lib().kb_last_error(ctx).decode() if ctx else "")
     return g
 
 

@@ -1,0 +1,157 @@
+"""Right-hand side of the multiloop flow for the vertex (Sec. III.C), as one step graph.
+
+At fixed vertex Γ and self-energy, the l-loop contributions to the derivative of the
+reducible vertex of channel r are
+
+    l = 1:   γ̇_r^(1) = B_r(Γ, Γ; Π̇),  Π̇ = G S + S G (the single-scale pair),
+    l = 2:   γ̇_r^(2) = L_r^(2) + R_r^(2),
+    l >= 3:  γ̇_r^(l) = L_r^(l) + C_r^(l) + R_r^(l),
+
+with L_r^(l) = B_r(γ̇_r̄^(l-1), Γ), R_r^(l) = B_r(Γ, γ̇_r̄^(l-1)), C_r^(l) = B_r(Γ, L_r^(l-1))
+(Π = G G; γ̇_r̄ = the sum over the channels other than r), and Γ̇ = Σ_l Σ_r γ̇_r^(l).  Per
+channel that is 1 + 2 + 3 (n_loops - 2) bubbles: 15 per channel, 45 per step, at six loops.
+
+Each channel has its own context (workspace), and the three run as parallel branches of
+one CUDA graph; a join entry separates the loop orders, because order l of channel r reads
+order l - 1 of all channels.  The slot γ̇^(l) serves as the output of order l (each branch
+writes its channel) and, with its channel mask excluding r, as the vertex γ̇_r̄^(l-1) of
+the next order.  L_r^(l) is computed once into its own slot (it is the right vertex of the
+next order's central part, a channel-r-only vertex without bare part) and added to γ̇_r^(l)
+by the library's slot addition.
+"""
+
+import torch
+
+from . import kb
+from .engine import CLASS_NAMES, Engine, StepGraph
+
+S_GAMMA = 0
+S_TOTAL = 1                    # Γ̇ = Σ_l γ̇^(l)
+
+
+def _s_order(l):               # γ̇^(l), l = 1 .. n_loops
+    return 1 + l
+
+
+def _s_left(l, n_loops):       # L^(l), l = 2 .. n_loops - 1
+    return 1 + n_loops + (l - 1)
+
+
+class MultiloopStep:
+    def __init__(self, grids, nq, U, Delta, T, vertex, n_loops=6, precision="mixed", A=5.0, device=0,
+                 symmetric=True, channels=(0, 1, 2)):
+        """vertex: {channel: (K1, K2, K2p, K3)} arrays of the reducible vertices γ_r (the bare
+        part U/2 is added by the library).  precision "mixed" keeps every vertex in complex64,
+        "fp64" in complex128."""
+        assert n_loops >= 1
+        assert _s_left(n_loops - 1, n_loops) < kb.KB_MAX_SLOTS
+        self.n_loops, self.precision = n_loops, precision
+        self.channels = tuple(channels)
+        dt = torch.complex64 if precision == "mixed" else torch.complex128
+        self.dtype = dt
+        self.e = {}
+        for r in self.channels:
+            e = Engine(grids, nq, A=A, device=device)
+            e.set_model(Delta, T)
+            self.e[r] = e
+        e0 = self.e[self.channels[0]]
+        e0.set_vertex(S_GAMMA, U=U, has_R=True, channels=vertex, dtype=dt, symmetric=symmetric)
+        for r in self.channels[1:]:
+            self.e[r].share_slot(S_GAMMA, e0, S_GAMMA, U=U, has_R=True, symmetric=symmetric)
+        sh = e0.class_shapes()
+        dev = e0.device
+        z = lambda: {(c, k): torch.zeros(sh[CLASS_NAMES[k]], dtype=dt, device=dev) for c in range(3) for k in range(4)}
+        self.total = z()
+        self.orders = [z() for _ in range(n_loops)]
+        self.lefts = {l: {r: {k: torch.zeros(sh[CLASS_NAMES[k]], dtype=dt, device=dev) for k in range(4)}
+                          for r in self.channels} for l in range(2, n_loops)}
+        for r, e in self.e.items():
+            others = 7 & ~(1 << r)
+            self._attach(e, S_TOTAL, self.total, 7)
+            for l in range(1, n_loops + 1):
+                self._attach(e, _s_order(l), self.orders[l - 1], others)
+            for l in range(2, n_loops):
+                kb.kb_set_vertex(e.ctx, _s_left(l, n_loops), False, 0.0)
+                kb.kb_set_vertex_channels(e.ctx, _s_left(l, n_loops), 1 << r)
+                kb.kb_set_vertex_symmetric(e.ctx, _s_left(l, n_loops), False)
+                e.tensors[_s_left(l, n_loops)] = {}
+                for k in range(4):
+                    e.attach(_s_left(l, n_loops), r, k, self.lefts[l][r][k])
+        self.descs = self._descs()
+        self.graph = None
+
+    @staticmethod
+    def _attach(e, slot, tensors, mask):
+        kb.kb_set_vertex(e.ctx, slot, False, 0.0)
+        kb.kb_set_vertex_channels(e.ctx, slot, mask)
+        kb.kb_set_vertex_symmetric(e.ctx, slot, False)
+        e.tensors[slot] = {}
+        for (c, k), t in tensors.items():
+            e.attach(slot, c, k, t)
+
+    def _descs(self):
+        """The step as a list of graph entries (bubbles, slot additions, joins)."""
+        L, prec, d = self.n_loops, self.precision, []
+        G = S_GAMMA
+        for r, e in self.e.items():
+            d.append(e.desc(r, G, G, _s_order(1), pi_kind=kb.KB_PI_GS_SG, precision=prec))
+        for l in range(2, L + 1):
+            d.append(kb.kb_join_desc())
+            prev, out = _s_order(l - 1), _s_order(l)
+            for r, e in self.e.items():
+                last = l == L
+                lslot = out if last else _s_left(l, L)
+                d.append(e.desc(r, prev, G, lslot, precision=prec))                          # L
+                if l >= 3:
+                    d.append(e.desc(r, G, _s_left(l - 1, L), out, beta=1.0 if last else 0.0,
+                                    precision=prec))                                         # C
+                d.append(e.desc(r, G, prev, out, beta=1.0 if (last or l >= 3) else 0.0,
+                                precision=prec))                                             # R
+                if not last:
+                    d.append(kb.kb_add_desc(e.ctx, r, lslot, out))
+        for r, e in self.e.items():
+            for l in range(1, L + 1):
+                d.append(kb.kb_add_desc(e.ctx, r, _s_order(l), S_TOTAL))
+        return d
+
+    def bubbles_per_step(self):
+        return sum(1 for x in self.descs if x.op == kb.KB_OP_BUBBLE)
+
+    def zero(self):
+        for t in self.total.values():
+            t.zero_()
+
+    def build(self):
+        self.graph = StepGraph(self.descs)
+        return self.graph
+
+    def run(self, stream=None):
+        """One step: Γ̇ accumulates into `total` (zero it first for a fresh derivative)."""
+        if self.graph is None:
+            self.build()
+        self.graph.launch(stream)
+
+    def run_eager(self, stream=None):
+        """The same entries launched one by one on one stream (reference for the graph)."""
+        st = (stream or torch.cuda.current_stream(self.e[self.channels[0]].device)).cuda_stream
+        for x in self.descs:
+            if x.op == kb.KB_OP_JOIN:
+                continue
+            if x.op == kb.KB_OP_ADD:
+                kb.kb_vertex_add(x.ctx, x.channel, x.slot_left, x.out_slot, x.class_mask, x.alpha, st)
+            else:
+                kb.kb_bubble(x.ctx, x.channel, x.slot_left, x.slot_right, x.out_slot, x.pi_kind, x.class_mask,
+                             x.alpha, x.beta, x.precision, st)
+
+    def order(self, l, ch):
+        return {CLASS_NAMES[k]: self.orders[l - 1][(ch, k)] for k in range(4)}
+
+    def derivative(self, ch):
+        return {CLASS_NAMES[k]: self.total[(ch, k)] for k in range(4)}
+
+    def close(self):
+        if self.graph is not None:
+            self.graph.close()
+            self.graph = None
+        for e in self.e.values():
+            e.close()

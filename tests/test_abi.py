@@ -40,3 +40,27 @@ def test_null_arguments_of_vjp_and_graph_rejected():
     assert L.kb_graph_launch(None, None) == kb.KB_ERR_ARG
     assert L.kb_graph_destroy(None) == kb.KB_ERR_ARG
     assert L.kb_set_workspace_limit(None, 1 << 30) == kb.KB_ERR_ARG
+
+
+def test_slot_add_and_graph_entry_kinds_rejected_without_context():
+    L = kb.lib()
+    assert L.kb_vertex_add(None, 0, 0, 1, 15, 1.0, None) == kb.KB_ERR_ARG
+    g = ctypes.c_void_p()
+    d = (kb.kb_bubble_desc * 2)(kb.kb_join_desc(), kb.kb_join_desc())     # joins only: no context
+    assert L.kb_graph_create(ctypes.byref(g), d, 2) == kb.KB_ERR_ARG and not g.value
+
+
+def test_graph_descriptor_layout_matches_header(tmp_path):
+    """sizeof and field offsets of kb_bubble_desc as the C compiler lays it out."""
+    import os
+    import subprocess
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "kb.h"\nint main(void) {\n'
+                   '  printf("%zu %zu %zu %zu\\n", sizeof(kb_bubble_desc), offsetof(kb_bubble_desc, alpha),\n'
+                   '         offsetof(kb_bubble_desc, precision), offsetof(kb_bubble_desc, op));\n  return 0;\n}\n')
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    D = kb.kb_bubble_desc
+    assert got == [ctypes.sizeof(D), D.alpha.offset, D.precision.offset, D.op.offset]
