@@ -124,7 +124,7 @@ kb_status kb_set_vertex_class(kb_ctx *ctx, int slot, int channel, int cls, void 
  * beta = 1 reproduces that).  Γ1 is the vertex carrying the external v (for t: the vertex on
  * the external legs 1', 1).  precision: KB_PREC_FP64 (plain, every step in FP64) or
  * KB_PREC_MIXED (FP32 gather, 3xTF32 tensor-core contraction with FP32 accumulation;
- * propagators, Π and the tail in FP64; its input classes must be complex64 with 32-byte
+ * propagators, Π and the tail in FP64; its input classes must be complex64 with 16-byte
  * aligned pointers, as every cudaMalloc or PyTorch allocation is).  The out slot's classes
  * must be attached and must not alias the inputs. */
 kb_status kb_bubble(kb_ctx *ctx, int channel, int slot_left, int slot_right, int out_slot, int pi_kind,
