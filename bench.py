@@ -360,7 +360,8 @@ def run_multiloop(args):
     from paper_2405_20996_gb300.multiloop import MultiloopStep
     g, nq, Ui, Ti = ML_SIZES[args.workload]
     dev = torch.device("cuda", 0)
-    ml = MultiloopStep(g, nq, Ui, DELTA, Ti, S.seeded_vertex(g, Ui, seed=4242), n_loops=6, precision="mixed")
+    ml = MultiloopStep(g, nq, Ui, DELTA, Ti, S.seeded_vertex(g, Ui, seed=4242), n_loops=6, precision="mixed",
+                       cache={"off": False, "left": "left", "both": True}[args.ml_cache])
     for e in ml.e.values():
         e.set_workspace_limit(args.ws_gb << 30)
     stream = torch.cuda.current_stream(dev)
@@ -436,6 +437,7 @@ def run_multiloop(args):
             "config": {"workload": "six-loop vertex flow step, a,p,t, K1 %d, K2 %dx%d, K3 %d^3, Nq %d, c64"
                                    % (g["n1"], g["n2w"], g["n2v"], g["n3w"], nq),
                        "bubbles_per_step": nb, "points_per_step": points, "U": Ui, "T": Ti,
+                       "record_cache": {r: ml.cached[r] for r in ml.cached} or "off",
                        "l2": "flushed (256 MB write) before every timed step",
                        "launch": "one CUDA graph per step, channels as branches, a join per loop order"},
             "eager": {"value": points / (ms_eager / 1e3), "ms_per_step": ms_eager}, "gpu_launches": per_step,
@@ -505,6 +507,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling captures)")
     ap.add_argument("--no-graph", action="store_true", help="eager launches instead of one step graph")
     ap.add_argument("--ws-gb", type=int, default=8, help="device workspace limit per context (GiB)")
+    ap.add_argument("--ml-cache", default="left", choices=["off", "left", "both"],
+                    help="multiloop workloads: record cache of the full vertex (off, left side, both sides)")
     ap.add_argument("--workload", default="step", choices=["step", "points32", "vjp", "multiloop", "multiloop-large"],
                     help="step: the default three-channel line; points32 / vjp / multiloop: the batching, "
                          "adjoint and multiloop paths")

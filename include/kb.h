@@ -188,8 +188,10 @@ typedef struct kb_graph kb_graph;
  *   KB_OP_JOIN    every later entry, on every branch, waits for every earlier entry of
  *                 every branch (ctx may be NULL; the other fields are ignored) — the
  *                 point where the next loop order of a multiloop step reads the
- *                 derivatives of all channels of the previous one. */
-enum { KB_OP_BUBBLE = 0, KB_OP_ADD = 1, KB_OP_JOIN = 2 };
+ *                 derivatives of all channels of the previous one;
+ *   KB_OP_CACHE   kb_vertex_cache(ctx, slot_left, channel, class_mask = sides): the record
+ *                 cache is allocated at graph creation and rebuilt at every replay. */
+enum { KB_OP_BUBBLE = 0, KB_OP_ADD = 1, KB_OP_JOIN = 2, KB_OP_CACHE = 3 };
 
 typedef struct {
     kb_ctx *ctx;
@@ -213,6 +215,23 @@ kb_status kb_graph_destroy(kb_graph *graph);
  * is the sum of its left, central and right parts).  Asynchronous on `stream`. */
 kb_status kb_vertex_add(kb_ctx *ctx, int channel, int slot_src, int slot_dst, unsigned class_mask, double alpha,
                         void *stream);
+
+/* Record cache of a vertex slot (mixed precision; Sec. II.D.1 class split): the part of
+ * the slot's vertex that the K2 contraction of channel `channel` gathers at every node —
+ * the other channels' classes at the converted frequencies, FP32, 16 components (two spin
+ * records for t) — for every (w, v) of the K2 grids and every interior quadrature node:
+ * side bit 0 as the left vertex (records at (w, v, v''_j)), bit 1 as the right vertex of
+ * the K2' contraction (records at (w, v''_j, v')).  Each side takes
+ * n2w * n2v * (nq - 2) * 128 bytes (twice that for t), allocated by the library.  Later
+ * mixed-precision bubbles of `channel` that have this slot on a cached side stream the
+ * records instead of gathering them (the same FP32 records, summed in another order: the
+ * results agree to FP32 rounding); a vertex that stays fixed over many bubbles (the full
+ * vertex of a multiloop step, Sec. III.C) is then gathered once.  The cache reflects the slot's arrays when the build runs (asynchronous on
+ * `stream`): rebuild it after changing their contents.  Any kb_set_vertex* call on the
+ * slot or kb_set_grids makes it stale (then unused); kb_vertex_uncache frees it.
+ * KB_ERR_OOM if the cache does not fit. */
+kb_status kb_vertex_cache(kb_ctx *ctx, int slot, int channel, unsigned sides, void *stream);
+kb_status kb_vertex_uncache(kb_ctx *ctx, int slot);
 
 /* Device workspace limit of a context in bytes (default 4 GiB, or the KB_WORKSPACE_MB
  * environment variable at kb_create).  Larger limits let the K3 contraction batch more

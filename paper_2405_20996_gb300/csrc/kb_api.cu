@@ -121,6 +121,7 @@ kb_status kb_destroy(kb_ctx* ctx) {
     cudaFree(ctx->d_wq);
     cudaFree(ctx->d_sig);
     cudaFree(ctx->ws.ptr);
+    for (int s = 0; s < KB_MAX_SLOTS; ++s) kb_vertex_cache_free(ctx, s);
     prof_clear(ctx);
     delete ctx;
     return KB_OK;
@@ -145,6 +146,7 @@ kb_status kb_set_grids(kb_ctx* ctx, const kb_grid_desc* g) {
     KB_CUDA_TRY(ctx, cudaMemcpy(ctx->d_wq, w.data(), sizeof(double) * g->nq, cudaMemcpyHostToDevice));
     ctx->g = {g->n1, g->n2w, g->n2v, g->n3w, g->n3v, g->nq, g->A};
     ctx->grids_set = true;
+    for (int s = 0; s < KB_MAX_SLOTS; ++s) ++ctx->slot_gen[s];
     return KB_OK;
 }
 
@@ -193,6 +195,7 @@ kb_status kb_set_vertex(kb_ctx* ctx, int slot, int has_R, double U) {
     ctx->slots[slot].mask = 7;
     ctx->slots[slot].halfU = 0.5 * U;
     ctx->slot_set[slot] = true;
+    ++ctx->slot_gen[slot];
     return KB_OK;
 }
 
@@ -203,6 +206,7 @@ kb_status kb_set_vertex_channels(kb_ctx* ctx, int slot, unsigned mask) {
     }
     if (!ctx->slot_set[slot]) { ctx->err = "kb_set_vertex_channels: call kb_set_vertex first"; return KB_ERR_STATE; }
     ctx->slots[slot].mask = (int)mask;
+    ++ctx->slot_gen[slot];
     return KB_OK;
 }
 
@@ -229,6 +233,7 @@ kb_status kb_set_vertex_class(kb_ctx* ctx, int slot, int channel, int cls, void*
     }
     ctx->slots[slot].cls[channel][cls] = ptr;
     ctx->slots[slot].dt[channel][cls] = dtype;
+    ++ctx->slot_gen[slot];
     return KB_OK;
 }
 

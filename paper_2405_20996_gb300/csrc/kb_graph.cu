@@ -56,9 +56,10 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
         if (!c) return fail(c0, "kb_graph_create: null context in descriptor", KB_ERR_ARG);
         if (c->device != c0->device) return fail(c0, "kb_graph_create: contexts on different devices", KB_ERR_ARG);
         if (!c->grids_set || !c->model_set) return fail(c, "kb_graph_create: set grids and model first", KB_ERR_STATE);
-        if (d[i].op != KB_OP_BUBBLE && d[i].op != KB_OP_ADD)
+        if (d[i].op != KB_OP_BUBBLE && d[i].op != KB_OP_ADD && d[i].op != KB_OP_CACHE)
             return fail(c, "kb_graph_create: unknown entry kind", KB_ERR_ARG);
         if (d[i].channel < 0 || d[i].channel > 2 || (d[i].class_mask & ~KB_MASK_ALL) ||
+            (d[i].op == KB_OP_CACHE && (d[i].class_mask < 1 || d[i].class_mask > 3)) ||
             (d[i].op == KB_OP_BUBBLE && d[i].precision != KB_PREC_FP64 && d[i].precision != KB_PREC_MIXED))
             return fail(c, "kb_graph_create: descriptor out of range", KB_ERR_ARG);
         if (!index.count(c)) { index[c] = br.size(); br.push_back(Branch{c}); }
@@ -70,6 +71,11 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
     }
     if (cudaSetDevice(c0->device) != cudaSuccess) return fail(c0, "cudaSetDevice failed", KB_ERR_CUDA);
     // everything that allocates, synchronises or copies happens before the capture
+    for (int i = 0; i < n; ++i)
+        if (d[i].op == KB_OP_CACHE) {
+            kb_status s = kb_vertex_cache_prepare(d[i].ctx, d[i].slot_left, d[i].channel, d[i].class_mask);
+            if (s != KB_OK) return s;
+        }
     for (auto& b : br) {
         kb_status s = kb_ensure_workspace(b.ctx, b.need);
         if (s != KB_OK) return s;
@@ -132,6 +138,8 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
                 for (size_t b = 0; b < br.size(); ++b)
                     for (size_t o = 0; o < br.size(); ++o)
                         if (o != b) cudaStreamWaitEvent(br[b].st, ev[o], 0);
+            } else if (x.op == KB_OP_CACHE) {
+                st = kb_vertex_cache_launch(x.ctx, x.slot_left, x.channel, x.class_mask, br[index[x.ctx]].st);
             } else if (x.op == KB_OP_ADD) {
                 st = kb_vertex_add_impl(x.ctx, x.channel, x.slot_left, x.out_slot, x.class_mask, x.alpha,
                                         br[index[x.ctx]].st);

@@ -75,6 +75,18 @@ struct kb_ctx {
     size_t ws_limit = 0;
     bool prof_on = false;
     std::vector<kb_prof_rec> prof;
+    // bumped by every change of a slot (and of the grids); a record cache is valid only for
+    // the generation it was built from
+    unsigned long long slot_gen[KB_MAX_SLOTS] = {};
+    // record caches (kb_vertex_cache): side 0 = the slot as left vertex of the K2
+    // contraction, side 1 = as right vertex of the K2' contraction, for one channel
+    struct RecCache {
+        void* ptr[2] = {nullptr, nullptr};
+        size_t bytes[2] = {0, 0};
+        int channel = -1;
+        unsigned sides = 0;
+        unsigned long long gen = ~0ull;
+    } rc[KB_MAX_SLOTS];
 };
 
 // Bracket a launch with timing events when profiling is on.
@@ -116,6 +128,10 @@ kb_status kb_bubble_mixed(kb_ctx* ctx, int r, int sl, int sr, int so, int pi_kin
 kb_status kb_bubble_vjp_fp64(kb_ctx* ctx, int r, int sl, int sr, int sgo, int pi_kind, unsigned mask, double alpha,
                              int sgl, int sgr, void* const gGR[3], cudaStream_t st);
 kb_status kb_ensure_workspace(kb_ctx* ctx, size_t bytes);
+// record caches (kb_mixed.cu): allocation (no launch, may cudaMalloc) and the build launch
+kb_status kb_vertex_cache_prepare(kb_ctx* ctx, int slot, int channel, unsigned sides);
+kb_status kb_vertex_cache_launch(kb_ctx* ctx, int slot, int channel, unsigned sides, cudaStream_t st);
+void kb_vertex_cache_free(kb_ctx* ctx, int slot);
 // slot arithmetic (kb_ops.cu)
 kb_status kb_vertex_add_impl(kb_ctx* ctx, int channel, int src, int dst, unsigned mask, double alpha,
                              cudaStream_t st);

@@ -289,88 +289,67 @@ __device__ __forceinline__ float2 ld_stream(const float2* p) {
     return v;
 }
 
-// K2 (RIGHT = false): out(w, v)[A][C] = sum_j sum_s sum_B L_s(w, v, v''_j)[A][B] N_s(w, j)[B][C]
-//   with L the v-dependent part of Gamma1 without its own K2 class, plus
-//   K2own_s(w, v)[A][B] * SN_s(w)[B][C]  (the own K2 class does not depend on v'').
-// K2' (RIGHT = true): out(w, v')[A][C] = sum_j sum_s sum_D M_s(w, j)[A][D] R_s(w, v''_j, v')[D][C]
-//   + SM_s(w)[A][D] * K2'own_s(w, v')[D][C].
-// One CTA (128 threads) per (w, v).  Per tile of 128 nodes every thread gathers one record
-// into shared memory; then the 4x4 contraction runs with one output component per thread
-// (16 components x 8 record groups), so the gather carries no output accumulators.  The
-// endpoint nodes contribute only through the own class and are skipped in the tiles.
+__device__ __forceinline__ float4 ld_stream4(const float4* p) {
+    float4 v;
+    asm("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p));
+    return v;
+}
+
+// out <- beta * out over n complex elements (a class whose bubble part is identically zero:
+// alpha * 0 + beta * out).
+__global__ void k_mx_scale_class(void* out, int dt, size_t n, double beta) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        if (dt == KB_DT_C128) {
+            double2* p = reinterpret_cast<double2*>(out) + i;
+            *p = beta != 0.0 ? make_double2(beta * p->x, beta * p->y) : make_double2(0.0, 0.0);
+        } else {
+            float2* p = reinterpret_cast<float2*>(out) + i;
+            *p = beta != 0.0 ? make_float2((float)(beta * p->x), (float)(beta * p->y)) : make_float2(0.f, 0.f);
+        }
+    }
+}
+
+// Record cache of a vertex for the K2 (RIGHT = false) or K2' (RIGHT = true) contraction of
+// channel R: the records the node loop of k_mx_k2 gathers — the other channels' part of the
+// vertex at (w, v, v''_j) (left) or (w, v''_j, v') (right), FP32 — for every (w, v) of the
+// K2 grids and every interior node j = 1 .. nq-2, laid out [w][v][j-1][s][16] (s: the spin
+// records of the t channel, up-down then up-up).  One thread per record; a warp writes 32
+// consecutive 128-byte records.
 template <bool RIGHT, int R>
-__global__ void __launch_bounds__(128, 4) k_mx_k2(VertexF V, DfGrids G, MixedJob J, const float2* __restrict__ Tab,
-                                               const double2* __restrict__ Ssum, const double2* __restrict__ Ntil,
-                                               void* out, int odt, int w_off, int v_off) {
+__global__ void __launch_bounds__(128) k_mx_cache_k2(VertexF V, DfGrids G, int nq, float2* __restrict__ cache) {
     constexpr int NS = (R == KB_CH_T) ? 2 : 1;
-    // records of the quadrature nodes of one chunk: [0] up-down, [1] up-up (t only; the
-    // up-up record is the up-down one plus the exchanged term, so the direct lookups are
-    // done once for both spin terms)
-    __shared__ float2 rec[NS][128][17];
-    __shared__ float2 red[8][16];
-    int wi = w_off + blockIdx.y, vi = v_off + blockIdx.x;
+    const int wi = blockIdx.z, vi = blockIdx.y;
+    const int j = 1 + blockIdx.x * 128 + threadIdx.x;
+    if (j >= nq - 1) return;
     const df* qn = G.n3v + G.N3v;
-    df w = G.n2w[wi], ve = G.n2v[vi];
+    const df w = G.n2w[wi], ve = G.n2v[vi];
+    float2 g[16];
+    if (RIGHT) vertex_part_f32<R>(V, G, PARTS_UD, true, 32, w, qn[j], ve, g);
+    else vertex_part_f32<R>(V, G, PARTS_UD, false, 32, w, ve, qn[j], g);
+    float4* dst = reinterpret_cast<float4*>(cache + ((((size_t)wi * G.N2v + vi) * (nq - 2) + (j - 1)) * NS) * 16);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) dst[i] = make_float4(g[2 * i].x, g[2 * i].y, g[2 * i + 1].x, g[2 * i + 1].y);
+    if (NS == 2) {
+        if (RIGHT) vertex_part_f32<R>(V, G, PARTS_X, true, 32, w, qn[j], ve, g, true);
+        else vertex_part_f32<R>(V, G, PARTS_X, false, 32, w, ve, qn[j], g, true);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) dst[8 + i] = make_float4(g[2 * i].x, g[2 * i].y, g[2 * i + 1].x, g[2 * i + 1].y);
+    }
+}
+
+// The rest of a K2 (K2') output point after the node loop, for a thread holding the partial
+// sum acc of component (A, C) = (o >> 2, o & 3), o = tid & 15: the own K3 class through the
+// node-weighted sums, the own v-dependent class times the node sums, the reduction over the
+// 8 thread groups and the store.
+template <bool RIGHT, int R>
+__device__ __forceinline__ void k2_tail(const VertexF& V, const DfGrids& G, const MixedJob& J,
+                                        const double2* __restrict__ Ssum, const double2* __restrict__ Ntil, void* out,
+                                        int odt, int wi, int vi, df w, df ve, float2 acc,
+                                        float2 (*rec)[128][17], float2 (*red)[16]) {
+    constexpr int NS = (R == KB_CH_T) ? 2 : 1;
     const int tid = threadIdx.x, o = tid & 15, q = tid >> 4;
     const int A = o >> 2, C = o & 3;
-    float2 acc = make_float2(0.f, 0.f);
-    // spin term s uses up-up on the left for s = 0 and on the right for s = 1 (t channel)
-    const float2* T0 = Tab + ((size_t)wi * NS) * J.nq * 16;
-    const float2* T1 = T0 + (size_t)J.nq * 16;
-#pragma unroll 1
-    for (int j0 = 1; j0 < J.nq - 1; j0 += 128) {
-        int j = j0 + tid;
-        float2 g[16];
-        const bool valid = j < J.nq - 1;
-        if (valid) {
-            if (RIGHT) vertex_part_f32<R>(V, G, PARTS_UD, true, 32, w, qn[j], ve, g);
-            else vertex_part_f32<R>(V, G, PARTS_UD, false, 32, w, ve, qn[j], g);
-        } else {
-#pragma unroll
-            for (int c = 0; c < 16; ++c) g[c] = make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int c = 0; c < 16; ++c) rec[0][tid][c] = g[c];
-        if (NS == 2) {
-            if (valid) {
-                if (RIGHT) vertex_part_f32<R>(V, G, PARTS_X, true, 32, w, qn[j], ve, g, true);
-                else vertex_part_f32<R>(V, G, PARTS_X, false, 32, w, ve, qn[j], g, true);
-            }
-#pragma unroll
-            for (int c = 0; c < 16; ++c) rec[NS - 1][tid][c] = g[c];
-        }
-        __syncthreads();
-        int nrec = min(128, J.nq - 1 - j0);
-#pragma unroll 1
-        for (int rr = q; rr < nrec; rr += 8) {
-            const float2* t0 = T0 + (size_t)(j0 + rr) * 16;
-            if (NS == 1) {
-                if (!RIGHT) {
-#pragma unroll
-                    for (int B = 0; B < 4; ++B) cmac2(acc, rec[0][rr][cmap<R>(A, B)], ld_stream(t0 + 4 * B + C));
-                } else {
-#pragma unroll
-                    for (int D = 0; D < 4; ++D) cmac2(acc, ld_stream(t0 + 4 * A + D), rec[0][rr][cmap<R>(D, C)]);
-                }
-            } else {
-                const float2* t1 = T1 + (size_t)(j0 + rr) * 16;
-                if (!RIGHT) {
-#pragma unroll
-                    for (int B = 0; B < 4; ++B) {
-                        cmac2(acc, rec[NS - 1][rr][cmap<R>(A, B)], ld_stream(t0 + 4 * B + C));
-                        cmac2(acc, rec[0][rr][cmap<R>(A, B)], ld_stream(t1 + 4 * B + C));
-                    }
-                } else {
-#pragma unroll
-                    for (int D = 0; D < 4; ++D) {
-                        cmac2(acc, ld_stream(t0 + 4 * A + D), rec[0][rr][cmap<R>(D, C)]);
-                        cmac2(acc, ld_stream(t1 + 4 * A + D), rec[NS - 1][rr][cmap<R>(D, C)]);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-    }
     // own K3 class through the node-weighted sums: records at the K3 grid nodes X_m,
     // [0] up-down (pairs with N_0 + N_1, or N_0 for a, p), [1] the exchanged term of the
     // t channel's up-up component (pairs with N_0 left, N_1 right)
@@ -460,6 +439,165 @@ __global__ void __launch_bounds__(128, 4) k_mx_k2(VertexF V, DfGrids G, MixedJob
         for (int k = 0; k < 8; ++k) { re += red[k][o].x; im += red[k][o].y; }
         store_out(out, odt, ((size_t)wi * G.N2v + vi) * 16 + cmap<R>(A, C), make_double2(re, im), J.alpha, J.beta);
     }
+}
+
+// K2 (RIGHT = false): out(w, v)[A][C] = sum_j sum_s sum_B L_s(w, v, v''_j)[A][B] N_s(w, j)[B][C]
+//   with L the v-dependent part of Gamma1 without its own K2 class, plus
+//   K2own_s(w, v)[A][B] * SN_s(w)[B][C]  (the own K2 class does not depend on v'').
+// K2' (RIGHT = true): out(w, v')[A][C] = sum_j sum_s sum_D M_s(w, j)[A][D] R_s(w, v''_j, v')[D][C]
+//   + SM_s(w)[A][D] * K2'own_s(w, v')[D][C].
+// One CTA (128 threads) per (w, v).  Per tile of 128 nodes every thread gathers one record
+// into shared memory; then the 4x4 contraction runs with one output component per thread
+// (16 components x 8 record groups), so the gather carries no output accumulators.  The
+// endpoint nodes contribute only through the own class and are skipped in the tiles.
+template <bool RIGHT, int R>
+__global__ void __launch_bounds__(128, 4) k_mx_k2(VertexF V, DfGrids G, MixedJob J, const float2* __restrict__ Tab,
+                                               const double2* __restrict__ Ssum, const double2* __restrict__ Ntil,
+                                               void* out, int odt, int w_off, int v_off) {
+    constexpr int NS = (R == KB_CH_T) ? 2 : 1;
+    // records of the quadrature nodes of one chunk: [0] up-down, [1] up-up (t only; the
+    // up-up record is the up-down one plus the exchanged term, so the direct lookups are
+    // done once for both spin terms)
+    __shared__ float2 rec[NS][128][17];
+    __shared__ float2 red[8][16];
+    int wi = w_off + blockIdx.y, vi = v_off + blockIdx.x;
+    const df* qn = G.n3v + G.N3v;
+    df w = G.n2w[wi], ve = G.n2v[vi];
+    const int tid = threadIdx.x, o = tid & 15, q = tid >> 4;
+    const int A = o >> 2, C = o & 3;
+    float2 acc = make_float2(0.f, 0.f);
+    // spin term s uses up-up on the left for s = 0 and on the right for s = 1 (t channel)
+    const float2* T0 = Tab + ((size_t)wi * NS) * J.nq * 16;
+    const float2* T1 = T0 + (size_t)J.nq * 16;
+#pragma unroll 1
+    for (int j0 = 1; j0 < J.nq - 1; j0 += 128) {
+        int j = j0 + tid;
+        float2 g[16];
+        const bool valid = j < J.nq - 1;
+        if (valid) {
+            if (RIGHT) vertex_part_f32<R>(V, G, PARTS_UD, true, 32, w, qn[j], ve, g);
+            else vertex_part_f32<R>(V, G, PARTS_UD, false, 32, w, ve, qn[j], g);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) g[c] = make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) rec[0][tid][c] = g[c];
+        if (NS == 2) {
+            if (valid) {
+                if (RIGHT) vertex_part_f32<R>(V, G, PARTS_X, true, 32, w, qn[j], ve, g, true);
+                else vertex_part_f32<R>(V, G, PARTS_X, false, 32, w, ve, qn[j], g, true);
+            }
+#pragma unroll
+            for (int c = 0; c < 16; ++c) rec[NS - 1][tid][c] = g[c];
+        }
+        __syncthreads();
+        int nrec = min(128, J.nq - 1 - j0);
+#pragma unroll 1
+        for (int rr = q; rr < nrec; rr += 8) {
+            const float2* t0 = T0 + (size_t)(j0 + rr) * 16;
+            if (NS == 1) {
+                if (!RIGHT) {
+#pragma unroll
+                    for (int B = 0; B < 4; ++B) cmac2(acc, rec[0][rr][cmap<R>(A, B)], ld_stream(t0 + 4 * B + C));
+                } else {
+#pragma unroll
+                    for (int D = 0; D < 4; ++D) cmac2(acc, ld_stream(t0 + 4 * A + D), rec[0][rr][cmap<R>(D, C)]);
+                }
+            } else {
+                const float2* t1 = T1 + (size_t)(j0 + rr) * 16;
+                if (!RIGHT) {
+#pragma unroll
+                    for (int B = 0; B < 4; ++B) {
+                        cmac2(acc, rec[NS - 1][rr][cmap<R>(A, B)], ld_stream(t0 + 4 * B + C));
+                        cmac2(acc, rec[0][rr][cmap<R>(A, B)], ld_stream(t1 + 4 * B + C));
+                    }
+                } else {
+#pragma unroll
+                    for (int D = 0; D < 4; ++D) {
+                        cmac2(acc, ld_stream(t0 + 4 * A + D), rec[0][rr][cmap<R>(D, C)]);
+                        cmac2(acc, ld_stream(t1 + 4 * A + D), rec[NS - 1][rr][cmap<R>(D, C)]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    k2_tail<RIGHT, R>(V, G, J, Ssum, Ntil, out, odt, wi, vi, w, ve, acc, rec, red);
+}
+
+// K2 / K2' from the record cache (k_mx_cache_k2): the same sums as k_mx_k2, with each
+// thread taking whole records — its node's 16-component record(s) and the node's
+// propagator-vertex table, both streamed from memory (a warp reads 32 consecutive 128-byte
+// records) — and all 16 outputs of a record in registers (64 complex MACs per record), so
+// the node loop is bound by HBM rather than by shared-memory traffic.  The 128 partial
+// outputs are then reduced into the (A, C)-per-thread layout of k2_tail.
+template <bool RIGHT, int R>
+__global__ void __launch_bounds__(128, 4) k_mx_k2_rc(VertexF V, DfGrids G, MixedJob J, const float2* __restrict__ Tab,
+                                                  const double2* __restrict__ Ssum, const double2* __restrict__ Ntil,
+                                                  void* out, int odt, int w_off, int v_off,
+                                                  const float2* __restrict__ cache) {
+    constexpr int NS = (R == KB_CH_T) ? 2 : 1;
+    __shared__ float2 rec[NS][128][17];
+    __shared__ float2 red[8][16];
+    const int wi = w_off + blockIdx.y, vi = v_off + blockIdx.x;
+    const df w = G.n2w[wi], ve = G.n2v[vi];
+    const int tid = threadIdx.x;
+    const float2* T0 = Tab + ((size_t)wi * NS) * J.nq * 16;
+    const float2* T1 = T0 + (size_t)J.nq * 16;
+    const float4* base = reinterpret_cast<const float4*>(cache + (((size_t)wi * G.N2v + vi) * (J.nq - 2)) * NS * 16);
+    float2 o16[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) o16[c] = make_float2(0.f, 0.f);
+    // out[A][C] += sum_B rec[cmap(A, B)] T[B][C]  (left)  or  sum_D T[A][D] rec[cmap(D, C)]  (right)
+    auto contract = [&](const float4* rp, const float2* tp) {
+        float2 rv[16], tv[16];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float4 u = ld_stream4(rp + i);
+            rv[2 * i] = make_float2(u.x, u.y);
+            rv[2 * i + 1] = make_float2(u.z, u.w);
+            const float4 t = ld_stream4(reinterpret_cast<const float4*>(tp) + i);
+            tv[2 * i] = make_float2(t.x, t.y);
+            tv[2 * i + 1] = make_float2(t.z, t.w);
+        }
+#pragma unroll
+        for (int A = 0; A < 4; ++A)
+#pragma unroll
+            for (int C = 0; C < 4; ++C)
+#pragma unroll
+                for (int B = 0; B < 4; ++B) {
+                    if (!RIGHT) cmac2(o16[4 * A + C], rv[cmap<R>(A, B)], tv[4 * B + C]);
+                    else cmac2(o16[4 * A + C], tv[4 * A + B], rv[cmap<R>(B, C)]);
+                }
+    };
+#pragma unroll 1
+    for (int j = 1 + tid; j < J.nq - 1; j += 128) {
+        const float4* rp = base + (size_t)(j - 1) * NS * 8;
+        if (NS == 1) {
+            contract(rp, T0 + (size_t)j * 16);
+        } else if (!RIGHT) {
+            contract(rp + 8, T0 + (size_t)j * 16);       // up-up record with table 0
+            contract(rp, T1 + (size_t)j * 16);           // up-down record with table 1
+        } else {
+            contract(rp, T0 + (size_t)j * 16);
+            contract(rp + 8, T1 + (size_t)j * 16);
+        }
+    }
+    // partials of the 128 threads -> thread (q, o) sums those of threads q, q + 8, ...
+#pragma unroll
+    for (int c = 0; c < 16; ++c) rec[0][tid][c] = o16[c];
+    __syncthreads();
+    const int o = tid & 15, q = tid >> 4;
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const float2 v = rec[0][q + 8 * i][o];
+        acc.x += v.x;
+        acc.y += v.y;
+    }
+    __syncthreads();
+    k2_tail<RIGHT, R>(V, G, J, Ssum, Ntil, out, odt, wi, vi, w, ve, acc, rec, red);
 }
 
 // TF32 split of an FP32 value: hi rounded to the 10-bit TF32 mantissa, lo = x - hi
@@ -750,6 +888,18 @@ static VertexF to_vf(const VertexDev& V, kb_ctx* ctx, bool& ok) {
     return F;
 }
 
+// The record cache of `slot` for channel r and side (0 left, 1 right), if it was built from
+// the slot's current state.
+static const float2* valid_cache(const kb_ctx* ctx, int slot, int r, int side) {
+    const kb_ctx::RecCache& c = ctx->rc[slot];
+    if (!c.ptr[side] || !((c.sides >> side) & 1) || c.channel != r || c.gen != ctx->slot_gen[slot]) return nullptr;
+    return static_cast<const float2*>(c.ptr[side]);
+}
+
+static size_t cache_side_bytes(const Grids& g, int r) {
+    return (size_t)g.n2w * g.n2v * (size_t)(g.nq - 2) * ((r == KB_CH_T) ? 2 : 1) * 16 * sizeof(float2);
+}
+
 // Workspace layout of one mixed-precision bubble of channel r (byte offsets into the
 // context's workspace) and the bytes it needs.
 struct MixedLayout {
@@ -795,6 +945,28 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
     VertexF VL = to_vf(ctx->slots[sl], ctx, ok1), VR = to_vf(ctx->slots[sr], ctx, ok2);
     if (!ok1 || !ok2) return KB_ERR_ARG;
     const VertexDev& VO = ctx->slots[so];
+    // The r-independent parts L0 = R + K1_r + K2'_r of the left vertex and R0 = R + K1_r + K2_r
+    // of the right one vanish when a slot has no bare part and leaves channel r out of its
+    // channel mask (the vertex gamma_rbar of the multiloop parts): then K1 = L0 Pi R0 and
+    // K2' = L0 Pi R^v' (left) or K2 = L^v Pi R0 (right) are zero, and only beta * out remains.
+    {
+        unsigned zero = 0;
+        const VertexDev& SL = ctx->slots[sl];
+        const VertexDev& SR = ctx->slots[sr];
+        if (!SL.has_R && !((SL.mask >> r) & 1)) zero |= (1u << KB_K1) | (1u << KB_K2P);
+        if (!SR.has_R && !((SR.mask >> r) & 1)) zero |= (1u << KB_K1) | (1u << KB_K2);
+        zero &= mask;
+        if (zero && beta != 1.0) {
+            for (int k = 0; k < 4; ++k) {
+                if (!((zero >> k) & 1)) continue;
+                const size_t n = (k == KB_K1 ? (size_t)g.n1 : (size_t)g.n2w * g.n2v) * 16;
+                KB_LAUNCH(ctx, st, "k_mx_scale_class");
+                k_mx_scale_class<<<(unsigned)std::min<size_t>((n + 255) / 256, 1216), 256, 0, st>>>(
+                    const_cast<void*>(VO.cls[r][k]), VO.dt[r][k], n, beta);
+            }
+        }
+        mask &= ~zero;
+    }
     // a bubble of a declared-symmetric vertex with itself: compute the independent part only
     const bool sym = (sl == sr) && ctx->slots[sl].symmetric && beta == 0.0 &&
                      (!((mask >> KB_K2P) & 1) || ((mask >> KB_K2) & 1)) && std::getenv("KB_NO_SYMMETRY") == nullptr;
@@ -857,17 +1029,31 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
             k_mx_ntilde<<<dim3((g.n3v * 16 + 127) / 128, g.n2w, ns * (t0 == 1 ? 1 : nt)), 128, 0, st>>>(
                 Nt, Mt, G, g.nq, ns, t0, Ntl);
         }
+        const float2* cacheL = valid_cache(ctx, sl, r, 0);
+        const float2* cacheR = valid_cache(ctx, sr, r, 1);
         if ((mask >> KB_K2) & 1) {
-            KB_LAUNCH(ctx, st, "k_mx_k2");
             int w_off = (sym && r != KB_CH_P) ? g.n2w / 2 : 0, v_off = (sym && r == KB_CH_P) ? g.n2v / 2 : 0;
-            k_mx_k2<false, r><<<dim3(g.n2v - v_off, g.n2w - w_off), 128, 0, st>>>(
-                VL, G, J, Nt, Ss, Ntl, const_cast<void*>(VO.cls[r][KB_K2]), VO.dt[r][KB_K2], w_off, v_off);
+            void* o = const_cast<void*>(VO.cls[r][KB_K2]);
+            const dim3 grid(g.n2v - v_off, g.n2w - w_off);
+            if (cacheL) {
+                KB_LAUNCH(ctx, st, "k_mx_k2c");
+                k_mx_k2_rc<false, r><<<grid, 128, 0, st>>>(VL, G, J, Nt, Ss, Ntl, o, VO.dt[r][KB_K2], w_off, v_off,
+                                                           cacheL);
+            } else {
+                KB_LAUNCH(ctx, st, "k_mx_k2");
+                k_mx_k2<false, r><<<grid, 128, 0, st>>>(VL, G, J, Nt, Ss, Ntl, o, VO.dt[r][KB_K2], w_off, v_off);
+            }
         }
         if (!sym && ((mask >> KB_K2P) & 1)) {
-            KB_LAUNCH(ctx, st, "k_mx_k2p");
-            k_mx_k2<true, r><<<dim3(g.n2v, g.n2w), 128, 0, st>>>(VR, G, J, Mt, Ss, Ntl,
-                                                              const_cast<void*>(VO.cls[r][KB_K2P]), VO.dt[r][KB_K2P],
-                                                              0, 0);
+            void* o = const_cast<void*>(VO.cls[r][KB_K2P]);
+            if (cacheR) {
+                KB_LAUNCH(ctx, st, "k_mx_k2pc");
+                k_mx_k2_rc<true, r><<<dim3(g.n2v, g.n2w), 128, 0, st>>>(VR, G, J, Mt, Ss, Ntl, o, VO.dt[r][KB_K2P], 0,
+                                                                        0, cacheR);
+            } else {
+                KB_LAUNCH(ctx, st, "k_mx_k2p");
+                k_mx_k2<true, r><<<dim3(g.n2v, g.n2w), 128, 0, st>>>(VR, G, J, Mt, Ss, Ntl, o, VO.dt[r][KB_K2P], 0, 0);
+            }
         }
     }
     if ((mask >> KB_K3) & 1) {
@@ -949,4 +1135,108 @@ kb_status kb_bubble_mixed(kb_ctx* ctx, int r, int sl, int sr, int so, int pi_kin
     if (r == KB_CH_A) return mixed_impl<KB_CH_A>(ctx, sl, sr, so, pi_kind, mask, alpha, beta, st);
     if (r == KB_CH_P) return mixed_impl<KB_CH_P>(ctx, sl, sr, so, pi_kind, mask, alpha, beta, st);
     return mixed_impl<KB_CH_T>(ctx, sl, sr, so, pi_kind, mask, alpha, beta, st);
+}
+
+void kb_vertex_cache_free(kb_ctx* ctx, int slot) {
+    kb_ctx::RecCache& c = ctx->rc[slot];
+    for (int side = 0; side < 2; ++side) {
+        if (c.ptr[side]) cudaFree(c.ptr[side]);
+        c.ptr[side] = nullptr;
+        c.bytes[side] = 0;
+    }
+    c.channel = -1;
+    c.sides = 0;
+    c.gen = ~0ull;
+}
+
+kb_status kb_vertex_cache_prepare(kb_ctx* ctx, int slot, int channel, unsigned sides) {
+    if (!ctx) return KB_ERR_ARG;
+    if (slot < 0 || slot >= KB_MAX_SLOTS || channel < 0 || channel > 2 || sides < 1 || sides > 3) {
+        ctx->err = "kb_vertex_cache: bad slot, channel or sides";
+        return KB_ERR_ARG;
+    }
+    if (!ctx->grids_set || !ctx->slot_set[slot]) {
+        ctx->err = "kb_vertex_cache: set the grids and the vertex first";
+        return KB_ERR_STATE;
+    }
+    bool ok;
+    to_vf(ctx->slots[slot], ctx, ok);
+    if (!ok) return KB_ERR_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return KB_ERR_CUDA;
+    kb_ctx::RecCache& c = ctx->rc[slot];
+    const size_t need = cache_side_bytes(ctx->g, channel);
+    for (int side = 0; side < 2; ++side) {
+        if (!((sides >> side) & 1)) continue;
+        if (c.ptr[side] && c.bytes[side] == need) continue;
+        if (c.ptr[side]) cudaFree(c.ptr[side]);
+        c.ptr[side] = nullptr;
+        c.bytes[side] = 0;
+        cudaError_t e = cudaMalloc(&c.ptr[side], need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c.ptr[side] = nullptr;
+            ctx->err = "kb_vertex_cache: cannot allocate the record cache";
+            return e == cudaErrorMemoryAllocation ? KB_ERR_OOM : KB_ERR_CUDA;
+        }
+        c.bytes[side] = need;
+    }
+    c.channel = channel;
+    c.sides = sides;
+    c.gen = ctx->slot_gen[slot];
+    return kb_ensure_workspace(ctx, mixed_layout(ctx, channel, 0).off_N);
+}
+
+template <int r>
+static void cache_launch(kb_ctx* ctx, int slot, const VertexF& V, unsigned sides, cudaStream_t st) {
+    const Grids& g = ctx->g;
+    const size_t ntab = (size_t)g.n1 + g.n2w + g.n2v + g.n3w + g.n3v + g.nq;
+    df* tab = reinterpret_cast<df*>(static_cast<char*>(ctx->ws.ptr) + mixed_layout(ctx, r, 0).off_tab);
+    DfGrids G;
+    G.n1 = tab; G.n2w = G.n1 + g.n1; G.n2v = G.n2w + g.n2w; G.n3w = G.n2v + g.n2v; G.n3v = G.n3w + g.n3w;
+    G.N1 = g.n1; G.N2w = g.n2w; G.N2v = g.n2v; G.N3w = g.n3w; G.N3v = g.n3v; G.A = (float)g.A;
+    {
+        KB_LAUNCH(ctx, st, "k_mx_tables");
+        k_mx_tables<<<(unsigned)((ntab + 255) / 256), 256, 0, st>>>(g.n1, g.n2w, g.n2v, g.n3w, g.n3v, g.nq, g.A, ctx->d_xq,
+                                                                    tab);
+    }
+    const dim3 grid((unsigned)((g.nq - 2 + 127) / 128), g.n2v, g.n2w);
+    for (int side = 0; side < 2; ++side) {
+        if (!((sides >> side) & 1)) continue;
+        KB_LAUNCH(ctx, st, "k_mx_cache_k2");
+        float2* dst = static_cast<float2*>(ctx->rc[slot].ptr[side]);
+        if (side == 0) k_mx_cache_k2<false, r><<<grid, 128, 0, st>>>(V, G, g.nq, dst);
+        else k_mx_cache_k2<true, r><<<grid, 128, 0, st>>>(V, G, g.nq, dst);
+    }
+}
+
+kb_status kb_vertex_cache_launch(kb_ctx* ctx, int slot, int channel, unsigned sides, cudaStream_t st) {
+    const kb_ctx::RecCache& c = ctx->rc[slot];
+    if (c.channel != channel || (c.sides & sides) != sides || c.gen != ctx->slot_gen[slot]) {
+        ctx->err = "kb_vertex_cache: cache not prepared for this slot state";
+        return KB_ERR_STATE;
+    }
+    bool ok;
+    VertexF V = to_vf(ctx->slots[slot], ctx, ok);
+    if (!ok) return KB_ERR_ARG;
+    if (channel == KB_CH_A) cache_launch<KB_CH_A>(ctx, slot, V, sides, st);
+    else if (channel == KB_CH_P) cache_launch<KB_CH_P>(ctx, slot, V, sides, st);
+    else cache_launch<KB_CH_T>(ctx, slot, V, sides, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { ctx->err = std::string("kb_vertex_cache: ") + cudaGetErrorString(e); return KB_ERR_CUDA; }
+    return KB_OK;
+}
+
+extern "C" kb_status kb_vertex_cache(kb_ctx* ctx, int slot, int channel, unsigned sides, void* stream) {
+    kb_status s = kb_vertex_cache_prepare(ctx, slot, channel, sides);
+    if (s != KB_OK) return s;
+    return kb_vertex_cache_launch(ctx, slot, channel, sides, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" kb_status kb_vertex_uncache(kb_ctx* ctx, int slot) {
+    if (!ctx) return KB_ERR_ARG;
+    if (slot < 0 || slot >= KB_MAX_SLOTS) { ctx->err = "kb_vertex_uncache: bad slot"; return KB_ERR_ARG; }
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    kb_vertex_cache_free(ctx, slot);
+    return KB_OK;
 }

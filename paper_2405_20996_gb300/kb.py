@@ -43,7 +43,7 @@ class kb_bubble_desc(C.Structure):
                 ("beta", C.c_double), ("precision", C.c_int), ("op", C.c_int)]
 
 
-KB_OP_BUBBLE, KB_OP_ADD, KB_OP_JOIN = 0, 1, 2
+KB_OP_BUBBLE, KB_OP_ADD, KB_OP_JOIN, KB_OP_CACHE = 0, 1, 2, 3
 KB_ERR_TOO_LARGE = 7
 KB_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -63,6 +63,8 @@ _SIGS = {
     "kb_bubble_vjp": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_double, C.c_int,
                       C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
     "kb_vertex_add": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_double, C.c_void_p],
+    "kb_vertex_cache": [C.c_void_p, C.c_int, C.c_int, C.c_uint, C.c_void_p],
+    "kb_vertex_uncache": [C.c_void_p, C.c_int],
     "kb_graph_create": [C.POINTER(C.c_void_p), C.POINTER(kb_bubble_desc), C.c_int],
     "kb_graph_launch": [C.c_void_p, C.c_void_p],
     "kb_graph_kernel_count": [C.c_void_p, C.POINTER(C.c_ulonglong)],
@@ -177,6 +179,20 @@ def kb_vertex_add(ctx, channel, slot_src, slot_dst, class_mask=KB_MASK_ALL, alph
 def kb_add_desc(ctx, channel, slot_src, slot_dst, class_mask=KB_MASK_ALL, alpha=1.0):
     """Step-graph entry: slot_dst += alpha * slot_src (classes of one channel)."""
     return kb_bubble_desc(ctx, channel, slot_src, -1, slot_dst, 0, class_mask, alpha, 0.0, 0, KB_OP_ADD)
+
+
+def kb_vertex_cache(ctx, slot, channel, sides=3, stream=0):
+    _check(ctx, lib().kb_vertex_cache(ctx, slot, channel, sides, stream))
+
+
+def kb_vertex_uncache(ctx, slot):
+    _check(ctx, lib().kb_vertex_uncache(ctx, slot))
+
+
+def kb_cache_desc(ctx, channel, slot, sides=3):
+    """Step-graph entry: rebuild the record cache of `slot` for `channel` (sides bit 0 left,
+    bit 1 right) at every replay."""
+    return kb_bubble_desc(ctx, channel, slot, -1, -1, 0, sides, 0.0, 0.0, 0, KB_OP_CACHE)
 
 
 def kb_join_desc():

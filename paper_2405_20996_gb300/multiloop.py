@@ -17,7 +17,10 @@ order l - 1 of all channels.  The slot γ̇^(l) serves as the output of order l 
 writes its channel) and, with its channel mask excluding r, as the vertex γ̇_r̄^(l-1) of
 the next order.  L_r^(l) is computed once into its own slot (it is the right vertex of the
 next order's central part, a channel-r-only vertex without bare part) and added to γ̇_r^(l)
-by the library's slot addition.
+by the library's slot addition.  Γ is the same in all 45 bubbles, so its records for the
+K2 and K2' contractions of channel r (the other channels at the converted frequencies, per
+(w, v, node)) are gathered once per step into a record cache that the later bubbles of that
+channel stream from HBM.
 """
 
 import torch
@@ -39,10 +42,13 @@ def _s_left(l, n_loops):       # L^(l), l = 2 .. n_loops - 1
 
 class MultiloopStep:
     def __init__(self, grids, nq, U, Delta, T, vertex, n_loops=6, precision="mixed", A=5.0, device=0,
-                 symmetric=True, channels=(0, 1, 2)):
+                 symmetric=True, channels=(0, 1, 2), cache="left", reserve_bytes=40 << 30):
         """vertex: {channel: (K1, K2, K2p, K3)} arrays of the reducible vertices γ_r (the bare
         part U/2 is added by the library).  precision "mixed" keeps every vertex in complex64,
-        "fp64" in complex128."""
+        "fp64" in complex128.  cache (mixed only): build the record cache of Γ's left side
+        (the K2 records of the first order and of the central parts; the right parts' K2 and
+        the left parts' K2' are zero classes, not computed) once per step: "left", where it
+        fits in the free device memory less reserve_bytes; True: both sides; False: none."""
         assert n_loops >= 1
         assert _s_left(n_loops - 1, n_loops) < kb.KB_MAX_SLOTS
         self.n_loops, self.precision = n_loops, precision
@@ -77,6 +83,16 @@ class MultiloopStep:
                 e.tensors[_s_left(l, n_loops)] = {}
                 for k in range(4):
                     e.attach(_s_left(l, n_loops), r, k, self.lefts[l][r][k])
+        self.cached = {}                                  # channel -> sides (bit 0 left, 1 right)
+        if cache and precision == "mixed":
+            side_bytes = lambda r: grids["n2w"] * grids["n2v"] * (nq - 2) * (2 if r == 2 else 1) * 128
+            budget = torch.cuda.mem_get_info(dev)[0] - reserve_bytes if cache == "left" else float("inf")
+            used = 0
+            for side in ((0,) if cache == "left" else (0, 1)):
+                for r in self.channels:
+                    if used + side_bytes(r) <= budget:
+                        self.cached[r] = self.cached.get(r, 0) | (1 << side)
+                        used += side_bytes(r)
         self.descs = self._descs()
         self.graph = None
 
@@ -94,6 +110,8 @@ class MultiloopStep:
         L, prec, d = self.n_loops, self.precision, []
         G = S_GAMMA
         for r, e in self.e.items():
+            if r in self.cached:
+                d.append(kb.kb_cache_desc(e.ctx, r, G, self.cached[r]))       # Γ's records
             d.append(e.desc(r, G, G, _s_order(1), pi_kind=kb.KB_PI_GS_SG, precision=prec))
         for l in range(2, L + 1):
             d.append(kb.kb_join_desc())
@@ -137,7 +155,9 @@ class MultiloopStep:
         for x in self.descs:
             if x.op == kb.KB_OP_JOIN:
                 continue
-            if x.op == kb.KB_OP_ADD:
+            if x.op == kb.KB_OP_CACHE:
+                kb.kb_vertex_cache(x.ctx, x.slot_left, x.channel, x.class_mask, st)
+            elif x.op == kb.KB_OP_ADD:
                 kb.kb_vertex_add(x.ctx, x.channel, x.slot_left, x.out_slot, x.class_mask, x.alpha, st)
             else:
                 kb.kb_bubble(x.ctx, x.channel, x.slot_left, x.slot_right, x.out_slot, x.pi_kind, x.class_mask,

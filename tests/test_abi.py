@@ -64,3 +64,9 @@ def test_graph_descriptor_layout_matches_header(tmp_path):
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     D = kb.kb_bubble_desc
     assert got == [ctypes.sizeof(D), D.alpha.offset, D.precision.offset, D.op.offset]
+
+
+def test_record_cache_calls_rejected_without_context():
+    L = kb.lib()
+    assert L.kb_vertex_cache(None, 0, 0, 3, None) == kb.KB_ERR_ARG
+    assert L.kb_vertex_uncache(None, 0) == kb.KB_ERR_ARG
