@@ -361,7 +361,7 @@ def run_multiloop(args):
     g, nq, Ui, Ti = ML_SIZES[args.workload]
     dev = torch.device("cuda", 0)
     ml = MultiloopStep(g, nq, Ui, DELTA, Ti, S.seeded_vertex(g, Ui, seed=4242), n_loops=6, precision="mixed",
-                       cache={"off": False, "left": "left", "both": True}[args.ml_cache])
+                       cache={"off": False, "auto": "auto", "all": True}[args.ml_cache])
     for e in ml.e.values():
         e.set_workspace_limit(args.ws_gb << 30)
     stream = torch.cuda.current_stream(dev)
@@ -507,8 +507,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling captures)")
     ap.add_argument("--no-graph", action="store_true", help="eager launches instead of one step graph")
     ap.add_argument("--ws-gb", type=int, default=8, help="device workspace limit per context (GiB)")
-    ap.add_argument("--ml-cache", default="left", choices=["off", "left", "both"],
-                    help="multiloop workloads: record cache of the full vertex (off, left side, both sides)")
+    ap.add_argument("--ml-cache", default="auto", choices=["off", "auto", "all"],
+                    help="multiloop workloads: record cache of the full vertex (off, the useful sides, all sides)")
     ap.add_argument("--workload", default="step", choices=["step", "points32", "vjp", "multiloop", "multiloop-large"],
                     help="step: the default three-channel line; points32 / vjp / multiloop: the batching, "
                          "adjoint and multiloop paths")

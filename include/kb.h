@@ -216,19 +216,24 @@ kb_status kb_graph_destroy(kb_graph *graph);
 kb_status kb_vertex_add(kb_ctx *ctx, int channel, int slot_src, int slot_dst, unsigned class_mask, double alpha,
                         void *stream);
 
-/* Record cache of a vertex slot (mixed precision; Sec. II.D.1 class split): the part of
- * the slot's vertex that the K2 contraction of channel `channel` gathers at every node —
- * the other channels' classes at the converted frequencies, FP32, 16 components (two spin
- * records for t) — for every (w, v) of the K2 grids and every interior quadrature node:
- * side bit 0 as the left vertex (records at (w, v, v''_j)), bit 1 as the right vertex of
- * the K2' contraction (records at (w, v''_j, v')).  Each side takes
- * n2w * n2v * (nq - 2) * 128 bytes (twice that for t), allocated by the library.  Later
+/* Record cache of a vertex slot (mixed precision; Sec. II.D.1 class split), for the
+ * bubbles of channel `channel`.  Sides (bits of `sides`):
+ *   1  the part of the vertex that the K2 contraction gathers at every node as the left
+ *      vertex — the other channels' classes at the converted frequencies, FP32, 16
+ *      components (two spin records for t) — at every (w, v) of the K2 grids and interior
+ *      node: n2w * n2v * (nq - 2) * 128 bytes (twice that for t);
+ *   2  the same as the right vertex of the K2' contraction (records at (w, v''_j, v'));
+ *   4  the K3 left tile of every bosonic frequency (TF32 hi/lo planes as the tensor-core
+ *      contraction reads them): n3w * 4 * (4 n3v) * (4 nq) * 4 bytes (twice for t);
+ *   8  the K3 right tile with Π = G G folded in (used by bubbles with KB_PI_GG).
+ * Allocated by the library.  Later
  * mixed-precision bubbles of `channel` that have this slot on a cached side stream the
  * records instead of gathering them (the same FP32 records, summed in another order: the
  * results agree to FP32 rounding); a vertex that stays fixed over many bubbles (the full
  * vertex of a multiloop step, Sec. III.C) is then gathered once.  The cache reflects the slot's arrays when the build runs (asynchronous on
  * `stream`): rebuild it after changing their contents.  Any kb_set_vertex* call on the
- * slot or kb_set_grids makes it stale (then unused); kb_vertex_uncache frees it.
+ * slot, kb_set_grids, kb_set_model or kb_set_self_energy makes it stale (then unused);
+ * kb_vertex_uncache frees it.
  * KB_ERR_OOM if the cache does not fit. */
 kb_status kb_vertex_cache(kb_ctx *ctx, int slot, int channel, unsigned sides, void *stream);
 kb_status kb_vertex_uncache(kb_ctx *ctx, int slot);

@@ -159,6 +159,7 @@ kb_status kb_set_model(kb_ctx* ctx, double Delta, double T, double eps) {
     ctx->m.T = T;
     ctx->m.eps = eps;
     ctx->model_set = true;
+    for (int s = 0; s < KB_MAX_SLOTS; ++s) ++ctx->slot_gen[s];     // cached K3 right tiles hold Π
     return KB_OK;
 }
 
@@ -169,6 +170,7 @@ kb_status kb_set_self_energy(kb_ctx* ctx, int n_sig, double A_sig, const double*
     ctx->d_sig = nullptr;
     ctx->m.n_sig = 0;
     ctx->m.sigR = ctx->m.sigK = nullptr;
+    for (int s = 0; s < KB_MAX_SLOTS; ++s) ++ctx->slot_gen[s];
     if (!sigR) return KB_OK;
     if (n_sig < 1 || !(A_sig > 0)) { ctx->err = "kb_set_self_energy: n_sig >= 1, A_sig > 0"; return KB_ERR_ARG; }
     std::vector<double2> h(2 * (size_t)n_sig);

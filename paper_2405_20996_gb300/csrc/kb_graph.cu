@@ -59,7 +59,7 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
         if (d[i].op != KB_OP_BUBBLE && d[i].op != KB_OP_ADD && d[i].op != KB_OP_CACHE)
             return fail(c, "kb_graph_create: unknown entry kind", KB_ERR_ARG);
         if (d[i].channel < 0 || d[i].channel > 2 || (d[i].class_mask & ~KB_MASK_ALL) ||
-            (d[i].op == KB_OP_CACHE && (d[i].class_mask < 1 || d[i].class_mask > 3)) ||
+            (d[i].op == KB_OP_CACHE && (d[i].class_mask < 1 || d[i].class_mask > 15)) ||
             (d[i].op == KB_OP_BUBBLE && d[i].precision != KB_PREC_FP64 && d[i].precision != KB_PREC_MIXED))
             return fail(c, "kb_graph_create: descriptor out of range", KB_ERR_ARG);
         if (!index.count(c)) { index[c] = br.size(); br.push_back(Branch{c}); }

@@ -78,11 +78,12 @@ struct kb_ctx {
     // bumped by every change of a slot (and of the grids); a record cache is valid only for
     // the generation it was built from
     unsigned long long slot_gen[KB_MAX_SLOTS] = {};
-    // record caches (kb_vertex_cache): side 0 = the slot as left vertex of the K2
-    // contraction, side 1 = as right vertex of the K2' contraction, for one channel
+    // record caches (kb_vertex_cache), for one channel: side 0 = the slot's records as left
+    // vertex of the K2 contraction, 1 = as right vertex of the K2' contraction, 2 = its K3
+    // left tile, 3 = its K3 right tile (with Π = G G folded in)
     struct RecCache {
-        void* ptr[2] = {nullptr, nullptr};
-        size_t bytes[2] = {0, 0};
+        void* ptr[4] = {nullptr, nullptr, nullptr, nullptr};
+        size_t bytes[4] = {0, 0, 0, 0};
         int channel = -1;
         unsigned sides = 0;
         unsigned long long gen = ~0ull;

@@ -896,8 +896,11 @@ static const float2* valid_cache(const kb_ctx* ctx, int slot, int r, int side) {
     return static_cast<const float2*>(c.ptr[side]);
 }
 
-static size_t cache_side_bytes(const Grids& g, int r) {
-    return (size_t)g.n2w * g.n2v * (size_t)(g.nq - 2) * ((r == KB_CH_T) ? 2 : 1) * 16 * sizeof(float2);
+static size_t cache_side_bytes(const Grids& g, int r, int side) {
+    const size_t ns = (r == KB_CH_T) ? 2 : 1;
+    if (side < 2) return (size_t)g.n2w * g.n2v * (size_t)(g.nq - 2) * ns * 16 * sizeof(float2);
+    // K3 tile of every bosonic frequency: 4 planes x (4 n3v rows) x (4 ns nq columns), FP32
+    return (size_t)g.n3w * 4 * (4 * (size_t)g.n3v) * (4 * ns * (size_t)g.nq) * sizeof(float);
 }
 
 // Workspace layout of one mixed-precision bubble of channel r (byte offsets into the
@@ -1066,34 +1069,43 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
         double2* Cm = reinterpret_cast<double2*>(TB + (size_t)chunk * 4 * rows * K);
         void* scratch = reinterpret_cast<char*>(Cm) + (size_t)chunk * rows * rows * sizeof(double2);
         bool use_tc = std::getenv("KB_K3_SIMT") == nullptr;
+        const float* cacheL3 = reinterpret_cast<const float*>(valid_cache(ctx, sl, r, 2));
+        const float* cacheR3 =
+            pi_kind == KB_PI_GG ? reinterpret_cast<const float*>(valid_cache(ctx, sr, r, 3)) : nullptr;
         int w3_lo = (sym && r != KB_CH_P) ? g.n3w / 2 : 0;
         // p (symmetric): rows v >= 0 only, the rest by crossing (k_mx_tile3, symmetry fill)
         const int vh3 = (sym && r == KB_CH_P) ? g.n3v / 2 : 0;
         const int rowsL = 4 * (g.n3v - vh3), rowsR = (int)rows;
         for (int w0 = w3_lo; w0 < g.n3w; w0 += chunk) {
             int nwc = std::min(chunk, g.n3w - w0);
+            float* TAc = TA;
+            float* TBc = TB;
             if (sym) {
                 KB_LAUNCH(ctx, st, "k_mx_tile3_both");
                 k_mx_tile3<2, r><<<dim3((g.nq + 127) / 128, g.n3v - vh3, nwc), 128, 0, st>>>(VL, G, J, w0, 0, vh3, rowsL,
                                                                                            rowsR, P3, TA, TB);
             } else {
-                {
+                if (cacheL3) {
+                    TAc = const_cast<float*>(cacheL3) + (size_t)w0 * 4 * rowsL * K;      // cached left tile
+                } else {
                     KB_LAUNCH(ctx, st, "k_mx_tile3_left");
                     k_mx_tile3<0, r><<<dim3((g.nq + 127) / 128, g.n3v, nwc), 128, 0, st>>>(VL, G, J, w0, 0, 0, rowsL,
                                                                                            rowsR, P3, TA, nullptr);
                 }
-                {
+                if (cacheR3) {
+                    TBc = const_cast<float*>(cacheR3) + (size_t)w0 * 4 * rowsR * K;      // cached right tile
+                } else {
                     KB_LAUNCH(ctx, st, "k_mx_tile3_right");
                     k_mx_tile3<1, r><<<dim3((g.nq + 127) / 128, g.n3v, nwc), 128, 0, st>>>(VR, G, J, w0, 0, 0, rowsL,
                                                                                            rowsR, P3, TB, nullptr);
                 }
             }
             bool done = false;
-            if (use_tc) done = kb_tc_k3(ctx, TA, TB, Cm, rowsL, rowsR, (int)K, nwc, scratch, tc_scratch, st);
+            if (use_tc) done = kb_tc_k3(ctx, TAc, TBc, Cm, rowsL, rowsR, (int)K, nwc, scratch, tc_scratch, st);
             if (!done) {
                 KB_LAUNCH(ctx, st, "k_mx_cgemm");
                 k_mx_cgemm<<<dim3((unsigned)((rowsR + 63) / 64), (unsigned)((rowsL + 63) / 64), nwc), 256, 0, st>>>(
-                    TA, TB, Cm, rowsL, rowsR, (int)K);
+                    TAc, TBc, Cm, rowsL, rowsR, (int)K);
             }
             {
                 KB_LAUNCH(ctx, st, "k_mx_scatter3");
@@ -1139,7 +1151,7 @@ kb_status kb_bubble_mixed(kb_ctx* ctx, int r, int sl, int sr, int so, int pi_kin
 
 void kb_vertex_cache_free(kb_ctx* ctx, int slot) {
     kb_ctx::RecCache& c = ctx->rc[slot];
-    for (int side = 0; side < 2; ++side) {
+    for (int side = 0; side < 4; ++side) {
         if (c.ptr[side]) cudaFree(c.ptr[side]);
         c.ptr[side] = nullptr;
         c.bytes[side] = 0;
@@ -1151,7 +1163,7 @@ void kb_vertex_cache_free(kb_ctx* ctx, int slot) {
 
 kb_status kb_vertex_cache_prepare(kb_ctx* ctx, int slot, int channel, unsigned sides) {
     if (!ctx) return KB_ERR_ARG;
-    if (slot < 0 || slot >= KB_MAX_SLOTS || channel < 0 || channel > 2 || sides < 1 || sides > 3) {
+    if (slot < 0 || slot >= KB_MAX_SLOTS || channel < 0 || channel > 2 || sides < 1 || sides > 15) {
         ctx->err = "kb_vertex_cache: bad slot, channel or sides";
         return KB_ERR_ARG;
     }
@@ -1164,9 +1176,9 @@ kb_status kb_vertex_cache_prepare(kb_ctx* ctx, int slot, int channel, unsigned s
     if (!ok) return KB_ERR_ARG;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return KB_ERR_CUDA;
     kb_ctx::RecCache& c = ctx->rc[slot];
-    const size_t need = cache_side_bytes(ctx->g, channel);
-    for (int side = 0; side < 2; ++side) {
+    for (int side = 0; side < 4; ++side) {
         if (!((sides >> side) & 1)) continue;
+        const size_t need = cache_side_bytes(ctx->g, channel, side);
         if (c.ptr[side] && c.bytes[side] == need) continue;
         if (c.ptr[side]) cudaFree(c.ptr[side]);
         c.ptr[side] = nullptr;
@@ -1183,7 +1195,8 @@ kb_status kb_vertex_cache_prepare(kb_ctx* ctx, int slot, int channel, unsigned s
     c.channel = channel;
     c.sides = sides;
     c.gen = ctx->slot_gen[slot];
-    return kb_ensure_workspace(ctx, mixed_layout(ctx, channel, 0).off_N);
+    // the frequency tables (and, for the right K3 tile, the Π table) of the build
+    return kb_ensure_workspace(ctx, mixed_layout(ctx, channel, 0).off_T);
 }
 
 template <int r>
@@ -1206,6 +1219,31 @@ static void cache_launch(kb_ctx* ctx, int slot, const VertexF& V, unsigned sides
         float2* dst = static_cast<float2*>(ctx->rc[slot].ptr[side]);
         if (side == 0) k_mx_cache_k2<false, r><<<grid, 128, 0, st>>>(V, G, g.nq, dst);
         else k_mx_cache_k2<true, r><<<grid, 128, 0, st>>>(V, G, g.nq, dst);
+    }
+    if (sides & 12) {
+        // K3 tiles of all bosonic frequencies, as the non-symmetric bubble builds them
+        // chunk by chunk; the right tile with Π = G G folded in
+        MixedJob J;
+        J.r = r; J.pi_kind = KB_PI_GG; J.ns = (r == KB_CH_T) ? 2 : 1; J.nq = g.nq;
+        J.M = channel_maps(r); J.alpha = 1.0; J.beta = 0.0;
+        const MixedLayout Lo = mixed_layout(ctx, r, 1u << KB_K3);
+        float2* P3 = reinterpret_cast<float2*>(static_cast<char*>(ctx->ws.ptr) + Lo.off_P3);
+        const int rows = (int)Lo.rows;
+        const dim3 g3((g.nq + 127) / 128, g.n3v, g.n3w);
+        if (sides & 4) {
+            KB_LAUNCH(ctx, st, "k_mx_cache_tile3");
+            k_mx_tile3<0, r><<<g3, 128, 0, st>>>(V, G, J, 0, 0, 0, rows, rows, P3,
+                                                 static_cast<float*>(ctx->rc[slot].ptr[2]), nullptr);
+        }
+        if (sides & 8) {
+            {
+                KB_LAUNCH(ctx, st, "k_mx_pi3");
+                k_mx_pi3<<<dim3((g.nq + 127) / 128, g.n3w), 128, 0, st>>>(G, ctx->m, J, ctx->d_xq, ctx->d_wq, P3);
+            }
+            KB_LAUNCH(ctx, st, "k_mx_cache_tile3");
+            k_mx_tile3<1, r><<<g3, 128, 0, st>>>(V, G, J, 0, 0, 0, rows, rows, P3,
+                                                 static_cast<float*>(ctx->rc[slot].ptr[3]), nullptr);
+        }
     }
 }
 

@@ -42,13 +42,13 @@ def _s_left(l, n_loops):       # L^(l), l = 2 .. n_loops - 1
 
 class MultiloopStep:
     def __init__(self, grids, nq, U, Delta, T, vertex, n_loops=6, precision="mixed", A=5.0, device=0,
-                 symmetric=True, channels=(0, 1, 2), cache="left", reserve_bytes=40 << 30):
+                 symmetric=True, channels=(0, 1, 2), cache="auto", reserve_bytes=40 << 30):
         """vertex: {channel: (K1, K2, K2p, K3)} arrays of the reducible vertices γ_r (the bare
         part U/2 is added by the library).  precision "mixed" keeps every vertex in complex64,
-        "fp64" in complex128.  cache (mixed only): build the record cache of Γ's left side
-        (the K2 records of the first order and of the central parts; the right parts' K2 and
-        the left parts' K2' are zero classes, not computed) once per step: "left", where it
-        fits in the free device memory less reserve_bytes; True: both sides; False: none."""
+        "fp64" in complex128.  cache (mixed only): rebuild the record cache of Γ once per
+        step — "auto": its K3 tiles and its K2 records as left vertex (the right parts' K2 and
+        the left parts' K2' are zero classes, not computed), as far as they fit in the free
+        device memory less reserve_bytes; True: every side; False: none."""
         assert n_loops >= 1
         assert _s_left(n_loops - 1, n_loops) < kb.KB_MAX_SLOTS
         self.n_loops, self.precision = n_loops, precision
@@ -83,16 +83,28 @@ class MultiloopStep:
                 e.tensors[_s_left(l, n_loops)] = {}
                 for k in range(4):
                     e.attach(_s_left(l, n_loops), r, k, self.lefts[l][r][k])
-        self.cached = {}                                  # channel -> sides (bit 0 left, 1 right)
+        # record cache of Γ (mixed only): channel -> sides (bit 0: K2 records as left vertex,
+        # 1: K2' records as right vertex, 2: K3 left tile, 3: K3 right tile with Π = G G)
+        self.cached = {}
         if cache and precision == "mixed":
-            side_bytes = lambda r: grids["n2w"] * grids["n2v"] * (nq - 2) * (2 if r == 2 else 1) * 128
-            budget = torch.cuda.mem_get_info(dev)[0] - reserve_bytes if cache == "left" else float("inf")
+            ns = lambda r: 2 if r == 2 else 1
+            nbytes = {0: lambda r: grids["n2w"] * grids["n2v"] * (nq - 2) * ns(r) * 128,
+                      2: lambda r: grids["n3w"] * 4 * 4 * grids["n3v"] * 4 * ns(r) * nq * 4}
+            nbytes[1], nbytes[3] = nbytes[0], nbytes[2]
+            if cache == "auto":
+                # the sides that serve nonzero classes, in order of time saved per byte: the K3
+                # tiles (left: 9 bubbles per channel, right: 5), then the K2 records of the
+                # first order and the central parts
+                order = [(r, sd) for sd in (2, 3, 0) for r in self.channels]
+                budget = torch.cuda.mem_get_info(dev)[0] - reserve_bytes
+            else:
+                order = [(r, sd) for sd in (0, 1, 2, 3) for r in self.channels]
+                budget = float("inf")
             used = 0
-            for side in ((0,) if cache == "left" else (0, 1)):
-                for r in self.channels:
-                    if used + side_bytes(r) <= budget:
-                        self.cached[r] = self.cached.get(r, 0) | (1 << side)
-                        used += side_bytes(r)
+            for r, sd in order:
+                if used + nbytes[sd](r) <= budget:
+                    self.cached[r] = self.cached.get(r, 0) | (1 << sd)
+                    used += nbytes[sd](r)
         self.descs = self._descs()
         self.graph = None
 

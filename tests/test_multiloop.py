@@ -134,8 +134,9 @@ def test_mixed_step_tracks_fp64():
 
 def test_record_cache_matches_gather_and_goes_stale():
     """kb_vertex_cache: the K2 (left) and K2' (right) contractions of a cached vertex agree with
-    the gathering kernels to FP32 rounding (same records, another summation order); any
-    change of the slot makes the cache stale (then unused)."""
+    the gathering kernels to FP32 rounding (same records, another summation order), the K3
+    class from its cached tiles is bit-identical; any change of the slot makes the cache
+    stale (then unused)."""
     from paper_2405_20996_gb300 import kb
     from paper_2405_20996_gb300.engine import Engine
     cfg = RAGGED
@@ -154,14 +155,18 @@ def test_record_cache_matches_gather_and_goes_stale():
             e.alloc_out(2, channels=(r,), dtype=torch.complex64)
             e.alloc_out(3, channels=(r,), dtype=torch.complex64)
             if use_cache:
-                kb.kb_vertex_cache(e.ctx, 0, r, 3, torch.cuda.current_stream().cuda_stream)
+                kb.kb_vertex_cache(e.ctx, 0, r, 15, torch.cuda.current_stream().cuda_stream)
             kb.kb_profile_enable(e.ctx, True)
             e.bubble(r, 1, 0, 2, precision="mixed")          # Γ on the right: its K2' records
             e.bubble(r, 0, 1, 3, precision="mixed")          # Γ on the left: its K2 records
             torch.cuda.synchronize()
-            names = set(kb.kb_profile_read(e.ctx))
+            prof = kb.kb_profile_read(e.ctx)
+            names = set(prof)
             kb.kb_profile_enable(e.ctx, False)
             assert ({"k_mx_k2c", "k_mx_k2pc"} <= names) == use_cache, names
+            # K3: Γ's tiles come from the cache, only Y's are built
+            ntile = 1 if use_cache else 2
+            assert prof["k_mx_tile3_left"][1] == prof["k_mx_tile3_right"][1] == ntile, prof
             outs[(use_cache, r)] = {s: {k: t.cpu().numpy() for k, t in e.out(s, r).items()} for s in (2, 3)}
             if use_cache:
                 # re-attaching a class of the cached slot makes the cache stale
@@ -193,7 +198,7 @@ def test_cached_multiloop_step_matches_uncached():
     for cache in (False, True):
         ml = MultiloopStep(cfg["grids"], cfg["nq"], cfg["U"], cfg["Delta"], cfg["T"], vertex, n_loops=4,
                            precision="mixed", cache=cache)
-        assert ml.cached == ({0: 3, 1: 3, 2: 3} if cache else {})
+        assert ml.cached == ({0: 15, 1: 15, 2: 15} if cache else {})
         ml.zero()
         ml.run()
         torch.cuda.synchronize()
