@@ -11,14 +11,17 @@ asymptotic classes K1, K2, K2', K3 (Sec. II.D.1).  I_r is the vertex slot of Γ 
 channel r left out of the slot's channel mask; the library still reads channel r's data
 as the crossing partner of the up-up component, as the vertex requires.
 
-Two solvers; every bubble goes through the library's plain FP64 path:
+Two solvers; the residual bubbles go through the library's plain FP64 path:
 
 - the damped fixed point γ ← (1 − m) γ + m B(γ) with mixing m, the scheme the paper
   describes for its parquet solver, stopped on the relative maximum-norm change;
 - Newton–Krylov on F(γ) = γ − B(γ): each Newton step solves J δ = −F by restarted
   GMRES.  B_r is bilinear in its two vertices, so the Jacobian product is
       J v = v − Σ_r [B_r(V_I_r, Γ) + B_r(I_r, V)],   V = Σ_r v_r (no bare part),
-  two bubbles per channel; J^H comes from kb_bubble_vjp (`adjoint`).
+  two bubbles per channel; J^H comes from kb_bubble_vjp (`adjoint`), and with it the
+  adjoint sensitivity of an observable of the converged vertex to the coupling U
+  (`sensitivity_U`: one GMRES solve with J^H instead of one Newton solve per parameter).
+  The Jacobian products may use the mixed-precision bubble (`jvp_precision`).
 
 The state is one flat complex128 device vector holding the 12 class arrays; the vertex
 slots are views of it, so no data moves between a solver update and the next bubble.  The
@@ -40,14 +43,22 @@ S_DELTA = 4                 # V = v_a + v_p + v_t (a tangent or adjoint directio
 S_DELTA_I = (5, 6, 7)       # V − v_r
 S_OUT = 8                   # bubble outputs, all channels
 S_GRAD = 9                  # adjoint accumulation, all channels
+S_RHAT = 10                 # the bare vertex of unit strength, no classes (∂/∂U)
 
 
 class ParquetPA:
-    """Parquet-approximation solver of one parameter point (grids, Nq, U, Δ, T)."""
+    """Parquet-approximation solver of one parameter point (grids, Nq, U, Δ, T).
 
-    def __init__(self, grids, nq, U, Delta, T, A=5.0, eps=0.0, device=0):
+    jvp_precision="mixed" evaluates the Jacobian products of Newton–Krylov with the
+    mixed-precision bubble (complex64 copies of the state in a second context, FP32 gather,
+    3xTF32 contraction, ~1e-6 relative error) while the residual F(γ) stays FP64: the Newton
+    iteration is then inexact only in its linear model, and converges to the FP64 fixed
+    point."""
+
+    def __init__(self, grids, nq, U, Delta, T, A=5.0, eps=0.0, device=0, jvp_precision="fp64"):
         self.e = Engine(grids, nq, A=A, device=device)
         self.e.set_model(Delta, T, eps)
+        self.jvp_precision = jvp_precision
         self.U = float(U)
         self.dev = self.e.device
         sh = self.e.class_shapes()
@@ -68,17 +79,33 @@ class ParquetPA:
         self._attach(S_OUT, self.out, False, 7)
         self._attach(S_GRAD, self.grad, False, 7)
         self.bubbles = 0
+        self.mixed_bubbles = 0
+        if jvp_precision == "mixed":
+            self.m = Engine(grids, nq, A=A, device=device)
+            self.m.set_model(Delta, T, eps)
+            z32 = lambda: torch.zeros(self.n, dtype=torch.complex64, device=self.dev)
+            self.gamma32, self.delta32 = z32(), z32()
+            self._attach(S_GAMMA, self.gamma32, True, 7, e=self.m)
+            self._attach(S_DELTA, self.delta32, False, 7, e=self.m)
+            for r in range(3):
+                self._attach(S_I[r], self.gamma32, True, 7 & ~(1 << r), e=self.m)
+                self._attach(S_DELTA_I[r], self.delta32, False, 7 & ~(1 << r), e=self.m)
+            self._attach(S_OUT, self.out, False, 7, e=self.m)
+            self._gamma32_of = None
 
     def close(self):
         self.e.close()
+        if self.jvp_precision == "mixed":
+            self.m.close()
 
-    def _attach(self, slot, buf, has_R, mask):
-        kb.kb_set_vertex(self.e.ctx, slot, has_R, self.U)
-        kb.kb_set_vertex_channels(self.e.ctx, slot, mask)
-        kb.kb_set_vertex_symmetric(self.e.ctx, slot, False)
-        self.e.tensors[slot] = {}
+    def _attach(self, slot, buf, has_R, mask, e=None):
+        e = e or self.e
+        kb.kb_set_vertex(e.ctx, slot, has_R, self.U)
+        kb.kb_set_vertex_channels(e.ctx, slot, mask)
+        kb.kb_set_vertex_symmetric(e.ctx, slot, False)
+        e.tensors[slot] = {}
         for ch, k, shape, off, n in self.layout:
-            self.e.attach(slot, ch, k, buf[off:off + n].view(shape))
+            e.attach(slot, ch, k, buf[off:off + n].view(shape))
 
     def classes(self, buf, ch):
         """{"K1", "K2", "K2p", "K3"} views of channel ch of a flat state vector."""
@@ -101,7 +128,17 @@ class ParquetPA:
         return gamma - self.bse(gamma)
 
     def jvp(self, gamma, v):
-        """J v at γ for F(γ) = γ − B(γ)."""
+        """J v at γ for F(γ) = γ − B(γ) (in the precision chosen for the Jacobian products)."""
+        if self.jvp_precision == "mixed":
+            if self._gamma32_of is not gamma:              # one conversion per Newton step
+                self.gamma32.copy_(gamma)
+                self._gamma32_of = gamma
+            self.delta32.copy_(v)
+            for r in range(3):
+                self.m.bubble(r, S_DELTA_I[r], S_GAMMA, S_OUT, precision="mixed")
+                self.m.bubble(r, S_I[r], S_DELTA, S_OUT, beta=1.0, precision="mixed")
+            self.mixed_bubbles += 6
+            return v - self.out
         self.gamma.copy_(gamma)
         self.delta.copy_(v)
         for r in range(3):
@@ -138,9 +175,14 @@ class ParquetPA:
         return g, hist
 
     def gmres(self, gamma, rhs, rtol, m=30, maxit=300):
-        """Restarted GMRES(m) for J x = rhs at γ (Arnoldi with modified Gram–Schmidt; the
-        small least-squares problem min ||β e1 − H y|| solved on the host each step).
-        Returns (x, number of Jacobian products, relative residual)."""
+        """Restarted GMRES(m) for J x = rhs at γ.  Returns (x, Jacobian products, relative
+        residual)."""
+        return self._gmres(lambda v: self.jvp(gamma, v), rhs, rtol, m, maxit)
+
+    def _gmres(self, apply, rhs, rtol, m, maxit):
+        """Restarted GMRES(m) for A x = rhs, A given by apply(v) (Arnoldi with modified
+        Gram–Schmidt; the small least-squares problem min ||β e1 − H y|| solved on the host
+        each step)."""
         x = torch.zeros_like(rhs)
         bnorm = float(torch.linalg.vector_norm(rhs))
         if bnorm == 0.0:
@@ -156,7 +198,7 @@ class ParquetPA:
             H = np.zeros((m + 1, m), dtype=np.complex128)
             y = None
             for k in range(m):
-                w = self.jvp(gamma, V[k])
+                w = apply(V[k])
                 its += 1
                 for i in range(k + 1):
                     h = torch.vdot(V[i], w)
@@ -175,8 +217,27 @@ class ParquetPA:
                 x = x + complex(y[i]) * V[i]
             if res <= rtol or its >= maxit:
                 break
-            r = rhs - self.jvp(gamma, x)
+            r = rhs - apply(x)
         return x, its, res
+
+    # ---- adjoint sensitivities ------------------------------------------------------------
+    def dF_dU(self, gamma):
+        """∂F/∂U at fixed γ: F = γ − B(γ) with R = U R̂ in both I_r and Γ, and B bilinear, so
+        ∂F/∂U = −Σ_r [B_r(R̂, Γ) + B_r(I_r, R̂)] (R̂ the bare vertex of unit strength)."""
+        kb.kb_set_vertex(self.e.ctx, S_RHAT, True, 1.0)
+        self.gamma.copy_(gamma)
+        for r in range(3):
+            self.e.bubble(r, S_RHAT, S_GAMMA, S_OUT, precision="fp64")
+            self.e.bubble(r, S_I[r], S_RHAT, S_OUT, beta=1.0, precision="fp64")
+        self.bubbles += 6
+        return -self.out.clone()
+
+    def sensitivity_U(self, gamma, c, rtol=1e-10, m=30, maxit=300):
+        """d/dU of the observable L = Re<c, γ*> at a converged γ* = gamma, by the adjoint
+        method: solve J^H λ = c with GMRES on the adjoint kernels' products, then
+        dL/dU = −Re<λ, ∂F/∂U>.  Returns (dL/dU, adjoint products, relative residual)."""
+        lam, its, res = self._gmres(lambda u: self.adjoint(gamma, u), c, rtol, m, maxit)
+        return -float(torch.vdot(lam, self.dF_dU(gamma)).real), its, res
 
     def newton_krylov(self, tol=1e-10, maxit=30, gmres_m=30, gmres_maxit=300, gamma0=None):
         """Inexact Newton; returns (γ, history of relative residuals, GMRES products per step)."""

@@ -107,3 +107,43 @@ def test_jacobian_and_adjoint_are_transposes():
         assert float(Bv.abs().max()) > 1e-3 * float(v.abs().max())
         assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs, scale)
     pa.close()
+
+
+def test_newton_krylov_with_mixed_precision_jacobian_products():
+    """Jacobian products from the mixed-precision bubble (complex64 state copies, ~1e-6
+    relative error) and the residual in FP64: Newton-Krylov still reaches the FP64 fixed
+    point, because the inexact linear model only slows the (already fast) convergence."""
+    from paper_2405_20996_gb300.parquet import ParquetPA
+    ref = _solver(SMALL)
+    g_fp, h_fp = ref.fixed_point(mix=0.5, tol=1e-11)
+    ref.close()
+    pa = ParquetPA(SMALL["grids"], SMALL["nq"], SMALL["U"], SMALL["Delta"], SMALL["T"], jvp_precision="mixed")
+    g_nk, h_nk, lin = pa.newton_krylov(tol=1e-11)
+    assert h_nk[-1] <= 1e-11, (h_nk, lin)
+    assert len(h_nk) <= 10, (h_nk, lin)
+    assert pa.mixed_bubbles > 0 and pa.bubbles == 3 * len(h_nk)   # FP64 only for the residuals
+    assert pa.rel(g_fp - g_nk, g_fp) < 1e-9
+    pa.close()
+
+
+def test_adjoint_sensitivity_to_U_matches_central_difference():
+    """dL/dU of L = Re<c, γ*(U)> from one adjoint solve J^H λ = c (GMRES on the VJP kernels)
+    equals the central difference of two converged solves at U ± h."""
+    from paper_2405_20996_gb300.parquet import ParquetPA
+    cfg = dict(SMALL, U=1.0)
+    h = 1e-3
+    sols = {}
+    for U in (cfg["U"] - h, cfg["U"] + h, cfg["U"]):
+        pa = ParquetPA(cfg["grids"], cfg["nq"], U, cfg["Delta"], cfg["T"])
+        g, hist, _ = pa.newton_krylov(tol=1e-13)
+        assert hist[-1] <= 1e-13, hist
+        sols[U] = (pa, g)
+    pa, g0 = sols[cfg["U"]]
+    c = torch.randn(pa.n, dtype=torch.complex128, generator=torch.Generator().manual_seed(11)).to(pa.dev)
+    dL, its, res = pa.sensitivity_U(g0, c)
+    assert res <= 1e-10, (its, res)
+    L = lambda g: float(torch.vdot(c, g).real)
+    fd = (L(sols[cfg["U"] + h][1]) - L(sols[cfg["U"] - h][1])) / (2 * h)
+    assert abs(dL - fd) <= 1e-5 * abs(fd), (dL, fd, its)
+    for p_, _ in sols.values():
+        p_.close()
