@@ -221,7 +221,7 @@ kb_status kb_vertex_add(kb_ctx *ctx, int channel, int slot_src, int slot_dst, un
  *   1  the part of the vertex that the K2 contraction gathers at every node as the left
  *      vertex — the other channels' classes at the converted frequencies, FP32, 16
  *      components (two spin records for t) — at every (w, v) of the K2 grids and interior
- *      node: n2w * n2v * (nq - 2) * 128 bytes (twice that for t);
+ *      node: n2w * n2v * (nq - 2, rounded up to a multiple of 32) * 128 bytes (twice for t);
  *   2  the same as the right vertex of the K2' contraction (records at (w, v''_j, v'));
  *   4  the K3 left tile of every bosonic frequency (TF32 hi/lo planes as the tensor-core
  *      contraction reads them): n3w * 4 * (4 n3v) * (4 nq) * 4 bytes (twice for t);

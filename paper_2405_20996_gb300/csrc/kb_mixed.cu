@@ -313,28 +313,35 @@ __global__ void k_mx_scale_class(void* out, int dt, size_t n, double beta) {
 // Record cache of a vertex for the K2 (RIGHT = false) or K2' (RIGHT = true) contraction of
 // channel R: the records the node loop of k_mx_k2 gathers — the other channels' part of the
 // vertex at (w, v, v''_j) (left) or (w, v''_j, v') (right), FP32 — for every (w, v) of the
-// K2 grids and every interior node j = 1 .. nq-2, laid out [w][v][j-1][s][16] (s: the spin
-// records of the t channel, up-down then up-up).  One thread per record; a warp writes 32
-// consecutive 128-byte records.
+// K2 grids and every interior node j = 1 .. nq-2.  Layout: the interior nodes of one (w, v)
+// in blocks of 32 (the last one padded), and within a block node-minor:
+//   float4 index ((((w N2v + v) nblk + b) NS + s) 8 + p) 32 + l,   node j = 1 + 32 b + l,
+// p the 16-byte piece of the 16-component record and s the spin record of the t channel
+// (up-down, then up-up), so that 32 lanes reading the same piece read 512 contiguous bytes.
+__host__ __device__ constexpr int rc_blocks(int nq) { return (nq - 2 + 31) / 32; }
+
 template <bool RIGHT, int R>
 __global__ void __launch_bounds__(128) k_mx_cache_k2(VertexF V, DfGrids G, int nq, float2* __restrict__ cache) {
     constexpr int NS = (R == KB_CH_T) ? 2 : 1;
     const int wi = blockIdx.z, vi = blockIdx.y;
-    const int j = 1 + blockIdx.x * 128 + threadIdx.x;
-    if (j >= nq - 1) return;
+    const int jj = blockIdx.x * 128 + threadIdx.x;            // interior node index j - 1
+    if (jj >= nq - 2) return;
+    const int j = jj + 1, b = jj >> 5, l = jj & 31;
     const df* qn = G.n3v + G.N3v;
     const df w = G.n2w[wi], ve = G.n2v[vi];
     float2 g[16];
     if (RIGHT) vertex_part_f32<R>(V, G, PARTS_UD, true, 32, w, qn[j], ve, g);
     else vertex_part_f32<R>(V, G, PARTS_UD, false, 32, w, ve, qn[j], g);
-    float4* dst = reinterpret_cast<float4*>(cache + ((((size_t)wi * G.N2v + vi) * (nq - 2) + (j - 1)) * NS) * 16);
+    float4* dst = reinterpret_cast<float4*>(cache) +
+                  ((((size_t)wi * G.N2v + vi) * rc_blocks(nq) + b) * NS) * 8 * 32 + l;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) dst[i] = make_float4(g[2 * i].x, g[2 * i].y, g[2 * i + 1].x, g[2 * i + 1].y);
+    for (int i = 0; i < 8; ++i) dst[i * 32] = make_float4(g[2 * i].x, g[2 * i].y, g[2 * i + 1].x, g[2 * i + 1].y);
     if (NS == 2) {
         if (RIGHT) vertex_part_f32<R>(V, G, PARTS_X, true, 32, w, qn[j], ve, g, true);
         else vertex_part_f32<R>(V, G, PARTS_X, false, 32, w, ve, qn[j], g, true);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) dst[8 + i] = make_float4(g[2 * i].x, g[2 * i].y, g[2 * i + 1].x, g[2 * i + 1].y);
+        for (int i = 0; i < 8; ++i)
+            dst[(8 + i) * 32] = make_float4(g[2 * i].x, g[2 * i].y, g[2 * i + 1].x, g[2 * i + 1].y);
     }
 }
 
@@ -527,10 +534,10 @@ __global__ void __launch_bounds__(128, 4) k_mx_k2(VertexF V, DfGrids G, MixedJob
 }
 
 // K2 / K2' from the record cache (k_mx_cache_k2): the same sums as k_mx_k2, with each
-// thread taking whole records — its node's 16-component record(s) and the node's
-// propagator-vertex table, both streamed from memory (a warp reads 32 consecutive 128-byte
-// records) — and all 16 outputs of a record in registers (64 complex MACs per record), so
-// the node loop is bound by HBM rather than by shared-memory traffic.  The 128 partial
+// thread taking whole records — its node's 16-component record(s), read from the cache's
+// node-minor blocks (a warp's 16-byte loads cover 512 contiguous bytes), and its node's
+// propagator-vertex table row, which the warp loads coalesced into padded shared memory —
+// and all 16 outputs of a record in registers (64 complex MACs per record).  The 128 partial
 // outputs are then reduced into the (A, C)-per-thread layout of k2_tail.
 template <bool RIGHT, int R>
 __global__ void __launch_bounds__(128, 4) k_mx_k2_rc(VertexF V, DfGrids G, MixedJob J, const float2* __restrict__ Tab,
@@ -538,53 +545,66 @@ __global__ void __launch_bounds__(128, 4) k_mx_k2_rc(VertexF V, DfGrids G, Mixed
                                                   void* out, int odt, int w_off, int v_off,
                                                   const float2* __restrict__ cache) {
     constexpr int NS = (R == KB_CH_T) ? 2 : 1;
-    __shared__ float2 rec[NS][128][17];
+    // the node loop stages table rows (per warp 32 rows, 16 bytes padding) in the memory that
+    // holds the partial sums and the tail's records afterwards
+    constexpr size_t REC_BYTES = (size_t)NS * 128 * 17 * sizeof(float2), ROW_BYTES = 4 * 32 * 9 * sizeof(float4);
+    __shared__ __align__(16) unsigned char sm_raw[REC_BYTES > ROW_BYTES ? REC_BYTES : ROW_BYTES];
     __shared__ float2 red[8][16];
+    float2 (*rec)[128][17] = reinterpret_cast<float2 (*)[128][17]>(sm_raw);
+    float4 (*trow)[32][9] = reinterpret_cast<float4 (*)[32][9]>(sm_raw);
     const int wi = w_off + blockIdx.y, vi = v_off + blockIdx.x;
     const df w = G.n2w[wi], ve = G.n2v[vi];
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, wp = tid >> 5, ln = tid & 31;
+    const int nblk = rc_blocks(J.nq);
     const float2* T0 = Tab + ((size_t)wi * NS) * J.nq * 16;
     const float2* T1 = T0 + (size_t)J.nq * 16;
-    const float4* base = reinterpret_cast<const float4*>(cache + (((size_t)wi * G.N2v + vi) * (J.nq - 2)) * NS * 16);
+    const float4* base = reinterpret_cast<const float4*>(cache) + ((size_t)wi * G.N2v + vi) * nblk * NS * 8 * 32;
     float2 o16[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) o16[c] = make_float2(0.f, 0.f);
-    // out[A][C] += sum_B rec[cmap(A, B)] T[B][C]  (left)  or  sum_D T[A][D] rec[cmap(D, C)]  (right)
-    auto contract = [&](const float4* rp, const float2* tp) {
-        float2 rv[16], tv[16];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const float4 u = ld_stream4(rp + i);
-            rv[2 * i] = make_float2(u.x, u.y);
-            rv[2 * i + 1] = make_float2(u.z, u.w);
-            const float4 t = ld_stream4(reinterpret_cast<const float4*>(tp) + i);
-            tv[2 * i] = make_float2(t.x, t.y);
-            tv[2 * i + 1] = make_float2(t.z, t.w);
-        }
-#pragma unroll
-        for (int A = 0; A < 4; ++A)
-#pragma unroll
-            for (int C = 0; C < 4; ++C)
-#pragma unroll
-                for (int B = 0; B < 4; ++B) {
-                    if (!RIGHT) cmac2(o16[4 * A + C], rv[cmap<R>(A, B)], tv[4 * B + C]);
-                    else cmac2(o16[4 * A + C], tv[4 * A + B], rv[cmap<R>(B, C)]);
-                }
-    };
 #pragma unroll 1
-    for (int j = 1 + tid; j < J.nq - 1; j += 128) {
-        const float4* rp = base + (size_t)(j - 1) * NS * 8;
-        if (NS == 1) {
-            contract(rp, T0 + (size_t)j * 16);
-        } else if (!RIGHT) {
-            contract(rp + 8, T0 + (size_t)j * 16);       // up-up record with table 0
-            contract(rp, T1 + (size_t)j * 16);           // up-down record with table 1
-        } else {
-            contract(rp, T0 + (size_t)j * 16);
-            contract(rp + 8, T1 + (size_t)j * 16);
+    for (int b = wp; b < nblk; b += 4) {                // warp-uniform loop over node blocks
+        const int j = 1 + 32 * b + ln;
+        const bool valid = j < J.nq - 1;
+#pragma unroll
+        for (int pass = 0; pass < NS; ++pass) {
+            // pass 0 pairs table 0 with the up-down record (right) or the up-up one (left of t);
+            // pass 1 table 1 with the other spin record
+            const int srec = (NS == 1) ? 0 : (RIGHT ? pass : 1 - pass);
+            const float2* Tt = pass == 0 ? T0 : T1;
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int idx = q * 32 + ln, n = idx >> 3, piece = idx & 7;
+                const int jn = min(1 + 32 * b + n, J.nq - 1);
+                trow[wp][n][piece] = ld_stream4(reinterpret_cast<const float4*>(Tt + (size_t)jn * 16) + piece);
+            }
+            __syncwarp();
+            float2 rv[16], tv[16];
+            const float4* rp = base + ((size_t)b * NS + srec) * 8 * 32 + ln;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                float4 u = ld_stream4(rp + i * 32);
+                if (!valid) u = make_float4(0.f, 0.f, 0.f, 0.f);
+                rv[2 * i] = make_float2(u.x, u.y);
+                rv[2 * i + 1] = make_float2(u.z, u.w);
+                const float4 t = trow[wp][ln][i];
+                tv[2 * i] = make_float2(t.x, t.y);
+                tv[2 * i + 1] = make_float2(t.z, t.w);
+            }
+#pragma unroll
+            for (int A = 0; A < 4; ++A)
+#pragma unroll
+                for (int C = 0; C < 4; ++C)
+#pragma unroll
+                    for (int B = 0; B < 4; ++B) {
+                        if (!RIGHT) cmac2(o16[4 * A + C], rv[cmap<R>(A, B)], tv[4 * B + C]);
+                        else cmac2(o16[4 * A + C], tv[4 * A + B], rv[cmap<R>(B, C)]);
+                    }
         }
     }
     // partials of the 128 threads -> thread (q, o) sums those of threads q, q + 8, ...
+    __syncthreads();                                   // every warp is done with its table rows
 #pragma unroll
     for (int c = 0; c < 16; ++c) rec[0][tid][c] = o16[c];
     __syncthreads();
@@ -898,7 +918,7 @@ static const float2* valid_cache(const kb_ctx* ctx, int slot, int r, int side) {
 
 static size_t cache_side_bytes(const Grids& g, int r, int side) {
     const size_t ns = (r == KB_CH_T) ? 2 : 1;
-    if (side < 2) return (size_t)g.n2w * g.n2v * (size_t)(g.nq - 2) * ns * 16 * sizeof(float2);
+    if (side < 2) return (size_t)g.n2w * g.n2v * (size_t)rc_blocks(g.nq) * 32 * ns * 16 * sizeof(float2);
     // K3 tile of every bosonic frequency: 4 planes x (4 n3v rows) x (4 ns nq columns), FP32
     return (size_t)g.n3w * 4 * (4 * (size_t)g.n3v) * (4 * ns * (size_t)g.nq) * sizeof(float);
 }

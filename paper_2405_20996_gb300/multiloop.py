@@ -88,7 +88,7 @@ class MultiloopStep:
         self.cached = {}
         if cache and precision == "mixed":
             ns = lambda r: 2 if r == 2 else 1
-            nbytes = {0: lambda r: grids["n2w"] * grids["n2v"] * (nq - 2) * ns(r) * 128,
+            nbytes = {0: lambda r: grids["n2w"] * grids["n2v"] * ((nq - 2 + 31) // 32 * 32) * ns(r) * 128,
                       2: lambda r: grids["n3w"] * 4 * 4 * grids["n3v"] * 4 * ns(r) * nq * 4}
             nbytes[1], nbytes[3] = nbytes[0], nbytes[2]
             if cache == "auto":
