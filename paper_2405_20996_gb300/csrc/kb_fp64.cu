@@ -164,6 +164,11 @@ kb_status kb_bubble_fp64(kb_ctx* ctx, int r, int sl, int sr, int so, int pi_kind
     const Grids& g = ctx->g;
     int ns = (r == KB_CH_T) ? 2 : 1;
     size_t K = (size_t)4 * ns * g.nq;
+    // classes that vanish identically (a side without bare part and without channel r)
+    const unsigned zero = kb_zero_classes(ctx, r, sl, sr, mask);
+    s = kb_scale_classes(ctx, r, so, zero, beta, st);
+    if (s != KB_OK) return s;
+    mask &= ~zero;
     for (int cls = 0; cls < 4; ++cls) {
         if (!((mask >> cls) & 1)) continue;
         int nw, nL, nR, nvg;

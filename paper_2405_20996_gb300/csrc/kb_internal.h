@@ -133,6 +133,9 @@ kb_status kb_ensure_workspace(kb_ctx* ctx, size_t bytes);
 kb_status kb_vertex_cache_prepare(kb_ctx* ctx, int slot, int channel, unsigned sides);
 kb_status kb_vertex_cache_launch(kb_ctx* ctx, int slot, int channel, unsigned sides, cudaStream_t st);
 void kb_vertex_cache_free(kb_ctx* ctx, int slot);
+// classes of a bubble that vanish identically, and out <- beta * out for them (kb_ops.cu)
+unsigned kb_zero_classes(const kb_ctx* ctx, int r, int sl, int sr, unsigned mask);
+kb_status kb_scale_classes(kb_ctx* ctx, int r, int so, unsigned classes, double beta, cudaStream_t st);
 // slot arithmetic (kb_ops.cu)
 kb_status kb_vertex_add_impl(kb_ctx* ctx, int channel, int src, int dst, unsigned mask, double alpha,
                              cudaStream_t st);

@@ -296,20 +296,6 @@ __device__ __forceinline__ float4 ld_stream4(const float4* p) {
     return v;
 }
 
-// out <- beta * out over n complex elements (a class whose bubble part is identically zero:
-// alpha * 0 + beta * out).
-__global__ void k_mx_scale_class(void* out, int dt, size_t n, double beta) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        if (dt == KB_DT_C128) {
-            double2* p = reinterpret_cast<double2*>(out) + i;
-            *p = beta != 0.0 ? make_double2(beta * p->x, beta * p->y) : make_double2(0.0, 0.0);
-        } else {
-            float2* p = reinterpret_cast<float2*>(out) + i;
-            *p = beta != 0.0 ? make_float2((float)(beta * p->x), (float)(beta * p->y)) : make_float2(0.f, 0.f);
-        }
-    }
-}
-
 // Record cache of a vertex for the K2 (RIGHT = false) or K2' (RIGHT = true) contraction of
 // channel R: the records the node loop of k_mx_k2 gathers — the other channels' part of the
 // vertex at (w, v, v''_j) (left) or (w, v''_j, v') (right), FP32 — for every (w, v) of the
@@ -968,26 +954,11 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
     VertexF VL = to_vf(ctx->slots[sl], ctx, ok1), VR = to_vf(ctx->slots[sr], ctx, ok2);
     if (!ok1 || !ok2) return KB_ERR_ARG;
     const VertexDev& VO = ctx->slots[so];
-    // The r-independent parts L0 = R + K1_r + K2'_r of the left vertex and R0 = R + K1_r + K2_r
-    // of the right one vanish when a slot has no bare part and leaves channel r out of its
-    // channel mask (the vertex gamma_rbar of the multiloop parts): then K1 = L0 Pi R0 and
-    // K2' = L0 Pi R^v' (left) or K2 = L^v Pi R0 (right) are zero, and only beta * out remains.
+    // classes that vanish identically (a side without bare part and without channel r)
     {
-        unsigned zero = 0;
-        const VertexDev& SL = ctx->slots[sl];
-        const VertexDev& SR = ctx->slots[sr];
-        if (!SL.has_R && !((SL.mask >> r) & 1)) zero |= (1u << KB_K1) | (1u << KB_K2P);
-        if (!SR.has_R && !((SR.mask >> r) & 1)) zero |= (1u << KB_K1) | (1u << KB_K2);
-        zero &= mask;
-        if (zero && beta != 1.0) {
-            for (int k = 0; k < 4; ++k) {
-                if (!((zero >> k) & 1)) continue;
-                const size_t n = (k == KB_K1 ? (size_t)g.n1 : (size_t)g.n2w * g.n2v) * 16;
-                KB_LAUNCH(ctx, st, "k_mx_scale_class");
-                k_mx_scale_class<<<(unsigned)std::min<size_t>((n + 255) / 256, 1216), 256, 0, st>>>(
-                    const_cast<void*>(VO.cls[r][k]), VO.dt[r][k], n, beta);
-            }
-        }
+        const unsigned zero = kb_zero_classes(ctx, r, sl, sr, mask);
+        kb_status zs = kb_scale_classes(ctx, r, so, zero, beta, st);
+        if (zs != KB_OK) return zs;
         mask &= ~zero;
     }
     // a bubble of a declared-symmetric vertex with itself: compute the independent part only

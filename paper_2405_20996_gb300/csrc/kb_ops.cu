@@ -95,3 +95,49 @@ extern "C" kb_status kb_vertex_add(kb_ctx* ctx, int channel, int slot_src, int s
     return kb_vertex_add_impl(ctx, channel, slot_src, slot_dst, class_mask, alpha,
                               reinterpret_cast<cudaStream_t>(stream));
 }
+
+// Classes of a bubble that vanish identically: the r-independent parts L0 = R + K1_r + K2'_r
+// of the left vertex and R0 = R + K1_r + K2_r of the right one are zero when a slot has no
+// bare part and leaves channel r out of its channel mask (the vertex gamma_rbar of the
+// multiloop parts, the directions of the parquet Jacobian); then K1 = L0 Pi R0 and
+// K2' = L0 Pi R^v' (left) or K2 = L^v Pi R0 (right) are zero.
+unsigned kb_zero_classes(const kb_ctx* ctx, int r, int sl, int sr, unsigned mask) {
+    unsigned zero = 0;
+    const VertexDev& L = ctx->slots[sl];
+    const VertexDev& R = ctx->slots[sr];
+    if (!L.has_R && !((L.mask >> r) & 1)) zero |= (1u << KB_K1) | (1u << KB_K2P);
+    if (!R.has_R && !((R.mask >> r) & 1)) zero |= (1u << KB_K1) | (1u << KB_K2);
+    return zero & mask;
+}
+
+namespace kb {
+namespace {
+// out <- beta * out over n complex elements (alpha * 0 + beta * out)
+__global__ void k_class_scale(void* out, int dt, size_t n, double beta) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        if (dt == KB_DT_C128) {
+            double2* p = reinterpret_cast<double2*>(out) + i;
+            *p = beta != 0.0 ? make_double2(beta * p->x, beta * p->y) : make_double2(0.0, 0.0);
+        } else {
+            float2* p = reinterpret_cast<float2*>(out) + i;
+            *p = beta != 0.0 ? make_float2((float)(beta * p->x), (float)(beta * p->y)) : make_float2(0.f, 0.f);
+        }
+    }
+}
+}  // namespace
+}  // namespace kb
+
+kb_status kb_scale_classes(kb_ctx* ctx, int r, int so, unsigned classes, double beta, cudaStream_t st) {
+    if (!classes || beta == 1.0) return KB_OK;
+    const VertexDev& O = ctx->slots[so];
+    for (int k = 0; k < 4; ++k) {
+        if (!((classes >> k) & 1)) continue;
+        const size_t n = class_points(ctx->g, k) * 16;
+        KB_LAUNCH(ctx, st, "k_class_scale");
+        k_class_scale<<<(unsigned)std::min<size_t>((n + 255) / 256, (size_t)152 * 8), 256, 0, st>>>(
+            const_cast<void*>(O.cls[r][k]), O.dt[r][k], n, beta);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { ctx->err = std::string("zero classes: ") + cudaGetErrorString(e); return KB_ERR_CUDA; }
+    return KB_OK;
+}
