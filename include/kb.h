@@ -56,6 +56,7 @@ enum { KB_CH_A = 0, KB_CH_P = 1, KB_CH_T = 2 };
 enum { KB_K1 = 0, KB_K2 = 1, KB_K2P = 2, KB_K3 = 3 };
 #define KB_MASK_ALL 0xFu
 enum { KB_PI_GG = 0, KB_PI_GS_SG = 1 };           /* Π = G G,  Π-dot = G S + S G */
+enum { KB_REG_DELTA = 0, KB_REG_U = 1, KB_REG_T = 2 };   /* flow schemes (kb_set_regulator) */
 enum { KB_DT_C128 = 0, KB_DT_C64 = 1 };           /* complex double / complex float */
 enum { KB_PREC_FP64 = 0, KB_PREC_MIXED = 1 };     /* plain FP64 / FP32 gather + 3xTF32 tensor-core contraction */
 #define KB_MAX_SLOTS 16
@@ -88,6 +89,19 @@ kb_status kb_set_model(kb_ctx *ctx, double Delta, double T, double eps);
  * interleaved complex double HOST arrays (copied); Σ reads 0 at x = ±1.  sigR == NULL
  * resets Σ = 0.  sigK may be NULL (Σ^K = 0). */
 kb_status kb_set_self_energy(kb_ctx *ctx, int n_sig, double A_sig, const double *sigR, const double *sigK);
+
+/* Flow scheme (Sec. III.C.3) of the single-scale propagator S = dG/dΛ at fixed Σ used by
+ * KB_PI_GS_SG (default KB_REG_DELTA):
+ *   KB_REG_DELTA  hybridisation flow, Λ = Δ: S^R = -i (G^R)^2;
+ *   KB_REG_U      interaction flow at Λ = lambda > 0: the propagator itself becomes
+ *                 G^R = λ / (v - eps + i Δ - λ Σ^R), G^K = G^R [Σ^K - 2 i Δ tanh(v/2T) / λ] G^A
+ *                 (so Π = G G scales by λ^2 at Σ = 0), and S^R = (v - eps + i Δ) / (v - eps +
+ *                 i Δ - λ Σ^R)^2; `lambda` is ignored by the other schemes;
+ *   KB_REG_T      temperature flow, Λ = T (T > 0): S^R = 0, S^K = G^R (i Δ v / (T^2
+ *                 cosh^2(v/2T))) G^A.
+ * S^K is always dG^K/dΛ of the general Keldysh component.  At x = ±1 the tail uses the
+ * limits v G -> λ [[0,1],[1,0]] and v S -> [[0,1],[1,0]] (interaction flow) or 0. */
+kb_status kb_set_regulator(kb_ctx *ctx, int kind, double lambda);
 
 /* Vertex slot `slot` (0 .. KB_MAX_SLOTS-1): the bare part R = Γ0 of the parquet
  * approximation (Sec. I.B: +U/2 on components with an odd number of quantum indices)

@@ -243,14 +243,21 @@ static void vertex_select(const ovtx *V, int r, int spin_uu, int side_right, int
 
 /* ------------------------------------------------------------------------------------
  * Propagators (Sec. II.D.4, III.C.3): G^R = 1 / (v - eps + i Delta - Sigma^R(v)),
- * G^A = (G^R)*, G^K = G^R [Sigma^K - 2 i Delta tanh(v/2T)] G^A.  Single-scale
- * propagator of the hybridisation flow: S = d/dDelta G at fixed Sigma, S^R = -i (G^R)^2.
- * Sigma tables (optional) are interpolated linearly in x with zero at x = +-1.
+ * G^A = (G^R)*, G^K = G^R [Sigma^K - 2 i Delta tanh(v/2T)] G^A.  Sigma tables (optional)
+ * are interpolated linearly in x with zero at x = +-1.
+ * Single-scale propagator S = d/dLambda G at fixed Sigma of the flow scheme (Sec. III.C.3):
+ *   reg 0, hybridisation flow: Lambda = Delta;
+ *   reg 1, interaction flow: G^R = lam / (v - eps + i Delta - lam Sigma^R), i.e. the bare
+ *          inverse propagator divided by lam, and G^K = G^R [Sigma^K - 2 i Delta th / lam] G^A
+ *          (the equilibrium Keldysh part of the scaled bare propagator); Lambda = lam;
+ *   reg 2, temperature flow: Lambda = T (only the Keldysh component depends on it).
  * ------------------------------------------------------------------------------------ */
 typedef struct {
     double Delta, T, eps, A_sig;
     int n_sig;                    /* 0: Sigma = 0 */
     const cplx *sigR, *sigK;
+    int reg;                      /* 0 hybridisation, 1 interaction, 2 temperature flow */
+    double lam;                   /* the interaction-flow parameter (reg 1) */
 } oprop;
 
 static double tanh_ft(double v, double T) {
@@ -267,29 +274,48 @@ static void prop_matrix(const oprop *P, int which, double v, cplx M[2][2]) {
         int m = stencil(v, P->n_sig, P->A_sig, id, wt);
         for (int a = 0; a < m; ++a) { sR += wt[a] * P->sigR[id[a]]; if (P->sigK) sK += wt[a] * P->sigK[id[a]]; }
     }
-    cplx GR = 1.0 / (v - P->eps + I * P->Delta - sR);
+    const double lam = (P->reg == 1) ? P->lam : 1.0;
+    const cplx g0inv = v - P->eps + I * P->Delta;          /* lam times the bare inverse */
+    cplx GR = 1.0 / (g0inv / lam - sR);
     cplx GA = conj(GR);
     double th = tanh_ft(v, P->T);
-    cplx mid = sK - 2.0 * I * P->Delta * th;
+    cplx mid = sK - 2.0 * I * P->Delta * th / lam;
     if (which == 0) {
         M[0][0] = GR * mid * GA;
         M[0][1] = GR;
         M[1][0] = GA;
         M[1][1] = 0;
     } else {
-        cplx SR = -I * GR * GR;
+        /* S^R = -(G^R)^2 d[(G^R)^-1]/dLambda: hybridisation -i (G^R)^2; interaction
+         * (G^R)^2 g0inv / lam^2; temperature 0.  dmid = d(mid)/dLambda: -2i th;
+         * +2i Delta th / lam^2; -2i Delta d(th)/dT. */
+        cplx SR, dmid;
+        if (P->reg == 1) {
+            SR = GR * GR * g0inv / (lam * lam);
+            dmid = 2.0 * I * P->Delta * th / (lam * lam);
+        } else if (P->reg == 2) {
+            double c = cosh(v / (2.0 * P->T));
+            double dth = -v / (2.0 * P->T * P->T) / (c * c);   /* d tanh(v/2T) / dT */
+            SR = 0;
+            dmid = -2.0 * I * P->Delta * dth;
+        } else {
+            SR = -I * GR * GR;
+            dmid = -2.0 * I * th;
+        }
         cplx SA = conj(SR);
-        M[0][0] = SR * mid * GA + GR * (-2.0 * I * th) * GA + GR * mid * SA;
+        M[0][0] = SR * mid * GA + GR * dmid * GA + GR * mid * SA;
         M[0][1] = SR;
         M[1][0] = SA;
         M[1][1] = 0;
     }
 }
 
-/* lim_{v->+-inf} v * P(v): G -> [[0,1],[1,0]], S -> 0 */
-static void prop_asym(int which, cplx M[2][2]) {
+/* lim_{v->+-inf} v * P(v): G -> lam [[0,1],[1,0]] (lam = 1 but in the interaction flow);
+ * S -> [[0,1],[1,0]] in the interaction flow (S^R -> 1/v), else 0 */
+static void prop_asym(const oprop *P, int which, cplx M[2][2]) {
+    double g = (which == 0) ? ((P->reg == 1) ? P->lam : 1.0) : ((P->reg == 1) ? 1.0 : 0.0);
     M[0][0] = 0; M[1][1] = 0;
-    M[0][1] = M[1][0] = (which == 0) ? 1.0 : 0.0;
+    M[0][1] = M[1][0] = g;
 }
 
 /* ------------------------------------------------------------------------------------
@@ -323,7 +349,7 @@ static void pi_matrix(const bctx *B, double nupp, int at_inf, double sgn_inf, cp
     if (at_inf) {
         /* lim v''^2 P(a3) P(a4) = s3 s4 * asym * asym (independent of the sign of v'') */
         (void)sgn_inf;
-        prop_asym(0, G3); prop_asym(0, G4); prop_asym(1, S3); prop_asym(1, S4);
+        prop_asym(B->P, 0, G3); prop_asym(B->P, 0, G4); prop_asym(B->P, 1, S3); prop_asym(B->P, 1, S4);
         for (int i = 0; i < 2; ++i)
             for (int j = 0; j < 2; ++j) {
                 G3[i][j] *= s3; S3[i][j] *= s3; G4[i][j] *= s4; S4[i][j] *= s4;

@@ -151,14 +151,31 @@ kb_status kb_set_grids(kb_ctx* ctx, const kb_grid_desc* g) {
 }
 
 kb_status kb_set_model(kb_ctx* ctx, double Delta, double T, double eps) {
-    if (!ctx || !(Delta > 0) || !(T >= 0) || !std::isfinite(eps)) {
-        if (ctx) ctx->err = "kb_set_model: need Delta > 0, T >= 0, finite eps";
+    if (!ctx || !(Delta > 0) || !(T >= 0) || !std::isfinite(eps) || (ctx->m.reg == KB_REG_T && !(T > 0))) {
+        if (ctx) ctx->err = "kb_set_model: need Delta > 0, T >= 0 (T > 0 in the temperature flow), finite eps";
         return KB_ERR_ARG;
     }
     ctx->m.Delta = Delta;
     ctx->m.T = T;
     ctx->m.eps = eps;
     ctx->model_set = true;
+    for (int s = 0; s < KB_MAX_SLOTS; ++s) ++ctx->slot_gen[s];     // cached K3 right tiles hold Π
+    return KB_OK;
+}
+
+kb_status kb_set_regulator(kb_ctx* ctx, int kind, double lambda) {
+    if (!ctx) return KB_ERR_ARG;
+    if ((kind != KB_REG_DELTA && kind != KB_REG_U && kind != KB_REG_T) ||
+        (kind == KB_REG_U && !(lambda > 0 && std::isfinite(lambda)))) {
+        ctx->err = "kb_set_regulator: unknown scheme, or lambda <= 0 for the interaction flow";
+        return KB_ERR_ARG;
+    }
+    if (kind == KB_REG_T && ctx->model_set && !(ctx->m.T > 0)) {
+        ctx->err = "kb_set_regulator: the temperature flow needs T > 0";
+        return KB_ERR_ARG;
+    }
+    ctx->m.reg = kind;
+    ctx->m.lam = (kind == KB_REG_U) ? lambda : 1.0;
     for (int s = 0; s < KB_MAX_SLOTS; ++s) ++ctx->slot_gen[s];     // cached K3 right tiles hold Π
     return KB_OK;
 }

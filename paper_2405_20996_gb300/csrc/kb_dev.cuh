@@ -60,8 +60,10 @@ __device__ __forceinline__ double tanh_T(double v, double T) {
     return tanh(v / (2.0 * T));
 }
 
-// 2x2 Keldysh matrix of G (which = 0) or S (which = 1) at frequency v; index [a][a'],
-// 0 = classical, 1 = quantum: [[K, R], [A, 0]].
+// 2x2 Keldysh matrix of G (which = 0) or of the single-scale propagator S = dG/dΛ at fixed
+// Σ of the flow scheme m.reg (which = 1) at frequency v; index [a][a'], 0 = classical,
+// 1 = quantum: [[K, R], [A, 0]].  The interaction flow divides the bare inverse propagator
+// by λ = m.lam: G^R = 1 / ((v - eps + iΔ) / λ - Σ^R), G^K = G^R [Σ^K - 2iΔ th / λ] G^A.
 __device__ inline void prop2x2(const Model& m, int which, double v, double2 P[2][2]) {
     double2 sR = make_double2(0, 0), sK = make_double2(0, 0);
     if (m.n_sig > 0) {
@@ -73,19 +75,34 @@ __device__ inline void prop2x2(const Model& m, int which, double v, double2 P[2]
             sK = cadd(sK, cscale(m.sigK[k + 1], t));
         }
     }
-    double2 GR = cinv(make_double2(v - m.eps - sR.x, m.Delta - sR.y));
+    const double lam = (m.reg == KB_REG_U) ? m.lam : 1.0;
+    const double2 g0 = make_double2(v - m.eps, m.Delta);          // v - eps + i Delta
+    double2 GR = cinv(make_double2(g0.x / lam - sR.x, g0.y / lam - sR.y));
     double2 GA = cconj(GR);
     double th = tanh_T(v, m.T);
-    double2 mid = make_double2(sK.x, sK.y - 2.0 * m.Delta * th);
+    double2 mid = make_double2(sK.x, sK.y - 2.0 * m.Delta * th / lam);
     if (which == 0) {
         P[0][0] = cmul(cmul(GR, mid), GA);
         P[0][1] = GR;
         P[1][0] = GA;
     } else {
-        double2 SR = cmul(make_double2(0.0, -1.0), cmul(GR, GR));
+        // S^R = -(G^R)^2 d[(G^R)^-1]/dΛ and dmid = d(mid)/dΛ per scheme
+        double2 SR, dmid;
+        if (m.reg == KB_REG_U) {
+            SR = cscale(cmul(cmul(GR, GR), g0), 1.0 / (lam * lam));
+            dmid = make_double2(0.0, 2.0 * m.Delta * th / (lam * lam));
+        } else if (m.reg == KB_REG_T) {
+            const double c = cosh(v / (2.0 * m.T));
+            const double dth = -v / (2.0 * m.T * m.T) / (c * c);      // d tanh(v/2T) / dT
+            SR = make_double2(0.0, 0.0);
+            dmid = make_double2(0.0, -2.0 * m.Delta * dth);
+        } else {
+            SR = cmul(make_double2(0.0, -1.0), cmul(GR, GR));
+            dmid = make_double2(0.0, -2.0 * th);
+        }
         double2 SA = cconj(SR);
         double2 t1 = cmul(cmul(SR, mid), GA);
-        double2 t2 = cmul(cmul(GR, make_double2(0.0, -2.0 * th)), GA);
+        double2 t2 = cmul(cmul(GR, dmid), GA);
         double2 t3 = cmul(cmul(GR, mid), SA);
         P[0][0] = cadd(cadd(t1, t2), t3);
         P[0][1] = SR;
@@ -96,8 +113,9 @@ __device__ inline void prop2x2(const Model& m, int which, double v, double2 P[2]
 
 // Pi table entry (all 16 [B][D]) for node j at bosonic w, scaled by
 // c_r * w_j * J_j / (2 pi i); at x_j = +-1 the limit of J * P(arg3) * P(arg4) is used:
-// J / v''^2 -> pi / (2A), v'' * G -> [[0, 1], [1, 0]] times the sign of v'' in the
-// argument, v'' * S -> 0 (Sec. II.G.6 tail reading).
+// J / v''^2 -> pi / (2A), v'' * G -> λ [[0, 1], [1, 0]] times the sign of v'' in the
+// argument (λ = 1 but in the interaction flow), v'' * S -> [[0, 1], [1, 0]] in the
+// interaction flow (S^R -> 1/v) and 0 otherwise (Sec. II.G.6 tail reading).
 __device__ inline void pi_entry(const Model& m, const ChannelMaps& M, int r, int pi_kind, double A, double w,
                                 double xj, double wj, double2 out[16]) {
     double cr = (r == KB_CH_T) ? -1.0 : 1.0;
@@ -105,12 +123,14 @@ __device__ inline void pi_entry(const Model& m, const ChannelMaps& M, int r, int
     double scale;
     if (xj <= -1.0 || xj >= 1.0) {
         double s3 = 1.0, s4 = (r == KB_CH_P) ? -1.0 : 1.0;
+        const double gl = (m.reg == KB_REG_U) ? m.lam : 1.0, sl = (m.reg == KB_REG_U) ? 1.0 : 0.0;
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b) {
                 double g = (a != b) ? 1.0 : 0.0;
-                P3[a][b] = make_double2(g * s3, 0);
-                P4[a][b] = make_double2(g * s4, 0);
-                S3[a][b] = S4[a][b] = make_double2(0, 0);
+                P3[a][b] = make_double2(g * gl * s3, 0);
+                P4[a][b] = make_double2(g * gl * s4, 0);
+                S3[a][b] = make_double2(g * sl * s3, 0);
+                S4[a][b] = make_double2(g * sl * s4, 0);
             }
         scale = KB_PI / (2.0 * A);
     } else {

@@ -34,6 +34,8 @@ struct Model {
     double A_sig;
     const double2* sigR;     // device, n_sig entries or nullptr
     const double2* sigK;
+    int reg = KB_REG_DELTA;  // flow scheme of the single-scale propagator
+    double lam = 1.0;        // interaction-flow parameter (G^R = lam / (v - eps + i Delta - lam Sigma^R))
 };
 
 // Keldysh index maps of channel r (matrix form of the 16-component contraction):

@@ -39,6 +39,10 @@ class Engine:
     def set_model(self, Delta, T, eps=0.0):
         kb.kb_set_model(self.ctx, Delta, T, eps)
 
+    def set_regulator(self, kind, lam=1.0):
+        """Flow scheme of the single-scale propagator (kb.KB_REG_DELTA / _U / _T)."""
+        kb.kb_set_regulator(self.ctx, kind, lam)
+
     def set_self_energy(self, sigR=None, sigK=None, A_sig=5.0):
         kb.kb_set_self_energy(self.ctx, sigR, sigK, A_sig)
 

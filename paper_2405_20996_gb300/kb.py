@@ -54,6 +54,7 @@ _SIGS = {
     "kb_set_grids": [C.c_void_p, C.POINTER(kb_grid_desc)],
     "kb_set_model": [C.c_void_p, C.c_double, C.c_double, C.c_double],
     "kb_set_self_energy": [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p],
+    "kb_set_regulator": [C.c_void_p, C.c_int, C.c_double],
     "kb_set_vertex": [C.c_void_p, C.c_int, C.c_int, C.c_double],
     "kb_set_vertex_channels": [C.c_void_p, C.c_int, C.c_uint],
     "kb_set_vertex_symmetric": [C.c_void_p, C.c_int, C.c_int],
@@ -130,6 +131,13 @@ def kb_set_grids(ctx, n1, n2w, n2v, n3w, n3v, nq, A=5.0):
 
 def kb_set_model(ctx, Delta, T, eps=0.0):
     _check(ctx, lib().kb_set_model(ctx, Delta, T, eps))
+
+
+KB_REG_DELTA, KB_REG_U, KB_REG_T = 0, 1, 2
+
+
+def kb_set_regulator(ctx, kind, lam=1.0):
+    _check(ctx, lib().kb_set_regulator(ctx, kind, lam))
 
 
 def kb_set_self_energy(ctx, sigR=None, sigK=None, A_sig=5.0):

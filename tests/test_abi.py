@@ -70,3 +70,7 @@ def test_record_cache_calls_rejected_without_context():
     L = kb.lib()
     assert L.kb_vertex_cache(None, 0, 0, 3, None) == kb.KB_ERR_ARG
     assert L.kb_vertex_uncache(None, 0) == kb.KB_ERR_ARG
+
+
+def test_regulator_call_rejected_without_context():
+    assert kb.lib().kb_set_regulator(None, 0, 1.0) == kb.KB_ERR_ARG
