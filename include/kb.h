@@ -103,6 +103,13 @@ kb_status kb_set_self_energy(kb_ctx *ctx, int n_sig, double A_sig, const double 
  * limits v G -> λ [[0,1],[1,0]] and v S -> [[0,1],[1,0]] (interaction flow) or 0. */
 kb_status kb_set_regulator(kb_ctx *ctx, int kind, double lambda);
 
+/* Katanin substitution (Sec. III.C.3: the differentiated propagator G-dot = S + G Σ-dot G):
+ * n_dsig values of dΣ^R/dΛ (and dΣ^K/dΛ, may be NULL) on the tan grid of scale A_dsig,
+ * interleaved complex double HOST arrays (copied), read linearly in x with zero at
+ * x = ±1.  KB_PI_GS_SG then uses G-dot in place of S.  dsigR == NULL switches it off. */
+kb_status kb_set_self_energy_derivative(kb_ctx *ctx, int n_dsig, double A_dsig, const double *dsigR,
+                                        const double *dsigK);
+
 /* Vertex slot `slot` (0 .. KB_MAX_SLOTS-1): the bare part R = Γ0 of the parquet
  * approximation (Sec. I.B: +U/2 on components with an odd number of quantum indices)
  * when has_R != 0, and no classes.  Classes are attached with kb_set_vertex_class. */
@@ -166,7 +173,7 @@ kb_status kb_bubble(kb_ctx *ctx, int channel, int slot_left, int slot_right, int
  *                    side 1 at v''-w/2 or w/2-v''; G^A = (G^R)* and G^K = tanh(v/2T)(G^R -
  *                    G^A) are taken as functions of G^R (equilibrium FDR, Sec. II.D.4).
  *                    Needs pi_kind KB_PI_GG and no self-energy table (else
- *                    KB_ERR_UNSUPPORTED); the tail nodes (v'' = ±inf) carry no G dependence.
+ *                    KB_ERR_UNSUPPORTED; also with a dΣ/dΛ table); the tail nodes (v'' = ±inf) carry no G dependence.
  * Gradient classes must be complex128 and must not alias any input.  The bare part
  * R = Γ0 is a fixed parameter (no gradient).  precision: KB_PREC_FP64 only (others return
  * KB_ERR_UNSUPPORTED). */

@@ -258,7 +258,21 @@ typedef struct {
     const cplx *sigR, *sigK;
     int reg;                      /* 0 hybridisation, 1 interaction, 2 temperature flow */
     double lam;                   /* the interaction-flow parameter (reg 1) */
+    int n_dsig;                   /* > 0: Katanin substitution with the table dSigma/dLambda */
+    double A_dsig;
+    const cplx *dsigR, *dsigK;
 } oprop;
+
+/* retarded and Keldysh parts of a self-energy table at v (linear in x, zero at x = +-1) */
+static void sigma_at(int n, double A, const cplx *tR, const cplx *tK, double v, cplx *sR, cplx *sK) {
+    *sR = 0;
+    *sK = 0;
+    if (n <= 0) return;
+    int id[2];
+    double wt[2];
+    int m = stencil(v, n, A, id, wt);
+    for (int a = 0; a < m; ++a) { *sR += wt[a] * tR[id[a]]; if (tK) *sK += wt[a] * tK[id[a]]; }
+}
 
 static double tanh_ft(double v, double T) {
     if (T <= 0.0) return v > 0 ? 1.0 : (v < 0 ? -1.0 : 0.0);
@@ -267,13 +281,8 @@ static double tanh_ft(double v, double T) {
 
 /* 2x2 Keldysh matrices M[a][a'] (a, a' = 0 classical, 1 quantum). which: 0 = G, 1 = S */
 static void prop_matrix(const oprop *P, int which, double v, cplx M[2][2]) {
-    cplx sR = 0, sK = 0;
-    if (P->n_sig > 0) {
-        int id[2];
-        double wt[2];
-        int m = stencil(v, P->n_sig, P->A_sig, id, wt);
-        for (int a = 0; a < m; ++a) { sR += wt[a] * P->sigR[id[a]]; if (P->sigK) sK += wt[a] * P->sigK[id[a]]; }
-    }
+    cplx sR, sK;
+    sigma_at(P->n_sig, P->A_sig, P->sigR, P->sigK, v, &sR, &sK);
     const double lam = (P->reg == 1) ? P->lam : 1.0;
     const cplx g0inv = v - P->eps + I * P->Delta;          /* lam times the bare inverse */
     cplx GR = 1.0 / (g0inv / lam - sR);
@@ -307,6 +316,16 @@ static void prop_matrix(const oprop *P, int which, double v, cplx M[2][2]) {
         M[0][1] = SR;
         M[1][0] = SA;
         M[1][1] = 0;
+        if (P->n_dsig > 0) {
+            /* Katanin substitution: S -> S + G dSigma G, the contour matrix product with
+             * dSigma = [[0, dS^A], [dS^R, dS^K]] in the [[K, R], [A, 0]] layout of G */
+            cplx dR, dK;
+            sigma_at(P->n_dsig, P->A_dsig, P->dsigR, P->dsigK, v, &dR, &dK);
+            cplx dA = conj(dR), GK = GR * mid * GA;
+            M[0][1] += GR * dR * GR;
+            M[1][0] += GA * dA * GA;
+            M[0][0] += GR * dR * GK + GK * dA * GA + GR * dK * GA;
+        }
     }
 }
 
@@ -815,7 +834,7 @@ int og_bubble_vjp_points(const ovtx *V1, const ovtx *V2, const oprop *P, int pi_
                          int Nq, int npts, const double *freqs, const cplx *gbar, const int *iw, ograd *G1,
                          ograd *G2, cplx *gGR, int n_gr, int nthreads) {
     if (r < 0 || r > 2 || Nq < 5 || (Nq - 1) % 4) return -1;
-    if (gGR && (pi_kind != 0 || P->n_sig > 0 || !iw)) return -3;
+    if (gGR && (pi_kind != 0 || P->n_sig > 0 || P->n_dsig > 0 || !iw)) return -3;
     double *xq = malloc(sizeof(double) * Nq), *wq = malloc(sizeof(double) * Nq);
     if (!xq || !wq) { free(xq); free(wq); return -2; }
     og_gl5_rule(Nq, xq, wq);

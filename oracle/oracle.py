@@ -62,7 +62,8 @@ class _OVtx(C.Structure):
 class _OProp(C.Structure):
     _fields_ = [("Delta", C.c_double), ("T", C.c_double), ("eps", C.c_double), ("A_sig", C.c_double),
                 ("n_sig", C.c_int), ("sigR", C.c_void_p), ("sigK", C.c_void_p), ("reg", C.c_int),
-                ("lam", C.c_double)]
+                ("lam", C.c_double), ("n_dsig", C.c_int), ("A_dsig", C.c_double), ("dsigR", C.c_void_p),
+                ("dsigK", C.c_void_p)]
 
 
 REG_DELTA, REG_U, REG_T = 0, 1, 2
@@ -104,14 +105,22 @@ class Vertex:
 class Prop:
     """G^R = 1/(v - eps + i Delta - Sigma^R(v)) with optional Sigma tables on a tan grid, and
     the single-scale propagator of the flow scheme reg (REG_DELTA, REG_U with parameter lam:
-    G^R = lam / (v - eps + i Delta - lam Sigma^R), REG_T)."""
+    G^R = lam / (v - eps + i Delta - lam Sigma^R), REG_T), with the Katanin substitution
+    S + G dSigma G when dSigma/dLambda tables are given."""
 
-    def __init__(self, Delta=1.0, T=0.1, eps=0.0, sigR=None, sigK=None, A_sig=5.0, reg=REG_DELTA, lam=1.0):
+    def __init__(self, Delta=1.0, T=0.1, eps=0.0, sigR=None, sigK=None, A_sig=5.0, reg=REG_DELTA, lam=1.0,
+                 dsigR=None, dsigK=None, A_dsig=5.0):
         self.sigR = None if sigR is None else np.ascontiguousarray(sigR, dtype=np.complex128)
         self.sigK = None if sigK is None else np.ascontiguousarray(sigK, dtype=np.complex128)
+        self.dsigR = None if dsigR is None else np.ascontiguousarray(dsigR, dtype=np.complex128)
+        self.dsigK = None if dsigK is None else np.ascontiguousarray(dsigK, dtype=np.complex128)
         s = _OProp()
         s.Delta, s.T, s.eps, s.A_sig = Delta, T, eps, A_sig
         s.reg, s.lam = int(reg), float(lam)
+        s.n_dsig = 0 if self.dsigR is None else len(self.dsigR)
+        s.A_dsig = A_dsig
+        s.dsigR = None if self.dsigR is None else self.dsigR.ctypes.data
+        s.dsigK = None if self.dsigK is None else self.dsigK.ctypes.data
         s.n_sig = 0 if self.sigR is None else len(self.sigR)
         s.sigR = None if self.sigR is None else self.sigR.ctypes.data
         s.sigK = None if self.sigK is None else self.sigK.ctypes.data

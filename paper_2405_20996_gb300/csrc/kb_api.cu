@@ -120,6 +120,7 @@ kb_status kb_destroy(kb_ctx* ctx) {
     cudaFree(ctx->d_xq);
     cudaFree(ctx->d_wq);
     cudaFree(ctx->d_sig);
+    cudaFree(ctx->d_dsig);
     cudaFree(ctx->ws.ptr);
     for (int s = 0; s < KB_MAX_SLOTS; ++s) kb_vertex_cache_free(ctx, s);
     prof_clear(ctx);
@@ -160,6 +161,30 @@ kb_status kb_set_model(kb_ctx* ctx, double Delta, double T, double eps) {
     ctx->m.eps = eps;
     ctx->model_set = true;
     for (int s = 0; s < KB_MAX_SLOTS; ++s) ++ctx->slot_gen[s];     // cached K3 right tiles hold Π
+    return KB_OK;
+}
+
+kb_status kb_set_self_energy_derivative(kb_ctx* ctx, int n, double A, const double* dsigR, const double* dsigK) {
+    if (!ctx) return KB_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    cudaFree(ctx->d_dsig);
+    ctx->d_dsig = nullptr;
+    ctx->m.n_dsig = 0;
+    ctx->m.dsigR = ctx->m.dsigK = nullptr;
+    for (int s = 0; s < KB_MAX_SLOTS; ++s) ++ctx->slot_gen[s];
+    if (!dsigR) return KB_OK;
+    if (n < 1 || !(A > 0)) { ctx->err = "kb_set_self_energy_derivative: n >= 1, A > 0"; return KB_ERR_ARG; }
+    std::vector<double2> h(2 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        h[i] = make_double2(dsigR[2 * i], dsigR[2 * i + 1]);
+        h[n + i] = dsigK ? make_double2(dsigK[2 * i], dsigK[2 * i + 1]) : make_double2(0, 0);
+    }
+    KB_CUDA_TRY(ctx, cudaMalloc(&ctx->d_dsig, sizeof(double2) * h.size()));
+    KB_CUDA_TRY(ctx, cudaMemcpy(ctx->d_dsig, h.data(), sizeof(double2) * h.size(), cudaMemcpyHostToDevice));
+    ctx->m.n_dsig = n;
+    ctx->m.A_dsig = A;
+    ctx->m.dsigR = ctx->d_dsig;
+    ctx->m.dsigK = ctx->d_dsig + n;
     return KB_OK;
 }
 
@@ -333,7 +358,7 @@ kb_status kb_bubble_vjp(kb_ctx* ctx, int channel, int sl, int sr, int sgo, int p
     }
     void* tabs[3] = {grad_GR_K1, grad_GR_K2, grad_GR_K3};
     bool any_gr = grad_GR_K1 || grad_GR_K2 || grad_GR_K3;
-    if (any_gr && (pi_kind != KB_PI_GG || ctx->m.n_sig > 0)) {
+    if (any_gr && (pi_kind != KB_PI_GG || ctx->m.n_sig > 0 || ctx->m.n_dsig > 0)) {
         ctx->err = "kb_bubble_vjp: the G^R gradient needs pi_kind GG and no self-energy table (FDR form of G^K)";
         return KB_ERR_UNSUPPORTED;
     }

@@ -107,6 +107,22 @@ __device__ inline void prop2x2(const Model& m, int which, double v, double2 P[2]
         P[0][0] = cadd(cadd(t1, t2), t3);
         P[0][1] = SR;
         P[1][0] = SA;
+        if (m.n_dsig > 0) {
+            // Katanin substitution S -> S + G dSigma G: the contour product with
+            // dSigma = [[0, dS^A], [dS^R, dS^K]] in the [[K, R], [A, 0]] layout of G
+            double2 dR = make_double2(0, 0), dK = make_double2(0, 0);
+            double t;
+            int k = xstencil(v, m.n_dsig, m.A_dsig, t);
+            if (k >= 0) { dR = cadd(dR, cscale(m.dsigR[k], 1.0 - t)); dK = cadd(dK, cscale(m.dsigK[k], 1.0 - t)); }
+            if (k >= -1 && k + 1 <= m.n_dsig - 1) {
+                dR = cadd(dR, cscale(m.dsigR[k + 1], t));
+                dK = cadd(dK, cscale(m.dsigK[k + 1], t));
+            }
+            const double2 dA = cconj(dR), GK = cmul(cmul(GR, mid), GA);
+            P[0][1] = cadd(P[0][1], cmul(cmul(GR, dR), GR));
+            P[1][0] = cadd(P[1][0], cmul(cmul(GA, dA), GA));
+            P[0][0] = cadd(P[0][0], cadd(cadd(cmul(cmul(GR, dR), GK), cmul(cmul(GK, dA), GA)), cmul(cmul(GR, dK), GA)));
+        }
     }
     P[1][1] = make_double2(0, 0);
 }

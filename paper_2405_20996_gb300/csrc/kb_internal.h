@@ -36,6 +36,10 @@ struct Model {
     const double2* sigK;
     int reg = KB_REG_DELTA;  // flow scheme of the single-scale propagator
     double lam = 1.0;        // interaction-flow parameter (G^R = lam / (v - eps + i Delta - lam Sigma^R))
+    int n_dsig = 0;          // > 0: Katanin substitution S -> S + G dSigma G with these tables
+    double A_dsig = 5.0;
+    const double2* dsigR = nullptr;
+    const double2* dsigK = nullptr;
 };
 
 // Keldysh index maps of channel r (matrix form of the 16-component contraction):
@@ -69,6 +73,7 @@ struct kb_ctx {
     double* d_xq = nullptr;   // quadrature nodes x_j (device, nq)
     double* d_wq = nullptr;   // weights w_j (device, nq)
     double2* d_sig = nullptr; // Sigma tables (2 * n_sig)
+    double2* d_dsig = nullptr; // dSigma/dLambda tables (2 * n_dsig), Katanin substitution
     kb::VertexDev slots[KB_MAX_SLOTS];
     bool slot_set[KB_MAX_SLOTS];
     kb::Workspace ws;

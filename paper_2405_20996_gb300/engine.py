@@ -43,6 +43,10 @@ class Engine:
         """Flow scheme of the single-scale propagator (kb.KB_REG_DELTA / _U / _T)."""
         kb.kb_set_regulator(self.ctx, kind, lam)
 
+    def set_self_energy_derivative(self, dsigR=None, dsigK=None, A_dsig=5.0):
+        """dΣ/dΛ tables: the Katanin substitution S -> S + G dΣ G in Π-dot."""
+        kb.kb_set_self_energy_derivative(self.ctx, dsigR, dsigK, A_dsig)
+
     def set_self_energy(self, sigR=None, sigK=None, A_sig=5.0):
         kb.kb_set_self_energy(self.ctx, sigR, sigK, A_sig)
 

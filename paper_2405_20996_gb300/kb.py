@@ -55,6 +55,7 @@ _SIGS = {
     "kb_set_model": [C.c_void_p, C.c_double, C.c_double, C.c_double],
     "kb_set_self_energy": [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p],
     "kb_set_regulator": [C.c_void_p, C.c_int, C.c_double],
+    "kb_set_self_energy_derivative": [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p],
     "kb_set_vertex": [C.c_void_p, C.c_int, C.c_int, C.c_double],
     "kb_set_vertex_channels": [C.c_void_p, C.c_int, C.c_uint],
     "kb_set_vertex_symmetric": [C.c_void_p, C.c_int, C.c_int],
@@ -138,6 +139,17 @@ KB_REG_DELTA, KB_REG_U, KB_REG_T = 0, 1, 2
 
 def kb_set_regulator(ctx, kind, lam=1.0):
     _check(ctx, lib().kb_set_regulator(ctx, kind, lam))
+
+
+def kb_set_self_energy_derivative(ctx, dsigR=None, dsigK=None, A_dsig=5.0):
+    import numpy as np
+    if dsigR is None:
+        _check(ctx, lib().kb_set_self_energy_derivative(ctx, 0, A_dsig, None, None))
+        return
+    r = np.ascontiguousarray(np.asarray(dsigR, dtype=np.complex128))
+    k = None if dsigK is None else np.ascontiguousarray(np.asarray(dsigK, dtype=np.complex128))
+    _check(ctx, lib().kb_set_self_energy_derivative(ctx, len(r), A_dsig, r.ctypes.data,
+                                                    None if k is None else k.ctypes.data))
 
 
 def kb_set_self_energy(ctx, sigR=None, sigK=None, A_sig=5.0):

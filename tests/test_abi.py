@@ -74,3 +74,7 @@ def test_record_cache_calls_rejected_without_context():
 
 def test_regulator_call_rejected_without_context():
     assert kb.lib().kb_set_regulator(None, 0, 1.0) == kb.KB_ERR_ARG
+
+
+def test_self_energy_derivative_call_rejected_without_context():
+    assert kb.lib().kb_set_self_energy_derivative(None, 0, 5.0, None, None) == kb.KB_ERR_ARG

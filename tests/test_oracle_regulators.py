@@ -65,3 +65,25 @@ def test_temperature_flow_single_scale_closed_form():
     ref = 1j * D * V * np.abs(gr) ** 2 * 4 * e / (1 + e) ** 2 / T ** 2
     assert np.all(s[:, 0, 1] == 0) and np.all(s[:, 1, 0] == 0)
     assert np.allclose(s[:, 0, 0], ref, rtol=1e-13, atol=1e-300)
+
+
+@pytest.mark.parametrize("reg,par", [(O.REG_DELTA, "Delta"), (O.REG_U, "lam"), (O.REG_T, "T")])
+def test_katanin_substitution_is_the_total_derivative(reg, par):
+    """With Sigma(Lambda) = Sigma0 + Lambda Sigma1 the Katanin-substituted single-scale
+    propagator S + G Sigma1 G is the total derivative dG/dLambda (chain rule)."""
+    base = dict(Delta=0.8, T=0.2, eps=0.15, lam=0.7)
+    s0R, s1R = _sig(), S.seeded_sigma(21, seed=9, scale=0.2)
+    s0K, s1K = 1j * np.abs(s0R).astype(np.complex128), 0.5j * np.abs(s1R).astype(np.complex128)
+    h = 1e-5 * base[par]
+
+    def G(delta):
+        kw = dict(base)
+        kw[par] += delta
+        lam_tot = kw[par]
+        return O.prop_eval(O.Prop(Delta=kw["Delta"], T=kw["T"], eps=kw["eps"], reg=reg, lam=kw["lam"],
+                                  sigR=s0R + lam_tot * s1R, sigK=s0K + lam_tot * s1K), 0, V)
+
+    fd = (G(h) - G(-h)) / (2 * h)
+    L = base[par]
+    kat = O.prop_eval(O.Prop(reg=reg, **base, sigR=s0R + L * s1R, sigK=s0K + L * s1K, dsigR=s1R, dsigK=s1K), 1, V)
+    assert np.abs(kat - fd).max() <= 1e-7 * np.abs(fd).max(), (reg, np.abs(kat - fd).max())
