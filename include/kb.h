@@ -259,6 +259,17 @@ kb_status kb_vertex_add(kb_ctx *ctx, int channel, int slot_src, int slot_dst, un
 kb_status kb_vertex_cache(kb_ctx *ctx, int slot, int channel, unsigned sides, void *stream);
 kb_status kb_vertex_uncache(kb_ctx *ctx, int slot);
 
+/* The full vertex of slot `slot` — its bare part and the classes of its included channels
+ * (excluded channels still enter the up-up component as crossing partners), each read at
+ * the point converted to its own channel variables (Sec. II.D.1) and interpolated linearly
+ * in x (Sec. II.G.7) — at n points (w, v, v') in the variables of channel `channel`:
+ * freqs is a DEVICE array [n][3] of doubles (±inf allowed: a class at an infinite argument
+ * reads 0), out a DEVICE complex128 array [n][16] in the Keldysh order above; spin_uu != 0
+ * gives the up-up component, else up-down.  E.g. the slice of the paper's post-processing:
+ * channel t, w = 0, (v, v') on a grid.  Asynchronous on `stream`. */
+kb_status kb_vertex_eval(kb_ctx *ctx, int slot, int channel, int spin_uu, int n, const double *freqs, void *out,
+                         void *stream);
+
 /* Device workspace limit of a context in bytes (default 4 GiB, or the KB_WORKSPACE_MB
  * environment variable at kb_create).  Larger limits let the K3 contraction batch more
  * bosonic frequencies per launch; smaller ones bound memory when many contexts coexist.

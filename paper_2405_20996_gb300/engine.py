@@ -124,6 +124,16 @@ class Engine:
         for (ch, k), t in other.tensors[other_slot].items():
             self.attach(slot, ch, k, t)
 
+    def vertex_eval(self, slot, channel, freqs, spin_uu=False, stream=None):
+        """The full vertex of a slot at points (w, v, v') in the variables of `channel`
+        (array-like [n][3]); returns a complex128 device tensor [n][16].  For the t-channel
+        slice at zero transfer frequency pass channel 2 and points (0, v, v')."""
+        f = torch.as_tensor(freqs, dtype=torch.float64).reshape(-1, 3).to(self.device).contiguous()
+        out = torch.empty((f.shape[0], 16), dtype=torch.complex128, device=self.device)
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        kb.kb_vertex_eval(self.ctx, slot, channel, spin_uu, f.shape[0], f.data_ptr(), out.data_ptr(), st)
+        return out
+
     def set_workspace_limit(self, nbytes):
         kb.kb_set_workspace_limit(self.ctx, nbytes)
 

@@ -65,6 +65,7 @@ _SIGS = {
     "kb_bubble_vjp": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_double, C.c_int,
                       C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
     "kb_vertex_add": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_double, C.c_void_p],
+    "kb_vertex_eval": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p],
     "kb_vertex_cache": [C.c_void_p, C.c_int, C.c_int, C.c_uint, C.c_void_p],
     "kb_vertex_uncache": [C.c_void_p, C.c_int],
     "kb_graph_create": [C.POINTER(C.c_void_p), C.POINTER(kb_bubble_desc), C.c_int],
@@ -194,6 +195,10 @@ def kb_bubble_vjp(ctx, channel, slot_left, slot_right, gout_slot, pi_kind=KB_PI_
 
 def kb_vertex_add(ctx, channel, slot_src, slot_dst, class_mask=KB_MASK_ALL, alpha=1.0, stream=0):
     _check(ctx, lib().kb_vertex_add(ctx, channel, slot_src, slot_dst, class_mask, alpha, stream))
+
+
+def kb_vertex_eval(ctx, slot, channel, spin_uu, n, freqs_ptr, out_ptr, stream=0):
+    _check(ctx, lib().kb_vertex_eval(ctx, slot, channel, int(bool(spin_uu)), n, freqs_ptr, out_ptr, stream))
 
 
 def kb_add_desc(ctx, channel, slot_src, slot_dst, class_mask=KB_MASK_ALL, alpha=1.0):

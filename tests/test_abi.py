@@ -78,3 +78,7 @@ def test_regulator_call_rejected_without_context():
 
 def test_self_energy_derivative_call_rejected_without_context():
     assert kb.lib().kb_set_self_energy_derivative(None, 0, 5.0, None, None) == kb.KB_ERR_ARG
+
+
+def test_vertex_eval_rejected_without_context():
+    assert kb.lib().kb_vertex_eval(None, 0, 0, 0, 1, None, None, None) == kb.KB_ERR_ARG
