@@ -364,6 +364,7 @@ def run_multiloop(args):
                        cache={"off": False, "auto": "auto", "all": True}[args.ml_cache])
     for e in ml.e.values():
         e.set_workspace_limit(args.ws_gb << 30)
+        e.set_autotune(not args.no_autotune)
     stream = torch.cuda.current_stream(dev)
     nb = ml.bubbles_per_step()
     points = nb * sum(class_points(g).values())
@@ -553,6 +554,8 @@ def main():
     ap.add_argument("--ml-cache", default="auto", choices=["off", "auto", "all"],
                     help="multiloop workloads: record cache of the full vertex (off, the useful sides, all sides)")
     ap.add_argument("--fp-maxit", type=int, default=40, help="parquet workload: fixed-point iteration cap")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the wave-model split-K factors instead of timing candidates before the step graph")
     ap.add_argument("--workload", default="step",
                     choices=["step", "points32", "vjp", "multiloop", "multiloop-large", "parquet"],
                     help="step: the default three-channel line; points32 / vjp / multiloop: the batching, "
@@ -595,6 +598,7 @@ def main():
         e = Engine(GRIDS, NQ, device=local)
         e.set_model(DELTA, T)
         e.set_workspace_limit(args.ws_gb << 30)
+        e.set_autotune(not args.no_autotune)
         if not engs:
             # the seeded vertex is conjugation- and crossing-symmetric by construction
             e.set_vertex(0, U=U, has_R=True, channels=ch, dtype=torch.complex64, symmetric=True)

@@ -270,6 +270,14 @@ kb_status kb_vertex_uncache(kb_ctx *ctx, int slot);
 kb_status kb_vertex_eval(kb_ctx *ctx, int slot, int channel, int spin_uu, int n, const double *freqs, void *out,
                          void *stream);
 
+/* Autotuning of the tensor-core K3 contraction (default off): with `on`, the first
+ * mixed-precision bubble of each contraction shape (rows, columns, K, batch of bosonic
+ * frequencies) times up to four split-K factors ranked by the wave model and keeps the
+ * fastest for that shape and device (process-wide table); kb_graph_create tunes the shapes
+ * of its bubbles before capturing.  Tuning runs extra launches on the workspace only; any
+ * split-K factor gives the same result up to the rounding of the segment sums. */
+kb_status kb_set_autotune(kb_ctx *ctx, int on);
+
 /* Device workspace limit of a context in bytes (default 4 GiB, or the KB_WORKSPACE_MB
  * environment variable at kb_create).  Larger limits let the K3 contraction batch more
  * bosonic frequencies per launch; smaller ones bound memory when many contexts coexist.

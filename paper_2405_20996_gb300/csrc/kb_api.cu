@@ -372,6 +372,12 @@ kb_status kb_bubble_vjp(kb_ctx* ctx, int channel, int sl, int sr, int sgo, int p
                               reinterpret_cast<cudaStream_t>(stream));
 }
 
+kb_status kb_set_autotune(kb_ctx* ctx, int on) {
+    if (!ctx) return KB_ERR_ARG;
+    ctx->autotune = on != 0;
+    return KB_OK;
+}
+
 kb_status kb_set_workspace_limit(kb_ctx* ctx, unsigned long long bytes) {
     if (!ctx || bytes < (1ull << 20)) return KB_ERR_ARG;
     ctx->ws_limit = (size_t)bytes;

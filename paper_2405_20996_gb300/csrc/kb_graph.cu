@@ -86,6 +86,15 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
     for (int i = 0; i < n; ++i) any_mixed |= d[i].op == KB_OP_BUBBLE && d[i].precision == KB_PREC_MIXED;
     if (any_mixed && !kb_tc_prepare(c0->device))
         return fail(c0, "kb_graph_create: tensor-core kernel setup failed", KB_ERR_CUDA);
+    // contexts with autotuning on: tune their contraction shapes now (timing is not possible
+    // inside a capture); the replays use the tuned split-K factors
+    for (int i = 0; i < n; ++i) {
+        const kb_bubble_desc& x = d[i];
+        if (x.op != KB_OP_BUBBLE || x.precision != KB_PREC_MIXED || !x.ctx->autotune) continue;
+        kb_status s = kb_mixed_tune(x.ctx, x.channel, x.slot_left, x.slot_right, x.class_mask, x.beta, nullptr);
+        if (s != KB_OK) return s;
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(c0, "kb_graph_create: tuning failed", KB_ERR_CUDA);
 
     cudaStream_t s0 = nullptr;
     cudaEvent_t fork = nullptr;

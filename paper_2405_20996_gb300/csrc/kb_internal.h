@@ -80,6 +80,7 @@ struct kb_ctx {
     unsigned long long launches = 0;
     std::string err;
     size_t ws_limit = 0;
+    bool autotune = false;    // time the tensor-core contraction's split-K candidates per shape
     bool prof_on = false;
     std::vector<kb_prof_rec> prof;
     // bumped by every change of a slot (and of the grids); a record cache is valid only for
@@ -143,6 +144,11 @@ void kb_vertex_cache_free(kb_ctx* ctx, int slot);
 // classes of a bubble that vanish identically, and out <- beta * out for them (kb_ops.cu)
 unsigned kb_zero_classes(const kb_ctx* ctx, int r, int sl, int sr, unsigned mask);
 kb_status kb_scale_classes(kb_ctx* ctx, int r, int so, unsigned classes, double beta, cudaStream_t st);
+// split-K autotuning of the tensor-core contraction (kb_tc.cu) and the shapes of a mixed
+// bubble's K3 contraction tuned ahead of a graph capture (kb_mixed.cu)
+bool kb_tc_tune(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
+                void* scratch, size_t scratch_bytes, cudaStream_t st);
+kb_status kb_mixed_tune(kb_ctx* ctx, int r, int sl, int sr, unsigned mask, double beta, cudaStream_t st);
 // slot arithmetic (kb_ops.cu)
 kb_status kb_vertex_add_impl(kb_ctx* ctx, int channel, int src, int dst, unsigned mask, double alpha,
                              cudaStream_t st);

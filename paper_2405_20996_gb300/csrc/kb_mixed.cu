@@ -1269,3 +1269,29 @@ extern "C" kb_status kb_vertex_uncache(kb_ctx* ctx, int slot) {
     kb_vertex_cache_free(ctx, slot);
     return KB_OK;
 }
+
+// Tune the split-K factor of the tensor-core contraction for the K3 shapes this bubble will
+// use (the full chunks of bosonic frequencies and the last partial one), on the context's
+// workspace as operands (any values do for timing); for step graphs, before the capture.
+kb_status kb_mixed_tune(kb_ctx* ctx, int r, int sl, int sr, unsigned mask, double beta, cudaStream_t st) {
+    mask &= ~kb_zero_classes(ctx, r, sl, sr, mask);
+    if (!((mask >> KB_K3) & 1) || std::getenv("KB_K3_SIMT")) return KB_OK;
+    const Grids& g = ctx->g;
+    const bool sym = (sl == sr) && ctx->slots[sl].symmetric && beta == 0.0 &&
+                     (!((mask >> KB_K2P) & 1) || ((mask >> KB_K2) & 1)) && std::getenv("KB_NO_SYMMETRY") == nullptr;
+    const MixedLayout Lo = mixed_layout(ctx, r, mask);
+    kb_status s = kb_ensure_workspace(ctx, Lo.need);
+    if (s != KB_OK) return s;
+    char* ws = static_cast<char*>(ctx->ws.ptr);
+    float* TA = reinterpret_cast<float*>(ws + Lo.off_T);
+    float* TB = TA + (size_t)Lo.chunk * 4 * Lo.rows * Lo.K;
+    double2* Cm = reinterpret_cast<double2*>(TB + (size_t)Lo.chunk * 4 * Lo.rows * Lo.K);
+    void* scratch = reinterpret_cast<char*>(Cm) + (size_t)Lo.chunk * Lo.rows * Lo.rows * sizeof(double2);
+    const int w3_lo = (sym && r != KB_CH_P) ? g.n3w / 2 : 0;
+    const int vh3 = (sym && r == KB_CH_P) ? g.n3v / 2 : 0;
+    const int rowsL = 4 * (g.n3v - vh3), rowsR = (int)Lo.rows, nw = g.n3w - w3_lo;
+    const int full = std::min(Lo.chunk, nw), last = nw % Lo.chunk;
+    kb_tc_tune(ctx, TA, TB, Cm, rowsL, rowsR, (int)Lo.K, full, scratch, Lo.tc_scratch, st);
+    if (last && last != full) kb_tc_tune(ctx, TA, TB, Cm, rowsL, rowsR, (int)Lo.K, last, scratch, Lo.tc_scratch, st);
+    return cudaGetLastError() == cudaSuccess ? KB_OK : KB_ERR_CUDA;
+}

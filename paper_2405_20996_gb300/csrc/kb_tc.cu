@@ -20,9 +20,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
 
 #include <string>
 
@@ -414,33 +418,106 @@ static bool tc_prepare(int device) {
     return encoder() != nullptr;
 }
 
+// Split-K candidates for one contraction shape, best first by the wave model: a split s
+// gives base * s CTAs (base = batch x tiles x 2 parts) of at least 8 segments of K each,
+// whose partial sums must fit the scratch; the model rates the fraction of the last wave
+// that is busy, with a small charge per split for the reduction.
+static std::vector<int> split_candidates(int device, int M, int N, int K, int batch, size_t scratch_bytes) {
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const int mtiles = (M + MT - 1) / MT, ntiles = (N + NTT - 1) / NTT, nchunks = (K + KC - 1) / KC;
+    const long base = (long)batch * mtiles * ntiles * 2;
+    std::vector<std::pair<double, int>> c;
+    for (int s = 1; s <= 64; ++s) {
+        if ((nchunks + s - 1) / s < 8 * SEG) break;
+        if ((size_t)s * batch * M * N * sizeof(double2) > scratch_bytes) break;
+        const long units = base * s, waves = (units + sms - 1) / sms;
+        c.push_back({(double)units / (waves * sms) * (1.0 - 0.002 * s), s});
+    }
+    if (c.empty()) return {1};
+    std::stable_sort(c.begin(), c.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
+        return a.first > b.first + 1e-9;
+    });
+    std::vector<int> out;
+    for (auto& x : c) out.push_back(x.second);
+    return out;
+}
+
+// Autotuned splits, per device and shape (M, N, K, batch); filled by tc_tune.
+static std::mutex g_tune_mu;
+static std::map<std::array<int, 5>, int> g_tuned;
+
+static int tuned_split(int device, int M, int N, int K, int batch) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find({device, M, N, K, batch});
+    return it == g_tuned.end() ? 0 : it->second;
+}
+
+static bool launch_split(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
+                         void* scratch, int split, cudaStream_t st);
+
 static bool launch(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
                    void* scratch, size_t scratch_bytes, cudaStream_t st) {
+    const int nchunks = (K + KC - 1) / KC;
+    int best = tuned_split(ctx->device, M, N, K, batch);
+    if (best <= 0 || (size_t)best * batch * M * N * sizeof(double2) > scratch_bytes)
+        best = split_candidates(ctx->device, M, N, K, batch, scratch_bytes)[0];
+    const char* cps_env = std::getenv("KB_TC_CPS");   // developer override: K chunks per split
+    if (cps_env && std::atoi(cps_env) > 0) {
+        int cps = std::atoi(cps_env);
+        int s = (nchunks + cps - 1) / cps;
+        if ((size_t)s * batch * M * N * sizeof(double2) <= scratch_bytes) best = s;
+    }
+    return launch_split(ctx, At, Bt, Cm, M, N, K, batch, scratch, best, st);
+}
+
+// Time up to four of the wave model's best splits for this shape (the kernel and its
+// split-K reduction, two runs each, CUDA events on the stream) and remember the fastest.
+// Reads At/Bt and writes only the scratch and Cm, so any operands of the right shape do;
+// not while the stream is being captured.
+static bool tune(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
+                 void* scratch, size_t scratch_bytes, cudaStream_t st) {
+    if (tuned_split(ctx->device, M, N, K, batch) > 0) return true;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+    std::vector<int> cand = split_candidates(ctx->device, M, N, K, batch, scratch_bytes);
+    if (cand.size() > 4) cand.resize(4);
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return false;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return false; }
+    int best = cand[0];
+    float best_ms = 1e30f;
+    for (int s : cand) {
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(a, st);
+            if (!launch_split(ctx, At, Bt, Cm, M, N, K, batch, scratch, s, st)) { ms_min = 1e30f; break; }
+            cudaEventRecord(b, st);
+            if (cudaEventSynchronize(b) != cudaSuccess) { ms_min = 1e30f; break; }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, a, b);
+            ms_min = std::min(ms_min, ms);
+        }
+        if (ms_min < best_ms) { best_ms = ms_min; best = s; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (std::getenv("KB_TC_VERBOSE"))
+        std::fprintf(stderr, "k_tc_k3 autotune: M %d N %d K %d batch %d -> ksplit %d (%.3f ms)\n", M, N, K, batch,
+                     best, best_ms);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[{ctx->device, M, N, K, batch}] = best;
+    return true;
+}
+
+static bool launch_split(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
+                         void* scratch, int best, cudaStream_t st) {
     TcJob J;
     J.M = M; J.N = N; J.K = K; J.batch = batch;
     J.mtiles = (M + MT - 1) / MT;
     J.ntiles = (N + NTT - 1) / NTT;
     J.nchunks = (K + KC - 1) / KC;
-    int sms = 152;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    int base = batch * J.mtiles * J.ntiles * 2;     // x 2: real and imaginary part
-    int best = 1;
-    double best_eff = 0;
-    for (int s = 1; s <= 64; ++s) {
-        if ((J.nchunks + s - 1) / s < 8 * SEG) break;
-        size_t need = (size_t)s * batch * M * N * sizeof(double2);
-        if (need > scratch_bytes) break;
-        long units = (long)base * s;
-        long waves = (units + sms - 1) / sms;
-        double eff = (double)units / (waves * sms) * (1.0 - 0.002 * s);
-        if (eff > best_eff + 1e-9) { best_eff = eff; best = s; }
-    }
-    const char* cps_env = std::getenv("KB_TC_CPS");   // developer override: K chunks per split
-    if (cps_env && std::atoi(cps_env) > 0) {
-        int cps = std::atoi(cps_env);
-        int s = (J.nchunks + cps - 1) / cps;
-        if ((size_t)s * batch * M * N * sizeof(double2) <= scratch_bytes) best = s;
-    }
+    const int base = batch * J.mtiles * J.ntiles * 2;     // x 2: real and imaginary part
     J.ksplit = best;
     J.chunks_per_split = (J.nchunks + best - 1) / best;
     if (std::getenv("KB_TC_VERBOSE"))
@@ -489,7 +566,16 @@ bool kb_tc_k3(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M,
     using namespace kb::tc;
     if ((K % 4) != 0 || (reinterpret_cast<uintptr_t>(At) & 15) || (reinterpret_cast<uintptr_t>(Bt) & 15))
         return false;
+    if (ctx->autotune) tune(ctx, At, Bt, Cm, M, N, K, batch, scratch, scratch_bytes, st);
     return launch(ctx, At, Bt, Cm, M, N, K, batch, scratch, scratch_bytes, st);
+}
+
+bool kb_tc_tune(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
+                void* scratch, size_t scratch_bytes, cudaStream_t st) {
+    using namespace kb::tc;
+    if ((K % 4) != 0 || (reinterpret_cast<uintptr_t>(At) & 15) || (reinterpret_cast<uintptr_t>(Bt) & 15))
+        return false;
+    return tune(ctx, At, Bt, Cm, M, N, K, batch, scratch, scratch_bytes, st);
 }
 
 bool kb_tc_prepare(int device) { return kb::tc::tc_prepare(device); }

@@ -134,6 +134,10 @@ class Engine:
         kb.kb_vertex_eval(self.ctx, slot, channel, spin_uu, f.shape[0], f.data_ptr(), out.data_ptr(), st)
         return out
 
+    def set_autotune(self, on=True):
+        """Time the tensor-core contraction's split-K candidates per shape (kb_set_autotune)."""
+        kb.kb_set_autotune(self.ctx, on)
+
     def set_workspace_limit(self, nbytes):
         kb.kb_set_workspace_limit(self.ctx, nbytes)
 

@@ -73,6 +73,7 @@ _SIGS = {
     "kb_graph_kernel_count": [C.c_void_p, C.POINTER(C.c_ulonglong)],
     "kb_graph_destroy": [C.c_void_p],
     "kb_set_workspace_limit": [C.c_void_p, C.c_ulonglong],
+    "kb_set_autotune": [C.c_void_p, C.c_int],
     "kb_workspace_bytes": [C.c_void_p, C.POINTER(C.c_ulonglong)],
     "kb_check_device": [C.c_void_p],
     "kb_launch_count": [C.c_void_p, C.POINTER(C.c_ulonglong)],
@@ -248,6 +249,10 @@ def kb_graph_kernel_count(graph):
 
 def kb_graph_destroy(graph):
     _check(None, lib().kb_graph_destroy(graph))
+
+
+def kb_set_autotune(ctx, on=True):
+    _check(ctx, lib().kb_set_autotune(ctx, int(bool(on))))
 
 
 def kb_set_workspace_limit(ctx, nbytes):

@@ -91,3 +91,44 @@ def test_graph_rejects_bad_descriptor():
     # the context still works eagerly afterwards
     e.bubble(0, 0, 0, 1)
     torch.cuda.synchronize()
+
+
+def test_autotuned_contraction_matches_and_tunes_once():
+    """kb_set_autotune: the first mixed bubble of a shape times several split-K factors
+    (extra k_tc_k3 launches), later ones reuse the choice; the output agrees with the
+    untuned bubble to the FP32 segment-sum rounding; a step graph tunes before capturing."""
+    import numpy as np
+    import torch
+    import seeded as S
+    from helpers import rel_err
+    from paper_2405_20996_gb300 import kb
+    from paper_2405_20996_gb300.engine import Engine, StepGraph
+    cfg = dict(grids=dict(n1=37, n2w=13, n2v=11, n3w=9, n3v=11), nq=201, U=1.5, Delta=1.0, T=0.2)
+    g = cfg["grids"]
+    ch = S.seeded_vertex(g, cfg["U"], seed=41)
+    outs = []
+    for tune in (False, True):
+        e = Engine(g, cfg["nq"])
+        e.set_model(cfg["Delta"], cfg["T"])
+        e.set_autotune(tune)
+        e.set_vertex(0, U=cfg["U"], has_R=True, channels=ch, dtype=torch.complex64, symmetric=True)
+        e.alloc_out(1)
+        counts = []
+        for rep in range(2):
+            kb.kb_profile_enable(e.ctx, True)
+            e.bubble(2, 0, 0, 1, precision="mixed")
+            torch.cuda.synchronize()
+            counts.append(kb.kb_profile_read(e.ctx)["k_tc_k3"][1])
+            kb.kb_profile_enable(e.ctx, False)
+        outs.append({k: v.cpu().numpy() for k, v in e.out(1, 2).items()})
+        if tune:
+            assert counts[0] > counts[1], counts          # tuning launches only the first time
+            gr = StepGraph([e.desc(r, 0, 0, 1, precision="mixed") for r in range(3)])
+            gr.launch()
+            torch.cuda.synchronize()
+            gr.close()
+        else:
+            assert counts[0] == counts[1], counts
+        e.close()
+    for k in outs[0]:
+        assert rel_err(outs[1][k], outs[0][k]) <= 1e-6, k
