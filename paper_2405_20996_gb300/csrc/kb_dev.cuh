@@ -16,8 +16,8 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 __device__ __forceinline__ double2 cinv(double2 a) {
-    double d = a.x * a.x + a.y * a.y;
-    return make_double2(a.x / d, -a.y / d);
+    const double id = 1.0 / (a.x * a.x + a.y * a.y);
+    return make_double2(a.x * id, -a.y * id);
 }
 // z += a * b
 __device__ __forceinline__ void cfma(double2& z, double2 a, double2 b) {
@@ -132,8 +132,10 @@ __device__ inline void prop2x2(const Model& m, int which, double v, double2 P[2]
 // J / v''^2 -> pi / (2A), v'' * G -> λ [[0, 1], [1, 0]] times the sign of v'' in the
 // argument (λ = 1 but in the interaction flow), v'' * S -> [[0, 1], [1, 0]] in the
 // interaction flow (S^R -> 1/v) and 0 otherwise (Sec. II.G.6 tail reading).
+// vnode: the node frequency v''_j = A tan(pi x_j / 2) when the caller has it (have_v), so
+// that the tangent is not evaluated again.
 __device__ inline void pi_entry(const Model& m, const ChannelMaps& M, int r, int pi_kind, double A, double w,
-                                double xj, double wj, double2 out[16]) {
+                                double xj, double wj, double2 out[16], double vnode = 0.0, bool have_v = false) {
     double cr = (r == KB_CH_T) ? -1.0 : 1.0;
     double2 P3[2][2], P4[2][2], S3[2][2], S4[2][2];
     double scale;
@@ -150,8 +152,8 @@ __device__ inline void pi_entry(const Model& m, const ChannelMaps& M, int r, int
             }
         scale = KB_PI / (2.0 * A);
     } else {
-        double tn = tan(0.5 * KB_PI * xj);
-        double vpp = A * tn;
+        const double tn = have_v ? vnode / A : tan(0.5 * KB_PI * xj);
+        const double vpp = have_v ? vnode : A * tn;
         double a3, a4;
         if (r == KB_CH_P) { a3 = 0.5 * w + vpp; a4 = 0.5 * w - vpp; }
         else { a3 = vpp + 0.5 * w; a4 = vpp - 0.5 * w; }

@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(128) k_mx_prep_k2(VertexF VL, VertexF VR, DfGr
     float2 Pf[16];
     {
         double2 Pi[16];
-        pi_entry(m, J.M, J.r, J.pi_kind, G.A, (double)w.h + (double)w.l, xq[j], wq[j], Pi);
+        pi_entry(m, J.M, J.r, J.pi_kind, G.A, (double)w.h + (double)w.l, xq[j], wq[j], Pi,
+                     (double)G.n3v[G.N3v + j].h + (double)G.n3v[G.N3v + j].l, true);
 #pragma unroll
         for (int i = 0; i < 16; ++i) Pf[i] = make_float2((float)Pi[i].x, (float)Pi[i].y);
     }
@@ -114,7 +115,8 @@ __global__ void k_mx_pi3(DfGrids G, Model m, MixedJob J, const double* __restric
     if (j >= J.nq) return;
     df w = G.n3w[wi];
     double2 Pi[16];
-    pi_entry(m, J.M, J.r, J.pi_kind, G.A, (double)w.h + (double)w.l, xq[j], wq[j], Pi);
+    pi_entry(m, J.M, J.r, J.pi_kind, G.A, (double)w.h + (double)w.l, xq[j], wq[j], Pi,
+                     (double)G.n3v[G.N3v + j].h + (double)G.n3v[G.N3v + j].l, true);
     float2* o = Pt + ((size_t)wi * J.nq + j) * 16;
 #pragma unroll
     for (int i = 0; i < 16; ++i) o[i] = make_float2((float)Pi[i].x, (float)Pi[i].y);
@@ -177,7 +179,8 @@ __global__ void __launch_bounds__(128) k_mx_k1(VertexF VL, VertexF VR, DfGrids G
         float2 Pf[16];
         {
             double2 Pi[16];
-            pi_entry(m, J.M, J.r, J.pi_kind, G.A, (double)w.h + (double)w.l, xq[j], wq[j], Pi);
+            pi_entry(m, J.M, J.r, J.pi_kind, G.A, (double)w.h + (double)w.l, xq[j], wq[j], Pi,
+                     (double)G.n3v[G.N3v + j].h + (double)G.n3v[G.N3v + j].l, true);
 #pragma unroll
             for (int i = 0; i < 16; ++i) Pf[i] = make_float2((float)Pi[i].x, (float)Pi[i].y);
         }
