@@ -40,6 +40,37 @@ def _s_left(l, n_loops):       # L^(l), l = 2 .. n_loops - 1
     return 1 + n_loops + (l - 1)
 
 
+def step_entries(channels, n_loops, cached=None):
+    """The entries of one step, as plain tuples (host logic, no device):
+    ("cache", r, slot, sides), ("bubble", r, left, right, out, pi_kind, beta),
+    ("add", r, src, dst), ("join",).  Per channel r: order 1 into γ̇^(1); order l the left
+    part (into its own slot, or straight into γ̇^(l) at the last order), the central part
+    from the previous order's left part (l >= 3), the right part, and the left part added;
+    finally every order added into Γ̇."""
+    L, G, ent = n_loops, S_GAMMA, []
+    cached = cached or {}
+    for r in channels:
+        if r in cached:
+            ent.append(("cache", r, G, cached[r]))       # Γ's records
+        ent.append(("bubble", r, G, G, _s_order(1), kb.KB_PI_GS_SG, 0.0))
+    for l in range(2, L + 1):
+        ent.append(("join",))
+        prev, out = _s_order(l - 1), _s_order(l)
+        last = l == L
+        for r in channels:
+            lslot = out if last else _s_left(l, L)
+            ent.append(("bubble", r, prev, G, lslot, kb.KB_PI_GG, 0.0))                               # L
+            if l >= 3:
+                ent.append(("bubble", r, G, _s_left(l - 1, L), out, kb.KB_PI_GG, 1.0 if last else 0.0))   # C
+            ent.append(("bubble", r, G, prev, out, kb.KB_PI_GG, 1.0 if (last or l >= 3) else 0.0))    # R
+            if not last:
+                ent.append(("add", r, lslot, out))
+    for r in channels:
+        for l in range(1, L + 1):
+            ent.append(("add", r, _s_order(l), S_TOTAL))
+    return ent
+
+
 class MultiloopStep:
     def __init__(self, grids, nq, U, Delta, T, vertex, n_loops=6, precision="mixed", A=5.0, device=0,
                  symmetric=True, channels=(0, 1, 2), cache="auto", reserve_bytes=40 << 30):
@@ -119,29 +150,20 @@ class MultiloopStep:
 
     def _descs(self):
         """The step as a list of graph entries (bubbles, slot additions, joins)."""
-        L, prec, d = self.n_loops, self.precision, []
-        G = S_GAMMA
-        for r, e in self.e.items():
-            if r in self.cached:
-                d.append(kb.kb_cache_desc(e.ctx, r, G, self.cached[r]))       # Γ's records
-            d.append(e.desc(r, G, G, _s_order(1), pi_kind=kb.KB_PI_GS_SG, precision=prec))
-        for l in range(2, L + 1):
-            d.append(kb.kb_join_desc())
-            prev, out = _s_order(l - 1), _s_order(l)
-            for r, e in self.e.items():
-                last = l == L
-                lslot = out if last else _s_left(l, L)
-                d.append(e.desc(r, prev, G, lslot, precision=prec))                          # L
-                if l >= 3:
-                    d.append(e.desc(r, G, _s_left(l - 1, L), out, beta=1.0 if last else 0.0,
-                                    precision=prec))                                         # C
-                d.append(e.desc(r, G, prev, out, beta=1.0 if (last or l >= 3) else 0.0,
-                                precision=prec))                                             # R
-                if not last:
-                    d.append(kb.kb_add_desc(e.ctx, r, lslot, out))
-        for r, e in self.e.items():
-            for l in range(1, L + 1):
-                d.append(kb.kb_add_desc(e.ctx, r, _s_order(l), S_TOTAL))
+        d = []
+        for x in step_entries(self.channels, self.n_loops, self.cached):
+            if x[0] == "join":
+                d.append(kb.kb_join_desc())
+                continue
+            kind, r = x[0], x[1]
+            e = self.e[r]
+            if kind == "cache":
+                d.append(kb.kb_cache_desc(e.ctx, r, x[2], x[3]))
+            elif kind == "add":
+                d.append(kb.kb_add_desc(e.ctx, r, x[2], x[3]))
+            else:
+                _, _, left, right, out, pi, beta = x
+                d.append(e.desc(r, left, right, out, pi_kind=pi, beta=beta, precision=self.precision))
         return d
 
     def bubbles_per_step(self):
