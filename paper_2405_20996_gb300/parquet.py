@@ -179,7 +179,8 @@ class ParquetPA:
         residual)."""
         return self._gmres(lambda v: self.jvp(gamma, v), rhs, rtol, m, maxit)
 
-    def _gmres(self, apply, rhs, rtol, m, maxit):
+    @staticmethod
+    def _gmres(apply, rhs, rtol, m, maxit):
         """Restarted GMRES(m) for A x = rhs, A given by apply(v) (Arnoldi with modified
         Gram–Schmidt; the small least-squares problem min ||β e1 − H y|| solved on the host
         each step)."""

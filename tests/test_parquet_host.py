@@ -1,0 +1,59 @@
+"""Host logic of the parquet solvers, on the CPU with stand-in maps (no library calls):
+
+- restarted GMRES against a dense solve, for a nonsymmetric complex matrix, with restarts;
+- the damped fixed point and inexact Newton-Krylov on a small quadratic map
+  B(γ) = c + Q(γ, γ) (the bilinear structure of the Bethe-Salpeter right-hand side, with
+  J v = v - Q(v, γ) - Q(γ, v)): both reach the same fixed point, Newton-Krylov in a handful
+  of steps with its residual falling faster than linearly."""
+
+import numpy as np
+import torch
+
+from paper_2405_20996_gb300.parquet import ParquetPA
+
+
+def test_gmres_matches_dense_solve():
+    rng = np.random.default_rng(0)
+    n = 120
+    A = np.eye(n) * 3 + (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    At = torch.from_numpy(A)
+    x, its, res = ParquetPA._gmres(lambda v: At @ v, torch.from_numpy(b), 1e-12, 15, 400)
+    assert res <= 1e-12 and its > 15                      # converged, with at least one restart
+    ref = np.linalg.solve(A, b)
+    assert np.abs(x.numpy() - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+class _Toy(ParquetPA):
+    """Stand-in with B(γ) = c + Q(γ, γ) on C^n."""
+
+    def __init__(self, n=12, seed=1, scale=0.15):
+        rng = np.random.default_rng(seed)
+        self.T = torch.from_numpy((rng.standard_normal((n, n, n)) + 1j * rng.standard_normal((n, n, n))) * scale / n)
+        self.c = torch.from_numpy(rng.standard_normal(n) + 1j * rng.standard_normal(n))
+        self.gamma = torch.zeros(n, dtype=torch.complex128)
+        self.bubbles = 0
+
+    def Q(self, x, y):
+        return torch.einsum("ijk,j,k->i", self.T, x, y)
+
+    def bse(self, g):
+        self.bubbles += 1
+        return self.c + self.Q(g, g)
+
+    def jvp(self, g, v):
+        return v - self.Q(v, g) - self.Q(g, v)
+
+
+def test_fixed_point_and_newton_krylov_on_a_quadratic_map():
+    toy = _Toy()
+    g_fp, h_fp = toy.fixed_point(mix=0.5, tol=1e-13, maxit=2000)
+    assert h_fp[-1] <= 1e-13
+    g_nk, h_nk, lin = toy.newton_krylov(tol=1e-13, gmres_m=12)
+    assert h_nk[-1] <= 1e-13 and len(h_nk) <= 8, h_nk
+    assert torch.abs(g_fp - g_nk).max() <= 1e-11 * torch.abs(g_fp).max()
+    # fixed point of the map itself
+    assert torch.abs(toy.c + toy.Q(g_nk, g_nk) - g_nk).max() <= 1e-12 * torch.abs(g_nk).max()
+    # faster than linear: each late step gains more than the previous one
+    r = [x for x in h_nk if x > 0]
+    assert r[-2] < r[-3] ** 1.5 or r[-2] < 1e-9, h_nk
