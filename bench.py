@@ -366,7 +366,7 @@ def run_multiloop(args):
         e.set_workspace_limit(args.ws_gb << 30)
         e.set_autotune(not args.no_autotune)
     stream = torch.cuda.current_stream(dev)
-    nb = ml.bubbles_per_step()
+    nb = ml.parts_per_step()                 # delivered parts (order 2's right parts as symmetry images)
     points = nb * sum(class_points(g).values())
     graph = ml.build()
 
@@ -437,7 +437,8 @@ def run_multiloop(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "six-loop vertex flow step, a,p,t, K1 %d, K2 %dx%d, K3 %d^3, Nq %d, c64"
                                    % (g["n1"], g["n2w"], g["n2v"], g["n3w"], nq),
-                       "bubbles_per_step": nb, "points_per_step": points, "U": Ui, "T": Ti,
+                       "bubbles_per_step": nb, "bubble_calls_per_step": ml.bubbles_per_step(),
+                       "points_per_step": points, "U": Ui, "T": Ti,
                        "record_cache": {r: ml.cached[r] for r in ml.cached} or "off",
                        "l2": "flushed (256 MB write) before every timed step",
                        "launch": "one CUDA graph per step, channels as branches, a join per loop order"},

@@ -211,8 +211,9 @@ typedef struct kb_graph kb_graph;
  *                 point where the next loop order of a multiloop step reads the
  *                 derivatives of all channels of the previous one;
  *   KB_OP_CACHE   kb_vertex_cache(ctx, slot_left, channel, class_mask = sides): the record
- *                 cache is allocated at graph creation and rebuilt at every replay. */
-enum { KB_OP_BUBBLE = 0, KB_OP_ADD = 1, KB_OP_JOIN = 2, KB_OP_CACHE = 3 };
+ *                 cache is allocated at graph creation and rebuilt at every replay;
+ *   KB_OP_IMAGE   kb_vertex_image(ctx, channel, slot_left, out_slot, class_mask). */
+enum { KB_OP_BUBBLE = 0, KB_OP_ADD = 1, KB_OP_JOIN = 2, KB_OP_CACHE = 3, KB_OP_IMAGE = 4 };
 
 typedef struct {
     kb_ctx *ctx;
@@ -236,6 +237,16 @@ kb_status kb_graph_destroy(kb_graph *graph);
  * is the sum of its left, central and right parts).  Asynchronous on `stream`. */
 kb_status kb_vertex_add(kb_ctx *ctx, int channel, int slot_src, int slot_dst, unsigned class_mask, double alpha,
                         void *stream);
+
+/* Symmetry image (Sec. II.G.3): the classes (class_mask, of the destination) of channel
+ * `channel` of slot_dst are overwritten with the image of those of slot_src — conjugation
+ * in a and p (w, v, v') -> (w, v', v), conjugation after crossing in t (the same w, v <-> v'),
+ * with the Keldysh permutations, complex conjugation and sign (-1)^(1+Σa); destination K2
+ * comes from source K2' and vice versa.  For conjugation- and crossing-symmetric Γ and X the
+ * right part B_r(Γ, X) is the image of the left part B_r(X, Γ), so a multiloop order whose
+ * input is symmetric needs one of the two bubbles.  Source and destination classes must be
+ * attached, of one dtype and distinct.  Asynchronous on `stream`. */
+kb_status kb_vertex_image(kb_ctx *ctx, int channel, int slot_src, int slot_dst, unsigned class_mask, void *stream);
 
 /* Record cache of a vertex slot (mixed precision; Sec. II.D.1 class split), for the
  * bubbles of channel `channel`.  Sides (bits of `sides`):

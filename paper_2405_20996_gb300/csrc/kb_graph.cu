@@ -56,7 +56,7 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
         if (!c) return fail(c0, "kb_graph_create: null context in descriptor", KB_ERR_ARG);
         if (c->device != c0->device) return fail(c0, "kb_graph_create: contexts on different devices", KB_ERR_ARG);
         if (!c->grids_set || !c->model_set) return fail(c, "kb_graph_create: set grids and model first", KB_ERR_STATE);
-        if (d[i].op != KB_OP_BUBBLE && d[i].op != KB_OP_ADD && d[i].op != KB_OP_CACHE)
+        if (d[i].op != KB_OP_BUBBLE && d[i].op != KB_OP_ADD && d[i].op != KB_OP_CACHE && d[i].op != KB_OP_IMAGE)
             return fail(c, "kb_graph_create: unknown entry kind", KB_ERR_ARG);
         if (d[i].channel < 0 || d[i].channel > 2 || (d[i].class_mask & ~KB_MASK_ALL) ||
             (d[i].op == KB_OP_CACHE && (d[i].class_mask < 1 || d[i].class_mask > 15)) ||
@@ -149,6 +149,8 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
                         if (o != b) cudaStreamWaitEvent(br[b].st, ev[o], 0);
             } else if (x.op == KB_OP_CACHE) {
                 st = kb_vertex_cache_launch(x.ctx, x.slot_left, x.channel, x.class_mask, br[index[x.ctx]].st);
+            } else if (x.op == KB_OP_IMAGE) {
+                st = kb_vertex_image_impl(x.ctx, x.channel, x.slot_left, x.out_slot, x.class_mask, br[index[x.ctx]].st);
             } else if (x.op == KB_OP_ADD) {
                 st = kb_vertex_add_impl(x.ctx, x.channel, x.slot_left, x.out_slot, x.class_mask, x.alpha,
                                         br[index[x.ctx]].st);

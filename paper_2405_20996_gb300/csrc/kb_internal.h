@@ -149,6 +149,8 @@ kb_status kb_scale_classes(kb_ctx* ctx, int r, int so, unsigned classes, double 
 bool kb_tc_tune(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
                 void* scratch, size_t scratch_bytes, cudaStream_t st);
 kb_status kb_mixed_tune(kb_ctx* ctx, int r, int sl, int sr, unsigned mask, double beta, cudaStream_t st);
+// symmetry image of a channel's classes into another slot (kb_ops.cu)
+kb_status kb_vertex_image_impl(kb_ctx* ctx, int channel, int src, int dst, unsigned mask, cudaStream_t st);
 // slot arithmetic (kb_ops.cu)
 kb_status kb_vertex_add_impl(kb_ctx* ctx, int channel, int src, int dst, unsigned mask, double alpha,
                              cudaStream_t st);

@@ -141,3 +141,93 @@ kb_status kb_scale_classes(kb_ctx* ctx, int r, int so, unsigned classes, double 
     if (e != cudaSuccess) { ctx->err = std::string("zero classes: ") + cudaGetErrorString(e); return KB_ERR_CUDA; }
     return KB_OK;
 }
+
+// ---------------------------------------------------------------------------------------
+// Symmetry image of a channel's classes (Sec. II.G.3): for a conjugation- and
+// crossing-symmetric pair of vertices the right multiloop part B_r(Γ, X) is the image of the
+// left one B_r(X, Γ) — the conjugation in a and p ((w, v, v') -> (w, v', v), Keldysh
+// (a1'a2'|a1a2) -> (a1a2|a1'a2'), complex conjugate, sign (-1)^(1+Σa)), the conjugation after
+// crossing in t (the same w, v <-> v', both Keldysh permutations).  K2 and K2' trade places.
+namespace kb {
+namespace {
+
+__host__ __device__ constexpr int img_perm_c(int c) { return ((c & 3) << 2) | (c >> 2); }
+__host__ __device__ constexpr int img_perm_x(int c) {
+    return (((c >> 2) & 1) << 3) | (((c >> 3) & 1) << 2) | ((c & 1) << 1) | ((c >> 1) & 1);
+}
+__host__ __device__ constexpr double img_sign(int c) {
+    return (((c & 1) + ((c >> 1) & 1) + ((c >> 2) & 1) + ((c >> 3) & 1)) & 1) ? 1.0 : -1.0;
+}
+
+// dst class of layout [nw][nv][nvp][16] from the src class; swap: K3 (v, v') -> (v', v)
+template <typename T>
+__global__ void k_class_image(T* __restrict__ dst, const T* __restrict__ src, int t_channel, int swap, int nw, int nv,
+                              int nvp) {
+    const size_t total = (size_t)nw * nv * nvp * 16;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i % 16);
+        size_t rest = i / 16;
+        const int ip = (int)(rest % nvp);
+        rest /= nvp;
+        const int iv = (int)(rest % nv);
+        const int iw = (int)(rest / nv);
+        const int pc = t_channel ? img_perm_x(img_perm_c(c)) : img_perm_c(c);
+        const size_t se = swap ? ((((size_t)iw * nv + ip) * nvp + iv) * 16 + pc) : ((i / 16) * 16 + pc);
+        const double sg = img_sign(c);
+        const T v = src[se];
+        dst[i] = T{(decltype(v.x))(sg * v.x), (decltype(v.x))(-sg * v.y)};
+    }
+}
+
+}  // namespace
+}  // namespace kb
+
+kb_status kb_vertex_image_impl(kb_ctx* ctx, int channel, int src, int dst, unsigned mask, cudaStream_t st) {
+    if (!ctx) return KB_ERR_ARG;
+    if (channel < 0 || channel > 2 || src < 0 || src >= KB_MAX_SLOTS || dst < 0 || dst >= KB_MAX_SLOTS ||
+        src == dst || (mask & ~KB_MASK_ALL)) {
+        ctx->err = "kb_vertex_image: argument out of range";
+        return KB_ERR_ARG;
+    }
+    if (!ctx->grids_set) { ctx->err = "kb_vertex_image: set grids first"; return KB_ERR_STATE; }
+    const VertexDev& S = ctx->slots[src];
+    const VertexDev& D = ctx->slots[dst];
+    const Grids& g = ctx->g;
+    // destination class k is the image of source class from[k]
+    const int from[4] = {KB_K1, KB_K2P, KB_K2, KB_K3};
+    for (int k = 0; k < 4; ++k) {
+        if (!((mask >> k) & 1)) continue;
+        const int ks = from[k];
+        if (!D.cls[channel][k] || !S.cls[channel][ks] || D.dt[channel][k] != S.dt[channel][ks] ||
+            D.cls[channel][k] == S.cls[channel][ks]) {
+            ctx->err = "kb_vertex_image: classes must be attached, of one dtype and distinct";
+            return KB_ERR_ARG;
+        }
+    }
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return KB_ERR_CUDA;
+    for (int k = 0; k < 4; ++k) {
+        if (!((mask >> k) & 1)) continue;
+        const int ks = from[k];
+        int nw = g.n1, nv = 1, nvp = 1;
+        if (k == KB_K2 || k == KB_K2P) { nw = g.n2w; nv = g.n2v; }
+        if (k == KB_K3) { nw = g.n3w; nv = g.n3v; nvp = g.n3v; }
+        const size_t total = (size_t)nw * nv * nvp * 16;
+        const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)152 * 8);
+        const int tch = channel == KB_CH_T, swap = k == KB_K3;
+        KB_LAUNCH(ctx, st, "k_class_image");
+        if (D.dt[channel][k] == KB_DT_C64)
+            k_class_image<float2><<<blocks, 256, 0, st>>>((float2*)D.cls[channel][k], (const float2*)S.cls[channel][ks],
+                                                          tch, swap, nw, nv, nvp);
+        else
+            k_class_image<double2><<<blocks, 256, 0, st>>>((double2*)D.cls[channel][k],
+                                                           (const double2*)S.cls[channel][ks], tch, swap, nw, nv, nvp);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { ctx->err = std::string("kb_vertex_image: ") + cudaGetErrorString(e); return KB_ERR_CUDA; }
+    return KB_OK;
+}
+
+extern "C" kb_status kb_vertex_image(kb_ctx* ctx, int channel, int slot_src, int slot_dst, unsigned class_mask,
+                                     void* stream) {
+    return kb_vertex_image_impl(ctx, channel, slot_src, slot_dst, class_mask, reinterpret_cast<cudaStream_t>(stream));
+}

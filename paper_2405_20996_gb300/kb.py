@@ -43,7 +43,7 @@ class kb_bubble_desc(C.Structure):
                 ("beta", C.c_double), ("precision", C.c_int), ("op", C.c_int)]
 
 
-KB_OP_BUBBLE, KB_OP_ADD, KB_OP_JOIN, KB_OP_CACHE = 0, 1, 2, 3
+KB_OP_BUBBLE, KB_OP_ADD, KB_OP_JOIN, KB_OP_CACHE, KB_OP_IMAGE = 0, 1, 2, 3, 4
 KB_ERR_TOO_LARGE = 7
 KB_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -67,6 +67,7 @@ _SIGS = {
     "kb_vertex_add": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_double, C.c_void_p],
     "kb_vertex_eval": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p],
     "kb_vertex_cache": [C.c_void_p, C.c_int, C.c_int, C.c_uint, C.c_void_p],
+    "kb_vertex_image": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_void_p],
     "kb_vertex_uncache": [C.c_void_p, C.c_int],
     "kb_graph_create": [C.POINTER(C.c_void_p), C.POINTER(kb_bubble_desc), C.c_int],
     "kb_graph_launch": [C.c_void_p, C.c_void_p],
@@ -219,6 +220,15 @@ def kb_cache_desc(ctx, channel, slot, sides=3):
     """Step-graph entry: rebuild the record cache of `slot` for `channel` (sides bit 0 left,
     bit 1 right) at every replay."""
     return kb_bubble_desc(ctx, channel, slot, -1, -1, 0, sides, 0.0, 0.0, 0, KB_OP_CACHE)
+
+
+def kb_vertex_image(ctx, channel, slot_src, slot_dst, class_mask=KB_MASK_ALL, stream=0):
+    _check(ctx, lib().kb_vertex_image(ctx, channel, slot_src, slot_dst, class_mask, stream))
+
+
+def kb_image_desc(ctx, channel, slot_src, slot_dst, class_mask=KB_MASK_ALL):
+    """Step-graph entry: slot_dst = the symmetry image of slot_src (one channel)."""
+    return kb_bubble_desc(ctx, channel, slot_src, -1, slot_dst, 0, class_mask, 0.0, 0.0, 0, KB_OP_IMAGE)
 
 
 def kb_join_desc():

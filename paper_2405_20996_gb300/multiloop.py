@@ -40,13 +40,15 @@ def _s_left(l, n_loops):       # L^(l), l = 2 .. n_loops - 1
     return 1 + n_loops + (l - 1)
 
 
-def step_entries(channels, n_loops, cached=None):
+def step_entries(channels, n_loops, cached=None, image_r2=False):
     """The entries of one step, as plain tuples (host logic, no device):
     ("cache", r, slot, sides), ("bubble", r, left, right, out, pi_kind, beta),
-    ("add", r, src, dst), ("join",).  Per channel r: order 1 into γ̇^(1); order l the left
-    part (into its own slot, or straight into γ̇^(l) at the last order), the central part
-    from the previous order's left part (l >= 3), the right part, and the left part added;
-    finally every order added into Γ̇."""
+    ("image", r, src, dst), ("add", r, src, dst), ("join",).  Per channel r: order 1 into
+    γ̇^(1); order l the left part (into its own slot, or straight into γ̇^(l) at the last
+    order), the central part from the previous order's left part (l >= 3), the right part,
+    and the left part added; finally every order added into Γ̇.  image_r2: Γ is conjugation-
+    and crossing-symmetric, so γ̇^(1) (from the symmetric one-loop bubble) is too, and the
+    second order's right part is the symmetry image of its left part (kb_vertex_image)."""
     L, G, ent = n_loops, S_GAMMA, []
     cached = cached or {}
     for r in channels:
@@ -62,7 +64,10 @@ def step_entries(channels, n_loops, cached=None):
             ent.append(("bubble", r, prev, G, lslot, kb.KB_PI_GG, 0.0))                               # L
             if l >= 3:
                 ent.append(("bubble", r, G, _s_left(l - 1, L), out, kb.KB_PI_GG, 1.0 if last else 0.0))   # C
-            ent.append(("bubble", r, G, prev, out, kb.KB_PI_GG, 1.0 if (last or l >= 3) else 0.0))    # R
+            if image_r2 and l == 2 and not last:
+                ent.append(("image", r, lslot, out))                                                 # R = I_r[L]
+            else:
+                ent.append(("bubble", r, G, prev, out, kb.KB_PI_GG, 1.0 if (last or l >= 3) else 0.0))    # R
             if not last:
                 ent.append(("add", r, lslot, out))
     for r in channels:
@@ -116,6 +121,7 @@ class MultiloopStep:
                     e.attach(_s_left(l, n_loops), r, k, self.lefts[l][r][k])
         # record cache of Γ (mixed only): channel -> sides (bit 0: K2 records as left vertex,
         # 1: K2' records as right vertex, 2: K3 left tile, 3: K3 right tile with Π = G G)
+        self.image_r2 = bool(symmetric)
         self.cached = {}
         if cache and precision == "mixed":
             ns = lambda r: 2 if r == 2 else 1
@@ -151,7 +157,7 @@ class MultiloopStep:
     def _descs(self):
         """The step as a list of graph entries (bubbles, slot additions, joins)."""
         d = []
-        for x in step_entries(self.channels, self.n_loops, self.cached):
+        for x in step_entries(self.channels, self.n_loops, self.cached, image_r2=self.image_r2):
             if x[0] == "join":
                 d.append(kb.kb_join_desc())
                 continue
@@ -161,6 +167,8 @@ class MultiloopStep:
                 d.append(kb.kb_cache_desc(e.ctx, r, x[2], x[3]))
             elif kind == "add":
                 d.append(kb.kb_add_desc(e.ctx, r, x[2], x[3]))
+            elif kind == "image":
+                d.append(kb.kb_image_desc(e.ctx, r, x[2], x[3]))
             else:
                 _, _, left, right, out, pi, beta = x
                 d.append(e.desc(r, left, right, out, pi_kind=pi, beta=beta, precision=self.precision))
@@ -168,6 +176,10 @@ class MultiloopStep:
 
     def bubbles_per_step(self):
         return sum(1 for x in self.descs if x.op == kb.KB_OP_BUBBLE)
+
+    def parts_per_step(self):
+        """Bubble parts delivered per step: the bubbles and the right parts made as images."""
+        return sum(1 for x in self.descs if x.op in (kb.KB_OP_BUBBLE, kb.KB_OP_IMAGE))
 
     def zero(self):
         for t in self.total.values():
@@ -191,6 +203,8 @@ class MultiloopStep:
                 continue
             if x.op == kb.KB_OP_CACHE:
                 kb.kb_vertex_cache(x.ctx, x.slot_left, x.channel, x.class_mask, st)
+            elif x.op == kb.KB_OP_IMAGE:
+                kb.kb_vertex_image(x.ctx, x.channel, x.slot_left, x.out_slot, x.class_mask, st)
             elif x.op == kb.KB_OP_ADD:
                 kb.kb_vertex_add(x.ctx, x.channel, x.slot_left, x.out_slot, x.class_mask, x.alpha, st)
             else:

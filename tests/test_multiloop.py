@@ -114,7 +114,8 @@ def test_graph_replay_equals_eager(precision):
     for r in range(3):
         for k, v in ml.derivative(r).items():
             assert np.array_equal(v.cpu().numpy(), ta[r][k]), (r, k)
-    assert ml.bubbles_per_step() == 3 * (1 + 2 + 3 * (ml.n_loops - 2))
+    assert ml.parts_per_step() == 3 * (1 + 2 + 3 * (ml.n_loops - 2))
+    assert ml.bubbles_per_step() == ml.parts_per_step() - 3          # order 2's right parts as images
     ml.close()
 
 

@@ -33,14 +33,14 @@ def _expected(channels, n_loops):
     return order
 
 
-def _replay(channels, n_loops):
+def _replay(channels, n_loops, image_r2=False):
     """Apply the entries to slots holding sums of symbolic terms; the vertex a bubble reads
     from an order slot is named by its order and the channel left out (the mask)."""
     slots = collections.defaultdict(list)      # (slot, channel) -> list of terms
     name_of_order = {1 + l: l for l in range(1, n_loops + 1)}
     joined_upto = 1                            # orders complete in all channels
     written = set()
-    for x in step_entries(channels, n_loops):
+    for x in step_entries(channels, n_loops, image_r2=image_r2):
         if x[0] == "join":
             joined_upto += 1
             continue
@@ -48,6 +48,21 @@ def _replay(channels, n_loops):
             _, r, src, dst = x
             assert (src, r) in written
             slots[(dst, r)] = slots[(dst, r)] + slots[(src, r)]
+            written.add((dst, r))
+            continue
+        if x[0] == "image":
+            # the symmetry image of a left part B_r(X|G) is the right part B_r(G|X)
+            _, r, src, dst = x
+            (term,) = slots[(src, r)]
+            head, body = term.split("(", 1)
+            lr, pi = body[:-1].rsplit(";", 1)
+            depth, cut = 0, None
+            for i, ch in enumerate(lr):
+                depth += ch == "("
+                depth -= ch == ")"
+                if ch == "|" and depth == 0:
+                    cut = i
+            slots[(dst, r)] = ["%s(%s|%s;%s)" % (head, lr[cut + 1:], lr[:cut], pi)]
             written.add((dst, r))
             continue
         if x[0] != "bubble":
@@ -71,10 +86,11 @@ def _replay(channels, n_loops):
     return slots
 
 
+@pytest.mark.parametrize("image_r2", [False, True])
 @pytest.mark.parametrize("n_loops", [1, 2, 3, 4, 6])
-def test_entries_build_the_loop_order_recursion(n_loops):
+def test_entries_build_the_loop_order_recursion(n_loops, image_r2):
     ch = (0, 1, 2)
-    slots = _replay(ch, n_loops)
+    slots = _replay(ch, n_loops, image_r2)
     exp = _expected(ch, n_loops)
     for l in range(1, n_loops + 1):
         for r in ch:
@@ -82,8 +98,9 @@ def test_entries_build_the_loop_order_recursion(n_loops):
     for r in ch:
         total = sorted(t for l in range(1, n_loops + 1) for t in exp[(l, r)])
         assert sorted(slots[(S_TOTAL, r)]) == total
-    bubbles = sum(1 for x in step_entries(ch, n_loops) if x[0] == "bubble")
-    assert bubbles == 3 * (1 + (2 if n_loops >= 2 else 0) + 3 * max(0, n_loops - 2))
+    bubbles = sum(1 for x in step_entries(ch, n_loops, image_r2=image_r2) if x[0] == "bubble")
+    saved = 3 if (image_r2 and n_loops >= 3) else 0
+    assert bubbles == 3 * (1 + (2 if n_loops >= 2 else 0) + 3 * max(0, n_loops - 2)) - saved
 
 
 def test_slot_budget_and_cache_entries():
