@@ -1,0 +1,117 @@
+"""Vertex flow of the multiloop fRG (Sec. III.C) in the interaction-flow scheme, with the
+self-energy held fixed.
+
+The interaction flow scales the propagator, G_Λ = Λ G at Σ = 0 (Sec. III.C.3), from Λ ≈ 0
+(where γ = 0) to Λ = 1.  The vertex's reducible parts obey dγ_r/dΛ = Σ_{l ≤ n} γ̇_r^(l), the
+right-hand side of the n-loop flow built by `MultiloopStep` (one-loop part with
+Π-dot = G S + S G, S = dG/dΛ, then the left, central and right parts); with all loop orders
+the flow reproduces the parquet solution at the final Λ (the parquet approximation's R = Γ0
+does not depend on Λ).  The integrator is the embedded Runge–Kutta pair of Cash and Karp
+(orders 5 and 4, six stages) with step-size control on the maximum norm, the scheme the
+paper uses for its flows.  The self-energy flow (Σ-dot with its loop and multiloop
+corrections) is not part of this module.
+"""
+
+import numpy as np
+import torch
+
+from . import kb
+from .engine import CLASS_NAMES
+from .multiloop import S_GAMMA, MultiloopStep
+
+# Cash-Karp Butcher tableau (published coefficients of the embedded 5(4) pair)
+_C = (0.0, 1 / 5, 3 / 10, 3 / 5, 1.0, 7 / 8)
+_A = ((),
+      (1 / 5,),
+      (3 / 40, 9 / 40),
+      (3 / 10, -9 / 10, 6 / 5),
+      (-11 / 54, 5 / 2, -70 / 27, 35 / 27),
+      (1631 / 55296, 175 / 512, 575 / 13824, 44275 / 110592, 253 / 4096))
+_B5 = (37 / 378, 0.0, 250 / 621, 125 / 594, 0.0, 512 / 1771)
+_B4 = (2825 / 27648, 0.0, 18575 / 48384, 13525 / 55296, 277 / 14336, 1 / 4)
+
+
+class VertexFlow:
+    """n-loop vertex flow of one parameter point (grids, Nq, U, Δ, T) in the interaction flow."""
+
+    def __init__(self, grids, nq, U, Delta, T, n_loops=6, precision="fp64", A=5.0, device=0):
+        g = grids
+        shapes = {"K1": (g["n1"], 16), "K2": (g["n2w"], g["n2v"], 16), "K2p": (g["n2w"], g["n2v"], 16),
+                  "K3": (g["n3w"], g["n3v"], g["n3v"], 16)}
+        zero = {c: tuple(np.zeros(shapes[k], dtype=np.complex128) for k in CLASS_NAMES) for c in range(3)}
+        # Γ along the flow is not kept exactly symmetric by the central parts' discretisation,
+        # so no symmetry reduction is used
+        self.ml = MultiloopStep(grids, nq, U, Delta, T, zero, n_loops=n_loops, precision=precision, A=A,
+                                device=device, symmetric=False, cache=False)
+        e0 = self.ml.e[self.ml.channels[0]]
+        self.gamma_t = [e0.tensors[S_GAMMA][(c, k)] for c in range(3) for k in range(4)]
+        self.sizes = [t.numel() for t in self.gamma_t]
+        self.dtype = self.gamma_t[0].dtype
+        self.dev = e0.device
+        self.rhs_calls = 0
+
+    def close(self):
+        self.ml.close()
+
+    # flat state <-> the Γ slot's class tensors
+    def _store(self, y):
+        off = 0
+        for t, n in zip(self.gamma_t, self.sizes):
+            t.view(-1).copy_(y[off:off + n])
+            off += n
+
+    def _total(self):
+        return torch.cat([self.ml.total[(c, k)].reshape(-1) for c in range(3) for k in range(4)])
+
+    def channels(self, y):
+        """{channel: {class: tensor}} views of a flat state."""
+        out, off = {}, 0
+        for c in range(3):
+            out[c] = {}
+            for k in range(4):
+                n = self.sizes[4 * c + k]
+                out[c][CLASS_NAMES[k]] = y[off:off + n].view(self.gamma_t[4 * c + k].shape)
+                off += n
+        return out
+
+    def rhs(self, lam, y):
+        """dγ/dΛ at Λ = lam: the multiloop right-hand side with the interaction-flow propagator."""
+        for e in self.ml.e.values():
+            e.set_regulator(kb.KB_REG_U, lam)
+        self._store(y)
+        self.ml.zero()
+        self.ml.run_eager()
+        self.rhs_calls += 1
+        return self._total().clone()
+
+    def integrate(self, lam0, lam1, y0=None, h0=0.05, rtol=1e-6, atol=1e-10, max_steps=500):
+        """Cash–Karp integration from Λ = lam0 (state y0, default 0) to lam1; returns
+        (y, accepted steps, rejected steps)."""
+        y = torch.zeros(sum(self.sizes), dtype=self.dtype, device=self.dev) if y0 is None else y0.clone()
+        lam, h = float(lam0), float(h0)
+        acc = rej = 0
+        while lam < lam1 - 1e-14 and acc + rej < max_steps:
+            h = min(h, lam1 - lam)
+            k = []
+            for s in range(6):
+                ys = y.clone()
+                for j, a in enumerate(_A[s]):
+                    if a != 0.0:
+                        ys += (h * a) * k[j]
+                k.append(self.rhs(lam + _C[s] * h, ys))
+            y5 = y.clone()
+            y4 = y.clone()
+            for s in range(6):
+                if _B5[s] != 0.0:
+                    y5 += (h * _B5[s]) * k[s]
+                if _B4[s] != 0.0:
+                    y4 += (h * _B4[s]) * k[s]
+            scale = atol + rtol * max(float(y.abs().max()), float(y5.abs().max()))
+            err = float((y5 - y4).abs().max()) / scale
+            if err <= 1.0:
+                y, lam = y5, lam + h
+                acc += 1
+            else:
+                rej += 1
+            h *= min(5.0, max(0.2, 0.9 * (err if err > 0 else 1e-10) ** -0.2))
+        return y, acc, rej
