@@ -1,14 +1,15 @@
 """Vertex flow of the multiloop fRG (Sec. III.C) in the interaction-flow scheme, with the
 self-energy held fixed.
 
-The interaction flow scales the propagator, G_Λ = Λ G at Σ = 0 (Sec. III.C.3), from Λ ≈ 0
+The interaction flow scales the propagator, G_Λ = Λ G at Σ = 0 (Sec. III.C.2), from Λ ≈ 0
 (where γ = 0) to Λ = 1.  The vertex's reducible parts obey dγ_r/dΛ = Σ_{l ≤ n} γ̇_r^(l), the
 right-hand side of the n-loop flow built by `MultiloopStep` (one-loop part with
 Π-dot = G S + S G, S = dG/dΛ, then the left, central and right parts); with all loop orders
 the flow reproduces the parquet solution at the final Λ (the parquet approximation's R = Γ0
 does not depend on Λ).  The integrator is the embedded Runge–Kutta pair of Cash and Karp
 (orders 5 and 4, six stages) with step-size control on the maximum norm, the scheme the
-paper uses for its flows.  The self-energy flow (Σ-dot with its loop and multiloop
+paper uses for its flows (Sec. III.C.1); the step advances with the fifth-order solution and
+the difference of the two solutions is the error estimate.  The self-energy flow (Σ-dot with its loop and multiloop
 corrections) is not part of this module.
 """
 
@@ -84,9 +85,10 @@ class VertexFlow:
         self.rhs_calls += 1
         return self._total().clone()
 
-    def integrate(self, lam0, lam1, y0=None, h0=0.05, rtol=1e-6, atol=1e-10, max_steps=500):
+    def integrate(self, lam0, lam1, y0=None, h0=0.05, rtol=1e-6, atol=1e-10, max_steps=500, callback=None):
         """Cash–Karp integration from Λ = lam0 (state y0, default 0) to lam1; returns
-        (y, accepted steps, rejected steps)."""
+        (y, accepted steps, rejected steps).  callback(Λ, y) after every accepted step (e.g.
+        a checkpoint layer); a run resumes from a saved (Λ, y)."""
         y = torch.zeros(sum(self.sizes), dtype=self.dtype, device=self.dev) if y0 is None else y0.clone()
         lam, h = float(lam0), float(h0)
         acc = rej = 0
@@ -111,6 +113,8 @@ class VertexFlow:
             if err <= 1.0:
                 y, lam = y5, lam + h
                 acc += 1
+                if callback is not None:
+                    callback(lam, y)
             else:
                 rej += 1
             h *= min(5.0, max(0.2, 0.9 * (err if err > 0 else 1e-10) ** -0.2))

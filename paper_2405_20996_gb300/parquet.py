@@ -1,13 +1,13 @@
 """Parquet approximation solved with the library's bubble (Sec. III.B).
 
 The parquet approximation takes the totally irreducible vertex as the bare one, R = Γ0
-(strength U; Sec. II.B).  With the self-energy held fixed (the context's Σ table, or Σ = 0),
+(strength U; Sec. I.B).  With the self-energy held fixed (the context's Σ table, or Σ = 0),
 the reducible vertices of the three channels solve the Bethe–Salpeter equations
 
     γ_r = B_r(I_r, Γ),   I_r = Γ − γ_r,   Γ = R + γ_a + γ_p + γ_t,   r ∈ {a, p, t},
 
 where B_r carries the channel prefactor c_r (1, 1/2, −1) and γ_r is stored as its
-asymptotic classes K1, K2, K2', K3 (Sec. II.D.1).  I_r is the vertex slot of Γ with
+asymptotic classes K1, K2, K2', K3 (Sec. II.C.1).  I_r is the vertex slot of Γ with
 channel r left out of the slot's channel mask; the library still reads channel r's data
 as the crossing partner of the up-up component, as the vertex requires.
 
@@ -162,16 +162,19 @@ class ParquetPA:
         return float(diff.abs().max()) / max(float(ref.abs().max()), 1e-300)
 
     # ---- solvers ------------------------------------------------------------------------
-    def fixed_point(self, mix=0.5, tol=1e-10, maxit=500, gamma0=None):
-        """Damped iteration; returns (γ, history of relative residuals)."""
+    def fixed_point(self, mix=0.5, tol=1e-10, maxit=500, gamma0=None, callback=None):
+        """Damped iteration; returns (γ, history of relative residuals).  callback(it, γ, r)
+        after every iteration (e.g. a checkpoint); gamma0 resumes from a saved state."""
         g = torch.zeros_like(self.gamma) if gamma0 is None else gamma0.clone()
         hist = []
-        for _ in range(maxit):
+        for it in range(maxit):
             b = self.bse(g)
             hist.append(self.rel(g - b, b))
             if hist[-1] <= tol:
                 return b, hist
             g = (1.0 - mix) * g + mix * b
+            if callback is not None:
+                callback(it, g, hist[-1])
         return g, hist
 
     def gmres(self, gamma, rhs, rtol, m=30, maxit=300):
@@ -240,11 +243,12 @@ class ParquetPA:
         lam, its, res = self._gmres(lambda u: self.adjoint(gamma, u), c, rtol, m, maxit)
         return -float(torch.vdot(lam, self.dF_dU(gamma)).real), its, res
 
-    def newton_krylov(self, tol=1e-10, maxit=30, gmres_m=30, gmres_maxit=300, gamma0=None):
-        """Inexact Newton; returns (γ, history of relative residuals, GMRES products per step)."""
+    def newton_krylov(self, tol=1e-10, maxit=30, gmres_m=30, gmres_maxit=300, gamma0=None, callback=None):
+        """Inexact Newton; returns (γ, history of relative residuals, GMRES products per step).
+        callback(step, γ, r) after every Newton step; gamma0 resumes from a saved state."""
         g = torch.zeros_like(self.gamma) if gamma0 is None else gamma0.clone()
         hist, lin = [], []
-        for _ in range(maxit):
+        for step in range(maxit):
             b = self.bse(g)
             F = g - b
             hist.append(self.rel(F, b))
@@ -254,4 +258,6 @@ class ParquetPA:
             d, its, _ = self.gmres(g, -F, eta, gmres_m, gmres_maxit)
             lin.append(its)
             g = g + d
+            if callback is not None:
+                callback(step, g, hist[-1])
         return g, hist, lin
