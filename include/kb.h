@@ -2,15 +2,15 @@
  * kb.h — C ABI of the GB300 Keldysh loop-bubble library (libkb.so).
  *
  * The library evaluates the loop bubble of the single-impurity Anderson model in the
- * Keldysh formalism (KeldyshQFT paper, arXiv:2405.20996, Sec. II.E.1 "bubble_function"):
+ * Keldysh formalism (KeldyshQFT paper, arXiv:2405.20996, Sec. II.D.1 "bubble_function"):
  *
  *     B_r(w, v, v') = c_r ∫ dv''/(2πi) Γ1(w, v, v'') Π_r(w, v'') Γ2(w, v'', v'),
  *
  * in the channels r = a, p, t (c_a = 1, c_p = 1/2 × 2 equal spin terms, c_t = −1 with the
  * up-up/up-down spin sum), for all 16 Keldysh components, with the propagator pair
- * Π = G G or Π-dot = G S + S G (Sec. II.D.5).  The v'' integral is the fixed composite
+ * Π = G G or Π-dot = G S + S G (Sec. II.C.5).  The v'' integral is the fixed composite
  * 5-point Gauss-Lobatto rule in the grid's auxiliary variable x (Sec. II.G.4–II.G.5);
- * vertices are the asymptotic classes K1, K2, K2', K3 per channel (Sec. II.D.1) read by
+ * vertices are the asymptotic classes K1, K2, K2', K3 per channel (Sec. II.C.1) read by
  * linear interpolation in x (Sec. II.G.7).  Loop parts of the multiloop flow (Sec. III.C:
  * one-loop Γ∘Π-dot∘Γ, left γ-dot∘Π∘Γ, right Γ∘Π∘γ-dot, central Γ∘Π∘(left part)) and the
  * parquet Bethe–Salpeter step (Sec. III.B) are bubbles of different vertex slots and
@@ -82,15 +82,15 @@ kb_status kb_set_grids(kb_ctx *ctx, const kb_grid_desc *g);
 /* Model (Sec. I.A, III.A.1): flat hybridisation Δ, temperature T (T = 0 allowed), and the
  * effective level eps (0 for the symmetric model with the Hartree shift absorbed).
  * G^R(v) = 1/(v − eps + iΔ − Σ^R(v)), G^K = G^R [Σ^K − 2iΔ tanh(v/2T)] G^A, and the
- * hybridisation-flow single-scale propagator S = ∂G/∂Δ at fixed Σ (Sec. III.C.3). */
+ * hybridisation-flow single-scale propagator S = ∂G/∂Δ at fixed Σ (Sec. III.C.2). */
 kb_status kb_set_model(kb_ctx *ctx, double Delta, double T, double eps);
 
-/* Optional dynamic self-energy (Sec. II.D.2): n_sig points on a tan grid of scale A_sig,
+/* Optional dynamic self-energy (Sec. II.C.2): n_sig points on a tan grid of scale A_sig,
  * interleaved complex double HOST arrays (copied); Σ reads 0 at x = ±1.  sigR == NULL
  * resets Σ = 0.  sigK may be NULL (Σ^K = 0). */
 kb_status kb_set_self_energy(kb_ctx *ctx, int n_sig, double A_sig, const double *sigR, const double *sigK);
 
-/* Flow scheme (Sec. III.C.3) of the single-scale propagator S = dG/dΛ at fixed Σ used by
+/* Flow scheme (Sec. III.C.2) of the single-scale propagator S = dG/dΛ at fixed Σ used by
  * KB_PI_GS_SG (default KB_REG_DELTA):
  *   KB_REG_DELTA  hybridisation flow, Λ = Δ: S^R = -i (G^R)^2;
  *   KB_REG_U      interaction flow at Λ = lambda > 0: the propagator itself becomes
@@ -103,7 +103,7 @@ kb_status kb_set_self_energy(kb_ctx *ctx, int n_sig, double A_sig, const double 
  * limits v G -> λ [[0,1],[1,0]] and v S -> [[0,1],[1,0]] (interaction flow) or 0. */
 kb_status kb_set_regulator(kb_ctx *ctx, int kind, double lambda);
 
-/* Katanin substitution (Sec. III.C.3: the differentiated propagator G-dot = S + G Σ-dot G):
+/* Katanin substitution (Sec. III.C.2: the differentiated propagator G-dot = S + G Σ-dot G):
  * n_dsig values of dΣ^R/dΛ (and dΣ^K/dΛ, may be NULL) on the tan grid of scale A_dsig,
  * interleaved complex double HOST arrays (copied), read linearly in x with zero at
  * x = ±1.  KB_PI_GS_SG then uses G-dot in place of S.  dsigR == NULL switches it off. */
@@ -141,7 +141,7 @@ kb_status kb_set_vertex_class(kb_ctx *ctx, int slot, int channel, int cls, void 
 
 /* The bubble of channel `channel` with Γ1 = slot_left, Γ2 = slot_right and propagator pair
  * pi_kind, written into the classes (class_mask bits 1 << KB_K1 .. 1 << KB_K3) of channel
- * `channel` of slot out_slot:  out ← alpha · B + beta · out  (the paper adds, Sec. II.E.1;
+ * `channel` of slot out_slot:  out ← alpha · B + beta · out  (the paper adds, Sec. II.D.1;
  * beta = 1 reproduces that).  Γ1 is the vertex carrying the external v (for t: the vertex on
  * the external legs 1', 1).  precision: KB_PREC_FP64 (plain, every step in FP64) or
  * KB_PREC_MIXED (FP32 gather, 3xTF32 tensor-core contraction with FP32 accumulation;
@@ -171,7 +171,7 @@ kb_status kb_bubble(kb_ctx *ctx, int channel, int slot_left, int slot_right, int
  *                    [w][node][side], w on the K1 (n1), K2 (n2w; K2 and K2' add) or K3
  *                    (n3w) grid, side 0 the propagator at v''+w/2 (a, t) or w/2+v'' (p),
  *                    side 1 at v''-w/2 or w/2-v''; G^A = (G^R)* and G^K = tanh(v/2T)(G^R -
- *                    G^A) are taken as functions of G^R (equilibrium FDR, Sec. II.D.4).
+ *                    G^A) are taken as functions of G^R (equilibrium FDR, Sec. II.C.4).
  *                    Needs pi_kind KB_PI_GG and no self-energy table (else
  *                    KB_ERR_UNSUPPORTED; also with a dΣ/dΛ table); the tail nodes (v'' = ±inf) carry no G dependence.
  * Gradient classes must be complex128 and must not alias any input.  The bare part
@@ -248,7 +248,7 @@ kb_status kb_vertex_add(kb_ctx *ctx, int channel, int slot_src, int slot_dst, un
  * attached, of one dtype and distinct.  Asynchronous on `stream`. */
 kb_status kb_vertex_image(kb_ctx *ctx, int channel, int slot_src, int slot_dst, unsigned class_mask, void *stream);
 
-/* Record cache of a vertex slot (mixed precision; Sec. II.D.1 class split), for the
+/* Record cache of a vertex slot (mixed precision; Sec. II.C.1 class split), for the
  * bubbles of channel `channel`.  Sides (bits of `sides`):
  *   1  the part of the vertex that the K2 contraction gathers at every node as the left
  *      vertex — the other channels' classes at the converted frequencies, FP32, 16
@@ -272,7 +272,7 @@ kb_status kb_vertex_uncache(kb_ctx *ctx, int slot);
 
 /* The full vertex of slot `slot` — its bare part and the classes of its included channels
  * (excluded channels still enter the up-up component as crossing partners), each read at
- * the point converted to its own channel variables (Sec. II.D.1) and interpolated linearly
+ * the point converted to its own channel variables (Sec. II.C.1) and interpolated linearly
  * in x (Sec. II.G.7) — at n points (w, v, v') in the variables of channel `channel`:
  * freqs is a DEVICE array [n][3] of doubles (±inf allowed: a class at an infinite argument
  * reads 0), out a DEVICE complex128 array [n][16] in the Keldysh order above; spin_uu != 0

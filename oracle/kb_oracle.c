@@ -10,9 +10,9 @@
  *   B_r(w, v, v')^{alpha} = c_r * sum_j  w_j/(2 pi i) * J(x_j)
  *        * sum_{beta} Gamma1^{...}(w, v, v''_j) Pi_r^{beta}(w, v''_j) Gamma2^{...}(w, v''_j, v')
  *
- *   - the bubble Gamma1 o Pi_r o Gamma2 of two vertices in channel r (Sec. II.E.1,
+ *   - the bubble Gamma1 o Pi_r o Gamma2 of two vertices in channel r (Sec. II.D.1,
  *     "bubble_function"), with the propagator pair Pi = G G or Pi-dot = G S + S G
- *     (Sec. II.D.5, "Bubble");
+ *     (Sec. II.C.5, "Bubble");
  *   - the v'' integral taken by a fixed composite 5-point Gauss-Lobatto rule in the
  *     auxiliary variable x of the frequency grid v = A tan(pi x / 2)
  *     (Sec. II.G.4 and II.G.5; x covers [-1, 1] including v = +-inf, where the
@@ -21,7 +21,7 @@
  *     by multilinear interpolation in x ("linear_on_aux", Sec. II.G.7) with zero
  *     values at x = +-1;
  *   - the output split into classes by which parts of the two vertices are used
- *     (Sec. II.D.1: parts whose external legs do / do not meet at one bare vertex).
+ *     (Sec. II.C.1: parts whose external legs do / do not meet at one bare vertex).
  *
  * Conventions (readings of the paper where it defers to its companion paper):
  *   Keldysh: 1 = classical, 2 = quantum; G^{1|1} = G^K, G^{1|2} = G^R, G^{2|1} = G^A,
@@ -79,7 +79,7 @@ static int stencil(double nu, int n, double A, int idx[2], double wt[2]) {
 }
 
 /* ------------------------------------------------------------------------------------
- * Vertex object: bare part plus, per channel, the four asymptotic classes (Sec. II.D.1).
+ * Vertex object: bare part plus, per channel, the four asymptotic classes (Sec. II.C.1).
  * ------------------------------------------------------------------------------------ */
 typedef struct {
     int n1, n2w, n2v, n3w, n3v;   /* class grids (shared by the three channels) */
@@ -216,7 +216,7 @@ static void parts_uu(const ovtx *V, int r, double w, double v, double vp, int wa
     }
 }
 
-/* Selection of vertex parts (Sec. II.D.1).  For the left vertex Gamma1(w, v, v''):
+/* Selection of vertex parts (Sec. II.C.1).  For the left vertex Gamma1(w, v, v''):
  *   SEL_ZERO = R + K1_r + K2'_r   (independent of the external v)
  *   SEL_NU   = K2_r + K3_r + other channels
  * for the right vertex Gamma2(w, v'', v'):
@@ -242,10 +242,10 @@ static void vertex_select(const ovtx *V, int r, int spin_uu, int side_right, int
 }
 
 /* ------------------------------------------------------------------------------------
- * Propagators (Sec. II.D.4, III.C.3): G^R = 1 / (v - eps + i Delta - Sigma^R(v)),
+ * Propagators (Sec. II.C.4, III.C.2): G^R = 1 / (v - eps + i Delta - Sigma^R(v)),
  * G^A = (G^R)*, G^K = G^R [Sigma^K - 2 i Delta tanh(v/2T)] G^A.  Sigma tables (optional)
  * are interpolated linearly in x with zero at x = +-1.
- * Single-scale propagator S = d/dLambda G at fixed Sigma of the flow scheme (Sec. III.C.3):
+ * Single-scale propagator S = d/dLambda G at fixed Sigma of the flow scheme (Sec. III.C.2):
  *   reg 0, hybridisation flow: Lambda = Delta;
  *   reg 1, interaction flow: G^R = lam / (v - eps + i Delta - lam Sigma^R), i.e. the bare
  *          inverse propagator divided by lam, and G^K = G^R [Sigma^K - 2 i Delta th / lam] G^A
@@ -350,7 +350,7 @@ typedef struct {
     double w, v, vp;
 } bctx;
 
-/* Arguments of the two propagators of the bubble in channel r (Sec. II.D.5):
+/* Arguments of the two propagators of the bubble in channel r (Sec. II.C.5):
  * a, t: v'' + w/2 and v'' - w/2; p: w/2 + v'' and w/2 - v''. */
 static void prop_args(int r, double w, double nupp, double *a3, double *a4) {
     if (r == 1) { *a3 = w / 2 + nupp; *a4 = w / 2 - nupp; }
@@ -625,7 +625,7 @@ int og_bubble_points_adaptive(const ovtx *V1, const ovtx *V2, const oprop *P, in
  * respect to a stored value e is sum over outputs o of conj(dB_o/de) bar(B_o).
  * With respect to the retarded propagator at one sample frequency, the advanced and
  * Keldysh components are functions of it in equilibrium without a self-energy table:
- * G^A = (G^R)*, G^K = tanh(v/2T) (G^R - G^A) (the FDR, Sec. II.D.4), so
+ * G^A = (G^R)*, G^K = tanh(v/2T) (G^R - G^A) (the FDR, Sec. II.C.4), so
  *     bar(G^R) = bar(G^{1|2}) + conj(bar(G^{2|1})) + th (bar(G^{1|1}) - conj(bar(G^{1|1}))).
  * The bare part R = Gamma_0 is a fixed parameter and gets no gradient.
  * ------------------------------------------------------------------------------------ */

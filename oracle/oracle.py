@@ -22,7 +22,7 @@ LIB = os.path.join(BUILD, "liboracle.so")
 CH_A, CH_P, CH_T = 0, 1, 2
 SEL_ZERO, SEL_NU, SEL_FULL = 0, 1, 2
 PI_GG, PI_GS = 0, 1
-# (left selection, right selection) of each output class (Sec. II.D.1)
+# (left selection, right selection) of each output class (Sec. II.C.1)
 CLASS_SEL = {"K1": (SEL_ZERO, SEL_ZERO), "K2": (SEL_NU, SEL_ZERO),
              "K2p": (SEL_ZERO, SEL_NU), "K3": (SEL_NU, SEL_NU)}
 

@@ -10,7 +10,7 @@
 namespace kb {
 
 // Keldysh index maps per channel, from the bubble's leg routing (Sec. III.B diagrams with
-// the channel parametrisations of Sec. II.D.1):
+// the channel parametrisations of Sec. II.C.1):
 //   a: Gamma1^{a1' b4' | b3 a2} G^{b3|b3'}(v''+w/2) G^{b4|b4'}(v''-w/2) Gamma2^{b3' a2' | a1 b4}
 //      A = (a1', a2), B = (b4', b3), D = (b3', b4), C = (a2', a1)
 //   p: Gamma1^{a1' a2' | b3 b4} G^{b3|b3'}(w/2+v'') G^{b4|b4'}(w/2-v'') Gamma2^{b3' b4' | a1 a2}

@@ -1,6 +1,6 @@
 // Device helpers shared by the FP64 and mixed-precision kernels: complex FP64 arithmetic,
-// propagators (Sec. II.D.4, III.C.3), the x-grid stencil (Sec. II.G.4, II.G.7), channel
-// frequency maps (Sec. II.D.1) and the Pi table (Sec. II.D.5).
+// propagators (Sec. II.C.4, III.C.2), the x-grid stencil (Sec. II.G.4, II.G.7), channel
+// frequency maps (Sec. II.C.1) and the Pi table (Sec. II.C.5).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -43,7 +43,7 @@ __device__ __forceinline__ int xstencil(double v, int n, double A, double& t) {
     return k;
 }
 
-// legs (v1', v2', v1, v2) from channel variables (w, v, vp) and back (Sec. II.D.1)
+// legs (v1', v2', v1, v2) from channel variables (w, v, vp) and back (Sec. II.C.1)
 __device__ __forceinline__ void legs_of(int r, double w, double v, double vp, double L[4]) {
     if (r == KB_CH_A) { L[0] = v + 0.5 * w; L[3] = v - 0.5 * w; L[2] = vp + 0.5 * w; L[1] = vp - 0.5 * w; }
     else if (r == KB_CH_P) { L[0] = 0.5 * w + v; L[1] = 0.5 * w - v; L[2] = 0.5 * w + vp; L[3] = 0.5 * w - vp; }

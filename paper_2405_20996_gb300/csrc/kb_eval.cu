@@ -1,6 +1,6 @@
 // Point evaluation of a stored vertex: the full vertex of a slot — the bare part and the
 // asymptotic classes of its channels, each read at the point converted to its own channel
-// variables (Sec. II.D.1) and interpolated linearly in x (Sec. II.G.7) — at arbitrary
+// variables (Sec. II.C.1) and interpolated linearly in x (Sec. II.G.7) — at arbitrary
 // frequencies given in the variables of one channel.  The paper's post-processing reads
 // such slices of the full vertex, e.g. the t-channel plane (w_t = 0, v_t, v'_t).
 #include <cstdio>

@@ -27,7 +27,7 @@ struct VertexDev {
     int symmetric;           // declared conjugation + crossing symmetric
 };
 
-// Propagator model (Sec. III.A.1, III.C.3).
+// Propagator model (Sec. III.A.1, III.C.2).
 struct Model {
     double Delta, T, eps;
     int n_sig;

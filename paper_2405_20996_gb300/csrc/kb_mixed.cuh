@@ -109,7 +109,7 @@ __device__ __forceinline__ void cmac2(float2& acc, float2 x, float2 y) {
     acc = __ffma2_rn(make_float2(-x.y, x.y), make_float2(y.y, y.x), acc);
 }
 
-// legs (v1', v2', v1, v2) and channel variables in double-float (Sec. II.D.1)
+// legs (v1', v2', v1, v2) and channel variables in double-float (Sec. II.C.1)
 __device__ __forceinline__ void df_legs(int r, df w, df v, df vp, df L[4]) {
     df hw = df_half(w);
     if (r == KB_CH_A) { L[0] = df_add(v, hw); L[3] = df_sub(v, hw); L[2] = df_add(vp, hw); L[1] = df_sub(vp, hw); }

@@ -11,7 +11,7 @@
 // and the tile gradients are scattered through the transpose of the interpolation, the
 // class split, the channel conversion and the up-up exchange into the gradient slots
 // (atomic FP64 adds).  The Pi gradient is pulled back to G^R at the two sample frequencies
-// of every (w, node), with G^A = (G^R)* and G^K = tanh(v/2T)(G^R - G^A) (FDR, Sec. II.D.4).
+// of every (w, node), with G^A = (G^R)* and G^K = tanh(v/2T)(G^R - G^A) (FDR, Sec. II.C.4).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>

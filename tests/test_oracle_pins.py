@@ -78,7 +78,7 @@ def test_pt2_k1_matches_independent_bubble(r):
         assert abs(Rt - ref) <= 1e-9 * abs(ref), (om, Rt, ref)
         assert np.abs(B[i, ee]).max() <= 1e-12 * abs(ref)                       # causality
         assert abs(Ad - np.conj(Rt)) <= 1e-13 * abs(ref)                        # K1^A = (K1^R)*
-        # bosonic FDR: K1^K = coth(w/2T) (K1^R - K1^A)  (Sec. II.F.2, K1 relation)
+        # bosonic FDR: K1^K = coth(w/2T) (K1^R - K1^A)  (Sec. II.E.2, K1 relation)
         assert abs(np.tanh(om / (2 * T)) * Kd - (Rt - Ad)) <= 1e-9 * abs(ref)
         # the printed form: Im K1^R = -(i/2) tanh(w/2T) K1^K
         assert abs(Rt.imag - (-0.5j * np.tanh(om / (2 * T)) * Kd).real) <= 1e-9 * abs(ref)
@@ -138,7 +138,7 @@ def test_conjugation_and_crossing_of_seeded_bubble(r):
 @pytest.mark.parametrize("r", [0, 1, 2])
 def test_class_split_sums_to_unsplit(r):
     """K1 + K2 + K2' + K3 at one (w, v, v') equals the contraction of the full vertices
-    (linearity of the class split, Sec. II.D.1)."""
+    (linearity of the class split, Sec. II.C.1)."""
     V = O.Vertex(G_TINY, U=1.0, has_R=True, channels=S.seeded_vertex(G_TINY, 1.0, seed=11))
     P = O.Prop(Delta=1.0, T=0.1)
     f = np.array([[0.3, -1.1, 2.2], [-2.0, 0.5, 0.5], [0.0, 7.0, -0.2]])
@@ -254,8 +254,8 @@ def test_fixed_rule_vs_adaptive_brute_force():
 
 
 def test_propagator_sum_rule_kk_fdr():
-    """G^R of the flat-band model: spectral sum rule (Sec. II.F.4), Kramers-Kronig
-    (Sec. II.F.3) and the FDR G^K = 2i tanh(v/2T) Im G^R (Sec. II.F.2); also with a
+    """G^R of the flat-band model: spectral sum rule (Sec. II.E.4), Kramers-Kronig
+    (Sec. II.E.3) and the FDR G^K = 2i tanh(v/2T) Im G^R (Sec. II.E.2); also with a
     Sigma table the Dyson G satisfies the same FDR when Sigma^K obeys it."""
     P = O.Prop(Delta=1.0, T=0.1)
     A = lambda v: -O.prop_eval(P, 0, np.atleast_1d(v))[:, 0, 1].imag / np.pi

@@ -1,4 +1,4 @@
-"""Pins of the oracle's flow-scheme propagators (Sec. III.C.3), independent of its code:
+"""Pins of the oracle's flow-scheme propagators (Sec. III.C.2), independent of its code:
 
 - S = dG/dLambda at fixed Sigma, for the hybridisation (Lambda = Delta), interaction
   (Lambda = lam) and temperature (Lambda = T) flows, against central finite differences of

@@ -1,4 +1,4 @@
-"""Flow schemes of the single-scale propagator on the GPU (kb_set_regulator, Sec. III.C.3):
+"""Flow schemes of the single-scale propagator on the GPU (kb_set_regulator, Sec. III.C.2):
 the interaction and temperature flows, Π = G G and Π-dot = G S + S G, FP64 (<= 1e-10) and
 mixed (<= 1e-6) against the oracle with the same scheme, every channel and class; bad
 scheme arguments are refused."""
