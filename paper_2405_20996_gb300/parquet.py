@@ -11,10 +11,12 @@ asymptotic classes K1, K2, K2', K3 (Sec. II.C.1).  I_r is the vertex slot of Γ 
 channel r left out of the slot's channel mask; the library still reads channel r's data
 as the crossing partner of the up-up component, as the vertex requires.
 
-Two solvers; the residual bubbles go through the library's plain FP64 path:
+Three solvers; the residual bubbles go through the library's plain FP64 path:
 
 - the damped fixed point γ ← (1 − m) γ + m B(γ) with mixing m, the scheme the paper
   describes for its parquet solver, stopped on the relative maximum-norm change;
+- Anderson acceleration of that iteration over the last few iterates (`anderson`), the
+  paper's other mixing scheme;
 - Newton–Krylov on F(γ) = γ − B(γ): each Newton step solves J δ = −F by restarted
   GMRES.  B_r is bilinear in its two vertices, so the Jacobian product is
       J v = v − Σ_r [B_r(V_I_r, Γ) + B_r(I_r, V)],   V = Σ_r v_r (no bare part),
@@ -173,6 +175,49 @@ class ParquetPA:
             if hist[-1] <= tol:
                 return b, hist
             g = (1.0 - mix) * g + mix * b
+            if callback is not None:
+                callback(it, g, hist[-1])
+        return g, hist
+
+    def anderson(self, mix=0.5, m=5, tol=1e-10, maxit=500, gamma0=None, callback=None, cond_max=1e10):
+        """Anderson acceleration of the damped iteration (the paper's alternative to plain
+        mixing in the parquet solver, Sec. III.B), in the form of Walker and Ni (SIAM J.
+        Numer. Anal. 49, 1715 (2011)): with g_k = BSE(γ_k), f_k = g_k − γ_k and the last m
+        differences ΔG, ΔF of g and f, the coefficients c minimise ||f_k − ΔF c||_2 and
+        γ_{k+1} = (g_k − ΔG c) − (1 − mix)(f_k − ΔF c).  The least-squares problem is solved by
+        QR; the oldest differences are dropped while R's diagonal spans more than cond_max.
+        m = 0 is the damped iteration.  Returns (γ, history of relative residuals)."""
+        g = torch.zeros_like(self.gamma) if gamma0 is None else gamma0.clone()
+        hist = []
+        dF, dG = [], []
+        f_prev = b_prev = None
+        for it in range(maxit):
+            b = self.bse(g)
+            f = b - g
+            hist.append(self.rel(f, b))
+            if hist[-1] <= tol:
+                return b, hist
+            if f_prev is not None and m > 0:
+                dF.append(f - f_prev)
+                dG.append(b - b_prev)
+                if len(dF) > m:
+                    dF.pop(0)
+                    dG.pop(0)
+            f_prev, b_prev = f, b
+            g_next = None
+            while dF:
+                Q, R = torch.linalg.qr(torch.stack(dF, dim=1))
+                d = R.diagonal().abs()
+                if float(d.min()) * cond_max < float(d.max()) or float(d.max()) == 0.0:
+                    dF.pop(0)
+                    dG.pop(0)
+                    continue
+                c = torch.linalg.solve_triangular(R, (Q.conj().T @ f).unsqueeze(1), upper=True).squeeze(1)
+                fa = f - torch.stack(dF, dim=1) @ c
+                ba = b - torch.stack(dG, dim=1) @ c
+                g_next = ba - (1.0 - mix) * fa
+                break
+            g = (1.0 - mix) * g + mix * b if g_next is None else g_next
             if callback is not None:
                 callback(it, g, hist[-1])
         return g, hist

@@ -4,7 +4,11 @@
 - the damped fixed point and inexact Newton-Krylov on a small quadratic map
   B(γ) = c + Q(γ, γ) (the bilinear structure of the Bethe-Salpeter right-hand side, with
   J v = v - Q(v, γ) - Q(γ, v)): both reach the same fixed point, Newton-Krylov in a handful
-  of steps with its residual falling faster than linearly."""
+  of steps with its residual falling faster than linearly;
+- Anderson acceleration: with no memory it is the damped iteration step for step; on an
+  affine map with undamped updates and memory at least the dimension it terminates like
+  GMRES (Walker and Ni, Theorem 2.2); on the quadratic map it needs fewer right-hand sides
+  than the damped iteration and reaches the same fixed point."""
 
 import numpy as np
 import torch
@@ -57,3 +61,48 @@ def test_fixed_point_and_newton_krylov_on_a_quadratic_map():
     # faster than linear: each late step gains more than the previous one
     r = [x for x in h_nk if x > 0]
     assert r[-2] < r[-3] ** 1.5 or r[-2] < 1e-9, h_nk
+
+
+class _Affine(ParquetPA):
+    """Stand-in with B(γ) = c + A γ (spectral radius 0.9) on C^n."""
+
+    def __init__(self, n=8, seed=2):
+        rng = np.random.default_rng(seed)
+        A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        A *= 0.9 / np.abs(np.linalg.eigvals(A)).max()
+        self.A = torch.from_numpy(A)
+        self.c = torch.from_numpy(rng.standard_normal(n) + 1j * rng.standard_normal(n))
+        self.gamma = torch.zeros(n, dtype=torch.complex128)
+        self.bubbles = 0
+        self.sol = torch.from_numpy(np.linalg.solve(np.eye(n) - A, self.c.numpy()))
+
+    def bse(self, g):
+        self.bubbles += 1
+        return self.c + self.A @ g
+
+
+def test_anderson_without_memory_is_the_damped_iteration():
+    a, b = _Toy(), _Toy()
+    _, h_fp = a.fixed_point(mix=0.4, tol=0.0, maxit=25)
+    g_aa, h_aa = b.anderson(mix=0.4, m=0, tol=0.0, maxit=25)
+    assert h_aa == h_fp
+
+
+def test_anderson_terminates_like_gmres_on_an_affine_map():
+    aff = _Affine(n=8)
+    g, h = aff.anderson(mix=1.0, m=20, tol=1e-12, maxit=40)
+    assert h[-1] <= 1e-12 and len(h) <= 8 + 3, h
+    assert torch.abs(g - aff.sol).max() <= 1e-10 * torch.abs(aff.sol).max()
+    # the damped iteration contracts only by the spectral radius per step
+    _, h_fp = _Affine(n=8).fixed_point(mix=1.0, tol=1e-12, maxit=40)
+    assert h_fp[-1] > 1e-6
+
+
+def test_anderson_on_the_quadratic_map():
+    toy = _Toy()
+    g_fp, h_fp = toy.fixed_point(mix=0.5, tol=1e-13, maxit=2000)
+    n_fp = toy.bubbles
+    toy.bubbles = 0
+    g_aa, h_aa = toy.anderson(mix=0.5, m=5, tol=1e-13, maxit=2000)
+    assert h_aa[-1] <= 1e-13 and toy.bubbles <= 0.6 * n_fp, (toy.bubbles, n_fp)
+    assert torch.abs(g_aa - g_fp).max() <= 1e-11 * torch.abs(g_fp).max()
