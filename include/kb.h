@@ -111,7 +111,7 @@ kb_status kb_set_self_energy_derivative(kb_ctx *ctx, int n_dsig, double A_dsig, 
                                         const double *dsigK);
 
 /* Vertex slot `slot` (0 .. KB_MAX_SLOTS-1): the bare part R = Γ0 of the parquet
- * approximation (Sec. I.B: +U/2 on components with an odd number of quantum indices)
+ * approximation (Sec. I.B: -U/2 on components with an odd number of quantum indices)
  * when has_R != 0, and no classes.  Classes are attached with kb_set_vertex_class. */
 kb_status kb_set_vertex(kb_ctx *ctx, int slot, int has_R, double U);
 

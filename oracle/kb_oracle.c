@@ -26,7 +26,10 @@
  * Conventions (readings of the paper where it defers to its companion paper):
  *   Keldysh: 1 = classical, 2 = quantum; G^{1|1} = G^K, G^{1|2} = G^R, G^{2|1} = G^A,
  *   G^{2|2} = 0.  Bare vertex (parquet approximation R = Gamma_0, Sec. I.B):
- *   Gamma_0^{up,down} = +U/2 on components with an odd number of quantum indices.
+ *   Gamma_0^{up,down} = -U/2 on components with an odd number of quantum indices (the
+ *   sign that, with the bubble's measure below and the loop's sign of the Schwinger-Dyson
+ *   equation of Sec. III.B, gives the Hartree shift U (n - 1/2) of a repulsive U and a
+ *   causal second-order self-energy; see og_loop).
  *   Channel variables: a: w = v1'-v2, v = (v1'+v2)/2, v' = (v1+v2')/2;
  *   p: w = v1'+v2', v = (v1'-v2')/2, v' = (v1-v2)/2; t: w = v2'-v2, v = (v1'+v1)/2,
  *   v' = (v2'+v2)/2.  Spin: only the up-down component is stored; the up-up component
@@ -97,7 +100,7 @@ static int popc4(int c) { return (c & 1) + ((c >> 1) & 1) + ((c >> 2) & 1) + ((c
 
 /* Bare vertex, up-down component, 16 Keldysh components (Sec. I.B, PA R = Gamma_0). */
 static void bare_vertex(const ovtx *V, cplx out[16]) {
-    for (int c = 0; c < 16; ++c) out[c] = (V->has_R && (popc4(c) & 1)) ? 0.5 * V->U : 0.0;
+    for (int c = 0; c < 16; ++c) out[c] = (V->has_R && (popc4(c) & 1)) ? -0.5 * V->U : 0.0;
 }
 
 /* Add f * class(w, v, v') of channel ch into out (16 comps). k: 0 K1, 1 K2, 2 K2', 3 K3. */
@@ -877,4 +880,209 @@ int og_bubble_vjp_points(const ovtx *V1, const ovtx *V2, const oprop *P, int pi_
     free(xq);
     free(wq);
     return fail ? -2 : 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Self-energy loop (Sec. II.D.2, the `loop` function): the vertex closed by one
+ * propagator line,
+ *   Sigma^{a1'|a1}(v) = - int dv'/(2 pi i) sum_{a2', a2} Gamma_s^{a1' a2'|a1 a2}(v, v'|v, v')
+ *                          P^{a2|a2'}(v'),
+ *   Gamma_s = Gamma_ud + Gamma_uu   (the internal line's spin summed, SU(2)),
+ * the vertex read in t-channel variables (w_t = 0, v_t = v, v'_t = v').  Sigma is a 2x2
+ * Keldysh matrix: (q|c) = Sigma^R, (c|q) = Sigma^A, (q|q) = Sigma^K, (c|c) = 0 for a causal
+ * result.  Readings (the loop's equation is in the companion paper): the measure is the
+ * bubble's dv'/(2 pi i) and the sign is the minus of the first term of the Schwinger-Dyson
+ * equation (Sec. III.B):
+ *   Sigma = - int dv'/(2 pi i) Gamma_s . P,
+ * so that the bare vertex (-U/2) gives the Hartree shift U (n - 1/2) of Sec. III.A.1 and the
+ * second-order vertex gives a causal self-energy obeying the FDR; the v' integral is the
+ * symmetric principal value at v' = +-inf (equal-time average of the retarded and advanced
+ * lines).
+ *
+ * Discretisation (the bubble's composite GL5 rule in x = (2/pi) atan(v'/A)): the vertex
+ * splits into its v'-independent part C(v) (R, K1_t(0), K2_t(0, v) and the crossed
+ * K1_a(0), K2_a(0, v)) and the rest D(v, v'), which vanishes at x = +-1.  Then
+ *   Sigma = C(v) . I_P + int D P,   I_P = int dv' [P(v') - M v'/(v'^2 + A^2)]
+ * with M = lim v' P(v'): the subtracted term is odd and integrates to zero.  At x = +-1 the
+ * rule takes the limits of the integrands times J(x) = dv'/dx:
+ *   J [P - M v'/(v'^2+A^2)] -> (pi / 2A) N_+-,   N_+- = lim_{v' -> +-inf} v' (v' P - M);
+ *   J D P -> +-M . D_+-,   D_+- = sum over the classes that decay through one argument
+ *   y ~ +-v' of (their value at the last grid node along that argument) (N + 1)/2,
+ * since a class interpolated to zero at x = +-1 falls like (1 -+ x_y) (N + 1)/2 and
+ * (1 -+ x_y) v' -> 2A/pi, while J P -> (pi/2A) M v'.  Classes with two diverging
+ * arguments fall like 1/v'^2 and drop out.  Only P = G is supported here.
+ * ------------------------------------------------------------------------------------ */
+
+/* N_+- of G (side = +1 or -1): with Sigma tables vanishing at x = +-1,
+ * v' G^R = lam v' / (v' - eps + i Delta - lam Sigma^R) gives N^R = lam (eps - i Delta),
+ * N^A = (N^R)*, and v'^2 G^K -> lam^2 (-2 i Delta tanh(+-inf) / lam). */
+static void prop_tail2(const oprop *P, int side, cplx N[2][2]) {
+    const double lam = (P->reg == 1) ? P->lam : 1.0;
+    const double th = (double)side;              /* tanh(v'/2T) at v' = +-inf, any T >= 0 */
+    N[0][1] = lam * (P->eps - I * P->Delta);
+    N[1][0] = conj(N[0][1]);
+    N[0][0] = -2.0 * I * P->Delta * th * lam;
+    N[1][1] = 0;
+}
+
+/* f * (value of class k of channel ch at its edge node along `axis` (0 w, 1 v, 2 v'),
+ * side +1 = last node, -1 = first node, interpolated in the other arguments), times
+ * (N + 1)/2 = 1 / (1 - X_last). */
+static void class_edge(const ovtx *V, int ch, int k, int axis, int side, double w, double v, double vp, double f,
+                       cplx out[16]) {
+    int nw, nv = 1, np = 1;
+    const cplx *D;
+    if (k == 0) { D = V->K1[ch]; nw = V->n1; }
+    else if (k == 1) { D = V->K2[ch]; nw = V->n2w; nv = V->n2v; }
+    else if (k == 2) { D = V->K2p[ch]; nw = V->n2w; np = V->n2v; }
+    else { D = V->K3[ch]; nw = V->n3w; nv = V->n3v; np = V->n3v; }
+    if (!D) return;
+    int iw[2], iv[2], ip[2], mw, mv, mp;
+    double ww[2], wv[2], wp[2];
+    int nax = (axis == 0) ? nw : (axis == 1) ? nv : np;
+    double g = f * 0.5 * (nax + 1);
+    if (axis == 0) { mw = 1; iw[0] = side > 0 ? nw - 1 : 0; ww[0] = g; }
+    else mw = stencil(w, nw, V->A, iw, ww);
+    if (k == 1 || k == 3) {
+        if (axis == 1) { mv = 1; iv[0] = side > 0 ? nv - 1 : 0; wv[0] = g; }
+        else mv = stencil(v, nv, V->A, iv, wv);
+    } else { mv = 1; iv[0] = 0; wv[0] = 1.0; }
+    if (k == 2 || k == 3) {
+        if (axis == 2) { mp = 1; ip[0] = side > 0 ? np - 1 : 0; wp[0] = g; }
+        else mp = stencil(vp, np, V->A, ip, wp);
+    } else { mp = 1; ip[0] = 0; wp[0] = 1.0; }
+    for (int a = 0; a < mw; ++a)
+        for (int b = 0; b < mv; ++b)
+            for (int e = 0; e < mp; ++e) {
+                size_t row = ((size_t)iw[a] * nv + iv[b]) * np + ip[e];
+                double c = ww[a] * wv[b] * wp[e];
+                for (int q = 0; q < 16; ++q) out[q] += c * D[row * 16 + q];
+            }
+}
+
+/* D_+- of Gamma_s = 2 Gamma_ud(v, v'|v, v') - Gamma_ud(v, v'|v', v) at v' -> side * inf
+ * (the exchanged term with Keldysh indices (a1' a2'|a2 a1); each channel's exchanged term
+ * comes from its crossing partner's data, a <-> t, p -> p, as for the up-up vertex). */
+static void loop_edge(const ovtx *V, double nu, int side, cplx E[16]) {
+    cplx ud[16], ex[16];
+    memset(ud, 0, sizeof(ud));
+    memset(ex, 0, sizeof(ex));
+    /* direct legs (v, v'|v, v'): t (0, v, v'), a (v - v', ., .), p (v + v', ., .) */
+    if ((V->mask >> 2) & 1) {
+        class_edge(V, 2, 2, 2, side, 0.0, nu, 0.0, 1.0, ud);   /* K2'_t(0, v') */
+        class_edge(V, 2, 3, 2, side, 0.0, nu, 0.0, 1.0, ud);   /* K3_t(0, v, v') */
+    }
+    if ((V->mask >> 0) & 1) class_edge(V, 0, 0, 0, -side, 0.0, 0.0, 0.0, 1.0, ud);   /* K1_a(v - v') */
+    if ((V->mask >> 1) & 1) class_edge(V, 1, 0, 0, side, 0.0, 0.0, 0.0, 1.0, ud);    /* K1_p(v + v') */
+    /* exchanged legs (v, v'|v', v): t (v' - v, ., .), a (0, v, v'), p (v + v', ., .) */
+    if ((V->mask >> 0) & 1) class_edge(V, 2, 0, 0, side, 0.0, 0.0, 0.0, 1.0, ex);    /* K1_t(v' - v) */
+    if ((V->mask >> 2) & 1) {
+        class_edge(V, 0, 2, 2, side, 0.0, nu, 0.0, 1.0, ex);   /* K2'_a(0, v') */
+        class_edge(V, 0, 3, 2, side, 0.0, nu, 0.0, 1.0, ex);   /* K3_a(0, v, v') */
+    }
+    if ((V->mask >> 1) & 1) class_edge(V, 1, 0, 0, side, 0.0, 0.0, 0.0, 1.0, ex);    /* K1_p(v + v') */
+    for (int c = 0; c < 16; ++c) {
+        int b1p = (c >> 3) & 1, b2p = (c >> 2) & 1, b1 = (c >> 1) & 1, b2 = c & 1;
+        E[c] = 2.0 * ud[c] - ex[kidx(b1p, b2p, b2, b1)];
+    }
+}
+
+/* Gamma_s . P contracted over the internal line: S[a1'][a1] += f sum G[a1' a2'|a1 a2] P[a2][a2'] */
+static void loop_contract(const cplx G[16], cplx P[2][2], cplx f, cplx S[2][2]) {
+    for (int a1p = 0; a1p < 2; ++a1p)
+        for (int a1 = 0; a1 < 2; ++a1) {
+            cplx s = 0;
+            for (int a2p = 0; a2p < 2; ++a2p)
+                for (int a2 = 0; a2 < 2; ++a2) s += G[kidx(a1p, a2p, a1, a2)] * P[a2][a2p];
+            S[a1p][a1] += f * s;
+        }
+}
+
+/* Gamma_s = Gamma_ud + Gamma_uu of the right-vertex selection sel at t-variables (0, v, v') */
+static void loop_vertex(const ovtx *V, int sel, double nu, double nup, cplx G[16]) {
+    cplx a[16], b[16];
+    vertex_select(V, 2, 0, 1, sel, 0.0, nu, nup, a);
+    vertex_select(V, 2, 1, 1, sel, 0.0, nu, nup, b);
+    for (int c = 0; c < 16; ++c) G[c] = a[c] + b[c];
+}
+
+/* Public: Sigma at npts frequencies nus; out[4 i + 2 a1' + a1] (0 classical, 1 quantum). */
+int og_loop(const ovtx *V, const oprop *P, int Nq, int npts, const double *nus, cplx *out, int nthreads) {
+    if (Nq < 5 || (Nq - 1) % 4) return -1;
+    double *xq = malloc(sizeof(double) * Nq), *wq = malloc(sizeof(double) * Nq);
+    if (!xq || !wq) { free(xq); free(wq); return -2; }
+    og_gl5_rule(Nq, xq, wq);
+    const double A = V->A;
+    cplx M[2][2], Np[2][2], Nm[2][2], IP[2][2];
+    prop_asym(P, 0, M);
+    prop_tail2(P, +1, Np);
+    prop_tail2(P, -1, Nm);
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            IP[a][b] = (wq[0] * Nm[a][b] + wq[Nq - 1] * Np[a][b]) * (PI / (2.0 * A));
+    for (int j = 1; j < Nq - 1; ++j) {
+        double tn = tan(PI * xq[j] / 2), nup = A * tn, jac = A * PI / 2 * (1.0 + tn * tn);
+        cplx G[2][2];
+        prop_matrix(P, 0, nup, G);
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) IP[a][b] += wq[j] * jac * (G[a][b] - M[a][b] * nup / (nup * nup + A * A));
+    }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int i = 0; i < npts; ++i) {
+        const double nu = nus[i];
+        cplx S[2][2] = {{0, 0}, {0, 0}}, Cv[16], E[16];
+        loop_vertex(V, SEL_ZERO, nu, 0.0, Cv);
+        loop_contract(Cv, IP, 1.0, S);
+        for (int j = 1; j < Nq - 1; ++j) {
+            double tn = tan(PI * xq[j] / 2), nup = A * tn, jac = A * PI / 2 * (1.0 + tn * tn);
+            cplx G[2][2], D[16];
+            prop_matrix(P, 0, nup, G);
+            loop_vertex(V, SEL_NU, nu, nup, D);
+            loop_contract(D, G, wq[j] * jac, S);
+        }
+        loop_edge(V, nu, +1, E);
+        loop_contract(E, M, wq[Nq - 1], S);
+        loop_edge(V, nu, -1, E);
+        loop_contract(E, M, -wq[0], S);
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) out[(size_t)4 * i + 2 * a + b] = -S[a][b] / (2.0 * PI * I);
+    }
+    free(xq);
+    free(wq);
+    return 0;
+}
+
+/* Integrand pieces of the loop at one x in (-1, 1), for limit tests:
+ * out[0..3] = J (P - M v'/(v'^2 + A^2))  -> (pi/2A) N_+- at x -> +-1,
+ * out[4..19] = (pi/2A) v' D(v, v')       -> +-D_+-  (D: the v'-dependent part of Gamma_s),
+ * out[20..23] = v' P(v')                 -> M. */
+int og_loop_pieces(const ovtx *V, const oprop *P, double nu, double x, cplx *out) {
+    const double A = V->A;
+    double tn = tan(PI * x / 2), nup = A * tn, jac = A * PI / 2 * (1.0 + tn * tn);
+    cplx G[2][2], M[2][2], D[16];
+    prop_matrix(P, 0, nup, G);
+    prop_asym(P, 0, M);
+    loop_vertex(V, SEL_NU, nu, nup, D);
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            out[2 * a + b] = jac * (G[a][b] - M[a][b] * nup / (nup * nup + A * A));
+            out[20 + 2 * a + b] = nup * G[a][b];
+        }
+    for (int c = 0; c < 16; ++c) out[4 + c] = (PI / (2.0 * A)) * nup * D[c];
+    return 0;
+}
+
+/* The limits the rule uses at x = +-1 (side): out[0..3] = (pi/2A) N_+-, out[4..19] = D_+-. */
+int og_loop_limits(const ovtx *V, const oprop *P, double nu, int side, cplx *out) {
+    cplx N[2][2], E[16];
+    prop_tail2(P, side, N);
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) out[2 * a + b] = N[a][b] * (PI / (2.0 * V->A));
+    memset(E, 0, sizeof(E));
+    loop_edge(V, nu, side, E);
+    for (int c = 0; c < 16; ++c) out[4 + c] = E[c];
+    return 0;
 }

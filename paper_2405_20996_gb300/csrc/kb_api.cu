@@ -237,7 +237,7 @@ kb_status kb_set_vertex(kb_ctx* ctx, int slot, int has_R, double U) {
     std::memset(&ctx->slots[slot], 0, sizeof(kb::VertexDev));
     ctx->slots[slot].has_R = has_R ? 1 : 0;
     ctx->slots[slot].mask = 7;
-    ctx->slots[slot].halfU = 0.5 * U;
+    ctx->slots[slot].bare = -0.5 * U;
     ctx->slot_set[slot] = true;
     ++ctx->slot_gen[slot];
     return KB_OK;

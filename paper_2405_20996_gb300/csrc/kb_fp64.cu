@@ -287,7 +287,7 @@ extern "C" kb_status kb_bubble_fp64_noalloc(const kb_grid_desc* gd, double Delta
     for (int i = 0; i < 2; ++i) {
         V[i].has_R = D[i]->has_R ? 1 : 0;
         V[i].mask = (int)D[i]->channels;
-        V[i].halfU = 0.5 * D[i]->U;
+        V[i].bare = -0.5 * D[i]->U;
         for (int c = 0; c < 3; ++c)
             for (int k = 0; k < 4; ++k) {
                 V[i].cls[c][k] = D[i]->cls[c][k];

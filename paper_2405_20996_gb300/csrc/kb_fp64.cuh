@@ -76,7 +76,7 @@ __device__ void vertex_part_f64(const VertexDev& V, const Grids& G, int r, bool 
     for (int o = 0; o < 16; ++o) out[o] = make_double2(0, 0);
     if (!nupart && !uu && V.has_R) {
 #pragma unroll
-        for (int o = 0; o < 16; ++o) out[o].x = (__popc(o) & 1) ? V.halfU : 0.0;
+        for (int o = 0; o < 16; ++o) out[o].x = (__popc(o) & 1) ? V.bare : 0.0;
     }
     int k_free = right ? 1 : 2, k_dep = right ? 2 : 1;
     int ka = nupart ? k_dep : 0, kb2 = nupart ? 3 : k_free;

@@ -23,7 +23,8 @@ struct VertexDev {
     int has_R;
     int mask;                // channels included (bit c); excluded channels serve only as
                              // crossing partners of the up-up component
-    double halfU;            // U / 2
+    double bare;             // bare vertex on the components with an odd number of
+                             // quantum indices: -U/2
     int symmetric;           // declared conjugation + crossing symmetric
 };
 

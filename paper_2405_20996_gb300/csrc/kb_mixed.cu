@@ -892,7 +892,7 @@ static VertexF to_vf(const VertexDev& V, kb_ctx* ctx, bool& ok) {
         }
     F.has_R = V.has_R;
     F.mask = V.mask;
-    F.halfU = (float)V.halfU;
+    F.bare = (float)V.bare;
     if (!ok) ctx->err = "mixed precision needs complex64 classes aligned to 16 bytes";
     return F;
 }

@@ -135,7 +135,7 @@ __host__ __device__ constexpr int cmap(int X, int Y) {
 struct VertexF {
     const float2* cls[3][4];
     int has_R, mask;
-    float halfU;
+    float bare;
 };
 
 // Corners of one class: nd dimensions with lower nodes kk[d], fractions tt[d] and sizes N[d]
@@ -266,7 +266,7 @@ __device__ __forceinline__ void vertex_part_f32(const VertexF& V, const DfGrids&
     }
     // the bare part is even under a1 <-> a2, so its up-up value R(12) - R(21) is zero
     if ((what & 1) && V.has_R && dir != exch) {
-        const float u = dir ? V.halfU : -V.halfU;
+        const float u = dir ? V.bare : -V.bare;
 #pragma unroll
         for (int o = 0; o < 16; ++o) out[o].x += (__popc(o) & 1) ? u : 0.f;
     }

@@ -80,7 +80,7 @@ class MultiloopStep:
     def __init__(self, grids, nq, U, Delta, T, vertex, n_loops=6, precision="mixed", A=5.0, device=0,
                  symmetric=True, channels=(0, 1, 2), cache="auto", reserve_bytes=40 << 30):
         """vertex: {channel: (K1, K2, K2p, K3)} arrays of the reducible vertices γ_r (the bare
-        part U/2 is added by the library).  precision "mixed" keeps every vertex in complex64,
+        part −U/2 is added by the library).  precision "mixed" keeps every vertex in complex64,
         "fp64" in complex128.  cache (mixed only): rebuild the record cache of Γ once per
         step — "auto": its K3 tiles and its K2 records as left vertex (the right parts' K2 and
         the left parts' K2' are zero classes, not computed), as far as they fit in the free

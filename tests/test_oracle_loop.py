@@ -1,0 +1,138 @@
+"""Pins of the oracle's self-energy loop (Sec. II.D.2), independent of its code:
+
+- the limits the rule uses at x = +-1 equal the integrand's values as x -> +-1, evaluated
+  through the general vertex and propagator routines (numerical limit, O(1 - |x|));
+- bare vertex: the loop is the Hartree shift U (n - 1/2) (Sec. III.A.1) with n from the
+  Lorentzian spectral function by QUADPACK (T > 0) or in closed form (T = 0); its (c|c) and
+  Keldysh components vanish;
+- the principal value at v' = +-inf: a constant K1_t on the Keldysh component that picks
+  G^R alone gives int dv' G^R/(2 pi i) = -1/2 (equal-time average);
+- second order: with the interaction flow's homogeneity (G_L = L G, S = G, Sigma2 of degree 3
+  in G), the loop of the second-order vertex is 3 Sigma2; Im Sigma2^R against the textbook
+  double spectral integral of the symmetric Anderson model, converging at second order in
+  the grid spacing; causality, FDR and particle-hole symmetry of the result;
+- linearity in the vertex."""
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+import seeded
+from oracle import oracle as O
+
+G = dict(n1=21, n2w=9, n2v=11, n3w=7, n3v=9)
+K = lambda a1p, a2p, a1, a2: 8 * a1p + 4 * a2p + 2 * a1 + a2
+
+
+def _seeded(U=1.0, seed=3, include=(0, 1, 2)):
+    return O.Vertex(G, U=U, has_R=True, channels=seeded.seeded_vertex(G, U=U, seed=seed), include=include)
+
+
+@pytest.mark.parametrize("nu", [0.0, 0.7, -2.3])
+def test_loop_endpoint_limits(nu):
+    V = _seeded()
+    sR = seeded.seeded_sigma(17, seed=5)
+    sK = 2j * np.tanh(seeded.grid_freqs(17) / 0.2) * sR.imag          # equilibrium Keldysh part
+    P = O.Prop(Delta=1.0, T=0.1, eps=0.3, sigR=sR, sigK=sK)
+    for side in (1, -1):
+        N, E = O.loop_limits(V, P, nu, side)
+        errs = []
+        for d in (1e-4, 1e-5):
+            a, b, c = O.loop_pieces(V, P, nu, side * (1 - d))
+            errs.append((np.abs(a - N).max(), np.abs(b - side * E).max() / np.abs(E).max(),
+                         np.abs(c - np.array([[0, 1], [1, 0]])).max()))
+        for k in range(3):
+            assert errs[1][k] <= 0.2 * errs[0][k] + 1e-12, (side, k, errs)    # O(1 - |x|)
+        assert errs[1][0] <= 1e-4 and errs[1][1] <= 1e-5 and errs[1][2] <= 1e-4, errs
+
+
+@pytest.mark.parametrize("T", [0.1, 0.0])
+def test_loop_of_bare_vertex_is_the_hartree_shift(T):
+    U, D = 1.3, 1.0
+    V = O.Vertex(G, U=U, has_R=True)
+    for eps in (0.0, 0.3, -0.8):
+        P = O.Prop(Delta=D, T=T, eps=eps)
+        S = O.loop(V, P, 1001, np.array([0.0, 1.5, -4.0]))
+        if T > 0:
+            A = lambda v: (D / np.pi) / ((v - eps) ** 2 + D ** 2)
+            n = integrate.quad(lambda v: 0.5 * (1 - np.tanh(v / (2 * T))) * A(v), -np.inf, np.inf,
+                               epsabs=1e-14, epsrel=1e-14, limit=400)[0]
+        else:
+            n = 0.5 - np.arctan(eps / D) / np.pi
+        ref = U * (n - 0.5)
+        assert np.abs(S[:, 1, 0] - ref).max() <= 1e-9 * U, (eps, S[:, 1, 0], ref)   # Sigma^R
+        assert np.abs(S[:, 0, 1] - ref).max() <= 1e-9 * U                           # Sigma^A
+        assert np.abs(S[:, 0, 0]).max() <= 1e-12 and np.abs(S[:, 1, 1]).max() <= 1e-12
+
+
+def test_loop_principal_value_at_infinity():
+    """Only K1_t, constant in w, on component (c q|c c): Gamma_s = 2 K1_t (the up-up vertex's
+    own-channel part, no crossing partner), and Sigma^{c|c} = -2c int dv' G^R/(2 pi i) = c."""
+    c = 0.37 - 0.21j
+    K1 = np.zeros((G["n1"], 16), dtype=np.complex128)
+    K1[:, K(0, 1, 0, 0)] = c
+    V = O.Vertex(G, channels={2: (K1, None, None, None)}, include=(2,))
+    for eps in (0.0, 0.4):
+        S = O.loop(V, O.Prop(Delta=0.8, T=0.05, eps=eps), 4001, np.array([0.0, 2.0]))
+        assert np.abs(S[:, 0, 0] - c).max() <= 1e-9
+        assert np.abs(S[:, 1, 0]).max() + np.abs(S[:, 0, 1]).max() + np.abs(S[:, 1, 1]).max() <= 1e-12
+
+
+def _sigma2_spectral(nus, U, T, D, n=800):
+    """Im Sigma2^R(w) = -pi U^2 int de1 de2 A1 A2 A3 [n3 (1-n1)(1-n2) + (1-n3) n1 n2],
+    e3 = e1 + e2 - w, A Lorentzian (e = D tan(theta) makes A de = dtheta / pi)."""
+    x, wx = np.polynomial.legendre.leggauss(n)
+    th, wth = x * np.pi / 2, wx * np.pi / 2
+    e = D * np.tan(th)
+    nf = lambda v: 0.5 * (1 - np.tanh(v / (2 * T)))
+    A = lambda v: (D / np.pi) / (v ** 2 + D ** 2)
+    E1, E2 = np.meshgrid(e, e, indexing="ij")
+    W = np.outer(wth, wth) / np.pi ** 2
+    out = []
+    for w in nus:
+        E3 = E1 + E2 - w
+        n1, n2, n3 = nf(E1), nf(E2), nf(E3)
+        out.append(-np.pi * U ** 2 * np.sum(W * A(E3) * (n3 * (1 - n1) * (1 - n2) + (1 - n3) * n1 * n2)))
+    return np.array(out)
+
+
+def _loop_of_second_order_vertex(n1, nq, U, T, D, nus):
+    g = dict(n1=n1, n2w=3, n2v=3, n3w=3, n3v=3)
+    P = O.Prop(Delta=D, T=T)
+    V0 = O.Vertex(g, U=U, has_R=True)
+    ch = {r: (O.bubble_all(V0, V0, P, r, nq, classes=("K1",))["K1"], None, None, None) for r in range(3)}
+    return O.loop(O.Vertex(g, channels=ch), P, nq, nus)
+
+
+def test_loop_of_second_order_vertex_is_three_sigma2():
+    U, T, D = 1.0, 0.1, 1.0
+    nus = np.array([0.0, 0.5, 1.0, -0.5, -1.0])
+    ref = _sigma2_spectral(nus[:3], U, T, D)
+    errs = []
+    for n1, nq in ((201, 801), (401, 1601)):
+        S = _loop_of_second_order_vertex(n1, nq, U, T, D, nus) / 3
+        SR = S[:, 1, 0]
+        errs.append(np.abs(SR[:3].imag - ref).max())
+    assert errs[1] <= 5e-4 * np.abs(ref).max() and errs[1] <= 0.35 * errs[0], errs   # O(h^2)
+    # causality, FDR, conjugation and particle-hole symmetry of the finer result
+    assert (SR.imag < 0).all()
+    assert np.abs(S[:, 0, 1] - np.conj(SR)).max() <= 1e-14
+    fdr = 2j * np.tanh(nus / (2 * T)) * SR.imag
+    assert np.abs(S[:, 1, 1] - fdr).max() <= 1e-3 * np.abs(SR).max()
+    assert np.abs(S[:, 0, 0]).max() <= 1e-3 * np.abs(SR).max()
+    assert np.abs(SR[3:] + np.conj(SR[1:3])).max() <= 1e-12 * np.abs(SR).max()   # Re odd, Im even
+    assert (SR[1:3].real < 0).all()                                               # Re Sigma2' < 0
+
+
+def test_loop_is_linear_in_the_vertex():
+    a, b = 0.7 - 0.2j, -1.3
+    ch1 = seeded.seeded_vertex(G, U=1.0, seed=3)
+    ch2 = seeded.seeded_vertex(G, U=0.4, seed=9)
+    chs = {c: tuple(a * x + b * y for x, y in zip(ch1[c], ch2[c])) for c in range(3)}
+    Vs = O.Vertex(G, channels=chs)
+    P = O.Prop(Delta=1.0, T=0.1, eps=0.2)
+    nus = np.array([0.0, 0.9, -3.1])
+    V1c, V2c = O.Vertex(G, channels=ch1), O.Vertex(G, channels=ch2)
+    S = O.loop(Vs, P, 401, nus)
+    ref = a * O.loop(V1c, P, 401, nus) + b * O.loop(V2c, P, 401, nus)
+    assert np.abs(S - ref).max() <= 1e-13 * np.abs(ref).max()

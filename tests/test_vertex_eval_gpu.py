@@ -48,7 +48,7 @@ def test_vertex_eval_matches_oracle(dtype, include):
 
 
 def test_t_channel_slice_at_zero_transfer():
-    """The slice (w_t = 0, v, v') of a vertex with only the bare part is U/2 on the
+    """The slice (w_t = 0, v, v') of a vertex with only the bare part is -U/2 on the
     components with an odd number of quantum indices, everywhere; with classes it matches
     the oracle on a grid of (v, v')."""
     from paper_2405_20996_gb300.engine import Engine
@@ -61,7 +61,7 @@ def test_t_channel_slice_at_zero_transfer():
     f = np.array([(0.0, a, b) for a in v for b in v])
     got = e.vertex_eval(0, 2, f).cpu().numpy()
     odd = np.array([bin(c).count("1") % 2 for c in range(16)], dtype=float)
-    assert np.allclose(got, 0.5 * cfg["U"] * odd[None, :], rtol=0, atol=1e-15)
+    assert np.allclose(got, -0.5 * cfg["U"] * odd[None, :], rtol=0, atol=1e-15)
     ch = S.seeded_vertex(g, cfg["U"], seed=72)
     e.set_vertex(1, U=cfg["U"], has_R=True, channels=ch)
     got = e.vertex_eval(1, 2, f).cpu().numpy()
