@@ -548,6 +548,49 @@ def run_vjp(args):
     return 0
 
 
+def run_loop(args):
+    """Self-energy loop (kb_loop, plain FP64) of the full vertex at the step's sizes (K1 401,
+    K2 101^2, K3 51^3 in all three channels with the bare part, Nq 4001, U/Delta = 2,
+    T = 0.05) at 401 frequencies (the K1 grid).  Unit: integrand evaluations (frequency x
+    interior node) per second.  Algorithmic work per evaluation: the interpolated reads of
+    both spin components of the v'-dependent vertex part (144 class corners of 16 complex
+    values, 64 flops each) and the two Keldysh contractions (288 flops); corners that fall
+    outside a grid are counted too, so `achieved` is an upper bound."""
+    import torch
+    import seeded as S
+    from paper_2405_20996_gb300 import kb
+    from paper_2405_20996_gb300.engine import Engine
+    g = dict(n1=401, n2w=101, n2v=101, n3w=51, n3v=51)
+    dev = torch.device("cuda", 0)
+    e = Engine(g, NQ, device=0)
+    e.set_model(DELTA, T)
+    e.set_vertex(0, U=U, has_R=True, channels=S.seeded_vertex(g, U, seed=91))
+    nus = torch.from_numpy(S.grid_freqs(g["n1"])).to(dev)
+    out = torch.empty((nus.numel(), 2, 2), dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        kb.kb_loop(e.ctx, 0, nus.numel(), nus.data_ptr(), out.data_ptr(), stream.cuda_stream)
+
+    ms = _timed(step, args.steps, max(args.warmup, 3), stream)
+    kb.kb_check_device(e.ctx)
+    evals = nus.numel() * (NQ - 2)
+    flops = evals * (144 * 64 + 288)
+    ach = flops / (ms / 1e3) / 1e12
+    line = {"metric": "self-energy loop integrand evaluations/s", "value": evals / (ms / 1e3),
+            "unit": "evaluations/s", "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "loop of the full vertex, K1 401, K2 101x101, K3 51^3, Nq 4001, 401 frequencies",
+                       "evaluations_per_step": evals, "l2": "vertex 17 MB per K3 channel, L2-resident"},
+            "roofline": {"kernel": "k_loop", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                         "note": "upper-bound flop count; FP64 peak derived from SM count and clock"}}
+    print(json.dumps(line))
+    e.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -567,7 +610,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the wave-model split-K factors instead of timing candidates before the step graph")
     ap.add_argument("--workload", default="step",
-                    choices=["step", "points32", "vjp", "multiloop", "multiloop-large", "parquet"],
+                    choices=["step", "points32", "vjp", "multiloop", "multiloop-large", "parquet", "loop"],
                     help="step: the default three-channel line; points32 / vjp / multiloop: the batching, "
                          "adjoint and multiloop paths")
     args = ap.parse_args()
@@ -576,6 +619,8 @@ def main():
             return run_multiloop(args)
         if args.workload == "parquet":
             return run_parquet(args)
+        if args.workload == "loop":
+            return run_loop(args)
         return run_points32(args) if args.workload == "points32" else run_vjp(args)
     chans = tuple(sorted({"apt".index(c) for c in args.channels}))
     if not chans:
