@@ -570,7 +570,7 @@ def run_loop(args):
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        kb.kb_loop(e.ctx, 0, nus.numel(), nus.data_ptr(), out.data_ptr(), stream.cuda_stream)
+        kb.kb_loop(e.ctx, 0, 0, nus.numel(), nus.data_ptr(), out.data_ptr(), stream.cuda_stream)
 
     ms = _timed(step, args.steps, max(args.warmup, 3), stream)
     kb.kb_check_device(e.ctx)

@@ -282,9 +282,11 @@ kb_status kb_vertex_eval(kb_ctx *ctx, int slot, int channel, int spin_uu, int n,
                          void *stream);
 
 /* Self-energy loop (the paper's `loop` function, Sec. II.D.2): the vertex of slot `slot`
- * closed by one propagator line G of the context's model,
+ * closed by one propagator line P of the context's model — which = 0: P = G; which = 1:
+ * P = S, the single-scale propagator of the flow scheme (kb_set_regulator, with the
+ * Katanin substitution when set), the one-loop term of the self-energy flow —
  *   Sigma^{a1'|a1}(v) = - int dv'/(2 pi i) sum_{a2', a2} Gamma_s^{a1' a2'|a1 a2}(v, v'|v, v')
- *                          G^{a2|a2'}(v'),   Gamma_s = Gamma_up-down + Gamma_up-up,
+ *                          P^{a2|a2'}(v'),   Gamma_s = Gamma_up-down + Gamma_up-up,
  * with the vertex read in t-channel variables (w_t = 0, v, v') and the internal line's
  * spin summed (SU(2)).  The minus sign is that of the Schwinger-Dyson equation's bare term
  * (Sec. III.B): with the bare vertex -U/2 the loop of R alone is the Hartree shift
@@ -294,7 +296,7 @@ kb_status kb_vertex_eval(kb_ctx *ctx, int slot, int channel, int spin_uu, int n,
  * [n][2][2] indexed [a1'][a1] (0 classical, 1 quantum): (1,0) = Sigma^R, (0,1) = Sigma^A,
  * (1,1) = Sigma^K, (0,0) = 0 for a causal result.  Plain FP64.  Requires the grids, the
  * model and the slot.  Asynchronous on `stream`. */
-kb_status kb_loop(kb_ctx *ctx, int slot, int n, const double *nus, void *out, void *stream);
+kb_status kb_loop(kb_ctx *ctx, int slot, int which, int n, const double *nus, void *out, void *stream);
 
 /* Autotuning of the tensor-core K3 contraction (default off): with `on`, the first
  * mixed-precision bubble of each contraction shape (rows, columns, K, batch of bosonic

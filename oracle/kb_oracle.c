@@ -910,18 +910,36 @@ int og_bubble_vjp_points(const ovtx *V1, const ovtx *V2, const oprop *P, int pi_
  *   y ~ +-v' of (their value at the last grid node along that argument) (N + 1)/2,
  * since a class interpolated to zero at x = +-1 falls like (1 -+ x_y) (N + 1)/2 and
  * (1 -+ x_y) v' -> 2A/pi, while J P -> (pi/2A) M v'.  Classes with two diverging
- * arguments fall like 1/v'^2 and drop out.  Only P = G is supported here.
+ * arguments fall like 1/v'^2 and drop out.  P = G, or P = S of the flow scheme (with the
+ * Katanin substitution when its tables are set) for the self-energy flow's loop(Gamma, S).
  * ------------------------------------------------------------------------------------ */
 
-/* N_+- of G (side = +1 or -1): with Sigma tables vanishing at x = +-1,
- * v' G^R = lam v' / (v' - eps + i Delta - lam Sigma^R) gives N^R = lam (eps - i Delta),
- * N^A = (N^R)*, and v'^2 G^K -> lam^2 (-2 i Delta tanh(+-inf) / lam). */
-static void prop_tail2(const oprop *P, int side, cplx N[2][2]) {
+/* N_+- = lim_{v' -> +-inf} v' (v' P - M) (side = +1 or -1), with Sigma (and dSigma) tables
+ * vanishing at x = +-1 and th = tanh(+-inf) = +-1:
+ *   G: v' G^R = lam v' / (v' - eps + i Delta - lam Sigma^R) gives N^R = lam (eps - i Delta),
+ *      and v'^2 G^K -> lam^2 (-2 i Delta th / lam);
+ *   S, hybridisation flow: S^R = -i (G^R)^2 gives N^R = -i; S^K -> G^R (-2 i th) G^A;
+ *   S, interaction flow: S = G / lam at Sigma = 0 to this order: N^R = eps - i Delta,
+ *      N^K = -2 i Delta th;
+ *   S, temperature flow: S^R = 0 and S^K falls exponentially: N = 0.
+ * The Katanin term G dSigma G falls like 1/v'^3 and adds nothing.  N^A = (N^R)*. */
+static void prop_tail2(const oprop *P, int which, int side, cplx N[2][2]) {
     const double lam = (P->reg == 1) ? P->lam : 1.0;
-    const double th = (double)side;              /* tanh(v'/2T) at v' = +-inf, any T >= 0 */
-    N[0][1] = lam * (P->eps - I * P->Delta);
+    const double th = (double)side;
+    if (which == 0) {
+        N[0][1] = lam * (P->eps - I * P->Delta);
+        N[0][0] = -2.0 * I * P->Delta * th * lam;
+    } else if (P->reg == 1) {
+        N[0][1] = P->eps - I * P->Delta;
+        N[0][0] = -2.0 * I * P->Delta * th;
+    } else if (P->reg == 2) {
+        N[0][1] = 0;
+        N[0][0] = 0;
+    } else {
+        N[0][1] = -I;
+        N[0][0] = -2.0 * I * th;
+    }
     N[1][0] = conj(N[0][1]);
-    N[0][0] = -2.0 * I * P->Delta * th * lam;
     N[1][1] = 0;
 }
 
@@ -1006,24 +1024,26 @@ static void loop_vertex(const ovtx *V, int sel, double nu, double nup, cplx G[16
     for (int c = 0; c < 16; ++c) G[c] = a[c] + b[c];
 }
 
-/* Public: Sigma at npts frequencies nus; out[4 i + 2 a1' + a1] (0 classical, 1 quantum). */
-int og_loop(const ovtx *V, const oprop *P, int Nq, int npts, const double *nus, cplx *out, int nthreads) {
-    if (Nq < 5 || (Nq - 1) % 4) return -1;
+/* Public: Sigma at npts frequencies nus with P = G (which 0) or S (which 1);
+ * out[4 i + 2 a1' + a1] (0 classical, 1 quantum). */
+int og_loop(const ovtx *V, const oprop *P, int which, int Nq, int npts, const double *nus, cplx *out,
+            int nthreads) {
+    if (Nq < 5 || (Nq - 1) % 4 || which < 0 || which > 1) return -1;
     double *xq = malloc(sizeof(double) * Nq), *wq = malloc(sizeof(double) * Nq);
     if (!xq || !wq) { free(xq); free(wq); return -2; }
     og_gl5_rule(Nq, xq, wq);
     const double A = V->A;
     cplx M[2][2], Np[2][2], Nm[2][2], IP[2][2];
-    prop_asym(P, 0, M);
-    prop_tail2(P, +1, Np);
-    prop_tail2(P, -1, Nm);
+    prop_asym(P, which, M);
+    prop_tail2(P, which, +1, Np);
+    prop_tail2(P, which, -1, Nm);
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
             IP[a][b] = (wq[0] * Nm[a][b] + wq[Nq - 1] * Np[a][b]) * (PI / (2.0 * A));
     for (int j = 1; j < Nq - 1; ++j) {
         double tn = tan(PI * xq[j] / 2), nup = A * tn, jac = A * PI / 2 * (1.0 + tn * tn);
         cplx G[2][2];
-        prop_matrix(P, 0, nup, G);
+        prop_matrix(P, which, nup, G);
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b) IP[a][b] += wq[j] * jac * (G[a][b] - M[a][b] * nup / (nup * nup + A * A));
     }
@@ -1039,7 +1059,7 @@ int og_loop(const ovtx *V, const oprop *P, int Nq, int npts, const double *nus, 
         for (int j = 1; j < Nq - 1; ++j) {
             double tn = tan(PI * xq[j] / 2), nup = A * tn, jac = A * PI / 2 * (1.0 + tn * tn);
             cplx G[2][2], D[16];
-            prop_matrix(P, 0, nup, G);
+            prop_matrix(P, which, nup, G);
             loop_vertex(V, SEL_NU, nu, nup, D);
             loop_contract(D, G, wq[j] * jac, S);
         }
@@ -1058,13 +1078,13 @@ int og_loop(const ovtx *V, const oprop *P, int Nq, int npts, const double *nus, 
 /* Integrand pieces of the loop at one x in (-1, 1), for limit tests:
  * out[0..3] = J (P - M v'/(v'^2 + A^2))  -> (pi/2A) N_+- at x -> +-1,
  * out[4..19] = (pi/2A) v' D(v, v')       -> +-D_+-  (D: the v'-dependent part of Gamma_s),
- * out[20..23] = v' P(v')                 -> M. */
-int og_loop_pieces(const ovtx *V, const oprop *P, double nu, double x, cplx *out) {
+ * out[20..23] = v' P(v')                 -> M  (P = G for which 0, S for which 1). */
+int og_loop_pieces(const ovtx *V, const oprop *P, int which, double nu, double x, cplx *out) {
     const double A = V->A;
     double tn = tan(PI * x / 2), nup = A * tn, jac = A * PI / 2 * (1.0 + tn * tn);
     cplx G[2][2], M[2][2], D[16];
-    prop_matrix(P, 0, nup, G);
-    prop_asym(P, 0, M);
+    prop_matrix(P, which, nup, G);
+    prop_asym(P, which, M);
     loop_vertex(V, SEL_NU, nu, nup, D);
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) {
@@ -1076,9 +1096,9 @@ int og_loop_pieces(const ovtx *V, const oprop *P, double nu, double x, cplx *out
 }
 
 /* The limits the rule uses at x = +-1 (side): out[0..3] = (pi/2A) N_+-, out[4..19] = D_+-. */
-int og_loop_limits(const ovtx *V, const oprop *P, double nu, int side, cplx *out) {
+int og_loop_limits(const ovtx *V, const oprop *P, int which, double nu, int side, cplx *out) {
     cplx N[2][2], E[16];
-    prop_tail2(P, side, N);
+    prop_tail2(P, which, side, N);
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) out[2 * a + b] = N[a][b] * (PI / (2.0 * V->A));
     memset(E, 0, sizeof(E));

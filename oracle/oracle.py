@@ -283,30 +283,33 @@ def prop_eval(P, which, v):
     return out
 
 
-def loop(V, P, Nq, nus, nthreads=0):
+def loop(V, P, Nq, nus, nthreads=0, which=0):
     """Self-energy loop Sigma^{a1'|a1}(v) = -int dv'/(2 pi i) sum Gamma_s^{a1' a2'|a1 a2}(v, v'|v, v')
-    G^{a2|a2'}(v') with Gamma_s = Gamma_ud + Gamma_uu (Sec. II.D.2; readings in kb_oracle.c).
+    P^{a2|a2'}(v') with Gamma_s = Gamma_ud + Gamma_uu (Sec. II.D.2; readings in kb_oracle.c),
+    P = G (which 0) or the flow scheme's single-scale propagator S (which 1).
     Returns (n, 2, 2) complex: [a1'][a1], 0 = classical, 1 = quantum."""
     nus = np.ascontiguousarray(nus, dtype=np.float64)
     out = np.zeros((len(nus), 2, 2), dtype=np.complex128)
-    rc = lib().og_loop(V.ptr(), P.ptr(), C.c_int(Nq), C.c_int(len(nus)), _dptr(nus),
+    rc = lib().og_loop(V.ptr(), P.ptr(), C.c_int(which), C.c_int(Nq), C.c_int(len(nus)), _dptr(nus),
                        out.ctypes.data_as(C.c_void_p), C.c_int(nthreads))
     if rc != 0:
         raise RuntimeError("og_loop failed: %d" % rc)
     return out
 
 
-def loop_pieces(V, P, nu, x):
-    """(J (G - M v'/(v'^2+A^2)) [2x2], (pi/2A) v' D(v, v') [16], v' G [2x2]) at one x in (-1, 1)."""
+def loop_pieces(V, P, nu, x, which=0):
+    """(J (P - M v'/(v'^2+A^2)) [2x2], (pi/2A) v' D(v, v') [16], v' P [2x2]) at one x in (-1, 1)."""
     out = np.zeros(24, dtype=np.complex128)
-    lib().og_loop_pieces(V.ptr(), P.ptr(), C.c_double(nu), C.c_double(x), out.ctypes.data_as(C.c_void_p))
+    lib().og_loop_pieces(V.ptr(), P.ptr(), C.c_int(which), C.c_double(nu), C.c_double(x),
+                         out.ctypes.data_as(C.c_void_p))
     return out[:4].reshape(2, 2), out[4:20], out[20:].reshape(2, 2)
 
 
-def loop_limits(V, P, nu, side):
+def loop_limits(V, P, nu, side, which=0):
     """The loop rule's values at x = side (+-1): ((pi/2A) N [2x2], D_edge [16])."""
     out = np.zeros(20, dtype=np.complex128)
-    lib().og_loop_limits(V.ptr(), P.ptr(), C.c_double(nu), C.c_int(side), out.ctypes.data_as(C.c_void_p))
+    lib().og_loop_limits(V.ptr(), P.ptr(), C.c_int(which), C.c_double(nu), C.c_int(side),
+                         out.ctypes.data_as(C.c_void_p))
     return out[:4].reshape(2, 2), out[4:]
 
 

@@ -5,8 +5,9 @@
 // such slices of the full vertex, e.g. the t-channel plane (w_t = 0, v_t, v'_t).
 //
 // The self-energy loop (Sec. II.D.2) closes the vertex with one propagator line:
-//   Sigma^{a1'|a1}(v) = - int dv'/(2 pi i) sum Gamma_s^{a1' a2'|a1 a2}(v, v'|v, v') G^{a2|a2'}(v'),
-//   Gamma_s = Gamma_ud + Gamma_uu, the vertex in t-channel variables (0, v, v'),
+//   Sigma^{a1'|a1}(v) = - int dv'/(2 pi i) sum Gamma_s^{a1' a2'|a1 a2}(v, v'|v, v') P^{a2|a2'}(v'),
+//   Gamma_s = Gamma_ud + Gamma_uu, the vertex in t-channel variables (0, v, v'), P = G or the
+//   single-scale propagator S of the flow scheme (the self-energy flow's loop(Gamma, S)),
 // the sign of the Schwinger-Dyson equation's bare term (Sec. III.B), the v' integral the
 // symmetric principal value at +-inf.  On the composite GL5 rule in x = (2/pi) atan(v'/A):
 // the v'-independent part C(v) (R + K1_t + K2_t of both spin components) multiplies
@@ -122,8 +123,28 @@ __device__ __forceinline__ void loop_contract(const double2 Gam[16], const doubl
 
 constexpr int LOOP_THREADS = 256;
 
+// Asymptotics of the line P (which 0: G, 1: S of the flow scheme) with Sigma tables vanishing
+// at x = +-1: M = lim v' P = mm [[0, 1], [1, 0]] and N_+- = lim v'(v' P - M) with
+// N^R = nR, N^A = nR*, N^K_+- = -+ i nK (N^{qq} = 0):
+//   G: mm = lam, nR = lam (eps - i Delta), nK = 2 lam Delta;
+//   S, hybridisation flow (S^R = -i G^R G^R): mm = 0, nR = -i, nK = 2;
+//   S, interaction flow (S = G / lam at this order): mm = 1, nR = eps - i Delta, nK = 2 Delta;
+//   S, temperature flow: all zero (S^R = 0, S^K falls exponentially).
+// The Katanin term G dSigma G falls like 1/v'^3 and adds nothing.
+struct LineTail {
+    double mm, nK;
+    double2 nR;
+};
+__device__ __forceinline__ LineTail line_tail(const Model& m, int which) {
+    const double lam = (m.reg == KB_REG_U) ? m.lam : 1.0;
+    if (which == 0) return {lam, 2.0 * lam * m.Delta, make_double2(lam * m.eps, -lam * m.Delta)};
+    if (m.reg == KB_REG_U) return {1.0, 2.0 * m.Delta, make_double2(m.eps, -m.Delta)};
+    if (m.reg == KB_REG_T) return {0.0, 0.0, make_double2(0.0, 0.0)};
+    return {0.0, 2.0, make_double2(0.0, -1.0)};
+}
+
 // One block per output frequency; threads stride over the interior nodes 1 .. nq-2.
-__global__ void __launch_bounds__(LOOP_THREADS) k_loop(VertexDev V, Grids G, Model m, int n,
+__global__ void __launch_bounds__(LOOP_THREADS) k_loop(VertexDev V, Grids G, Model m, int which, int n,
                                                        const double* __restrict__ nus,
                                                        const double* __restrict__ xq,
                                                        const double* __restrict__ wq, double2* __restrict__ out) {
@@ -131,7 +152,7 @@ __global__ void __launch_bounds__(LOOP_THREADS) k_loop(VertexDev V, Grids G, Mod
     if (i >= n) return;
     const double nu = nus[i], A = G.A;
     const int nq = G.nq;
-    const double lam = (m.reg == KB_REG_U) ? m.lam : 1.0;
+    const LineTail tl = line_tail(m, which);
     double2 acc[8];                       // [0..3] int D G over [a1'][a1], [4..7] I_G over [a2][a2']
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = make_double2(0.0, 0.0);
@@ -139,9 +160,9 @@ __global__ void __launch_bounds__(LOOP_THREADS) k_loop(VertexDev V, Grids G, Mod
         const double tn = tan(0.5 * KB_PI * xq[j]);
         const double nup = A * tn, f = wq[j] * (0.5 * A * KB_PI * (1.0 + tn * tn));
         double2 P[2][2];
-        prop2x2(m, 0, nup, P);
+        prop2x2(m, which, nup, P);
         P[1][1] = make_double2(0.0, 0.0);
-        const double sub = lam * nup / (nup * nup + A * A);
+        const double sub = tl.mm * nup / (nup * nup + A * A);
         acc[4].x = fma(f, P[0][0].x, acc[4].x);         acc[4].y = fma(f, P[0][0].y, acc[4].y);
         acc[5].x = fma(f, P[0][1].x - sub, acc[5].x);   acc[5].y = fma(f, P[0][1].y, acc[5].y);
         acc[6].x = fma(f, P[1][0].x - sub, acc[6].x);   acc[6].y = fma(f, P[1][0].y, acc[6].y);
@@ -172,18 +193,19 @@ __global__ void __launch_bounds__(LOOP_THREADS) k_loop(VertexDev V, Grids G, Mod
         for (int k = 0; k < LOOP_THREADS / 32; ++k) { S[q] = cadd(S[q], red[k][q]); t = cadd(t, red[k][4 + q]); }
         IG[q >> 1][q & 1] = t;
     }
-    // the rule's end nodes of I_G: (pi/2A) N_-+ with N^K = -+2i lam Delta, N^R = lam (eps - i Delta)
+    // the rule's end nodes of I_P: (pi/2A) N_-+ (x = -1 with weight wq[0], x = +1 with wq[nq-1])
     const double c0 = wq[0] * KB_PI / (2.0 * A), c1 = wq[nq - 1] * KB_PI / (2.0 * A);
-    IG[0][0].y += (c0 - c1) * 2.0 * lam * m.Delta;
-    IG[0][1] = cadd(IG[0][1], cscale(make_double2(lam * m.eps, -lam * m.Delta), c0 + c1));
-    IG[1][0] = cadd(IG[1][0], cscale(make_double2(lam * m.eps, lam * m.Delta), c0 + c1));
+    IG[0][0].y += (c0 - c1) * tl.nK;
+    IG[0][1] = cadd(IG[0][1], cscale(tl.nR, c0 + c1));
+    IG[1][0] = cadd(IG[1][0], cscale(cconj(tl.nR), c0 + c1));
     double2 Cv[16];
     vertex_part_f64(V, G, KB_CH_T, false, true, false, 0.0, nu, 0.0, Cv);
     loop_contract(Cv, IG, 1.0, S);
     vertex_part_f64(V, G, KB_CH_T, true, true, false, 0.0, nu, 0.0, Cv);
     loop_contract(Cv, IG, 1.0, S);
-    // end nodes of int D G: +-M D_+-, M = lam [[0, 1], [1, 0]]
-    double2 Mm[2][2] = {{make_double2(0.0, 0.0), make_double2(lam, 0.0)}, {make_double2(lam, 0.0), make_double2(0.0, 0.0)}};
+    // end nodes of int D P: +-M D_+-
+    double2 Mm[2][2] = {{make_double2(0.0, 0.0), make_double2(tl.mm, 0.0)},
+                        {make_double2(tl.mm, 0.0), make_double2(0.0, 0.0)}};
     double2 E[16];
     loop_edge(V, G, nu, +1, E);
     loop_contract(E, Mm, wq[nq - 1], S);
@@ -224,10 +246,11 @@ extern "C" kb_status kb_vertex_eval(kb_ctx* ctx, int slot, int channel, int spin
     return KB_OK;
 }
 
-extern "C" kb_status kb_loop(kb_ctx* ctx, int slot, int n, const double* nus, void* out, void* stream) {
+extern "C" kb_status kb_loop(kb_ctx* ctx, int slot, int which, int n, const double* nus, void* out,
+                             void* stream) {
     if (!ctx) return KB_ERR_ARG;
-    if (slot < 0 || slot >= KB_MAX_SLOTS || n < 0 || (n > 0 && (!nus || !out))) {
-        ctx->err = "kb_loop: bad slot, count or pointer";
+    if (slot < 0 || slot >= KB_MAX_SLOTS || which < 0 || which > 1 || n < 0 || (n > 0 && (!nus || !out))) {
+        ctx->err = "kb_loop: bad slot, line, count or pointer";
         return KB_ERR_ARG;
     }
     if (!ctx->grids_set || !ctx->model_set || !ctx->slot_set[slot]) {
@@ -239,8 +262,8 @@ extern "C" kb_status kb_loop(kb_ctx* ctx, int slot, int n, const double* nus, vo
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     {
         KB_LAUNCH(ctx, st, "k_loop");
-        k_loop<<<n, LOOP_THREADS, 0, st>>>(ctx->slots[slot], ctx->g, ctx->m, n, nus, ctx->d_xq, ctx->d_wq,
-                                           static_cast<double2*>(out));
+        k_loop<<<n, LOOP_THREADS, 0, st>>>(ctx->slots[slot], ctx->g, ctx->m, which, n, nus, ctx->d_xq,
+                                           ctx->d_wq, static_cast<double2*>(out));
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { ctx->err = std::string("kb_loop: ") + cudaGetErrorString(e); return KB_ERR_CUDA; }

@@ -66,7 +66,7 @@ _SIGS = {
                       C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
     "kb_vertex_add": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_double, C.c_void_p],
     "kb_vertex_eval": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p],
-    "kb_loop": [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p],
+    "kb_loop": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p],
     "kb_vertex_cache": [C.c_void_p, C.c_int, C.c_int, C.c_uint, C.c_void_p],
     "kb_vertex_image": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_void_p],
     "kb_vertex_uncache": [C.c_void_p, C.c_int],
@@ -204,8 +204,8 @@ def kb_vertex_eval(ctx, slot, channel, spin_uu, n, freqs_ptr, out_ptr, stream=0)
     _check(ctx, lib().kb_vertex_eval(ctx, slot, channel, int(bool(spin_uu)), n, freqs_ptr, out_ptr, stream))
 
 
-def kb_loop(ctx, slot, n, nus_ptr, out_ptr, stream=0):
-    _check(ctx, lib().kb_loop(ctx, slot, n, nus_ptr, out_ptr, stream))
+def kb_loop(ctx, slot, which, n, nus_ptr, out_ptr, stream=0):
+    _check(ctx, lib().kb_loop(ctx, slot, which, n, nus_ptr, out_ptr, stream))
 
 
 def kb_add_desc(ctx, channel, slot_src, slot_dst, class_mask=KB_MASK_ALL, alpha=1.0):

@@ -85,7 +85,7 @@ def test_vertex_eval_rejected_without_context():
 
 
 def test_loop_rejected_without_context():
-    assert kb.lib().kb_loop(None, 0, 1, None, None, None) == kb.KB_ERR_ARG
+    assert kb.lib().kb_loop(None, 0, 0, 1, None, None, None) == kb.KB_ERR_ARG
 
 
 def test_vertex_image_rejected_without_context():

@@ -1,6 +1,7 @@
 """Self-energy loop on the GPU (kb_loop): the FP64 kernel equals the oracle's loop element by
 element — seeded vertex with every class in the three channels, complex128 and complex64
 classes, a channel-subset slot, a Sigma table, the interaction flow's scaled propagator,
+the single-scale propagator of each flow scheme (with the Katanin substitution),
 frequencies on, between and far beyond the grids — and the bare vertex alone gives the
 Hartree shift U (n - 1/2)."""
 
@@ -76,4 +77,29 @@ def test_loop_of_bare_vertex_is_the_hartree_shift():
     assert np.abs(got[:, 1, 0] - U * (n - 0.5)).max() <= 1e-9 * U
     assert np.abs(got[:, 0, 1] - U * (n - 0.5)).max() <= 1e-9 * U
     assert np.abs(got[:, 0, 0]).max() <= 1e-12 and np.abs(got[:, 1, 1]).max() <= 1e-12
+    e.close()
+
+
+@pytest.mark.parametrize("reg,lam,katanin", [(0, 1.0, False), (1, 0.7, False), (2, 1.0, False), (0, 1.0, True)])
+def test_single_scale_loop_matches_oracle(reg, lam, katanin):
+    from paper_2405_20996_gb300.engine import Engine
+    cfg = RAGGED
+    g = cfg["grids"]
+    ch = S.seeded_vertex(g, cfg["U"], seed=83)
+    sR = S.seeded_sigma(23, seed=6)
+    sK = 2j * np.tanh(S.grid_freqs(23) / (2 * cfg["T"])) * sR.imag
+    dR = S.seeded_sigma(19, seed=7) if katanin else None
+    dK = 2j * np.tanh(S.grid_freqs(19) / (2 * cfg["T"])) * dR.imag if katanin else None
+    e = Engine(g, cfg["nq"])
+    e.set_model(cfg["Delta"], cfg["T"], eps=0.15)
+    e.set_self_energy(sR, sK)
+    e.set_regulator(reg, lam)
+    if katanin:
+        e.set_self_energy_derivative(dR, dK)
+    e.set_vertex(0, U=cfg["U"], has_R=True, channels=ch)
+    nus = _nus()
+    got = e.loop(0, nus, single_scale=True).cpu().numpy()
+    P = O.Prop(Delta=cfg["Delta"], T=cfg["T"], eps=0.15, sigR=sR, sigK=sK, reg=reg, lam=lam, dsigR=dR, dsigK=dK)
+    ref = O.loop(O.Vertex(g, U=cfg["U"], has_R=True, channels=ch), P, cfg["nq"], nus, which=1)
+    assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max(), np.abs(got - ref).max()
     e.close()

@@ -28,22 +28,60 @@ def _seeded(U=1.0, seed=3, include=(0, 1, 2)):
     return O.Vertex(G, U=U, has_R=True, channels=seeded.seeded_vertex(G, U=U, seed=seed), include=include)
 
 
+def _sigma_tables(n=17, seed=5, T=0.1):
+    sR = seeded.seeded_sigma(n, seed=seed)
+    sK = 2j * np.tanh(seeded.grid_freqs(n) / (2 * T)) * sR.imag         # equilibrium Keldysh part
+    return sR, sK
+
+
+# (propagator: 0 G, 1 S; flow scheme; lambda; Katanin tables) and lim v' P(v') for each
+CASES = [(0, O.REG_DELTA, 1.0, False, 1.0), (0, O.REG_U, 0.7, False, 0.7), (1, O.REG_DELTA, 1.0, False, 0.0),
+         (1, O.REG_U, 0.7, False, 1.0), (1, O.REG_T, 1.0, False, 0.0), (1, O.REG_DELTA, 1.0, True, 0.0)]
+
+
+@pytest.mark.parametrize("case", CASES)
 @pytest.mark.parametrize("nu", [0.0, 0.7, -2.3])
-def test_loop_endpoint_limits(nu):
+def test_loop_endpoint_limits(nu, case):
+    which, reg, lam, katanin, m = case
     V = _seeded()
-    sR = seeded.seeded_sigma(17, seed=5)
-    sK = 2j * np.tanh(seeded.grid_freqs(17) / 0.2) * sR.imag          # equilibrium Keldysh part
-    P = O.Prop(Delta=1.0, T=0.1, eps=0.3, sigR=sR, sigK=sK)
+    sR, sK = _sigma_tables()
+    dR, dK = _sigma_tables(13, seed=8) if katanin else (None, None)
+    P = O.Prop(Delta=1.0, T=0.1, eps=0.3, sigR=sR, sigK=sK, reg=reg, lam=lam, dsigR=dR, dsigK=dK)
+    M = m * np.array([[0, 1], [1, 0]])
     for side in (1, -1):
-        N, E = O.loop_limits(V, P, nu, side)
+        N, E = O.loop_limits(V, P, nu, side, which=which)
         errs = []
         for d in (1e-4, 1e-5):
-            a, b, c = O.loop_pieces(V, P, nu, side * (1 - d))
-            errs.append((np.abs(a - N).max(), np.abs(b - side * E).max() / np.abs(E).max(),
-                         np.abs(c - np.array([[0, 1], [1, 0]])).max()))
+            a, b, c = O.loop_pieces(V, P, nu, side * (1 - d), which=which)
+            errs.append((np.abs(a - N).max(), np.abs(b - side * E).max() / np.abs(E).max(), np.abs(c - M).max()))
         for k in range(3):
             assert errs[1][k] <= 0.2 * errs[0][k] + 1e-12, (side, k, errs)    # O(1 - |x|)
         assert errs[1][0] <= 1e-4 and errs[1][1] <= 1e-5 and errs[1][2] <= 1e-4, errs
+
+
+@pytest.mark.parametrize("reg,lam,katanin", [(O.REG_DELTA, 1.0, False), (O.REG_U, 0.7, False),
+                                             (O.REG_T, 1.0, False), (O.REG_DELTA, 1.0, True)])
+def test_loop_with_single_scale_propagator_is_the_derivative(reg, lam, katanin):
+    """loop(Gamma, S) = d/dLambda loop(Gamma, G_Lambda) at fixed Sigma (the self-energy flow's
+    one-loop term), by central differences in the flow parameter (Delta, lambda or T); with
+    the Katanin tables the derivative is taken along Sigma + Lambda dSigma."""
+    V = _seeded()
+    sR, sK = _sigma_tables()
+    dR, dK = _sigma_tables(17, seed=8) if katanin else (None, None)     # on Sigma's grid
+    D, T, eps, h = 1.0, 0.1, 0.3, 1e-4
+    nus = np.array([0.0, 0.8, -2.5, 9.0])
+
+    def G_at(t):
+        par = dict(Delta=D, T=T, eps=eps, reg=reg, lam=lam)
+        key = {O.REG_DELTA: "Delta", O.REG_U: "lam", O.REG_T: "T"}[reg]
+        par[key] = par[key] + t
+        sr, sk = (sR + t * dR, sK + t * dK) if katanin else (sR, sK)
+        return O.Prop(sigR=sr, sigK=sk, **par)
+
+    fd = (O.loop(V, G_at(h), 401, nus) - O.loop(V, G_at(-h), 401, nus)) / (2 * h)
+    P = O.Prop(Delta=D, T=T, eps=eps, sigR=sR, sigK=sK, reg=reg, lam=lam, dsigR=dR, dsigK=dK)
+    S = O.loop(V, P, 401, nus, which=1)
+    assert np.abs(S - fd).max() <= 1e-6 * np.abs(S).max(), np.abs(S - fd).max() / np.abs(S).max()
 
 
 @pytest.mark.parametrize("T", [0.1, 0.0])
