@@ -1,5 +1,5 @@
 """Vertex flow of the multiloop fRG (Sec. III.C) in the interaction-flow scheme, with the
-self-energy held fixed.
+self-energy held fixed or flowing at one loop.
 
 The interaction flow scales the propagator, G_Λ = Λ G at Σ = 0 (Sec. III.C.2), from Λ ≈ 0
 (where γ = 0) to Λ = 1.  The vertex's reducible parts obey dγ_r/dΛ = Σ_{l ≤ n} γ̇_r^(l), the
@@ -9,8 +9,13 @@ the flow reproduces the parquet solution at the final Λ (the parquet approximat
 does not depend on Λ).  The integrator is the embedded Runge–Kutta pair of Cash and Karp
 (orders 5 and 4, six stages) with step-size control on the maximum norm, the scheme the
 paper uses for its flows (Sec. III.C.1); the step advances with the fifth-order solution and
-the difference of the two solutions is the error estimate.  The self-energy flow (Σ-dot with its loop and multiloop
-corrections) is not part of this module.
+the difference of the two solutions is the error estimate.
+
+With n_sig > 0 the self-energy flows too, at one loop: Σ-dot = loop(Γ, S) (the `loop`
+function with the single-scale propagator at fixed Σ), Σ stored on an n_sig-point tan grid
+(the library's Σ tables, linear in x, zero at v = ±inf), and the vertex's Π-dot takes the
+Katanin substitution S -> S + G Σ-dot G.  The multiloop corrections of Σ-dot (its t̄ and t
+terms) are not included, so only the one-loop flow (n_loops = 1) is complete in Σ.
 """
 
 import numpy as np
@@ -35,7 +40,7 @@ _B4 = (2825 / 27648, 0.0, 18575 / 48384, 13525 / 55296, 277 / 14336, 1 / 4)
 class VertexFlow:
     """n-loop vertex flow of one parameter point (grids, Nq, U, Δ, T) in the interaction flow."""
 
-    def __init__(self, grids, nq, U, Delta, T, n_loops=6, precision="fp64", A=5.0, device=0):
+    def __init__(self, grids, nq, U, Delta, T, n_loops=6, precision="fp64", A=5.0, device=0, n_sig=0):
         g = grids
         shapes = {"K1": (g["n1"], 16), "K2": (g["n2w"], g["n2v"], 16), "K2p": (g["n2w"], g["n2v"], 16),
                   "K3": (g["n3w"], g["n3v"], g["n3v"], 16)}
@@ -50,6 +55,11 @@ class VertexFlow:
         self.dtype = self.gamma_t[0].dtype
         self.dev = e0.device
         self.rhs_calls = 0
+        self.n_sig, self.A = int(n_sig), A
+        self.n_gamma = sum(self.sizes)
+        if self.n_sig:
+            x = -1.0 + 2.0 * (np.arange(self.n_sig) + 1) / (self.n_sig + 1)
+            self.sig_grid = A * np.tan(np.pi * x / 2)           # the Σ table's frequencies
 
     def close(self):
         self.ml.close()
@@ -64,6 +74,14 @@ class VertexFlow:
     def _total(self):
         return torch.cat([self.ml.total[(c, k)].reshape(-1) for c in range(3) for k in range(4)])
 
+    def size(self):
+        """Length of the flat state: the 12 class arrays, then Σ^R and Σ^K on the Σ grid."""
+        return self.n_gamma + 2 * self.n_sig
+
+    def sigma(self, y):
+        """(Σ^R, Σ^K) views of a flat state on the Σ grid (empty without a flowing Σ)."""
+        return y[self.n_gamma:self.n_gamma + self.n_sig], y[self.n_gamma + self.n_sig:]
+
     def channels(self, y):
         """{channel: {class: tensor}} views of a flat state."""
         out, off = {}, 0
@@ -76,20 +94,37 @@ class VertexFlow:
         return out
 
     def rhs(self, lam, y):
-        """dγ/dΛ at Λ = lam: the multiloop right-hand side with the interaction-flow propagator."""
-        for e in self.ml.e.values():
+        """dy/dΛ at Λ = lam: the multiloop right-hand side of the vertex with the
+        interaction-flow propagator, and with a flowing Σ its one-loop Σ-dot = loop(Γ, S)
+        followed by the vertex's Katanin substitution."""
+        engines = list(self.ml.e.values())
+        for e in engines:
             e.set_regulator(kb.KB_REG_U, lam)
-        self._store(y)
+        self._store(y[:self.n_gamma])
+        if self.n_sig:
+            sR, sK = (t.detach().cpu().numpy() for t in self.sigma(y))
+            for e in engines:
+                e.set_self_energy(sR, sK, self.A)
+                e.set_self_energy_derivative(None)
+            e0 = self.ml.e[self.ml.channels[0]]
+            ds = e0.loop(S_GAMMA, self.sig_grid, single_scale=True)
+            dR, dK = ds[:, 1, 0], ds[:, 1, 1]
+            dRh, dKh = dR.cpu().numpy(), dK.cpu().numpy()
+            for e in engines:
+                e.set_self_energy_derivative(dRh, dKh, self.A)
         self.ml.zero()
         self.ml.run_eager()
         self.rhs_calls += 1
-        return self._total().clone()
+        out = self._total()
+        if self.n_sig:
+            out = torch.cat([out, dR.to(out.dtype), dK.to(out.dtype)])
+        return out.clone()
 
     def integrate(self, lam0, lam1, y0=None, h0=0.05, rtol=1e-6, atol=1e-10, max_steps=500, callback=None):
         """Cash–Karp integration from Λ = lam0 (state y0, default 0) to lam1; returns
         (y, accepted steps, rejected steps).  callback(Λ, y) after every accepted step (e.g.
         a checkpoint layer); a run resumes from a saved (Λ, y)."""
-        y = torch.zeros(sum(self.sizes), dtype=self.dtype, device=self.dev) if y0 is None else y0.clone()
+        y = torch.zeros(self.size(), dtype=self.dtype, device=self.dev) if y0 is None else y0.clone()
         lam, h = float(lam0), float(h0)
         acc = rej = 0
         while lam < lam1 - 1e-14 and acc + rej < max_steps:
