@@ -45,7 +45,8 @@ S_DELTA = 4                 # V = v_a + v_p + v_t (a tangent or adjoint directio
 S_DELTA_I = (5, 6, 7)       # V − v_r
 S_OUT = 8                   # bubble outputs, all channels
 S_GRAD = 9                  # adjoint accumulation, all channels
-S_RHAT = 10                 # the bare vertex of unit strength, no classes (∂/∂U)
+S_RHAT = 10                 # the bare vertex of unit strength, no classes (∂/∂U, the SDE)
+S_X = 11                    # X̂ = B_a(R̂, Γ) of the Schwinger–Dyson equation: channel a only
 
 
 class ParquetPA:
@@ -159,6 +160,9 @@ class ParquetPA:
             self.e.bubble_vjp(r, S_I[r], S_GAMMA, S_OUT, grad_left=S_GRAD, grad_right=S_GRAD)
         return u - self.grad
 
+    def _zero_state(self):
+        return torch.zeros_like(self.gamma)
+
     @staticmethod
     def rel(diff, ref):
         return float(diff.abs().max()) / max(float(ref.abs().max()), 1e-300)
@@ -167,7 +171,7 @@ class ParquetPA:
     def fixed_point(self, mix=0.5, tol=1e-10, maxit=500, gamma0=None, callback=None):
         """Damped iteration; returns (γ, history of relative residuals).  callback(it, γ, r)
         after every iteration (e.g. a checkpoint); gamma0 resumes from a saved state."""
-        g = torch.zeros_like(self.gamma) if gamma0 is None else gamma0.clone()
+        g = self._zero_state() if gamma0 is None else gamma0.clone()
         hist = []
         for it in range(maxit):
             b = self.bse(g)
@@ -187,7 +191,7 @@ class ParquetPA:
         γ_{k+1} = (g_k − ΔG c) − (1 − mix)(f_k − ΔF c).  The least-squares problem is solved by
         QR; the oldest differences are dropped while R's diagonal spans more than cond_max.
         m = 0 is the damped iteration.  Returns (γ, history of relative residuals)."""
-        g = torch.zeros_like(self.gamma) if gamma0 is None else gamma0.clone()
+        g = self._zero_state() if gamma0 is None else gamma0.clone()
         hist = []
         dF, dG = [], []
         f_prev = b_prev = None
@@ -306,3 +310,69 @@ class ParquetPA:
             if callback is not None:
                 callback(step, g, hist[-1])
         return g, hist, lin
+
+
+class ParquetSDE(ParquetPA):
+    """Parquet approximation with a self-consistent self-energy from the Schwinger–Dyson
+    equation (Sec. III.B), the self-energy on an n_sig-point tan grid (the library's Σ
+    tables: linear in x, zero at v = ±inf).
+
+    The state is z = [γ (the 12 class arrays), Σ^R, Σ^K]; the map sets G[Σ] and returns the
+    Bethe–Salpeter right-hand sides B_r(I_r, Γ) and the Schwinger–Dyson self-energy, both
+    with that G.  SDE in its a-channel form: the bare vertex, an a-channel bubble to the full
+    vertex and the line that closes it,
+        Σ = U loop(R̂) + loop_ud(B_a(R, Γ)) = U [loop(R̂) + ½ loop(X̂)],   X̂ = B_a(R̂, Γ),
+    where loop is kb_loop (Σ = −∫dv'/(2πi) Γ_s G with Γ_s = Γ_ud + Γ_uu) and the closed line
+    joins legs 2' (on Γ) and 2 (on R), so only X̂'s up-down part enters: X̂ sits in a slot
+    with channel a alone and no crossing-partner data, where Γ_s = 2 X̂_ud.  loop(R̂) is the
+    Hartree shift per unit U (zero at particle-hole symmetry).  At second order this is the
+    sunset self-energy exactly (pinned against the textbook spectral integral).  The paper
+    also combines the p- and t-channel forms; only the a-channel form is built.  Solved
+    with the damped iteration or Anderson acceleration on z (the Newton–Krylov Jacobian
+    of the base class does not include Σ)."""
+
+    def __init__(self, grids, nq, U, Delta, T, n_sig=41, A=5.0, eps=0.0, device=0):
+        super().__init__(grids, nq, U, Delta, T, A=A, eps=eps, device=device)
+        self.n_sig, self.A_sig = int(n_sig), A
+        x = -1.0 + 2.0 * (np.arange(self.n_sig) + 1) / (self.n_sig + 1)
+        self.sig_grid = A * np.tan(np.pi * x / 2)
+        sh = self.e.class_shapes()
+        self.xa = [torch.zeros(sh[name], dtype=torch.complex128, device=self.dev) for name in CLASS_NAMES]
+        kb.kb_set_vertex(self.e.ctx, S_X, False, 0.0)
+        kb.kb_set_vertex_channels(self.e.ctx, S_X, 1 << 0)
+        kb.kb_set_vertex_symmetric(self.e.ctx, S_X, False)
+        self.e.tensors[S_X] = {}
+        for k in range(4):
+            self.e.attach(S_X, 0, k, self.xa[k])
+        kb.kb_set_vertex(self.e.ctx, S_RHAT, True, 1.0)
+
+    def _zero_state(self):
+        return torch.zeros(self.n + 2 * self.n_sig, dtype=torch.complex128, device=self.dev)
+
+    def split(self, z):
+        """(γ, Σ^R, Σ^K) views of a state."""
+        return z[:self.n], z[self.n:self.n + self.n_sig], z[self.n + self.n_sig:]
+
+    def set_sigma(self, sR, sK):
+        self.e.set_self_energy(sR.detach().cpu().numpy(), sK.detach().cpu().numpy(), self.A_sig)
+
+    def sde(self, gamma):
+        """(Σ^R, Σ^K) on the Σ grid from the SDE for γ, with the context's current G."""
+        self.gamma.copy_(gamma)
+        self.e.bubble(0, S_RHAT, S_GAMMA, S_X, precision="fp64")
+        self.bubbles += 1
+        s = self.U * (self.e.loop(S_RHAT, self.sig_grid) + 0.5 * self.e.loop(S_X, self.sig_grid))
+        return s[:, 1, 0], s[:, 1, 1]
+
+    def bse(self, z):
+        """The joint map: [B_r(I_r, Γ), Σ_SDE] at G[Σ]."""
+        g, sR, sK = self.split(z)
+        self.set_sigma(sR, sK)
+        b = ParquetPA.bse(self, g)
+        sR2, sK2 = self.sde(g)
+        return torch.cat([b, sR2, sK2])
+
+    def jvp(self, gamma, v):
+        raise NotImplementedError("the Jacobian products do not include the self-energy")
+
+    adjoint = jvp
