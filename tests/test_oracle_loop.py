@@ -11,7 +11,10 @@
   in G), the loop of the second-order vertex is 3 Sigma2; Im Sigma2^R against the textbook
   double spectral integral of the symmetric Anderson model, converging at second order in
   the grid spacing; causality, FDR and particle-hole symmetry of the result;
-- linearity in the vertex."""
+- linearity in the vertex;
+- brute force: the fixed rule converges to an adaptive integration of the defining
+  integrand (vertex and propagator through the general routines, x paired with -x for the
+  principal value) for a seeded vertex with every class."""
 
 import numpy as np
 import pytest
@@ -174,3 +177,29 @@ def test_loop_is_linear_in_the_vertex():
     S = O.loop(Vs, P, 401, nus)
     ref = a * O.loop(V1c, P, 401, nus) + b * O.loop(V2c, P, 401, nus)
     assert np.abs(S - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def _loop_brute(V, P, nu, A=5.0):
+    """-int dv'/(2 pi i) Gamma_s . G by adaptive quadrature in x, the integrand at x and -x
+    summed (symmetric principal value), each point through vertex_eval and prop_eval."""
+    def f(x):
+        xs = np.array([x, -x])
+        nup = A * np.tan(np.pi * xs / 2)
+        J = A * np.pi / 2 * (1 + np.tan(np.pi * xs / 2) ** 2)
+        pts = np.stack([np.zeros(2), np.full(2, nu), nup], axis=1)
+        Gs = O.vertex_eval(V, 2, 0, 1, O.SEL_FULL, pts) + O.vertex_eval(V, 2, 1, 1, O.SEL_FULL, pts)
+        Gs = Gs.reshape(2, 2, 2, 2, 2)                          # [point][a1'][a2'][a1][a2]
+        S = np.einsum("npqrs,nsq->npr", Gs, O.prop_eval(P, 0, nup))
+        S = -(J[:, None, None] * S).sum(0) / (2j * np.pi)
+        return np.concatenate([S.real.ravel(), S.imag.ravel()])
+    res, _ = integrate.quad_vec(f, 0.0, 1.0, epsabs=1e-12, epsrel=1e-12, limit=20000)
+    return (res[:4] + 1j * res[4:]).reshape(2, 2)
+
+
+def test_loop_fixed_rule_converges_to_adaptive_brute_force():
+    V = _seeded()
+    P = O.Prop(Delta=1.0, T=0.1, eps=0.3)
+    for nu in (0.0, 1.3):
+        ref = _loop_brute(V, P, nu)
+        errs = [np.abs(O.loop(V, P, nq, np.array([nu]))[0] - ref).max() / np.abs(ref).max() for nq in (1001, 4001)]
+        assert errs[1] <= 0.2 * errs[0] and errs[1] <= 5e-6, (nu, errs)
