@@ -282,7 +282,9 @@ static double tanh_ft(double v, double T) {
     return tanh(v / (2.0 * T));
 }
 
-/* 2x2 Keldysh matrices M[a][a'] (a, a' = 0 classical, 1 quantum). which: 0 = G, 1 = S */
+/* 2x2 Keldysh matrices M[a][a'] (a, a' = 0 classical, 1 quantum). which: 0 = G, 1 = S,
+ * 2 = G dSigma G alone (the line with one insertion of the dSigma tables, the multiloop
+ * self-energy flow's t term) */
 static void prop_matrix(const oprop *P, int which, double v, cplx M[2][2]) {
     cplx sR, sK;
     sigma_at(P->n_sig, P->A_sig, P->sigR, P->sigK, v, &sR, &sK);
@@ -296,6 +298,15 @@ static void prop_matrix(const oprop *P, int which, double v, cplx M[2][2]) {
         M[0][0] = GR * mid * GA;
         M[0][1] = GR;
         M[1][0] = GA;
+        M[1][1] = 0;
+    } else if (which == 2) {
+        /* the contour product G dSigma G with dSigma = [[0, dS^A], [dS^R, dS^K]] */
+        cplx dR = 0, dK = 0;
+        if (P->n_dsig > 0) sigma_at(P->n_dsig, P->A_dsig, P->dsigR, P->dsigK, v, &dR, &dK);
+        cplx dA = conj(dR), GK = GR * mid * GA;
+        M[0][1] = GR * dR * GR;
+        M[1][0] = GA * dA * GA;
+        M[0][0] = GR * dR * GK + GK * dA * GA + GR * dK * GA;
         M[1][1] = 0;
     } else {
         /* S^R = -(G^R)^2 d[(G^R)^-1]/dLambda: hybridisation -i (G^R)^2; interaction
@@ -335,7 +346,7 @@ static void prop_matrix(const oprop *P, int which, double v, cplx M[2][2]) {
 /* lim_{v->+-inf} v * P(v): G -> lam [[0,1],[1,0]] (lam = 1 but in the interaction flow);
  * S -> [[0,1],[1,0]] in the interaction flow (S^R -> 1/v), else 0 */
 static void prop_asym(const oprop *P, int which, cplx M[2][2]) {
-    double g = (which == 0) ? ((P->reg == 1) ? P->lam : 1.0) : ((P->reg == 1) ? 1.0 : 0.0);
+    double g = (which == 0) ? ((P->reg == 1) ? P->lam : 1.0) : (which == 1 && P->reg == 1) ? 1.0 : 0.0;
     M[0][0] = 0; M[1][1] = 0;
     M[0][1] = M[1][0] = g;
 }
@@ -922,11 +933,15 @@ int og_bubble_vjp_points(const ovtx *V1, const ovtx *V2, const oprop *P, int pi_
  *   S, interaction flow: S = G / lam at Sigma = 0 to this order: N^R = eps - i Delta,
  *      N^K = -2 i Delta th;
  *   S, temperature flow: S^R = 0 and S^K falls exponentially: N = 0.
- * The Katanin term G dSigma G falls like 1/v'^3 and adds nothing.  N^A = (N^R)*. */
+ * The Katanin term G dSigma G falls like 1/v'^3 and adds nothing, and the line G dSigma G
+ * alone (which 2) has N = 0.  N^A = (N^R)*. */
 static void prop_tail2(const oprop *P, int which, int side, cplx N[2][2]) {
     const double lam = (P->reg == 1) ? P->lam : 1.0;
     const double th = (double)side;
-    if (which == 0) {
+    if (which == 2) {
+        N[0][1] = 0;
+        N[0][0] = 0;
+    } else if (which == 0) {
         N[0][1] = lam * (P->eps - I * P->Delta);
         N[0][0] = -2.0 * I * P->Delta * th * lam;
     } else if (P->reg == 1) {
@@ -1024,11 +1039,11 @@ static void loop_vertex(const ovtx *V, int sel, double nu, double nup, cplx G[16
     for (int c = 0; c < 16; ++c) G[c] = a[c] + b[c];
 }
 
-/* Public: Sigma at npts frequencies nus with P = G (which 0) or S (which 1);
+/* Public: Sigma at npts frequencies nus with P = G (which 0), S (which 1) or G dSigma G (which 2);
  * out[4 i + 2 a1' + a1] (0 classical, 1 quantum). */
 int og_loop(const ovtx *V, const oprop *P, int which, int Nq, int npts, const double *nus, cplx *out,
             int nthreads) {
-    if (Nq < 5 || (Nq - 1) % 4 || which < 0 || which > 1) return -1;
+    if (Nq < 5 || (Nq - 1) % 4 || which < 0 || which > 2) return -1;
     double *xq = malloc(sizeof(double) * Nq), *wq = malloc(sizeof(double) * Nq);
     if (!xq || !wq) { free(xq); free(wq); return -2; }
     og_gl5_rule(Nq, xq, wq);

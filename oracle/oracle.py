@@ -286,7 +286,8 @@ def prop_eval(P, which, v):
 def loop(V, P, Nq, nus, nthreads=0, which=0):
     """Self-energy loop Sigma^{a1'|a1}(v) = -int dv'/(2 pi i) sum Gamma_s^{a1' a2'|a1 a2}(v, v'|v, v')
     P^{a2|a2'}(v') with Gamma_s = Gamma_ud + Gamma_uu (Sec. II.D.2; readings in kb_oracle.c),
-    P = G (which 0) or the flow scheme's single-scale propagator S (which 1).
+    P = G (which 0), the flow scheme's single-scale propagator S (which 1), or the line with one
+    insertion of the dSigma tables, G dSigma G (which 2).
     Returns (n, 2, 2) complex: [a1'][a1], 0 = classical, 1 = quantum."""
     nus = np.ascontiguousarray(nus, dtype=np.float64)
     out = np.zeros((len(nus), 2, 2), dtype=np.complex128)

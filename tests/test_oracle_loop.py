@@ -12,6 +12,8 @@
   double spectral integral of the symmetric Anderson model, converging at second order in
   the grid spacing; causality, FDR and particle-hole symmetry of the result;
 - linearity in the vertex;
+- the line with one self-energy insertion, G dSigma G: it is the derivative of the Dyson
+  propagator along dSigma, and the loop with it is the derivative of the loop along dSigma;
 - brute force: the fixed rule converges to an adaptive integration of the defining
   integrand (vertex and propagator through the general routines, x paired with -x for the
   principal value) for a seeded vertex with every class."""
@@ -39,7 +41,8 @@ def _sigma_tables(n=17, seed=5, T=0.1):
 
 # (propagator: 0 G, 1 S; flow scheme; lambda; Katanin tables) and lim v' P(v') for each
 CASES = [(0, O.REG_DELTA, 1.0, False, 1.0), (0, O.REG_U, 0.7, False, 0.7), (1, O.REG_DELTA, 1.0, False, 0.0),
-         (1, O.REG_U, 0.7, False, 1.0), (1, O.REG_T, 1.0, False, 0.0), (1, O.REG_DELTA, 1.0, True, 0.0)]
+         (1, O.REG_U, 0.7, False, 1.0), (1, O.REG_T, 1.0, False, 0.0), (1, O.REG_DELTA, 1.0, True, 0.0),
+         (2, O.REG_DELTA, 1.0, True, 0.0)]
 
 
 @pytest.mark.parametrize("case", CASES)
@@ -203,3 +206,22 @@ def test_loop_fixed_rule_converges_to_adaptive_brute_force():
         ref = _loop_brute(V, P, nu)
         errs = [np.abs(O.loop(V, P, nq, np.array([nu]))[0] - ref).max() / np.abs(ref).max() for nq in (1001, 4001)]
         assert errs[1] <= 0.2 * errs[0] and errs[1] <= 5e-6, (nu, errs)
+
+
+def test_line_with_a_self_energy_insertion_is_the_derivative_along_dsigma():
+    """G dSigma G (which 2) = d/dt G[Sigma + t dSigma] (the contour product, all four Keldysh
+    entries), and loop(Gamma, G dSigma G) = d/dt loop(Gamma, G[Sigma + t dSigma]) at t = 0."""
+    sR, sK = _sigma_tables()
+    dR, dK = _sigma_tables(17, seed=8)
+    D, T, eps, h = 1.0, 0.1, 0.3, 1e-4
+    at = lambda t: O.Prop(Delta=D, T=T, eps=eps, sigR=sR + t * dR, sigK=sK + t * dK)
+    P = O.Prop(Delta=D, T=T, eps=eps, sigR=sR, sigK=sK, dsigR=dR, dsigK=dK)
+    v = np.array([-30.0, -2.2, -0.4, 0.0, 0.1, 0.9, 4.0, 77.0])
+    line = O.prop_eval(P, 2, v)
+    fd = (O.prop_eval(at(h), 0, v) - O.prop_eval(at(-h), 0, v)) / (2 * h)
+    assert np.abs(line - fd).max() <= 1e-7 * np.abs(line).max()
+    V = _seeded()
+    nus = np.array([0.0, 0.8, -2.5, 9.0])
+    S = O.loop(V, P, 401, nus, which=2)
+    fdl = (O.loop(V, at(h), 401, nus) - O.loop(V, at(-h), 401, nus)) / (2 * h)
+    assert np.abs(S - fdl).max() <= 1e-6 * np.abs(S).max(), np.abs(S - fdl).max() / np.abs(S).max()
