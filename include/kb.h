@@ -284,7 +284,9 @@ kb_status kb_vertex_eval(kb_ctx *ctx, int slot, int channel, int spin_uu, int n,
 /* Self-energy loop (the paper's `loop` function, Sec. II.D.2): the vertex of slot `slot`
  * closed by one propagator line P of the context's model — which = 0: P = G; which = 1:
  * P = S, the single-scale propagator of the flow scheme (kb_set_regulator, with the
- * Katanin substitution when set), the one-loop term of the self-energy flow —
+ * Katanin substitution when set), the one-loop term of the self-energy flow; which = 2:
+ * P = G dSigma G, one insertion of the kb_set_self_energy_derivative tables (zero without
+ * them), the line of the multiloop self-energy flow's t term —
  *   Sigma^{a1'|a1}(v) = - int dv'/(2 pi i) sum_{a2', a2} Gamma_s^{a1' a2'|a1 a2}(v, v'|v, v')
  *                          P^{a2|a2'}(v'),   Gamma_s = Gamma_up-down + Gamma_up-up,
  * with the vertex read in t-channel variables (w_t = 0, v, v') and the internal line's

@@ -6,8 +6,9 @@
 //
 // The self-energy loop (Sec. II.D.2) closes the vertex with one propagator line:
 //   Sigma^{a1'|a1}(v) = - int dv'/(2 pi i) sum Gamma_s^{a1' a2'|a1 a2}(v, v'|v, v') P^{a2|a2'}(v'),
-//   Gamma_s = Gamma_ud + Gamma_uu, the vertex in t-channel variables (0, v, v'), P = G or the
-//   single-scale propagator S of the flow scheme (the self-energy flow's loop(Gamma, S)),
+//   Gamma_s = Gamma_ud + Gamma_uu, the vertex in t-channel variables (0, v, v'), P = G, the
+//   single-scale propagator S of the flow scheme (the self-energy flow's loop(Gamma, S)) or
+//   the line G dSigma G with one insertion of the dSigma tables (its multiloop t term),
 // the sign of the Schwinger-Dyson equation's bare term (Sec. III.B), the v' integral the
 // symmetric principal value at +-inf.  On the composite GL5 rule in x = (2/pi) atan(v'/A):
 // the v'-independent part C(v) (R + K1_t + K2_t of both spin components) multiplies
@@ -131,16 +132,41 @@ constexpr int LOOP_THREADS = 256;
 //   S, interaction flow (S = G / lam at this order): mm = 1, nR = eps - i Delta, nK = 2 Delta;
 //   S, temperature flow: all zero (S^R = 0, S^K falls exponentially).
 // The Katanin term G dSigma G falls like 1/v'^3 and adds nothing.
+// The line with one insertion of the dSigma tables, G dSigma G (which 2), falls like 1/v'^3:
+// all zero.
 struct LineTail {
     double mm, nK;
     double2 nR;
 };
 __device__ __forceinline__ LineTail line_tail(const Model& m, int which) {
     const double lam = (m.reg == KB_REG_U) ? m.lam : 1.0;
+    if (which == 2) return {0.0, 0.0, make_double2(0.0, 0.0)};
     if (which == 0) return {lam, 2.0 * lam * m.Delta, make_double2(lam * m.eps, -lam * m.Delta)};
     if (m.reg == KB_REG_U) return {1.0, 2.0 * m.Delta, make_double2(m.eps, -m.Delta)};
     if (m.reg == KB_REG_T) return {0.0, 0.0, make_double2(0.0, 0.0)};
     return {0.0, 2.0, make_double2(0.0, -1.0)};
+}
+
+// G dSigma G at v: the contour product with dSigma = [[0, dS^A], [dS^R, dS^K]] (the dSigma
+// tables, linear in x, zero at x = +-1) in the [[K, R], [A, 0]] layout of G; zero without tables.
+__device__ void line_with_insertion(const Model& m, double v, double2 P[2][2]) {
+    double2 Gm[2][2];
+    prop2x2(m, 0, v, Gm);
+    double2 dR = make_double2(0, 0), dK = make_double2(0, 0);
+    if (m.n_dsig > 0) {
+        double t;
+        int k = xstencil(v, m.n_dsig, m.A_dsig, t);
+        if (k >= 0) { dR = cadd(dR, cscale(m.dsigR[k], 1.0 - t)); dK = cadd(dK, cscale(m.dsigK[k], 1.0 - t)); }
+        if (k >= -1 && k + 1 <= m.n_dsig - 1) {
+            dR = cadd(dR, cscale(m.dsigR[k + 1], t));
+            dK = cadd(dK, cscale(m.dsigK[k + 1], t));
+        }
+    }
+    const double2 GR = Gm[0][1], GA = Gm[1][0], GK = Gm[0][0], dA = cconj(dR);
+    P[0][1] = cmul(cmul(GR, dR), GR);
+    P[1][0] = cmul(cmul(GA, dA), GA);
+    P[0][0] = cadd(cadd(cmul(cmul(GR, dR), GK), cmul(cmul(GK, dA), GA)), cmul(cmul(GR, dK), GA));
+    P[1][1] = make_double2(0, 0);
 }
 
 // One block per output frequency; threads stride over the interior nodes 1 .. nq-2.
@@ -160,7 +186,8 @@ __global__ void __launch_bounds__(LOOP_THREADS) k_loop(VertexDev V, Grids G, Mod
         const double tn = tan(0.5 * KB_PI * xq[j]);
         const double nup = A * tn, f = wq[j] * (0.5 * A * KB_PI * (1.0 + tn * tn));
         double2 P[2][2];
-        prop2x2(m, which, nup, P);
+        if (which == 2) line_with_insertion(m, nup, P);
+        else prop2x2(m, which, nup, P);
         P[1][1] = make_double2(0.0, 0.0);
         const double sub = tl.mm * nup / (nup * nup + A * A);
         acc[4].x = fma(f, P[0][0].x, acc[4].x);         acc[4].y = fma(f, P[0][0].y, acc[4].y);
@@ -249,7 +276,7 @@ extern "C" kb_status kb_vertex_eval(kb_ctx* ctx, int slot, int channel, int spin
 extern "C" kb_status kb_loop(kb_ctx* ctx, int slot, int which, int n, const double* nus, void* out,
                              void* stream) {
     if (!ctx) return KB_ERR_ARG;
-    if (slot < 0 || slot >= KB_MAX_SLOTS || which < 0 || which > 1 || n < 0 || (n > 0 && (!nus || !out))) {
+    if (slot < 0 || slot >= KB_MAX_SLOTS || which < 0 || which > 2 || n < 0 || (n > 0 && (!nus || !out))) {
         ctx->err = "kb_loop: bad slot, line, count or pointer";
         return KB_ERR_ARG;
     }

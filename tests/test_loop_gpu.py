@@ -103,3 +103,25 @@ def test_single_scale_loop_matches_oracle(reg, lam, katanin):
     ref = O.loop(O.Vertex(g, U=cfg["U"], has_R=True, channels=ch), P, cfg["nq"], nus, which=1)
     assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max(), np.abs(got - ref).max()
     e.close()
+
+
+def test_loop_with_a_self_energy_insertion_matches_oracle():
+    from paper_2405_20996_gb300.engine import Engine
+    cfg = RAGGED
+    g = cfg["grids"]
+    ch = S.seeded_vertex(g, cfg["U"], seed=84)
+    sR = S.seeded_sigma(23, seed=6)
+    sK = 2j * np.tanh(S.grid_freqs(23) / (2 * cfg["T"])) * sR.imag
+    dR = S.seeded_sigma(19, seed=9)
+    dK = 2j * np.tanh(S.grid_freqs(19) / (2 * cfg["T"])) * dR.imag
+    e = Engine(g, cfg["nq"])
+    e.set_model(cfg["Delta"], cfg["T"], eps=0.15)
+    e.set_self_energy(sR, sK)
+    e.set_self_energy_derivative(dR, dK)
+    e.set_vertex(0, U=cfg["U"], has_R=True, channels=ch)
+    nus = _nus()
+    got = e.loop(0, nus, line=2).cpu().numpy()
+    P = O.Prop(Delta=cfg["Delta"], T=cfg["T"], eps=0.15, sigR=sR, sigK=sK, dsigR=dR, dsigK=dK)
+    ref = O.loop(O.Vertex(g, U=cfg["U"], has_R=True, channels=ch), P, cfg["nq"], nus, which=2)
+    assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max(), np.abs(got - ref).max()
+    e.close()
