@@ -11,11 +11,15 @@ does not depend on Λ).  The integrator is the embedded Runge–Kutta pair of Ca
 paper uses for its flows (Sec. III.C.1); the step advances with the fifth-order solution and
 the difference of the two solutions is the error estimate.
 
-With n_sig > 0 the self-energy flows too, at one loop: Σ-dot = loop(Γ, S) (the `loop`
-function with the single-scale propagator at fixed Σ), Σ stored on an n_sig-point tan grid
-(the library's Σ tables, linear in x, zero at v = ±inf), and the vertex's Π-dot takes the
-Katanin substitution S -> S + G Σ-dot G.  The multiloop corrections of Σ-dot (its t̄ and t
-terms) are not included, so only the one-loop flow (n_loops = 1) is complete in Σ.
+With n_sig > 0 the self-energy flows too, Σ stored on an n_sig-point tan grid (the
+library's Σ tables, linear in x, zero at v = ±inf), and the vertex's Π-dot takes the
+Katanin substitution S -> S + G Σ-dot G.  Σ-dot = L(Γ, S) at one and two loops, with L the
+`loop` function (the single-scale propagator at fixed Σ); from three loops on it adds the
+multiloop terms,
+    Σ-dot = L(Γ, S) + Σ-dot_t̄ + Σ-dot_t,   Σ-dot_t̄ = L(γ̇^C_t̄, G),   Σ-dot_t = L(Γ, G Σ-dot_t̄ G),
+γ̇^C_t̄ the central parts (orders l >= 3) of the a and p channels, and since the vertex's
+central parts depend on Σ-dot through the Katanin line, Σ-dot and the vertex step are
+iterated to self-consistency (at most sigma_iters times, relative change sigma_tol).
 """
 
 import numpy as np
@@ -23,7 +27,7 @@ import torch
 
 from . import kb
 from .engine import CLASS_NAMES
-from .multiloop import S_GAMMA, MultiloopStep
+from .multiloop import S_GAMMA, MultiloopStep, s_central
 
 # Cash-Karp Butcher tableau (published coefficients of the embedded 5(4) pair)
 _C = (0.0, 1 / 5, 3 / 10, 3 / 5, 1.0, 7 / 8)
@@ -40,7 +44,8 @@ _B4 = (2825 / 27648, 0.0, 18575 / 48384, 13525 / 55296, 277 / 14336, 1 / 4)
 class VertexFlow:
     """n-loop vertex flow of one parameter point (grids, Nq, U, Δ, T) in the interaction flow."""
 
-    def __init__(self, grids, nq, U, Delta, T, n_loops=6, precision="fp64", A=5.0, device=0, n_sig=0):
+    def __init__(self, grids, nq, U, Delta, T, n_loops=6, precision="fp64", A=5.0, device=0, n_sig=0,
+                 sigma_iters=10, sigma_tol=1e-8):
         g = grids
         shapes = {"K1": (g["n1"], 16), "K2": (g["n2w"], g["n2v"], 16), "K2p": (g["n2w"], g["n2v"], 16),
                   "K3": (g["n3w"], g["n3v"], g["n3v"], 16)}
@@ -48,7 +53,10 @@ class VertexFlow:
         # Γ along the flow is not kept exactly symmetric by the central parts' discretisation,
         # so no symmetry reduction is used
         self.ml = MultiloopStep(grids, nq, U, Delta, T, zero, n_loops=n_loops, precision=precision, A=A,
-                                device=device, symmetric=False, cache=False)
+                                device=device, symmetric=False, cache=False,
+                                keep_central=(n_sig > 0 and n_loops >= 3))
+        self.sigma_iters, self.sigma_tol = int(sigma_iters), float(sigma_tol)
+        self.sigma_iterations = 0
         e0 = self.ml.e[self.ml.channels[0]]
         self.gamma_t = [e0.tensors[S_GAMMA][(c, k)] for c in range(3) for k in range(4)]
         self.sizes = [t.numel() for t in self.gamma_t]
@@ -95,8 +103,9 @@ class VertexFlow:
 
     def rhs(self, lam, y):
         """dy/dΛ at Λ = lam: the multiloop right-hand side of the vertex with the
-        interaction-flow propagator, and with a flowing Σ its one-loop Σ-dot = loop(Γ, S)
-        followed by the vertex's Katanin substitution."""
+        interaction-flow propagator; with a flowing Σ, Σ-dot (one-loop term, and from three
+        loops on its t̄ and t terms, iterated with the vertex step) and the vertex's Katanin
+        substitution."""
         engines = list(self.ml.e.values())
         for e in engines:
             e.set_regulator(kb.KB_REG_U, lam)
@@ -107,13 +116,29 @@ class VertexFlow:
                 e.set_self_energy(sR, sK, self.A)
                 e.set_self_energy_derivative(None)
             e0 = self.ml.e[self.ml.channels[0]]
-            ds = e0.loop(S_GAMMA, self.sig_grid, single_scale=True)
+            d1 = e0.loop(S_GAMMA, self.sig_grid, single_scale=True)          # L(Γ, S)
+            ds = d1
+            for _ in range(self.sigma_iters if self.ml.keep_central else 1):
+                dRh, dKh = ds[:, 1, 0].cpu().numpy(), ds[:, 1, 1].cpu().numpy()
+                for e in engines:
+                    e.set_self_energy_derivative(dRh, dKh, self.A)
+                self.ml.zero()
+                self.ml.run_eager()
+                if not self.ml.keep_central:
+                    break
+                tb = e0.loop(s_central(self.ml.n_loops), self.sig_grid)           # L(γ̇^C_t̄, G)
+                e0.set_self_energy_derivative(tb[:, 1, 0].cpu().numpy(), tb[:, 1, 1].cpu().numpy(), self.A)
+                tt = e0.loop(S_GAMMA, self.sig_grid, line=2)                         # L(Γ, G Σ̇_t̄ G)
+                new = d1 + tb + tt
+                change = float((new - ds).abs().max()) / max(float(new.abs().max()), 1e-300)
+                ds = new
+                self.sigma_iterations += 1
+                if change <= self.sigma_tol:
+                    break
             dR, dK = ds[:, 1, 0], ds[:, 1, 1]
-            dRh, dKh = dR.cpu().numpy(), dK.cpu().numpy()
-            for e in engines:
-                e.set_self_energy_derivative(dRh, dKh, self.A)
-        self.ml.zero()
-        self.ml.run_eager()
+        else:
+            self.ml.zero()
+            self.ml.run_eager()
         self.rhs_calls += 1
         out = self._total()
         if self.n_sig:

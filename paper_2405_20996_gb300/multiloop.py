@@ -40,7 +40,11 @@ def _s_left(l, n_loops):       # L^(l), l = 2 .. n_loops - 1
     return 1 + n_loops + (l - 1)
 
 
-def step_entries(channels, n_loops, cached=None, image_r2=False):
+def s_central(n_loops):        # Σ_{l >= 3} C^(l), all channels (keep_central)
+    return max(2 * n_loops, n_loops + 2)
+
+
+def step_entries(channels, n_loops, cached=None, image_r2=False, keep_central=False):
     """The entries of one step, as plain tuples (host logic, no device):
     ("cache", r, slot, sides), ("bubble", r, left, right, out, pi_kind, beta),
     ("image", r, src, dst), ("add", r, src, dst), ("join",).  Per channel r: order 1 into
@@ -48,8 +52,13 @@ def step_entries(channels, n_loops, cached=None, image_r2=False):
     order), the central part from the previous order's left part (l >= 3), the right part,
     and the left part added; finally every order added into Γ̇.  image_r2: Γ is conjugation-
     and crossing-symmetric, so γ̇^(1) (from the symmetric one-loop bubble) is too, and the
-    second order's right part is the symmetry image of its left part (kb_vertex_image)."""
+    second order's right part is the symmetry image of its left part (kb_vertex_image).
+    keep_central: every central part C_r^(l) is also added into the slot s_central(n_loops)
+    (the multiloop self-energy flow's γ̇^C; zero it before the step); at the last order the
+    central part is then computed before the left part, so that it is alone in γ̇^(l) when
+    copied."""
     L, G, ent = n_loops, S_GAMMA, []
+    SC = s_central(L)
     cached = cached or {}
     for r in channels:
         if r in cached:
@@ -61,9 +70,16 @@ def step_entries(channels, n_loops, cached=None, image_r2=False):
         last = l == L
         for r in channels:
             lslot = out if last else _s_left(l, L)
-            ent.append(("bubble", r, prev, G, lslot, kb.KB_PI_GG, 0.0))                               # L
-            if l >= 3:
-                ent.append(("bubble", r, G, _s_left(l - 1, L), out, kb.KB_PI_GG, 1.0 if last else 0.0))   # C
+            if keep_central and last and l >= 3:
+                ent.append(("bubble", r, G, _s_left(l - 1, L), out, kb.KB_PI_GG, 0.0))               # C
+                ent.append(("add", r, out, SC))
+                ent.append(("bubble", r, prev, G, out, kb.KB_PI_GG, 1.0))                            # L
+            else:
+                ent.append(("bubble", r, prev, G, lslot, kb.KB_PI_GG, 0.0))                               # L
+                if l >= 3:
+                    ent.append(("bubble", r, G, _s_left(l - 1, L), out, kb.KB_PI_GG, 1.0 if last else 0.0))   # C
+                    if keep_central:
+                        ent.append(("add", r, out, SC))
             if image_r2 and l == 2 and not last:
                 ent.append(("image", r, lslot, out))                                                 # R = I_r[L]
             else:
@@ -78,7 +94,7 @@ def step_entries(channels, n_loops, cached=None, image_r2=False):
 
 class MultiloopStep:
     def __init__(self, grids, nq, U, Delta, T, vertex, n_loops=6, precision="mixed", A=5.0, device=0,
-                 symmetric=True, channels=(0, 1, 2), cache="auto", reserve_bytes=40 << 30):
+                 symmetric=True, channels=(0, 1, 2), cache="auto", reserve_bytes=40 << 30, keep_central=False):
         """vertex: {channel: (K1, K2, K2p, K3)} arrays of the reducible vertices γ_r (the bare
         part −U/2 is added by the library).  precision "mixed" keeps every vertex in complex64,
         "fp64" in complex128.  cache (mixed only): rebuild the record cache of Γ once per
@@ -87,6 +103,8 @@ class MultiloopStep:
         device memory less reserve_bytes; True: every side; False: none."""
         assert n_loops >= 1
         assert _s_left(n_loops - 1, n_loops) < kb.KB_MAX_SLOTS
+        assert not keep_central or s_central(n_loops) < kb.KB_MAX_SLOTS
+        self.keep_central = bool(keep_central)
         self.n_loops, self.precision = n_loops, precision
         self.channels = tuple(channels)
         dt = torch.complex64 if precision == "mixed" else torch.complex128
@@ -107,9 +125,14 @@ class MultiloopStep:
         self.orders = [z() for _ in range(n_loops)]
         self.lefts = {l: {r: {k: torch.zeros(sh[CLASS_NAMES[k]], dtype=dt, device=dev) for k in range(4)}
                           for r in self.channels} for l in range(2, n_loops)}
+        # Σ_{l >= 3} C^(l) of all channels: read by the self-energy loop as γ̇^C_t̄ (channels a and
+        # p; the t data enters only as the up-up crossing partner)
+        self.central = z() if self.keep_central else None
         for r, e in self.e.items():
             others = 7 & ~(1 << r)
             self._attach(e, S_TOTAL, self.total, 7)
+            if self.keep_central:
+                self._attach(e, s_central(n_loops), self.central, (1 << 0) | (1 << 1))
             for l in range(1, n_loops + 1):
                 self._attach(e, _s_order(l), self.orders[l - 1], others)
             for l in range(2, n_loops):
@@ -157,7 +180,8 @@ class MultiloopStep:
     def _descs(self):
         """The step as a list of graph entries (bubbles, slot additions, joins)."""
         d = []
-        for x in step_entries(self.channels, self.n_loops, self.cached, image_r2=self.image_r2):
+        for x in step_entries(self.channels, self.n_loops, self.cached, image_r2=self.image_r2,
+                              keep_central=self.keep_central):
             if x[0] == "join":
                 d.append(kb.kb_join_desc())
                 continue
@@ -184,6 +208,9 @@ class MultiloopStep:
     def zero(self):
         for t in self.total.values():
             t.zero_()
+        if self.central is not None:
+            for t in self.central.values():
+                t.zero_()
 
     def build(self):
         self.graph = StepGraph(self.descs)

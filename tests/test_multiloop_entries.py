@@ -6,14 +6,15 @@ contents, build exactly the loop-order recursion of the multiloop flow (Sec. III
 
 with γ̇_r̄ the channels other than r (the slot's channel mask), Γ̇ = Σ_l γ̇^(l); every slot is
 written before it is read within a branch, and no branch reads another channel's result of
-the same order before the join."""
+the same order before the join.  With keep_central the central parts C_r^(l) (l >= 3)
+are also collected, alone, in their own slot (the multiloop self-energy flow's γ̇^C)."""
 
 import collections
 
 import pytest
 
 from paper_2405_20996_gb300 import kb
-from paper_2405_20996_gb300.multiloop import S_GAMMA, S_TOTAL, step_entries
+from paper_2405_20996_gb300.multiloop import S_GAMMA, S_TOTAL, s_central, step_entries
 
 
 def _expected(channels, n_loops):
@@ -33,14 +34,14 @@ def _expected(channels, n_loops):
     return order
 
 
-def _replay(channels, n_loops, image_r2=False):
+def _replay(channels, n_loops, image_r2=False, keep_central=False):
     """Apply the entries to slots holding sums of symbolic terms; the vertex a bubble reads
     from an order slot is named by its order and the channel left out (the mask)."""
     slots = collections.defaultdict(list)      # (slot, channel) -> list of terms
     name_of_order = {1 + l: l for l in range(1, n_loops + 1)}
     joined_upto = 1                            # orders complete in all channels
     written = set()
-    for x in step_entries(channels, n_loops, image_r2=image_r2):
+    for x in step_entries(channels, n_loops, image_r2=image_r2, keep_central=keep_central):
         if x[0] == "join":
             joined_upto += 1
             continue
@@ -113,3 +114,25 @@ def test_slot_budget_and_cache_entries():
     for r in (0, 2):
         first_bubble = next(i for i, x in enumerate(ent) if x[0] == "bubble" and x[1] == r)
         assert next(i for i, x in enumerate(ent) if x[0] == "cache" and x[1] == r) < first_bubble
+
+
+@pytest.mark.parametrize("image_r2", [False, True])
+@pytest.mark.parametrize("n_loops", [2, 3, 4, 6])
+def test_entries_keep_the_central_parts(n_loops, image_r2):
+    ch = (0, 1, 2)
+    slots = _replay(ch, n_loops, image_r2, keep_central=True)
+    exp = _expected(ch, n_loops)
+    for l in range(1, n_loops + 1):
+        for r in ch:
+            assert tuple(sorted(slots[(1 + l, r)])) == exp[(l, r)], (l, r)
+    left = {}
+    for l in range(2, n_loops + 1):
+        for r in ch:
+            left[(l, r)] = "B%d(o%d!%d|G;GG)" % (r, l - 1, r)
+    sc = s_central(n_loops)
+    assert sc < kb.KB_MAX_SLOTS
+    for r in ch:
+        central = sorted("B%d(G|%s;GG)" % (r, left[(l - 1, r)]) for l in range(3, n_loops + 1))
+        assert sorted(slots[(sc, r)]) == central, r
+    used = {s for x in step_entries(ch, n_loops, image_r2=image_r2) if x[0] == "bubble" for s in x[2:5]}
+    assert sc not in used
