@@ -1,0 +1,30 @@
+"""The oracle's multiloop flow driver (oracle/oracle_flow.py) against its parquet solution,
+on tiny grids (CPU): integrated from L ≈ 0 to 1 in the interaction flow, with Σ flowing and
+the multiloop self-energy terms, the six-loop flow's vertex lands within 2 % of the parquet
+approximation's (with the Schwinger–Dyson self-energy), four times closer than the one-loop
+flow's — the multiloop flow approaching the parquet solution (Sec. III.C).  The self-energy
+of the two routes differs by the grids' discretisation here (a few per cent at these sizes)."""
+
+import numpy as np
+
+from oracle import oracle_flow as F
+
+G = dict(n1=13, n2w=7, n2v=6, n3w=5, n3v=4)
+
+
+def _flat(gam):
+    return np.concatenate([gam[c][k].ravel() for c in range(3) for k in range(4)])
+
+
+def test_multiloop_flow_approaches_the_parquet_solution():
+    nq, U, D, T = 41, 1.0, 1.0, 0.2
+    nus = F.sig_grid(15)
+    gp, sRp, _ = F.parquet_sde(G, nq, U, D, T, nus, tol=1e-11)
+    ref = _flat(gp)
+    dev = {}
+    for n in (1, 6):
+        gf, sRf, sKf = F.mfrg_flow(G, nq, U, D, T, n, nus, steps=6)
+        dev[n] = np.abs(_flat(gf) - ref).max() / np.abs(ref).max()
+        assert np.abs(sRf - sRp).max() <= 0.1 * np.abs(sRp).max()
+        assert (sRf.imag <= 1e-12).all()
+    assert dev[6] <= 0.02 and dev[6] <= 0.25 * dev[1], dev
