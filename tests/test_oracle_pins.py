@@ -439,3 +439,34 @@ def test_multiloop_left_part_has_no_k1_k2p(r):
     # right correction Gamma o Pi o gamma-dot_rbar: no K1 and no K2
     B = O.bubble_all(V, Vd, P, r, 101)
     assert np.abs(B["K1"]).max() == 0.0 and np.abs(B["K2"]).max() == 0.0
+
+
+def test_third_order_k1_is_the_ladder_of_a_repulsive_coupling():
+    """K1 of the parquet solution at w = 0 to third order in U (a fit over three small
+    couplings): the third-order term is the ladder R Pi K1^(2) with R = -U/2, so its ratio to
+    the second-order term is -Pi_r(0)/2 with the textbook bubbles (particle-hole for a,
+    particle-particle for p) — the transverse-spin channel enhanced and the pairing channel
+    suppressed, as a repulsive U requires.  The ratio is odd in the bare vertex's sign, so
+    this pins that sign (C2) through the vertex alone."""
+    CLS = ("K1", "K2", "K2p", "K3")
+    g = dict(n1=21, n2w=7, n2v=6, n3w=5, n3v=4)
+    nq, D, T = 81, 1.0, 0.2
+    P = O.Prop(Delta=D, T=T)
+
+    def parquet(U, iters=40, mix=0.7):
+        gam = {c: [np.zeros(O.class_shape(g, k), dtype=np.complex128) for k in CLS] for c in range(3)}
+        for _ in range(iters):
+            Gam = O.Vertex(g, U=U, has_R=True, channels=gam)
+            new = {r: O.bubble_all(O.Vertex(g, U=U, has_R=True, channels=gam,
+                                            include=[c for c in range(3) if c != r]), Gam, P, r, nq)
+                   for r in range(3)}
+            gam = {c: [(1 - mix) * gam[c][k] + mix * new[c][CLS[k]] for k in range(4)] for c in range(3)}
+        return gam
+
+    Us = np.array([0.025, 0.05, 0.1])
+    w0 = g["n1"] // 2
+    sols = [parquet(U) for U in Us]
+    for r, pi in ((0, pi_R_ph(0.0, D, T)), (1, pi_R_pp(0.0, D, T))):
+        vals = np.array([s[r][0][w0][1].real / U ** 2 for s, U in zip(sols, Us)])   # component (c c|c q)
+        c4, c3, c2 = np.polyfit(Us, vals, 2)
+        assert abs(c3 / c2 / (-pi.real / 2) - 1) <= 2e-3, (r, c3 / c2, -pi.real / 2)
