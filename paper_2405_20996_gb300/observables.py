@@ -14,8 +14,14 @@ static-limit-positive bare susceptibilities:
     pairing (p channel, up-down):          χ_pair(ω) = +2 K1_p(ω) / U²   (χ0 = +Π_pp/2),
 
 so that their third order is the ladder χ = χ0 + U χ0² (spin, enhanced by a repulsive U) and
-χ = χ0 − U χ0² (pairing, suppressed).  The charge and longitudinal-spin combinations of the
-t channel (the companion paper's Eqs. C8) are not built.
+χ = χ0 − U χ0² (pairing, suppressed).
+
+Charge (t channel): the density response sums both spins of the t-channel pair,
+χ_c(ω) = 2 [K1_t^↑↓(ω) + K1_t^↑↑(ω)] / U², with the up-up part from crossing,
+K1_t^↑↑(ω) = K1_t^↑↓(ω) − K1_a^↑↓(−ω) (Keldysh indices a1 <-> a2), in the t channel's 4×4 form
+(rows (a1', a1), columns (a2', a2)) whose (even, odd) block is the retarded one; at second
+order χ_c = χ0 = −Π_ph/2, at third order the ladder χ0 − U χ0² (suppressed).  (The
+longitudinal spin combination K1_t^↑↑ − K1_t^↑↓ is the a channel's by that same crossing.)
 """
 
 import numpy as np
@@ -36,3 +42,18 @@ def susceptibility_from_K1(K1, channel, U):
     c = _COMP[channel]
     f = _SCALE[channel] / (U * U)
     return f * K1[:, c["R"]], f * K1[:, c["K"]]
+
+
+_T_COMP = {"R": 1, "K": 3}
+_SWAP12 = [(c & 12) | ((c & 1) << 1) | ((c >> 1) & 1) for c in range(16)]
+
+
+def charge_susceptibility_from_K1(K1_t, K1_a, U):
+    """χ_c^R(ω), χ_c^K(ω) from the t and a channels' K1 arrays [n1][16] on the same
+    (symmetric) bosonic grid, at coupling U."""
+    if U == 0:
+        raise ValueError("U = 0: K1 vanishes")
+    upup = K1_t - K1_a.flip(0)[:, _SWAP12] if hasattr(K1_a, "flip") else K1_t - K1_a[::-1][:, _SWAP12]
+    tot = K1_t + upup
+    f = 2.0 / (U * U)
+    return f * tot[:, _T_COMP["R"]], f * tot[:, _T_COMP["K"]]

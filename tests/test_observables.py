@@ -1,13 +1,13 @@
-"""Susceptibilities from K1 (observables.susceptibility_from_K1), on the oracle's vertices
-(CPU): at second order they are the textbook bare bubbles (χ_± = −Π_ph/2, χ_pair = Π_pp/2)
-with the bosonic FDR; at first order in U they are the ladders χ0 ± U χ0² (transverse spin
-enhanced, pairing suppressed by a repulsive U)."""
+"""Susceptibilities from K1 (observables), on the oracle's vertices (CPU): at second order
+they are the textbook bare bubbles (χ_± = χ_c = −Π_ph/2, χ_pair = Π_pp/2) with the bosonic
+FDR; at first order in U they are the ladders χ0 ± U χ0² (transverse spin enhanced, pairing
+and charge suppressed by a repulsive U)."""
 
 import numpy as np
 import pytest
 
 from oracle import oracle as O
-from paper_2405_20996_gb300.observables import susceptibility_from_K1
+from paper_2405_20996_gb300.observables import charge_susceptibility_from_K1, susceptibility_from_K1
 from test_oracle_pins import pi_R_ph, pi_R_pp
 
 CLS = ("K1", "K2", "K2p", "K3")
@@ -27,6 +27,12 @@ def test_second_order_is_the_bare_bubble_with_the_fdr():
             # bosonic FDR: chi^K = coth(w/2T) (chi^R - chi^A), chi^A = (chi^R)*
             assert abs(np.tanh(w[i] / (2 * T)) * chiK[i] - (chiR[i] - np.conj(chiR[i]))) <= 1e-9 * abs(ref)
         assert chiR[15].real > 0                                   # static limit positive
+    Ka = O.bubble_class(V, V, P, 0, "K1", 1001)
+    chiR, chiK = charge_susceptibility_from_K1(O.bubble_class(V, V, P, 2, "K1", 1001), Ka, U)
+    for i in (4, 11, 15, 20, 27):
+        ref = -pi_R_ph(w[i], D, T) / 2
+        assert abs(chiR[i] - ref) <= 1e-9 * abs(ref), (w[i], chiR[i], ref)
+        assert abs(np.tanh(w[i] / (2 * T)) * chiK[i] - (chiR[i] - np.conj(chiR[i]))) <= 1e-9 * abs(ref)
 
 
 def test_first_order_is_the_ladder():
@@ -47,8 +53,12 @@ def test_first_order_is_the_ladder():
     Us = np.array([0.025, 0.05, 0.1])
     w0 = g["n1"] // 2
     sols = [parquet(U) for U in Us]
-    for r, sign, chi0 in ((0, 1.0, -pi_R_ph(0.0, D, T).real / 2), (1, -1.0, pi_R_pp(0.0, D, T).real / 2)):
-        chi = np.array([susceptibility_from_K1(s[r][0], r, U)[0][w0].real for s, U in zip(sols, Us)])
+    cases = [(lambda s, U, r=r: susceptibility_from_K1(s[r][0], r, U)[0][w0].real, sign, chi0)
+             for r, sign, chi0 in ((0, 1.0, -pi_R_ph(0.0, D, T).real / 2), (1, -1.0, pi_R_pp(0.0, D, T).real / 2))]
+    cases.append((lambda s, U: charge_susceptibility_from_K1(s[2][0], s[0][0], U)[0][w0].real, -1.0,
+                  -pi_R_ph(0.0, D, T).real / 2))
+    for r, (get, sign, chi0) in enumerate(cases):
+        chi = np.array([get(s, U) for s, U in zip(sols, Us)])
         c2, c1, c0 = np.polyfit(Us, chi, 2)
         assert abs(c0 / chi0 - 1) <= 1e-3, (r, c0, chi0)
         assert abs(c1 / (sign * chi0 ** 2) - 1) <= 2e-3, (r, c1, sign * chi0 ** 2)
