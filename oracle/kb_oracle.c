@@ -996,7 +996,7 @@ static void class_edge(const ovtx *V, int ch, int k, int axis, int side, double 
 /* D_+- of Gamma_s = 2 Gamma_ud(v, v'|v, v') - Gamma_ud(v, v'|v', v) at v' -> side * inf
  * (the exchanged term with Keldysh indices (a1' a2'|a2 a1); each channel's exchanged term
  * comes from its crossing partner's data, a <-> t, p -> p, as for the up-up vertex). */
-static void loop_edge(const ovtx *V, double nu, int side, cplx E[16]) {
+static void loop_edge(const ovtx *V, double nu, int side, int ud_only, cplx E[16]) {
     cplx ud[16], ex[16];
     memset(ud, 0, sizeof(ud));
     memset(ex, 0, sizeof(ex));
@@ -1016,7 +1016,7 @@ static void loop_edge(const ovtx *V, double nu, int side, cplx E[16]) {
     if ((V->mask >> 1) & 1) class_edge(V, 1, 0, 0, side, 0.0, 0.0, 0.0, 1.0, ex);    /* K1_p(v + v') */
     for (int c = 0; c < 16; ++c) {
         int b1p = (c >> 3) & 1, b2p = (c >> 2) & 1, b1 = (c >> 1) & 1, b2 = c & 1;
-        E[c] = 2.0 * ud[c] - ex[kidx(b1p, b2p, b2, b1)];
+        E[c] = ud_only ? ud[c] : 2.0 * ud[c] - ex[kidx(b1p, b2p, b2, b1)];
     }
 }
 
@@ -1031,18 +1031,29 @@ static void loop_contract(const cplx G[16], cplx P[2][2], cplx f, cplx S[2][2]) 
         }
 }
 
-/* Gamma_s = Gamma_ud + Gamma_uu of the right-vertex selection sel at t-variables (0, v, v') */
-static void loop_vertex(const ovtx *V, int sel, double nu, double nup, cplx G[16]) {
+/* Gamma_s = Gamma_ud + Gamma_uu (or Gamma_ud alone) of the right-vertex selection sel at
+ * t-variables (0, v, v') */
+static void loop_vertex(const ovtx *V, int sel, double nu, double nup, int ud_only, cplx G[16]) {
     cplx a[16], b[16];
     vertex_select(V, 2, 0, 1, sel, 0.0, nu, nup, a);
+    if (ud_only) { for (int c = 0; c < 16; ++c) G[c] = a[c]; return; }
     vertex_select(V, 2, 1, 1, sel, 0.0, nu, nup, b);
     for (int c = 0; c < 16; ++c) G[c] = a[c] + b[c];
 }
 
 /* Public: Sigma at npts frequencies nus with P = G (which 0), S (which 1) or G dSigma G (which 2);
  * out[4 i + 2 a1' + a1] (0 classical, 1 quantum). */
+int og_loop_spin(const ovtx *V, const oprop *P, int which, int ud_only, int Nq, int npts, const double *nus,
+                 cplx *out, int nthreads);
 int og_loop(const ovtx *V, const oprop *P, int which, int Nq, int npts, const double *nus, cplx *out,
             int nthreads) {
+    return og_loop_spin(V, P, which, 0, Nq, npts, nus, out, nthreads);
+}
+
+/* The loop with the up-down vertex alone when ud_only (the closed line carrying the spin
+ * opposite to the external one, as in the Schwinger-Dyson equation's bubble forms). */
+int og_loop_spin(const ovtx *V, const oprop *P, int which, int ud_only, int Nq, int npts, const double *nus,
+                 cplx *out, int nthreads) {
     if (Nq < 5 || (Nq - 1) % 4 || which < 0 || which > 2) return -1;
     double *xq = malloc(sizeof(double) * Nq), *wq = malloc(sizeof(double) * Nq);
     if (!xq || !wq) { free(xq); free(wq); return -2; }
@@ -1069,18 +1080,18 @@ int og_loop(const ovtx *V, const oprop *P, int which, int Nq, int npts, const do
     for (int i = 0; i < npts; ++i) {
         const double nu = nus[i];
         cplx S[2][2] = {{0, 0}, {0, 0}}, Cv[16], E[16];
-        loop_vertex(V, SEL_ZERO, nu, 0.0, Cv);
+        loop_vertex(V, SEL_ZERO, nu, 0.0, ud_only, Cv);
         loop_contract(Cv, IP, 1.0, S);
         for (int j = 1; j < Nq - 1; ++j) {
             double tn = tan(PI * xq[j] / 2), nup = A * tn, jac = A * PI / 2 * (1.0 + tn * tn);
             cplx G[2][2], D[16];
             prop_matrix(P, which, nup, G);
-            loop_vertex(V, SEL_NU, nu, nup, D);
+            loop_vertex(V, SEL_NU, nu, nup, ud_only, D);
             loop_contract(D, G, wq[j] * jac, S);
         }
-        loop_edge(V, nu, +1, E);
+        loop_edge(V, nu, +1, ud_only, E);
         loop_contract(E, M, wq[Nq - 1], S);
-        loop_edge(V, nu, -1, E);
+        loop_edge(V, nu, -1, ud_only, E);
         loop_contract(E, M, -wq[0], S);
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b) out[(size_t)4 * i + 2 * a + b] = -S[a][b] / (2.0 * PI * I);
@@ -1100,7 +1111,7 @@ int og_loop_pieces(const ovtx *V, const oprop *P, int which, double nu, double x
     cplx G[2][2], M[2][2], D[16];
     prop_matrix(P, which, nup, G);
     prop_asym(P, which, M);
-    loop_vertex(V, SEL_NU, nu, nup, D);
+    loop_vertex(V, SEL_NU, nu, nup, 0, D);
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) {
             out[2 * a + b] = jac * (G[a][b] - M[a][b] * nup / (nup * nup + A * A));
@@ -1117,7 +1128,7 @@ int og_loop_limits(const ovtx *V, const oprop *P, int which, double nu, int side
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b) out[2 * a + b] = N[a][b] * (PI / (2.0 * V->A));
     memset(E, 0, sizeof(E));
-    loop_edge(V, nu, side, E);
+    loop_edge(V, nu, side, 0, E);
     for (int c = 0; c < 16; ++c) out[4 + c] = E[c];
     return 0;
 }

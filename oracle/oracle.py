@@ -50,6 +50,7 @@ def lib():
             L.og_bubble_points.restype = C.c_int
             L.og_bubble_points_adaptive.restype = C.c_int
             L.og_loop.restype = C.c_int
+            L.og_loop_spin.restype = C.c_int
             _lib = L
     return _lib
 
@@ -283,15 +284,16 @@ def prop_eval(P, which, v):
     return out
 
 
-def loop(V, P, Nq, nus, nthreads=0, which=0):
+def loop(V, P, Nq, nus, nthreads=0, which=0, ud_only=False):
     """Self-energy loop Sigma^{a1'|a1}(v) = -int dv'/(2 pi i) sum Gamma_s^{a1' a2'|a1 a2}(v, v'|v, v')
     P^{a2|a2'}(v') with Gamma_s = Gamma_ud + Gamma_uu (Sec. II.D.2; readings in kb_oracle.c),
     P = G (which 0), the flow scheme's single-scale propagator S (which 1), or the line with one
-    insertion of the dSigma tables, G dSigma G (which 2).
+    insertion of the dSigma tables, G dSigma G (which 2); ud_only: the up-down vertex alone.
     Returns (n, 2, 2) complex: [a1'][a1], 0 = classical, 1 = quantum."""
     nus = np.ascontiguousarray(nus, dtype=np.float64)
     out = np.zeros((len(nus), 2, 2), dtype=np.complex128)
-    rc = lib().og_loop(V.ptr(), P.ptr(), C.c_int(which), C.c_int(Nq), C.c_int(len(nus)), _dptr(nus),
+    rc = lib().og_loop_spin(V.ptr(), P.ptr(), C.c_int(which), C.c_int(int(bool(ud_only))), C.c_int(Nq),
+                            C.c_int(len(nus)), _dptr(nus),
                        out.ctypes.data_as(C.c_void_p), C.c_int(nthreads))
     if rc != 0:
         raise RuntimeError("og_loop failed: %d" % rc)

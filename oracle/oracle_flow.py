@@ -14,8 +14,8 @@ derivative are iterated together because Ġ contains Σ̇.  Integrated by the cl
 fourth-order Runge-Kutta rule with fixed steps.
 
 Parquet approximation with the Schwinger-Dyson equation (Sec. III.B): γ_r = B_r(I_r, Γ),
-Σ = U L(R̂, G) + ½ U L(X̂, G), X̂ = B_a(R̂, Γ) in a vertex holding channel a alone, at
-G = G[Σ] (L = 1), by the damped iteration.
+Σ = U L(R̂, G) + U L_ud(B_r(R̂, Γ), G) in its a- or p-channel form (L_ud the loop of the up-down
+vertex alone; the two forms, or their mean), at G = G[Σ] (L = 1), by the damped iteration.
 """
 
 import numpy as np
@@ -109,8 +109,9 @@ def mfrg_flow(grids, nq, U, D, T, n_loops, nus, lam0=1e-3, steps=20, A=5.0, mult
     return gam, sR, sK
 
 
-def parquet_sde(grids, nq, U, D, T, nus, mix=0.5, tol=1e-12, maxit=400, A=5.0):
-    """(γ, Σ^R, Σ^K) of the parquet approximation with the Schwinger-Dyson self-energy."""
+def parquet_sde(grids, nq, U, D, T, nus, mix=0.5, tol=1e-12, maxit=400, A=5.0, form="a"):
+    """(γ, Σ^R, Σ^K) of the parquet approximation with the Schwinger-Dyson self-energy in
+    its a-channel form, p-channel form, or the mean of the two (form "a", "p", "ap")."""
     n = len(nus)
     gam, sR, sK = _zero(grids), np.zeros(n, complex), np.zeros(n, complex)
     Rh = O.Vertex(grids, U=1.0, has_R=True)
@@ -121,8 +122,12 @@ def parquet_sde(grids, nq, U, D, T, nus, mix=0.5, tol=1e-12, maxit=400, A=5.0):
         for r in range(3):
             I_r = _vertex(grids, U, True, gam, include=[c for c in range(3) if c != r])
             new[r] = _classes(O.bubble_all(I_r, Gam, P, r, nq))
-        X = _classes(O.bubble_all(Rh, Gam, P, 0, nq))
-        s = U * (O.loop(Rh, P, nq, nus) + 0.5 * O.loop(O.Vertex(grids, channels={0: tuple(X)}, include=(0,)), P, nq, nus))
+        s = U * O.loop(Rh, P, nq, nus)
+        forms = {"a": (0,), "p": (1,), "ap": (0, 1)}[form]
+        for r in forms:
+            X = _classes(O.bubble_all(Rh, Gam, P, r, nq))
+            Vx = O.Vertex(grids, channels={r: tuple(X)}, include=(r,))
+            s = s + U / len(forms) * O.loop(Vx, P, nq, nus, ud_only=True)
         scale = max(max(np.abs(new[c][k]).max() for c in range(3) for k in range(4)), np.abs(s).max())
         change = max(max(np.abs(new[c][k] - gam[c][k]).max() for c in range(3) for k in range(4)),
                      np.abs(s[:, 1, 0] - sR).max(), np.abs(s[:, 1, 1] - sK).max()) / scale

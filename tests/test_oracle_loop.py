@@ -225,3 +225,23 @@ def test_line_with_a_self_energy_insertion_is_the_derivative_along_dsigma():
     S = O.loop(V, P, 401, nus, which=2)
     fdl = (O.loop(V, at(h), 401, nus) - O.loop(V, at(-h), 401, nus)) / (2 * h)
     assert np.abs(S - fdl).max() <= 1e-6 * np.abs(S).max(), np.abs(S - fdl).max() / np.abs(S).max()
+
+
+def test_up_down_loop_and_the_sde_forms_at_second_order():
+    """The loop of the up-down vertex alone: for a vertex holding channel a only (no crossing
+    partner data) it is half the spin-summed loop (the identity the a-channel SDE form uses);
+    at second order both the a- and the p-channel bubble closed this way are Σ2, against the
+    textbook spectral integral (the SDE's a and p forms, with the same coefficient)."""
+    U, T, D = 1.0, 0.1, 1.0
+    g = dict(n1=201, n2w=3, n2v=3, n3w=3, n3v=3)
+    P = O.Prop(Delta=D, T=T)
+    V0 = O.Vertex(g, U=U, has_R=True)
+    nus = np.array([0.5, 1.0])
+    ref = _sigma2_spectral(nus, U, T, D)
+    for r, coef in ((0, 1.0), (1, 1.0)):
+        K1 = O.bubble_all(V0, V0, P, r, 801, classes=("K1",))["K1"]
+        X = O.Vertex(g, channels={r: (K1, None, None, None)}, include=(r,))
+        ud = O.loop(X, P, 801, nus, ud_only=True)
+        if r == 0:
+            assert np.abs(ud - O.loop(X, P, 801, nus) / 2).max() <= 1e-14 * np.abs(ud).max()
+        assert np.abs(coef * ud[:, 1, 0].imag - ref).max() <= 3e-3 * np.abs(ref).max(), (r, coef * ud[:, 1, 0].imag, ref)
