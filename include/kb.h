@@ -286,7 +286,9 @@ kb_status kb_vertex_eval(kb_ctx *ctx, int slot, int channel, int spin_uu, int n,
  * P = S, the single-scale propagator of the flow scheme (kb_set_regulator, with the
  * Katanin substitution when set), the one-loop term of the self-energy flow; which = 2:
  * P = G dSigma G, one insertion of the kb_set_self_energy_derivative tables (zero without
- * them), the line of the multiloop self-energy flow's t term —
+ * them), the line of the multiloop self-energy flow's t term; or-ed with KB_LOOP_UD_ONLY:
+ * the up-down vertex alone (Gamma_s = Gamma_up-down, the Schwinger-Dyson equation's bubble
+ * forms) —
  *   Sigma^{a1'|a1}(v) = - int dv'/(2 pi i) sum_{a2', a2} Gamma_s^{a1' a2'|a1 a2}(v, v'|v, v')
  *                          P^{a2|a2'}(v'),   Gamma_s = Gamma_up-down + Gamma_up-up,
  * with the vertex read in t-channel variables (w_t = 0, v, v') and the internal line's
@@ -298,6 +300,7 @@ kb_status kb_vertex_eval(kb_ctx *ctx, int slot, int channel, int spin_uu, int n,
  * [n][2][2] indexed [a1'][a1] (0 classical, 1 quantum): (1,0) = Sigma^R, (0,1) = Sigma^A,
  * (1,1) = Sigma^K, (0,0) = 0 for a causal result.  Plain FP64.  Requires the grids, the
  * model and the slot.  Asynchronous on `stream`. */
+enum { KB_LOOP_UD_ONLY = 4 };   /* or-ed into `which`: the up-down vertex alone (Gamma_s = Gamma_up-down) */
 kb_status kb_loop(kb_ctx *ctx, int slot, int which, int n, const double *nus, void *out, void *stream);
 
 /* Autotuning of the tensor-core K3 contraction (default off): with `on`, the first

@@ -83,26 +83,30 @@ __device__ void acc_class_edge(const VertexDev& V, const Grids& G, int c, int k,
     }
 }
 
-// D_+- of Gamma_s = 2 Gamma_ud(v, v'|v, v') - Gamma_ud(v, v'|v', v) at v' -> side * inf; each
-// channel's exchanged term comes from its crossing partner's data (a <-> t, p -> p).
-// Direct legs: t (0, v, v'), a (v - v', ...), p (v + v', ...); exchanged legs: t (v' - v, ...),
-// a (0, v, v'), p (v + v', ...).
+// D_+- of Gamma_s = 2 Gamma_ud(v, v'|v, v') - Gamma_ud(v, v'|v', v) at v' -> side * inf (of
+// Gamma_ud alone when UD_ONLY); each channel's exchanged term comes from its crossing
+// partner's data (a <-> t, p -> p).  Direct legs: t (0, v, v'), a (v - v', ...), p (v + v', ...);
+// exchanged legs: t (v' - v, ...), a (0, v, v'), p (v + v', ...).
+template <bool UD_ONLY>
 __device__ void loop_edge(const VertexDev& V, const Grids& G, double nu, int side, double2 E[16]) {
+    constexpr double fd = UD_ONLY ? 1.0 : 2.0;
 #pragma unroll
     for (int o = 0; o < 16; ++o) E[o] = make_double2(0.0, 0.0);
     if ((V.mask >> KB_CH_T) & 1) {
-        acc_class_edge(V, G, KB_CH_T, 2, 2, side, 0.0, nu, 2.0, false, E);    // K2'_t(0, v')
-        acc_class_edge(V, G, KB_CH_T, 3, 2, side, 0.0, nu, 2.0, false, E);    // K3_t(0, v, v')
-        acc_class_edge(V, G, KB_CH_A, 2, 2, side, 0.0, nu, -1.0, true, E);    // K2'_a(0, v'), exchanged
-        acc_class_edge(V, G, KB_CH_A, 3, 2, side, 0.0, nu, -1.0, true, E);    // K3_a(0, v, v'), exchanged
+        acc_class_edge(V, G, KB_CH_T, 2, 2, side, 0.0, nu, fd, false, E);     // K2'_t(0, v')
+        acc_class_edge(V, G, KB_CH_T, 3, 2, side, 0.0, nu, fd, false, E);     // K3_t(0, v, v')
+        if (!UD_ONLY) {
+            acc_class_edge(V, G, KB_CH_A, 2, 2, side, 0.0, nu, -1.0, true, E);    // K2'_a(0, v'), exchanged
+            acc_class_edge(V, G, KB_CH_A, 3, 2, side, 0.0, nu, -1.0, true, E);    // K3_a(0, v, v'), exchanged
+        }
     }
     if ((V.mask >> KB_CH_A) & 1) {
-        acc_class_edge(V, G, KB_CH_A, 0, 0, -side, 0.0, 0.0, 2.0, false, E);  // K1_a(v - v')
-        acc_class_edge(V, G, KB_CH_T, 0, 0, side, 0.0, 0.0, -1.0, true, E);   // K1_t(v' - v), exchanged
+        acc_class_edge(V, G, KB_CH_A, 0, 0, -side, 0.0, 0.0, fd, false, E);   // K1_a(v - v')
+        if (!UD_ONLY) acc_class_edge(V, G, KB_CH_T, 0, 0, side, 0.0, 0.0, -1.0, true, E);   // K1_t(v' - v), exchanged
     }
     if ((V.mask >> KB_CH_P) & 1) {
-        acc_class_edge(V, G, KB_CH_P, 0, 0, side, 0.0, 0.0, 2.0, false, E);   // K1_p(v + v')
-        acc_class_edge(V, G, KB_CH_P, 0, 0, side, 0.0, 0.0, -1.0, true, E);   // K1_p(v + v'), exchanged
+        acc_class_edge(V, G, KB_CH_P, 0, 0, side, 0.0, 0.0, fd, false, E);    // K1_p(v + v')
+        if (!UD_ONLY) acc_class_edge(V, G, KB_CH_P, 0, 0, side, 0.0, 0.0, -1.0, true, E);   // K1_p(v + v'), exchanged
     }
 }
 
@@ -169,7 +173,10 @@ __device__ void line_with_insertion(const Model& m, double v, double2 P[2][2]) {
     P[1][1] = make_double2(0, 0);
 }
 
-// One block per output frequency; threads stride over the interior nodes 1 .. nq-2.
+// One block per output frequency; threads stride over the interior nodes 1 .. nq-2.  UD_ONLY:
+// the up-down vertex alone (the closed line carries the spin opposite to the external one, as
+// in the Schwinger-Dyson equation's bubble forms).
+template <bool UD_ONLY>
 __global__ void __launch_bounds__(LOOP_THREADS) k_loop(VertexDev V, Grids G, Model m, int which, int n,
                                                        const double* __restrict__ nus,
                                                        const double* __restrict__ xq,
@@ -196,8 +203,10 @@ __global__ void __launch_bounds__(LOOP_THREADS) k_loop(VertexDev V, Grids G, Mod
         double2 Dv[16];
         vertex_part_f64(V, G, KB_CH_T, false, true, true, 0.0, nu, nup, Dv);    // up-down
         loop_contract(Dv, P, f, acc);
-        vertex_part_f64(V, G, KB_CH_T, true, true, true, 0.0, nu, nup, Dv);     // up-up
-        loop_contract(Dv, P, f, acc);
+        if (!UD_ONLY) {
+            vertex_part_f64(V, G, KB_CH_T, true, true, true, 0.0, nu, nup, Dv);     // up-up
+            loop_contract(Dv, P, f, acc);
+        }
     }
     // block reduction: warp shuffles, then one slot per warp in shared memory
     __shared__ double2 red[LOOP_THREADS / 32][8];
@@ -228,15 +237,17 @@ __global__ void __launch_bounds__(LOOP_THREADS) k_loop(VertexDev V, Grids G, Mod
     double2 Cv[16];
     vertex_part_f64(V, G, KB_CH_T, false, true, false, 0.0, nu, 0.0, Cv);
     loop_contract(Cv, IG, 1.0, S);
-    vertex_part_f64(V, G, KB_CH_T, true, true, false, 0.0, nu, 0.0, Cv);
-    loop_contract(Cv, IG, 1.0, S);
+    if (!UD_ONLY) {
+        vertex_part_f64(V, G, KB_CH_T, true, true, false, 0.0, nu, 0.0, Cv);
+        loop_contract(Cv, IG, 1.0, S);
+    }
     // end nodes of int D P: +-M D_+-
     double2 Mm[2][2] = {{make_double2(0.0, 0.0), make_double2(tl.mm, 0.0)},
                         {make_double2(tl.mm, 0.0), make_double2(0.0, 0.0)}};
     double2 E[16];
-    loop_edge(V, G, nu, +1, E);
+    loop_edge<UD_ONLY>(V, G, nu, +1, E);
     loop_contract(E, Mm, wq[nq - 1], S);
-    loop_edge(V, G, nu, -1, E);
+    loop_edge<UD_ONLY>(V, G, nu, -1, E);
     loop_contract(E, Mm, -wq[0], S);
     // Sigma = -S / (2 pi i) = i S / (2 pi)
     const double s = 1.0 / (2.0 * KB_PI);
@@ -276,7 +287,10 @@ extern "C" kb_status kb_vertex_eval(kb_ctx* ctx, int slot, int channel, int spin
 extern "C" kb_status kb_loop(kb_ctx* ctx, int slot, int which, int n, const double* nus, void* out,
                              void* stream) {
     if (!ctx) return KB_ERR_ARG;
-    if (slot < 0 || slot >= KB_MAX_SLOTS || which < 0 || which > 2 || n < 0 || (n > 0 && (!nus || !out))) {
+    const int line = which & 3;
+    const bool ud_only = (which & KB_LOOP_UD_ONLY) != 0;
+    if (slot < 0 || slot >= KB_MAX_SLOTS || which < 0 || (which & ~(3 | KB_LOOP_UD_ONLY)) || line > 2 || n < 0 ||
+        (n > 0 && (!nus || !out))) {
         ctx->err = "kb_loop: bad slot, line, count or pointer";
         return KB_ERR_ARG;
     }
@@ -289,8 +303,12 @@ extern "C" kb_status kb_loop(kb_ctx* ctx, int slot, int which, int n, const doub
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     {
         KB_LAUNCH(ctx, st, "k_loop");
-        k_loop<<<n, LOOP_THREADS, 0, st>>>(ctx->slots[slot], ctx->g, ctx->m, which, n, nus, ctx->d_xq,
-                                           ctx->d_wq, static_cast<double2*>(out));
+        if (ud_only)
+            k_loop<true><<<n, LOOP_THREADS, 0, st>>>(ctx->slots[slot], ctx->g, ctx->m, line, n, nus, ctx->d_xq,
+                                                     ctx->d_wq, static_cast<double2*>(out));
+        else
+            k_loop<false><<<n, LOOP_THREADS, 0, st>>>(ctx->slots[slot], ctx->g, ctx->m, line, n, nus, ctx->d_xq,
+                                                      ctx->d_wq, static_cast<double2*>(out));
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { ctx->err = std::string("kb_loop: ") + cudaGetErrorString(e); return KB_ERR_CUDA; }

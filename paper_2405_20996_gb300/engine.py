@@ -134,16 +134,19 @@ class Engine:
         kb.kb_vertex_eval(self.ctx, slot, channel, spin_uu, f.shape[0], f.data_ptr(), out.data_ptr(), st)
         return out
 
-    def loop(self, slot, nus, single_scale=False, stream=None, line=None):
+    def loop(self, slot, nus, single_scale=False, stream=None, line=None, ud_only=False):
         """Self-energy loop of a slot's vertex (kb_loop) with the model's G, or with the flow
         scheme's single-scale propagator S when single_scale (line: 0 G, 1 S, 2 G dΣ G with the
-        self-energy-derivative tables, overriding single_scale), at frequencies nus;
+        self-energy-derivative tables, overriding single_scale; ud_only: the up-down vertex
+        alone), at frequencies nus;
         returns a complex128 device tensor [n][2][2] indexed [a1'][a1] (0 classical,
         1 quantum): [:, 1, 0] = Sigma^R, [:, 0, 1] = Sigma^A, [:, 1, 1] = Sigma^K."""
         v = torch.as_tensor(nus, dtype=torch.float64).reshape(-1).to(self.device).contiguous()
         out = torch.empty((v.shape[0], 2, 2), dtype=torch.complex128, device=self.device)
         st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
         which = int(bool(single_scale)) if line is None else int(line)
+        if ud_only:
+            which |= kb.KB_LOOP_UD_ONLY
         kb.kb_loop(self.ctx, slot, which, v.shape[0], v.data_ptr(), out.data_ptr(), st)
         return out
 

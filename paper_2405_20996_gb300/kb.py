@@ -139,6 +139,7 @@ def kb_set_model(ctx, Delta, T, eps=0.0):
 
 
 KB_REG_DELTA, KB_REG_U, KB_REG_T = 0, 1, 2
+KB_LOOP_UD_ONLY = 4                  # or-ed into kb_loop's line: the up-down vertex alone
 
 
 def kb_set_regulator(ctx, kind, lam=1.0):

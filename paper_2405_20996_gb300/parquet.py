@@ -47,6 +47,7 @@ S_OUT = 8                   # bubble outputs, all channels
 S_GRAD = 9                  # adjoint accumulation, all channels
 S_RHAT = 10                 # the bare vertex of unit strength, no classes (∂/∂U, the SDE)
 S_X = 11                    # X̂ = B_a(R̂, Γ) of the Schwinger–Dyson equation: channel a only
+S_XP = 12                   # B_p(R̂, Γ), the SDE's p-channel form: channel p only
 
 
 class ParquetPA:
@@ -326,13 +327,17 @@ class ParquetSDE(ParquetPA):
     joins legs 2' (on Γ) and 2 (on R), so only X̂'s up-down part enters: X̂ sits in a slot
     with channel a alone and no crossing-partner data, where Γ_s = 2 X̂_ud.  loop(R̂) is the
     Hartree shift per unit U (zero at particle-hole symmetry).  At second order this is the
-    sunset self-energy exactly (pinned against the textbook spectral integral).  The paper
-    also combines the p- and t-channel forms; only the a-channel form is built.  Solved
+    sunset self-energy exactly (pinned against the textbook spectral integral).  form "p"
+    takes the p-channel form U [loop(R̂) + loop_ud(B_p(R̂, Γ))] and "ap" the mean of the
+    two (the paper combines the forms), both through kb_loop's up-down-only line.  Solved
     with the damped iteration or Anderson acceleration on z (the Newton–Krylov Jacobian
     of the base class does not include Σ)."""
 
-    def __init__(self, grids, nq, U, Delta, T, n_sig=41, A=5.0, eps=0.0, device=0):
+    def __init__(self, grids, nq, U, Delta, T, n_sig=41, A=5.0, eps=0.0, device=0, form="a"):
         super().__init__(grids, nq, U, Delta, T, A=A, eps=eps, device=device)
+        if form not in ("a", "p", "ap"):
+            raise ValueError("form: 'a', 'p' or 'ap'")
+        self.form = form
         self.n_sig, self.A_sig = int(n_sig), A
         x = -1.0 + 2.0 * (np.arange(self.n_sig) + 1) / (self.n_sig + 1)
         self.sig_grid = A * np.tan(np.pi * x / 2)
@@ -344,6 +349,14 @@ class ParquetSDE(ParquetPA):
         self.e.tensors[S_X] = {}
         for k in range(4):
             self.e.attach(S_X, 0, k, self.xa[k])
+        if form != "a":
+            self.xp = [torch.zeros(sh[name], dtype=torch.complex128, device=self.dev) for name in CLASS_NAMES]
+            kb.kb_set_vertex(self.e.ctx, S_XP, False, 0.0)
+            kb.kb_set_vertex_channels(self.e.ctx, S_XP, 1 << 1)
+            kb.kb_set_vertex_symmetric(self.e.ctx, S_XP, False)
+            self.e.tensors[S_XP] = {}
+            for k in range(4):
+                self.e.attach(S_XP, 1, k, self.xp[k])
         kb.kb_set_vertex(self.e.ctx, S_RHAT, True, 1.0)
 
     def _zero_state(self):
@@ -359,9 +372,18 @@ class ParquetSDE(ParquetPA):
     def sde(self, gamma):
         """(Σ^R, Σ^K) on the Σ grid from the SDE for γ, with the context's current G."""
         self.gamma.copy_(gamma)
-        self.e.bubble(0, S_RHAT, S_GAMMA, S_X, precision="fp64")
-        self.bubbles += 1
-        s = self.U * (self.e.loop(S_RHAT, self.sig_grid) + 0.5 * self.e.loop(S_X, self.sig_grid))
+        s = self.e.loop(S_RHAT, self.sig_grid)
+        if self.form == "a":
+            self.e.bubble(0, S_RHAT, S_GAMMA, S_X, precision="fp64")
+            self.bubbles += 1
+            s = s + 0.5 * self.e.loop(S_X, self.sig_grid)
+        else:
+            forms = ((0, S_X), (1, S_XP)) if self.form == "ap" else ((1, S_XP),)
+            for r, slot in forms:
+                self.e.bubble(r, S_RHAT, S_GAMMA, slot, precision="fp64")
+                self.bubbles += 1
+                s = s + self.e.loop(slot, self.sig_grid, ud_only=True) / len(forms)
+        s = self.U * s
         return s[:, 1, 0], s[:, 1, 1]
 
     def bse(self, z):
