@@ -8,7 +8,9 @@
 - Anderson acceleration: with no memory it is the damped iteration step for step; on an
   affine map with undamped updates and memory at least the dimension it terminates like
   GMRES (Walker and Ni, Theorem 2.2); on the quadratic map it needs fewer right-hand sides
-  than the damped iteration and reaches the same fixed point."""
+  than the damped iteration and reaches the same fixed point;
+- the Schwinger–Dyson self-energy's a and p forms and their mean issue the right bubbles and
+  combine the loops with the right weights (stand-in context)."""
 
 import numpy as np
 import torch
@@ -106,3 +108,39 @@ def test_anderson_on_the_quadratic_map():
     g_aa, h_aa = toy.anderson(mix=0.5, m=5, tol=1e-13, maxit=2000)
     assert h_aa[-1] <= 1e-13 and toy.bubbles <= 0.6 * n_fp, (toy.bubbles, n_fp)
     assert torch.abs(g_aa - g_fp).max() <= 1e-11 * torch.abs(g_fp).max()
+
+
+class _SDEEngine:
+    """Stand-in for the context of ParquetSDE.sde: records bubbles and returns loops that
+    depend on the slot and on whether the up-down vertex alone is asked for."""
+
+    def __init__(self, n):
+        self.n, self.calls = n, []
+
+    def bubble(self, r, sl, sr, so, precision="fp64"):
+        self.calls.append(("bubble", r, sl, sr, so))
+
+    def loop(self, slot, nus, ud_only=False):
+        self.calls.append(("loop", slot, ud_only))
+        v = {10: 1.0, 11: 3.0, 12: 5.0}[slot] * (7.0 if ud_only else 1.0)
+        out = torch.zeros((self.n, 2, 2), dtype=torch.complex128)
+        out[:, 1, 0], out[:, 1, 1] = v, 1j * v
+        return out
+
+
+def test_sde_forms_combine_the_loops():
+    from paper_2405_20996_gb300.parquet import S_GAMMA, S_RHAT, S_X, S_XP, ParquetSDE
+    for form, expect in (("a", 1.0 + 0.5 * 3.0), ("p", 1.0 + 7 * 5.0), ("ap", 1.0 + 0.5 * (7 * 3.0 + 7 * 5.0))):
+        pa = ParquetSDE.__new__(ParquetSDE)
+        pa.form, pa.U, pa.bubbles = form, 2.0, 0
+        pa.sig_grid = np.linspace(-1.0, 1.0, 3)
+        pa.gamma = torch.zeros(4, dtype=torch.complex128)
+        pa.e = _SDEEngine(3)
+        sR, sK = pa.sde(torch.ones(4, dtype=torch.complex128))
+        assert torch.allclose(sR, torch.full((3,), 2.0 * expect, dtype=torch.complex128)), (form, sR)
+        assert torch.allclose(sK, torch.full((3,), 2.0j * expect, dtype=torch.complex128))
+        bubbles = [c for c in pa.e.calls if c[0] == "bubble"]
+        want = {"a": [(0, S_X)], "p": [(1, S_XP)], "ap": [(0, S_X), (1, S_XP)]}[form]
+        assert [(c[1], c[4]) for c in bubbles] == want
+        assert all(c[2] == S_RHAT and c[3] == S_GAMMA for c in bubbles)
+        assert pa.bubbles == len(want)
