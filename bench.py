@@ -235,6 +235,31 @@ def oracle_rate(budget_s=12.0, seed=0):
     return rate, cores, desc, elapsed
 
 
+def oracle_loop_rate(grids, channels, budget_s=10.0, seed=0):
+    """Oracle self-energy loop rate (integrand evaluations/s) on a random sample of the loop
+    workload's frequencies (the K1 grid), sized to about budget_s of CPU time; returns (rate,
+    cores, description)."""
+    import seeded as S
+    from oracle import oracle as O
+    V = O.Vertex(grids, U=U, has_R=True, channels=channels)
+    P = O.Prop(Delta=DELTA, T=T)
+    nus = S.grid_freqs(grids["n1"])
+    rng = np.random.default_rng(seed)
+    cores = os.cpu_count() or 1
+    m = min(cores, len(nus))
+    t0 = time.perf_counter()
+    O.loop(V, P, NQ, nus[rng.integers(0, len(nus), size=m)])          # one frequency per thread
+    per = (time.perf_counter() - t0) / m
+    n = int(max(1, min(len(nus), budget_s / max(per, 1e-9))))
+    pick = nus if n == len(nus) else nus[rng.integers(0, len(nus), size=n)]
+    t0 = time.perf_counter()
+    O.loop(V, P, NQ, pick)
+    el = time.perf_counter() - t0
+    desc = ("%s of the K1 grid x %d interior nodes, %.1f s CPU wall"
+            % ("all %d frequencies" % n if n == len(nus) else "%d random frequencies" % n, NQ - 2, el))
+    return n * (NQ - 2) / el, cores, desc
+
+
 def run_reference(args):
     ws, rank, _ = dist_setup()
     if rank != 0:
@@ -574,6 +599,10 @@ def run_loop(args):
 
     ms = _timed(step, args.steps, max(args.warmup, 3), stream)
     kb.kb_check_device(e.ctx)
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, cores, desc = oracle_loop_rate(g, S.seeded_vertex(g, U, seed=91))
+        cpu = {"value": rate, "unit": "evaluations/s", "cores": cores, "kind": "oracle", "sample": desc}
     evals = nus.numel() * (NQ - 2)
     flops = evals * (144 * 64 + 288)
     ach = flops / (ms / 1e3) / 1e12
@@ -585,7 +614,8 @@ def run_loop(args):
                        "evaluations_per_step": evals, "l2": "vertex 17 MB per K3 channel, L2-resident"},
             "roofline": {"kernel": "k_loop", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                         "note": "upper-bound flop count; FP64 peak derived from SM count and clock"}}
+                         "note": "upper-bound flop count; FP64 peak derived from SM count and clock"},
+            "cpu_baseline": cpu}
     print(json.dumps(line))
     e.close()
     return 0
