@@ -470,3 +470,32 @@ def test_third_order_k1_is_the_ladder_of_a_repulsive_coupling():
         vals = np.array([s[r][0][w0][1].real / U ** 2 for s, U in zip(sols, Us)])   # component (c c|c q)
         c4, c3, c2 = np.polyfit(Us, vals, 2)
         assert abs(c3 / c2 / (-pi.real / 2) - 1) <= 2e-3, (r, c3 / c2, -pi.real / 2)
+
+
+def test_parquet_classes_keep_the_bare_vertex_keldysh_structure():
+    """The bare vertex depends on the parity of the quantum indices only, and the bubble passes
+    that on: in the parquet solution each K1 parity block carries one number (4 distinct
+    components of 16) and K2, K2' pair their components up to sign (8 distinct), K3 keeps all
+    16, exactly, in every channel."""
+    CLS = ("K1", "K2", "K2p", "K3")
+    g = dict(n1=13, n2w=7, n2v=6, n3w=5, n3v=4)
+    nq, U = 41, 1.0
+    P = O.Prop(Delta=1.0, T=0.2)
+    gam = {c: [np.zeros(O.class_shape(g, k), dtype=np.complex128) for k in CLS] for c in range(3)}
+    for _ in range(25):
+        Gam = O.Vertex(g, U=U, has_R=True, channels=gam)
+        new = {r: O.bubble_all(O.Vertex(g, U=U, has_R=True, channels=gam, include=[c for c in range(3) if c != r]),
+                               Gam, P, r, nq) for r in range(3)}
+        gam = {c: [0.5 * gam[c][k] + 0.5 * new[c][CLS[k]] for k in range(4)] for c in range(3)}
+
+    def distinct(X):
+        X = X.reshape(-1, 16)
+        tol = 1e-13 * np.abs(X).max()
+        groups = []
+        for c in range(16):
+            if not any(min(np.abs(X[:, c] - X[:, q]).max(), np.abs(X[:, c] + X[:, q]).max()) <= tol for q in groups):
+                groups.append(c)
+        return len(groups)
+
+    for r in range(3):
+        assert [distinct(gam[r][k]) for k in range(4)] == [4, 8, 8, 16], r
