@@ -199,8 +199,25 @@ def _loop_brute(V, P, nu, A=5.0):
     return (res[:4] + 1j * res[4:]).reshape(2, 2)
 
 
-def test_loop_fixed_rule_converges_to_adaptive_brute_force():
-    V = _seeded()
+def _flat_vertex(seed=11):
+    """Classes that stay finite out to the grid edges and differ between the two ends (K1
+    ramps from -1 to 1 across the w grid, K2' and K3 across the v' grid), so that the rule's
+    end-node limits carry weight and do not cancel between x = -1 and x = +1."""
+    rng = np.random.default_rng(seed)
+    rnd = lambda *sh: rng.standard_normal(sh) + 1j * rng.standard_normal(sh)
+    ramp = lambda n: np.linspace(-1.0, 1.0, n)
+    ch = {}
+    for c in range(3):
+        K1 = ramp(G["n1"])[:, None] * rnd(16)[None, :]
+        K2p = ramp(G["n2v"])[None, :, None] * rnd(G["n2w"], 1, 16)
+        K3 = ramp(G["n3v"])[None, None, :, None] * rnd(G["n3w"], G["n3v"], 1, 16)
+        ch[c] = (0.1 * K1, None, 0.1 * K2p, 0.1 * K3)
+    return O.Vertex(G, U=1.0, has_R=True, channels=ch)
+
+
+@pytest.mark.parametrize("flat", [False, True])
+def test_loop_fixed_rule_converges_to_adaptive_brute_force(flat):
+    V = _flat_vertex() if flat else _seeded()
     P = O.Prop(Delta=1.0, T=0.1, eps=0.3)
     for nu in (0.0, 1.3):
         ref = _loop_brute(V, P, nu)
