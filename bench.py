@@ -632,6 +632,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--channels", default="apt", help="subset of a, p, t (profiling captures)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling captures)")
+    ap.add_argument("--no-fp64-check", action="store_true",
+                    help="skip the plain-FP64 step behind per_class_err and fp64_gpu (profiling captures)")
     ap.add_argument("--no-graph", action="store_true", help="eager launches instead of one step graph")
     ap.add_argument("--ws-gb", type=int, default=8, help="device workspace limit per context (GiB)")
     ap.add_argument("--ml-cache", default="auto", choices=["off", "auto", "all"],
@@ -808,6 +810,53 @@ def main():
                     others.append(e)
         roof["others"] = others
 
+    # ---- the error clause of the metric: one plain-FP64 step of the same bubbles on the same
+    # (complex64) vertex; per channel and class the relative max-norm error of the mixed
+    # outputs (the last timed step's) against it, and the FP64 step's own rate ----
+    per_class_err, fp64_gpu = None, None
+    if prec == "mixed" and not args.no_fp64_check:
+        CN = ("K1", "K2", "K2p", "K3")
+        for r, e in engs.items():
+            e.alloc_out(2, channels=(r,), dtype=torch.complex128)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(stream)
+        for r in chans:
+            engs[r].bubble(r, 0, 0, 2, precision="fp64", stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a.elapsed_time(b)
+        fp64_gpu = {"value": points / (ms64 / 1e3), "ms_per_step": ms64, "steps": 1,
+                    "note": "plain FP64 path (FP64 gather and FP64 SIMT contraction), same vertex and outputs, "
+                            "one step after the mixed ones"}
+        per_class_err = {}
+        worst = 0.0
+        for r in chans:
+            mx, fp = engs[r].out(1, r), engs[r].out(2, r)
+            d = {}
+            for k in CN:
+                num = float((mx[k].to(torch.complex128) - fp[k]).abs().max())
+                den = float(fp[k].abs().max())
+                d[k] = num / den if den > 0 else num
+                worst = max(worst, d[k])
+            per_class_err["apt"[r]] = d
+        per_class_err["max"] = worst
+        per_class_err["tolerance"] = 1e-6
+
+    # ---- the dominant kernel counted by output points alone: 32 Nq real flops per output
+    # point it computes (4 Nq complex multiply-adds), against the FP32 pipe ----
+    if roof is not None and roof.get("kernel") == "k_mx_k2":
+        half = lambda n: n - n // 2
+        comp = {0: half(GRIDS["n2w"]) * GRIDS["n2v"], 1: GRIDS["n2w"] * half(GRIDS["n2v"]),
+                2: half(GRIDS["n2w"]) * GRIDS["n2v"]}
+        f8 = sum(comp[r] * 16 * 32.0 * NQ for r in chans) * args.steps
+        a8 = f8 / (dms / 1e3) / 1e12
+        roof["frac_s8d"] = a8 / FP32_PEAK_TFLOPS
+        roof["achieved_s8d"] = a8
+        roof["note_s8d"] = ("32 Nq flops per computed K2 point (the independent half), i.e. the contraction's "
+                            "4 Nq complex multiply-adds per point without the gather, against the same FP32 pipe peak")
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and len(chans) == 3:
         rate, cores, desc, _ = oracle_rate(budget_s=args.ref_budget)
@@ -825,6 +874,7 @@ def main():
                            else "eager, one stream"},
                 "e2e": e2e,
                 "gpu_launches": int(launches_timed), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+                "per_class_err": per_class_err, "fp64_gpu": fp64_gpu,
                 "kernels_ms": {k: round(v[0] / args.steps, 4) for k, v in prof.items()},
                 "kernels_ms_note": "per-kernel CUDA-event times of the same steps run eagerly (sum %.3f ms/step)"
                                    % (sum(v[0] for v in prof.values()) / args.steps),

@@ -352,7 +352,12 @@ kb_status kb_profile_read(kb_ctx *ctx, int index, const char **name, double *ms,
  *
  * No context is used.  The caller passes the grids, the model (Sigma = 0: G^R = 1/(v - eps
  * + i Delta)), the two vertices as device pointers in the layout above, and the device
- * output array of class `cls` of channel `channel` (out <- alpha B + beta out).
+ * output array of class `cls` of channel `channel` (out <- alpha B + beta out).  With
+ * pi_kind = KB_PI_GS_SG the single-scale propagator S is always that of the hybridisation
+ * flow (S^R = -i (G^R)^2, the KB_REG_DELTA scheme of kb_set_regulator); the other flow
+ * schemes need a context.  `stream` must belong to the current device (KB_ERR_ARG
+ * otherwise), and the call refuses to start (KB_ERR_CUDA) while an earlier launch error is
+ * pending on this thread; it returns at the first chunk whose launches fail.
  * The first call on a device looks up the array's device address (and uploads the small
  * index tables); make that first call before any stream capture.  All calls share the one
  * array, and each call overwrites every scratch element it reads, so no call depends on an

@@ -276,13 +276,22 @@ extern "C" kb_status kb_bubble_fp64_noalloc(const kb_grid_desc* gd, double Delta
         gd->n1 < 1 || gd->n2w < 1 || gd->n2v < 1 || gd->n3w < 1 || gd->n3v < 1 || gd->nq < 5 ||
         (gd->nq - 1) % 4 || !(gd->A > 0) || left->channels > 7 || right->channels > 7)
         return KB_ERR_ARG;
+    // a launch error left pending by earlier work is not this call's to report or clear
+    if (cudaPeekAtLastError() != cudaSuccess) return KB_ERR_CUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return KB_ERR_CUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    {
+        // the scratch address is per device: the stream must belong to the current device
+        int sdev = -1;
+        if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) return KB_ERR_CUDA;
+        if (sdev != dev) return KB_ERR_ARG;
+    }
     kb_status s = noalloc_setup(dev);
     if (s != KB_OK) return s;
     Grids g{gd->n1, gd->n2w, gd->n2v, gd->n3w, gd->n3v, gd->nq, gd->A};
     Model m{Delta, T, eps, 0, 1.0, nullptr, nullptr};
-    VertexDev V[2];
+    VertexDev V[2]{};
     const kb_vertex_desc* D[2] = {left, right};
     for (int i = 0; i < 2; ++i) {
         V[i].has_R = D[i]->has_R ? 1 : 0;
@@ -304,7 +313,6 @@ extern "C" kb_status kb_bubble_fp64_noalloc(const kb_grid_desc* gd, double Delta
                    (size_t)4 * nR * K * sizeof(double2) + (size_t)16 * nL * nR * sizeof(double2);
     if (table + per_w > KB_NOALLOC_SCRATCH_BYTES) return KB_ERR_TOO_LARGE;
     int chunk = (int)std::min<size_t>(nw, (KB_NOALLOC_SCRATCH_BYTES - table) / per_w);
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     char* base = static_cast<char*>(g_noalloc_ptr[dev]);
     double* xq = reinterpret_cast<double*>(base);
     double* wq = xq + (g.nq + 31) / 32 * 32;
@@ -313,6 +321,7 @@ extern "C" kb_status kb_bubble_fp64_noalloc(const kb_grid_desc* gd, double Delta
     double2* Rt = Lt + (size_t)chunk * 4 * nL * K;
     double2* Gm = Rt + (size_t)chunk * 4 * nR * K;
     k_gl5_table<<<(g.nq + 127) / 128, 128, 0, st>>>(g.nq, xq, wq);
+    if (cudaGetLastError() != cudaSuccess) return KB_ERR_CUDA;
     for (int w0 = 0; w0 < nw; w0 += chunk) {
         ClassJob J;
         J.r = r; J.pi_kind = pi_kind; J.ns = ns; J.nq = g.nq;
@@ -331,6 +340,9 @@ extern "C" kb_status kb_bubble_fp64_noalloc(const kb_grid_desc* gd, double Delta
             k_zgemm_f64<<<dim3((Nc + 31) / 32, (Mr + 31) / 32, J.nw_chunk), 256, 0, st>>>(Lt, Rt, Gm, Mr, Nc, (int)K);
         size_t tot = (size_t)J.nw_chunk * nL * nR * 16;
         k_scatter<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(J, cls, Gm, out, out_dtype, alpha, beta);
+        // stop at the first chunk whose launches failed (the entry check above guarantees
+        // that the error, if any, comes from this call's launches)
+        if (cudaGetLastError() != cudaSuccess) return KB_ERR_CUDA;
     }
-    return cudaGetLastError() == cudaSuccess ? KB_OK : KB_ERR_CUDA;
+    return KB_OK;
 }

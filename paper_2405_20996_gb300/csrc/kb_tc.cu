@@ -6,8 +6,9 @@
 // descriptor.  A CTA computes either the real or the imaginary part of a 128 x 128 output
 // tile (6 MMAs of N = 128 per k-step): the register file holds the compensated running
 // sums of 128 x 128 real values, and N = 128 halves the shared-memory operand reads per MMA
-// flop against complex 128 x 64 tiles.  Accumulation in FP32 in tensor memory restarted
-// every SEG K chunks; finished segments are added into compensated FP32 sums in registers,
+// flop against complex 128 x 64 tiles.  Every CTA loads all of its operand planes itself
+// (plain TMA into its own shared memory; no thread-block clusters).  Accumulation in FP32
+// in tensor memory restarted every SEG K chunks; finished segments are added into compensated FP32 sums in registers,
 // the K dimension is split over CTAs and the split partials are added in FP64.
 //
 // Operands (written by k_mx_tile3): A = [batch][plane][M][K], B = [batch][plane][N][K],
@@ -76,22 +77,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
-// The same tile into the shared memory of every CTA of the cluster in cta_mask (same offset,
-// same barrier offset in each).
-__device__ __forceinline__ void tma_load_3d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
-                                               uint16_t cta_mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "h"(cta_mask)
-        : "memory");
-}
-
-__device__ __forceinline__ void cluster_sync_all() {
-    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 // Shared-memory matrix descriptor (tcgen05): K-major operand, 64-byte swizzle, 8-row
 // groups 512 bytes apart.
 __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
@@ -121,15 +106,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t ad, uint64_t bd, 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
-}
-// arrive, once the MMAs issued so far have completed, on the barrier at this offset in every
-// CTA of cta_mask
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t cta_mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
-        "h"(cta_mask)
-        : "memory");
 }
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -202,8 +178,7 @@ __global__ void __maxnreg__(96)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(segempty + 2);
     __shared__ volatile int s_fail;
 
-    // clusters of two CTAs: rank 0 the real part, rank 1 the imaginary part of one tile; both
-    // need the same operand tiles, so each loads half of the planes and multicasts them
+    // neighbouring CTAs: even the real part, odd the imaginary part of one tile
     const int part = blockIdx.x & 1;
     int unit = blockIdx.x >> 1;
     int ks = unit % J.ksplit;
@@ -219,8 +194,7 @@ __global__ void __maxnreg__(96)
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        // empty[s]: one arrival from the MMA warp of each CTA of the pair
-        for (int s = 0; s < STAGES_S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 2); }
+        for (int s = 0; s < STAGES_S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
         for (int i = 0; i < 2; ++i) { mbar_init(&segfull[i], 1); mbar_init(&segempty[i], 32 * EPI_WARPS); }
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -235,7 +209,6 @@ __global__ void __maxnreg__(96)
     __syncthreads();
     fence_after();
     uint32_t tbase = *tslot;
-    cluster_sync_all();          // the peer's barriers are initialised before any multicast
 
     if (warp == 0) {
         if (lane == 0) {
@@ -246,20 +219,19 @@ __global__ void __maxnreg__(96)
                 if (s_fail) break;
                 if (i >= STAGES_S && !mbar_wait(&empty[s], ph ^ 1)) { atomicOr(&g_tc_status, 1); s_fail = 1; break; }
                 unsigned char* st = smem + s * STAGE;
-                mbar_expect_tx(&full[s], STAGE);          // own half + the peer's half
+                mbar_expect_tx(&full[s], STAGE);
                 int kx = (c0 + i) * KC;
-                for (int p = 2 * part; p < 2 * part + 2; ++p) {
-                    tma_load_3d_mc(st + p * A_PLANE, &tmA, &full[s], kx, mt * MT, 4 * b + p, (uint16_t)3);
-                    tma_load_3d_mc(st + 4 * A_PLANE + p * B_PLANE, &tmB, &full[s], kx, nt * NT, 4 * b + p,
-                                   (uint16_t)3);
+                for (int p = 0; p < 4; ++p) {
+                    tma_load_3d(st + p * A_PLANE, &tmA, &full[s], kx, mt * MT, 4 * b + p);
+                    tma_load_3d(st + 4 * A_PLANE + p * B_PLANE, &tmB, &full[s], kx, nt * NT, 4 * b + p);
                 }
                 issued |= 1u << s;
                 phases = (phases & ~(1u << s)) | (ph << s);
             }
             for (int s = 0; s < STAGES_S; ++s)
                 if (((issued >> s) & 1) && !mbar_wait(&full[s], (phases >> s) & 1)) atomicOr(&g_tc_status, 1);
-            // tail: both CTAs' MMAs have released every stage, so no arrival from the peer
-            // is still on its way to this CTA's barriers when it leaves
+            // tail: the MMAs have released every stage, so no commit arrival is still on its
+            // way to this CTA's barriers when it leaves
             if (!s_fail)
                 for (int s = 0; s < STAGES_S; ++s)
                     if (((issued >> s) & 1) && !mbar_wait(&empty[s], (phases >> s) & 1)) atomicOr(&g_tc_status, 1);
@@ -305,7 +277,7 @@ __global__ void __maxnreg__(96)
                         mma_tf32(dacc, ail, brh, id_pos, 1);
                     }
                 }
-                mma_commit_mc(&empty[s], (uint16_t)3);   // the stage is free once both CTAs are done
+                mma_commit(&empty[s]);                   // the stage is free once its MMAs are done
                 if ((i % SEG) == SEG - 1 || i == nck - 1) mma_commit(&segfull[buf]);
             }
         }
@@ -350,7 +322,6 @@ __global__ void __maxnreg__(96)
     fence_before();
     __syncthreads();
     fence_after();
-    cluster_sync_all();          // no multicast write or arrival for this CTA is still pending
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TMEM_COLS) : "memory");
 }
@@ -530,19 +501,7 @@ static bool launch_split(kb_ctx* ctx, const float* At, const float* Bt, double2*
     double2* P = reinterpret_cast<double2*>(scratch);
     {
         KB_LAUNCH(ctx, st, "k_tc_k3");
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)(base * J.ksplit));
-        cfg.blockDim = dim3(NTHREADS_S);
-        cfg.dynamicSmemBytes = smem;
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = 2;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        cudaLaunchKernelEx(&cfg, k_tc_k3, ma, mb, J, P);
+        k_tc_k3<<<(unsigned)(base * J.ksplit), NTHREADS_S, smem, st>>>(ma, mb, J, P);
     }
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) {
