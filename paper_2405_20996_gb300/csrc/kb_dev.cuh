@@ -134,17 +134,23 @@ __device__ inline void prop2x2(const Model& m, int which, double v, double2 P[2]
 // interaction flow (S^R -> 1/v) and 0 otherwise (Sec. II.G.6 tail reading).
 // vnode: the node frequency v''_j = A tan(pi x_j / 2) when the caller has it (have_v), so
 // that the tangent is not evaluated again.
-__device__ inline void pi_entry(const Model& m, const ChannelMaps& M, int r, int pi_kind, double A, double w,
-                                double xj, double wj, double2 out[16], double vnode = 0.0, bool have_v = false) {
-    double cr = (r == KB_CH_T) ? -1.0 : 1.0;
+// Channel R at compile time: the Keldysh indices (b3, b3', b4, b4') of the two lines map to
+// the rows B and columns D of the table as in channel_maps (kb_api.cu), and with every
+// index fixed at compile time the 2x2 propagator matrices stay in registers.
+template <int R>
+__device__ __forceinline__ void pi_entry_t(const Model& m, int pi_kind, double A, double w, double xj, double wj,
+                                           double2 out[16], double vnode = 0.0, bool have_v = false) {
+    constexpr double cr = (R == KB_CH_T) ? -1.0 : 1.0;
     double2 P3[2][2], P4[2][2], S3[2][2], S4[2][2];
     double scale;
     if (xj <= -1.0 || xj >= 1.0) {
-        double s3 = 1.0, s4 = (r == KB_CH_P) ? -1.0 : 1.0;
+        constexpr double s3 = 1.0, s4 = (R == KB_CH_P) ? -1.0 : 1.0;
         const double gl = (m.reg == KB_REG_U) ? m.lam : 1.0, sl = (m.reg == KB_REG_U) ? 1.0 : 0.0;
+#pragma unroll
         for (int a = 0; a < 2; ++a)
+#pragma unroll
             for (int b = 0; b < 2; ++b) {
-                double g = (a != b) ? 1.0 : 0.0;
+                const double g = (a != b) ? 1.0 : 0.0;
                 P3[a][b] = make_double2(g * gl * s3, 0);
                 P4[a][b] = make_double2(g * gl * s4, 0);
                 S3[a][b] = make_double2(g * sl * s3, 0);
@@ -155,25 +161,42 @@ __device__ inline void pi_entry(const Model& m, const ChannelMaps& M, int r, int
         const double tn = have_v ? vnode / A : tan(0.5 * KB_PI * xj);
         const double vpp = have_v ? vnode : A * tn;
         double a3, a4;
-        if (r == KB_CH_P) { a3 = 0.5 * w + vpp; a4 = 0.5 * w - vpp; }
+        if (R == KB_CH_P) { a3 = 0.5 * w + vpp; a4 = 0.5 * w - vpp; }
         else { a3 = vpp + 0.5 * w; a4 = vpp - 0.5 * w; }
         prop2x2(m, 0, a3, P3);
         prop2x2(m, 0, a4, P4);
         if (pi_kind == KB_PI_GS_SG) { prop2x2(m, 1, a3, S3); prop2x2(m, 1, a4, S4); }
+        else {
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) S3[a][b] = S4[a][b] = make_double2(0, 0);
+        }
         scale = 0.5 * A * KB_PI * (1.0 + tn * tn);
     }
     // c_r * w_j * scale / (2 pi i) = -i * (c_r w_j scale / 2 pi)
-    double f = cr * wj * scale / (2.0 * KB_PI);
-    for (int B = 0; B < 4; ++B)
-        for (int D = 0; D < 4; ++D) {
-            const int* q = M.piq[B][D];
-            double2 v;
-            if (pi_kind == KB_PI_GS_SG)
-                v = cadd(cmul(P3[q[0]][q[1]], S4[q[2]][q[3]]), cmul(S3[q[0]][q[1]], P4[q[2]][q[3]]));
-            else
-                v = cmul(P3[q[0]][q[1]], P4[q[2]][q[3]]);
-            out[4 * B + D] = make_double2(f * v.y, -f * v.x);   // times -i f
-        }
+    const double f = cr * wj * scale / (2.0 * KB_PI);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int b3 = q >> 3, b3p = (q >> 2) & 1, b4 = (q >> 1) & 1, b4p = q & 1;
+        const int B = (R == KB_CH_A) ? 2 * b4p + b3 : (R == KB_CH_P ? 2 * b3 + b4 : 2 * b3p + b4);
+        const int D = (R == KB_CH_A) ? 2 * b3p + b4 : (R == KB_CH_P ? 2 * b3p + b4p : 2 * b4p + b3);
+        double2 v;
+        if (pi_kind == KB_PI_GS_SG)
+            v = cadd(cmul(P3[b3][b3p], S4[b4][b4p]), cmul(S3[b3][b3p], P4[b4][b4p]));
+        else
+            v = cmul(P3[b3][b3p], P4[b4][b4p]);
+        out[4 * B + D] = make_double2(f * v.y, -f * v.x);   // times -i f
+    }
+}
+
+// The same for a channel known only at run time.
+__device__ inline void pi_entry(const Model& m, const ChannelMaps& M, int r, int pi_kind, double A, double w,
+                                double xj, double wj, double2 out[16], double vnode = 0.0, bool have_v = false) {
+    (void)M;
+    if (r == KB_CH_A) pi_entry_t<KB_CH_A>(m, pi_kind, A, w, xj, wj, out, vnode, have_v);
+    else if (r == KB_CH_P) pi_entry_t<KB_CH_P>(m, pi_kind, A, w, xj, wj, out, vnode, have_v);
+    else pi_entry_t<KB_CH_T>(m, pi_kind, A, w, xj, wj, out, vnode, have_v);
 }
 
 }  // namespace kb

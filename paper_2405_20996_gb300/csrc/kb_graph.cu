@@ -86,6 +86,8 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
     for (int i = 0; i < n; ++i) any_mixed |= d[i].op == KB_OP_BUBBLE && d[i].precision == KB_PREC_MIXED;
     if (any_mixed && !kb_tc_prepare(c0->device))
         return fail(c0, "kb_graph_create: tensor-core kernel setup failed", KB_ERR_CUDA);
+    if (any_mixed && !kb_mixed_prepare(c0->device))
+        return fail(c0, "kb_graph_create: mixed-path kernel setup failed", KB_ERR_CUDA);
     // contexts with autotuning on: tune their contraction shapes now (timing is not possible
     // inside a capture); the replays use the tuned split-K factors
     for (int i = 0; i < n; ++i) {

@@ -161,3 +161,4 @@ size_t kb_fp64_workspace_need(const kb_ctx* ctx, int r, unsigned mask);
 size_t kb_mixed_workspace_need(const kb_ctx* ctx, int r, unsigned mask);
 kb_status kb_fp64_prepare(kb_ctx* ctx);
 bool kb_tc_prepare(int device);
+bool kb_mixed_prepare(int device);

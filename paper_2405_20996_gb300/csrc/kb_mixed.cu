@@ -13,6 +13,7 @@
 //   K3 contraction: tcgen05 3xTF32 (kb_tc.cu) or the SIMT reference k_mx_cgemm
 //   k_mx_scatter3 out <- alpha B + beta out for K3
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(128) k_mx_prep_k2(VertexF VL, VertexF VR, DfGr
     float2 Pf[16];
     {
         double2 Pi[16];
-        pi_entry(m, J.M, J.r, J.pi_kind, G.A, (double)w.h + (double)w.l, xq[j], wq[j], Pi,
+        pi_entry_t<R>(m, J.pi_kind, G.A, (double)w.h + (double)w.l, xq[j], wq[j], Pi,
                      (double)G.n3v[G.N3v + j].h + (double)G.n3v[G.N3v + j].l, true);
 #pragma unroll
         for (int i = 0; i < 16; ++i) Pf[i] = make_float2((float)Pi[i].x, (float)Pi[i].y);
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(128) k_mx_k1(VertexF VL, VertexF VR, DfGrids G
         float2 Pf[16];
         {
             double2 Pi[16];
-            pi_entry(m, J.M, J.r, J.pi_kind, G.A, (double)w.h + (double)w.l, xq[j], wq[j], Pi,
+            pi_entry_t<R>(m, J.pi_kind, G.A, (double)w.h + (double)w.l, xq[j], wq[j], Pi,
                      (double)G.n3v[G.N3v + j].h + (double)G.n3v[G.N3v + j].l, true);
 #pragma unroll
             for (int i = 0; i < 16; ++i) Pf[i] = make_float2((float)Pi[i].x, (float)Pi[i].y);
@@ -442,84 +443,175 @@ __device__ __forceinline__ void k2_tail(const VertexF& V, const DfGrids& G, cons
 //   K2own_s(w, v)[A][B] * SN_s(w)[B][C]  (the own K2 class does not depend on v'').
 // K2' (RIGHT = true): out(w, v')[A][C] = sum_j sum_s sum_D M_s(w, j)[A][D] R_s(w, v''_j, v')[D][C]
 //   + SM_s(w)[A][D] * K2'own_s(w, v')[D][C].
-// One CTA (128 threads) per (w, v).  Per tile of 128 nodes every thread gathers one record
-// into shared memory; then the 4x4 contraction runs with one output component per thread
-// (16 components x 8 record groups), so the gather carries no output accumulators.  The
-// endpoint nodes contribute only through the own class and are skipped in the tiles.
+// One CTA (128 threads) per (w, v); the interior nodes in chunks of CH = 128 / NG (NG lookup
+// groups: the two other channels, and for t their exchanged partners):
+//   1. corner lists: one thread per (node, group) finds the stencils of the group's classes
+//      and writes its 18 (record, weight) pairs to shared memory; the chunk's rows of the
+//      propagator-vertex table are staged beside them (t: combined per spin record);
+//   2. gather: 8 lanes per node, lane l reading the 16-byte piece l (components 2l, 2l+1) of
+//      every corner record, so one warp-wide load covers the full records of 4 nodes and each
+//      quarter-warp reads one 128-byte line (the L1 delivers one line per quarter-warp and
+//      cycle, so this is the fewest wavefronts a corner can cost); each lane multiplies its
+//      two interpolated components into the table rows they meet and keeps 8 partial outputs
+//      across all nodes;
+//   3. the partials are reduced over lanes and warps into the (A, C)-per-thread layout of
+//      k2_tail, which adds the own classes and stores.
+// The endpoint nodes contribute only through the own class and are not gathered.  (Reading
+// each record once for a run of neighbouring nodes, by one thread or by a lane group, cut the
+// L1 traffic but cost more instructions than it saved, measured on the a channel.)
+template <int R>
+__host__ __device__ constexpr size_t k2_smem_bytes() {
+    constexpr int NS = (R == KB_CH_T) ? 2 : 1;
+    constexpr int CH = 128 / (2 * NS);
+    constexpr size_t loop = (size_t)2 * NS * 18 * CH * sizeof(int2) + (size_t)NS * CH * 9 * sizeof(float4);
+    constexpr size_t tail = (size_t)NS * 128 * 17 * sizeof(float2);
+    return loop > tail ? loop : tail;
+}
+
 template <bool RIGHT, int R>
-__global__ void __launch_bounds__(128, 4) k_mx_k2(VertexF V, DfGrids G, MixedJob J, const float2* __restrict__ Tab,
+__global__ void __launch_bounds__(128, 6) k_mx_k2(VertexF V, DfGrids G, MixedJob J, const float2* __restrict__ Tab,
                                                const double2* __restrict__ Ssum, const double2* __restrict__ Ntil,
                                                void* out, int odt, int w_off, int v_off) {
     constexpr int NS = (R == KB_CH_T) ? 2 : 1;
-    // records of the quadrature nodes of one chunk: [0] up-down, [1] up-up (t only; the
-    // up-up record is the up-down one plus the exchanged term, so the direct lookups are
-    // done once for both spin terms)
-    __shared__ float2 rec[NS][128][17];
+    constexpr int NG = 2 * NS;
+    constexpr int CH = 128 / NG;
+    constexpr size_t CL_BYTES = (size_t)NG * 18 * CH * sizeof(int2);
+    extern __shared__ __align__(16) unsigned char k2_smem[];
     __shared__ float2 red[8][16];
-    int wi = w_off + blockIdx.y, vi = v_off + blockIdx.x;
+    int2* cl = reinterpret_cast<int2*>(k2_smem);                          // [g][k][n]
+    float4* trow = reinterpret_cast<float4*>(k2_smem + CL_BYTES);         // [s][n][9]
+    const int wi = w_off + blockIdx.y, vi = v_off + blockIdx.x;
     const df* qn = G.n3v + G.N3v;
-    df w = G.n2w[wi], ve = G.n2v[vi];
-    const int tid = threadIdx.x, o = tid & 15, q = tid >> 4;
-    const int A = o >> 2, C = o & 3;
-    float2 acc = make_float2(0.f, 0.f);
-    // spin term s uses up-up on the left for s = 0 and on the right for s = 1 (t channel)
+    const df w = G.n2w[wi], ve = G.n2v[vi];
+    const int tid = threadIdx.x, wp = tid >> 5, lane = tid & 31, gi = lane >> 3, l = lane & 7;
     const float2* T0 = Tab + ((size_t)wi * NS) * J.nq * 16;
     const float2* T1 = T0 + (size_t)J.nq * 16;
+    // this lane's record components 2l + e as matrix entries (X_e, Y_e) of channel R's map
+    int Xe[2], Ye[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        int xy = 0;
+        for (int q = 0; q < 16; ++q)
+            if (cmap<R>(q >> 2, q & 3) == 2 * l + e) xy = q;
+        Xe[e] = xy >> 2;
+        Ye[e] = xy & 3;
+    }
+    // partial outputs: left o[e][C] belongs to out[X_e][C], right o[e][A] to out[A][Y_e]
+    float2 o[2][4];
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) o[e][c] = make_float2(0.f, 0.f);
 #pragma unroll 1
-    for (int j0 = 1; j0 < J.nq - 1; j0 += 128) {
-        int j = j0 + tid;
-        float2 g[16];
-        const bool valid = j < J.nq - 1;
-        if (valid) {
-            if (RIGHT) vertex_part_f32<R>(V, G, PARTS_UD, true, 32, w, qn[j], ve, g);
-            else vertex_part_f32<R>(V, G, PARTS_UD, false, 32, w, ve, qn[j], g);
-        } else {
-#pragma unroll
-            for (int c = 0; c < 16; ++c) g[c] = make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int c = 0; c < 16; ++c) rec[0][tid][c] = g[c];
-        if (NS == 2) {
-            if (valid) {
-                if (RIGHT) vertex_part_f32<R>(V, G, PARTS_X, true, 32, w, qn[j], ve, g, true);
-                else vertex_part_f32<R>(V, G, PARTS_X, false, 32, w, ve, qn[j], g, true);
+    for (int j0 = 1; j0 < J.nq - 1; j0 += CH) {
+        {
+            // 1. corner lists, one (node, group) per thread; a warp's items share g
+            const int n = tid % CH, g = tid / CH, j = j0 + n;
+            int2* dst = cl + (size_t)g * 18 * CH + n;
+            if (j < J.nq - 1) {
+                if (RIGHT) group_corners_rt<R>(V, G, g, w, qn[j], ve, dst, CH);
+                else group_corners_rt<R>(V, G, g, w, ve, qn[j], dst, CH);
+            } else {
+                no_corners18(dst, CH);
             }
-#pragma unroll
-            for (int c = 0; c < 16; ++c) rec[NS - 1][tid][c] = g[c];
+        }
+        // table rows; t: left (T0 + T1, T0) pairs with (up-down, exchanged term) since
+        // up-up = up-down + exchanged term and the sum is uu T0 + ud T1; right (T0 + T1, T1)
+#pragma unroll 1
+        for (int it = tid; it < CH * 8; it += 128) {
+            const int n = it >> 3, piece = it & 7, j = j0 + n;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+            if (j < J.nq - 1) {
+                a = ld_stream4(reinterpret_cast<const float4*>(T0 + (size_t)j * 16) + piece);
+                if (NS == 2) b = ld_stream4(reinterpret_cast<const float4*>(T1 + (size_t)j * 16) + piece);
+            }
+            if (NS == 1) {
+                trow[n * 9 + piece] = a;
+            } else {
+                trow[n * 9 + piece] = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+                trow[(CH + n) * 9 + piece] = RIGHT ? b : a;
+            }
         }
         __syncthreads();
-        int nrec = min(128, J.nq - 1 - j0);
+        // 2. gather and contraction, 4 nodes per warp at a time
 #pragma unroll 1
-        for (int rr = q; rr < nrec; rr += 8) {
-            const float2* t0 = T0 + (size_t)(j0 + rr) * 16;
-            if (NS == 1) {
-                if (!RIGHT) {
+        for (int n = wp * 4 + gi; n < CH; n += 16) {
+            float2 d0 = make_float2(0.f, 0.f), d1 = d0, x0 = d0, x1 = d0;
+            gather_list<group_channel<R, 0>()>(V, cl + n, CH, l, d0, d1);
+            gather_list<group_channel<R, 1>()>(V, cl + 18 * CH + n, CH, l, d0, d1);
+            if (NS == 2) {
+                gather_list_x<group_channel<R, 2>()>(V, cl + 2 * 18 * CH + n, CH, l, x0, x1);
+                gather_list_x<group_channel<R, 3>()>(V, cl + 3 * 18 * CH + n, CH, l, x0, x1);
+            }
 #pragma unroll
-                    for (int B = 0; B < 4; ++B) cmac2(acc, rec[0][rr][cmap<R>(A, B)], ld_stream(t0 + 4 * B + C));
-                } else {
+            for (int e = 0; e < 2; ++e) {
+                const float2 dv = e ? d1 : d0, xv = e ? x1 : x0;
 #pragma unroll
-                    for (int D = 0; D < 4; ++D) cmac2(acc, ld_stream(t0 + 4 * A + D), rec[0][rr][cmap<R>(D, C)]);
-                }
-            } else {
-                const float2* t1 = T1 + (size_t)(j0 + rr) * 16;
-                if (!RIGHT) {
+                for (int s = 0; s < NS; ++s) {
+                    const float4* tr = trow + (s * CH + n) * 9;
+                    const float2 rv = s == 0 ? dv : xv;
+                    if (!RIGHT) {
+                        // row Y_e of the table: components 4 Y_e .. 4 Y_e + 3
+                        const float4 p0 = tr[2 * Ye[e]], p1 = tr[2 * Ye[e] + 1];
+                        cmac2(o[e][0], rv, make_float2(p0.x, p0.y));
+                        cmac2(o[e][1], rv, make_float2(p0.z, p0.w));
+                        cmac2(o[e][2], rv, make_float2(p1.x, p1.y));
+                        cmac2(o[e][3], rv, make_float2(p1.z, p1.w));
+                    } else {
+                        // column X_e of the table: components 4 A + X_e
 #pragma unroll
-                    for (int B = 0; B < 4; ++B) {
-                        cmac2(acc, rec[NS - 1][rr][cmap<R>(A, B)], ld_stream(t0 + 4 * B + C));
-                        cmac2(acc, rec[0][rr][cmap<R>(A, B)], ld_stream(t1 + 4 * B + C));
-                    }
-                } else {
-#pragma unroll
-                    for (int D = 0; D < 4; ++D) {
-                        cmac2(acc, ld_stream(t0 + 4 * A + D), rec[0][rr][cmap<R>(D, C)]);
-                        cmac2(acc, ld_stream(t1 + 4 * A + D), rec[NS - 1][rr][cmap<R>(D, C)]);
+                        for (int A = 0; A < 4; ++A) {
+                            const float4 p = tr[2 * A + (Xe[e] >> 1)];
+                            cmac2(o[e][A], (Xe[e] & 1) ? make_float2(p.z, p.w) : make_float2(p.x, p.y), rv);
+                        }
                     }
                 }
             }
         }
         __syncthreads();
     }
-    k2_tail<RIGHT, R>(V, G, J, Ssum, Ntil, out, odt, wi, vi, w, ve, acc, rec, red);
+    // 3. sum over the four node groups of a warp, then over the lanes and warps that hold
+    // parts of the same output
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float2 v = o[e][c];
+            v.x += __shfl_xor_sync(0xffffffffu, v.x, 8);
+            v.y += __shfl_xor_sync(0xffffffffu, v.y, 8);
+            v.x += __shfl_xor_sync(0xffffffffu, v.x, 16);
+            v.y += __shfl_xor_sync(0xffffffffu, v.y, 16);
+            o[e][c] = v;
+        }
+    float2* part = reinterpret_cast<float2*>(k2_smem);                   // [warp][l][e][4]
+    if (gi == 0) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) part[((wp * 8 + l) * 2 + e) * 4 + c] = o[e][c];
+    }
+    __syncthreads();
+    float2 acc = make_float2(0.f, 0.f);
+    if (tid < 16) {
+        const int A = tid >> 2, C = tid & 3;
+        for (int ll = 0; ll < 8; ++ll)
+            for (int e = 0; e < 2; ++e) {
+                int xy = 0;
+                for (int q = 0; q < 16; ++q)
+                    if (cmap<R>(q >> 2, q & 3) == 2 * ll + e) xy = q;
+                const bool mine = RIGHT ? ((xy & 3) == C) : ((xy >> 2) == A);
+                if (!mine) continue;
+                const int c = RIGHT ? A : C;
+                for (int ww = 0; ww < 4; ++ww) {
+                    const float2 v = part[((ww * 8 + ll) * 2 + e) * 4 + c];
+                    acc.x += v.x;
+                    acc.y += v.y;
+                }
+            }
+    }
+    __syncthreads();
+    k2_tail<RIGHT, R>(V, G, J, Ssum, Ntil, out, odt, wi, vi, w, ve, acc,
+                      reinterpret_cast<float2 (*)[128][17]>(k2_smem), red);
 }
 
 // K2 / K2' from the record cache (k_mx_cache_k2): the same sums as k_mx_k2, with each
@@ -949,6 +1041,23 @@ static MixedLayout mixed_layout(const kb_ctx* ctx, int r, unsigned mask) {
 
 size_t kb_mixed_workspace_need(const kb_ctx* ctx, int r, unsigned mask) { return mixed_layout(ctx, r, mask).need; }
 
+// One-time per device (not a stream operation, so done before any capture): the dynamic
+// shared memory of the K2 gather beyond the default 48 KB.
+static bool mixed_prepare(int device) {
+    static bool done[64] = {};
+    if (device < 0 || device >= 64) return false;
+    if (done[device]) return true;
+    bool ok = true;
+    ok = ok && cudaFuncSetAttribute(k_mx_k2<false, KB_CH_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)k2_smem_bytes<KB_CH_T>()) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_mx_k2<true, KB_CH_T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)k2_smem_bytes<KB_CH_T>()) == cudaSuccess;
+    done[device] = ok;
+    return ok;
+}
+
+bool kb_mixed_prepare(int device) { return mixed_prepare(device); }
+
 template <int r>
 static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, unsigned mask, double alpha, double beta,
                             cudaStream_t st) {
@@ -978,6 +1087,10 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
     const size_t ntab = (size_t)g.n1 + g.n2w + g.n2v + g.n3w + g.n3v + g.nq;
     kb_status s = kb_ensure_workspace(ctx, Lo.need);
     if (s != KB_OK) return s;
+    if (!mixed_prepare(ctx->device)) {
+        ctx->err = "mixed path: cannot set the K2 gather's shared-memory size";
+        return KB_ERR_CUDA;
+    }
     char* ws = static_cast<char*>(ctx->ws.ptr);
     df* tab = reinterpret_cast<df*>(ws + off_tab);
     float2* Nt = reinterpret_cast<float2*>(ws + off_N);
@@ -1038,7 +1151,8 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
                                                            cacheL);
             } else {
                 KB_LAUNCH(ctx, st, "k_mx_k2");
-                k_mx_k2<false, r><<<grid, 128, 0, st>>>(VL, G, J, Nt, Ss, Ntl, o, VO.dt[r][KB_K2], w_off, v_off);
+                k_mx_k2<false, r><<<grid, 128, k2_smem_bytes<r>(), st>>>(VL, G, J, Nt, Ss, Ntl, o, VO.dt[r][KB_K2],
+                                                                         w_off, v_off);
             }
         }
         if (!sym && ((mask >> KB_K2P) & 1)) {
@@ -1049,7 +1163,8 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
                                                                         0, cacheR);
             } else {
                 KB_LAUNCH(ctx, st, "k_mx_k2p");
-                k_mx_k2<true, r><<<dim3(g.n2v, g.n2w), 128, 0, st>>>(VR, G, J, Mt, Ss, Ntl, o, VO.dt[r][KB_K2P], 0, 0);
+                k_mx_k2<true, r><<<dim3(g.n2v, g.n2w), 128, k2_smem_bytes<r>(), st>>>(VR, G, J, Mt, Ss, Ntl, o,
+                                                                                      VO.dt[r][KB_K2P], 0, 0);
             }
         }
     }

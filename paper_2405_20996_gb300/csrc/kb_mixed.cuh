@@ -138,6 +138,18 @@ struct VertexF {
     float bare;
 };
 
+// Class pointer of channel ch (a runtime value) without indexing the parameter struct at run
+// time, which would copy it to local memory: a chain of selects over the 12 entries.
+__device__ __forceinline__ const float2* vcls(const VertexF& V, int ch, int k) {
+    const float2* p = nullptr;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (c == ch && q == k) p = V.cls[c][q];
+    return p;
+}
+
 // Corners of one class: nd dimensions with lower nodes kk[d], fractions tt[d] and sizes N[d]
 // (row-major data, 16 complex components per record); the corner code exists once.
 __device__ __forceinline__ void corners(const float2* __restrict__ D, int nd, int k0, int k1, int k2, float t0,
@@ -216,10 +228,10 @@ __device__ __forceinline__ Sten7 stencils7(const VertexF& V, int ch, unsigned cl
     const bool fw = isfinite(gw.h), fv = isfinite(gv.h), fp = isfinite(gp.h);
     const float ia = 1.f / G.A;
     const float xw = fw ? x_est(gw.h, ia) : 0.f, xv = fv ? x_est(gv.h, ia) : 0.f, xp = fp ? x_est(gp.h, ia) : 0.f;
-    S.u0 = (classes & 1) && V.cls[ch][0] && fw;
-    S.u1 = (classes & 2) && V.cls[ch][1] && fw && fv;
-    S.u2 = (classes & 4) && V.cls[ch][2] && fw && fp;
-    S.u3 = (classes & 8) && V.cls[ch][3] && fw && fv && fp;
+    S.u0 = (classes & 1) && vcls(V, ch, 0) && fw;
+    S.u1 = (classes & 2) && vcls(V, ch, 1) && fw && fv;
+    S.u2 = (classes & 4) && vcls(V, ch, 2) && fw && fp;
+    S.u3 = (classes & 8) && vcls(V, ch, 3) && fw && fv && fp;
     S.tw1 = S.tw2 = S.tw3 = S.tv2 = S.tv3 = S.tp2 = S.tp3 = 0.f;
     S.kw1 = S.kw2 = S.kw3 = S.kv2 = S.kv3 = S.kp2 = S.kp3 = 0;
     if (S.u0) S.kw1 = stencil_x(gw, xw, G.n1, G.N1, G.A, S.tw1);
@@ -236,10 +248,10 @@ __device__ __forceinline__ Sten7 stencils7(const VertexF& V, int ch, unsigned cl
 
 __device__ __forceinline__ void apply7(const VertexF& V, int ch, const Sten7& S, const DfGrids& G, float f, bool sw,
                                        float2 out[16]) {
-    if (S.u0) corners(V.cls[ch][0], 1, S.kw1, 0, 0, S.tw1, 0.f, 0.f, G.N1, 1, 1, f, sw, out);
-    if (S.u1) corners(V.cls[ch][1], 2, S.kw2, S.kv2, 0, S.tw2, S.tv2, 0.f, G.N2w, G.N2v, 1, f, sw, out);
-    if (S.u2) corners(V.cls[ch][2], 2, S.kw2, S.kp2, 0, S.tw2, S.tp2, 0.f, G.N2w, G.N2v, 1, f, sw, out);
-    if (S.u3) corners(V.cls[ch][3], 3, S.kw3, S.kv3, S.kp3, S.tw3, S.tv3, S.tp3, G.N3w, G.N3v, G.N3v, f, sw, out);
+    if (S.u0) corners(vcls(V, ch, 0), 1, S.kw1, 0, 0, S.tw1, 0.f, 0.f, G.N1, 1, 1, f, sw, out);
+    if (S.u1) corners(vcls(V, ch, 1), 2, S.kw2, S.kv2, 0, S.tw2, S.tv2, 0.f, G.N2w, G.N2v, 1, f, sw, out);
+    if (S.u2) corners(vcls(V, ch, 2), 2, S.kw2, S.kp2, 0, S.tw2, S.tp2, 0.f, G.N2w, G.N2v, 1, f, sw, out);
+    if (S.u3) corners(vcls(V, ch, 3), 3, S.kw3, S.kv3, S.kp3, S.tw3, S.tv3, S.tp3, G.N3w, G.N3v, G.N3v, f, sw, out);
 }
 
 // Parts of the vertex relative to channel r at r-variables (w, v, vp), FP32 accumulation.
@@ -315,6 +327,151 @@ __device__ __forceinline__ void vertex_part_f32(const VertexF& V, const DfGrids&
         }
         Sten7 S = stencils7(V, ch, classes, G, gw, gv, gp);
         apply7(V, ch, S, G, f, sw, out);
+    }
+}
+
+
+// ------------------------------------------------------------------------------------
+// Other channels' part of a vertex seen from channel r, by lookup group.
+// ------------------------------------------------------------------------------------
+
+// Channel read by lookup group g of channel r (compile time): g = 0, 1 the two channels
+// c != r, direct; g = 2, 3 their exchanged partners (crossing partner a <-> t, p -> p).
+template <int r, int g>
+__host__ __device__ constexpr int group_channel() {
+    return g < 2 ? ((g & 1) ? (r == KB_CH_T ? KB_CH_P : KB_CH_T) : (r == KB_CH_A ? KB_CH_P : KB_CH_A))
+                 : ((g & 1) ? (r == KB_CH_T ? KB_CH_P : KB_CH_A)
+                            : (r == KB_CH_A ? KB_CH_P : KB_CH_T));
+}
+// The channel c != r whose inclusion in the vertex decides group g.
+template <int r, int g>
+__host__ __device__ constexpr int group_source() {
+    return (g & 1) ? (r == KB_CH_T ? KB_CH_P : KB_CH_T) : (r == KB_CH_A ? KB_CH_P : KB_CH_A);
+}
+
+// Component of the looked-up record that lands on component c under the exchange of the
+// Keldysh indices a1 <-> a2 (bits 1 and 0 of c); an involution.
+__host__ __device__ constexpr int kswap12(int c) { return (c & 12) | ((c & 1) << 1) | ((c >> 1) & 1); }
+
+// ------------------------------------------------------------------------------------
+// Corner lists: the interpolation of a lookup written out as (record index, weight) pairs
+// by the thread that found the stencil, read by the lanes that hold the record components.
+// ------------------------------------------------------------------------------------
+
+// The 18 corners of one channel's classes from its stencils: K1 (k = 0, 1), K2 (2 .. 5), K2'
+// (6 .. 9), K3 (10 .. 17), as (record index in the class array, weight bits), times f; a
+// corner outside its grid, of an absent class or of zero weight gets index -1.
+__device__ __forceinline__ void corner_list18(const Sten7& S, const DfGrids& G, float f, int2* dst, int stride) {
+    auto put = [&](int k, bool ok, int off, float wgt) {
+        const bool use = ok && wgt != 0.f;
+        dst[k * stride] = make_int2(use ? off : -1, __float_as_int(use ? wgt : 0.f));
+    };
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+        put(c, S.u0 && (c ? S.kw1 + 1 < G.N1 : S.kw1 >= 0), S.kw1 + c, f * (c ? S.tw1 : 1.f - S.tw1));
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int bw = c & 1, bv = c >> 1;
+        const bool okw = bw ? S.kw2 + 1 < G.N2w : S.kw2 >= 0;
+        const float fw = f * (bw ? S.tw2 : 1.f - S.tw2);
+        put(2 + c, S.u1 && okw && (bv ? S.kv2 + 1 < G.N2v : S.kv2 >= 0), (S.kw2 + bw) * G.N2v + S.kv2 + bv,
+            fw * (bv ? S.tv2 : 1.f - S.tv2));
+        put(6 + c, S.u2 && okw && (bv ? S.kp2 + 1 < G.N2v : S.kp2 >= 0), (S.kw2 + bw) * G.N2v + S.kp2 + bv,
+            fw * (bv ? S.tp2 : 1.f - S.tp2));
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int bw = c & 1, bv = (c >> 1) & 1, bp = c >> 2;
+        const bool ok = S.u3 && (bw ? S.kw3 + 1 < G.N3w : S.kw3 >= 0) && (bv ? S.kv3 + 1 < G.N3v : S.kv3 >= 0) &&
+                        (bp ? S.kp3 + 1 < G.N3v : S.kp3 >= 0);
+        const float wg = f * (bw ? S.tw3 : 1.f - S.tw3) * (bv ? S.tv3 : 1.f - S.tv3) * (bp ? S.tp3 : 1.f - S.tp3);
+        put(10 + c, ok, ((S.kw3 + bw) * G.N3v + S.kv3 + bv) * G.N3v + S.kp3 + bp, wg);
+    }
+}
+
+__device__ __forceinline__ void no_corners18(int2* dst, int stride) {
+#pragma unroll
+    for (int k = 0; k < 18; ++k) dst[k * stride] = make_int2(-1, 0);
+}
+
+// Corner list of lookup group G of the other channels' part seen from channel r at the
+// r-variables (w, v, vp) (an exchanged group carries the factor -1; its Keldysh index swap
+// a1 <-> a2 is applied by the reader).
+template <int r, int G>
+__device__ __forceinline__ void group_corners(const VertexF& V, const DfGrids& Gr, df w, df v, df vp, int2* dst,
+                                              int stride) {
+    constexpr int c = group_source<r, G>(), ch = group_channel<r, G>();
+    if (!((V.mask >> c) & 1)) { no_corners18(dst, stride); return; }
+    df L[4];
+    df_legs(r, w, v, vp, L);
+    df gw, gv, gp;
+    if (G < 2) {
+        df_vars(c, L, gw, gv, gp);
+    } else {
+        df S4[4] = {L[0], L[1], L[3], L[2]};
+        df_vars(ch, S4, gw, gv, gp);
+    }
+    corner_list18(stencils7(V, ch, 15, Gr, gw, gv, gp), Gr, G < 2 ? 1.f : -1.f, dst, stride);
+}
+
+// The same with the group (and so the channel) known only at run time: one copy of the
+// stencil code serves every group (four inlined copies measured slower, from instruction
+// fetch), the class pointers are selected without indexing the parameter struct.
+template <int r>
+__device__ __forceinline__ void group_corners_rt(const VertexF& V, const DfGrids& Gr, int g, df w, df v, df vp,
+                                                 int2* dst, int stride) {
+    const int c = (g & 1) ? ((r == KB_CH_T) ? KB_CH_P : KB_CH_T) : ((r == KB_CH_A) ? KB_CH_P : KB_CH_A);
+    if (!((V.mask >> c) & 1)) { no_corners18(dst, stride); return; }
+    df L[4];
+    df_legs(r, w, v, vp, L);
+    df gw, gv, gp;
+    int ch = c;
+    if (g < 2) {
+        df_vars(c, L, gw, gv, gp);
+    } else {
+        ch = (c == KB_CH_A) ? KB_CH_T : (c == KB_CH_T ? KB_CH_A : KB_CH_P);
+        df S4[4] = {L[0], L[1], L[3], L[2]};
+        df_vars(ch, S4, gw, gv, gp);
+    }
+    corner_list18(stencils7(V, ch, 15, Gr, gw, gv, gp), Gr, g < 2 ? 1.f : -1.f, dst, stride);
+}
+
+// Corner class of corner k of a corner list.
+__host__ __device__ constexpr int corner_class(int k) { return k < 2 ? 0 : (k < 6 ? 1 : (k < 10 ? 2 : 3)); }
+
+// Gather of one corner list by a group of 8 lanes: lane l accumulates components 2l, 2l+1
+// (one 16-byte piece of every corner record), acc += sum_k w_k rec_k[2l .. 2l+1], so that one
+// warp-wide load delivers the full records of the 4 nodes its lane groups hold.
+template <int ch>
+__device__ __forceinline__ void gather_list(const VertexF& V, const int2* __restrict__ cl, int stride, int l,
+                                            float2& a0, float2& a1) {
+#pragma unroll
+    for (int k = 0; k < 18; ++k) {
+        const int2 cw = cl[k * stride];
+        if (cw.x >= 0) {
+            const float4 u = __ldg(reinterpret_cast<const float4*>(V.cls[ch][corner_class(k)]) + (size_t)cw.x * 8 + l);
+            const float2 wv = make_float2(__int_as_float(cw.y), __int_as_float(cw.y));
+            a0 = __ffma2_rn(wv, make_float2(u.x, u.y), a0);
+            a1 = __ffma2_rn(wv, make_float2(u.z, u.w), a1);
+        }
+    }
+}
+
+// The same for an exchanged group: lane l takes components kswap12(2l), kswap12(2l+1).
+template <int ch>
+__device__ __forceinline__ void gather_list_x(const VertexF& V, const int2* __restrict__ cl, int stride, int l,
+                                              float2& a0, float2& a1) {
+    const int s0 = kswap12(2 * l), s1 = kswap12(2 * l + 1);
+#pragma unroll
+    for (int k = 0; k < 18; ++k) {
+        const int2 cw = cl[k * stride];
+        if (cw.x >= 0) {
+            const float2* rec = V.cls[ch][corner_class(k)] + (size_t)cw.x * 16;
+            const float2 u0 = __ldg(rec + s0), u1 = __ldg(rec + s1);
+            const float2 wv = make_float2(__int_as_float(cw.y), __int_as_float(cw.y));
+            a0 = __ffma2_rn(wv, u0, a0);
+            a1 = __ffma2_rn(wv, u1, a1);
+        }
     }
 }
 
