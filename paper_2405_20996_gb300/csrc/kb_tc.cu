@@ -137,15 +137,31 @@ struct TcJob {
     int M, N, K, batch, mtiles, ntiles, ksplit, chunks_per_split, nchunks;
 };
 
-// Segmented accumulation: tensor memory holds two buffers of one 128 x NT FP32
-// accumulator (the CTA's part); the MMA warp restarts a buffer every SEG K chunks and the
-// epilogue warps add each finished segment into compensated (Kahan) FP32 running sums held
-// in registers, so no plain FP32 accumulator ever sums more than SEG * KC * 6 / 8 products.
+// Segmented accumulation: tensor memory holds two buffers of the CTA's 128 x 128 FP32
+// accumulators; the MMA warp restarts a buffer every SEG K chunks and the epilogue warps add
+// each finished segment into compensated (Kahan) FP32 running sums held in registers, so no
+// plain FP32 accumulator ever sums more than SEG * KC * 6 / 8 products.
+// Two tile shapes (template BOTH):
+//   BOTH = false  one CTA per real or imaginary part of a 128 x 128 complex tile, N = 128
+//                 MMAs (6 per k-step); the Re and Im CTAs of a tile each load all 8 planes;
+//   BOTH = true   one CTA for both parts of a 128 x 64 complex tile, N = 64 MMAs (12 per
+//                 k-step) into a real and an imaginary accumulator, so every operand byte
+//                 is loaded once per tile.
+// Both hold 128 x 128 running sums per CTA (the register budget of the Kahan epilogue).
 constexpr int SEG = 2;
-constexpr int NTT = 128;                      // N columns per CTA
 constexpr int EPI_WARPS = 16;                 // 4 per TMEM lane quarter, 32 columns each
 constexpr int NTHREADS_S = 64 + 32 * EPI_WARPS;
-constexpr int STAGES_S = 3;
+
+template <bool BOTH>
+struct TcShape {
+    static constexpr int NT = BOTH ? 64 : 128;            // B rows (complex columns) per CTA
+    static constexpr int STAGES = BOTH ? 4 : 3;
+    static constexpr uint32_t A_PLANE = MT * KC * 4;      // 8 KB
+    static constexpr uint32_t B_PLANE = NT * KC * 4;      // 4 or 8 KB
+    static constexpr uint32_t STAGE = 4 * A_PLANE + 4 * B_PLANE;
+    static constexpr int PARTS = BOTH ? 1 : 2;            // CTAs per tile
+    static constexpr size_t smem() { return (size_t)STAGES * STAGE + 128 + 1024; }
+};
 
 // Compensated (Kahan) summation of two columns at once with packed FP32 operations:
 // s is the running sum, n the negated compensation (the rounding error still to be added).
@@ -161,13 +177,13 @@ __device__ __forceinline__ void kahan2(float2& s, float2& n, float2 x) {
 }
 
 // partial sums P[ks][b][M][N] double2
+template <bool BOTH>
 __global__ void __maxnreg__(96)
     k_tc_k3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcJob J,
             double2* __restrict__ P) {
-    constexpr int NT = NTT;
-    constexpr uint32_t A_PLANE = MT * KC * 4;      // 8 KB
-    constexpr uint32_t B_PLANE = NT * KC * 4;      // 8 KB
-    constexpr uint32_t STAGE = 4 * A_PLANE + 4 * B_PLANE;
+    using S = TcShape<BOTH>;
+    constexpr int NT = S::NT, STAGES_S = S::STAGES;
+    constexpr uint32_t A_PLANE = S::A_PLANE, B_PLANE = S::B_PLANE, STAGE = S::STAGE;
     constexpr uint32_t TMEM_COLS = 256;            // 2 buffers x 128 columns
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -178,9 +194,9 @@ __global__ void __maxnreg__(96)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(segempty + 2);
     __shared__ volatile int s_fail;
 
-    // neighbouring CTAs: even the real part, odd the imaginary part of one tile
-    const int part = blockIdx.x & 1;
-    int unit = blockIdx.x >> 1;
+    // BOTH = false: neighbouring CTAs are the real and the imaginary part of one tile
+    const int part = BOTH ? 0 : (blockIdx.x & 1);
+    int unit = BOTH ? blockIdx.x : (blockIdx.x >> 1);
     int ks = unit % J.ksplit;
     int rest = unit / J.ksplit;
     int nt = rest % J.ntiles;
@@ -250,7 +266,7 @@ __global__ void __maxnreg__(96)
                 }
                 if (!mbar_wait(&full[s], ph)) { atomicOr(&g_tc_status, 2); s_fail = 1; break; }
                 fence_after();
-                const uint32_t dacc = tbase + buf * NT;
+                const uint32_t dacc = tbase + buf * 128;
                 uint32_t sa = smem_u32(smem + s * STAGE);
                 uint32_t sb = sa + 4 * A_PLANE;
 #pragma unroll
@@ -261,20 +277,22 @@ __global__ void __maxnreg__(96)
                     uint64_t brh = sdesc_sw64(sb + 0 * B_PLANE + off), brl = sdesc_sw64(sb + 1 * B_PLANE + off);
                     uint64_t bih = sdesc_sw64(sb + 2 * B_PLANE + off), bil = sdesc_sw64(sb + 3 * B_PLANE + off);
                     uint32_t first = (seg_start && kk == 0) ? 0u : 1u;
-                    if (part == 0) {          // Re = Ar Br - Ai Bi
+                    if (BOTH || part == 0) {   // Re = Ar Br - Ai Bi
                         mma_tf32(dacc, arh, brh, id_pos, first);
                         mma_tf32(dacc, arh, brl, id_pos, 1);
                         mma_tf32(dacc, arl, brh, id_pos, 1);
                         mma_tf32(dacc, aih, bih, id_neg, 1);
                         mma_tf32(dacc, aih, bil, id_neg, 1);
                         mma_tf32(dacc, ail, bih, id_neg, 1);
-                    } else {                  // Im = Ar Bi + Ai Br
-                        mma_tf32(dacc, arh, bih, id_pos, first);
-                        mma_tf32(dacc, arh, bil, id_pos, 1);
-                        mma_tf32(dacc, arl, bih, id_pos, 1);
-                        mma_tf32(dacc, aih, brh, id_pos, 1);
-                        mma_tf32(dacc, aih, brl, id_pos, 1);
-                        mma_tf32(dacc, ail, brh, id_pos, 1);
+                    }
+                    if (BOTH || part == 1) {   // Im = Ar Bi + Ai Br
+                        const uint32_t di = BOTH ? dacc + 64 : dacc;
+                        mma_tf32(di, arh, bih, id_pos, first);
+                        mma_tf32(di, arh, bil, id_pos, 1);
+                        mma_tf32(di, arl, bih, id_pos, 1);
+                        mma_tf32(di, aih, brh, id_pos, 1);
+                        mma_tf32(di, aih, brl, id_pos, 1);
+                        mma_tf32(di, ail, brh, id_pos, 1);
                     }
                 }
                 mma_commit(&empty[s]);                   // the stage is free once its MMAs are done
@@ -282,7 +300,8 @@ __global__ void __maxnreg__(96)
             }
         }
     } else {
-        // epilogue warps 2 .. 2+EPI_WARPS-1: lane quarter q, 32-column group cg
+        // epilogue warps 2 .. 2+EPI_WARPS-1: lane quarter q, 32-column group cg of the 128
+        // accumulator columns (BOTH: cg 0, 1 real, 2, 3 imaginary part of 64 columns)
         int e = warp - 2;
         int q = warp & 3, cg = e >> 2;
         float2 sm[16], ng[16];       // columns (2i, 2i+1): running sums and negated compensations
@@ -295,7 +314,7 @@ __global__ void __maxnreg__(96)
                 atomicOr(&g_tc_status, 4); ok = false; break;
             }
             fence_after();
-            uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * NT + cg * 32);
+            uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 128 + cg * 32);
             // two 16-column loads, one wait each
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -309,9 +328,10 @@ __global__ void __maxnreg__(96)
         }
         int row = mt * MT + q * 32 + lane;
         if (ok && row < J.M) {
-            // this CTA's part (.x real / .y imaginary) of the FP64 partial
-            double* out = reinterpret_cast<double*>(P + (((size_t)ks * J.batch + b) * J.M + row) * J.N) + part;
-            int col0 = nt * NT + cg * 32;
+            // the FP64 partial: .x real / .y imaginary part of this CTA's columns
+            const int pp = BOTH ? (cg >> 1) : part;
+            double* out = reinterpret_cast<double*>(P + (((size_t)ks * J.batch + b) * J.M + row) * J.N) + pp;
+            int col0 = nt * NT + (BOTH ? (cg & 1) : cg) * 32;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 if (col0 + 2 * i < J.N) out[2 * (col0 + 2 * i)] = (double)sm[i].x + (double)ng[i].x;
@@ -370,34 +390,41 @@ static bool make_map(CUtensorMap* m, const float* base, int K, int rows, int pla
     return r == CUDA_SUCCESS;
 }
 
-static size_t tc_smem_bytes() {
-    constexpr size_t STAGE = 4 * MT * KC * 4 + 4 * NTT * KC * 4;
-    return STAGES_S * STAGE + 128 + 1024;
-}
-
-// One-time per device: opt the kernel in to its dynamic shared memory (not a stream
-// operation, so it is done before any capture) and resolve the tensor-map encoder.
+// One-time per device: opt both kernel shapes in to their dynamic shared memory (not a
+// stream operation, so it is done before any capture) and resolve the tensor-map encoder.
 static bool tc_prepare(int device) {
     static bool attr_set[64] = {};
     if (device < 0 || device >= 64) return false;
     if (!attr_set[device]) {
-        if (cudaFuncSetAttribute(k_tc_k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes()) !=
-            cudaSuccess)
+        if (cudaFuncSetAttribute(k_tc_k3<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TcShape<true>::smem()) != cudaSuccess ||
+            cudaFuncSetAttribute(k_tc_k3<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TcShape<false>::smem()) != cudaSuccess)
             return false;
         attr_set[device] = true;
     }
     return encoder() != nullptr;
 }
 
-// Split-K candidates for one contraction shape, best first by the wave model: a split s
-// gives base * s CTAs (base = batch x tiles x 2 parts) of at least 8 segments of K each,
-// whose partial sums must fit the scratch; the model rates the fraction of the last wave
-// that is busy, with a small charge per split for the reduction.
-static std::vector<int> split_candidates(int device, int M, int N, int K, int batch, size_t scratch_bytes) {
+// A launch shape of the contraction: the tile shape (1: both parts per CTA, 128 x 64
+// complex; 0: one part per CTA, 128 x 128) and the split-K factor.
+struct TcPlan {
+    int both, split;
+};
+
+static int tc_cols(int both) { return both ? TcShape<true>::NT : TcShape<false>::NT; }
+static int tc_parts(int both) { return both ? TcShape<true>::PARTS : TcShape<false>::PARTS; }
+
+// Split-K candidates for one contraction shape and tile shape, best first by the wave
+// model: a split s gives base * s CTAs (base = batch x tiles x CTAs per tile) of at least 8
+// segments of K each, whose partial sums must fit the scratch; the model rates the fraction
+// of the last wave that is busy, with a small charge per split for the reduction.
+static std::vector<std::pair<double, int>> split_candidates(int device, int both, int M, int N, int K, int batch,
+                                                            size_t scratch_bytes) {
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    const int mtiles = (M + MT - 1) / MT, ntiles = (N + NTT - 1) / NTT, nchunks = (K + KC - 1) / KC;
-    const long base = (long)batch * mtiles * ntiles * 2;
+    const int mtiles = (M + MT - 1) / MT, ntiles = (N + tc_cols(both) - 1) / tc_cols(both), nchunks = (K + KC - 1) / KC;
+    const long base = (long)batch * mtiles * ntiles * tc_parts(both);
     std::vector<std::pair<double, int>> c;
     for (int s = 1; s <= 64; ++s) {
         if ((nchunks + s - 1) / s < 8 * SEG) break;
@@ -405,103 +432,119 @@ static std::vector<int> split_candidates(int device, int M, int N, int K, int ba
         const long units = base * s, waves = (units + sms - 1) / sms;
         c.push_back({(double)units / (waves * sms) * (1.0 - 0.002 * s), s});
     }
-    if (c.empty()) return {1};
+    if (c.empty()) c.push_back({0.0, 1});
     std::stable_sort(c.begin(), c.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
         return a.first > b.first + 1e-9;
     });
-    std::vector<int> out;
-    for (auto& x : c) out.push_back(x.second);
-    return out;
+    return c;
 }
 
-// Autotuned splits, per device and shape (M, N, K, batch); filled by tc_tune.
-static std::mutex g_tune_mu;
-static std::map<std::array<int, 5>, int> g_tuned;
+// Default plan without timing: the tile shape from KB_TC_SHAPE (developer override) or both
+// parts per CTA, and the wave model's best split for it.
+static TcPlan default_plan(int device, int M, int N, int K, int batch, size_t scratch_bytes) {
+    const char* sh = std::getenv("KB_TC_SHAPE");
+    const int both = (sh && std::atoi(sh) == 0) ? 0 : 1;
+    return {both, split_candidates(device, both, M, N, K, batch, scratch_bytes)[0].second};
+}
 
-static int tuned_split(int device, int M, int N, int K, int batch) {
+// Autotuned plans, per device and shape (M, N, K, batch); filled by tc_tune.
+static std::mutex g_tune_mu;
+static std::map<std::array<int, 5>, TcPlan> g_tuned;
+
+static bool tuned_plan(int device, int M, int N, int K, int batch, TcPlan& p) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find({device, M, N, K, batch});
-    return it == g_tuned.end() ? 0 : it->second;
+    if (it == g_tuned.end()) return false;
+    p = it->second;
+    return true;
 }
 
-static bool launch_split(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
-                         void* scratch, int split, cudaStream_t st);
+static bool launch_plan(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
+                        void* scratch, TcPlan plan, cudaStream_t st);
 
 static bool launch(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
                    void* scratch, size_t scratch_bytes, cudaStream_t st) {
     const int nchunks = (K + KC - 1) / KC;
-    int best = tuned_split(ctx->device, M, N, K, batch);
-    if (best <= 0 || (size_t)best * batch * M * N * sizeof(double2) > scratch_bytes)
-        best = split_candidates(ctx->device, M, N, K, batch, scratch_bytes)[0];
+    TcPlan plan;
+    if (!tuned_plan(ctx->device, M, N, K, batch, plan) ||
+        (size_t)plan.split * batch * M * N * sizeof(double2) > scratch_bytes)
+        plan = default_plan(ctx->device, M, N, K, batch, scratch_bytes);
     const char* cps_env = std::getenv("KB_TC_CPS");   // developer override: K chunks per split
     if (cps_env && std::atoi(cps_env) > 0) {
         int cps = std::atoi(cps_env);
         int s = (nchunks + cps - 1) / cps;
-        if ((size_t)s * batch * M * N * sizeof(double2) <= scratch_bytes) best = s;
+        if ((size_t)s * batch * M * N * sizeof(double2) <= scratch_bytes) plan.split = s;
     }
-    return launch_split(ctx, At, Bt, Cm, M, N, K, batch, scratch, best, st);
+    return launch_plan(ctx, At, Bt, Cm, M, N, K, batch, scratch, plan, st);
 }
 
-// Time up to four of the wave model's best splits for this shape (the kernel and its
-// split-K reduction, two runs each, CUDA events on the stream) and remember the fastest.
-// Reads At/Bt and writes only the scratch and Cm, so any operands of the right shape do;
-// not while the stream is being captured.
+// Time the wave model's three best splits of each tile shape for this contraction shape
+// (the kernel and its split-K reduction, two runs each, CUDA events on the stream) and
+// remember the fastest plan.  Reads At/Bt and writes only the scratch and Cm, so any
+// operands of the right shape do; not while the stream is being captured.
 static bool tune(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
                  void* scratch, size_t scratch_bytes, cudaStream_t st) {
-    if (tuned_split(ctx->device, M, N, K, batch) > 0) return true;
+    TcPlan have;
+    if (tuned_plan(ctx->device, M, N, K, batch, have)) return true;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
-    std::vector<int> cand = split_candidates(ctx->device, M, N, K, batch, scratch_bytes);
-    if (cand.size() > 4) cand.resize(4);
+    std::vector<TcPlan> cand;
+    for (int both = 1; both >= 0; --both) {
+        auto c = split_candidates(ctx->device, both, M, N, K, batch, scratch_bytes);
+        for (size_t i = 0; i < c.size() && i < 3; ++i) cand.push_back({both, c[i].second});
+    }
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess) return false;
     if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return false; }
-    int best = cand[0];
+    TcPlan best = cand[0];
     float best_ms = 1e30f;
-    for (int s : cand) {
+    for (const TcPlan& pl : cand) {
         float ms_min = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
             cudaEventRecord(a, st);
-            if (!launch_split(ctx, At, Bt, Cm, M, N, K, batch, scratch, s, st)) { ms_min = 1e30f; break; }
+            if (!launch_plan(ctx, At, Bt, Cm, M, N, K, batch, scratch, pl, st)) { ms_min = 1e30f; break; }
             cudaEventRecord(b, st);
             if (cudaEventSynchronize(b) != cudaSuccess) { ms_min = 1e30f; break; }
             float ms = 0;
             cudaEventElapsedTime(&ms, a, b);
             ms_min = std::min(ms_min, ms);
         }
-        if (ms_min < best_ms) { best_ms = ms_min; best = s; }
+        if (ms_min < best_ms) { best_ms = ms_min; best = pl; }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (std::getenv("KB_TC_VERBOSE"))
-        std::fprintf(stderr, "k_tc_k3 autotune: M %d N %d K %d batch %d -> ksplit %d (%.3f ms)\n", M, N, K, batch,
-                     best, best_ms);
+        std::fprintf(stderr, "k_tc_k3 autotune: M %d N %d K %d batch %d -> %s ksplit %d (%.3f ms)\n", M, N, K, batch,
+                     best.both ? "re+im per CTA" : "one part per CTA", best.split, best_ms);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned[{ctx->device, M, N, K, batch}] = best;
     return true;
 }
 
-static bool launch_split(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
-                         void* scratch, int best, cudaStream_t st) {
+static bool launch_plan(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
+                        void* scratch, TcPlan plan, cudaStream_t st) {
     TcJob J;
     J.M = M; J.N = N; J.K = K; J.batch = batch;
+    const int cols = tc_cols(plan.both);
     J.mtiles = (M + MT - 1) / MT;
-    J.ntiles = (N + NTT - 1) / NTT;
+    J.ntiles = (N + cols - 1) / cols;
     J.nchunks = (K + KC - 1) / KC;
-    const int base = batch * J.mtiles * J.ntiles * 2;     // x 2: real and imaginary part
-    J.ksplit = best;
-    J.chunks_per_split = (J.nchunks + best - 1) / best;
+    const int base = batch * J.mtiles * J.ntiles * tc_parts(plan.both);
+    J.ksplit = plan.split;
+    J.chunks_per_split = (J.nchunks + plan.split - 1) / plan.split;
     if (std::getenv("KB_TC_VERBOSE"))
-        std::fprintf(stderr, "k_tc_k3: M %d N %d K %d batch %d tiles %dx%d ksplit %d chunks/split %d\n", M, N, K, batch,
-                     J.mtiles, J.ntiles, J.ksplit, J.chunks_per_split);
+        std::fprintf(stderr, "k_tc_k3: M %d N %d K %d batch %d tiles %dx%d (%s) ksplit %d chunks/split %d\n", M, N, K,
+                     batch, J.mtiles, J.ntiles, plan.both ? "re+im" : "part", J.ksplit, J.chunks_per_split);
     CUtensorMap ma, mb;
-    if (!make_map(&ma, At, K, M, 4 * batch, MT) || !make_map(&mb, Bt, K, N, 4 * batch, NTT)) return false;
-    size_t smem = tc_smem_bytes();
+    if (!make_map(&ma, At, K, M, 4 * batch, MT) || !make_map(&mb, Bt, K, N, 4 * batch, cols)) return false;
     if (!tc_prepare(ctx->device)) return false;
     double2* P = reinterpret_cast<double2*>(scratch);
     {
         KB_LAUNCH(ctx, st, "k_tc_k3");
-        k_tc_k3<<<(unsigned)(base * J.ksplit), NTHREADS_S, smem, st>>>(ma, mb, J, P);
+        if (plan.both)
+            k_tc_k3<true><<<(unsigned)(base * J.ksplit), NTHREADS_S, TcShape<true>::smem(), st>>>(ma, mb, J, P);
+        else
+            k_tc_k3<false><<<(unsigned)(base * J.ksplit), NTHREADS_S, TcShape<false>::smem(), st>>>(ma, mb, J, P);
     }
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) {
