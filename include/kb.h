@@ -197,8 +197,11 @@ kb_status kb_bubble_vjp(kb_ctx *ctx, int channel, int slot_left, int slot_right,
  * keeps the contexts and every attached array alive until kb_graph_destroy.  All contexts
  * must be on one device.  On failure nothing is kept and the message is in
  * kb_last_error of the context of the failing (or the first) descriptor.
- * kb_graph_launch enqueues one replay on `stream` (asynchronous, like kb_bubble);
- * kb_graph_kernel_count gives the kernels one replay runs.
+ * kb_graph_launch enqueues one replay on `stream` (asynchronous, like kb_bubble); it returns
+ * KB_ERR_STATE without launching once a context of the graph has replaced device memory the
+ * captured kernels address (its workspace grew for a larger bubble, kb_set_grids,
+ * kb_set_self_energy(_derivative), or a record cache was freed or re-allocated) — create
+ * the graph again then.  kb_graph_kernel_count gives the kernels one replay runs.
  * --------------------------------------------------------------------------------------- */
 typedef struct kb_graph kb_graph;
 
@@ -314,13 +317,29 @@ kb_status kb_set_autotune(kb_ctx *ctx, int on);
 /* Device workspace limit of a context in bytes (default 4 GiB, or the KB_WORKSPACE_MB
  * environment variable at kb_create).  Larger limits let the K3 contraction batch more
  * bosonic frequencies per launch; smaller ones bound memory when many contexts coexist.
- * Takes effect at the next call that sizes the workspace. */
+ * Takes effect at the next call that sizes the workspace.  The workspace grows on demand,
+ * stream-ordered on the calling stream (no device-wide synchronisation): a context's calls
+ * must therefore be ordered, one stream or streams the caller orders; inside a stream
+ * capture it cannot grow (KB_ERR_STATE), so size it first (kb_graph_create does). */
 kb_status kb_set_workspace_limit(kb_ctx *ctx, unsigned long long bytes);
 
 /* Synchronise the context's device and report device-side failures since the last check:
  * KB_ERR_TIMEOUT if a bounded wait inside a tensor-core kernel gave up (that kernel's output
  * is then incomplete), KB_ERR_CUDA for a CUDA error.  Clears the timeout flag. */
 kb_status kb_check_device(kb_ctx *ctx);
+
+/* Test hooks of the failure paths (no effect on results otherwise):
+ * kb_inject_alloc_failures: the next n workspace allocations of this context report
+ *   KB_ERR_OOM as a failed cudaMalloc would, before anything of that call is launched;
+ * kb_set_wait_budget: the clock-cycle budget of the bounded wait of kb_check_wait (0
+ *   restores the default, ~2 s); the tensor-core kernels keep their fixed budget of ~2 s;
+ * kb_check_wait: launches one CTA that waits, with that budget, on a shared-memory barrier
+ *   nothing arrives on — the wait gives up, the kernel records it in the device status and
+ *   returns; the next kb_check_device reports KB_ERR_TIMEOUT and clears it, and the context
+ *   stays usable.  It exercises the timeout path without any copy or MMA in flight. */
+kb_status kb_inject_alloc_failures(kb_ctx *ctx, int n);
+kb_status kb_set_wait_budget(kb_ctx *ctx, long long cycles);
+kb_status kb_check_wait(kb_ctx *ctx, void *stream);
 
 /* Bytes of device workspace the library currently holds (grows on demand). */
 kb_status kb_workspace_bytes(kb_ctx *ctx, unsigned long long *bytes);

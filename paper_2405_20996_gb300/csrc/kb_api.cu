@@ -72,16 +72,34 @@ static void gl5_nodes(int nq, std::vector<double>& x, std::vector<double>& w) {
 
 }  // namespace kb
 
-kb_status kb_ensure_workspace(kb_ctx* ctx, size_t bytes) {
+kb_status kb_ensure_workspace(kb_ctx* ctx, size_t bytes, cudaStream_t st, bool sync) {
     if (ctx->ws.bytes >= bytes) return KB_OK;
-    if (ctx->ws.ptr) {
-        cudaDeviceSynchronize();
-        cudaFree(ctx->ws.ptr);
-        ctx->ws.ptr = nullptr;
-        ctx->ws.bytes = 0;
+    if (ctx->fail_allocs > 0) {
+        --ctx->fail_allocs;
+        ctx->err = "workspace allocation failed (injected by kb_inject_alloc_failures)";
+        return KB_ERR_OOM;
     }
-    KB_CUDA_TRY(ctx, cudaMalloc(&ctx->ws.ptr, bytes));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (!sync && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+        ctx->err = "the workspace would have to grow inside a stream capture; size it before the capture";
+        return KB_ERR_STATE;
+    }
+    if (sync) {
+        KB_CUDA_TRY(ctx, cudaDeviceSynchronize());
+        st = nullptr;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->err = std::string("workspace allocation: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? KB_ERR_OOM : KB_ERR_CUDA;
+    }
+    if (ctx->ws.ptr) KB_CUDA_TRY(ctx, cudaFreeAsync(ctx->ws.ptr, st));
+    if (sync) KB_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    ctx->ws.ptr = p;
     ctx->ws.bytes = bytes;
+    ++ctx->mem_gen;
     return KB_OK;
 }
 
@@ -121,7 +139,10 @@ kb_status kb_destroy(kb_ctx* ctx) {
     cudaFree(ctx->d_wq);
     cudaFree(ctx->d_sig);
     cudaFree(ctx->d_dsig);
-    cudaFree(ctx->ws.ptr);
+    if (ctx->ws.ptr) {
+        cudaFreeAsync(ctx->ws.ptr, nullptr);
+        cudaDeviceSynchronize();
+    }
     for (int s = 0; s < KB_MAX_SLOTS; ++s) kb_vertex_cache_free(ctx, s);
     prof_clear(ctx);
     delete ctx;
@@ -140,6 +161,7 @@ kb_status kb_set_grids(kb_ctx* ctx, const kb_grid_desc* g) {
     kb::gl5_nodes(g->nq, x, w);
     cudaFree(ctx->d_xq);
     cudaFree(ctx->d_wq);
+    ++ctx->mem_gen;
     ctx->d_xq = ctx->d_wq = nullptr;
     KB_CUDA_TRY(ctx, cudaMalloc(&ctx->d_xq, sizeof(double) * g->nq));
     KB_CUDA_TRY(ctx, cudaMalloc(&ctx->d_wq, sizeof(double) * g->nq));
@@ -167,6 +189,7 @@ kb_status kb_set_model(kb_ctx* ctx, double Delta, double T, double eps) {
 kb_status kb_set_self_energy_derivative(kb_ctx* ctx, int n, double A, const double* dsigR, const double* dsigK) {
     if (!ctx) return KB_ERR_ARG;
     cudaSetDevice(ctx->device);
+    if (ctx->d_dsig) ++ctx->mem_gen;
     cudaFree(ctx->d_dsig);
     ctx->d_dsig = nullptr;
     ctx->m.n_dsig = 0;
@@ -208,6 +231,7 @@ kb_status kb_set_regulator(kb_ctx* ctx, int kind, double lambda) {
 kb_status kb_set_self_energy(kb_ctx* ctx, int n_sig, double A_sig, const double* sigR, const double* sigK) {
     if (!ctx) return KB_ERR_ARG;
     cudaSetDevice(ctx->device);
+    if (ctx->d_sig) ++ctx->mem_gen;
     cudaFree(ctx->d_sig);
     ctx->d_sig = nullptr;
     ctx->m.n_sig = 0;
@@ -381,6 +405,18 @@ kb_status kb_set_autotune(kb_ctx* ctx, int on) {
 kb_status kb_set_workspace_limit(kb_ctx* ctx, unsigned long long bytes) {
     if (!ctx || bytes < (1ull << 20)) return KB_ERR_ARG;
     ctx->ws_limit = (size_t)bytes;
+    return KB_OK;
+}
+
+kb_status kb_inject_alloc_failures(kb_ctx* ctx, int n) {
+    if (!ctx || n < 0) return KB_ERR_ARG;
+    ctx->fail_allocs = n;
+    return KB_OK;
+}
+
+kb_status kb_set_wait_budget(kb_ctx* ctx, long long cycles) {
+    if (!ctx || cycles < 0) return KB_ERR_ARG;
+    ctx->wait_budget = cycles;
     return KB_OK;
 }
 

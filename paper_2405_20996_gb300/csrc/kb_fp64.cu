@@ -176,7 +176,7 @@ kb_status kb_bubble_fp64(kb_ctx* ctx, int r, int sl, int sr, int so, int pi_kind
         size_t per_w;
         int chunk;
         fp64_chunking(ctx, r, cls, per_w, chunk);
-        s = kb_ensure_workspace(ctx, per_w * chunk);
+        s = kb_ensure_workspace(ctx, per_w * chunk, st);
         if (s != KB_OK) return s;
         char* base = static_cast<char*>(ctx->ws.ptr);
         double2* Pi = reinterpret_cast<double2*>(base);

@@ -17,6 +17,9 @@ struct kb_graph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<std::pair<kb_ctx*, unsigned long long>> launches;   // kernels per replay, per context
+    // each context's memory generation at capture: the graph's kernels hold its workspace,
+    // table and record-cache addresses, so it must not run once any of them was replaced
+    std::vector<std::pair<kb_ctx*, unsigned long long>> mem_gen;
     unsigned long long kernels = 0;
 };
 
@@ -77,7 +80,7 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
             if (s != KB_OK) return s;
         }
     for (auto& b : br) {
-        kb_status s = kb_ensure_workspace(b.ctx, b.need);
+        kb_status s = kb_ensure_workspace(b.ctx, b.need, nullptr, true);
         if (s != KB_OK) return s;
         s = kb_fp64_prepare(b.ctx);
         if (s != KB_OK) return s;
@@ -178,7 +181,11 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
         unsigned long long k = br[i].ctx->launches - br[i].launches0;
         br[i].ctx->launches = br[i].launches0;   // captured, not run
         br[i].ctx->prof_on = prof[i];
-        if (g) { g->launches.push_back({br[i].ctx, k}); g->kernels += k; }
+        if (g) {
+            g->launches.push_back({br[i].ctx, k});
+            g->mem_gen.push_back({br[i].ctx, br[i].ctx->mem_gen});
+            g->kernels += k;
+        }
     }
     if (st == KB_OK) {
         cudaError_t e = cudaGraphInstantiate(&g->exec, graph, 0);
@@ -201,6 +208,12 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
 
 kb_status kb_graph_launch(kb_graph* g, void* stream) {
     if (!g || !g->exec) return KB_ERR_ARG;
+    for (auto& p : g->mem_gen)
+        if (p.first->mem_gen != p.second) {
+            p.first->err = "kb_graph_launch: the context's workspace, tables or record caches changed since the "
+                           "capture; create the graph again";
+            return KB_ERR_STATE;
+        }
     if (cudaSetDevice(g->device) != cudaSuccess) return KB_ERR_CUDA;
     if (cudaGraphLaunch(g->exec, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess) return KB_ERR_CUDA;
     for (auto& p : g->launches) p.first->launches += p.second;

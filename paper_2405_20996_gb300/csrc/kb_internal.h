@@ -82,6 +82,11 @@ struct kb_ctx {
     std::string err;
     size_t ws_limit = 0;
     bool autotune = false;    // time the tensor-core contraction's split-K candidates per shape
+    // bumped whenever device memory that a captured step graph may reference (the workspace,
+    // a record cache) is freed or replaced; a graph refuses to launch after a change
+    unsigned long long mem_gen = 0;
+    int fail_allocs = 0;      // test hook: the next n workspace allocations report out of memory
+    long long wait_budget = 0; // clock cycles a bounded device wait may take (0: the default)
     bool prof_on = false;
     std::vector<kb_prof_rec> prof;
     // bumped by every change of a slot (and of the grids); a record cache is valid only for
@@ -137,7 +142,11 @@ kb_status kb_bubble_mixed(kb_ctx* ctx, int r, int sl, int sr, int so, int pi_kin
                           double beta, cudaStream_t st);
 kb_status kb_bubble_vjp_fp64(kb_ctx* ctx, int r, int sl, int sr, int sgo, int pi_kind, unsigned mask, double alpha,
                              int sgl, int sgr, void* const gGR[3], cudaStream_t st);
-kb_status kb_ensure_workspace(kb_ctx* ctx, size_t bytes);
+// Grow the context's workspace to at least `bytes`, stream-ordered on st (the old buffer is
+// released after the work already queued on st); sync = true first waits for the whole
+// device (used outside the bubble calls, where no stream orders the context's earlier work).
+// Refuses (KB_ERR_STATE) to grow while st is being captured.
+kb_status kb_ensure_workspace(kb_ctx* ctx, size_t bytes, cudaStream_t st, bool sync = false);
 // record caches (kb_mixed.cu): allocation (no launch, may cudaMalloc) and the build launch
 kb_status kb_vertex_cache_prepare(kb_ctx* ctx, int slot, int channel, unsigned sides);
 kb_status kb_vertex_cache_launch(kb_ctx* ctx, int slot, int channel, unsigned sides, cudaStream_t st);

@@ -1085,7 +1085,7 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
                  off_T = Lo.off_T, rows = Lo.rows, K = Lo.K, tc_scratch = Lo.tc_scratch;
     const int chunk = Lo.chunk;
     const size_t ntab = (size_t)g.n1 + g.n2w + g.n2v + g.n3w + g.n3v + g.nq;
-    kb_status s = kb_ensure_workspace(ctx, Lo.need);
+    kb_status s = kb_ensure_workspace(ctx, Lo.need, st);
     if (s != KB_OK) return s;
     if (!mixed_prepare(ctx->device)) {
         ctx->err = "mixed path: cannot set the K2 gather's shared-memory size";
@@ -1260,6 +1260,7 @@ kb_status kb_bubble_mixed(kb_ctx* ctx, int r, int sl, int sr, int so, int pi_kin
 
 void kb_vertex_cache_free(kb_ctx* ctx, int slot) {
     kb_ctx::RecCache& c = ctx->rc[slot];
+    if (c.ptr[0] || c.ptr[1] || c.ptr[2] || c.ptr[3]) ++ctx->mem_gen;
     for (int side = 0; side < 4; ++side) {
         if (c.ptr[side]) cudaFree(c.ptr[side]);
         c.ptr[side] = nullptr;
@@ -1289,7 +1290,10 @@ kb_status kb_vertex_cache_prepare(kb_ctx* ctx, int slot, int channel, unsigned s
         if (!((sides >> side) & 1)) continue;
         const size_t need = cache_side_bytes(ctx->g, channel, side);
         if (c.ptr[side] && c.bytes[side] == need) continue;
-        if (c.ptr[side]) cudaFree(c.ptr[side]);
+        if (c.ptr[side]) {
+            cudaFree(c.ptr[side]);
+            ++ctx->mem_gen;
+        }
         c.ptr[side] = nullptr;
         c.bytes[side] = 0;
         cudaError_t e = cudaMalloc(&c.ptr[side], need);
@@ -1305,7 +1309,7 @@ kb_status kb_vertex_cache_prepare(kb_ctx* ctx, int slot, int channel, unsigned s
     c.sides = sides;
     c.gen = ctx->slot_gen[slot];
     // the frequency tables (and, for the right K3 tile, the Π table) of the build
-    return kb_ensure_workspace(ctx, mixed_layout(ctx, channel, 0).off_T);
+    return kb_ensure_workspace(ctx, mixed_layout(ctx, channel, 0).off_T, nullptr, true);
 }
 
 template <int r>
@@ -1398,7 +1402,7 @@ kb_status kb_mixed_tune(kb_ctx* ctx, int r, int sl, int sr, unsigned mask, doubl
     const bool sym = (sl == sr) && ctx->slots[sl].symmetric && beta == 0.0 &&
                      (!((mask >> KB_K2P) & 1) || ((mask >> KB_K2) & 1)) && std::getenv("KB_NO_SYMMETRY") == nullptr;
     const MixedLayout Lo = mixed_layout(ctx, r, mask);
-    kb_status s = kb_ensure_workspace(ctx, Lo.need);
+    kb_status s = kb_ensure_workspace(ctx, Lo.need, st);
     if (s != KB_OK) return s;
     char* ws = static_cast<char*>(ctx->ws.ptr);
     float* TA = reinterpret_cast<float*>(ws + Lo.off_T);

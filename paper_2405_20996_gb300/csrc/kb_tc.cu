@@ -61,11 +61,11 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget = WAIT_BUDGET) {
     if (mbar_try(bar, parity)) return true;
     long long t0 = clock64();
     while (!mbar_try(bar, parity))
-        if (clock64() - t0 > WAIT_BUDGET) return false;
+        if (clock64() - t0 > budget) return false;
     return true;
 }
 
@@ -191,7 +191,8 @@ __global__ void __maxnreg__(96)
     uint64_t* empty = full + STAGES_S;
     uint64_t* segfull = empty + STAGES_S;       // [2]
     uint64_t* segempty = segfull + 2;           // [2]
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(segempty + 2);
+    uint64_t* drain = segempty + 2;             // [1] every MMA of this CTA has completed
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
     __shared__ volatile int s_fail;
 
     // BOTH = false: neighbouring CTAs are the real and the imaginary part of one tile
@@ -212,6 +213,7 @@ __global__ void __maxnreg__(96)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES_S; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
         for (int i = 0; i < 2; ++i) { mbar_init(&segfull[i], 1); mbar_init(&segempty[i], 32 * EPI_WARPS); }
+        mbar_init(drain, 1);
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -298,6 +300,10 @@ __global__ void __maxnreg__(96)
                 mma_commit(&empty[s]);                   // the stage is free once its MMAs are done
                 if ((i % SEG) == SEG - 1 || i == nck - 1) mma_commit(&segfull[buf]);
             }
+            // whether the loop finished or gave up: every MMA issued so far completes before
+            // the tensor memory is released at the end
+            mma_commit(drain);
+            if (!mbar_wait(drain, 0)) atomicOr(&g_tc_status, 2);
         }
     } else {
         // epilogue warps 2 .. 2+EPI_WARPS-1: lane quarter q, 32-column group cg of the 128
@@ -344,6 +350,17 @@ __global__ void __maxnreg__(96)
     fence_after();
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TMEM_COLS) : "memory");
+}
+
+// Bounded-wait probe: one thread waits, with the given budget, on a shared-memory barrier
+// that nothing arrives on; the wait gives up, the device status records it (bit 3) and the
+// kernel returns.  No copy or MMA is in flight, so giving up leaves nothing behind.
+__global__ void k_wait_probe(long long budget) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(&bar, 0, budget)) atomicOr(&g_tc_status, 8);
 }
 
 // C[b][m][n] = sum over splits of P (FP64)
@@ -581,6 +598,20 @@ bool kb_tc_tune(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int 
 }
 
 bool kb_tc_prepare(int device) { return kb::tc::tc_prepare(device); }
+
+extern "C" kb_status kb_check_wait(kb_ctx* ctx, void* stream) {
+    if (!ctx) return KB_ERR_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return KB_ERR_CUDA;
+    const long long budget = ctx->wait_budget > 0 ? ctx->wait_budget : kb::tc::WAIT_BUDGET;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    {
+        KB_LAUNCH(ctx, st, "k_wait_probe");
+        kb::tc::k_wait_probe<<<1, 32, 0, st>>>(budget);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { ctx->err = std::string("k_wait_probe launch: ") + cudaGetErrorString(e); return KB_ERR_CUDA; }
+    return KB_OK;
+}
 
 int kb_tc_take_status() {
     int v = 0, z = 0;

@@ -347,7 +347,7 @@ kb_status kb_bubble_vjp_fp64(kb_ctx* ctx, int r, int sl, int sr, int sgo, int pi
         size_t tileL = (size_t)4 * nL * K, tileR = (size_t)4 * nR * K, nGb = (size_t)16 * nL * nR;
         size_t per_w = ((size_t)g.nq * 16 * (want_gr ? 2 : 1) + 2 * tileL + 2 * tileR + nGb) * sizeof(double2);
         int chunk = (int)std::max<size_t>(1, std::min<size_t>(nw, ctx->ws_limit / per_w));
-        kb_status s = kb_ensure_workspace(ctx, per_w * chunk);
+        kb_status s = kb_ensure_workspace(ctx, per_w * chunk, st);
         if (s != KB_OK) return s;
         double2* Pi = static_cast<double2*>(ctx->ws.ptr);
         double2* Lt = Pi + (size_t)chunk * g.nq * 16;

@@ -78,6 +78,9 @@ _SIGS = {
     "kb_set_autotune": [C.c_void_p, C.c_int],
     "kb_workspace_bytes": [C.c_void_p, C.POINTER(C.c_ulonglong)],
     "kb_check_device": [C.c_void_p],
+    "kb_inject_alloc_failures": [C.c_void_p, C.c_int],
+    "kb_set_wait_budget": [C.c_void_p, C.c_longlong],
+    "kb_check_wait": [C.c_void_p, C.c_void_p],
     "kb_launch_count": [C.c_void_p, C.POINTER(C.c_ulonglong)],
     "kb_bubble_fp64_noalloc": [C.POINTER(kb_grid_desc), C.c_double, C.c_double, C.c_double,
                                C.POINTER(kb_vertex_desc), C.POINTER(kb_vertex_desc), C.c_int, C.c_int, C.c_int,
@@ -316,3 +319,15 @@ def kb_bubble_fp64_noalloc(grid, Delta, T, eps, left, right, channel, pi_kind, c
     """Allocation-free FP64 bubble of one class (see include/kb.h); returns the status."""
     return lib().kb_bubble_fp64_noalloc(C.byref(grid), Delta, T, eps, C.byref(left), C.byref(right), channel,
                                         pi_kind, cls, out_ptr, out_dtype, alpha, beta, stream)
+
+
+def kb_inject_alloc_failures(ctx, n):
+    _check(ctx, lib().kb_inject_alloc_failures(ctx, int(n)))
+
+
+def kb_set_wait_budget(ctx, cycles):
+    _check(ctx, lib().kb_set_wait_budget(ctx, int(cycles)))
+
+
+def kb_check_wait(ctx, stream=None):
+    _check(ctx, lib().kb_check_wait(ctx, stream))

@@ -90,3 +90,10 @@ def test_loop_rejected_without_context():
 
 def test_vertex_image_rejected_without_context():
     assert kb.lib().kb_vertex_image(None, 0, 0, 1, 15, None) == kb.KB_ERR_ARG
+
+
+def test_failure_hooks_reject_null_context():
+    L = kb.lib()
+    assert L.kb_inject_alloc_failures(None, 1) == kb.KB_ERR_ARG
+    assert L.kb_set_wait_budget(None, 0) == kb.KB_ERR_ARG
+    assert L.kb_check_wait(None, None) == kb.KB_ERR_ARG
