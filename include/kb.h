@@ -401,6 +401,21 @@ kb_status kb_bubble_fp64_noalloc(const kb_grid_desc *g, double Delta, double T, 
                                  int pi_kind, int cls, void *out, int out_dtype, double alpha, double beta,
                                  void *stream);
 
+/* Susceptibilities from the K1 class of channel `channel` of a slot (the paper's
+ * post-processing, Sec. II.E.5: K1_r = R χ_r R for a converged parquet vertex, R = -U/2 on
+ * the components with an odd number of quantum indices), on the K1 grid, into the DEVICE
+ * array `out` of n1 x 2 complex doubles [w][χ^R, χ^K]:
+ *   KB_CH_A  transverse spin, χ = -2 K1_a / U² on the retarded (component 1) and Keldysh (3)
+ *            blocks;
+ *   KB_CH_P  pairing, χ = +2 K1_p / U² (components 8 and 9);
+ *   KB_CH_T  charge, both spins of the pair: χ = 2 [K1_t(ω) + K1_t^uu(ω)] / U² with
+ *            K1_t^uu(ω) = K1_t(ω) - K1_a(-ω), a1 <-> a2 swapped (needs the slot's a-channel K1).
+ * At second order these are the bare bubbles (-Π_ph/2, Π_pp/2, -Π_ph/2).  With U = 1 the same
+ * readout gives the leg contraction from the K1 of a bubble chain closed by a unit bare vertex
+ * (R̂ Π R̂ + R̂ Π Γ Π R̂, built from kb_bubble calls).  K1 in c128 or c64; asynchronous on
+ * `stream`. */
+kb_status kb_susceptibility_k1(kb_ctx *ctx, int channel, int slot, double U, void *out, void *stream);
+
 /* Human-readable description of the last error on this context (never NULL). */
 const char *kb_last_error(kb_ctx *ctx);
 

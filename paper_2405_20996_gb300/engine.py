@@ -150,6 +150,36 @@ class Engine:
         kb.kb_loop(self.ctx, slot, which, v.shape[0], v.data_ptr(), out.data_ptr(), st)
         return out
 
+    def susceptibility(self, channel, slot, U, stream=None):
+        """χ^R(ω), χ^K(ω) on the K1 grid from the K1 class of a slot (kb_susceptibility_k1):
+        a transverse spin, p pairing, t charge; complex128 device tensor [n1][2]."""
+        out = torch.empty((self.grids["n1"], 2), dtype=torch.complex128, device=self.device)
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        kb.kb_susceptibility_k1(self.ctx, channel, slot, U, out.data_ptr(), st)
+        return out
+
+    def susceptibility_legs(self, channel, slot, precision="fp64", scratch=(13, 14, 15), stream=None):
+        """χ^R(ω), χ^K(ω) from the full vertex of a slot by contracting pairs of external legs
+        (Sec. II.E.5, channels a and p): the K1 of the chain R̂ Π R̂ + R̂ Π Γ Π R̂ closed by a unit
+        bare vertex R̂, from three bubbles — X = B_r(Γ, R̂) (only K1, K2 survive), then
+        B_r(R̂, R̂) + B_r(R̂, X) in K1 — read out like the vertex's own K1 at U = 1.  Uses the
+        three scratch slots for R̂, X and the chain."""
+        if channel not in (0, 1):
+            raise ValueError("the leg contraction is built for the a and p channels")
+        s_r, s_x, s_y = scratch
+        dt = torch.complex64 if precision == "mixed" else torch.complex128
+        kb.kb_set_vertex(self.ctx, s_r, True, 1.0)
+        kb.kb_set_vertex_symmetric(self.ctx, s_r, False)
+        self.tensors[s_r] = {}
+        self.alloc_out(s_x, channels=(channel,), dtype=dt, classes=(0, 1))
+        kb.kb_set_vertex_channels(self.ctx, s_x, 1 << channel)
+        self.alloc_out(s_y, channels=(channel,), dtype=dt, classes=(0,))
+        k1, k2 = 1 << kb.KB_K1, 1 << kb.KB_K2
+        self.bubble(channel, slot, s_r, s_x, class_mask=k1 | k2, precision=precision, stream=stream)
+        self.bubble(channel, s_r, s_r, s_y, class_mask=k1, precision=precision, stream=stream)
+        self.bubble(channel, s_r, s_x, s_y, class_mask=k1, beta=1.0, precision=precision, stream=stream)
+        return self.susceptibility(channel, s_y, 1.0, stream=stream)
+
     def set_autotune(self, on=True):
         """Time the tensor-core contraction's split-K candidates per shape (kb_set_autotune)."""
         kb.kb_set_autotune(self.ctx, on)

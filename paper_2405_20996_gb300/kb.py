@@ -81,6 +81,7 @@ _SIGS = {
     "kb_inject_alloc_failures": [C.c_void_p, C.c_int],
     "kb_set_wait_budget": [C.c_void_p, C.c_longlong],
     "kb_check_wait": [C.c_void_p, C.c_void_p],
+    "kb_susceptibility_k1": [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p],
     "kb_launch_count": [C.c_void_p, C.POINTER(C.c_ulonglong)],
     "kb_bubble_fp64_noalloc": [C.POINTER(kb_grid_desc), C.c_double, C.c_double, C.c_double,
                                C.POINTER(kb_vertex_desc), C.POINTER(kb_vertex_desc), C.c_int, C.c_int, C.c_int,
@@ -331,3 +332,7 @@ def kb_set_wait_budget(ctx, cycles):
 
 def kb_check_wait(ctx, stream=None):
     _check(ctx, lib().kb_check_wait(ctx, stream))
+
+
+def kb_susceptibility_k1(ctx, channel, slot, U, out_ptr, stream=None):
+    _check(ctx, lib().kb_susceptibility_k1(ctx, channel, slot, U, out_ptr, stream))

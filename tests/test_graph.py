@@ -168,7 +168,7 @@ def test_graph_of_32_uneven_points_matches_oracle():
     gr = StepGraph(descs)
     gr.launch()
     torch.cuda.synchronize()
-    worst = 0.0
+    worst, where = 0.0, None
     for (e, g, Ui, Ti, ch), ref_e in zip(pts, eager):
         got = _snapshot(e, 1, (0, 1, 2))
         for key in ref_e:
@@ -180,9 +180,10 @@ def test_graph_of_32_uneven_points_matches_oracle():
             ref = O.bubble_all(V, V, P, r, nq)
             for k, name in enumerate(CLS):
                 err = rel_err(got[(r, k)].cpu().numpy(), ref[name])
-                worst = max(worst, err)
+                if err > worst:
+                    worst, where = err, (g["n3v"], round(Ui, 3), round(Ti, 4), "apt"[r], name)
                 assert err <= 1e-6, (g["n3v"], Ui, Ti, r, name, err)
-    print("32 uneven points: worst class error %.2e" % worst)
+    print("32 uneven points: worst class error %.2e at (n3, U, T, channel, class) = %s" % (worst, where))
     gr.close()
     for e, *_ in pts:
         e.close()
