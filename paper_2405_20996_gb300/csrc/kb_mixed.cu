@@ -446,7 +446,8 @@ __device__ __forceinline__ void k2_tail(const VertexF& V, const DfGrids& G, cons
 // One CTA (128 threads) per (w, v); the interior nodes in chunks of CH = 128 / NG (NG lookup
 // groups: the two other channels, and for t their exchanged partners):
 //   1. corner lists: one thread per (node, group) finds the stencils of the group's classes
-//      and writes its 18 (record, weight) pairs to shared memory; the chunk's rows of the
+//      and writes its 18 corner weights and 4 class base records to shared memory (a
+//      reading lane then takes 4 bytes per corner); the chunk's rows of the
 //      propagator-vertex table are staged beside them (t: combined per spin record);
 //   2. gather: 8 lanes per node, lane l reading the 16-byte piece l (components 2l, 2l+1) of
 //      every corner record, so one warp-wide load covers the full records of 4 nodes and each
@@ -463,7 +464,7 @@ template <int R>
 __host__ __device__ constexpr size_t k2_smem_bytes() {
     constexpr int NS = (R == KB_CH_T) ? 2 : 1;
     constexpr int CH = 128 / (2 * NS);
-    constexpr size_t loop = (size_t)2 * NS * 18 * CH * sizeof(int2) + (size_t)NS * CH * 9 * sizeof(float4);
+    constexpr size_t loop = (size_t)2 * NS * CH * (sizeof(int4) + 9 * sizeof(float2)) + (size_t)NS * CH * 9 * sizeof(float4);
     constexpr size_t tail = (size_t)NS * 128 * 17 * sizeof(float2);
     return loop > tail ? loop : tail;
 }
@@ -475,10 +476,12 @@ __global__ void __launch_bounds__(128, 6) k_mx_k2(VertexF V, DfGrids G, MixedJob
     constexpr int NS = (R == KB_CH_T) ? 2 : 1;
     constexpr int NG = 2 * NS;
     constexpr int CH = 128 / NG;
-    constexpr size_t CL_BYTES = (size_t)NG * 18 * CH * sizeof(int2);
+    constexpr size_t BASE_BYTES = (size_t)NG * CH * sizeof(int4);
+    constexpr size_t CL_BYTES = BASE_BYTES + (size_t)NG * 9 * CH * sizeof(float2);
     extern __shared__ __align__(16) unsigned char k2_smem[];
     __shared__ float2 red[8][16];
-    int2* cl = reinterpret_cast<int2*>(k2_smem);                          // [g][k][n]
+    int4* cb = reinterpret_cast<int4*>(k2_smem);                          // [g][n] class bases
+    float2* cw = reinterpret_cast<float2*>(k2_smem + BASE_BYTES);         // [g][pair][n] weights
     float4* trow = reinterpret_cast<float4*>(k2_smem + CL_BYTES);         // [s][n][9]
     const int wi = w_off + blockIdx.y, vi = v_off + blockIdx.x;
     const df* qn = G.n3v + G.N3v;
@@ -507,12 +510,13 @@ __global__ void __launch_bounds__(128, 6) k_mx_k2(VertexF V, DfGrids G, MixedJob
         {
             // 1. corner lists, one (node, group) per thread; a warp's items share g
             const int n = tid % CH, g = tid / CH, j = j0 + n;
-            int2* dst = cl + (size_t)g * 18 * CH + n;
+            int4* bd = cb + g * CH + n;
+            float2* wd = cw + (size_t)g * 9 * CH + n;
             if (j < J.nq - 1) {
-                if (RIGHT) group_corners_rt<R>(V, G, g, w, qn[j], ve, dst, CH);
-                else group_corners_rt<R>(V, G, g, w, ve, qn[j], dst, CH);
+                if (RIGHT) group_corners_rt<R>(V, G, g, w, qn[j], ve, bd, wd, CH);
+                else group_corners_rt<R>(V, G, g, w, ve, qn[j], bd, wd, CH);
             } else {
-                no_corners18(dst, CH);
+                no_corners18(bd, wd, CH);
             }
         }
         // table rows; t: left (T0 + T1, T0) pairs with (up-down, exchanged term) since
@@ -537,11 +541,11 @@ __global__ void __launch_bounds__(128, 6) k_mx_k2(VertexF V, DfGrids G, MixedJob
 #pragma unroll 1
         for (int n = wp * 4 + gi; n < CH; n += 16) {
             float2 d0 = make_float2(0.f, 0.f), d1 = d0, x0 = d0, x1 = d0;
-            gather_list<group_channel<R, 0>()>(V, cl + n, CH, l, d0, d1);
-            gather_list<group_channel<R, 1>()>(V, cl + 18 * CH + n, CH, l, d0, d1);
+            gather_list<group_channel<R, 0>()>(V, G, cb + n, cw + n, CH, l, d0, d1);
+            gather_list<group_channel<R, 1>()>(V, G, cb + CH + n, cw + 9 * CH + n, CH, l, d0, d1);
             if (NS == 2) {
-                gather_list_x<group_channel<R, 2>()>(V, cl + 2 * 18 * CH + n, CH, l, x0, x1);
-                gather_list_x<group_channel<R, 3>()>(V, cl + 3 * 18 * CH + n, CH, l, x0, x1);
+                gather_list_x<group_channel<R, 2>()>(V, G, cb + 2 * CH + n, cw + 2 * 9 * CH + n, CH, l, x0, x1);
+                gather_list_x<group_channel<R, 3>()>(V, G, cb + 3 * CH + n, cw + 3 * 9 * CH + n, CH, l, x0, x1);
             }
 #pragma unroll
             for (int e = 0; e < 2; ++e) {

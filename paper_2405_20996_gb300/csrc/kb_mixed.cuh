@@ -354,74 +354,61 @@ __host__ __device__ constexpr int group_source() {
 __host__ __device__ constexpr int kswap12(int c) { return (c & 12) | ((c & 1) << 1) | ((c >> 1) & 1); }
 
 // ------------------------------------------------------------------------------------
-// Corner lists: the interpolation of a lookup written out as (record index, weight) pairs
-// by the thread that found the stencil, read by the lanes that hold the record components.
+// Corner lists: the interpolation of a lookup written out by the thread that found the
+// stencil, read by the lanes that hold the record components.  Compact form: per class the
+// record index of its first corner (the others follow at fixed offsets of the grid strides)
+// and per corner its weight, so that a reading lane takes 4 bytes per corner plus 16 per
+// lookup from shared memory.
 // ------------------------------------------------------------------------------------
 
-// The 18 corners of one channel's classes from its stencils: K1 (k = 0, 1), K2 (2 .. 5), K2'
-// (6 .. 9), K3 (10 .. 17), as (record index in the class array, weight bits), times f; a
-// corner outside its grid, of an absent class or of zero weight gets index -1.
-__device__ __forceinline__ void corner_list18(const Sten7& S, const DfGrids& G, float f, int2* dst, int stride) {
-    auto put = [&](int k, bool ok, int off, float wgt) {
-        const bool use = ok && wgt != 0.f;
-        dst[k * stride] = make_int2(use ? off : -1, __float_as_int(use ? wgt : 0.f));
-    };
+// The 18 corners of one channel's classes from its stencils, times f: base = record index of
+// the first corner of K1 (kw1), K2 (kw2 N2v + kv2), K2' (kw2 N2v + kp2) and K3
+// ((kw3 N3v + kv3) N3v + kp3); the weights in pairs whose second corner is the next record:
+// wt[0] K1 (kw1, kw1 + 1); wt[1 + bw] K2 (bw, 0), (bw, 1); wt[3 + bw] K2' likewise;
+// wt[5 + 2 bw + bv] K3 (bw, bv, 0), (bw, bv, 1).  Corner (bw, bv) of K2 is record
+// base + bw N2v + bv, corner (bw, bv, bp) of K3 is base + bw N3v^2 + bv N3v + bp.  A corner
+// outside its grid or of an absent class has weight 0 and is not read.
+__device__ __forceinline__ void corner_weights18(const Sten7& S, const DfGrids& G, float f, int4* base, float2* wt,
+                                                 int stride) {
+    *base = make_int4(S.kw1, S.kw2 * G.N2v + S.kv2, S.kw2 * G.N2v + S.kp2, (S.kw3 * G.N3v + S.kv3) * G.N3v + S.kp3);
+    auto lin = [](bool ok, float w) { return ok ? w : 0.f; };
+    wt[0] = make_float2(lin(S.u0 && S.kw1 >= 0, f * (1.f - S.tw1)), lin(S.u0 && S.kw1 + 1 < G.N1, f * S.tw1));
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
-        put(c, S.u0 && (c ? S.kw1 + 1 < G.N1 : S.kw1 >= 0), S.kw1 + c, f * (c ? S.tw1 : 1.f - S.tw1));
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int bw = c & 1, bv = c >> 1;
+    for (int bw = 0; bw < 2; ++bw) {
         const bool okw = bw ? S.kw2 + 1 < G.N2w : S.kw2 >= 0;
         const float fw = f * (bw ? S.tw2 : 1.f - S.tw2);
-        put(2 + c, S.u1 && okw && (bv ? S.kv2 + 1 < G.N2v : S.kv2 >= 0), (S.kw2 + bw) * G.N2v + S.kv2 + bv,
-            fw * (bv ? S.tv2 : 1.f - S.tv2));
-        put(6 + c, S.u2 && okw && (bv ? S.kp2 + 1 < G.N2v : S.kp2 >= 0), (S.kw2 + bw) * G.N2v + S.kp2 + bv,
-            fw * (bv ? S.tp2 : 1.f - S.tp2));
+        wt[(1 + bw) * stride] = make_float2(lin(S.u1 && okw && S.kv2 >= 0, fw * (1.f - S.tv2)),
+                                            lin(S.u1 && okw && S.kv2 + 1 < G.N2v, fw * S.tv2));
+        wt[(3 + bw) * stride] = make_float2(lin(S.u2 && okw && S.kp2 >= 0, fw * (1.f - S.tp2)),
+                                            lin(S.u2 && okw && S.kp2 + 1 < G.N2v, fw * S.tp2));
     }
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int bw = c & 1, bv = (c >> 1) & 1, bp = c >> 2;
-        const bool ok = S.u3 && (bw ? S.kw3 + 1 < G.N3w : S.kw3 >= 0) && (bv ? S.kv3 + 1 < G.N3v : S.kv3 >= 0) &&
-                        (bp ? S.kp3 + 1 < G.N3v : S.kp3 >= 0);
-        const float wg = f * (bw ? S.tw3 : 1.f - S.tw3) * (bv ? S.tv3 : 1.f - S.tv3) * (bp ? S.tp3 : 1.f - S.tp3);
-        put(10 + c, ok, ((S.kw3 + bw) * G.N3v + S.kv3 + bv) * G.N3v + S.kp3 + bp, wg);
+    for (int q = 0; q < 4; ++q) {
+        const int bw = q >> 1, bv = q & 1;
+        const bool ok = S.u3 && (bw ? S.kw3 + 1 < G.N3w : S.kw3 >= 0) && (bv ? S.kv3 + 1 < G.N3v : S.kv3 >= 0);
+        const float fwv = f * (bw ? S.tw3 : 1.f - S.tw3) * (bv ? S.tv3 : 1.f - S.tv3);
+        wt[(5 + q) * stride] = make_float2(lin(ok && S.kp3 >= 0, fwv * (1.f - S.tp3)),
+                                           lin(ok && S.kp3 + 1 < G.N3v, fwv * S.tp3));
     }
 }
 
-__device__ __forceinline__ void no_corners18(int2* dst, int stride) {
+__device__ __forceinline__ void no_corners18(int4* base, float2* wt, int stride) {
+    *base = make_int4(0, 0, 0, 0);
 #pragma unroll
-    for (int k = 0; k < 18; ++k) dst[k * stride] = make_int2(-1, 0);
+    for (int i = 0; i < 9; ++i) wt[i * stride] = make_float2(0.f, 0.f);
 }
 
-// Corner list of lookup group G of the other channels' part seen from channel r at the
-// r-variables (w, v, vp) (an exchanged group carries the factor -1; its Keldysh index swap
-// a1 <-> a2 is applied by the reader).
-template <int r, int G>
-__device__ __forceinline__ void group_corners(const VertexF& V, const DfGrids& Gr, df w, df v, df vp, int2* dst,
-                                              int stride) {
-    constexpr int c = group_source<r, G>(), ch = group_channel<r, G>();
-    if (!((V.mask >> c) & 1)) { no_corners18(dst, stride); return; }
-    df L[4];
-    df_legs(r, w, v, vp, L);
-    df gw, gv, gp;
-    if (G < 2) {
-        df_vars(c, L, gw, gv, gp);
-    } else {
-        df S4[4] = {L[0], L[1], L[3], L[2]};
-        df_vars(ch, S4, gw, gv, gp);
-    }
-    corner_list18(stencils7(V, ch, 15, Gr, gw, gv, gp), Gr, G < 2 ? 1.f : -1.f, dst, stride);
-}
-
-// The same with the group (and so the channel) known only at run time: one copy of the
-// stencil code serves every group (four inlined copies measured slower, from instruction
-// fetch), the class pointers are selected without indexing the parameter struct.
+// Corner list of lookup group g of the other channels' part seen from channel r at the
+// r-variables (w, v, vp), with the group (and so the channel) known only at run time: one
+// copy of the stencil code serves every group (four inlined copies measured slower, from
+// instruction fetch), the class pointers are selected without indexing the parameter
+// struct.  An exchanged group (g >= 2) carries the factor -1; its Keldysh index swap
+// a1 <-> a2 is applied by the reader.
 template <int r>
 __device__ __forceinline__ void group_corners_rt(const VertexF& V, const DfGrids& Gr, int g, df w, df v, df vp,
-                                                 int2* dst, int stride) {
+                                                 int4* base, float2* wt, int stride) {
     const int c = (g & 1) ? ((r == KB_CH_T) ? KB_CH_P : KB_CH_T) : ((r == KB_CH_A) ? KB_CH_P : KB_CH_A);
-    if (!((V.mask >> c) & 1)) { no_corners18(dst, stride); return; }
+    if (!((V.mask >> c) & 1)) { no_corners18(base, wt, stride); return; }
     df L[4];
     df_legs(r, w, v, vp, L);
     df gw, gv, gp;
@@ -433,46 +420,87 @@ __device__ __forceinline__ void group_corners_rt(const VertexF& V, const DfGrids
         df S4[4] = {L[0], L[1], L[3], L[2]};
         df_vars(ch, S4, gw, gv, gp);
     }
-    corner_list18(stencils7(V, ch, 15, Gr, gw, gv, gp), Gr, g < 2 ? 1.f : -1.f, dst, stride);
+    corner_weights18(stencils7(V, ch, 15, Gr, gw, gv, gp), Gr, g < 2 ? 1.f : -1.f, base, wt, stride);
 }
 
-// Corner class of corner k of a corner list.
-__host__ __device__ constexpr int corner_class(int k) { return k < 2 ? 0 : (k < 6 ? 1 : (k < 10 ? 2 : 3)); }
-
-// Gather of one corner list by a group of 8 lanes: lane l accumulates components 2l, 2l+1
-// (one 16-byte piece of every corner record), acc += sum_k w_k rec_k[2l .. 2l+1], so that one
-// warp-wide load delivers the full records of the 4 nodes its lane groups hold.
-template <int ch>
-__device__ __forceinline__ void gather_list(const VertexF& V, const int2* __restrict__ cl, int stride, int l,
-                                            float2& a0, float2& a1) {
-#pragma unroll
-    for (int k = 0; k < 18; ++k) {
-        const int2 cw = cl[k * stride];
-        if (cw.x >= 0) {
-            const float4 u = __ldg(reinterpret_cast<const float4*>(V.cls[ch][corner_class(k)]) + (size_t)cw.x * 8 + l);
-            const float2 wv = make_float2(__int_as_float(cw.y), __int_as_float(cw.y));
-            a0 = __ffma2_rn(wv, make_float2(u.x, u.y), a0);
-            a1 = __ffma2_rn(wv, make_float2(u.z, u.w), a1);
-        }
+// One pair of corners (records p and p + 1) of a lane group's gather: lane l reads the
+// 16-byte piece l of each record with a nonzero weight (p already points at piece l).
+__device__ __forceinline__ void corner_pair(const float4* p, float2 w, float2& a0, float2& a1) {
+    if (w.x != 0.f) {
+        const float4 u = __ldg(p);
+        a0 = __ffma2_rn(make_float2(w.x, w.x), make_float2(u.x, u.y), a0);
+        a1 = __ffma2_rn(make_float2(w.x, w.x), make_float2(u.z, u.w), a1);
     }
+    if (w.y != 0.f) {
+        const float4 u = __ldg(p + 8);
+        a0 = __ffma2_rn(make_float2(w.y, w.y), make_float2(u.x, u.y), a0);
+        a1 = __ffma2_rn(make_float2(w.y, w.y), make_float2(u.z, u.w), a1);
+    }
+}
+
+// The same for an exchanged group: components s0, s1 of records p and p + 1 (float2 units).
+__device__ __forceinline__ void corner_pair_x(const float2* p, int s0, int s1, float2 w, float2& a0, float2& a1) {
+    if (w.x != 0.f) {
+        const float2 u0 = __ldg(p + s0), u1 = __ldg(p + s1);
+        a0 = __ffma2_rn(make_float2(w.x, w.x), u0, a0);
+        a1 = __ffma2_rn(make_float2(w.x, w.x), u1, a1);
+    }
+    if (w.y != 0.f) {
+        const float2 u0 = __ldg(p + 16 + s0), u1 = __ldg(p + 16 + s1);
+        a0 = __ffma2_rn(make_float2(w.y, w.y), u0, a0);
+        a1 = __ffma2_rn(make_float2(w.y, w.y), u1, a1);
+    }
+}
+
+// Gather of one compact corner list by a group of 8 lanes: lane l accumulates components
+// 2l, 2l+1 (one 16-byte piece of every corner record), acc += sum_k w_k rec_k[2l .. 2l+1],
+// so that one warp-wide load delivers the full records of the 4 nodes its lane groups hold.
+template <int ch>
+__device__ __forceinline__ void gather_list(const VertexF& V, const DfGrids& G, const int4* __restrict__ base,
+                                            const float2* __restrict__ wt, int stride, int l, float2& a0,
+                                            float2& a1) {
+    const int4 b = *base;
+    float2 w[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) w[i] = wt[i * stride];
+    const float4* c1 = reinterpret_cast<const float4*>(V.cls[ch][0]) + l;
+    const float4* c2 = reinterpret_cast<const float4*>(V.cls[ch][1]) + l;
+    const float4* c2p = reinterpret_cast<const float4*>(V.cls[ch][2]) + l;
+    const float4* c3 = reinterpret_cast<const float4*>(V.cls[ch][3]) + l;
+    const size_t s2 = (size_t)G.N2v * 8, s3 = (size_t)G.N3v * 8, s33 = (size_t)G.N3v * G.N3v * 8;
+    corner_pair(c1 + (size_t)b.x * 8, w[0], a0, a1);
+    corner_pair(c2 + (size_t)b.y * 8, w[1], a0, a1);
+    corner_pair(c2 + (size_t)b.y * 8 + s2, w[2], a0, a1);
+    corner_pair(c2p + (size_t)b.z * 8, w[3], a0, a1);
+    corner_pair(c2p + (size_t)b.z * 8 + s2, w[4], a0, a1);
+    const float4* p3 = c3 + (size_t)b.w * 8;
+    corner_pair(p3, w[5], a0, a1);
+    corner_pair(p3 + s3, w[6], a0, a1);
+    corner_pair(p3 + s33, w[7], a0, a1);
+    corner_pair(p3 + s33 + s3, w[8], a0, a1);
 }
 
 // The same for an exchanged group: lane l takes components kswap12(2l), kswap12(2l+1).
 template <int ch>
-__device__ __forceinline__ void gather_list_x(const VertexF& V, const int2* __restrict__ cl, int stride, int l,
-                                              float2& a0, float2& a1) {
+__device__ __forceinline__ void gather_list_x(const VertexF& V, const DfGrids& G, const int4* __restrict__ base,
+                                              const float2* __restrict__ wt, int stride, int l, float2& a0,
+                                              float2& a1) {
     const int s0 = kswap12(2 * l), s1 = kswap12(2 * l + 1);
+    const int4 b = *base;
+    float2 w[9];
 #pragma unroll
-    for (int k = 0; k < 18; ++k) {
-        const int2 cw = cl[k * stride];
-        if (cw.x >= 0) {
-            const float2* rec = V.cls[ch][corner_class(k)] + (size_t)cw.x * 16;
-            const float2 u0 = __ldg(rec + s0), u1 = __ldg(rec + s1);
-            const float2 wv = make_float2(__int_as_float(cw.y), __int_as_float(cw.y));
-            a0 = __ffma2_rn(wv, u0, a0);
-            a1 = __ffma2_rn(wv, u1, a1);
-        }
-    }
+    for (int i = 0; i < 9; ++i) w[i] = wt[i * stride];
+    const size_t s2 = (size_t)G.N2v * 16, s3 = (size_t)G.N3v * 16, s33 = (size_t)G.N3v * G.N3v * 16;
+    corner_pair_x(V.cls[ch][0] + (size_t)b.x * 16, s0, s1, w[0], a0, a1);
+    corner_pair_x(V.cls[ch][1] + (size_t)b.y * 16, s0, s1, w[1], a0, a1);
+    corner_pair_x(V.cls[ch][1] + (size_t)b.y * 16 + s2, s0, s1, w[2], a0, a1);
+    corner_pair_x(V.cls[ch][2] + (size_t)b.z * 16, s0, s1, w[3], a0, a1);
+    corner_pair_x(V.cls[ch][2] + (size_t)b.z * 16 + s2, s0, s1, w[4], a0, a1);
+    const float2* p3 = V.cls[ch][3] + (size_t)b.w * 16;
+    corner_pair_x(p3, s0, s1, w[5], a0, a1);
+    corner_pair_x(p3 + s3, s0, s1, w[6], a0, a1);
+    corner_pair_x(p3 + s33, s0, s1, w[7], a0, a1);
+    corner_pair_x(p3 + s33 + s3, s0, s1, w[8], a0, a1);
 }
 
 }  // namespace kb
