@@ -175,8 +175,11 @@ kb_status kb_bubble(kb_ctx *ctx, int channel, int slot_left, int slot_right, int
  *                    Needs pi_kind KB_PI_GG and no self-energy table (else
  *                    KB_ERR_UNSUPPORTED; also with a dΣ/dΛ table); the tail nodes (v'' = ±inf) carry no G dependence.
  * Gradient classes must be complex128 and must not alias any input.  The bare part
- * R = Γ0 is a fixed parameter (no gradient).  precision: KB_PREC_FP64 only (others return
- * KB_ERR_UNSUPPORTED). */
+ * R = Γ0 is a fixed parameter (no gradient).  precision: KB_PREC_FP64 (every step in FP64)
+ * or KB_PREC_MIXED (the input vertices complex64 and 16-byte aligned, else KB_ERR_ARG: their
+ * records evaluated as the mixed forward evaluates them, FP32 tiles and GEMMs, while the
+ * scatter into the complex128 gradient classes and the Π gradient accumulate in FP64; the
+ * Π table and the pull-back to G^R are FP64); any other value is KB_ERR_ARG. */
 kb_status kb_bubble_vjp(kb_ctx *ctx, int channel, int slot_left, int slot_right, int gout_slot, int pi_kind,
                         unsigned class_mask, double alpha, int grad_left_slot, int grad_right_slot,
                         void *grad_GR_K1, void *grad_GR_K2, void *grad_GR_K3, int precision, void *stream);

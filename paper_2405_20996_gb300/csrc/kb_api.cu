@@ -386,12 +386,15 @@ kb_status kb_bubble_vjp(kb_ctx* ctx, int channel, int sl, int sr, int sgo, int p
         ctx->err = "kb_bubble_vjp: the G^R gradient needs pi_kind GG and no self-energy table (FDR form of G^K)";
         return KB_ERR_UNSUPPORTED;
     }
-    if (precision != KB_PREC_FP64) {
-        ctx->err = "kb_bubble_vjp: only KB_PREC_FP64 is built";
-        return KB_ERR_UNSUPPORTED;
+    if (precision != KB_PREC_FP64 && precision != KB_PREC_MIXED) {
+        ctx->err = "kb_bubble_vjp: precision must be KB_PREC_FP64 or KB_PREC_MIXED";
+        return KB_ERR_ARG;
     }
     if (mask == 0 || (sgl < 0 && sgr < 0 && !any_gr)) return KB_OK;
     if (cudaSetDevice(ctx->device) != cudaSuccess) { ctx->err = "cudaSetDevice failed"; return KB_ERR_CUDA; }
+    if (precision == KB_PREC_MIXED)
+        return kb_bubble_vjp_mixed(ctx, channel, sl, sr, sgo, pi_kind, mask, alpha, sgl, sgr, any_gr ? tabs : nullptr,
+                                   reinterpret_cast<cudaStream_t>(stream));
     return kb_bubble_vjp_fp64(ctx, channel, sl, sr, sgo, pi_kind, mask, alpha, sgl, sgr, any_gr ? tabs : nullptr,
                               reinterpret_cast<cudaStream_t>(stream));
 }

@@ -142,6 +142,8 @@ kb_status kb_bubble_mixed(kb_ctx* ctx, int r, int sl, int sr, int so, int pi_kin
                           double beta, cudaStream_t st);
 kb_status kb_bubble_vjp_fp64(kb_ctx* ctx, int r, int sl, int sr, int sgo, int pi_kind, unsigned mask, double alpha,
                              int sgl, int sgr, void* const gGR[3], cudaStream_t st);
+kb_status kb_bubble_vjp_mixed(kb_ctx* ctx, int r, int sl, int sr, int sgo, int pi_kind, unsigned mask, double alpha,
+                             int sgl, int sgr, void* const gGR[3], cudaStream_t st);
 // Grow the context's workspace to at least `bytes`, stream-ordered on st (the old buffer is
 // released after the work already queued on st); sync = true first waits for the whole
 // device (used outside the bubble calls, where no stream orders the context's earlier work).

@@ -1062,6 +1062,22 @@ static bool mixed_prepare(int device) {
 
 bool kb_mixed_prepare(int device) { return mixed_prepare(device); }
 
+bool kb::kb_slot_f32(kb_ctx* ctx, int slot, VertexF& F) {
+    bool ok;
+    F = to_vf(ctx->slots[slot], ctx, ok);
+    return ok;
+}
+
+void kb::kb_mixed_tables(kb_ctx* ctx, df* tab, DfGrids& G, cudaStream_t st) {
+    const Grids& g = ctx->g;
+    const size_t ntab = (size_t)g.n1 + g.n2w + g.n2v + g.n3w + g.n3v + g.nq;
+    G.n1 = tab; G.n2w = G.n1 + g.n1; G.n2v = G.n2w + g.n2w; G.n3w = G.n2v + g.n2v; G.n3v = G.n3w + g.n3w;
+    G.N1 = g.n1; G.N2w = g.n2w; G.N2v = g.n2v; G.N3w = g.n3w; G.N3v = g.n3v; G.A = (float)g.A;
+    KB_LAUNCH(ctx, st, "k_mx_tables");
+    k_mx_tables<<<(unsigned)((ntab + 255) / 256), 256, 0, st>>>(g.n1, g.n2w, g.n2v, g.n3w, g.n3v, g.nq, g.A, ctx->d_xq,
+                                                                tab);
+}
+
 template <int r>
 static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, unsigned mask, double alpha, double beta,
                             cudaStream_t st) {

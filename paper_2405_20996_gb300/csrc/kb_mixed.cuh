@@ -503,4 +503,12 @@ __device__ __forceinline__ void gather_list_x(const VertexF& V, const DfGrids& G
     corner_pair_x(p3 + s33 + s3, s0, s1, w[8], a0, a1);
 }
 
+// Host helpers of the mixed path (kb_mixed.cu) shared with its adjoint (kb_vjp.cu): the
+// FP32 view of a slot (false, with the context's error set, unless every attached class is
+// complex64 and 16-byte aligned), and the double-float node tables of the class grids and
+// the quadrature written into tab (n1 + n2w + n2v + n3w + n3v + nq entries) with G pointing
+// into them.
+bool kb_slot_f32(kb_ctx* ctx, int slot, VertexF& F);
+void kb_mixed_tables(kb_ctx* ctx, df* tab, DfGrids& G, cudaStream_t st);
+
 }  // namespace kb

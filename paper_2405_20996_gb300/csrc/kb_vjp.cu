@@ -17,6 +17,7 @@
 #include <cstdio>
 
 #include "kb_fp64.cuh"
+#include "kb_mixed.cuh"
 
 namespace kb {
 namespace {
@@ -315,6 +316,320 @@ __global__ void k_vjp_gr(Model m, ClassJob J, double A, const double* __restrict
     dst[1] = cadd(dst[1], pull(b4, th4));
 }
 
+
+// ------------------------------------------------------------------------------------
+// Mixed-precision adjoint: the same pipeline with the records of the complex64 vertex
+// evaluated as the mixed forward evaluates them (double-float frequencies and stencils,
+// FP32 interpolation, vertex_part_f32), FP32 tiles, products and GEMMs, and every sum
+// over many terms — the scatter into the complex128 gradient slots through the transposed
+// interpolation and the Pi gradient — accumulated with FP64 atomic adds.  The Pi table and
+// its pull-back to G^R stay FP64.
+// ------------------------------------------------------------------------------------
+
+// Transpose of corners(): every corner the forward reads, with the forward's FP32 weight,
+// receives weight * bar (component o of bar lands on component o, or o with a1 <-> a2 when
+// swap12, of the corner record).
+__device__ void corners_adj(double2* __restrict__ D, int nd, int k0, int k1, int k2, float t0, float t1, float t2,
+                            int N0, int N1, int N2, float f, bool swap12, const float2 bar[16]) {
+    int kk[3] = {k0, k1, k2}, N[3] = {N0, N1, N2};
+    float tt[3] = {t0, t1, t2};
+    int st[3] = {1, 1, 1};
+    if (nd == 2) st[0] = N[1];
+    if (nd == 3) { st[1] = N[2]; st[0] = N[1] * N[2]; }
+    const int base = kk[0] * st[0] + (nd >= 2 ? kk[1] * st[1] : 0) + (nd == 3 ? kk[2] * st[2] : 0);
+#pragma unroll 1
+    for (int cc = 0; cc < (1 << nd); ++cc) {
+        float wgt = f;
+        int of = base;
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (d < nd) {
+                const bool bt = (cc >> d) & 1;
+                ok = ok && (bt ? (kk[d] + 1 < N[d]) : (kk[d] >= 0));
+                wgt *= bt ? tt[d] : 1.f - tt[d];
+                of += bt ? st[d] : 0;
+            }
+        }
+        if (!ok || wgt == 0.f) continue;
+        double2* rec = D + (size_t)of * 16;
+        const double wd = wgt;
+#pragma unroll
+        for (int o = 0; o < 16; ++o) {
+            const int src = swap12 ? kswap12(o) : o;
+            atomicAdd(&rec[src].x, wd * bar[o].x);
+            atomicAdd(&rec[src].y, wd * bar[o].y);
+        }
+    }
+}
+
+__device__ __forceinline__ double2* grad_ptr(const VertexF& VG, int ch, int k) {
+    return reinterpret_cast<double2*>(const_cast<float2*>(vcls(VG, ch, k)));
+}
+
+// Transpose of vertex_part_f32 for the parts `what` (the bare part has no gradient).  VG
+// holds the gradient slot's complex128 classes (as pointers only) and the forward vertex's
+// channel mask; a class the gradient slot lacks receives nothing.
+template <int r>
+__device__ void vertex_part_adj_f32(const VertexF& VG, const DfGrids& G, int parts, bool right, int what, df w, df v,
+                                    df vp, const float2 bar[16]) {
+    const bool dir = parts & PARTS_UD, exch = parts & PARTS_X;
+    const int k_free = right ? 1 : 2, k_dep = right ? 2 : 1;
+    unsigned own = 0;
+    if (what & 2) own |= 1u << 0;
+    if (what & 4) own |= 1u << k_free;
+    if (what & 8) own |= 1u << k_dep;
+    if (what & 16) own |= 1u << 3;
+    if (!((VG.mask >> r) & 1)) own = 0;
+    const bool cross = (what & 32) && isfinite(v.h) && isfinite(vp.h);
+    constexpr int sr = (r == KB_CH_A) ? KB_CH_T : (r == KB_CH_T ? KB_CH_A : KB_CH_P);
+#pragma unroll 1
+    for (int grp = 0; grp < 6; ++grp) {
+        int ch;
+        unsigned classes;
+        float f = 1.f;
+        bool sw = false;
+        df gw, gv, gp;
+        if (grp == 0) {
+            if (!own || !dir) continue;
+            ch = r; classes = own; gw = w; gv = v; gp = vp;
+        } else if (grp == 1) {
+            if (!own || !exch) continue;
+            ch = sr; classes = own; f = -1.f; sw = true;
+            gw = (r == KB_CH_P) ? w : df_neg(w); gv = v; gp = (r == KB_CH_P) ? df_neg(vp) : vp;
+        } else {
+            if (!cross || (grp < 4 ? !dir : !exch)) continue;
+            const int c = (grp & 1) ? ((r == 2) ? 1 : 2) : ((r == 0) ? 1 : 0);
+            if (!((VG.mask >> c) & 1)) continue;
+            df L[4];
+            df_legs(r, w, v, vp, L);
+            classes = 15;
+            if (grp < 4) {
+                ch = c;
+                df_vars(c, L, gw, gv, gp);
+            } else {
+                ch = (c == KB_CH_A) ? KB_CH_T : (c == KB_CH_T ? KB_CH_A : KB_CH_P);
+                df S4[4] = {L[0], L[1], L[3], L[2]};
+                df_vars(ch, S4, gw, gv, gp);
+                f = -1.f;
+                sw = true;
+            }
+        }
+        const Sten7 S = stencils7(VG, ch, classes, G, gw, gv, gp);
+        if (S.u0) corners_adj(grad_ptr(VG, ch, 0), 1, S.kw1, 0, 0, S.tw1, 0.f, 0.f, G.N1, 1, 1, f, sw, bar);
+        if (S.u1)
+            corners_adj(grad_ptr(VG, ch, 1), 2, S.kw2, S.kv2, 0, S.tw2, S.tv2, 0.f, G.N2w, G.N2v, 1, f, sw, bar);
+        if (S.u2)
+            corners_adj(grad_ptr(VG, ch, 2), 2, S.kw2, S.kp2, 0, S.tw2, S.tp2, 0.f, G.N2w, G.N2v, 1, f, sw, bar);
+        if (S.u3)
+            corners_adj(grad_ptr(VG, ch, 3), 3, S.kw3, S.kv3, S.kp3, S.tw3, S.tv3, S.tp3, G.N3w, G.N3v, G.N3v, f, sw,
+                        bar);
+    }
+}
+
+// Frequencies and part selection of one tile record (w, external v, s, node j), as the
+// FP64 tile kernels take them: the spin term of the t channel is up-up for the left s = 0
+// and the right s = 1; the zero part reads R + K1_r + the external-free own class, the
+// v-part the external-dependent own class, K3_r and the other channels.
+struct RecArgs {
+    df w, vext, vpp;
+    int parts, what;
+};
+template <bool RIGHT>
+__device__ __forceinline__ RecArgs rec_args(const DfGrids& G, const ClassJob& J, const df* __restrict__ wgrid,
+                                            const df* __restrict__ vgrid, int wl, int vi, int s, int j) {
+    RecArgs a;
+    const bool nupart = RIGHT ? J.R_nu : J.L_nu;
+    a.w = wgrid[J.w0 + wl];
+    a.vext = nupart ? vgrid[vi] : df{0.f, 0.f};
+    a.vpp = (G.n3v + G.N3v)[j];
+    const bool uu = (J.r == KB_CH_T) && (RIGHT ? (s == 1) : (s == 0));
+    a.parts = uu ? PARTS_UU : PARTS_UD;
+    a.what = nupart ? (8 | 16 | 32) : (1 | 2 | 4);
+    return a;
+}
+
+// One thread per (w, external v, s, j): the left tile L (FP32) or the Pi-folded right tile
+// R' = sum_D Pi[B][D] R[D][C], as k_gather_f64.
+template <bool RIGHT, int R>
+__global__ void k_vjp_tile_f32(VertexF V, DfGrids G, ClassJob J, const df* __restrict__ wgrid,
+                               const df* __restrict__ vgrid, const double2* __restrict__ Pi, float2* __restrict__ tile) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y % J.ns, vi = blockIdx.y / J.ns, wl = blockIdx.z;
+    const int nrow = RIGHT ? J.nR : J.nL;
+    if (j >= J.nq || vi >= nrow) return;
+    const ChannelMaps& M = c_maps[R];
+    const RecArgs a = rec_args<RIGHT>(G, J, wgrid, vgrid, wl, vi, s, j);
+    float2 g[16];
+    if (RIGHT) vertex_part_f32<R>(V, G, a.parts, true, a.what, a.w, a.vpp, a.vext, g);
+    else vertex_part_f32<R>(V, G, a.parts, false, a.what, a.w, a.vext, a.vpp, g);
+    const size_t K = (size_t)4 * J.ns * J.nq, kcol = ((size_t)s * J.nq + j) * 4;
+    const size_t rowbase = (size_t)wl * 4 * nrow + (size_t)vi * 4;
+    if (!RIGHT) {
+        for (int A = 0; A < 4; ++A)
+            for (int B = 0; B < 4; ++B) tile[(rowbase + A) * K + kcol + B] = g[M.cL[A][B]];
+    } else {
+        const double2* P = Pi + ((size_t)wl * J.nq + j) * 16;
+        float2 pm[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) pm[i] = make_float2((float)P[i].x, (float)P[i].y);
+        for (int C = 0; C < 4; ++C)
+            for (int B = 0; B < 4; ++B) {
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int D = 0; D < 4; ++D) cmac2(acc, pm[4 * B + D], g[M.cR[D][C]]);
+                tile[(rowbase + C) * K + kcol + B] = acc;
+            }
+    }
+}
+
+// Gbar (FP32) = alpha * bar(out), laid out as k_vjp_gbar.
+__global__ void k_vjp_gbar_f32(ClassJob J, int cls, const void* gout, int dt, double alpha, float2* __restrict__ Gb) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)J.nw_chunk * J.nL * J.nR * 16) return;
+    const int o = idx % 16;
+    size_t rest = idx / 16;
+    const int vR = rest % J.nR;
+    rest /= J.nR;
+    const int vL = rest % J.nL;
+    const int wl = rest / J.nL;
+    const ChannelMaps& M = c_maps[J.r];
+    int A = 0, C = 0;
+    for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 4; ++c)
+            if (M.cO[a][c] == o) { A = a; C = c; }
+    const size_t w = J.w0 + wl;
+    size_t e;
+    if (cls == KB_K1) e = w * 16 + o;
+    else if (cls == KB_K2) e = (w * J.nL + vL) * 16 + o;
+    else if (cls == KB_K2P) e = (w * J.nR + vR) * 16 + o;
+    else e = ((w * J.nL + vL) * J.nR + vR) * 16 + o;
+    const double2 g = ld_c(gout, dt, e);
+    Gb[((size_t)wl * 4 * J.nL + 4 * vL + A) * (4 * J.nR) + 4 * vR + C] =
+        make_float2((float)(alpha * g.x), (float)(alpha * g.y));
+}
+
+// k_zgemm_gen in FP32 (complex, FP32 accumulation over the short inner dimension 4 nL or
+// 4 nR of the adjoint GEMMs).
+__global__ void __launch_bounds__(256) k_cgemm_gen_f32(const float2* __restrict__ A, const float2* __restrict__ B,
+                                                       float2* __restrict__ C, GemmDesc d) {
+    __shared__ float2 sA[16][33], sB[16][33];
+    const int b = blockIdx.z;
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    const float2* Ab = A + b * d.sAb;
+    const float2* Bb = B + b * d.sBb;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    float2 acc[2][2] = {};
+    for (int l0 = 0; l0 < d.L; l0 += 16) {
+        for (int t = threadIdx.x; t < 32 * 16; t += 256) {
+            const int ll = t / 32, rr = t % 32;
+            const int gi = i0 + rr, gj = j0 + rr, gl = l0 + ll;
+            float2 a = make_float2(0.f, 0.f), bv = a;
+            if (gi < d.I && gl < d.L) a = Ab[gi * d.sAi + gl * d.sAl];
+            if (gj < d.J && gl < d.L) bv = Bb[gl * d.sBl + gj * d.sBj];
+            if (d.conjA) a.y = -a.y;
+            if (d.conjB) bv.y = -bv.y;
+            sA[ll][rr] = a;
+            sB[ll][rr] = bv;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ll = 0; ll < 16; ++ll) {
+            const float2 a0 = sA[ll][ty], a1 = sA[ll][ty + 16];
+            const float2 b0 = sB[ll][tx], b1 = sB[ll][tx + 16];
+            cmac2(acc[0][0], a0, b0);
+            cmac2(acc[0][1], a0, b1);
+            cmac2(acc[1][0], a1, b0);
+            cmac2(acc[1][1], a1, b1);
+        }
+        __syncthreads();
+    }
+    for (int i = 0; i < 2; ++i)
+        for (int jj = 0; jj < 2; ++jj) {
+            const int gi = i0 + ty + 16 * i, gj = j0 + tx + 16 * jj;
+            if (gi < d.I && gj < d.J) C[b * d.sCb + gi * d.sCi + gj] = acc[i][jj];
+        }
+}
+
+// bar(L) -> gradient slot, one thread per (w, v, s, j) record in the order of k_vjp_left.
+template <int R>
+__global__ void k_vjp_left_f32(VertexF VG, DfGrids G, ClassJob J, const df* __restrict__ wgrid,
+                               const df* __restrict__ vgrid, const float2* __restrict__ gL) {
+    const size_t inner = (size_t)J.nw_chunk * J.ns * J.nL;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= inner * J.nq) return;
+    const int j = (int)(idx / inner);
+    size_t rest = idx % inner;
+    const int vi = (int)(rest % J.nL);
+    rest /= J.nL;
+    const int s = (int)(rest % J.ns);
+    const int wl = (int)(rest / J.ns);
+    const ChannelMaps& M = c_maps[R];
+    const RecArgs a = rec_args<false>(G, J, wgrid, vgrid, wl, vi, s, j);
+    const size_t K = (size_t)4 * J.ns * J.nq, kcol = ((size_t)s * J.nq + j) * 4;
+    const size_t rowbase = (size_t)wl * 4 * J.nL + (size_t)vi * 4;
+    float2 bar[16];
+    for (int A = 0; A < 4; ++A)
+        for (int B = 0; B < 4; ++B) bar[M.cL[A][B]] = gL[(rowbase + A) * K + kcol + B];
+    vertex_part_adj_f32<R>(VG, G, a.parts, false, a.what, a.w, a.vext, a.vpp, bar);
+}
+
+// bar(R') -> bar(R) = sum_B conj(Pi[B][D]) bar(R')[C][B] -> gradient slot (want_vertex), or
+// bar(Pi)[B][D] += sum_C conj(R[D][C]) bar(R')[C][B] (gPi), in the thread orders of k_vjp_right.
+template <int R>
+__global__ void k_vjp_right_f32(VertexF V, VertexF VG, bool want_vertex, DfGrids G, ClassJob J,
+                                const df* __restrict__ wgrid, const df* __restrict__ vgrid,
+                                const double2* __restrict__ Pi, const float2* __restrict__ gRp,
+                                double2* __restrict__ gPi) {
+    const size_t inner = (size_t)J.nw_chunk * J.ns * J.nR;
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= inner * J.nq) return;
+    int j, vi, s, wl;
+    size_t rest;
+    if (gPi) {
+        j = (int)(idx % J.nq);
+        rest = idx / J.nq;
+    } else {
+        j = (int)(idx / inner);
+        rest = idx % inner;
+    }
+    vi = (int)(rest % J.nR);
+    rest /= J.nR;
+    s = (int)(rest % J.ns);
+    wl = (int)(rest / J.ns);
+    const ChannelMaps& M = c_maps[R];
+    const RecArgs a = rec_args<true>(G, J, wgrid, vgrid, wl, vi, s, j);
+    const size_t K = (size_t)4 * J.ns * J.nq, kcol = ((size_t)s * J.nq + j) * 4;
+    const size_t rowbase = (size_t)wl * 4 * J.nR + (size_t)vi * 4;
+    float2 grp[4][4];   // [C][B]
+    for (int C = 0; C < 4; ++C)
+        for (int B = 0; B < 4; ++B) grp[C][B] = gRp[(rowbase + C) * K + kcol + B];
+    if (want_vertex) {
+        const double2* P = Pi + ((size_t)wl * J.nq + j) * 16;
+        float2 bar[16];
+        for (int D = 0; D < 4; ++D)
+            for (int C = 0; C < 4; ++C) {
+                float2 acc = make_float2(0.f, 0.f);
+                for (int B = 0; B < 4; ++B) cmac2(acc, make_float2((float)P[4 * B + D].x, -(float)P[4 * B + D].y), grp[C][B]);
+                bar[M.cR[D][C]] = acc;
+            }
+        vertex_part_adj_f32<R>(VG, G, a.parts, true, a.what, a.w, a.vpp, a.vext, bar);
+    }
+    if (gPi) {
+        float2 g[16];
+        vertex_part_f32<R>(V, G, a.parts, true, a.what, a.w, a.vpp, a.vext, g);
+        double2* dst = gPi + ((size_t)wl * J.nq + j) * 16;
+        for (int B = 0; B < 4; ++B)
+            for (int D = 0; D < 4; ++D) {
+                float2 acc = make_float2(0.f, 0.f);
+                for (int C = 0; C < 4; ++C) {
+                    const float2 rv = g[M.cR[D][C]];
+                    cmac2(acc, make_float2(rv.x, -rv.y), grp[C][B]);
+                }
+                atomic_cadd(dst + 4 * B + D, make_double2(acc.x, acc.y));
+            }
+    }
+}
 }  // namespace
 }  // namespace kb
 
@@ -429,4 +744,142 @@ kb_status kb_bubble_vjp_fp64(kb_ctx* ctx, int r, int sl, int sr, int sgo, int pi
         }
     }
     return KB_OK;
+}
+
+
+// Mixed-precision adjoint (kb_bubble_vjp with KB_PREC_MIXED): the pipeline of
+// kb_bubble_vjp_fp64 with FP32 tiles and GEMMs on the complex64 vertex.
+template <int R>
+static kb_status vjp_mixed_impl(kb_ctx* ctx, int sl, int sr, int sgo, int pi_kind, unsigned mask, double alpha,
+                                int sgl, int sgr, void* const gGR[3], cudaStream_t st) {
+    VertexF VL, VRt;
+    if (!kb_slot_f32(ctx, sl, VL) || !kb_slot_f32(ctx, sr, VRt)) return KB_ERR_ARG;
+    const VertexDev none{};
+    auto grad_view = [&](int gs, const VertexDev& fwd) {
+        const VertexDev& Gd = gs >= 0 ? ctx->slots[gs] : none;
+        VertexF F;
+        for (int c = 0; c < 3; ++c)
+            for (int k = 0; k < 4; ++k) F.cls[c][k] = reinterpret_cast<const float2*>(Gd.cls[c][k]);
+        F.has_R = 0;
+        F.mask = fwd.mask;
+        F.bare = 0.f;
+        return F;
+    };
+    const VertexF GVL = grad_view(sgl, ctx->slots[sl]), GVR = grad_view(sgr, ctx->slots[sr]);
+    const Grids& g = ctx->g;
+    const int ns = (R == KB_CH_T) ? 2 : 1;
+    const size_t K = (size_t)4 * ns * g.nq;
+    const size_t ntab = (size_t)g.n1 + g.n2w + g.n2v + g.n3w + g.n3v + g.nq;
+    const size_t tab_bytes = (ntab * sizeof(df) + 255) / 256 * 256;
+    for (int cls = 0; cls < 4; ++cls) {
+        if (!((mask >> cls) & 1)) continue;
+        double2* gtab = reinterpret_cast<double2*>(gGR ? gGR[cls == KB_K1 ? 0 : (cls == KB_K3 ? 2 : 1)] : nullptr);
+        const bool want_l = sgl >= 0, want_r = sgr >= 0, want_gr = gtab != nullptr;
+        if (!want_l && !want_r && !want_gr) continue;
+        int nw, nL, nR, nvg;
+        class_shape(g, cls, nw, nL, nR, nvg);
+        const size_t tileL = (size_t)4 * nL * K, tileR = (size_t)4 * nR * K, nGb = (size_t)16 * nL * nR;
+        const size_t per_w = (size_t)g.nq * 16 * sizeof(double2) * (want_gr ? 2 : 1) +
+                             (2 * tileL + 2 * tileR + nGb) * sizeof(float2);
+        const int chunk = (int)std::max<size_t>(1, std::min<size_t>(nw, ctx->ws_limit / per_w));
+        kb_status s = kb_ensure_workspace(ctx, tab_bytes + per_w * chunk, st);
+        if (s != KB_OK) return s;
+        char* ws = static_cast<char*>(ctx->ws.ptr);
+        DfGrids G;
+        kb_mixed_tables(ctx, reinterpret_cast<df*>(ws), G, st);
+        double2* Pi = reinterpret_cast<double2*>(ws + tab_bytes);
+        double2* gPi = Pi + (size_t)chunk * g.nq * 16;
+        float2* Lt = reinterpret_cast<float2*>(gPi + (want_gr ? (size_t)chunk * g.nq * 16 : 0));
+        float2* Rt = Lt + (size_t)chunk * tileL;
+        float2* gL = Rt + (size_t)chunk * tileR;
+        float2* gRp = gL + (size_t)chunk * tileL;
+        float2* Gb = gRp + (size_t)chunk * tileR;
+        const df* wgrid = cls == KB_K1 ? G.n1 : (cls == KB_K3 ? G.n3w : G.n2w);
+        const df* vgrid = cls == KB_K3 ? G.n3v : G.n2v;
+        for (int w0 = 0; w0 < nw; w0 += chunk) {
+            ClassJob J;
+            J.r = R; J.pi_kind = pi_kind; J.ns = ns; J.nq = g.nq;
+            J.nw_chunk = std::min(chunk, nw - w0); J.w0 = w0; J.nw_grid = nw;
+            J.nL = nL; J.nR = nR; J.nvL_grid = nvg; J.nvR_grid = nvg;
+            J.L_nu = (cls == KB_K2 || cls == KB_K3);
+            J.R_nu = (cls == KB_K2P || cls == KB_K3);
+            const int Mr = 4 * nL, Nc = 4 * nR;
+            {
+                KB_LAUNCH(ctx, st, "k_pi_table");
+                k_pi_table<<<dim3((g.nq + 127) / 128, J.nw_chunk), 128, 0, st>>>(ctx->m, J, g.A, ctx->d_xq, ctx->d_wq, Pi);
+            }
+            {
+                KB_LAUNCH(ctx, st, "k_vjp_tile_f32_left");
+                k_vjp_tile_f32<false, R><<<dim3((g.nq + 127) / 128, nL * ns, J.nw_chunk), 128, 0, st>>>(
+                    VL, G, J, wgrid, vgrid, Pi, Lt);
+            }
+            {
+                KB_LAUNCH(ctx, st, "k_vjp_tile_f32_right");
+                k_vjp_tile_f32<true, R><<<dim3((g.nq + 127) / 128, nR * ns, J.nw_chunk), 128, 0, st>>>(
+                    VRt, G, J, wgrid, vgrid, Pi, Rt);
+            }
+            {
+                KB_LAUNCH(ctx, st, "k_vjp_gbar_f32");
+                const size_t tot = (size_t)J.nw_chunk * nL * nR * 16;
+                k_vjp_gbar_f32<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(J, cls, ctx->slots[sgo].cls[R][cls],
+                                                                             ctx->slots[sgo].dt[R][cls], alpha, Gb);
+            }
+            if (want_l) {
+                GemmDesc d{Mr, (int)K, Nc, (long long)Mr * Nc, Nc, 1, (long long)tileR, (long long)K, 1,
+                           (long long)tileL, (long long)K, false, true};
+                {
+                    KB_LAUNCH(ctx, st, "k_cgemm_gen_f32");
+                    k_cgemm_gen_f32<<<dim3((unsigned)((K + 31) / 32), (Mr + 31) / 32, J.nw_chunk), 256, 0, st>>>(
+                        Gb, Rt, gL, d);
+                }
+                {
+                    KB_LAUNCH(ctx, st, "k_vjp_left_f32");
+                    const size_t tot = (size_t)J.nw_chunk * ns * nL * g.nq;
+                    k_vjp_left_f32<R><<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(GVL, G, J, wgrid, vgrid, gL);
+                }
+            }
+            if (want_r || want_gr) {
+                GemmDesc d{Nc, (int)K, Mr, (long long)Mr * Nc, 1, Nc, (long long)tileL, (long long)K, 1,
+                           (long long)tileR, (long long)K, false, true};
+                {
+                    KB_LAUNCH(ctx, st, "k_cgemm_gen_f32");
+                    k_cgemm_gen_f32<<<dim3((unsigned)((K + 31) / 32), (Nc + 31) / 32, J.nw_chunk), 256, 0, st>>>(
+                        Gb, Lt, gRp, d);
+                }
+                if (want_gr)
+                    KB_CUDA_TRY(ctx, cudaMemsetAsync(gPi, 0, (size_t)J.nw_chunk * g.nq * 16 * sizeof(double2), st));
+                const size_t tot = (size_t)J.nw_chunk * ns * nR * g.nq;
+                if (want_r) {
+                    KB_LAUNCH(ctx, st, "k_vjp_right_f32");
+                    k_vjp_right_f32<R><<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(VRt, GVR, true, G, J, wgrid,
+                                                                                     vgrid, Pi, gRp, nullptr);
+                }
+                if (want_gr) {
+                    {
+                        KB_LAUNCH(ctx, st, "k_vjp_right_f32");
+                        k_vjp_right_f32<R><<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(VRt, GVR, false, G, J, wgrid,
+                                                                                         vgrid, Pi, gRp, gPi);
+                    }
+                    KB_LAUNCH(ctx, st, "k_vjp_gr");
+                    k_vjp_gr<<<dim3((g.nq + 127) / 128, J.nw_chunk), 128, 0, st>>>(ctx->m, J, g.A, ctx->d_xq, ctx->d_wq,
+                                                                                 gPi, gtab);
+                }
+            }
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) { ctx->err = std::string("mixed vjp launch: ") + cudaGetErrorString(e); return KB_ERR_CUDA; }
+        }
+    }
+    return KB_OK;
+}
+
+kb_status kb_bubble_vjp_mixed(kb_ctx* ctx, int r, int sl, int sr, int sgo, int pi_kind, unsigned mask, double alpha,
+                              int sgl, int sgr, void* const gGR[3], cudaStream_t st) {
+    if (!g_vjp_maps_uploaded[ctx->device]) {
+        ChannelMaps h[3] = {channel_maps(0), channel_maps(1), channel_maps(2)};
+        KB_CUDA_TRY(ctx, cudaMemcpyToSymbol(c_maps, h, sizeof(h)));
+        g_vjp_maps_uploaded[ctx->device] = true;
+    }
+    if (r == KB_CH_A) return vjp_mixed_impl<KB_CH_A>(ctx, sl, sr, sgo, pi_kind, mask, alpha, sgl, sgr, gGR, st);
+    if (r == KB_CH_P) return vjp_mixed_impl<KB_CH_P>(ctx, sl, sr, sgo, pi_kind, mask, alpha, sgl, sgr, gGR, st);
+    return vjp_mixed_impl<KB_CH_T>(ctx, sl, sr, sgo, pi_kind, mask, alpha, sgl, sgr, gGR, st);
 }
