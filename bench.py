@@ -529,46 +529,55 @@ def run_parquet(args):
 
 def run_vjp(args):
     """Adjoint of the one-loop bubble of all three channels (K1 201, K2 81^2, K3 41^3,
-    Nq 4001, U/Delta = 2, T = 0.05): kb_bubble_vjp in FP64 with respect to the vertex (both
-    sides, one gradient slot) and G^R, beside the FP64 forward bubble.  Points: output
-    points whose gradient is pulled back per second."""
+    Nq 4001, U/Delta = 2, T = 0.05): kb_bubble_vjp with respect to the vertex (both sides,
+    one gradient slot) and G^R, beside the forward bubble of the same precision; mixed
+    (complex64 vertex, FP32 records and GEMMs, FP64 accumulation of the scatter) unless
+    --precision fp64.  Points: output points whose gradient is pulled back per second."""
     import torch
     import seeded as S
     from paper_2405_20996_gb300 import kb
     from paper_2405_20996_gb300.engine import Engine
+    prec = "fp64" if args.precision == "fp64" else "mixed"
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
     g = dict(n1=201, n2w=81, n2v=81, n3w=41, n3v=41)
     dev = torch.device("cuda", 0)
     e = Engine(g, NQ, device=0)
     e.set_model(DELTA, T)
-    e.set_vertex(0, U=U, has_R=True, channels=S.seeded_vertex(g, U, seed=77))
-    e.alloc_out(1)
+    e.set_vertex(0, U=U, has_R=True, channels=S.seeded_vertex(g, U, seed=77), dtype=dt)
+    e.alloc_out(1, dtype=dt)
     rng = np.random.default_rng(5)
     for t in e.tensors[1].values():
         t.copy_(torch.from_numpy(rng.standard_normal(t.shape) + 1j * rng.standard_normal(t.shape)))
     e.alloc_out(2)                                  # gradient slot (complex128, zeroed)
-    e.alloc_out(3)                                  # forward output slot
+    e.alloc_out(3, dtype=dt)                        # forward output slot
     tabs = e.gr_tables()
     stream = torch.cuda.current_stream(dev)
     points = 3 * sum(class_points(g).values())
 
     def vjp():
         for r in range(3):
-            e.bubble_vjp(r, 0, 0, 1, grad_left=2, grad_right=2, grad_gr=tabs, stream=stream)
+            e.bubble_vjp(r, 0, 0, 1, grad_left=2, grad_right=2, grad_gr=tabs, precision=prec, stream=stream)
 
     def fwd():
         for r in range(3):
-            e.bubble(r, 0, 0, 3, precision="fp64", stream=stream)
+            e.bubble(r, 0, 0, 3, precision=prec, stream=stream)
 
     ms_vjp = _timed(vjp, args.steps, min(args.warmup, 1), stream)
     ms_fwd = _timed(fwd, args.steps, min(args.warmup, 1), stream)
+    kb.kb_profile_enable(e.ctx, True)
+    vjp()
+    torch.cuda.synchronize()
+    prof = kb.kb_profile_read(e.ctx)
+    kb.kb_profile_enable(e.ctx, False)
     kb.kb_check_device(e.ctx)
     line = {"metric": "adjoint bubble points/s (w.v.v'.Keldysh, vertex + G^R gradients)",
             "value": points / (ms_vjp / 1e3), "unit": "points/s", "n_gpus": 1, "steps": args.steps,
             "warmup": min(args.warmup, 1), "ms_per_step": ms_vjp, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
             "config": {"workload": "VJP of the one-loop bubble a,p,t; K1 201, K2 81x81, K3 41^3, Nq 4001",
-                       "points_per_step": points},
-            "forward_fp64": {"value": points / (ms_fwd / 1e3), "ms_per_step": ms_fwd}}
+                       "precision": prec, "points_per_step": points},
+            "forward": {"precision": prec, "value": points / (ms_fwd / 1e3), "ms_per_step": ms_fwd},
+            "kernels_ms": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}}
     print(json.dumps(line))
     return 0
 

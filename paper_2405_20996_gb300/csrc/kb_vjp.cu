@@ -326,11 +326,52 @@ __global__ void k_vjp_gr(Model m, ClassJob J, double A, const double* __restrict
 // its pull-back to G^R stay FP64.
 // ------------------------------------------------------------------------------------
 
-// Transpose of corners(): every corner the forward reads, with the forward's FP32 weight,
-// receives weight * bar (component o of bar lands on component o, or o with a1 <-> a2 when
-// swap12, of the corner record).
-__device__ void corners_adj(double2* __restrict__ D, int nd, int k0, int k1, int k2, float t0, float t1, float t2,
-                            int N0, int N1, int N2, float f, bool swap12, const float2 bar[16]) {
+// Warp-cooperative scatter of one corner: lane L adds wgt * bar into record idx of D
+// (idx < 0: nothing), component o of bar onto component o, or o with a1 <-> a2 when swap12.
+// Consecutive lanes hold consecutive quadrature nodes, which mostly interpolate from the
+// same records, so the lanes that share a record first sum their 32 reals by a butterfly
+// reduce-scatter (lane L ends with real L of the sum) and then issue one FP64 atomic add
+// each: one warp-wide atomic per distinct record instead of 32 per lane.  All 32 lanes of
+// the warp must call it together.
+__device__ __forceinline__ void warp_scatter(double2* __restrict__ D, int idx, float wgt, bool swap12,
+                                             const float2 bar[16]) {
+    const int lane = threadIdx.x & 31;
+    unsigned todo = __ballot_sync(0xffffffffu, idx >= 0);
+    while (todo) {
+        const int lead = __ffs(todo) - 1;
+        const int lidx = __shfl_sync(0xffffffffu, idx, lead);
+        const bool mine = idx == lidx;
+        todo &= ~__ballot_sync(0xffffffffu, mine);
+        const float wm = mine ? wgt : 0.f;
+        float v[32];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            // source component of destination e: kswap12 exchanges 1 <-> 2 within each group of 4
+            const int q = e & 3;
+            const float2 b = (q == 1) ? (swap12 ? bar[e + 1] : bar[e])
+                                      : ((q == 2) ? (swap12 ? bar[e - 1] : bar[e]) : bar[e]);
+            v[2 * e] = wm * b.x;
+            v[2 * e + 1] = wm * b.y;
+        }
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) {
+            const bool hi = (lane & d) != 0;
+#pragma unroll
+            for (int i = 0; i < d; ++i) {
+                const float send = hi ? v[i] : v[i + d];
+                const float keep = hi ? v[i + d] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, d);
+            }
+        }
+        atomicAdd(reinterpret_cast<double*>(D + (size_t)lidx * 16) + lane, (double)v[0]);
+    }
+}
+
+// Transpose of corners() for one class, warp-cooperatively: corner cc of every lane's
+// stencil (valid: the lane's class applies) with the forward's FP32 weight.
+__device__ __forceinline__ void corners_adj_warp(double2* __restrict__ D, bool valid, int nd, int k0, int k1, int k2,
+                                                 float t0, float t1, float t2, int N0, int N1, int N2, float f,
+                                                 bool swap12, const float2 bar[16]) {
     int kk[3] = {k0, k1, k2}, N[3] = {N0, N1, N2};
     float tt[3] = {t0, t1, t2};
     int st[3] = {1, 1, 1};
@@ -341,7 +382,7 @@ __device__ void corners_adj(double2* __restrict__ D, int nd, int k0, int k1, int
     for (int cc = 0; cc < (1 << nd); ++cc) {
         float wgt = f;
         int of = base;
-        bool ok = true;
+        bool ok = valid;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             if (d < nd) {
@@ -351,15 +392,7 @@ __device__ void corners_adj(double2* __restrict__ D, int nd, int k0, int k1, int
                 of += bt ? st[d] : 0;
             }
         }
-        if (!ok || wgt == 0.f) continue;
-        double2* rec = D + (size_t)of * 16;
-        const double wd = wgt;
-#pragma unroll
-        for (int o = 0; o < 16; ++o) {
-            const int src = swap12 ? kswap12(o) : o;
-            atomicAdd(&rec[src].x, wd * bar[o].x);
-            atomicAdd(&rec[src].y, wd * bar[o].y);
-        }
+        warp_scatter(D, (ok && wgt != 0.f) ? of : -1, wgt, swap12, bar);
     }
 }
 
@@ -367,12 +400,14 @@ __device__ __forceinline__ double2* grad_ptr(const VertexF& VG, int ch, int k) {
     return reinterpret_cast<double2*>(const_cast<float2*>(vcls(VG, ch, k)));
 }
 
-// Transpose of vertex_part_f32 for the parts `what` (the bare part has no gradient).  VG
-// holds the gradient slot's complex128 classes (as pointers only) and the forward vertex's
-// channel mask; a class the gradient slot lacks receives nothing.
+// Transpose of vertex_part_f32 for the parts `what` (the bare part has no gradient), for
+// the records of a warp (lanes with live = false contribute nothing; the control flow is
+// uniform over the warp).  VG holds the gradient slot's complex128 classes (as pointers
+// only) and the forward vertex's channel mask; a class the gradient slot lacks receives
+// nothing.
 template <int r>
 __device__ void vertex_part_adj_f32(const VertexF& VG, const DfGrids& G, int parts, bool right, int what, df w, df v,
-                                    df vp, const float2 bar[16]) {
+                                    df vp, const float2 bar[16], bool live) {
     const bool dir = parts & PARTS_UD, exch = parts & PARTS_X;
     const int k_free = right ? 1 : 2, k_dep = right ? 2 : 1;
     unsigned own = 0;
@@ -381,14 +416,15 @@ __device__ void vertex_part_adj_f32(const VertexF& VG, const DfGrids& G, int par
     if (what & 8) own |= 1u << k_dep;
     if (what & 16) own |= 1u << 3;
     if (!((VG.mask >> r) & 1)) own = 0;
-    const bool cross = (what & 32) && isfinite(v.h) && isfinite(vp.h);
+    const bool cross_l = (what & 32) && isfinite(v.h) && isfinite(vp.h);
+    const bool cross = __any_sync(0xffffffffu, live && cross_l);
     constexpr int sr = (r == KB_CH_A) ? KB_CH_T : (r == KB_CH_T ? KB_CH_A : KB_CH_P);
 #pragma unroll 1
     for (int grp = 0; grp < 6; ++grp) {
         int ch;
         unsigned classes;
         float f = 1.f;
-        bool sw = false;
+        bool sw = false, ok = live;
         df gw, gv, gp;
         if (grp == 0) {
             if (!own || !dir) continue;
@@ -401,6 +437,7 @@ __device__ void vertex_part_adj_f32(const VertexF& VG, const DfGrids& G, int par
             if (!cross || (grp < 4 ? !dir : !exch)) continue;
             const int c = (grp & 1) ? ((r == 2) ? 1 : 2) : ((r == 0) ? 1 : 0);
             if (!((VG.mask >> c) & 1)) continue;
+            ok = ok && cross_l;
             df L[4];
             df_legs(r, w, v, vp, L);
             classes = 15;
@@ -416,14 +453,17 @@ __device__ void vertex_part_adj_f32(const VertexF& VG, const DfGrids& G, int par
             }
         }
         const Sten7 S = stencils7(VG, ch, classes, G, gw, gv, gp);
-        if (S.u0) corners_adj(grad_ptr(VG, ch, 0), 1, S.kw1, 0, 0, S.tw1, 0.f, 0.f, G.N1, 1, 1, f, sw, bar);
-        if (S.u1)
-            corners_adj(grad_ptr(VG, ch, 1), 2, S.kw2, S.kv2, 0, S.tw2, S.tv2, 0.f, G.N2w, G.N2v, 1, f, sw, bar);
-        if (S.u2)
-            corners_adj(grad_ptr(VG, ch, 2), 2, S.kw2, S.kp2, 0, S.tw2, S.tp2, 0.f, G.N2w, G.N2v, 1, f, sw, bar);
-        if (S.u3)
-            corners_adj(grad_ptr(VG, ch, 3), 3, S.kw3, S.kv3, S.kp3, S.tw3, S.tv3, S.tp3, G.N3w, G.N3v, G.N3v, f, sw,
-                        bar);
+        if ((classes & 1) && vcls(VG, ch, 0))
+            corners_adj_warp(grad_ptr(VG, ch, 0), ok && S.u0, 1, S.kw1, 0, 0, S.tw1, 0.f, 0.f, G.N1, 1, 1, f, sw, bar);
+        if ((classes & 2) && vcls(VG, ch, 1))
+            corners_adj_warp(grad_ptr(VG, ch, 1), ok && S.u1, 2, S.kw2, S.kv2, 0, S.tw2, S.tv2, 0.f, G.N2w, G.N2v, 1, f,
+                             sw, bar);
+        if ((classes & 4) && vcls(VG, ch, 2))
+            corners_adj_warp(grad_ptr(VG, ch, 2), ok && S.u2, 2, S.kw2, S.kp2, 0, S.tw2, S.tp2, 0.f, G.N2w, G.N2v, 1, f,
+                             sw, bar);
+        if ((classes & 8) && vcls(VG, ch, 3))
+            corners_adj_warp(grad_ptr(VG, ch, 3), ok && S.u3, 3, S.kw3, S.kv3, S.kp3, S.tw3, S.tv3, S.tp3, G.N3w, G.N3v,
+                             G.N3v, f, sw, bar);
     }
 }
 
@@ -551,84 +591,100 @@ __global__ void __launch_bounds__(256) k_cgemm_gen_f32(const float2* __restrict_
         }
 }
 
-// bar(L) -> gradient slot, one thread per (w, v, s, j) record in the order of k_vjp_left.
+// Warp w of a scatter launch: record row (wl, v, s) and nodes 32 b .. 32 b + 31 of it, one
+// node per lane (rows of nrow external points; nblk = ceil(nq / 32) blocks per row).
+struct WarpRec {
+    int wl, vi, s, j;
+    bool live, in;
+};
+__device__ __forceinline__ WarpRec warp_record(const ClassJob& J, int nrow) {
+    WarpRec q;
+    const int nblk = (J.nq + 31) / 32;
+    const size_t gw = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const size_t rows = (size_t)J.nw_chunk * J.ns * nrow;
+    q.in = gw < rows * nblk;                       // uniform over the warp
+    const size_t row = q.in ? gw / nblk : 0;
+    q.j = (int)(gw % nblk) * 32 + (int)(threadIdx.x & 31);
+    q.live = q.in && q.j < J.nq;
+    q.j = min(q.j, J.nq - 1);
+    q.vi = (int)(row % nrow);
+    q.s = (int)((row / nrow) % J.ns);
+    q.wl = (int)(row / nrow / J.ns);
+    return q;
+}
+
+// bar(L) -> gradient slot, one warp per 32 consecutive nodes of a (w, v, s) row.
 template <int R>
 __global__ void k_vjp_left_f32(VertexF VG, DfGrids G, ClassJob J, const df* __restrict__ wgrid,
                                const df* __restrict__ vgrid, const float2* __restrict__ gL) {
-    const size_t inner = (size_t)J.nw_chunk * J.ns * J.nL;
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= inner * J.nq) return;
-    const int j = (int)(idx / inner);
-    size_t rest = idx % inner;
-    const int vi = (int)(rest % J.nL);
-    rest /= J.nL;
-    const int s = (int)(rest % J.ns);
-    const int wl = (int)(rest / J.ns);
+    const WarpRec q = warp_record(J, J.nL);
+    if (!q.in) return;
     const ChannelMaps& M = c_maps[R];
-    const RecArgs a = rec_args<false>(G, J, wgrid, vgrid, wl, vi, s, j);
-    const size_t K = (size_t)4 * J.ns * J.nq, kcol = ((size_t)s * J.nq + j) * 4;
-    const size_t rowbase = (size_t)wl * 4 * J.nL + (size_t)vi * 4;
+    const RecArgs a = rec_args<false>(G, J, wgrid, vgrid, q.wl, q.vi, q.s, q.j);
+    const size_t K = (size_t)4 * J.ns * J.nq, kcol = ((size_t)q.s * J.nq + q.j) * 4;
+    const size_t rowbase = (size_t)q.wl * 4 * J.nL + (size_t)q.vi * 4;
     float2 bar[16];
     for (int A = 0; A < 4; ++A)
-        for (int B = 0; B < 4; ++B) bar[M.cL[A][B]] = gL[(rowbase + A) * K + kcol + B];
-    vertex_part_adj_f32<R>(VG, G, a.parts, false, a.what, a.w, a.vext, a.vpp, bar);
+        for (int B = 0; B < 4; ++B)
+            bar[M.cL[A][B]] = q.live ? gL[(rowbase + A) * K + kcol + B] : make_float2(0.f, 0.f);
+    vertex_part_adj_f32<R>(VG, G, a.parts, false, a.what, a.w, a.vext, a.vpp, bar, q.live);
 }
 
-// bar(R') -> bar(R) = sum_B conj(Pi[B][D]) bar(R')[C][B] -> gradient slot (want_vertex), or
-// bar(Pi)[B][D] += sum_C conj(R[D][C]) bar(R')[C][B] (gPi), in the thread orders of k_vjp_right.
+// bar(R') -> bar(R)[D][C] = sum_B conj(Pi[B][D]) bar(R')[C][B] -> gradient slot, one warp per
+// 32 consecutive nodes of a (w, v', s) row.
 template <int R>
-__global__ void k_vjp_right_f32(VertexF V, VertexF VG, bool want_vertex, DfGrids G, ClassJob J,
-                                const df* __restrict__ wgrid, const df* __restrict__ vgrid,
-                                const double2* __restrict__ Pi, const float2* __restrict__ gRp,
-                                double2* __restrict__ gPi) {
-    const size_t inner = (size_t)J.nw_chunk * J.ns * J.nR;
+__global__ void k_vjp_right_f32(VertexF VG, DfGrids G, ClassJob J, const df* __restrict__ wgrid,
+                                const df* __restrict__ vgrid, const double2* __restrict__ Pi,
+                                const float2* __restrict__ gRp) {
+    const WarpRec q = warp_record(J, J.nR);
+    if (!q.in) return;
+    const ChannelMaps& M = c_maps[R];
+    const RecArgs a = rec_args<true>(G, J, wgrid, vgrid, q.wl, q.vi, q.s, q.j);
+    const size_t K = (size_t)4 * J.ns * J.nq, kcol = ((size_t)q.s * J.nq + q.j) * 4;
+    const size_t rowbase = (size_t)q.wl * 4 * J.nR + (size_t)q.vi * 4;
+    const double2* P = Pi + ((size_t)q.wl * J.nq + q.j) * 16;
+    float2 bar[16];
+    for (int D = 0; D < 4; ++D)
+        for (int C = 0; C < 4; ++C) {
+            float2 acc = make_float2(0.f, 0.f);
+            if (q.live)
+                for (int B = 0; B < 4; ++B)
+                    cmac2(acc, make_float2((float)P[4 * B + D].x, -(float)P[4 * B + D].y),
+                          gRp[(rowbase + C) * K + kcol + B]);
+            bar[M.cR[D][C]] = acc;
+        }
+    vertex_part_adj_f32<R>(VG, G, a.parts, true, a.what, a.w, a.vpp, a.vext, bar, q.live);
+}
+
+// bar(Pi)[w][j][B][D] += sum_C conj(R[D][C]) bar(R')[C][B], one thread per (w, v', s, j)
+// record with consecutive threads on consecutive nodes (whose Pi entries differ).
+template <int R>
+__global__ void k_vjp_pi_f32(VertexF V, DfGrids G, ClassJob J, const df* __restrict__ wgrid,
+                             const df* __restrict__ vgrid, const float2* __restrict__ gRp, double2* __restrict__ gPi) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= inner * J.nq) return;
-    int j, vi, s, wl;
-    size_t rest;
-    if (gPi) {
-        j = (int)(idx % J.nq);
-        rest = idx / J.nq;
-    } else {
-        j = (int)(idx / inner);
-        rest = idx % inner;
-    }
-    vi = (int)(rest % J.nR);
+    if (idx >= (size_t)J.nw_chunk * J.ns * J.nR * J.nq) return;
+    const int j = (int)(idx % J.nq);
+    size_t rest = idx / J.nq;
+    const int vi = (int)(rest % J.nR);
     rest /= J.nR;
-    s = (int)(rest % J.ns);
-    wl = (int)(rest / J.ns);
+    const int s = (int)(rest % J.ns);
+    const int wl = (int)(rest / J.ns);
     const ChannelMaps& M = c_maps[R];
     const RecArgs a = rec_args<true>(G, J, wgrid, vgrid, wl, vi, s, j);
     const size_t K = (size_t)4 * J.ns * J.nq, kcol = ((size_t)s * J.nq + j) * 4;
     const size_t rowbase = (size_t)wl * 4 * J.nR + (size_t)vi * 4;
-    float2 grp[4][4];   // [C][B]
-    for (int C = 0; C < 4; ++C)
-        for (int B = 0; B < 4; ++B) grp[C][B] = gRp[(rowbase + C) * K + kcol + B];
-    if (want_vertex) {
-        const double2* P = Pi + ((size_t)wl * J.nq + j) * 16;
-        float2 bar[16];
-        for (int D = 0; D < 4; ++D)
+    float2 g[16];
+    vertex_part_f32<R>(V, G, a.parts, true, a.what, a.w, a.vpp, a.vext, g);
+    double2* dst = gPi + ((size_t)wl * J.nq + j) * 16;
+    for (int B = 0; B < 4; ++B)
+        for (int D = 0; D < 4; ++D) {
+            float2 acc = make_float2(0.f, 0.f);
             for (int C = 0; C < 4; ++C) {
-                float2 acc = make_float2(0.f, 0.f);
-                for (int B = 0; B < 4; ++B) cmac2(acc, make_float2((float)P[4 * B + D].x, -(float)P[4 * B + D].y), grp[C][B]);
-                bar[M.cR[D][C]] = acc;
+                const float2 rv = g[M.cR[D][C]];
+                cmac2(acc, make_float2(rv.x, -rv.y), gRp[(rowbase + C) * K + kcol + B]);
             }
-        vertex_part_adj_f32<R>(VG, G, a.parts, true, a.what, a.w, a.vpp, a.vext, bar);
-    }
-    if (gPi) {
-        float2 g[16];
-        vertex_part_f32<R>(V, G, a.parts, true, a.what, a.w, a.vpp, a.vext, g);
-        double2* dst = gPi + ((size_t)wl * J.nq + j) * 16;
-        for (int B = 0; B < 4; ++B)
-            for (int D = 0; D < 4; ++D) {
-                float2 acc = make_float2(0.f, 0.f);
-                for (int C = 0; C < 4; ++C) {
-                    const float2 rv = g[M.cR[D][C]];
-                    cmac2(acc, make_float2(rv.x, -rv.y), grp[C][B]);
-                }
-                atomic_cadd(dst + 4 * B + D, make_double2(acc.x, acc.y));
-            }
-    }
+            atomic_cadd(dst + 4 * B + D, make_double2(acc.x, acc.y));
+        }
 }
 }  // namespace
 }  // namespace kb
@@ -834,7 +890,7 @@ static kb_status vjp_mixed_impl(kb_ctx* ctx, int sl, int sr, int sgo, int pi_kin
                 }
                 {
                     KB_LAUNCH(ctx, st, "k_vjp_left_f32");
-                    const size_t tot = (size_t)J.nw_chunk * ns * nL * g.nq;
+                    const size_t tot = (size_t)J.nw_chunk * ns * nL * ((g.nq + 31) / 32) * 32;
                     k_vjp_left_f32<R><<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(GVL, G, J, wgrid, vgrid, gL);
                 }
             }
@@ -848,17 +904,18 @@ static kb_status vjp_mixed_impl(kb_ctx* ctx, int sl, int sr, int sgo, int pi_kin
                 }
                 if (want_gr)
                     KB_CUDA_TRY(ctx, cudaMemsetAsync(gPi, 0, (size_t)J.nw_chunk * g.nq * 16 * sizeof(double2), st));
-                const size_t tot = (size_t)J.nw_chunk * ns * nR * g.nq;
                 if (want_r) {
                     KB_LAUNCH(ctx, st, "k_vjp_right_f32");
-                    k_vjp_right_f32<R><<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(VRt, GVR, true, G, J, wgrid,
-                                                                                     vgrid, Pi, gRp, nullptr);
+                    const size_t tot = (size_t)J.nw_chunk * ns * nR * ((g.nq + 31) / 32) * 32;
+                    k_vjp_right_f32<R><<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(GVR, G, J, wgrid, vgrid, Pi,
+                                                                                     gRp);
                 }
                 if (want_gr) {
                     {
-                        KB_LAUNCH(ctx, st, "k_vjp_right_f32");
-                        k_vjp_right_f32<R><<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(VRt, GVR, false, G, J, wgrid,
-                                                                                         vgrid, Pi, gRp, gPi);
+                        KB_LAUNCH(ctx, st, "k_vjp_pi_f32");
+                        const size_t tot = (size_t)J.nw_chunk * ns * nR * g.nq;
+                        k_vjp_pi_f32<R><<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(VRt, G, J, wgrid, vgrid, gRp,
+                                                                                      gPi);
                     }
                     KB_LAUNCH(ctx, st, "k_vjp_gr");
                     k_vjp_gr<<<dim3((g.nq + 127) / 128, J.nw_chunk), 128, 0, st>>>(ctx->m, J, g.A, ctx->d_xq, ctx->d_wq,
