@@ -199,9 +199,10 @@ def dist_setup():
 # --------------------------------------------------------------------------------------
 # CPU oracle timing (reference arm and cpu_baseline)
 # --------------------------------------------------------------------------------------
-def oracle_rate(budget_s=12.0, seed=0):
+def oracle_rate(budget_s=12.0, seed=0, nthreads=0):
     """Oracle points/s on a stratified sample of the workload (all channels and classes,
-    sample sizes scaled to roughly budget_s of CPU time); returns (rate, description)."""
+    sample sizes scaled to roughly budget_s of CPU time) on nthreads threads (0: all host
+    cores); returns (rate, threads, description, elapsed)."""
     import seeded as S
     from oracle import oracle as O
     ch = S.seeded_vertex(GRIDS, U, seed=seed)
@@ -211,11 +212,11 @@ def oracle_rate(budget_s=12.0, seed=0):
     rng = np.random.default_rng(seed)
     shapes = {"K1": (GRIDS["n1"],), "K2": (GRIDS["n2w"], GRIDS["n2v"]), "K2p": (GRIDS["n2w"], GRIDS["n2v"]),
               "K3": (GRIDS["n3w"], GRIDS["n3v"], GRIDS["n3v"])}
-    cores = os.cpu_count() or 1
+    cores = nthreads or os.cpu_count() or 1
     # calibrate on a few K3 points
     idx = [tuple(int(rng.integers(0, n)) for n in shapes["K3"]) for _ in range(max(4, cores))]
     t0 = time.perf_counter()
-    O.bubble_class(V, V, P, 0, "K3", NQ, idx=idx)
+    O.bubble_class(V, V, P, 0, "K3", NQ, idx=idx, nthreads=nthreads)
     per_pt = (time.perf_counter() - t0) / len(idx)
     n_k3 = int(max(cores, min(4096, budget_s / 3 / 1.6 / max(per_pt, 1e-6))))
     n_small = max(cores, n_k3 // 4)
@@ -224,7 +225,7 @@ def oracle_rate(budget_s=12.0, seed=0):
         for cls, n in (("K1", n_small), ("K2", n_small), ("K2p", n_small), ("K3", n_k3)):
             idx = [tuple(int(rng.integers(0, m)) for m in shapes[cls]) for _ in range(n)]
             t0 = time.perf_counter()
-            O.bubble_class(V, V, P, r, cls, NQ, idx=idx)
+            O.bubble_class(V, V, P, r, cls, NQ, idx=idx, nthreads=nthreads)
             dt = time.perf_counter() - t0
             elapsed += dt
             sampled += n
@@ -869,7 +870,9 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and len(chans) == 3:
         rate, cores, desc, _ = oracle_rate(budget_s=args.ref_budget)
-        cpu = {"value": rate, "unit": "points/s", "cores": cores, "kind": "oracle", "sample": desc}
+        rate1, _, desc1, _ = oracle_rate(budget_s=4.0, seed=1, nthreads=1)
+        cpu = {"value": rate, "unit": "points/s", "cores": cores, "kind": "oracle", "sample": desc,
+               "single_thread": {"value": rate1, "unit": "points/s", "cores": 1, "sample": desc1}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
