@@ -540,11 +540,16 @@ def run_vjp(args):
     from paper_2405_20996_gb300.engine import Engine
     prec = "fp64" if args.precision == "fp64" else "mixed"
     dt = torch.complex128 if prec == "fp64" else torch.complex64
-    g = dict(n1=201, n2w=81, n2v=81, n3w=41, n3v=41)
+    large = args.workload == "vjp-large"
+    if large:      # the largest single-instance workload
+        g, nq, u, temp = dict(n1=801, n2w=201, n2v=201, n3w=101, n3v=101), 8001, 3.0, 0.01
+    else:
+        g, nq, u, temp = dict(n1=201, n2w=81, n2v=81, n3w=41, n3v=41), NQ, U, T
     dev = torch.device("cuda", 0)
-    e = Engine(g, NQ, device=0)
-    e.set_model(DELTA, T)
-    e.set_vertex(0, U=U, has_R=True, channels=S.seeded_vertex(g, U, seed=77), dtype=dt)
+    e = Engine(g, nq, device=0)
+    e.set_model(DELTA, temp)
+    e.set_workspace_limit(args.ws_gb << 30)
+    e.set_vertex(0, U=u, has_R=True, channels=S.seeded_vertex(g, u, seed=77), dtype=dt)
     e.alloc_out(1, dtype=dt)
     rng = np.random.default_rng(5)
     for t in e.tensors[1].values():
@@ -575,7 +580,8 @@ def run_vjp(args):
             "value": points / (ms_vjp / 1e3), "unit": "points/s", "n_gpus": 1, "steps": args.steps,
             "warmup": min(args.warmup, 1), "ms_per_step": ms_vjp, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
-            "config": {"workload": "VJP of the one-loop bubble a,p,t; K1 201, K2 81x81, K3 41^3, Nq 4001",
+            "config": {"workload": "VJP of the one-loop bubble a,p,t; K1 %d, K2 %dx%d, K3 %d^3, Nq %d"
+                                   % (g["n1"], g["n2w"], g["n2v"], g["n3w"], nq),
                        "precision": prec, "points_per_step": points},
             "forward": {"precision": prec, "value": points / (ms_fwd / 1e3), "ms_per_step": ms_fwd},
             "kernels_ms": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}}
@@ -652,7 +658,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the wave-model split-K factors instead of timing candidates before the step graph")
     ap.add_argument("--workload", default="step",
-                    choices=["step", "points32", "vjp", "multiloop", "multiloop-large", "parquet", "loop"],
+                    choices=["step", "points32", "vjp", "vjp-large", "multiloop", "multiloop-large", "parquet",
+                             "loop"],
                     help="step: the default three-channel line; points32 / vjp / multiloop: the batching, "
                          "adjoint and multiloop paths")
     args = ap.parse_args()

@@ -328,8 +328,16 @@ kb_status kb_set_workspace_limit(kb_ctx *ctx, unsigned long long bytes);
 
 /* Synchronise the context's device and report device-side failures since the last check:
  * KB_ERR_TIMEOUT if a bounded wait inside a tensor-core kernel gave up (that kernel's output
- * is then incomplete), KB_ERR_CUDA for a CUDA error.  Clears the timeout flag. */
+ * is then incomplete), KB_ERR_CUDA for a CUDA error, and, in a bounds-checked build,
+ * KB_ERR_STATE if a vertex record index from a frequency lookup fell outside its class (the
+ * access was skipped; the message names the first one).  Clears what it reports. */
 kb_status kb_check_device(kb_ctx *ctx);
+
+/* 1 if the library was compiled as the bounds-checked variant (-DKB_CHECKED: every vertex
+ * record index that comes from a frequency lookup — gathers, loop, adjoint scatters — is
+ * checked against its class's record count before the access; the stand-in for a memory
+ * checker), else 0. */
+int kb_build_checked(void);
 
 /* Test hooks of the failure paths (no effect on results otherwise):
  * kb_inject_alloc_failures: the next n workspace allocations of this context report

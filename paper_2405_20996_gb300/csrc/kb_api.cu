@@ -4,6 +4,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "kb_internal.h"
 
@@ -109,6 +110,27 @@ static void prof_clear(kb_ctx* ctx) {
 }
 
 int kb_tc_take_status();
+
+static std::vector<unsigned (*)(unsigned long long*)>& oob_registry() {
+    static std::vector<unsigned (*)(unsigned long long*)> r;
+    return r;
+}
+
+bool kb_oob_register(unsigned (*take)(unsigned long long*)) {
+    oob_registry().push_back(take);
+    return true;
+}
+
+unsigned kb_oob_take_all(unsigned long long* first) {
+    unsigned total = 0;
+    for (auto f : oob_registry()) {
+        unsigned long long fi = 0;
+        const unsigned n = f(&fi);
+        if (n && !total) *first = fi;
+        total += n;
+    }
+    return total;
+}
 
 extern "C" {
 
@@ -430,7 +452,24 @@ kb_status kb_check_device(kb_ctx* ctx) {
     int v = kb_tc_take_status();
     if (v < 0) { ctx->err = "kb_check_device: status read failed"; return KB_ERR_CUDA; }
     if (v) { ctx->err = "a bounded device-side wait gave up (tensor-core contraction)"; return KB_ERR_TIMEOUT; }
+    unsigned long long first = 0;
+    const unsigned oob = kb_oob_take_all(&first);
+    if (oob) {
+        char msg[160];
+        std::snprintf(msg, sizeof msg, "bounds-checked build: %u out-of-range record accesses skipped (first: site %llu, index %lld)",
+                      oob, first >> 48, (long long)(first & 0xffffffffffffull));
+        ctx->err = msg;
+        return KB_ERR_STATE;
+    }
     return KB_OK;
+}
+
+int kb_build_checked(void) {
+#ifdef KB_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 kb_status kb_workspace_bytes(kb_ctx* ctx, unsigned long long* bytes) {

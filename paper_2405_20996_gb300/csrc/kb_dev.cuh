@@ -8,6 +8,39 @@
 
 namespace kb {
 
+// Bounds-checked builds (compiled with -DKB_CHECKED): every vertex record index that comes
+// from a frequency lookup (the stencil corners of a gather, of an adjoint scatter) is checked
+// against the record count of its class before the access; an index outside it is counted,
+// the first one kept (site << 48 | index), and the access skipped.  kb_check_device reports
+// them.  In the normal build the check is the constant true and costs nothing.
+enum { KB_SITE_MIXED_REC = 1, KB_SITE_K2_GATHER = 2, KB_SITE_FP64_REC = 3, KB_SITE_FP64_ADJ = 4,
+       KB_SITE_MIXED_ADJ = 5 };
+#ifdef KB_CHECKED
+namespace {
+__device__ unsigned int kb_oob_count;
+__device__ unsigned long long kb_oob_first;
+unsigned kb_oob_take_here(unsigned long long* first) {
+    unsigned n = 0;
+    if (cudaMemcpyFromSymbol(&n, kb_oob_count, sizeof n) != cudaSuccess) return 0;
+    if (n) {
+        cudaMemcpyFromSymbol(first, kb_oob_first, sizeof *first);
+        const unsigned z = 0;
+        cudaMemcpyToSymbol(kb_oob_count, &z, sizeof z);
+    }
+    return n;
+}
+const bool kb_oob_registered = kb_oob_register(&kb_oob_take_here);
+}  // namespace
+__device__ __forceinline__ bool kb_rec_ok(long long idx, long long n, int site) {
+    if (idx >= 0 && idx < n) return true;
+    if (atomicAdd(&kb_oob_count, 1u) == 0u)
+        kb_oob_first = ((unsigned long long)site << 48) | ((unsigned long long)idx & 0xffffffffffffull);
+    return false;
+}
+#else
+__device__ __forceinline__ bool kb_rec_ok(long long, long long, int) { return true; }
+#endif
+
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {

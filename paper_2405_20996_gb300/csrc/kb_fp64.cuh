@@ -51,6 +51,9 @@ __device__ void acc_class_f64(const VertexDev& V, const Grids& G, int c, int k, 
                 if (k == 0) base = (size_t)iw * 16;
                 else if (k < 3) base = ((size_t)iw * nv + iv) * 16;
                 else base = (((size_t)iw * nv + iv) * nv + ip) * 16;
+                if (!kb_rec_ok((long long)(base / 16), (long long)nw * (k == 0 ? 1 : nv) * (k == 3 ? nv : 1),
+                               KB_SITE_FP64_REC))
+                    continue;
                 double g = f * fw * fv * fp;
 #pragma unroll
                 for (int o = 0; o < 16; ++o) {

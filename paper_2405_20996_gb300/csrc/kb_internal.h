@@ -173,3 +173,8 @@ size_t kb_mixed_workspace_need(const kb_ctx* ctx, int r, unsigned mask);
 kb_status kb_fp64_prepare(kb_ctx* ctx);
 bool kb_tc_prepare(int device);
 bool kb_mixed_prepare(int device);
+// Bounds-checked builds (KB_CHECKED): each translation unit registers a function that reads
+// and clears its count of skipped out-of-range record accesses (and the first offender,
+// site << 48 | index); kb_check_device polls them.
+bool kb_oob_register(unsigned (*take)(unsigned long long* first));
+unsigned kb_oob_take_all(unsigned long long* first);

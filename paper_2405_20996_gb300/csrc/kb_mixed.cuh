@@ -182,7 +182,7 @@ __device__ __forceinline__ void corners(const float2* __restrict__ D, int nd, in
                     of += bt ? st[d] : 0;
                 }
             }
-            bool use = ok && wgt != 0.f;
+            bool use = ok && wgt != 0.f && kb_rec_ok(of, (long long)N[0] * N[1] * N[2], KB_SITE_MIXED_REC);
             wg[e] = use ? wgt : 0.f;
             off[e] = use ? of : -1;
         }
@@ -423,15 +423,17 @@ __device__ __forceinline__ void group_corners_rt(const VertexF& V, const DfGrids
     corner_weights18(stencils7(V, ch, 15, Gr, gw, gv, gp), Gr, g < 2 ? 1.f : -1.f, base, wt, stride);
 }
 
-// One pair of corners (records p and p + 1) of a lane group's gather: lane l reads the
-// 16-byte piece l of each record with a nonzero weight (p already points at piece l).
-__device__ __forceinline__ void corner_pair(const float4* p, float2 w, float2& a0, float2& a1) {
-    if (w.x != 0.f) {
+// One pair of corners (records p and p + 1, record index i0 and i0 + 1 of a class of n
+// records) of a lane group's gather: lane l reads the 16-byte piece l of each record with a
+// nonzero weight (p already points at piece l).
+__device__ __forceinline__ void corner_pair(const float4* p, float2 w, float2& a0, float2& a1, long long i0,
+                                            long long n) {
+    if (w.x != 0.f && kb_rec_ok(i0, n, KB_SITE_K2_GATHER)) {
         const float4 u = __ldg(p);
         a0 = __ffma2_rn(make_float2(w.x, w.x), make_float2(u.x, u.y), a0);
         a1 = __ffma2_rn(make_float2(w.x, w.x), make_float2(u.z, u.w), a1);
     }
-    if (w.y != 0.f) {
+    if (w.y != 0.f && kb_rec_ok(i0 + 1, n, KB_SITE_K2_GATHER)) {
         const float4 u = __ldg(p + 8);
         a0 = __ffma2_rn(make_float2(w.y, w.y), make_float2(u.x, u.y), a0);
         a1 = __ffma2_rn(make_float2(w.y, w.y), make_float2(u.z, u.w), a1);
@@ -439,13 +441,14 @@ __device__ __forceinline__ void corner_pair(const float4* p, float2 w, float2& a
 }
 
 // The same for an exchanged group: components s0, s1 of records p and p + 1 (float2 units).
-__device__ __forceinline__ void corner_pair_x(const float2* p, int s0, int s1, float2 w, float2& a0, float2& a1) {
-    if (w.x != 0.f) {
+__device__ __forceinline__ void corner_pair_x(const float2* p, int s0, int s1, float2 w, float2& a0, float2& a1,
+                                              long long i0, long long n) {
+    if (w.x != 0.f && kb_rec_ok(i0, n, KB_SITE_K2_GATHER)) {
         const float2 u0 = __ldg(p + s0), u1 = __ldg(p + s1);
         a0 = __ffma2_rn(make_float2(w.x, w.x), u0, a0);
         a1 = __ffma2_rn(make_float2(w.x, w.x), u1, a1);
     }
-    if (w.y != 0.f) {
+    if (w.y != 0.f && kb_rec_ok(i0 + 1, n, KB_SITE_K2_GATHER)) {
         const float2 u0 = __ldg(p + 16 + s0), u1 = __ldg(p + 16 + s1);
         a0 = __ffma2_rn(make_float2(w.y, w.y), u0, a0);
         a1 = __ffma2_rn(make_float2(w.y, w.y), u1, a1);
@@ -468,16 +471,18 @@ __device__ __forceinline__ void gather_list(const VertexF& V, const DfGrids& G, 
     const float4* c2p = reinterpret_cast<const float4*>(V.cls[ch][2]) + l;
     const float4* c3 = reinterpret_cast<const float4*>(V.cls[ch][3]) + l;
     const size_t s2 = (size_t)G.N2v * 8, s3 = (size_t)G.N3v * 8, s33 = (size_t)G.N3v * G.N3v * 8;
-    corner_pair(c1 + (size_t)b.x * 8, w[0], a0, a1);
-    corner_pair(c2 + (size_t)b.y * 8, w[1], a0, a1);
-    corner_pair(c2 + (size_t)b.y * 8 + s2, w[2], a0, a1);
-    corner_pair(c2p + (size_t)b.z * 8, w[3], a0, a1);
-    corner_pair(c2p + (size_t)b.z * 8 + s2, w[4], a0, a1);
+    const long long n1 = G.N1, n2 = (long long)G.N2w * G.N2v, n3 = (long long)G.N3w * G.N3v * G.N3v;
+    const long long v2 = G.N2v, v3 = G.N3v, v33 = (long long)G.N3v * G.N3v;
+    corner_pair(c1 + (size_t)b.x * 8, w[0], a0, a1, b.x, n1);
+    corner_pair(c2 + (size_t)b.y * 8, w[1], a0, a1, b.y, n2);
+    corner_pair(c2 + (size_t)b.y * 8 + s2, w[2], a0, a1, b.y + v2, n2);
+    corner_pair(c2p + (size_t)b.z * 8, w[3], a0, a1, b.z, n2);
+    corner_pair(c2p + (size_t)b.z * 8 + s2, w[4], a0, a1, b.z + v2, n2);
     const float4* p3 = c3 + (size_t)b.w * 8;
-    corner_pair(p3, w[5], a0, a1);
-    corner_pair(p3 + s3, w[6], a0, a1);
-    corner_pair(p3 + s33, w[7], a0, a1);
-    corner_pair(p3 + s33 + s3, w[8], a0, a1);
+    corner_pair(p3, w[5], a0, a1, b.w, n3);
+    corner_pair(p3 + s3, w[6], a0, a1, b.w + v3, n3);
+    corner_pair(p3 + s33, w[7], a0, a1, b.w + v33, n3);
+    corner_pair(p3 + s33 + s3, w[8], a0, a1, b.w + v33 + v3, n3);
 }
 
 // The same for an exchanged group: lane l takes components kswap12(2l), kswap12(2l+1).
@@ -491,16 +496,18 @@ __device__ __forceinline__ void gather_list_x(const VertexF& V, const DfGrids& G
 #pragma unroll
     for (int i = 0; i < 9; ++i) w[i] = wt[i * stride];
     const size_t s2 = (size_t)G.N2v * 16, s3 = (size_t)G.N3v * 16, s33 = (size_t)G.N3v * G.N3v * 16;
-    corner_pair_x(V.cls[ch][0] + (size_t)b.x * 16, s0, s1, w[0], a0, a1);
-    corner_pair_x(V.cls[ch][1] + (size_t)b.y * 16, s0, s1, w[1], a0, a1);
-    corner_pair_x(V.cls[ch][1] + (size_t)b.y * 16 + s2, s0, s1, w[2], a0, a1);
-    corner_pair_x(V.cls[ch][2] + (size_t)b.z * 16, s0, s1, w[3], a0, a1);
-    corner_pair_x(V.cls[ch][2] + (size_t)b.z * 16 + s2, s0, s1, w[4], a0, a1);
+    const long long n1 = G.N1, n2 = (long long)G.N2w * G.N2v, n3 = (long long)G.N3w * G.N3v * G.N3v;
+    const long long v2 = G.N2v, v3 = G.N3v, v33 = (long long)G.N3v * G.N3v;
+    corner_pair_x(V.cls[ch][0] + (size_t)b.x * 16, s0, s1, w[0], a0, a1, b.x, n1);
+    corner_pair_x(V.cls[ch][1] + (size_t)b.y * 16, s0, s1, w[1], a0, a1, b.y, n2);
+    corner_pair_x(V.cls[ch][1] + (size_t)b.y * 16 + s2, s0, s1, w[2], a0, a1, b.y + v2, n2);
+    corner_pair_x(V.cls[ch][2] + (size_t)b.z * 16, s0, s1, w[3], a0, a1, b.z, n2);
+    corner_pair_x(V.cls[ch][2] + (size_t)b.z * 16 + s2, s0, s1, w[4], a0, a1, b.z + v2, n2);
     const float2* p3 = V.cls[ch][3] + (size_t)b.w * 16;
-    corner_pair_x(p3, s0, s1, w[5], a0, a1);
-    corner_pair_x(p3 + s3, s0, s1, w[6], a0, a1);
-    corner_pair_x(p3 + s33, s0, s1, w[7], a0, a1);
-    corner_pair_x(p3 + s33 + s3, s0, s1, w[8], a0, a1);
+    corner_pair_x(p3, s0, s1, w[5], a0, a1, b.w, n3);
+    corner_pair_x(p3 + s3, s0, s1, w[6], a0, a1, b.w + v3, n3);
+    corner_pair_x(p3 + s33, s0, s1, w[7], a0, a1, b.w + v33, n3);
+    corner_pair_x(p3 + s33 + s3, s0, s1, w[8], a0, a1, b.w + v33 + v3, n3);
 }
 
 // Host helpers of the mixed path (kb_mixed.cu) shared with its adjoint (kb_vjp.cu): the

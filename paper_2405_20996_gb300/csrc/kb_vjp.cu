@@ -62,6 +62,9 @@ __device__ void acc_class_adj_f64(const VertexDev& Gd, const Grids& G, int c, in
                 else base = (((size_t)iw * nv + iv) * nv + ip) * 16;
                 double g = f * fw * fv * fp;
                 if (g == 0.0) continue;
+                if (!kb_rec_ok((long long)(base / 16), (long long)nw * (k == 0 ? 1 : nv) * (k == 3 ? nv : 1),
+                               KB_SITE_FP64_ADJ))
+                    continue;
 #pragma unroll
                 for (int o = 0; o < 16; ++o) {
                     int src = swap12 ? ((o & 12) | ((o & 1) << 1) | ((o >> 1) & 1)) : o;
@@ -392,7 +395,8 @@ __device__ __forceinline__ void corners_adj_warp(double2* __restrict__ D, bool v
                 of += bt ? st[d] : 0;
             }
         }
-        warp_scatter(D, (ok && wgt != 0.f) ? of : -1, wgt, swap12, bar);
+        const bool use = ok && wgt != 0.f && kb_rec_ok(of, (long long)N[0] * N[1] * N[2], KB_SITE_MIXED_ADJ);
+        warp_scatter(D, use ? of : -1, wgt, swap12, bar);
     }
 }
 

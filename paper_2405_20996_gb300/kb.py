@@ -93,10 +93,11 @@ _SIGS = {
 
 
 def lib(path=None):
-    """Load libkb.so (building it in-tree first if it is missing or stale)."""
+    """Load libkb.so (building it in-tree first if it is missing or stale); with the
+    environment variable KB_CHECKED=1 the bounds-checked variant instead."""
     global _lib
     if _lib is None:
-        p = path or _build.build()
+        p = path or _build.build(checked=os.environ.get("KB_CHECKED") == "1")
         L = C.CDLL(p)
         for name, args in _SIGS.items():
             f = getattr(L, name)
@@ -104,6 +105,8 @@ def lib(path=None):
             f.restype = C.c_int
         L.kb_last_error.argtypes = [C.c_void_p]
         L.kb_last_error.restype = C.c_char_p
+        L.kb_build_checked.argtypes = []
+        L.kb_build_checked.restype = C.c_int
         _lib = L
     return _lib
 
@@ -336,3 +339,8 @@ def kb_check_wait(ctx, stream=None):
 
 def kb_susceptibility_k1(ctx, channel, slot, U, out_ptr, stream=None):
     _check(ctx, lib().kb_susceptibility_k1(ctx, channel, slot, U, out_ptr, stream))
+
+
+def kb_build_checked():
+    """1 if the loaded library is the bounds-checked variant (KB_CHECKED=1 at load)."""
+    return lib().kb_build_checked()
