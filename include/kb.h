@@ -333,6 +333,30 @@ kb_status kb_set_workspace_limit(kb_ctx *ctx, unsigned long long bytes);
  * access was skipped; the message names the first one).  Clears what it reports. */
 kb_status kb_check_device(kb_ctx *ctx);
 
+/* Physical-only Keldysh structure of a vertex (Sec. II.E.2 FDRs, Sec. II.G.3 symmetries).
+ * In the parquet approximation each class of channel r keeps the bare vertex's dependence on
+ * the parity of the quantum indices: with a component c = (a1', a2', a1, a2) written as
+ * (left pair, right pair) of the channel — a: (a1', a2), (a1, a2'); p: (a1', a2'), (a1, a2);
+ * t: (a1', a1), (a2', a2) — K1 depends on the two pairs' parities only (4 distinct numbers of
+ * 16), K2 on the left pair and the right parity (8), K2' on the left parity and the right
+ * pair (8), K3 on both pairs (16).
+ * kb_keldysh_check: residuals of these relations for the classes of `channel` in `slot`
+ *   (host out[8]): out[0..3] max |X_c − X_rep(c)| / max |X| for K1, K2, K2', K3 (0 for a
+ *   physical vertex; K3 is always 0; 0 for an absent class); for K1 in thermal equilibrium
+ *   at temperature T, relative to max |K1|: out[4] causality (the all-even block),
+ *   out[5] conjugation |K1^A − (K1^R)*| and out[6] the bosonic FDR
+ *   |tanh(w/2T) K1^K − (K1^R − K1^A)| (retarded block: the one of component 1 for a and t,
+ *   8 for p; advanced: its mirror; Keldysh: odd-odd); out[7] = 0.  Synchronises `stream`.
+ * kb_vertex_pack: writes the distinct components of class cls (records × 4, 8, 8 or 16, the
+ *   class's element type; device pointer dst, caller-owned) in the compact order d(c) = K1:
+ *   2 pl + pr; K2: 4 x + 2 y + pr (x, y the left pair's indices); K2': 4 pl + 2 x' + y';
+ *   K3: c — each from the smallest component c with that index.
+ * kb_vertex_unpack: the class from its distinct components (the inverse for a physical
+ *   vertex); overwrites the slot's class array.  Both are asynchronous on `stream`. */
+kb_status kb_keldysh_check(kb_ctx *ctx, int slot, int channel, double T, double *out, void *stream);
+kb_status kb_vertex_pack(kb_ctx *ctx, int slot, int channel, int cls, void *dst, void *stream);
+kb_status kb_vertex_unpack(kb_ctx *ctx, int slot, int channel, int cls, const void *src, void *stream);
+
 /* 1 if the library was compiled as the bounds-checked variant (-DKB_CHECKED: every vertex
  * record index that comes from a frequency lookup — gathers, loop, adjoint scatters — is
  * checked against its class's record count before the access; the stand-in for a memory

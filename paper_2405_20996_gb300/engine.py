@@ -180,6 +180,32 @@ class Engine:
         self.bubble(channel, s_r, s_x, s_y, class_mask=k1, beta=1.0, precision=precision, stream=stream)
         return self.susceptibility(channel, s_y, 1.0, stream=stream)
 
+    def keldysh_check(self, slot, channel, T, stream=None):
+        """Residuals of the physical Keldysh structure of a slot's channel (kb_keldysh_check):
+        {"K1", "K2", "K2p", "K3": parity-structure residual, "causality", "conjugation",
+        "fdr": the K1 equilibrium relations at temperature T}, each relative to the class max."""
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        r = kb.kb_keldysh_check(self.ctx, slot, channel, T, st)
+        return dict(zip(("K1", "K2", "K2p", "K3", "causality", "conjugation", "fdr"), r[:7]))
+
+    def pack_physical(self, slot, channel, k, stream=None):
+        """The distinct Keldysh components of class k (kb_vertex_pack): a device tensor
+        [records][4 | 8 | 8 | 16] of the class's dtype."""
+        t = self.tensors[slot][(channel, k)]
+        nd = (4, 8, 8, 16)[k]
+        out = torch.empty((t.numel() // 16, nd), dtype=t.dtype, device=self.device)
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        kb.kb_vertex_pack(self.ctx, slot, channel, k, out.data_ptr(), st)
+        return out
+
+    def unpack_physical(self, slot, channel, k, packed, stream=None):
+        """Overwrite class k of a slot from its distinct components (kb_vertex_unpack)."""
+        t = self.tensors[slot][(channel, k)]
+        assert packed.is_cuda and packed.is_contiguous() and packed.dtype == t.dtype
+        assert packed.numel() == t.numel() // 16 * (4, 8, 8, 16)[k]
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        kb.kb_vertex_unpack(self.ctx, slot, channel, k, packed.data_ptr(), st)
+
     def set_autotune(self, on=True):
         """Time the tensor-core contraction's split-K candidates per shape (kb_set_autotune)."""
         kb.kb_set_autotune(self.ctx, on)

@@ -82,6 +82,9 @@ _SIGS = {
     "kb_set_wait_budget": [C.c_void_p, C.c_longlong],
     "kb_check_wait": [C.c_void_p, C.c_void_p],
     "kb_susceptibility_k1": [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p],
+    "kb_keldysh_check": [C.c_void_p, C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double), C.c_void_p],
+    "kb_vertex_pack": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
+    "kb_vertex_unpack": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p],
     "kb_launch_count": [C.c_void_p, C.POINTER(C.c_ulonglong)],
     "kb_bubble_fp64_noalloc": [C.POINTER(kb_grid_desc), C.c_double, C.c_double, C.c_double,
                                C.POINTER(kb_vertex_desc), C.POINTER(kb_vertex_desc), C.c_int, C.c_int, C.c_int,
@@ -339,6 +342,21 @@ def kb_check_wait(ctx, stream=None):
 
 def kb_susceptibility_k1(ctx, channel, slot, U, out_ptr, stream=None):
     _check(ctx, lib().kb_susceptibility_k1(ctx, channel, slot, U, out_ptr, stream))
+
+
+def kb_keldysh_check(ctx, slot, channel, T, stream=None):
+    """Residuals of the physical Keldysh structure (8 floats, see include/kb.h)."""
+    out = (C.c_double * 8)()
+    _check(ctx, lib().kb_keldysh_check(ctx, slot, channel, T, out, stream))
+    return list(out)
+
+
+def kb_vertex_pack(ctx, slot, channel, cls, dst_ptr, stream=None):
+    _check(ctx, lib().kb_vertex_pack(ctx, slot, channel, cls, dst_ptr, stream))
+
+
+def kb_vertex_unpack(ctx, slot, channel, cls, src_ptr, stream=None):
+    _check(ctx, lib().kb_vertex_unpack(ctx, slot, channel, cls, src_ptr, stream))
 
 
 def kb_build_checked():

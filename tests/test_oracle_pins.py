@@ -499,3 +499,26 @@ def test_parquet_classes_keep_the_bare_vertex_keldysh_structure():
 
     for r in range(3):
         assert [distinct(gam[r][k]) for k in range(4)] == [4, 8, 8, 16], r
+    # the structure is exact and without signs: with each channel's leg pairs (a: (1', 2),
+    # (1, 2'); p: (1', 2'), (1, 2); t: (1', 1), (2', 2)) K1 depends on the two pairs'
+    # parities, K2 on the left pair and the right parity, K2' on the left parity and the
+    # right pair; a plausible slip (the pairs of another channel) breaks it
+    pairs = {0: ((0, 3), (2, 1)), 1: ((0, 1), (2, 3)), 2: ((0, 2), (1, 3))}
+
+    def key(pr, k, c):
+        b = ((c >> 3) & 1, (c >> 2) & 1, (c >> 1) & 1, c & 1)
+        L, R = (b[pr[0][0]], b[pr[0][1]]), (b[pr[1][0]], b[pr[1][1]])
+        return [((L[0] ^ L[1]), (R[0] ^ R[1])), (L, R[0] ^ R[1]), (L[0] ^ L[1], R), (L, R)][k]
+
+    def residual(X, pr, k):
+        X = X.reshape(-1, 16)
+        rep = {}
+        for c in range(16):
+            rep.setdefault(key(pr, k, c), c)
+        return max(np.abs(X[:, c] - X[:, rep[key(pr, k, c)]]).max() for c in range(16)) / np.abs(X).max()
+
+    for r in range(3):
+        for k in range(3):
+            assert residual(gam[r][k], pairs[r], k) == 0.0, (r, k)
+        wrong = pairs[(r + 1) % 3]
+        assert max(residual(gam[r][k], wrong, k) for k in range(3)) > 1e-3, r
