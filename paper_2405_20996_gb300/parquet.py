@@ -25,6 +25,12 @@ Three solvers; the residual bubbles go through the library's plain FP64 path:
   (`sensitivity_U`: one GMRES solve with J^H instead of one Newton solve per parameter).
   The Jacobian products may use the mixed-precision bubble (`jvp_precision`).
 
+symmetric_bse=True takes the symmetrised form the paper recommends for stability,
+    γ_r = ½ [B_r(I_r, Γ) + B_r(Γ, I_r)],
+the right-hand side as is and with I_r and Γ interchanged, averaged (Sec. III.B); it has the
+same fixed point (the two orders agree at the solution), and its Jacobian and adjoint are
+the averages of the two orders' (four bubbles per channel in J v, two adjoint calls).
+
 The state is one flat complex128 device vector holding the 12 class arrays; the vertex
 slots are views of it, so no data moves between a solver update and the next bubble.  The
 solvers' vector algebra (updates, norms, inner products) are PyTorch device operations;
@@ -59,8 +65,10 @@ class ParquetPA:
     iteration is then inexact only in its linear model, and converges to the FP64 fixed
     point."""
 
-    def __init__(self, grids, nq, U, Delta, T, A=5.0, eps=0.0, device=0, jvp_precision="fp64"):
+    def __init__(self, grids, nq, U, Delta, T, A=5.0, eps=0.0, device=0, jvp_precision="fp64",
+                 symmetric_bse=False):
         self.e = Engine(grids, nq, A=A, device=device)
+        self.symmetric_bse = bool(symmetric_bse)
         self.e.set_model(Delta, T, eps)
         self.jvp_precision = jvp_precision
         self.U = float(U)
@@ -121,12 +129,29 @@ class ParquetPA:
 
     # ---- the map and its derivatives ----------------------------------------------------
     def bse(self, gamma):
-        """Right-hand sides B_r(I_r, Γ) of the three Bethe–Salpeter equations at γ."""
+        """Right-hand sides B_r(I_r, Γ) of the three Bethe–Salpeter equations at γ (or their
+        symmetrised form ½ [B_r(I_r, Γ) + B_r(Γ, I_r)])."""
         self.gamma.copy_(gamma)
         for r in range(3):
-            self.e.bubble(r, S_I[r], S_GAMMA, S_OUT, precision="fp64")
-        self.bubbles += 3
+            if self.symmetric_bse:
+                self.e.bubble(r, S_I[r], S_GAMMA, S_OUT, alpha=0.5, precision="fp64")
+                self.e.bubble(r, S_GAMMA, S_I[r], S_OUT, alpha=0.5, beta=1.0, precision="fp64")
+            else:
+                self.e.bubble(r, S_I[r], S_GAMMA, S_OUT, precision="fp64")
+        self.bubbles += 6 if self.symmetric_bse else 3
         return self.out.clone()
+
+    def _jvp_bubbles(self, e, prec):
+        """Σ_r dB_r into S_OUT of engine e: B_r(V_I_r, Γ) + B_r(I_r, V), symmetrised with the
+        interchanged order when the symmetric form is used."""
+        a = 0.5 if self.symmetric_bse else 1.0
+        for r in range(3):
+            e.bubble(r, S_DELTA_I[r], S_GAMMA, S_OUT, alpha=a, precision=prec)
+            e.bubble(r, S_I[r], S_DELTA, S_OUT, alpha=a, beta=1.0, precision=prec)
+            if self.symmetric_bse:
+                e.bubble(r, S_DELTA, S_I[r], S_OUT, alpha=a, beta=1.0, precision=prec)
+                e.bubble(r, S_GAMMA, S_DELTA_I[r], S_OUT, alpha=a, beta=1.0, precision=prec)
+        return 12 if self.symmetric_bse else 6
 
     def residual(self, gamma):
         return gamma - self.bse(gamma)
@@ -138,17 +163,11 @@ class ParquetPA:
                 self.gamma32.copy_(gamma)
                 self._gamma32_of = gamma
             self.delta32.copy_(v)
-            for r in range(3):
-                self.m.bubble(r, S_DELTA_I[r], S_GAMMA, S_OUT, precision="mixed")
-                self.m.bubble(r, S_I[r], S_DELTA, S_OUT, beta=1.0, precision="mixed")
-            self.mixed_bubbles += 6
+            self.mixed_bubbles += self._jvp_bubbles(self.m, "mixed")
             return v - self.out
         self.gamma.copy_(gamma)
         self.delta.copy_(v)
-        for r in range(3):
-            self.e.bubble(r, S_DELTA_I[r], S_GAMMA, S_OUT, precision="fp64")
-            self.e.bubble(r, S_I[r], S_DELTA, S_OUT, beta=1.0, precision="fp64")
-        self.bubbles += 6
+        self.bubbles += self._jvp_bubbles(self.e, "fp64")
         return v - self.out
 
     def adjoint(self, gamma, u):
@@ -157,8 +176,11 @@ class ParquetPA:
         self.gamma.copy_(gamma)
         self.out.copy_(u)
         self.grad.zero_()
+        a = 0.5 if self.symmetric_bse else 1.0
         for r in range(3):
-            self.e.bubble_vjp(r, S_I[r], S_GAMMA, S_OUT, grad_left=S_GRAD, grad_right=S_GRAD)
+            self.e.bubble_vjp(r, S_I[r], S_GAMMA, S_OUT, alpha=a, grad_left=S_GRAD, grad_right=S_GRAD)
+            if self.symmetric_bse:
+                self.e.bubble_vjp(r, S_GAMMA, S_I[r], S_OUT, alpha=a, grad_left=S_GRAD, grad_right=S_GRAD)
         return u - self.grad
 
     def _zero_state(self):
@@ -280,10 +302,14 @@ class ParquetPA:
         ∂F/∂U = −Σ_r [B_r(R̂, Γ) + B_r(I_r, R̂)] (R̂ the bare vertex of unit strength)."""
         kb.kb_set_vertex(self.e.ctx, S_RHAT, True, 1.0)
         self.gamma.copy_(gamma)
+        a = 0.5 if self.symmetric_bse else 1.0
         for r in range(3):
-            self.e.bubble(r, S_RHAT, S_GAMMA, S_OUT, precision="fp64")
-            self.e.bubble(r, S_I[r], S_RHAT, S_OUT, beta=1.0, precision="fp64")
-        self.bubbles += 6
+            self.e.bubble(r, S_RHAT, S_GAMMA, S_OUT, alpha=a, precision="fp64")
+            self.e.bubble(r, S_I[r], S_RHAT, S_OUT, alpha=a, beta=1.0, precision="fp64")
+            if self.symmetric_bse:
+                self.e.bubble(r, S_RHAT, S_I[r], S_OUT, alpha=a, beta=1.0, precision="fp64")
+                self.e.bubble(r, S_GAMMA, S_RHAT, S_OUT, alpha=a, beta=1.0, precision="fp64")
+        self.bubbles += 12 if self.symmetric_bse else 6
         return -self.out.clone()
 
     def sensitivity_U(self, gamma, c, rtol=1e-10, m=30, maxit=300):
@@ -333,8 +359,8 @@ class ParquetSDE(ParquetPA):
     with the damped iteration or Anderson acceleration on z (the Newton–Krylov Jacobian
     of the base class does not include Σ)."""
 
-    def __init__(self, grids, nq, U, Delta, T, n_sig=41, A=5.0, eps=0.0, device=0, form="a"):
-        super().__init__(grids, nq, U, Delta, T, A=A, eps=eps, device=device)
+    def __init__(self, grids, nq, U, Delta, T, n_sig=41, A=5.0, eps=0.0, device=0, form="a", symmetric_bse=False):
+        super().__init__(grids, nq, U, Delta, T, A=A, eps=eps, device=device, symmetric_bse=symmetric_bse)
         if form not in ("a", "p", "ap"):
             raise ValueError("form: 'a', 'p' or 'ap'")
         self.form = form
