@@ -56,7 +56,7 @@ enum { KB_CH_A = 0, KB_CH_P = 1, KB_CH_T = 2 };
 enum { KB_K1 = 0, KB_K2 = 1, KB_K2P = 2, KB_K3 = 3 };
 #define KB_MASK_ALL 0xFu
 enum { KB_PI_GG = 0, KB_PI_GS_SG = 1 };           /* Π = G G,  Π-dot = G S + S G */
-enum { KB_REG_DELTA = 0, KB_REG_U = 1, KB_REG_T = 2 };   /* flow schemes (kb_set_regulator) */
+enum { KB_REG_DELTA = 0, KB_REG_U = 1, KB_REG_T = 2, KB_REG_NONE = 3 };   /* flow schemes (kb_set_regulator) */
 enum { KB_DT_C128 = 0, KB_DT_C64 = 1 };           /* complex double / complex float */
 enum { KB_PREC_FP64 = 0, KB_PREC_MIXED = 1 };     /* plain FP64 / FP32 gather + 3xTF32 tensor-core contraction */
 #define KB_MAX_SLOTS 16
@@ -98,7 +98,11 @@ kb_status kb_set_self_energy(kb_ctx *ctx, int n_sig, double A_sig, const double 
  *                 (so Π = G G scales by λ^2 at Σ = 0), and S^R = (v - eps + i Δ) / (v - eps +
  *                 i Δ - λ Σ^R)^2; `lambda` is ignored by the other schemes;
  *   KB_REG_T      temperature flow, Λ = T (T > 0): S^R = 0, S^K = G^R (i Δ v / (T^2
- *                 cosh^2(v/2T))) G^A.
+ *                 cosh^2(v/2T))) G^A;
+ *   KB_REG_NONE   no flow parameter: S = 0, so that with the Katanin tables of
+ *                 kb_set_self_energy_derivative KB_PI_GS_SG uses G dΣ G alone — the change
+ *                 of G (Dyson equation) along a change dΣ of the self-energy, e.g. for the
+ *                 Jacobian of a self-consistent Σ.
  * S^K is always dG^K/dΛ of the general Keldysh component.  At x = ±1 the tail uses the
  * limits v G -> λ [[0,1],[1,0]] and v S -> [[0,1],[1,0]] (interaction flow) or 0. */
 kb_status kb_set_regulator(kb_ctx *ctx, int kind, double lambda);

@@ -311,9 +311,13 @@ static void prop_matrix(const oprop *P, int which, double v, cplx M[2][2]) {
     } else {
         /* S^R = -(G^R)^2 d[(G^R)^-1]/dLambda: hybridisation -i (G^R)^2; interaction
          * (G^R)^2 g0inv / lam^2; temperature 0.  dmid = d(mid)/dLambda: -2i th;
-         * +2i Delta th / lam^2; -2i Delta d(th)/dT. */
+         * +2i Delta th / lam^2; -2i Delta d(th)/dT.  reg 3: no flow parameter, S = 0, so
+         * that with the dSigma tables S + G dSigma G is the change of G along dSigma. */
         cplx SR, dmid;
-        if (P->reg == 1) {
+        if (P->reg == 3) {
+            SR = 0;
+            dmid = 0;
+        } else if (P->reg == 1) {
             SR = GR * GR * g0inv / (lam * lam);
             dmid = 2.0 * I * P->Delta * th / (lam * lam);
         } else if (P->reg == 2) {
@@ -947,7 +951,7 @@ static void prop_tail2(const oprop *P, int which, int side, cplx N[2][2]) {
     } else if (P->reg == 1) {
         N[0][1] = P->eps - I * P->Delta;
         N[0][0] = -2.0 * I * P->Delta * th;
-    } else if (P->reg == 2) {
+    } else if (P->reg == 2 || P->reg == 3) {
         N[0][1] = 0;
         N[0][0] = 0;
     } else {

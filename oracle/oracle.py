@@ -68,7 +68,7 @@ class _OProp(C.Structure):
                 ("dsigK", C.c_void_p)]
 
 
-REG_DELTA, REG_U, REG_T = 0, 1, 2
+REG_DELTA, REG_U, REG_T, REG_NONE = 0, 1, 2, 3
 
 
 def grid(n, A=5.0):
@@ -107,8 +107,9 @@ class Vertex:
 class Prop:
     """G^R = 1/(v - eps + i Delta - Sigma^R(v)) with optional Sigma tables on a tan grid, and
     the single-scale propagator of the flow scheme reg (REG_DELTA, REG_U with parameter lam:
-    G^R = lam / (v - eps + i Delta - lam Sigma^R), REG_T), with the Katanin substitution
-    S + G dSigma G when dSigma/dLambda tables are given."""
+    G^R = lam / (v - eps + i Delta - lam Sigma^R), REG_T, or REG_NONE: S = 0), with the
+    Katanin substitution S + G dSigma G when dSigma/dLambda tables are given (with REG_NONE
+    the change of G along dSigma)."""
 
     def __init__(self, Delta=1.0, T=0.1, eps=0.0, sigR=None, sigK=None, A_sig=5.0, reg=REG_DELTA, lam=1.0,
                  dsigR=None, dsigK=None, A_dsig=5.0):

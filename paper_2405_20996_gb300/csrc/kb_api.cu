@@ -235,7 +235,7 @@ kb_status kb_set_self_energy_derivative(kb_ctx* ctx, int n, double A, const doub
 
 kb_status kb_set_regulator(kb_ctx* ctx, int kind, double lambda) {
     if (!ctx) return KB_ERR_ARG;
-    if ((kind != KB_REG_DELTA && kind != KB_REG_U && kind != KB_REG_T) ||
+    if ((kind != KB_REG_DELTA && kind != KB_REG_U && kind != KB_REG_T && kind != KB_REG_NONE) ||
         (kind == KB_REG_U && !(lambda > 0 && std::isfinite(lambda)))) {
         ctx->err = "kb_set_regulator: unknown scheme, or lambda <= 0 for the interaction flow";
         return KB_ERR_ARG;

@@ -121,7 +121,10 @@ __device__ inline void prop2x2(const Model& m, int which, double v, double2 P[2]
     } else {
         // S^R = -(G^R)^2 d[(G^R)^-1]/dΛ and dmid = d(mid)/dΛ per scheme
         double2 SR, dmid;
-        if (m.reg == KB_REG_U) {
+        if (m.reg == KB_REG_NONE) {
+            SR = make_double2(0.0, 0.0);
+            dmid = make_double2(0.0, 0.0);
+        } else if (m.reg == KB_REG_U) {
             SR = cscale(cmul(cmul(GR, GR), g0), 1.0 / (lam * lam));
             dmid = make_double2(0.0, 2.0 * m.Delta * th / (lam * lam));
         } else if (m.reg == KB_REG_T) {

@@ -134,7 +134,7 @@ constexpr int LOOP_THREADS = 256;
 //   G: mm = lam, nR = lam (eps - i Delta), nK = 2 lam Delta;
 //   S, hybridisation flow (S^R = -i G^R G^R): mm = 0, nR = -i, nK = 2;
 //   S, interaction flow (S = G / lam at this order): mm = 1, nR = eps - i Delta, nK = 2 Delta;
-//   S, temperature flow: all zero (S^R = 0, S^K falls exponentially).
+//   S, temperature flow: all zero (S^R = 0, S^K falls exponentially); no-flow scheme: S = 0.
 // The Katanin term G dSigma G falls like 1/v'^3 and adds nothing.
 // The line with one insertion of the dSigma tables, G dSigma G (which 2), falls like 1/v'^3:
 // all zero.
@@ -147,7 +147,7 @@ __device__ __forceinline__ LineTail line_tail(const Model& m, int which) {
     if (which == 2) return {0.0, 0.0, make_double2(0.0, 0.0)};
     if (which == 0) return {lam, 2.0 * lam * m.Delta, make_double2(lam * m.eps, -lam * m.Delta)};
     if (m.reg == KB_REG_U) return {1.0, 2.0 * m.Delta, make_double2(m.eps, -m.Delta)};
-    if (m.reg == KB_REG_T) return {0.0, 0.0, make_double2(0.0, 0.0)};
+    if (m.reg == KB_REG_T || m.reg == KB_REG_NONE) return {0.0, 0.0, make_double2(0.0, 0.0)};
     return {0.0, 2.0, make_double2(0.0, -1.0)};
 }
 

@@ -148,7 +148,7 @@ def kb_set_model(ctx, Delta, T, eps=0.0):
     _check(ctx, lib().kb_set_model(ctx, Delta, T, eps))
 
 
-KB_REG_DELTA, KB_REG_U, KB_REG_T = 0, 1, 2
+KB_REG_DELTA, KB_REG_U, KB_REG_T, KB_REG_NONE = 0, 1, 2, 3
 KB_LOOP_UD_ONLY = 4                  # or-ed into kb_loop's line: the up-down vertex alone
 
 

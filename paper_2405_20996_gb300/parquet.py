@@ -322,7 +322,7 @@ class ParquetPA:
     def newton_krylov(self, tol=1e-10, maxit=30, gmres_m=30, gmres_maxit=300, gamma0=None, callback=None):
         """Inexact Newton; returns (γ, history of relative residuals, GMRES products per step).
         callback(step, γ, r) after every Newton step; gamma0 resumes from a saved state."""
-        g = torch.zeros_like(self.gamma) if gamma0 is None else gamma0.clone()
+        g = self._zero_state() if gamma0 is None else gamma0.clone()
         hist, lin = [], []
         for step in range(maxit):
             b = self.bse(g)
@@ -356,8 +356,15 @@ class ParquetSDE(ParquetPA):
     sunset self-energy exactly (pinned against the textbook spectral integral).  form "p"
     takes the p-channel form U [loop(R̂) + loop_ud(B_p(R̂, Γ))] and "ap" the mean of the
     two (the paper combines the forms), both through kb_loop's up-down-only line.  Solved
-    with the damped iteration or Anderson acceleration on z (the Newton–Krylov Jacobian
-    of the base class does not include Σ)."""
+    with the damped iteration, Anderson acceleration or Newton–Krylov on z.
+
+    The Jacobian product J v of F(z) = z − M(z) in a direction v = [v_γ, δΣ^R, δΣ^K] adds to
+    the vertex terms of the base class the change of every propagator along δΣ: the Dyson
+    propagator changes by G δΣ G, which the library provides as the Katanin line of the
+    no-flow scheme (KB_REG_NONE: S = 0, the δΣ tables as the dΣ tables), so each bubble gains
+    B_r(·, ·; Π̇) with Π̇ = G (G δΣ G) + (G δΣ G) G, and each self-energy loop its G δΣ G line
+    (kb_loop line 2); the Schwinger–Dyson bubble X̂ changes by B(R̂, V) + B(R̂, Γ; Π̇).  The
+    adjoint of this map is not built (sensitivities need the Σ-free base class)."""
 
     def __init__(self, grids, nq, U, Delta, T, n_sig=41, A=5.0, eps=0.0, device=0, form="a", symmetric_bse=False):
         super().__init__(grids, nq, U, Delta, T, A=A, eps=eps, device=device, symmetric_bse=symmetric_bse)
@@ -384,6 +391,8 @@ class ParquetSDE(ParquetPA):
             for k in range(4):
                 self.e.attach(S_XP, 1, k, self.xp[k])
         kb.kb_set_vertex(self.e.ctx, S_RHAT, True, 1.0)
+        # S = 0, so that the Katanin line of Π-dot and of the loop is G δΣ G alone
+        self.e.set_regulator(kb.KB_REG_NONE)
 
     def _zero_state(self):
         return torch.zeros(self.n + 2 * self.n_sig, dtype=torch.complex128, device=self.dev)
@@ -420,7 +429,39 @@ class ParquetSDE(ParquetPA):
         sR2, sK2 = self.sde(g)
         return torch.cat([b, sR2, sK2])
 
-    def jvp(self, gamma, v):
-        raise NotImplementedError("the Jacobian products do not include the self-energy")
+    def jvp(self, z, v):
+        """J v at z = [γ, Σ^R, Σ^K] for F(z) = z − M(z), M the joint map of `bse`."""
+        g, sR, sK = self.split(z)
+        vg, vR, vK = self.split(v)
+        self.set_sigma(sR, sK)
+        self.e.set_self_energy_derivative(vR.detach().cpu().numpy(), vK.detach().cpu().numpy(), self.A_sig)
+        self.gamma.copy_(g)
+        self.delta.copy_(vg)
+        # Bethe–Salpeter right-hand sides: the vertex directions, then the propagators' change
+        self.bubbles += self._jvp_bubbles(self.e, "fp64")
+        a = 0.5 if self.symmetric_bse else 1.0
+        for r in range(3):
+            self.e.bubble(r, S_I[r], S_GAMMA, S_OUT, pi_kind=kb.KB_PI_GS_SG, alpha=a, beta=1.0, precision="fp64")
+            self.bubbles += 1
+            if self.symmetric_bse:
+                self.e.bubble(r, S_GAMMA, S_I[r], S_OUT, pi_kind=kb.KB_PI_GS_SG, alpha=a, beta=1.0, precision="fp64")
+                self.bubbles += 1
+        dB = self.out.clone()
+        # Schwinger–Dyson self-energy: the loops' G δΣ G lines and the change of X̂
+        ds = self.e.loop(S_RHAT, self.sig_grid, line=2)
+        forms = ((0, S_X),) if self.form == "a" else (((0, S_X), (1, S_XP)) if self.form == "ap" else ((1, S_XP),))
+        for r, slot in forms:
+            ud = self.form != "a"
+            w = 0.5 if self.form == "a" else 1.0 / len(forms)
+            self.e.bubble(r, S_RHAT, S_GAMMA, slot, precision="fp64")
+            ds = ds + w * self.e.loop(slot, self.sig_grid, line=2, ud_only=ud)
+            self.e.bubble(r, S_RHAT, S_DELTA, slot, precision="fp64")
+            self.e.bubble(r, S_RHAT, S_GAMMA, slot, pi_kind=kb.KB_PI_GS_SG, beta=1.0, precision="fp64")
+            ds = ds + w * self.e.loop(slot, self.sig_grid, ud_only=ud)
+            self.bubbles += 3
+        ds = self.U * ds
+        self.e.set_self_energy_derivative(None)
+        return v - torch.cat([dB, ds[:, 1, 0], ds[:, 1, 1]])
 
-    adjoint = jvp
+    def adjoint(self, z, u):
+        raise NotImplementedError("the adjoint of the self-energy-coupled map is not built")

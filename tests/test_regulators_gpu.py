@@ -68,11 +68,12 @@ def test_bad_regulator_arguments_refused():
     e.close()
 
 
-@pytest.mark.parametrize("reg", [0, 1])
+@pytest.mark.parametrize("reg", [0, 1, 3])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-6)])
 def test_katanin_substitution_matches_oracle(reg, precision, tol):
     """Π-dot with G-dot = S + G dΣ G (self-energy and its derivative as tables) against the
-    oracle with the same tables."""
+    oracle with the same tables; reg 3 (no flow parameter, S = 0) leaves G dΣ G alone, the
+    change of G along dΣ."""
     from paper_2405_20996_gb300.engine import Engine
     cfg = RAGGED
     g = cfg["grids"]
