@@ -218,7 +218,10 @@ __device__ __forceinline__ void pi_entry_t(const Model& m, int pi_kind, double A
         const int B = (R == KB_CH_A) ? 2 * b4p + b3 : (R == KB_CH_P ? 2 * b3 + b4 : 2 * b3p + b4);
         const int D = (R == KB_CH_A) ? 2 * b3p + b4 : (R == KB_CH_P ? 2 * b3p + b4p : 2 * b4p + b3);
         double2 v;
-        if (pi_kind == KB_PI_GS_SG)
+        // G^{2|2} = S^{2|2} = 0: a line with both indices quantum makes the entry vanish
+        if ((b3 == 1 && b3p == 1) || (b4 == 1 && b4p == 1))
+            v = make_double2(0.0, 0.0);
+        else if (pi_kind == KB_PI_GS_SG)
             v = cadd(cmul(P3[b3][b3p], S4[b4][b4p]), cmul(S3[b3][b3p], P4[b4][b4p]));
         else
             v = cmul(P3[b3][b3p], P4[b4][b4p]);

@@ -159,7 +159,7 @@ kb_status kb_scale_classes(kb_ctx* ctx, int r, int so, unsigned classes, double 
 // split-K autotuning of the tensor-core contraction (kb_tc.cu) and the shapes of a mixed
 // bubble's K3 contraction tuned ahead of a graph capture (kb_mixed.cu)
 bool kb_tc_tune(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
-                void* scratch, size_t scratch_bytes, cudaStream_t st);
+                void* scratch, size_t scratch_bytes, bool tri, cudaStream_t st);
 kb_status kb_mixed_tune(kb_ctx* ctx, int r, int sl, int sr, unsigned mask, double beta, cudaStream_t st);
 // symmetry image of a channel's classes into another slot (kb_ops.cu)
 kb_status kb_vertex_image_impl(kb_ctx* ctx, int channel, int src, int dst, unsigned mask, cudaStream_t st);

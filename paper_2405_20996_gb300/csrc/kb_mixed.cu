@@ -947,9 +947,10 @@ __global__ void __launch_bounds__(256) k_mx_cgemm(const float* __restrict__ At, 
         }
 }
 
-// out K3 <- alpha C + beta out, C[wl][(v - vh, A)][(v', C)] for v = vh .. nv-1
+// out K3 <- alpha C + beta out, C[wl][(v - vh, A)][(v', C)] for v = vh .. nv-1; with tri only
+// the points v <= v' (the rest is filled by k_mx_trifill).
 __global__ void k_mx_scatter3(MixedJob J, int w0, int nwc, int nv, int vh, const double2* __restrict__ Cm, void* out,
-                              int odt) {
+                              int odt, int tri) {
     const int nvL = nv - vh;
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     size_t total = (size_t)nwc * nvL * nv * 16;
@@ -960,6 +961,7 @@ __global__ void k_mx_scatter3(MixedJob J, int w0, int nwc, int nv, int vh, const
     rest /= nv;
     int vL = rest % nvL;
     int wl = (int)(rest / nvL);
+    if (tri && vh + vL > vR) return;
     int A = 0, C = 0;
     for (int a = 0; a < 4; ++a)
         for (int c = 0; c < 4; ++c)
@@ -969,13 +971,45 @@ __global__ void k_mx_scatter3(MixedJob J, int w0, int nwc, int nv, int vh, const
     store_out(out, odt, (((size_t)(w0 + wl) * nv + vh + vL) * nv + vR) * 16 + o, gv, J.alpha, J.beta);
 }
 
+// K3 points v > v' of the bosonic frequencies w0 .. nw-1 of a symmetric bubble as images of
+// the computed points (w, v', v) at the same w: conjugation with v <-> v' (a; kind 0) or
+// conjugation after crossing (t; kind 1), component c from component perm(c) with the sign
+// of the conjugation.  Class layout [w][v][v'][16]; reads and writes are disjoint (v' < v
+// read, v > v' written).
+__global__ void k_mx_trifill(void* outp, int dt, int kind, int w0, int nw, int nv) {
+    const size_t npair = (size_t)nv * (nv - 1) / 2;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)(nw - w0) * npair * 16) return;
+    const int c = idx % 16;
+    size_t rest = idx / 16;
+    const size_t pr = rest % npair;
+    const int iw = w0 + (int)(rest / npair);
+    // pair index pr -> (v, v') with v > v': v(v-1)/2 <= pr < v(v+1)/2
+    int v = (int)((1.0 + sqrt(1.0 + 8.0 * (double)pr)) * 0.5);
+    while ((size_t)v * (v - 1) / 2 > pr) --v;
+    while ((size_t)(v + 1) * v / 2 <= pr) ++v;
+    const int vp = (int)(pr - (size_t)v * (v - 1) / 2);
+    const int pc = kind == 0 ? perm_c(c) : perm_x(perm_c(c));
+    const float sg = sign_c(c);
+    const size_t de = (((size_t)iw * nv + v) * nv + vp) * 16 + c;
+    const size_t se = (((size_t)iw * nv + vp) * nv + v) * 16 + pc;
+    if (dt == KB_DT_C128) {
+        const double2 x = reinterpret_cast<const double2*>(outp)[se];
+        reinterpret_cast<double2*>(outp)[de] = make_double2(sg * x.x, -sg * x.y);
+    } else {
+        const float2 x = reinterpret_cast<const float2*>(outp)[se];
+        reinterpret_cast<float2*>(outp)[de] = make_float2(sg * x.x, -sg * x.y);
+    }
+}
+
 }  // namespace kb
 
 using namespace kb;
 
-// tcgen05 contraction of the K3 tiles (kb_tc.cu); returns false if not launched.
+// tcgen05 contraction of the K3 tiles (kb_tc.cu); returns false if not launched.  tri: the
+// output blocks whose points all have v > v' are not computed (filled by k_mx_trifill).
 bool kb_tc_k3(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
-              void* scratch, size_t scratch_bytes, cudaStream_t st);
+              void* scratch, size_t scratch_bytes, bool tri, cudaStream_t st);
 
 static VertexF to_vf(const VertexDev& V, kb_ctx* ctx, bool& ok) {
     VertexF F;
@@ -1205,6 +1239,9 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
         // p (symmetric): rows v >= 0 only, the rest by crossing (k_mx_tile3, symmetry fill)
         const int vh3 = (sym && r == KB_CH_P) ? g.n3v / 2 : 0;
         const int rowsL = 4 * (g.n3v - vh3), rowsR = (int)rows;
+        // a, t (symmetric): the points v > v' of each w are the images of (w, v', v) at the
+        // same w, so the contraction skips the blocks that hold only such points
+        const bool tri3 = sym && r != KB_CH_P;
         for (int w0 = w3_lo; w0 < g.n3w; w0 += chunk) {
             int nwc = std::min(chunk, g.n3w - w0);
             float* TAc = TA;
@@ -1230,7 +1267,7 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
                 }
             }
             bool done = false;
-            if (use_tc) done = kb_tc_k3(ctx, TAc, TBc, Cm, rowsL, rowsR, (int)K, nwc, scratch, tc_scratch, st);
+            if (use_tc) done = kb_tc_k3(ctx, TAc, TBc, Cm, rowsL, rowsR, (int)K, nwc, scratch, tc_scratch, tri3, st);
             if (!done) {
                 KB_LAUNCH(ctx, st, "k_mx_cgemm");
                 k_mx_cgemm<<<dim3((unsigned)((rowsR + 63) / 64), (unsigned)((rowsL + 63) / 64), nwc), 256, 0, st>>>(
@@ -1241,8 +1278,15 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
                 size_t tot = (size_t)nwc * (g.n3v - vh3) * g.n3v * 16;
                 k_mx_scatter3<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(J, w0, nwc, g.n3v, vh3, Cm,
                                                                             const_cast<void*>(VO.cls[r][KB_K3]),
-                                                                            VO.dt[r][KB_K3]);
+                                                                            VO.dt[r][KB_K3], tri3 ? 1 : 0);
             }
+        }
+        if (tri3 && g.n3v > 1) {
+            KB_LAUNCH(ctx, st, "k_mx_trifill");
+            const size_t tot = (size_t)(g.n3w - w3_lo) * g.n3v * (g.n3v - 1) / 2 * 16;
+            k_mx_trifill<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(const_cast<void*>(VO.cls[r][KB_K3]),
+                                                                       VO.dt[r][KB_K3], r == KB_CH_A ? 0 : 1, w3_lo,
+                                                                       g.n3w, g.n3v);
         }
     }
     if (sym) {
@@ -1432,8 +1476,10 @@ kb_status kb_mixed_tune(kb_ctx* ctx, int r, int sl, int sr, unsigned mask, doubl
     const int w3_lo = (sym && r != KB_CH_P) ? g.n3w / 2 : 0;
     const int vh3 = (sym && r == KB_CH_P) ? g.n3v / 2 : 0;
     const int rowsL = 4 * (g.n3v - vh3), rowsR = (int)Lo.rows, nw = g.n3w - w3_lo;
+    const bool tri3 = sym && r != KB_CH_P;
     const int full = std::min(Lo.chunk, nw), last = nw % Lo.chunk;
-    kb_tc_tune(ctx, TA, TB, Cm, rowsL, rowsR, (int)Lo.K, full, scratch, Lo.tc_scratch, st);
-    if (last && last != full) kb_tc_tune(ctx, TA, TB, Cm, rowsL, rowsR, (int)Lo.K, last, scratch, Lo.tc_scratch, st);
+    kb_tc_tune(ctx, TA, TB, Cm, rowsL, rowsR, (int)Lo.K, full, scratch, Lo.tc_scratch, tri3, st);
+    if (last && last != full)
+        kb_tc_tune(ctx, TA, TB, Cm, rowsL, rowsR, (int)Lo.K, last, scratch, Lo.tc_scratch, tri3, st);
     return cudaGetLastError() == cudaSuccess ? KB_OK : KB_ERR_CUDA;
 }

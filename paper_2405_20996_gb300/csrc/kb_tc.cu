@@ -135,7 +135,24 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
 
 struct TcJob {
     int M, N, K, batch, mtiles, ntiles, ksplit, chunks_per_split, nchunks;
+    int tiles;   // output tiles per batch entry that are computed
+    int tri;     // 1: M = N and the tiles whose rows all lie below their columns' diagonal are skipped
 };
+
+// Lowest N tile of M tile mt that is computed.  Rows are (v, A) = 4 v + A and columns
+// (v', C) = 4 v' + C; with tri set, a tile whose smallest row frequency v exceeds its
+// largest column frequency v' (MT mt >= cols (nt + 1)) holds only points with v > v', which
+// the caller fills as the conjugation images of computed points (w, v', v).
+__host__ __device__ inline int tc_nt_lo(int mt, int cols, int ntiles, bool tri) {
+    if (!tri) return 0;
+    const int lo = (MT * mt) / cols;
+    return lo < ntiles ? lo : ntiles - 1;
+}
+__host__ __device__ inline int tc_tiles(int mtiles, int ntiles, int cols, bool tri) {
+    int n = 0;
+    for (int mt = 0; mt < mtiles; ++mt) n += ntiles - tc_nt_lo(mt, cols, ntiles, tri);
+    return n;
+}
 
 // Segmented accumulation: tensor memory holds two buffers of the CTA's 128 x 128 FP32
 // accumulators; the MMA warp restarts a buffer every SEG K chunks and the epilogue warps add
@@ -200,10 +217,14 @@ __global__ void __maxnreg__(96)
     int unit = BOTH ? blockIdx.x : (blockIdx.x >> 1);
     int ks = unit % J.ksplit;
     int rest = unit / J.ksplit;
-    int nt = rest % J.ntiles;
-    rest /= J.ntiles;
-    int mt = rest % J.mtiles;
-    int b = rest / J.mtiles;
+    int tile = rest % J.tiles;
+    int b = rest / J.tiles;
+    int mt = 0, nt = 0;
+    for (mt = 0; mt < J.mtiles; ++mt) {
+        const int lo = tc_nt_lo(mt, NT, J.ntiles, J.tri != 0), cnt = J.ntiles - lo;
+        if (tile < cnt) { nt = lo + tile; break; }
+        tile -= cnt;
+    }
     int c0 = ks * J.chunks_per_split;
     int c1 = min(J.nchunks, c0 + J.chunks_per_split);
     int nck = max(0, c1 - c0);
@@ -363,10 +384,16 @@ __global__ void k_wait_probe(long long budget) {
     if (!mbar_wait(&bar, 0, budget)) atomicOr(&g_tc_status, 8);
 }
 
-// C[b][m][n] = sum over splits of P (FP64)
-__global__ void k_tc_reduce(const double2* __restrict__ P, double2* __restrict__ C, size_t per_split, int ksplit) {
+// C[b][m][n] = sum over splits of P (FP64); with tri (M = N) only the points whose row
+// frequency m / 4 does not exceed the column frequency n / 4 (the others are not read).
+__global__ void k_tc_reduce(const double2* __restrict__ P, double2* __restrict__ C, size_t per_split, int ksplit,
+                            int N, int tri) {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= per_split) return;
+    if (tri) {
+        const int n = (int)(i % N), m = (int)((i / N) % N);
+        if ((m >> 2) > (n >> 2)) return;
+    }
     double re = 0, im = 0;
     for (int k = 0; k < ksplit; ++k) {
         double2 v = P[(size_t)k * per_split + i];
@@ -437,11 +464,11 @@ static int tc_parts(int both) { return both ? TcShape<true>::PARTS : TcShape<fal
 // segments of K each, whose partial sums must fit the scratch; the model rates the fraction
 // of the last wave that is busy, with a small charge per split for the reduction.
 static std::vector<std::pair<double, int>> split_candidates(int device, int both, int M, int N, int K, int batch,
-                                                            size_t scratch_bytes) {
+                                                            size_t scratch_bytes, bool tri) {
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     const int mtiles = (M + MT - 1) / MT, ntiles = (N + tc_cols(both) - 1) / tc_cols(both), nchunks = (K + KC - 1) / KC;
-    const long base = (long)batch * mtiles * ntiles * tc_parts(both);
+    const long base = (long)batch * tc_tiles(mtiles, ntiles, tc_cols(both), tri) * tc_parts(both);
     std::vector<std::pair<double, int>> c;
     for (int s = 1; s <= 64; ++s) {
         if ((nchunks + s - 1) / s < 8 * SEG) break;
@@ -458,41 +485,41 @@ static std::vector<std::pair<double, int>> split_candidates(int device, int both
 
 // Default plan without timing: the tile shape from KB_TC_SHAPE (developer override) or both
 // parts per CTA, and the wave model's best split for it.
-static TcPlan default_plan(int device, int M, int N, int K, int batch, size_t scratch_bytes) {
+static TcPlan default_plan(int device, int M, int N, int K, int batch, size_t scratch_bytes, bool tri) {
     const char* sh = std::getenv("KB_TC_SHAPE");
     const int both = (sh && std::atoi(sh) == 0) ? 0 : 1;
-    return {both, split_candidates(device, both, M, N, K, batch, scratch_bytes)[0].second};
+    return {both, split_candidates(device, both, M, N, K, batch, scratch_bytes, tri)[0].second};
 }
 
-// Autotuned plans, per device and shape (M, N, K, batch); filled by tc_tune.
+// Autotuned plans, per device and shape (M, N, K, batch, triangle); filled by tc_tune.
 static std::mutex g_tune_mu;
-static std::map<std::array<int, 5>, TcPlan> g_tuned;
+static std::map<std::array<int, 6>, TcPlan> g_tuned;
 
-static bool tuned_plan(int device, int M, int N, int K, int batch, TcPlan& p) {
+static bool tuned_plan(int device, int M, int N, int K, int batch, bool tri, TcPlan& p) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tuned.find({device, M, N, K, batch});
+    auto it = g_tuned.find({device, M, N, K, batch, tri ? 1 : 0});
     if (it == g_tuned.end()) return false;
     p = it->second;
     return true;
 }
 
 static bool launch_plan(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
-                        void* scratch, TcPlan plan, cudaStream_t st);
+                        void* scratch, TcPlan plan, bool tri, cudaStream_t st);
 
 static bool launch(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
-                   void* scratch, size_t scratch_bytes, cudaStream_t st) {
+                   void* scratch, size_t scratch_bytes, bool tri, cudaStream_t st) {
     const int nchunks = (K + KC - 1) / KC;
     TcPlan plan;
-    if (!tuned_plan(ctx->device, M, N, K, batch, plan) ||
+    if (!tuned_plan(ctx->device, M, N, K, batch, tri, plan) ||
         (size_t)plan.split * batch * M * N * sizeof(double2) > scratch_bytes)
-        plan = default_plan(ctx->device, M, N, K, batch, scratch_bytes);
+        plan = default_plan(ctx->device, M, N, K, batch, scratch_bytes, tri);
     const char* cps_env = std::getenv("KB_TC_CPS");   // developer override: K chunks per split
     if (cps_env && std::atoi(cps_env) > 0) {
         int cps = std::atoi(cps_env);
         int s = (nchunks + cps - 1) / cps;
         if ((size_t)s * batch * M * N * sizeof(double2) <= scratch_bytes) plan.split = s;
     }
-    return launch_plan(ctx, At, Bt, Cm, M, N, K, batch, scratch, plan, st);
+    return launch_plan(ctx, At, Bt, Cm, M, N, K, batch, scratch, plan, tri, st);
 }
 
 // Time the wave model's three best splits of each tile shape for this contraction shape
@@ -500,14 +527,14 @@ static bool launch(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, i
 // remember the fastest plan.  Reads At/Bt and writes only the scratch and Cm, so any
 // operands of the right shape do; not while the stream is being captured.
 static bool tune(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
-                 void* scratch, size_t scratch_bytes, cudaStream_t st) {
+                 void* scratch, size_t scratch_bytes, bool tri, cudaStream_t st) {
     TcPlan have;
-    if (tuned_plan(ctx->device, M, N, K, batch, have)) return true;
+    if (tuned_plan(ctx->device, M, N, K, batch, tri, have)) return true;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
     std::vector<TcPlan> cand;
     for (int both = 1; both >= 0; --both) {
-        auto c = split_candidates(ctx->device, both, M, N, K, batch, scratch_bytes);
+        auto c = split_candidates(ctx->device, both, M, N, K, batch, scratch_bytes, tri);
         for (size_t i = 0; i < c.size() && i < 3; ++i) cand.push_back({both, c[i].second});
     }
     cudaEvent_t a, b;
@@ -519,7 +546,7 @@ static bool tune(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int
         float ms_min = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
             cudaEventRecord(a, st);
-            if (!launch_plan(ctx, At, Bt, Cm, M, N, K, batch, scratch, pl, st)) { ms_min = 1e30f; break; }
+            if (!launch_plan(ctx, At, Bt, Cm, M, N, K, batch, scratch, pl, tri, st)) { ms_min = 1e30f; break; }
             cudaEventRecord(b, st);
             if (cudaEventSynchronize(b) != cudaSuccess) { ms_min = 1e30f; break; }
             float ms = 0;
@@ -531,27 +558,31 @@ static bool tune(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (std::getenv("KB_TC_VERBOSE"))
-        std::fprintf(stderr, "k_tc_k3 autotune: M %d N %d K %d batch %d -> %s ksplit %d (%.3f ms)\n", M, N, K, batch,
-                     best.both ? "re+im per CTA" : "one part per CTA", best.split, best_ms);
+        std::fprintf(stderr, "k_tc_k3 autotune: M %d N %d K %d batch %d%s -> %s ksplit %d (%.3f ms)\n", M, N, K,
+                     batch, tri ? " (triangle)" : "", best.both ? "re+im per CTA" : "one part per CTA", best.split,
+                     best_ms);
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tuned[{ctx->device, M, N, K, batch}] = best;
+    g_tuned[{ctx->device, M, N, K, batch, tri ? 1 : 0}] = best;
     return true;
 }
 
 static bool launch_plan(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
-                        void* scratch, TcPlan plan, cudaStream_t st) {
+                        void* scratch, TcPlan plan, bool tri, cudaStream_t st) {
     TcJob J;
     J.M = M; J.N = N; J.K = K; J.batch = batch;
     const int cols = tc_cols(plan.both);
     J.mtiles = (M + MT - 1) / MT;
     J.ntiles = (N + cols - 1) / cols;
     J.nchunks = (K + KC - 1) / KC;
-    const int base = batch * J.mtiles * J.ntiles * tc_parts(plan.both);
+    J.tri = (tri && M == N) ? 1 : 0;
+    J.tiles = tc_tiles(J.mtiles, J.ntiles, cols, J.tri != 0);
+    const int base = batch * J.tiles * tc_parts(plan.both);
     J.ksplit = plan.split;
     J.chunks_per_split = (J.nchunks + plan.split - 1) / plan.split;
     if (std::getenv("KB_TC_VERBOSE"))
-        std::fprintf(stderr, "k_tc_k3: M %d N %d K %d batch %d tiles %dx%d (%s) ksplit %d chunks/split %d\n", M, N, K,
-                     batch, J.mtiles, J.ntiles, plan.both ? "re+im" : "part", J.ksplit, J.chunks_per_split);
+        std::fprintf(stderr, "k_tc_k3: M %d N %d K %d batch %d tiles %dx%d, %d computed (%s) ksplit %d chunks/split %d\n",
+                     M, N, K, batch, J.mtiles, J.ntiles, J.tiles, plan.both ? "re+im" : "part", J.ksplit,
+                     J.chunks_per_split);
     CUtensorMap ma, mb;
     if (!make_map(&ma, At, K, M, 4 * batch, MT) || !make_map(&mb, Bt, K, N, 4 * batch, cols)) return false;
     if (!tc_prepare(ctx->device)) return false;
@@ -572,7 +603,7 @@ static bool launch_plan(kb_ctx* ctx, const float* At, const float* Bt, double2* 
     {
         KB_LAUNCH(ctx, st, "k_tc_reduce");
         size_t per = (size_t)batch * M * N;
-        k_tc_reduce<<<(unsigned)((per + 255) / 256), 256, 0, st>>>(P, Cm, per, J.ksplit);
+        k_tc_reduce<<<(unsigned)((per + 255) / 256), 256, 0, st>>>(P, Cm, per, J.ksplit, N, J.tri);
     }
     return cudaGetLastError() == cudaSuccess;
 }
@@ -581,20 +612,22 @@ static bool launch_plan(kb_ctx* ctx, const float* At, const float* Bt, double2* 
 }  // namespace kb
 
 bool kb_tc_k3(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch, void* scratch,
-              size_t scratch_bytes, cudaStream_t st) {
+              size_t scratch_bytes, bool tri, cudaStream_t st) {
     using namespace kb::tc;
     if ((K % 4) != 0 || (reinterpret_cast<uintptr_t>(At) & 15) || (reinterpret_cast<uintptr_t>(Bt) & 15))
         return false;
-    if (ctx->autotune) tune(ctx, At, Bt, Cm, M, N, K, batch, scratch, scratch_bytes, st);
-    return launch(ctx, At, Bt, Cm, M, N, K, batch, scratch, scratch_bytes, st);
+    if (tri && M != N) return false;
+    if (ctx->autotune) tune(ctx, At, Bt, Cm, M, N, K, batch, scratch, scratch_bytes, tri, st);
+    return launch(ctx, At, Bt, Cm, M, N, K, batch, scratch, scratch_bytes, tri, st);
 }
 
 bool kb_tc_tune(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
-                void* scratch, size_t scratch_bytes, cudaStream_t st) {
+                void* scratch, size_t scratch_bytes, bool tri, cudaStream_t st) {
     using namespace kb::tc;
     if ((K % 4) != 0 || (reinterpret_cast<uintptr_t>(At) & 15) || (reinterpret_cast<uintptr_t>(Bt) & 15))
         return false;
-    return tune(ctx, At, Bt, Cm, M, N, K, batch, scratch, scratch_bytes, st);
+    if (tri && M != N) return false;
+    return tune(ctx, At, Bt, Cm, M, N, K, batch, scratch, scratch_bytes, tri, st);
 }
 
 bool kb_tc_prepare(int device) { return kb::tc::tc_prepare(device); }
