@@ -438,6 +438,32 @@ __device__ __forceinline__ void k2_tail(const VertexF& V, const DfGrids& G, cons
     }
 }
 
+// Bosonic stencils of the K2 gather's lookup groups per (group, v of the K2 grid, node):
+// tab[(g * N2v + v) * nq + j] (see stencils7_tab); left side (K2) with (v, v'') = (v, node),
+// right side (K2') with (node, v).  The transfer frequencies do not depend on w, which is set
+// to 0 here.
+template <bool RIGHT, int R>
+__global__ void k_mx_bsten(DfGrids G, int nq, float4* __restrict__ tab) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x, vi = blockIdx.y, g = blockIdx.z;
+    if (j >= nq) return;
+    const df* qn = G.n3v + G.N3v;
+    const df zero = {0.f, 0.f};
+    df gw, gv, gp;
+    if (RIGHT) group_vars<R>(g, zero, qn[j], G.n2v[vi], gw, gv, gp);
+    else group_vars<R>(g, zero, G.n2v[vi], qn[j], gw, gv, gp);
+    float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+    unsigned bits = 1u << 31;
+    if (isfinite(gw.h)) {
+        const float xw = x_est(gw.h, 1.f / G.A);
+        const int k1 = stencil_x(gw, xw, G.n1, G.N1, G.A, o.x);
+        const int k2 = stencil_x(gw, xw, G.n2w, G.N2w, G.A, o.y);
+        const int k3 = stencil_x(gw, xw, G.n3w, G.N3w, G.A, o.z);
+        bits = (unsigned)(k1 + 1) | ((unsigned)(k2 + 1) << 11) | ((unsigned)(k3 + 1) << 21);
+    }
+    o.w = __uint_as_float(bits);
+    tab[((size_t)g * G.N2v + vi) * nq + j] = o;
+}
+
 // K2 (RIGHT = false): out(w, v)[A][C] = sum_j sum_s sum_B L_s(w, v, v''_j)[A][B] N_s(w, j)[B][C]
 //   with L the v-dependent part of Gamma1 without its own K2 class, plus
 //   K2own_s(w, v)[A][B] * SN_s(w)[B][C]  (the own K2 class does not depend on v'').
@@ -472,7 +498,8 @@ __host__ __device__ constexpr size_t k2_smem_bytes() {
 template <bool RIGHT, int R>
 __global__ void __launch_bounds__(128, 6) k_mx_k2(VertexF V, DfGrids G, MixedJob J, const float2* __restrict__ Tab,
                                                const double2* __restrict__ Ssum, const double2* __restrict__ Ntil,
-                                               void* out, int odt, int w_off, int v_off) {
+                                               void* out, int odt, int w_off, int v_off,
+                                               const float4* __restrict__ bst) {
     constexpr int NS = (R == KB_CH_T) ? 2 : 1;
     constexpr int NG = 2 * NS;
     constexpr int CH = 128 / NG;
@@ -512,7 +539,11 @@ __global__ void __launch_bounds__(128, 6) k_mx_k2(VertexF V, DfGrids G, MixedJob
             const int n = tid % CH, g = tid / CH, j = j0 + n;
             int4* bd = cb + g * CH + n;
             float2* wd = cw + (size_t)g * 9 * CH + n;
-            if (j < J.nq - 1) {
+            if (j < J.nq - 1 && bst) {
+                const float4 bt = bst[((size_t)g * G.N2v + vi) * J.nq + j];
+                if (RIGHT) group_corners_tab<R>(V, G, g, w, qn[j], ve, bt, bd, wd, CH);
+                else group_corners_tab<R>(V, G, g, w, ve, qn[j], bt, bd, wd, CH);
+            } else if (j < J.nq - 1) {
                 if (RIGHT) group_corners_rt<R>(V, G, g, w, qn[j], ve, bd, wd, CH);
                 else group_corners_rt<R>(V, G, g, w, ve, qn[j], bd, wd, CH);
             } else {
@@ -1045,7 +1076,7 @@ static size_t cache_side_bytes(const Grids& g, int r, int side) {
 // Workspace layout of one mixed-precision bubble of channel r (byte offsets into the
 // context's workspace) and the bytes it needs.
 struct MixedLayout {
-    size_t off_tab, off_N, off_M, off_S, off_P3, off_K1, off_NT, off_T, rows, K, per_w, tc_scratch, need;
+    size_t off_tab, off_N, off_M, off_S, off_P3, off_K1, off_NT, off_BS, off_T, rows, K, per_w, tc_scratch, need;
     int chunk;
 };
 
@@ -1066,7 +1097,10 @@ static MixedLayout mixed_layout(const kb_ctx* ctx, int r, unsigned mask) {
     size_t szK1 = (size_t)g.n1 * K1_SLICES * 16 * sizeof(double2);
     L.off_NT = (L.off_K1 + szK1 + 255) / 256 * 256;
     size_t szNT = (size_t)2 * g.n2w * ns * g.n3v * 16 * sizeof(double2);
-    L.off_T = (L.off_NT + szNT + 1023) / 1024 * 1024;
+    // bosonic stencils of the K2 gather's lookup groups (one side at a time)
+    L.off_BS = (L.off_NT + szNT + 255) / 256 * 256;
+    size_t szBS = (size_t)2 * ns * g.n2v * g.nq * sizeof(float4);
+    L.off_T = (L.off_BS + szBS + 1023) / 1024 * 1024;
     L.rows = (size_t)4 * g.n3v;
     L.K = (size_t)4 * ns * g.nq;
     L.per_w = 2 * 4 * L.rows * L.K * sizeof(float) + L.rows * L.rows * sizeof(double2) + 1024;
@@ -1195,6 +1229,18 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
         }
         const float2* cacheL = valid_cache(ctx, sl, r, 0);
         const float2* cacheR = valid_cache(ctx, sr, r, 1);
+        // bosonic stencils of the gather's lookup groups, tabulated per (group, v, node)
+        // before each gather side (grids within the packing limits; else found in the gather)
+        float4* bst = (g.n1 <= BSTEN_MAX_N1 && g.n2w <= BSTEN_MAX_NW && g.n3w <= BSTEN_MAX_NW)
+                          ? reinterpret_cast<float4*>(ws + Lo.off_BS)
+                          : nullptr;
+        auto bsten = [&](bool right) {
+            if (!bst) return;
+            KB_LAUNCH(ctx, st, "k_mx_bsten");
+            const dim3 grid((g.nq + 127) / 128, g.n2v, 2 * ns);
+            if (right) k_mx_bsten<true, r><<<grid, 128, 0, st>>>(G, g.nq, bst);
+            else k_mx_bsten<false, r><<<grid, 128, 0, st>>>(G, g.nq, bst);
+        };
         if ((mask >> KB_K2) & 1) {
             int w_off = (sym && r != KB_CH_P) ? g.n2w / 2 : 0, v_off = (sym && r == KB_CH_P) ? g.n2v / 2 : 0;
             void* o = const_cast<void*>(VO.cls[r][KB_K2]);
@@ -1204,9 +1250,10 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
                 k_mx_k2_rc<false, r><<<grid, 128, 0, st>>>(VL, G, J, Nt, Ss, Ntl, o, VO.dt[r][KB_K2], w_off, v_off,
                                                            cacheL);
             } else {
+                bsten(false);
                 KB_LAUNCH(ctx, st, "k_mx_k2");
                 k_mx_k2<false, r><<<grid, 128, k2_smem_bytes<r>(), st>>>(VL, G, J, Nt, Ss, Ntl, o, VO.dt[r][KB_K2],
-                                                                         w_off, v_off);
+                                                                         w_off, v_off, bst);
             }
         }
         if (!sym && ((mask >> KB_K2P) & 1)) {
@@ -1216,9 +1263,10 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
                 k_mx_k2_rc<true, r><<<dim3(g.n2v, g.n2w), 128, 0, st>>>(VR, G, J, Mt, Ss, Ntl, o, VO.dt[r][KB_K2P], 0,
                                                                         0, cacheR);
             } else {
+                bsten(true);
                 KB_LAUNCH(ctx, st, "k_mx_k2p");
                 k_mx_k2<true, r><<<dim3(g.n2v, g.n2w), 128, k2_smem_bytes<r>(), st>>>(VR, G, J, Mt, Ss, Ntl, o,
-                                                                                      VO.dt[r][KB_K2P], 0, 0);
+                                                                                      VO.dt[r][KB_K2P], 0, 0, bst);
             }
         }
     }

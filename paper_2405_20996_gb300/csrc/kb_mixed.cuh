@@ -423,6 +423,69 @@ __device__ __forceinline__ void group_corners_rt(const VertexF& V, const DfGrids
     corner_weights18(stencils7(V, ch, 15, Gr, gw, gv, gp), Gr, g < 2 ? 1.f : -1.f, base, wt, stride);
 }
 
+// Bosonic stencils of a lookup group, tabulated.  The other channels' transfer frequency
+// seen from channel r is v + v'', v'' - v or v - v'' (Sec. II.C.1 parametrisations): it does
+// not depend on the bosonic frequency w of channel r, so its three stencils (K1, K2 and K3
+// bosonic grids) are found once per (group, v, node) and shared by every w.  Packed as
+// (t on the K1 grid, t on the K2 grid, t on the K3 grid, bits) with bits = (k1 + 1) |
+// (k2 + 1) << 11 | (k3 + 1) << 21, bit 31 set when the frequency is not finite; this needs
+// N1 <= 2046 and N2w, N3w <= 1022.
+constexpr int BSTEN_MAX_N1 = 2046, BSTEN_MAX_NW = 1022;
+
+__device__ __forceinline__ Sten7 stencils7_tab(const VertexF& V, int ch, const DfGrids& G, float4 bt, df gv, df gp) {
+    Sten7 S;
+    const unsigned b = __float_as_uint(bt.w);
+    const bool fw = !(b >> 31), fv = isfinite(gv.h), fp = isfinite(gp.h);
+    const float ia = 1.f / G.A;
+    const float xv = fv ? x_est(gv.h, ia) : 0.f, xp = fp ? x_est(gp.h, ia) : 0.f;
+    S.u0 = vcls(V, ch, 0) && fw;
+    S.u1 = vcls(V, ch, 1) && fw && fv;
+    S.u2 = vcls(V, ch, 2) && fw && fp;
+    S.u3 = vcls(V, ch, 3) && fw && fv && fp;
+    S.tw1 = S.tw2 = S.tw3 = S.tv2 = S.tv3 = S.tp2 = S.tp3 = 0.f;
+    S.kw1 = S.kw2 = S.kw3 = S.kv2 = S.kv3 = S.kp2 = S.kp3 = 0;
+    if (S.u0) { S.kw1 = (int)(b & 2047u) - 1; S.tw1 = bt.x; }
+    if (S.u1 || S.u2) { S.kw2 = (int)((b >> 11) & 1023u) - 1; S.tw2 = bt.y; }
+    if (S.u1) S.kv2 = stencil_x(gv, xv, G.n2v, G.N2v, G.A, S.tv2);
+    if (S.u2) S.kp2 = stencil_x(gp, xp, G.n2v, G.N2v, G.A, S.tp2);
+    if (S.u3) {
+        S.kw3 = (int)((b >> 21) & 1023u) - 1;
+        S.tw3 = bt.z;
+        S.kv3 = stencil_x(gv, xv, G.n3v, G.N3v, G.A, S.tv3);
+        S.kp3 = stencil_x(gp, xp, G.n3v, G.N3v, G.A, S.tp3);
+    }
+    return S;
+}
+
+// Channel variables of lookup group g of channel r at the r-variables (w, v, vp): the
+// channel read and its (w, v, vp); an exchanged group reads the crossing partner at the
+// legs with v1 <-> v2 exchanged.
+template <int r>
+__device__ __forceinline__ int group_vars(int g, df w, df v, df vp, df& gw, df& gv, df& gp) {
+    const int c = (g & 1) ? ((r == KB_CH_T) ? KB_CH_P : KB_CH_T) : ((r == KB_CH_A) ? KB_CH_P : KB_CH_A);
+    df L[4];
+    df_legs(r, w, v, vp, L);
+    if (g < 2) {
+        df_vars(c, L, gw, gv, gp);
+        return c;
+    }
+    const int ch = (c == KB_CH_A) ? KB_CH_T : (c == KB_CH_T ? KB_CH_A : KB_CH_P);
+    df S4[4] = {L[0], L[1], L[3], L[2]};
+    df_vars(ch, S4, gw, gv, gp);
+    return ch;
+}
+
+// group_corners_rt with the bosonic stencils taken from the table entry bt.
+template <int r>
+__device__ __forceinline__ void group_corners_tab(const VertexF& V, const DfGrids& Gr, int g, df w, df v, df vp,
+                                                  float4 bt, int4* base, float2* wt, int stride) {
+    const int c = (g & 1) ? ((r == KB_CH_T) ? KB_CH_P : KB_CH_T) : ((r == KB_CH_A) ? KB_CH_P : KB_CH_A);
+    if (!((V.mask >> c) & 1)) { no_corners18(base, wt, stride); return; }
+    df gw, gv, gp;
+    const int ch = group_vars<r>(g, w, v, vp, gw, gv, gp);
+    corner_weights18(stencils7_tab(V, ch, Gr, bt, gv, gp), Gr, g < 2 ? 1.f : -1.f, base, wt, stride);
+}
+
 // One pair of corners (records p and p + 1, record index i0 and i0 + 1 of a class of n
 // records) of a lane group's gather: lane l reads the 16-byte piece l of each record with a
 // nonzero weight (p already points at piece l).
