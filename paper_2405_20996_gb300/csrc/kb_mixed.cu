@@ -345,7 +345,10 @@ __device__ __forceinline__ void k2_tail(const VertexF& V, const DfGrids& G, cons
                                         int odt, int wi, int vi, df w, df ve, float2 acc,
                                         float2 (*rec)[128][17], float2 (*red)[16]) {
     constexpr int NS = (R == KB_CH_T) ? 2 : 1;
+    // the work is done by the first 128 threads; a larger block (k_mx_k2's producer warps)
+    // only joins the barriers
     const int tid = threadIdx.x, o = tid & 15, q = tid >> 4;
+    const bool act = tid < 128;
     const int A = o >> 2, C = o & 3;
     // own K3 class through the node-weighted sums: records at the K3 grid nodes X_m,
     // [0] up-down (pairs with N_0 + N_1, or N_0 for a, p), [1] the exchanged term of the
@@ -355,7 +358,7 @@ __device__ __forceinline__ void k2_tail(const VertexF& V, const DfGrids& G, cons
 #pragma unroll 1
         for (int m0 = 0; m0 < G.N3v; m0 += 128) {
             const int m = m0 + tid;
-            if (m < G.N3v) {
+            if (act && m < G.N3v) {
                 float2 g[16];
                 if (RIGHT) vertex_part_f32<R>(V, G, PARTS_UD, true, 16, w, G.n3v[m], ve, g);
                 else vertex_part_f32<R>(V, G, PARTS_UD, false, 16, w, ve, G.n3v[m], g);
@@ -371,7 +374,7 @@ __device__ __forceinline__ void k2_tail(const VertexF& V, const DfGrids& G, cons
             __syncthreads();
             const int nrec = min(128, G.N3v - m0);
 #pragma unroll 1
-            for (int rr = q; rr < nrec; rr += 8) {
+            for (int rr = q; act && rr < nrec; rr += 8) {
                 const double2* n0 = Nb + (size_t)(m0 + rr) * 16;
                 const double2* n1 = n0 + (size_t)G.N3v * 16;
                 if (!RIGHT) {
@@ -428,7 +431,7 @@ __device__ __forceinline__ void k2_tail(const VertexF& V, const DfGrids& G, cons
             }
         }
     }
-    red[q][o] = acc;
+    if (act) red[q][o] = acc;
     __syncthreads();
     if (q == 0) {
         double re = 0, im = 0;
@@ -469,157 +472,212 @@ __global__ void k_mx_bsten(DfGrids G, int nq, float4* __restrict__ tab) {
 //   K2own_s(w, v)[A][B] * SN_s(w)[B][C]  (the own K2 class does not depend on v'').
 // K2' (RIGHT = true): out(w, v')[A][C] = sum_j sum_s sum_D M_s(w, j)[A][D] R_s(w, v''_j, v')[D][C]
 //   + SM_s(w)[A][D] * K2'own_s(w, v')[D][C].
-// One CTA (128 threads) per (w, v); the interior nodes in chunks of CH = 128 / NG (NG lookup
-// groups: the two other channels, and for t their exchanged partners):
-//   1. corner lists: one thread per (node, group) finds the stencils of the group's classes
-//      and writes its 18 corner weights and 4 class base records to shared memory (a
-//      reading lane then takes 4 bytes per corner); the chunk's rows of the
-//      propagator-vertex table are staged beside them (t: combined per spin record);
-//   2. gather: 8 lanes per node, lane l reading the 16-byte piece l (components 2l, 2l+1) of
-//      every corner record, so one warp-wide load covers the full records of 4 nodes and each
-//      quarter-warp reads one 128-byte line (the L1 delivers one line per quarter-warp and
-//      cycle, so this is the fewest wavefronts a corner can cost); each lane multiplies its
-//      two interpolated components into the table rows they meet and keeps 8 partial outputs
-//      across all nodes;
-//   3. the partials are reduced over lanes and warps into the (A, C)-per-thread layout of
-//      k2_tail, which adds the own classes and stores.
+// One CTA per (w, v) with two warp roles working on chunks of CH = 128 / NG interior nodes
+// (NG lookup groups: the two other channels, and for t their exchanged partners), the
+// chunks' shared-memory buffers double-buffered so that the roles overlap:
+//   producers (K2_PROD threads, warps 4-7), one chunk ahead: the corner lists, one
+//      (node, group) item at a time — the stencils of the group's classes (the bosonic ones
+//      from the k_mx_bsten table), its 18 corner weights and 4 class base records (a
+//      reading lane then takes 4 bytes per corner) — and the chunk's rows of the
+//      propagator-vertex table (t: combined per spin record);
+//   consumers (K2_CONS threads, warps 0-3): 8 lanes per node, lane l reading the 16-byte
+//      piece l (components 2l, 2l+1) of every corner record, so one warp-wide load covers the
+//      full records of 4 nodes and each quarter-warp reads one 128-byte line (the L1 delivers
+//      one line per quarter-warp and cycle, so this is the fewest wavefronts a corner can
+//      cost); each lane multiplies its two interpolated components into the table rows they
+//      meet and keeps 8 partial outputs across all nodes.
+// Hand-over through named barriers: FULL(b) (producers arrive, consumers wait) and EMPTY(b)
+// (consumers arrive, producers wait), each generation completed by all K2_THREADS threads.
+// The corner lists are latency-bound ALU work and the gather is bound by the L1 data stage,
+// so the two overlap instead of alternating.  Then the partials are reduced over lanes and
+// warps into the (A, C)-per-thread layout of k2_tail, which adds the own classes and stores.
 // The endpoint nodes contribute only through the own class and are not gathered.  (Reading
 // each record once for a run of neighbouring nodes, by one thread or by a lane group, cut the
 // L1 traffic but cost more instructions than it saved, measured on the a channel.)
+constexpr int K2_CONS = 128, K2_PROD = 128, K2_THREADS = K2_CONS + K2_PROD;
+constexpr int K2_BAR_FULL = 1, K2_BAR_EMPTY = 3;    // named barriers 1, 2 and 3, 4
+
+// named barrier ID0 + b (b = 0 or 1) with all K2_THREADS threads taking part; the IDs are
+// immediates so that the kernel reserves only the barriers it uses
+template <int ID0>
+__device__ __forceinline__ void nbar_sync(int b) {
+    if (b) asm volatile("bar.sync %0, %1;" ::"n"(ID0 + 1), "n"(K2_THREADS) : "memory");
+    else asm volatile("bar.sync %0, %1;" ::"n"(ID0), "n"(K2_THREADS) : "memory");
+}
+template <int ID0>
+__device__ __forceinline__ void nbar_arrive(int b) {
+    if (b) asm volatile("bar.arrive %0, %1;" ::"n"(ID0 + 1), "n"(K2_THREADS) : "memory");
+    else asm volatile("bar.arrive %0, %1;" ::"n"(ID0), "n"(K2_THREADS) : "memory");
+}
+
+// one chunk buffer: class bases int4[NG][CH], weights float2[NG][9][CH], table rows
+// float4[NS][CH][9]
+template <int R>
+__host__ __device__ constexpr size_t k2_buf_bytes() {
+    constexpr int NS = (R == KB_CH_T) ? 2 : 1;
+    constexpr int CH = 128 / (2 * NS);
+    return (size_t)2 * NS * CH * (sizeof(int4) + 9 * sizeof(float2)) + (size_t)NS * CH * 9 * sizeof(float4);
+}
 template <int R>
 __host__ __device__ constexpr size_t k2_smem_bytes() {
     constexpr int NS = (R == KB_CH_T) ? 2 : 1;
-    constexpr int CH = 128 / (2 * NS);
-    constexpr size_t loop = (size_t)2 * NS * CH * (sizeof(int4) + 9 * sizeof(float2)) + (size_t)NS * CH * 9 * sizeof(float4);
+    constexpr size_t loop = 2 * k2_buf_bytes<R>();
     constexpr size_t tail = (size_t)NS * 128 * 17 * sizeof(float2);
     return loop > tail ? loop : tail;
 }
 
 template <bool RIGHT, int R>
-__global__ void __launch_bounds__(128, 6) k_mx_k2(VertexF V, DfGrids G, MixedJob J, const float2* __restrict__ Tab,
-                                               const double2* __restrict__ Ssum, const double2* __restrict__ Ntil,
-                                               void* out, int odt, int w_off, int v_off,
-                                               const float4* __restrict__ bst) {
+__global__ void __launch_bounds__(K2_THREADS, 3) k_mx_k2(VertexF V, DfGrids G, MixedJob J, const float2* __restrict__ Tab,
+                                                      const double2* __restrict__ Ssum, const double2* __restrict__ Ntil,
+                                                      void* out, int odt, int w_off, int v_off,
+                                                      const float4* __restrict__ bst) {
     constexpr int NS = (R == KB_CH_T) ? 2 : 1;
     constexpr int NG = 2 * NS;
     constexpr int CH = 128 / NG;
+    constexpr size_t BUF = k2_buf_bytes<R>();
     constexpr size_t BASE_BYTES = (size_t)NG * CH * sizeof(int4);
     constexpr size_t CL_BYTES = BASE_BYTES + (size_t)NG * 9 * CH * sizeof(float2);
     extern __shared__ __align__(16) unsigned char k2_smem[];
     __shared__ float2 red[8][16];
-    int4* cb = reinterpret_cast<int4*>(k2_smem);                          // [g][n] class bases
-    float2* cw = reinterpret_cast<float2*>(k2_smem + BASE_BYTES);         // [g][pair][n] weights
-    float4* trow = reinterpret_cast<float4*>(k2_smem + CL_BYTES);         // [s][n][9]
     const int wi = w_off + blockIdx.y, vi = v_off + blockIdx.x;
     const df* qn = G.n3v + G.N3v;
     const df w = G.n2w[wi], ve = G.n2v[vi];
     const int tid = threadIdx.x, wp = tid >> 5, lane = tid & 31, gi = lane >> 3, l = lane & 7;
-    const float2* T0 = Tab + ((size_t)wi * NS) * J.nq * 16;
-    const float2* T1 = T0 + (size_t)J.nq * 16;
-    // this lane's record components 2l + e as matrix entries (X_e, Y_e) of channel R's map
-    int Xe[2], Ye[2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        int xy = 0;
-        for (int q = 0; q < 16; ++q)
-            if (cmap<R>(q >> 2, q & 3) == 2 * l + e) xy = q;
-        Xe[e] = xy >> 2;
-        Ye[e] = xy & 3;
-    }
-    // partial outputs: left o[e][C] belongs to out[X_e][C], right o[e][A] to out[A][Y_e]
+    const int nch = (J.nq - 2 + CH - 1) / CH;          // chunks of the interior nodes 1 .. nq-2
+    // partial outputs of a consumer lane: left o[e][C] belongs to out[X_e][C], right o[e][A]
+    // to out[A][Y_e]
     float2 o[2][4];
 #pragma unroll
     for (int e = 0; e < 2; ++e)
 #pragma unroll
         for (int c = 0; c < 4; ++c) o[e][c] = make_float2(0.f, 0.f);
+    if (tid >= K2_CONS) {
+        // producers: corner lists and table rows of chunk c into buffer c & 1
+        const int pt = tid - K2_CONS;
+        const float2* T0 = Tab + ((size_t)wi * NS) * J.nq * 16;
+        const float2* T1 = T0 + (size_t)J.nq * 16;
 #pragma unroll 1
-    for (int j0 = 1; j0 < J.nq - 1; j0 += CH) {
-        {
-            // 1. corner lists, one (node, group) per thread; a warp's items share g
-            const int n = tid % CH, g = tid / CH, j = j0 + n;
-            int4* bd = cb + g * CH + n;
-            float2* wd = cw + (size_t)g * 9 * CH + n;
-            if (j < J.nq - 1 && bst) {
-                const float4 bt = bst[((size_t)g * G.N2v + vi) * J.nq + j];
-                if (RIGHT) group_corners_tab<R>(V, G, g, w, qn[j], ve, bt, bd, wd, CH);
-                else group_corners_tab<R>(V, G, g, w, ve, qn[j], bt, bd, wd, CH);
-            } else if (j < J.nq - 1) {
-                if (RIGHT) group_corners_rt<R>(V, G, g, w, qn[j], ve, bd, wd, CH);
-                else group_corners_rt<R>(V, G, g, w, ve, qn[j], bd, wd, CH);
-            } else {
-                no_corners18(bd, wd, CH);
+        for (int c = 0; c < nch; ++c) {
+            const int b = c & 1, j0 = 1 + c * CH;
+            if (c >= 2) nbar_sync<K2_BAR_EMPTY>(b);                 // chunk c - 2 consumed
+            unsigned char* buf = k2_smem + b * BUF;
+            int4* cb = reinterpret_cast<int4*>(buf);                      // [g][n] class bases
+            float2* cw = reinterpret_cast<float2*>(buf + BASE_BYTES);     // [g][pair][n] weights
+            float4* trow = reinterpret_cast<float4*>(buf + CL_BYTES);     // [s][n][9]
+            // (node, group) items; a warp's items share g
+#pragma unroll 1
+            for (int it = pt; it < NG * CH; it += K2_PROD) {
+                const int n = it % CH, g = it / CH, j = j0 + n;
+                int4* bd = cb + g * CH + n;
+                float2* wd = cw + (size_t)g * 9 * CH + n;
+                if (j < J.nq - 1 && bst) {
+                    const float4 bt = bst[((size_t)g * G.N2v + vi) * J.nq + j];
+                    if (RIGHT) group_corners_tab<R>(V, G, g, w, qn[j], ve, bt, bd, wd, CH);
+                    else group_corners_tab<R>(V, G, g, w, ve, qn[j], bt, bd, wd, CH);
+                } else if (j < J.nq - 1) {
+                    if (RIGHT) group_corners_rt<R>(V, G, g, w, qn[j], ve, bd, wd, CH);
+                    else group_corners_rt<R>(V, G, g, w, ve, qn[j], bd, wd, CH);
+                } else {
+                    no_corners18(bd, wd, CH);
+                }
             }
+            // table rows; t: left (T0 + T1, T0) pairs with (up-down, exchanged term) since
+            // up-up = up-down + exchanged term and the sum is uu T0 + ud T1; right (T0 + T1, T1)
+#pragma unroll 1
+            for (int it = pt; it < CH * 8; it += K2_PROD) {
+                const int n = it >> 3, piece = it & 7, j = j0 + n;
+                float4 a = make_float4(0.f, 0.f, 0.f, 0.f), bb = a;
+                if (j < J.nq - 1) {
+                    a = ld_stream4(reinterpret_cast<const float4*>(T0 + (size_t)j * 16) + piece);
+                    if (NS == 2) bb = ld_stream4(reinterpret_cast<const float4*>(T1 + (size_t)j * 16) + piece);
+                }
+                if (NS == 1) {
+                    trow[n * 9 + piece] = a;
+                } else {
+                    trow[n * 9 + piece] = make_float4(a.x + bb.x, a.y + bb.y, a.z + bb.z, a.w + bb.w);
+                    trow[(CH + n) * 9 + piece] = RIGHT ? bb : a;
+                }
+            }
+            nbar_arrive<K2_BAR_FULL>(b);                                // chunk c ready
         }
-        // table rows; t: left (T0 + T1, T0) pairs with (up-down, exchanged term) since
-        // up-up = up-down + exchanged term and the sum is uu T0 + ud T1; right (T0 + T1, T1)
+        // the consumers' releases of the last two chunks, so that every barrier generation
+        // is completed
 #pragma unroll 1
-        for (int it = tid; it < CH * 8; it += 128) {
-            const int n = it >> 3, piece = it & 7, j = j0 + n;
-            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-            if (j < J.nq - 1) {
-                a = ld_stream4(reinterpret_cast<const float4*>(T0 + (size_t)j * 16) + piece);
-                if (NS == 2) b = ld_stream4(reinterpret_cast<const float4*>(T1 + (size_t)j * 16) + piece);
-            }
-            if (NS == 1) {
-                trow[n * 9 + piece] = a;
-            } else {
-                trow[n * 9 + piece] = make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
-                trow[(CH + n) * 9 + piece] = RIGHT ? b : a;
-            }
+        for (int c = nch >= 2 ? nch - 2 : 0; c < nch; ++c) nbar_sync<K2_BAR_EMPTY>(c & 1);
+    } else {
+        // consumers: this lane's record components 2l + e as matrix entries (X_e, Y_e) of
+        // channel R's map
+        int Xe[2], Ye[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            int xy = 0;
+            for (int q = 0; q < 16; ++q)
+                if (cmap<R>(q >> 2, q & 3) == 2 * l + e) xy = q;
+            Xe[e] = xy >> 2;
+            Ye[e] = xy & 3;
         }
-        __syncthreads();
-        // 2. gather and contraction, 4 nodes per warp at a time
 #pragma unroll 1
-        for (int n = wp * 4 + gi; n < CH; n += 16) {
-            float2 d0 = make_float2(0.f, 0.f), d1 = d0, x0 = d0, x1 = d0;
-            gather_list<group_channel<R, 0>()>(V, G, cb + n, cw + n, CH, l, d0, d1);
-            gather_list<group_channel<R, 1>()>(V, G, cb + CH + n, cw + 9 * CH + n, CH, l, d0, d1);
-            if (NS == 2) {
-                gather_list_x<group_channel<R, 2>()>(V, G, cb + 2 * CH + n, cw + 2 * 9 * CH + n, CH, l, x0, x1);
-                gather_list_x<group_channel<R, 3>()>(V, G, cb + 3 * CH + n, cw + 3 * 9 * CH + n, CH, l, x0, x1);
-            }
+        for (int c = 0; c < nch; ++c) {
+            const int b = c & 1;
+            nbar_sync<K2_BAR_FULL>(b);                                  // chunk c ready
+            const unsigned char* buf = k2_smem + b * BUF;
+            const int4* cb = reinterpret_cast<const int4*>(buf);
+            const float2* cw = reinterpret_cast<const float2*>(buf + BASE_BYTES);
+            const float4* trow = reinterpret_cast<const float4*>(buf + CL_BYTES);
+            // gather and contraction, 4 nodes per warp at a time
+#pragma unroll 1
+            for (int n = wp * 4 + gi; n < CH; n += 16) {
+                float2 d0 = make_float2(0.f, 0.f), d1 = d0, x0 = d0, x1 = d0;
+                gather_list<group_channel<R, 0>()>(V, G, cb + n, cw + n, CH, l, d0, d1);
+                gather_list<group_channel<R, 1>()>(V, G, cb + CH + n, cw + 9 * CH + n, CH, l, d0, d1);
+                if (NS == 2) {
+                    gather_list_x<group_channel<R, 2>()>(V, G, cb + 2 * CH + n, cw + 2 * 9 * CH + n, CH, l, x0, x1);
+                    gather_list_x<group_channel<R, 3>()>(V, G, cb + 3 * CH + n, cw + 3 * 9 * CH + n, CH, l, x0, x1);
+                }
 #pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const float2 dv = e ? d1 : d0, xv = e ? x1 : x0;
+                for (int e = 0; e < 2; ++e) {
+                    const float2 dv = e ? d1 : d0, xv = e ? x1 : x0;
 #pragma unroll
-                for (int s = 0; s < NS; ++s) {
-                    const float4* tr = trow + (s * CH + n) * 9;
-                    const float2 rv = s == 0 ? dv : xv;
-                    if (!RIGHT) {
-                        // row Y_e of the table: components 4 Y_e .. 4 Y_e + 3
-                        const float4 p0 = tr[2 * Ye[e]], p1 = tr[2 * Ye[e] + 1];
-                        cmac2(o[e][0], rv, make_float2(p0.x, p0.y));
-                        cmac2(o[e][1], rv, make_float2(p0.z, p0.w));
-                        cmac2(o[e][2], rv, make_float2(p1.x, p1.y));
-                        cmac2(o[e][3], rv, make_float2(p1.z, p1.w));
-                    } else {
-                        // column X_e of the table: components 4 A + X_e
+                    for (int s = 0; s < NS; ++s) {
+                        const float4* tr = trow + (s * CH + n) * 9;
+                        const float2 rv = s == 0 ? dv : xv;
+                        if (!RIGHT) {
+                            // row Y_e of the table: components 4 Y_e .. 4 Y_e + 3
+                            const float4 p0 = tr[2 * Ye[e]], p1 = tr[2 * Ye[e] + 1];
+                            cmac2(o[e][0], rv, make_float2(p0.x, p0.y));
+                            cmac2(o[e][1], rv, make_float2(p0.z, p0.w));
+                            cmac2(o[e][2], rv, make_float2(p1.x, p1.y));
+                            cmac2(o[e][3], rv, make_float2(p1.z, p1.w));
+                        } else {
+                            // column X_e of the table: components 4 A + X_e
 #pragma unroll
-                        for (int A = 0; A < 4; ++A) {
-                            const float4 p = tr[2 * A + (Xe[e] >> 1)];
-                            cmac2(o[e][A], (Xe[e] & 1) ? make_float2(p.z, p.w) : make_float2(p.x, p.y), rv);
+                            for (int A = 0; A < 4; ++A) {
+                                const float4 p = tr[2 * A + (Xe[e] >> 1)];
+                                cmac2(o[e][A], (Xe[e] & 1) ? make_float2(p.z, p.w) : make_float2(p.x, p.y), rv);
+                            }
                         }
                     }
                 }
             }
+            nbar_arrive<K2_BAR_EMPTY>(b);                               // chunk c consumed
         }
-        __syncthreads();
+        // sum over the four node groups of a warp
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float2 v = o[e][c];
+                v.x += __shfl_xor_sync(0xffffffffu, v.x, 8);
+                v.y += __shfl_xor_sync(0xffffffffu, v.y, 8);
+                v.x += __shfl_xor_sync(0xffffffffu, v.x, 16);
+                v.y += __shfl_xor_sync(0xffffffffu, v.y, 16);
+                o[e][c] = v;
+            }
     }
-    // 3. sum over the four node groups of a warp, then over the lanes and warps that hold
-    // parts of the same output
-#pragma unroll
-    for (int e = 0; e < 2; ++e)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            float2 v = o[e][c];
-            v.x += __shfl_xor_sync(0xffffffffu, v.x, 8);
-            v.y += __shfl_xor_sync(0xffffffffu, v.y, 8);
-            v.x += __shfl_xor_sync(0xffffffffu, v.x, 16);
-            v.y += __shfl_xor_sync(0xffffffffu, v.y, 16);
-            o[e][c] = v;
-        }
+    __syncthreads();                                                    // every buffer is free
+    // sum over the lanes and warps that hold parts of the same output
     float2* part = reinterpret_cast<float2*>(k2_smem);                   // [warp][l][e][4]
-    if (gi == 0) {
+    if (tid < K2_CONS && gi == 0) {
 #pragma unroll
         for (int e = 0; e < 2; ++e)
 #pragma unroll
@@ -1252,7 +1310,7 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
             } else {
                 bsten(false);
                 KB_LAUNCH(ctx, st, "k_mx_k2");
-                k_mx_k2<false, r><<<grid, 128, k2_smem_bytes<r>(), st>>>(VL, G, J, Nt, Ss, Ntl, o, VO.dt[r][KB_K2],
+                k_mx_k2<false, r><<<grid, K2_THREADS, k2_smem_bytes<r>(), st>>>(VL, G, J, Nt, Ss, Ntl, o, VO.dt[r][KB_K2],
                                                                          w_off, v_off, bst);
             }
         }
@@ -1265,7 +1323,7 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
             } else {
                 bsten(true);
                 KB_LAUNCH(ctx, st, "k_mx_k2p");
-                k_mx_k2<true, r><<<dim3(g.n2v, g.n2w), 128, k2_smem_bytes<r>(), st>>>(VR, G, J, Mt, Ss, Ntl, o,
+                k_mx_k2<true, r><<<dim3(g.n2v, g.n2w), K2_THREADS, k2_smem_bytes<r>(), st>>>(VR, G, J, Mt, Ss, Ntl, o,
                                                                                       VO.dt[r][KB_K2P], 0, 0, bst);
             }
         }
