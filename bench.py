@@ -95,15 +95,19 @@ def mixed_kernel_work(channels=(0, 1, 2)):
     r3t = half(g["n3w"]) * g["n3v"] * nq
     w["k_mx_tile3_both"] = (0 in channels) * r3a * (48 * 64 + 512) + (1 in channels) * r3p * (48 * 64 + 2 * 512) + \
         (2 in channels) * r3t * ((48 + 48) * 64 + 2 * 512)
-    # k_tc_k3 (useful)
+    # k_tc_k3 (useful): 8 flops per complex multiply-add of the points the method needs, i.e.
+    # a, t: the pairs v <= v' (the others are conjugation images, and the contraction skips
+    # the output blocks that hold only v > v'; the diagonal blocks it computes in full are
+    # not credited); p: rows v >= 0 (the rest by crossing), all v'
     N = 4 * g["n3v"]
+    n3 = g["n3v"]
     tc = 0.0
     for r, nw in ((0, half(g["n3w"])), (1, g["n3w"]), (2, half(g["n3w"]))):
         if r not in channels:
             continue
         ns = 2 if r == 2 else 1
-        M = 4 * half(g["n3v"]) if r == 1 else N      # p: rows v >= 0, the rest by crossing
-        tc += 8.0 * M * N * (4 * ns * nq) * nw
+        MN = 4 * half(n3) * N if r == 1 else 16 * n3 * (n3 + 1) // 2
+        tc += 8.0 * MN * (4 * ns * nq) * nw
     w["k_tc_k3"] = tc
     return w
 
