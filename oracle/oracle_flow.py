@@ -15,7 +15,9 @@ fourth-order Runge-Kutta rule with fixed steps.
 
 Parquet approximation with the Schwinger-Dyson equation (Sec. III.B): γ_r = B_r(I_r, Γ),
 Σ = U L(R̂, G) + U L_ud(B_r(R̂, Γ), G) in its a- or p-channel form (L_ud the loop of the up-down
-vertex alone; the two forms, or their mean), at G = G[Σ] (L = 1), by the damped iteration.
+vertex alone), or its t-channel form U L(R̂, G) + U L_uu of B_a(R̂, Γ) with B_t(R̂, Γ) as
+crossing-partner data (sde_map), or the mean of forms, at G = G[Σ] (L = 1), by the damped
+iteration.
 """
 
 import numpy as np
@@ -109,12 +111,51 @@ def mfrg_flow(grids, nq, U, D, T, n_loops, nus, lam0=1e-3, steps=20, A=5.0, mult
     return gam, sR, sK
 
 
+SDE_FORMS = ("a", "p", "ap", "t", "apt")
+
+
+def sde_map(grids, nq, U, Gam, P, nus, form="a"):
+    """The Schwinger-Dyson self-energy (Sec. III.B) at the frequencies nus for the full vertex
+    Gam and the propagators P, [n][2][2] as oracle.loop returns it:
+        Σ = U L(R̂) + U Σ_f L_f / (number of forms),   X̂_r = B_r(R̂, Γ),
+    with R̂ the bare vertex of unit strength and L the loop (Hartree part U L(R̂)).  The bare
+    vertex, a bubble to Γ and the closing line can be drawn in each channel:
+      a: L_ud of X̂_a (a slot with channel a alone, no crossing-partner data): the line joins
+         legs 2' (on Γ) and 2 (on R̂) and carries the spin opposite to the external one;
+      p: L_ud of X̂_p likewise;
+      t: the t bubble holds legs 1', 1 on R̂ and 2', 2 on Γ, so the line must join 1 and 2',
+         and it carries the external spin: with SU(2) (the magnetic combination of the
+         up-up and up-down vertices is minus the up-down vertex with legs 1 and 2 exchanged)
+         and crossing, the up-up t bubble of R̂ with Γ is X̂_t − X[X̂_a], X the exchange of
+         legs 1 and 2; closed on 1 and 2' this is the up-up loop L_uu = L − L_ud of a vertex
+         holding X̂_a in channel a and X̂_t as its crossing-partner data (the exchanged term
+         reads X̂_t at the exchanged legs).
+    form "ap" and "apt" average the forms (the paper combines them)."""
+    Rh = O.Vertex(grids, U=1.0, has_R=True)
+    s = U * O.loop(Rh, P, nq, nus)
+    if form not in SDE_FORMS:
+        raise ValueError("form: one of %s" % (SDE_FORMS,))
+    terms = form
+    X = {}
+    for r in ((0,) if "a" in terms or "t" in terms else ()) + ((1,) if "p" in terms else ()) + \
+            ((2,) if "t" in terms else ()):
+        X[r] = _classes(O.bubble_all(Rh, Gam, P, r, nq))
+    for f in terms:
+        if f in "ap":
+            r = 0 if f == "a" else 1
+            Vx = O.Vertex(grids, channels={r: tuple(X[r])}, include=(r,))
+            s = s + U / len(terms) * O.loop(Vx, P, nq, nus, ud_only=True)
+        else:
+            Vx = O.Vertex(grids, channels={0: tuple(X[0]), 2: tuple(X[2])}, include=(0,))
+            s = s + U / len(terms) * (O.loop(Vx, P, nq, nus) - O.loop(Vx, P, nq, nus, ud_only=True))
+    return s
+
+
 def parquet_sde(grids, nq, U, D, T, nus, mix=0.5, tol=1e-12, maxit=400, A=5.0, form="a"):
     """(γ, Σ^R, Σ^K) of the parquet approximation with the Schwinger-Dyson self-energy in
-    its a-channel form, p-channel form, or the mean of the two (form "a", "p", "ap")."""
+    the form `form` of sde_map ("a", "p", "ap", "t", "apt")."""
     n = len(nus)
     gam, sR, sK = _zero(grids), np.zeros(n, complex), np.zeros(n, complex)
-    Rh = O.Vertex(grids, U=1.0, has_R=True)
     for _ in range(maxit):
         P = O.Prop(Delta=D, T=T, sigR=sR, sigK=sK)
         Gam = _vertex(grids, U, True, gam)
@@ -122,12 +163,7 @@ def parquet_sde(grids, nq, U, D, T, nus, mix=0.5, tol=1e-12, maxit=400, A=5.0, f
         for r in range(3):
             I_r = _vertex(grids, U, True, gam, include=[c for c in range(3) if c != r])
             new[r] = _classes(O.bubble_all(I_r, Gam, P, r, nq))
-        s = U * O.loop(Rh, P, nq, nus)
-        forms = {"a": (0,), "p": (1,), "ap": (0, 1)}[form]
-        for r in forms:
-            X = _classes(O.bubble_all(Rh, Gam, P, r, nq))
-            Vx = O.Vertex(grids, channels={r: tuple(X)}, include=(r,))
-            s = s + U / len(forms) * O.loop(Vx, P, nq, nus, ud_only=True)
+        s = sde_map(grids, nq, U, Gam, P, nus, form)
         scale = max(max(np.abs(new[c][k]).max() for c in range(3) for k in range(4)), np.abs(s).max())
         change = max(max(np.abs(new[c][k] - gam[c][k]).max() for c in range(3) for k in range(4)),
                      np.abs(s[:, 1, 0] - sR).max(), np.abs(s[:, 1, 1] - sK).max()) / scale

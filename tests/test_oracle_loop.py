@@ -262,3 +262,38 @@ def test_up_down_loop_and_the_sde_forms_at_second_order():
         if r == 0:
             assert np.abs(ud - O.loop(X, P, 801, nus) / 2).max() <= 1e-14 * np.abs(ud).max()
         assert np.abs(coef * ud[:, 1, 0].imag - ref).max() <= 3e-3 * np.abs(ref).max(), (r, coef * ud[:, 1, 0].imag, ref)
+
+
+def test_sde_t_form_pins():
+    """The Schwinger-Dyson equation's t-channel form (oracle_flow.sde_map), whose line joins
+    legs 1 and 2' of the t bubble and carries the external spin (the up-up loop of B_a(R̂, Γ)
+    with B_t(R̂, Γ) as crossing-partner data):
+    - second order (Γ = R): the up-down t bubble of R̂ with R vanishes (Γ0's up-up part is
+      zero), so the t form is the a form, i.e. the sunset the a form is pinned to;
+    - third order (Γ = R + Σ_r B_r(R, R), the exact second-order vertex): on the same grids
+      the t form lies exactly at the mean of the a and p forms — which differ by
+      discretisation at this order — while the t term taken with the opposite sign, or twice,
+      does not;
+    - for a seeded vertex the t form is not that mean (it is an independent form)."""
+    from oracle import oracle_flow as F
+    g = dict(n1=41, n2w=13, n2v=13, n3w=9, n3v=9)
+    nq, U = 401, 0.3
+    nus = F.sig_grid(21)
+    P = O.Prop(Delta=1.0, T=0.2)
+    R = O.Vertex(g, U=U, has_R=True)
+    m2 = {f: F.sde_map(g, nq, U, R, P, nus, f) for f in ("a", "t")}
+    assert np.abs(m2["t"] - m2["a"]).max() <= 1e-14 * np.abs(m2["a"]).max()
+    g2 = {r: F._classes(O.bubble_all(R, R, P, r, nq)) for r in range(3)}
+    Gam = F._vertex(g, U, True, g2)
+    m3 = {f: F.sde_map(g, nq, U, Gam, P, nus, f) for f in F.SDE_FORMS}
+    s = np.abs(m3["a"]).max()
+    mid = 0.5 * (m3["a"] + m3["p"])
+    assert np.abs(m3["t"] - mid).max() <= 1e-13 * s
+    assert np.abs(m3["apt"] - (m3["a"] + m3["p"] + m3["t"]) / 3).max() <= 1e-14 * s
+    dt = m3["t"] - m3["a"]                       # the t form's own term, U (L_uu - L_ud(X̂_a))
+    assert np.abs(dt).max() >= 3e-3 * s
+    for wrong in (m3["a"] - dt, m3["a"] + 2 * dt):
+        assert np.abs(wrong - mid).max() >= 0.5 * np.abs(dt).max()
+    Vs = _seeded(U=1.0, seed=3)
+    ms = {f: F.sde_map(G, 201, 1.0, Vs, P, nus, f) for f in ("a", "p", "t")}
+    assert np.abs(ms["t"] - 0.5 * (ms["a"] + ms["p"])).max() >= 1e-2 * np.abs(ms["a"]).max()
