@@ -54,6 +54,9 @@ S_GRAD = 9                  # adjoint accumulation, all channels
 S_RHAT = 10                 # the bare vertex of unit strength, no classes (∂/∂U, the SDE)
 S_X = 11                    # X̂ = B_a(R̂, Γ) of the Schwinger–Dyson equation: channel a only
 S_XP = 12                   # B_p(R̂, Γ), the SDE's p-channel form: channel p only
+S_XT = 13                   # the SDE's t-channel form: channel a = B_a(R̂, Γ) (the S_X arrays),
+                            # channel t = B_t(R̂, Γ) as crossing-partner data, mask {a}
+SDE_FORMS = ("a", "p", "ap", "t", "apt")
 
 
 class ParquetPA:
@@ -354,9 +357,14 @@ class ParquetSDE(ParquetPA):
     with channel a alone and no crossing-partner data, where Γ_s = 2 X̂_ud.  loop(R̂) is the
     Hartree shift per unit U (zero at particle-hole symmetry).  At second order this is the
     sunset self-energy exactly (pinned against the textbook spectral integral).  form "p"
-    takes the p-channel form U [loop(R̂) + loop_ud(B_p(R̂, Γ))] and "ap" the mean of the
-    two (the paper combines the forms), both through kb_loop's up-down-only line.  Solved
-    with the damped iteration, Anderson acceleration or Newton–Krylov on z.
+    takes the p-channel form U [loop(R̂) + loop_ud(B_p(R̂, Γ))], both through kb_loop's
+    up-down-only line.  form "t" draws the bubble in the t channel: R̂ then holds legs 1', 1
+    and Γ legs 2', 2, the closing line joins 1 and 2' and carries the external spin, and
+    with SU(2) and crossing the up-up t bubble is B_t(R̂, Γ) − X[B_a(R̂, Γ)] (X: legs 1 and 2
+    exchanged), so Σ = U [loop(R̂) + loop_uu(S_XT)] with loop_uu = loop − loop_ud of a slot
+    holding B_a(R̂, Γ) in channel a and B_t(R̂, Γ) as its crossing-partner data.  "ap" and
+    "apt" average the forms (the paper combines them).  Solved with the damped iteration,
+    Anderson acceleration or Newton–Krylov on z.
 
     The Jacobian product J v of F(z) = z − M(z) in a direction v = [v_γ, δΣ^R, δΣ^K] adds to
     the vertex terms of the base class the change of every propagator along δΣ: the Dyson
@@ -368,8 +376,8 @@ class ParquetSDE(ParquetPA):
 
     def __init__(self, grids, nq, U, Delta, T, n_sig=41, A=5.0, eps=0.0, device=0, form="a", symmetric_bse=False):
         super().__init__(grids, nq, U, Delta, T, A=A, eps=eps, device=device, symmetric_bse=symmetric_bse)
-        if form not in ("a", "p", "ap"):
-            raise ValueError("form: 'a', 'p' or 'ap'")
+        if form not in SDE_FORMS:
+            raise ValueError("form: one of %s" % (SDE_FORMS,))
         self.form = form
         self.n_sig, self.A_sig = int(n_sig), A
         x = -1.0 + 2.0 * (np.arange(self.n_sig) + 1) / (self.n_sig + 1)
@@ -382,7 +390,16 @@ class ParquetSDE(ParquetPA):
         self.e.tensors[S_X] = {}
         for k in range(4):
             self.e.attach(S_X, 0, k, self.xa[k])
-        if form != "a":
+        if "t" in form:
+            self.xt = [torch.zeros(sh[name], dtype=torch.complex128, device=self.dev) for name in CLASS_NAMES]
+            kb.kb_set_vertex(self.e.ctx, S_XT, False, 0.0)
+            kb.kb_set_vertex_channels(self.e.ctx, S_XT, 1 << 0)
+            kb.kb_set_vertex_symmetric(self.e.ctx, S_XT, False)
+            self.e.tensors[S_XT] = {}
+            for k in range(4):
+                self.e.attach(S_XT, 0, k, self.xa[k])
+                self.e.attach(S_XT, 2, k, self.xt[k])
+        if "p" in form:
             self.xp = [torch.zeros(sh[name], dtype=torch.complex128, device=self.dev) for name in CLASS_NAMES]
             kb.kb_set_vertex(self.e.ctx, S_XP, False, 0.0)
             kb.kb_set_vertex_channels(self.e.ctx, S_XP, 1 << 1)
@@ -404,20 +421,38 @@ class ParquetSDE(ParquetPA):
     def set_sigma(self, sR, sK):
         self.e.set_self_energy(sR.detach().cpu().numpy(), sK.detach().cpu().numpy(), self.A_sig)
 
+    def _sde_terms(self):
+        """Terms of the form: (slot, bubbles (channel, output slot) that fill it, loop, weight);
+        loop "half": ½ loop (channel a alone, no partner data: the up-down loop), "ud":
+        loop_ud, "uu": loop − loop_ud."""
+        a_half = (S_X, ((0, S_X),), "half")
+        a = (S_X, ((0, S_X),), "ud")
+        p = (S_XP, ((1, S_XP),), "ud")
+        t = (S_XT, ((0, S_X), (2, S_XT)), "uu")
+        terms = {"a": (a_half,), "p": (p,), "ap": (a, p), "t": (t,), "apt": (a, p, t)}[self.form]
+        return [(slot, bub, mode, 1.0 / len(terms)) for slot, bub, mode in terms]
+
+    def _sde_bubbles(self):
+        out = []
+        for _, bub, _, _ in self._sde_terms():
+            out += [b for b in bub if b not in out]
+        return out
+
+    def _sde_loop(self, slot, mode, line=None):
+        if mode == "half":
+            return 0.5 * self.e.loop(slot, self.sig_grid, line=line)
+        ud = self.e.loop(slot, self.sig_grid, line=line, ud_only=True)
+        return ud if mode == "ud" else self.e.loop(slot, self.sig_grid, line=line) - ud
+
     def sde(self, gamma):
         """(Σ^R, Σ^K) on the Σ grid from the SDE for γ, with the context's current G."""
         self.gamma.copy_(gamma)
         s = self.e.loop(S_RHAT, self.sig_grid)
-        if self.form == "a":
-            self.e.bubble(0, S_RHAT, S_GAMMA, S_X, precision="fp64")
+        for r, slot in self._sde_bubbles():
+            self.e.bubble(r, S_RHAT, S_GAMMA, slot, precision="fp64")
             self.bubbles += 1
-            s = s + 0.5 * self.e.loop(S_X, self.sig_grid)
-        else:
-            forms = ((0, S_X), (1, S_XP)) if self.form == "ap" else ((1, S_XP),)
-            for r, slot in forms:
-                self.e.bubble(r, S_RHAT, S_GAMMA, slot, precision="fp64")
-                self.bubbles += 1
-                s = s + self.e.loop(slot, self.sig_grid, ud_only=True) / len(forms)
+        for slot, _, mode, w in self._sde_terms():
+            s = s + w * self._sde_loop(slot, mode)
         s = self.U * s
         return s[:, 1, 0], s[:, 1, 1]
 
@@ -449,16 +484,17 @@ class ParquetSDE(ParquetPA):
         dB = self.out.clone()
         # Schwinger–Dyson self-energy: the loops' G δΣ G lines and the change of X̂
         ds = self.e.loop(S_RHAT, self.sig_grid, line=2)
-        forms = ((0, S_X),) if self.form == "a" else (((0, S_X), (1, S_XP)) if self.form == "ap" else ((1, S_XP),))
-        for r, slot in forms:
-            ud = self.form != "a"
-            w = 0.5 if self.form == "a" else 1.0 / len(forms)
+        bubbles, terms = self._sde_bubbles(), self._sde_terms()
+        for r, slot in bubbles:
             self.e.bubble(r, S_RHAT, S_GAMMA, slot, precision="fp64")
-            ds = ds + w * self.e.loop(slot, self.sig_grid, line=2, ud_only=ud)
+        for slot, _, mode, w in terms:
+            ds = ds + w * self._sde_loop(slot, mode, line=2)
+        for r, slot in bubbles:
             self.e.bubble(r, S_RHAT, S_DELTA, slot, precision="fp64")
             self.e.bubble(r, S_RHAT, S_GAMMA, slot, pi_kind=kb.KB_PI_GS_SG, beta=1.0, precision="fp64")
-            ds = ds + w * self.e.loop(slot, self.sig_grid, ud_only=ud)
             self.bubbles += 3
+        for slot, _, mode, w in terms:
+            ds = ds + w * self._sde_loop(slot, mode)
         ds = self.U * ds
         self.e.set_self_energy_derivative(None)
         return v - torch.cat([dB, ds[:, 1, 0], ds[:, 1, 1]])

@@ -6,9 +6,9 @@
   t̄ and t terms iterated with the vertex step to self-consistency (Sec. III.C);
 - the up-down-only line of the self-energy loop (kb_loop with KB_LOOP_UD_ONLY) equals the
   oracle's loop(ud_only=True);
-- the Schwinger–Dyson self-energy in its p-channel form and in the mean of the a and p forms
-  (ParquetSDE form "p", "ap") equals the oracle's composition of bubbles and up-down loops
-  (Sec. III.B)."""
+- the Schwinger–Dyson self-energy in its p-channel form, its t-channel form and the means of
+  forms (ParquetSDE form "p", "ap", "t", "apt") equals the oracle's composition of bubbles and
+  up-down or up-up loops (Sec. III.B)."""
 
 import numpy as np
 import pytest
@@ -90,7 +90,7 @@ def test_loop_up_down_only_matches_oracle(dtype):
     e.close()
 
 
-@pytest.mark.parametrize("form", ["p", "ap"])
+@pytest.mark.parametrize("form", ["p", "ap", "t", "apt"])
 def test_sde_forms_match_oracle(form):
     from paper_2405_20996_gb300.parquet import ParquetSDE
     g = G_SMALL
@@ -117,13 +117,36 @@ def test_sde_forms_match_oracle(form):
         for name in CLS:
             assert _rel(got[name].cpu().numpy(), ref[name]) <= TOL, (r, name)
     Rh = O.Vertex(g, U=1.0, has_R=True)
-    s = U * O.loop(Rh, P, nq, pa.sig_grid)
-    forms = {"p": (1,), "ap": (0, 1)}[form]
-    for r in forms:
-        X = O.bubble_all(Rh, Gam, P, r, nq)
-        VX = O.Vertex(g, channels={r: tuple(X[name] for name in CLS)}, include=(r,))
-        s = s + U / len(forms) * O.loop(VX, P, nq, pa.sig_grid, ud_only=True)
+    if form in ("p", "ap"):
+        s = U * O.loop(Rh, P, nq, pa.sig_grid)
+        forms = {"p": (1,), "ap": (0, 1)}[form]
+        for r in forms:
+            X = O.bubble_all(Rh, Gam, P, r, nq)
+            VX = O.Vertex(g, channels={r: tuple(X[name] for name in CLS)}, include=(r,))
+            s = s + U / len(forms) * O.loop(VX, P, nq, pa.sig_grid, ud_only=True)
+    else:
+        s = OF.sde_map(g, nq, U, Gam, P, pa.sig_grid, form)
     scale = np.abs(s).max()
     assert np.abs(oR.cpu().numpy() - s[:, 1, 0]).max() <= TOL * scale
     assert np.abs(oK.cpu().numpy() - s[:, 1, 1]).max() <= TOL * scale
+    pa.close()
+
+
+def test_sde_t_form_fixed_point_matches_oracle():
+    """The self-consistent parquet solution with the Schwinger–Dyson self-energy in the mean
+    of its a, p and t forms: the GPU fixed point (Newton–Krylov on the joint state) equals the
+    oracle's damped iteration (oracle_flow.parquet_sde(form="apt")) on small grids."""
+    from paper_2405_20996_gb300.parquet import ParquetSDE
+    g = G_SMALL
+    nq, U, D, T, n_sig = 41, 1.0, 1.0, 0.2, 9
+    pa = ParquetSDE(g, nq, U, D, T, n_sig=n_sig, form="apt")
+    z, h, _ = pa.newton_krylov(tol=1e-12)
+    assert h[-1] <= 1e-12, h
+    gam, sR, _ = pa.split(z)
+    og, osR, _ = OF.parquet_sde(g, nq, U, D, T, pa.sig_grid, tol=1e-13, maxit=2000, form="apt")
+    assert _rel(sR.cpu().numpy(), osR) <= 1e-9
+    for c in range(3):
+        got = pa.classes(gam, c)
+        for k, name in enumerate(CLS):
+            assert _rel(got[name].cpu().numpy(), og[c][k]) <= 1e-9, (c, name)
     pa.close()

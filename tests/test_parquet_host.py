@@ -120,17 +120,20 @@ class _SDEEngine:
     def bubble(self, r, sl, sr, so, precision="fp64"):
         self.calls.append(("bubble", r, sl, sr, so))
 
-    def loop(self, slot, nus, ud_only=False):
+    def loop(self, slot, nus, ud_only=False, line=None):
         self.calls.append(("loop", slot, ud_only))
-        v = {10: 1.0, 11: 3.0, 12: 5.0}[slot] * (7.0 if ud_only else 1.0)
+        v = {10: 1.0, 11: 3.0, 12: 5.0, 13: 11.0}[slot] * (7.0 if ud_only else 1.0)
         out = torch.zeros((self.n, 2, 2), dtype=torch.complex128)
         out[:, 1, 0], out[:, 1, 1] = v, 1j * v
         return out
 
 
 def test_sde_forms_combine_the_loops():
-    from paper_2405_20996_gb300.parquet import S_GAMMA, S_RHAT, S_X, S_XP, ParquetSDE
-    for form, expect in (("a", 1.0 + 0.5 * 3.0), ("p", 1.0 + 7 * 5.0), ("ap", 1.0 + 0.5 * (7 * 3.0 + 7 * 5.0))):
+    from paper_2405_20996_gb300.parquet import S_GAMMA, S_RHAT, S_X, S_XP, S_XT, ParquetSDE
+    # the t form takes loop - loop_ud of its slot (the up-up loop)
+    tt = 11.0 - 7 * 11.0
+    for form, expect in (("a", 1.0 + 0.5 * 3.0), ("p", 1.0 + 7 * 5.0), ("ap", 1.0 + 0.5 * (7 * 3.0 + 7 * 5.0)),
+                         ("t", 1.0 + tt), ("apt", 1.0 + (7 * 3.0 + 7 * 5.0 + tt) / 3)):
         pa = ParquetSDE.__new__(ParquetSDE)
         pa.form, pa.U, pa.bubbles = form, 2.0, 0
         pa.sig_grid = np.linspace(-1.0, 1.0, 3)
@@ -140,7 +143,8 @@ def test_sde_forms_combine_the_loops():
         assert torch.allclose(sR, torch.full((3,), 2.0 * expect, dtype=torch.complex128)), (form, sR)
         assert torch.allclose(sK, torch.full((3,), 2.0j * expect, dtype=torch.complex128))
         bubbles = [c for c in pa.e.calls if c[0] == "bubble"]
-        want = {"a": [(0, S_X)], "p": [(1, S_XP)], "ap": [(0, S_X), (1, S_XP)]}[form]
+        want = {"a": [(0, S_X)], "p": [(1, S_XP)], "ap": [(0, S_X), (1, S_XP)], "t": [(0, S_X), (2, S_XT)],
+                "apt": [(0, S_X), (1, S_XP), (2, S_XT)]}[form]
         assert [(c[1], c[4]) for c in bubbles] == want
         assert all(c[2] == S_RHAT and c[3] == S_GAMMA for c in bubbles)
         assert pa.bubbles == len(want)

@@ -7,7 +7,7 @@
   at U = 0.25 and 0.5 extrapolated in U² is the second-order self-energy, whose Im Σ^R is the
   textbook double spectral integral; the solution is causal and obeys the FDR;
 - the Jacobian product of the joint map (vertex directions and the propagators' change
-  along δΣ) equals central differences of the map, for the a, p and ap forms and the
+  along δΣ) equals central differences of the map, for the a, p, ap, t and apt forms and the
   symmetrised Bethe–Salpeter form, and Newton–Krylov on the joint state reaches the
   Anderson-accelerated fixed point."""
 
@@ -103,7 +103,8 @@ def _seeded_state(pa, g, U, T, seed):
     return z
 
 
-@pytest.mark.parametrize("form,sym", [("a", False), ("p", False), ("ap", False), ("a", True)])
+@pytest.mark.parametrize("form,sym", [("a", False), ("p", False), ("ap", False), ("t", False), ("apt", False),
+                                      ("a", True)])
 def test_sde_jacobian_matches_central_differences(form, sym):
     from paper_2405_20996_gb300.parquet import ParquetSDE
     g = dict(n1=13, n2w=7, n2v=6, n3w=5, n3v=4)
