@@ -88,9 +88,11 @@ __device__ __forceinline__ void vars_of(int c, const double L[4], double& w, dou
     else { w = L[1] - L[3]; v = 0.5 * (L[0] + L[2]); vp = 0.5 * (L[1] + L[3]); }
 }
 
+// tanh(v / 2T); the argument as v times 1/(2T), a loop invariant of the callers (GB300's
+// FP64 divide costs several FMA issue slots)
 __device__ __forceinline__ double tanh_T(double v, double T) {
     if (T <= 0.0) return v > 0.0 ? 1.0 : (v < 0.0 ? -1.0 : 0.0);
-    return tanh(v / (2.0 * T));
+    return tanh(v * (0.5 / T));
 }
 
 // 2x2 Keldysh matrix of G (which = 0) or of the single-scale propagator S = dG/dΛ at fixed
@@ -109,11 +111,12 @@ __device__ inline void prop2x2(const Model& m, int which, double v, double2 P[2]
         }
     }
     const double lam = (m.reg == KB_REG_U) ? m.lam : 1.0;
+    const double ilam = (m.reg == KB_REG_U) ? 1.0 / m.lam : 1.0;
     const double2 g0 = make_double2(v - m.eps, m.Delta);          // v - eps + i Delta
-    double2 GR = cinv(make_double2(g0.x / lam - sR.x, g0.y / lam - sR.y));
+    double2 GR = cinv(make_double2(g0.x * ilam - sR.x, g0.y * ilam - sR.y));
     double2 GA = cconj(GR);
     double th = tanh_T(v, m.T);
-    double2 mid = make_double2(sK.x, sK.y - 2.0 * m.Delta * th / lam);
+    double2 mid = make_double2(sK.x, sK.y - 2.0 * m.Delta * th * ilam);
     if (which == 0) {
         P[0][0] = cmul(cmul(GR, mid), GA);
         P[0][1] = GR;
@@ -211,7 +214,7 @@ __device__ __forceinline__ void pi_entry_t(const Model& m, int pi_kind, double A
         scale = 0.5 * A * KB_PI * (1.0 + tn * tn);
     }
     // c_r * w_j * scale / (2 pi i) = -i * (c_r w_j scale / 2 pi)
-    const double f = cr * wj * scale / (2.0 * KB_PI);
+    const double f = cr * wj * scale * (0.5 / KB_PI);
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
         const int b3 = q >> 3, b3p = (q >> 2) & 1, b4 = (q >> 1) & 1, b4p = q & 1;
