@@ -629,10 +629,29 @@ __global__ void __launch_bounds__(K2_THREADS, 3) k_mx_k2(VertexF V, DfGrids G, M
             for (int n = wp * 4 + gi; n < CH; n += 16) {
                 float2 d0 = make_float2(0.f, 0.f), d1 = d0, x0 = d0, x1 = d0;
                 gather_list<group_channel<R, 0>()>(V, G, cb + n, cw + n, CH, l, d0, d1);
-                gather_list<group_channel<R, 1>()>(V, G, cb + CH + n, cw + 9 * CH + n, CH, l, d0, d1);
                 if (NS == 2) {
+                    // t: group 3, the exchanged partner of group 1 (p at the legs with 1 and 2
+                    // exchanged: the same w_p and v_p, v'_p negated), has group 1's K1 and K2
+                    // corners with weights of opposite sign, so they are read once: group 1's
+                    // K1 + K2 sum s enters the exchanged term as -s[kswap12(c)]; kswap12
+                    // exchanges components 4m + 1 and 4m + 2, held by lanes l and l ^ 1
+                    float2 s0 = make_float2(0.f, 0.f), s1 = s0;
+                    gather_list<group_channel<R, 1>(), true>(V, G, cb + CH + n, cw + 9 * CH + n, CH, l, d0, d1,
+                                                             &s0, &s1);
+                    d0 = make_float2(d0.x + s0.x, d0.y + s0.y);
+                    d1 = make_float2(d1.x + s1.x, d1.y + s1.y);
                     gather_list_x<group_channel<R, 2>()>(V, G, cb + 2 * CH + n, cw + 2 * 9 * CH + n, CH, l, x0, x1);
-                    gather_list_x<group_channel<R, 3>()>(V, G, cb + 3 * CH + n, cw + 3 * 9 * CH + n, CH, l, x0, x1);
+                    gather_list_x<group_channel<R, 3>(), true>(V, G, cb + 3 * CH + n, cw + 3 * 9 * CH + n, CH, l,
+                                                               x0, x1);
+                    const bool odd = l & 1;
+                    const float2 send = odd ? s0 : s1;
+                    const float2 recv = make_float2(__shfl_xor_sync(0xffffffffu, send.x, 1),
+                                                    __shfl_xor_sync(0xffffffffu, send.y, 1));
+                    const float2 e0 = odd ? recv : s0, e1 = odd ? s1 : recv;
+                    x0 = make_float2(x0.x - e0.x, x0.y - e0.y);
+                    x1 = make_float2(x1.x - e1.x, x1.y - e1.y);
+                } else {
+                    gather_list<group_channel<R, 1>()>(V, G, cb + CH + n, cw + 9 * CH + n, CH, l, d0, d1);
                 }
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {

@@ -521,10 +521,12 @@ __device__ __forceinline__ void corner_pair_x(const float2* p, int s0, int s1, f
 // Gather of one compact corner list by a group of 8 lanes: lane l accumulates components
 // 2l, 2l+1 (one 16-byte piece of every corner record), acc += sum_k w_k rec_k[2l .. 2l+1],
 // so that one warp-wide load delivers the full records of the 4 nodes its lane groups hold.
-template <int ch>
+// With SPLIT the K1 and K2 corners accumulate into s0, s1 instead (the t channel reuses
+// them for the exchanged p group, which has the same K1 and K2 corners).
+template <int ch, bool SPLIT = false>
 __device__ __forceinline__ void gather_list(const VertexF& V, const DfGrids& G, const int4* __restrict__ base,
                                             const float2* __restrict__ wt, int stride, int l, float2& a0,
-                                            float2& a1) {
+                                            float2& a1, float2* s0 = nullptr, float2* s1 = nullptr) {
     const int4 b = *base;
     float2 w[9];
 #pragma unroll
@@ -536,9 +538,15 @@ __device__ __forceinline__ void gather_list(const VertexF& V, const DfGrids& G, 
     const size_t s2 = (size_t)G.N2v * 8, s3 = (size_t)G.N3v * 8, s33 = (size_t)G.N3v * G.N3v * 8;
     const long long n1 = G.N1, n2 = (long long)G.N2w * G.N2v, n3 = (long long)G.N3w * G.N3v * G.N3v;
     const long long v2 = G.N2v, v3 = G.N3v, v33 = (long long)G.N3v * G.N3v;
-    corner_pair(c1 + (size_t)b.x * 8, w[0], a0, a1, b.x, n1);
-    corner_pair(c2 + (size_t)b.y * 8, w[1], a0, a1, b.y, n2);
-    corner_pair(c2 + (size_t)b.y * 8 + s2, w[2], a0, a1, b.y + v2, n2);
+    if (SPLIT) {
+        corner_pair(c1 + (size_t)b.x * 8, w[0], *s0, *s1, b.x, n1);
+        corner_pair(c2 + (size_t)b.y * 8, w[1], *s0, *s1, b.y, n2);
+        corner_pair(c2 + (size_t)b.y * 8 + s2, w[2], *s0, *s1, b.y + v2, n2);
+    } else {
+        corner_pair(c1 + (size_t)b.x * 8, w[0], a0, a1, b.x, n1);
+        corner_pair(c2 + (size_t)b.y * 8, w[1], a0, a1, b.y, n2);
+        corner_pair(c2 + (size_t)b.y * 8 + s2, w[2], a0, a1, b.y + v2, n2);
+    }
     corner_pair(c2p + (size_t)b.z * 8, w[3], a0, a1, b.z, n2);
     corner_pair(c2p + (size_t)b.z * 8 + s2, w[4], a0, a1, b.z + v2, n2);
     const float4* p3 = c3 + (size_t)b.w * 8;
@@ -549,7 +557,8 @@ __device__ __forceinline__ void gather_list(const VertexF& V, const DfGrids& G, 
 }
 
 // The same for an exchanged group: lane l takes components kswap12(2l), kswap12(2l+1).
-template <int ch>
+// With SKIP12 the K1 and K2 corners are left out (the caller adds them from the direct group).
+template <int ch, bool SKIP12 = false>
 __device__ __forceinline__ void gather_list_x(const VertexF& V, const DfGrids& G, const int4* __restrict__ base,
                                               const float2* __restrict__ wt, int stride, int l, float2& a0,
                                               float2& a1) {
@@ -561,9 +570,11 @@ __device__ __forceinline__ void gather_list_x(const VertexF& V, const DfGrids& G
     const size_t s2 = (size_t)G.N2v * 16, s3 = (size_t)G.N3v * 16, s33 = (size_t)G.N3v * G.N3v * 16;
     const long long n1 = G.N1, n2 = (long long)G.N2w * G.N2v, n3 = (long long)G.N3w * G.N3v * G.N3v;
     const long long v2 = G.N2v, v3 = G.N3v, v33 = (long long)G.N3v * G.N3v;
-    corner_pair_x(V.cls[ch][0] + (size_t)b.x * 16, s0, s1, w[0], a0, a1, b.x, n1);
-    corner_pair_x(V.cls[ch][1] + (size_t)b.y * 16, s0, s1, w[1], a0, a1, b.y, n2);
-    corner_pair_x(V.cls[ch][1] + (size_t)b.y * 16 + s2, s0, s1, w[2], a0, a1, b.y + v2, n2);
+    if (!SKIP12) {
+        corner_pair_x(V.cls[ch][0] + (size_t)b.x * 16, s0, s1, w[0], a0, a1, b.x, n1);
+        corner_pair_x(V.cls[ch][1] + (size_t)b.y * 16, s0, s1, w[1], a0, a1, b.y, n2);
+        corner_pair_x(V.cls[ch][1] + (size_t)b.y * 16 + s2, s0, s1, w[2], a0, a1, b.y + v2, n2);
+    }
     corner_pair_x(V.cls[ch][2] + (size_t)b.z * 16, s0, s1, w[3], a0, a1, b.z, n2);
     corner_pair_x(V.cls[ch][2] + (size_t)b.z * 16 + s2, s0, s1, w[4], a0, a1, b.z + v2, n2);
     const float2* p3 = V.cls[ch][3] + (size_t)b.w * 16;
