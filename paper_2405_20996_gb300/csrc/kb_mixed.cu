@@ -862,7 +862,7 @@ __device__ __forceinline__ void write_planes(float* base, size_t plane, size_t r
 // records through crossing, Gamma2(w, -v'', -v) = X[Gamma2(w, v'', v)], written at the
 // mirrored node nq-1-j (the node set is symmetric under v'' -> -v'').
 template <int MODE, int R>
-__global__ void __launch_bounds__(128, 4) k_mx_tile3(VertexF V, DfGrids G, MixedJob J, int w0, int wt0, int vh,
+__global__ void __launch_bounds__(128, 6) k_mx_tile3(VertexF V, DfGrids G, MixedJob J, int w0, int wt0, int vh,
                                                   int rowsL, int rowsR, const float2* __restrict__ Pt,
                                                   float* __restrict__ tile, float* __restrict__ tileR) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -886,8 +886,8 @@ __global__ void __launch_bounds__(128, 4) k_mx_tile3(VertexF V, DfGrids G, Mixed
 #pragma unroll 1
     for (int pass = 0; pass < NS; ++pass) {
         const int parts = pass == 0 ? PARTS_UD : PARTS_X;
-        if (RIGHT) vertex_part_f32<R>(V, G, parts, true, 8 | 16 | 32, w, qn[j], ve, g, pass > 0);
-        else vertex_part_f32<R>(V, G, parts, false, 8 | 16 | 32, w, ve, qn[j], g, pass > 0);
+        if (RIGHT) vertex_part_f32<R, true>(V, G, parts, true, 8 | 16 | 32, w, qn[j], ve, g, pass > 0);
+        else vertex_part_f32<R, true>(V, G, parts, false, 8 | 16 | 32, w, ve, qn[j], g, pass > 0);
         const bool uu = pass > 0;
         const int s = (NS == 1) ? 0 : (RIGHT ? (uu ? 1 : 0) : (uu ? 0 : 1));
         if (MODE != 1) {

@@ -151,7 +151,10 @@ __device__ __forceinline__ const float2* vcls(const VertexF& V, int ch, int k) {
 }
 
 // Corners of one class: nd dimensions with lower nodes kk[d], fractions tt[d] and sizes N[d]
-// (row-major data, 16 complex components per record); the corner code exists once.
+// (row-major data, 16 complex components per record); the corner code exists once.  Two
+// records are loaded before either is applied; ONE: one record at a time (fewer registers,
+// for the K3 tile kernel, which runs more CTAs per SM instead).
+template <bool ONE = false>
 __device__ __forceinline__ void corners(const float2* __restrict__ D, int nd, int k0, int k1, int k2, float t0,
                                         float t1, float t2, int N0, int N1, int N2, float f, bool swap12,
                                         float2 acc[16]) {
@@ -162,6 +165,43 @@ __device__ __forceinline__ void corners(const float2* __restrict__ D, int nd, in
     if (nd == 3) { st[1] = N[2]; st[0] = N[1] * N[2]; }
     int base = kk[0] * st[0] + (nd >= 2 ? kk[1] * st[1] : 0) + (nd == 3 ? kk[2] * st[2] : 0);
     int ncorner = 1 << nd;   // even
+    if (ONE) {
+#pragma unroll 1
+        for (int c = 0; c < ncorner; ++c) {
+            float wgt = f;
+            int of = base;
+            bool ok = true;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (d < nd) {
+                    bool bt = (c >> d) & 1;
+                    ok = ok && (bt ? (kk[d] + 1 < N[d]) : (kk[d] >= 0));
+                    wgt *= bt ? tt[d] : 1.f - tt[d];
+                    of += bt ? st[d] : 0;
+                }
+            }
+            if (!(ok && wgt != 0.f && kb_rec_ok(of, (long long)N[0] * N[1] * N[2], KB_SITE_MIXED_REC))) continue;
+            float4 u[8];
+            const float4* q = reinterpret_cast<const float4*>(D + (size_t)of * 16);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) u[i] = __ldg(q + i);
+            const float2 g = make_float2(wgt, wgt);
+#pragma unroll
+            for (int grp = 0; grp < 4; ++grp) {
+                float2 a0 = make_float2(u[2 * grp].x, u[2 * grp].y), a1 = make_float2(u[2 * grp].z, u[2 * grp].w);
+                float2 a2 = make_float2(u[2 * grp + 1].x, u[2 * grp + 1].y);
+                float2 a3 = make_float2(u[2 * grp + 1].z, u[2 * grp + 1].w);
+                if (swap12) {
+                    float2 t0 = a1; a1 = a2; a2 = t0;
+                }
+                acc[4 * grp + 0] = __ffma2_rn(g, a0, acc[4 * grp + 0]);
+                acc[4 * grp + 1] = __ffma2_rn(g, a1, acc[4 * grp + 1]);
+                acc[4 * grp + 2] = __ffma2_rn(g, a2, acc[4 * grp + 2]);
+                acc[4 * grp + 3] = __ffma2_rn(g, a3, acc[4 * grp + 3]);
+            }
+        }
+        return;
+    }
     // two corners per iteration: both records are loaded before either is applied
 #pragma unroll 1
     for (int c = 0; c < ncorner; c += 2) {
@@ -246,12 +286,13 @@ __device__ __forceinline__ Sten7 stencils7(const VertexF& V, int ch, unsigned cl
     return S;
 }
 
+template <bool ONE = false>
 __device__ __forceinline__ void apply7(const VertexF& V, int ch, const Sten7& S, const DfGrids& G, float f, bool sw,
                                        float2 out[16]) {
-    if (S.u0) corners(vcls(V, ch, 0), 1, S.kw1, 0, 0, S.tw1, 0.f, 0.f, G.N1, 1, 1, f, sw, out);
-    if (S.u1) corners(vcls(V, ch, 1), 2, S.kw2, S.kv2, 0, S.tw2, S.tv2, 0.f, G.N2w, G.N2v, 1, f, sw, out);
-    if (S.u2) corners(vcls(V, ch, 2), 2, S.kw2, S.kp2, 0, S.tw2, S.tp2, 0.f, G.N2w, G.N2v, 1, f, sw, out);
-    if (S.u3) corners(vcls(V, ch, 3), 3, S.kw3, S.kv3, S.kp3, S.tw3, S.tv3, S.tp3, G.N3w, G.N3v, G.N3v, f, sw, out);
+    if (S.u0) corners<ONE>(vcls(V, ch, 0), 1, S.kw1, 0, 0, S.tw1, 0.f, 0.f, G.N1, 1, 1, f, sw, out);
+    if (S.u1) corners<ONE>(vcls(V, ch, 1), 2, S.kw2, S.kv2, 0, S.tw2, S.tv2, 0.f, G.N2w, G.N2v, 1, f, sw, out);
+    if (S.u2) corners<ONE>(vcls(V, ch, 2), 2, S.kw2, S.kp2, 0, S.tw2, S.tp2, 0.f, G.N2w, G.N2v, 1, f, sw, out);
+    if (S.u3) corners<ONE>(vcls(V, ch, 3), 3, S.kw3, S.kv3, S.kp3, S.tw3, S.tv3, S.tp3, G.N3w, G.N3v, G.N3v, f, sw, out);
 }
 
 // Parts of the vertex relative to channel r at r-variables (w, v, vp), FP32 accumulation.
@@ -268,7 +309,7 @@ __device__ __forceinline__ void apply7(const VertexF& V, int ch, const Sten7& S,
 // independent stencil computations overlap.
 constexpr int PARTS_UD = 1, PARTS_X = 2, PARTS_UU = 3;
 
-template <int r>
+template <int r, bool ONE = false>
 __device__ __forceinline__ void vertex_part_f32(const VertexF& V, const DfGrids& G, int parts, bool right, int what,
                                                 df w, df v, df vp, float2 out[16], bool accumulate = false) {
     const bool dir = parts & PARTS_UD, exch = parts & PARTS_X;
@@ -326,7 +367,7 @@ __device__ __forceinline__ void vertex_part_f32(const VertexF& V, const DfGrids&
             }
         }
         Sten7 S = stencils7(V, ch, classes, G, gw, gv, gp);
-        apply7(V, ch, S, G, f, sw, out);
+        apply7<ONE>(V, ch, S, G, f, sw, out);
     }
 }
 
