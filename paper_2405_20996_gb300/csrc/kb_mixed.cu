@@ -256,8 +256,20 @@ __device__ __forceinline__ int first_not_below(const df* __restrict__ qn, int lo
     return lo;
 }
 
+// Stencil of every quadrature node on the K3 fermionic grid (lower node, fraction), the same
+// for every w, spin and component of k_mx_ntilde.
+__global__ void k_mx_nstencil(DfGrids G, int nq, int2* __restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nq) return;
+    const df* qn = G.n3v + G.N3v;
+    float tt = 0.f;
+    int k = -2;
+    if (j > 0 && j < nq - 1) k = stencil_x(qn[j], x_est(qn[j].h, 1.f / G.A), G.n3v, G.N3v, G.A, tt);
+    out[j] = make_int2(k, __float_as_int(tt));
+}
+
 __global__ void k_mx_ntilde(const float2* __restrict__ Nt, const float2* __restrict__ Mt, DfGrids G, int nq, int ns,
-                            int t0, double2* __restrict__ out) {
+                            int t0, const int2* __restrict__ nst, double2* __restrict__ out) {
     // one thread per (grid node m, Keldysh component o) of one (w, s, table)
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     const int wi = blockIdx.y, s = blockIdx.z % ns, t = t0 + blockIdx.z / ns;
@@ -265,7 +277,6 @@ __global__ void k_mx_ntilde(const float2* __restrict__ Nt, const float2* __restr
     if (m >= G.N3v) return;
     const float2* T = (t == 0 ? Nt : Mt) + ((size_t)wi * ns + s) * nq * 16 + o;
     const df* qn = G.n3v + G.N3v;
-    const float ia = 1.f / G.A;
     // nodes whose stencil can touch grid node m lie between X_{m-1} and X_{m+1}
     int jl = (m == 0) ? 1 : first_not_below(qn, 1, nq - 2, G.n3v[m - 1]) - 1;
     int jh = (m == G.N3v - 1) ? nq - 2 : first_not_below(qn, 1, nq - 2, G.n3v[m + 1]);
@@ -273,8 +284,9 @@ __global__ void k_mx_ntilde(const float2* __restrict__ Nt, const float2* __restr
     jh = min(jh, nq - 2);
     double ax = 0.0, ay = 0.0;
     for (int j = jl; j <= jh; ++j) {
-        float tt;
-        const int k = stencil_x(qn[j], x_est(qn[j].h, ia), G.n3v, G.N3v, G.A, tt);
+        const int2 st = __ldg(nst + j);
+        const int k = st.x;
+        const float tt = __int_as_float(st.y);
         const float ph = (k == m) ? 1.f - tt : ((k + 1 == m) ? tt : 0.f);
         if (ph == 0.f) continue;
         const float2 x = __ldg(T + (size_t)j * 16);
@@ -1153,7 +1165,8 @@ static size_t cache_side_bytes(const Grids& g, int r, int side) {
 // Workspace layout of one mixed-precision bubble of channel r (byte offsets into the
 // context's workspace) and the bytes it needs.
 struct MixedLayout {
-    size_t off_tab, off_N, off_M, off_S, off_P3, off_K1, off_NT, off_BS, off_T, rows, K, per_w, tc_scratch, need;
+    size_t off_tab, off_N, off_M, off_S, off_P3, off_K1, off_NT, off_BS, off_NS, off_T, rows, K, per_w, tc_scratch,
+        need;
     int chunk;
 };
 
@@ -1177,7 +1190,10 @@ static MixedLayout mixed_layout(const kb_ctx* ctx, int r, unsigned mask) {
     // bosonic stencils of the K2 gather's lookup groups (one side at a time)
     L.off_BS = (L.off_NT + szNT + 255) / 256 * 256;
     size_t szBS = (size_t)2 * ns * g.n2v * g.nq * sizeof(float4);
-    L.off_T = (L.off_BS + szBS + 1023) / 1024 * 1024;
+    // the nodes' stencils on the K3 fermionic grid (k_mx_nstencil)
+    L.off_NS = (L.off_BS + szBS + 255) / 256 * 256;
+    size_t szNS = (size_t)g.nq * sizeof(int2);
+    L.off_T = (L.off_NS + szNS + 1023) / 1024 * 1024;
     L.rows = (size_t)4 * g.n3v;
     L.K = (size_t)4 * ns * g.nq;
     L.per_w = 2 * 4 * L.rows * L.K * sizeof(float) + L.rows * L.rows * sizeof(double2) + 1024;
@@ -1298,11 +1314,16 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
         }
         {
             // left (N) table for K2; the right (M) table only when K2' is gathered
+            int2* nst = reinterpret_cast<int2*>(ws + Lo.off_NS);
+            {
+                KB_LAUNCH(ctx, st, "k_mx_nstencil");
+                k_mx_nstencil<<<(g.nq + 127) / 128, 128, 0, st>>>(G, g.nq, nst);
+            }
             KB_LAUNCH(ctx, st, "k_mx_ntilde");
             const int nt = (!sym && ((mask >> KB_K2P) & 1)) ? 2 : 1;
             const int t0 = ((mask >> KB_K2) & 1) ? 0 : 1;
             k_mx_ntilde<<<dim3((g.n3v * 16 + 127) / 128, g.n2w, ns * (t0 == 1 ? 1 : nt)), 128, 0, st>>>(
-                Nt, Mt, G, g.nq, ns, t0, Ntl);
+                Nt, Mt, G, g.nq, ns, t0, nst, Ntl);
         }
         const float2* cacheL = valid_cache(ctx, sl, r, 0);
         const float2* cacheR = valid_cache(ctx, sr, r, 1);
