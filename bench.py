@@ -65,7 +65,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 TF32_OVER_BF16 = 1.1 / 2.25
 
 
-def mixed_kernel_work(channels=(0, 1, 2)):
+def mixed_kernel_work(channels=(0, 1, 2), t_su2=False):
     """Algorithmic work per step of the symmetric mixed path, by kernel (flops).
     Gather kernels: every interpolation corner adds 16 complex values times a real weight
     (64 flops); a record (one (w, v, node) of one spin term) has nominally 44 corners in
@@ -93,8 +93,9 @@ def mixed_kernel_work(channels=(0, 1, 2)):
     r3a = half(g["n3w"]) * g["n3v"] * nq
     r3p = g["n3w"] * half(g["n3v"]) * nq
     r3t = half(g["n3w"]) * g["n3v"] * nq
+    # t in its SU(2) form: one density record per side (both lookups, one Pi fold)
     w["k_mx_tile3_both"] = (0 in channels) * r3a * (48 * 64 + 512) + (1 in channels) * r3p * (48 * 64 + 2 * 512) + \
-        (2 in channels) * r3t * ((48 + 48) * 64 + 2 * 512)
+        (2 in channels) * r3t * ((48 + 48) * 64 + (1 if t_su2 else 2) * 512)
     # k_tc_k3 (useful): 8 flops per complex multiply-add of the points the method needs, i.e.
     # a, t: the pairs v <= v' (the others are conjugation images, and the contraction skips
     # the output blocks that hold only v > v'; the diagonal blocks it computes in full are
@@ -105,7 +106,7 @@ def mixed_kernel_work(channels=(0, 1, 2)):
     for r, nw in ((0, half(g["n3w"])), (1, g["n3w"]), (2, half(g["n3w"]))):
         if r not in channels:
             continue
-        ns = 2 if r == 2 else 1
+        ns = 2 if (r == 2 and not t_su2) else 1      # the SU(2) form contracts one density record
         MN = 4 * half(n3) * N if r == 1 else 16 * n3 * (n3 + 1) // 2
         tc += 8.0 * MN * (4 * ns * nq) * nw
     w["k_tc_k3"] = tc
@@ -655,6 +656,8 @@ def main():
     ap.add_argument("--no-fp64-check", action="store_true",
                     help="skip the plain-FP64 step behind per_class_err and fp64_gpu (profiling captures)")
     ap.add_argument("--no-graph", action="store_true", help="eager launches instead of one step graph")
+    ap.add_argument("--no-t-su2", action="store_true",
+                    help="the t bubble's two spin terms contracted directly instead of its SU(2) form")
     ap.add_argument("--ws-gb", type=int, default=8, help="device workspace limit per context (GiB)")
     ap.add_argument("--ml-cache", default="auto", choices=["off", "auto", "all"],
                     help="multiloop workloads: record cache of the full vertex (off, the useful sides, all sides)")
@@ -719,13 +722,26 @@ def main():
 
     points = POINTS_PER_STEP * len(chans) // 3
 
+    # the t bubble in its SU(2) form (mixed precision, with the a bubble in the same step):
+    # its K3 from the density contraction (half the quadrature length) and the a bubble's K3
+    su2 = prec == "mixed" and 0 in chans and 2 in chans and not args.no_t_su2
+
     def step_eager():
         for r in chans:
-            engs[r].bubble(r, 0, 0, 1, precision=prec, stream=stream)
+            if r == 2 and su2:
+                engs[2].bubble_t_su2(0, 1, stream=stream)
+            else:
+                engs[r].bubble(r, 0, 0, 1, precision=prec, stream=stream)
+        if su2:
+            engs[2].t_su2_finish(1, engs[0].out(1, 0)["K3"], stream=stream)
 
     graph = None
     if not args.no_graph:
-        graph = StepGraph([engs[r].desc(r, 0, 0, 1, precision=prec) for r in chans], device=dev)
+        descs = [engs[r].desc_t_su2(0, 1) if (r == 2 and su2) else engs[r].desc(r, 0, 0, 1, precision=prec)
+                 for r in chans]
+        if su2:
+            descs.append(engs[2].desc_t_su2_finish(1, engs[0], 1))
+        graph = StepGraph(descs, device=dev)
 
     def step():
         if graph is not None:
@@ -817,7 +833,7 @@ def main():
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "share": share,
                 "note": "FP64 FMA pipe peak derived from 152 SMs x 2 DFMA/clk x 2.07 GHz"}
     else:
-        work = mixed_kernel_work(chans) if prec == "mixed" else {}
+        work = mixed_kernel_work(chans, t_su2=su2) if prec == "mixed" else {}
         roof = roofline_entry(name, dms, args.steps, work, bf16) or {
             "kernel": name, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
             "traffic": None}
@@ -894,7 +910,9 @@ def main():
                            "l2": "flushed (256 MB write) before every timed step", "parallelism": "weak: one "
                            "independent parameter point per GPU",
                            "launch": "one CUDA graph per step (channels as parallel branches)" if graph is not None
-                           else "eager, one stream"},
+                           else "eager, one stream",
+                           "t_channel": "SU(2) form: K3 from the density contraction and the a bubble" if su2
+                           else "both spin terms contracted"},
                 "e2e": e2e,
                 "gpu_launches": int(launches_timed), "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
                 "per_class_err": per_class_err, "fp64_gpu": fp64_gpu,

@@ -155,6 +155,29 @@ kb_status kb_set_vertex_class(kb_ctx *ctx, int slot, int channel, int cls, void 
 kb_status kb_bubble(kb_ctx *ctx, int channel, int slot_left, int slot_right, int out_slot, int pi_kind,
                     unsigned class_mask, double alpha, double beta, int precision, void *stream);
 
+/* The t-channel bubble of a vertex with itself in its SU(2) form (the symmetry reduction of
+ * the spin sums, Sec. II.G.3, of the t bubble drawn in Sec. III.B): with Γ^d = Γ_uu + Γ_ud the
+ * density combination and X the exchange of legs 1 and 2, the magnetic combination is
+ * Γ_uu − Γ_ud = −X[Γ_ud], and exchanging legs 1 and 2 turns the t bubble into the a bubble,
+ * so   B_t(Γ, Γ) = ½ (−Γ^d Π_t Γ^d) + ½ X[B_a(Γ, Γ)],
+ * where X[B_a](w, v, v') = B_a(−w, v, v') with the Keldysh indices a1, a2 exchanged.  The
+ * density contraction has one spin record per side, half the quadrature length of the two
+ * spin terms kb_bubble contracts.  Two calls:
+ *   kb_bubble_t_su2: out ← α B_t for K1, K2, K2' (as kb_bubble with β = 0, mixed precision)
+ *     and, for K3, α/2 times the density contraction at the independent points (w ≥ 0,
+ *     v ≤ v'); slot: a slot declared symmetric (kb_set_vertex_symmetric) with its bare part
+ *     or channel t; out_slot: channel t classes attached (KB_ERR_STATE otherwise);
+ *   kb_t_su2_finish: K3 of channel t of out_slot += α/2 X[a_k3] at those points, then its
+ *     other points as the t channel's symmetry images; a_k3: DEVICE array, the K3 class
+ *     [n3w][n3v][n3v][16] (c64 or c128, a_dtype) of B_a(Γ, Γ) with α = 1, β = 0, the same
+ *     vertex, propagator pair, grids and model — e.g. another context's output, which the
+ *     caller orders before this call (same stream, an event, or a step graph's
+ *     KB_OP_T_SU2_FINISH entry).
+ * Precision: mixed only (the K3 density contraction on tcgen05); asynchronous on `stream`. */
+kb_status kb_bubble_t_su2(kb_ctx *ctx, int slot, int out_slot, int pi_kind, unsigned class_mask, double alpha,
+                          void *stream);
+kb_status kb_t_su2_finish(kb_ctx *ctx, int out_slot, const void *a_k3, int a_dtype, double alpha, void *stream);
+
 /* Vector-jacobian product (adjoint) of kb_bubble (the differentiation pattern of the
  * method: gradients of a scalar loss through B_r, e.g. for Newton-Krylov solves of the
  * parquet equations, Sec. III.B).
@@ -222,8 +245,13 @@ typedef struct kb_graph kb_graph;
  *                 derivatives of all channels of the previous one;
  *   KB_OP_CACHE   kb_vertex_cache(ctx, slot_left, channel, class_mask = sides): the record
  *                 cache is allocated at graph creation and rebuilt at every replay;
- *   KB_OP_IMAGE   kb_vertex_image(ctx, channel, slot_left, out_slot, class_mask). */
-enum { KB_OP_BUBBLE = 0, KB_OP_ADD = 1, KB_OP_JOIN = 2, KB_OP_CACHE = 3, KB_OP_IMAGE = 4 };
+ *   KB_OP_IMAGE   kb_vertex_image(ctx, channel, slot_left, out_slot, class_mask);
+ *   KB_OP_T_SU2   kb_bubble_t_su2(ctx, slot_left, out_slot, pi_kind, class_mask, alpha);
+ *   KB_OP_T_SU2_FINISH  kb_t_su2_finish(ctx, out_slot, K3 of channel a of slot slot2 of
+ *                 context ctx2, alpha), after every earlier entry of ctx2's branch (ctx2
+ *                 must have entries in the graph; ctx's branch waits for them there). */
+enum { KB_OP_BUBBLE = 0, KB_OP_ADD = 1, KB_OP_JOIN = 2, KB_OP_CACHE = 3, KB_OP_IMAGE = 4, KB_OP_T_SU2 = 5,
+       KB_OP_T_SU2_FINISH = 6 };
 
 typedef struct {
     kb_ctx *ctx;
@@ -232,6 +260,8 @@ typedef struct {
     double alpha, beta;
     int precision;
     int op;
+    kb_ctx *ctx2;                   /* KB_OP_T_SU2_FINISH: the context and slot of B_a */
+    int slot2;
 } kb_bubble_desc;
 
 kb_status kb_graph_create(kb_graph **graph, const kb_bubble_desc *bubbles, int n);

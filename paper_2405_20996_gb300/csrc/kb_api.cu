@@ -327,6 +327,54 @@ kb_status kb_set_vertex_class(kb_ctx* ctx, int slot, int channel, int cls, void*
     return KB_OK;
 }
 
+kb_status kb_bubble_t_su2(kb_ctx* ctx, int slot, int so, int pi_kind, unsigned mask, double alpha, void* stream) {
+    if (!ctx) return KB_ERR_ARG;
+    if (!ctx->grids_set || !ctx->model_set) {
+        ctx->err = "kb_bubble_t_su2: set grids and model first";
+        return KB_ERR_STATE;
+    }
+    if (slot < 0 || slot >= KB_MAX_SLOTS || so < 0 || so >= KB_MAX_SLOTS ||
+        (pi_kind != KB_PI_GG && pi_kind != KB_PI_GS_SG) || (mask & ~KB_MASK_ALL) || !std::isfinite(alpha)) {
+        ctx->err = "kb_bubble_t_su2: argument out of range";
+        return KB_ERR_ARG;
+    }
+    if (!ctx->slot_set[slot] || !ctx->slot_set[so]) { ctx->err = "kb_bubble_t_su2: slot not set"; return KB_ERR_STATE; }
+    for (int k = 0; k < 4; ++k)
+        if ((mask >> k) & 1) {
+            const void* o = ctx->slots[so].cls[KB_CH_T][k];
+            if (!o) { ctx->err = "kb_bubble_t_su2: output class not attached"; return KB_ERR_STATE; }
+            for (int c = 0; c < 3; ++c)
+                for (int q = 0; q < 4; ++q)
+                    if (o == ctx->slots[slot].cls[c][q]) {
+                        ctx->err = "kb_bubble_t_su2: output aliases an input class";
+                        return KB_ERR_ARG;
+                    }
+        }
+    if (mask == 0) return KB_OK;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) { ctx->err = "cudaSetDevice failed"; return KB_ERR_CUDA; }
+    return kb_bubble_mixed_t_su2(ctx, slot, so, pi_kind, mask, alpha, reinterpret_cast<cudaStream_t>(stream));
+}
+
+kb_status kb_t_su2_finish(kb_ctx* ctx, int so, const void* a_k3, int a_dtype, double alpha, void* stream) {
+    if (!ctx) return KB_ERR_ARG;
+    if (!ctx->grids_set) { ctx->err = "kb_t_su2_finish: set grids first"; return KB_ERR_STATE; }
+    if (so < 0 || so >= KB_MAX_SLOTS || !a_k3 || (a_dtype != KB_DT_C64 && a_dtype != KB_DT_C128) ||
+        !std::isfinite(alpha)) {
+        ctx->err = "kb_t_su2_finish: argument out of range";
+        return KB_ERR_ARG;
+    }
+    if (!ctx->slot_set[so] || !ctx->slots[so].cls[KB_CH_T][KB_K3]) {
+        ctx->err = "kb_t_su2_finish: the output slot's t-channel K3 class is not attached";
+        return KB_ERR_STATE;
+    }
+    if (ctx->slots[so].cls[KB_CH_T][KB_K3] == a_k3) {
+        ctx->err = "kb_t_su2_finish: the a-channel K3 array aliases the output";
+        return KB_ERR_ARG;
+    }
+    if (cudaSetDevice(ctx->device) != cudaSuccess) { ctx->err = "cudaSetDevice failed"; return KB_ERR_CUDA; }
+    return kb_t_su2_finish_impl(ctx, so, a_k3, a_dtype, alpha, reinterpret_cast<cudaStream_t>(stream));
+}
+
 kb_status kb_bubble(kb_ctx* ctx, int channel, int sl, int sr, int so, int pi_kind, unsigned mask, double alpha,
                     double beta, int precision, void* stream) {
     if (!ctx) return KB_ERR_ARG;

@@ -59,17 +59,31 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
         if (!c) return fail(c0, "kb_graph_create: null context in descriptor", KB_ERR_ARG);
         if (c->device != c0->device) return fail(c0, "kb_graph_create: contexts on different devices", KB_ERR_ARG);
         if (!c->grids_set || !c->model_set) return fail(c, "kb_graph_create: set grids and model first", KB_ERR_STATE);
-        if (d[i].op != KB_OP_BUBBLE && d[i].op != KB_OP_ADD && d[i].op != KB_OP_CACHE && d[i].op != KB_OP_IMAGE)
+        if (d[i].op != KB_OP_BUBBLE && d[i].op != KB_OP_ADD && d[i].op != KB_OP_CACHE && d[i].op != KB_OP_IMAGE &&
+            d[i].op != KB_OP_T_SU2 && d[i].op != KB_OP_T_SU2_FINISH)
             return fail(c, "kb_graph_create: unknown entry kind", KB_ERR_ARG);
+        if (d[i].op == KB_OP_T_SU2_FINISH) {
+            kb_ctx* c2 = d[i].ctx2;
+            if (!c2 || d[i].slot2 < 0 || d[i].slot2 >= KB_MAX_SLOTS || !c2->slot_set[d[i].slot2] ||
+                !c2->slots[d[i].slot2].cls[KB_CH_A][KB_K3])
+                return fail(c, "kb_graph_create: the a-channel K3 source of a T_SU2_FINISH entry is not set",
+                            KB_ERR_ARG);
+            bool seen = false;
+            for (int q = 0; q < i; ++q) seen |= d[q].op != KB_OP_JOIN && d[q].ctx == c2;
+            if (!seen)
+                return fail(c, "kb_graph_create: the source context of a T_SU2_FINISH entry has no earlier entries",
+                            KB_ERR_ARG);
+        }
         if (d[i].channel < 0 || d[i].channel > 2 || (d[i].class_mask & ~KB_MASK_ALL) ||
             (d[i].op == KB_OP_CACHE && (d[i].class_mask < 1 || d[i].class_mask > 15)) ||
             (d[i].op == KB_OP_BUBBLE && d[i].precision != KB_PREC_FP64 && d[i].precision != KB_PREC_MIXED))
             return fail(c, "kb_graph_create: descriptor out of range", KB_ERR_ARG);
         if (!index.count(c)) { index[c] = br.size(); br.push_back(Branch{c}); }
-        if (d[i].op != KB_OP_BUBBLE) continue;
+        if (d[i].op != KB_OP_BUBBLE && d[i].op != KB_OP_T_SU2) continue;
         Branch& b = br[index[c]];
-        size_t need = d[i].precision == KB_PREC_FP64 ? kb_fp64_workspace_need(c, d[i].channel, d[i].class_mask)
-                                                     : kb_mixed_workspace_need(c, d[i].channel, d[i].class_mask);
+        size_t need = d[i].op == KB_OP_T_SU2 ? kb_mixed_workspace_need(c, KB_CH_T, d[i].class_mask)
+                      : d[i].precision == KB_PREC_FP64 ? kb_fp64_workspace_need(c, d[i].channel, d[i].class_mask)
+                                                       : kb_mixed_workspace_need(c, d[i].channel, d[i].class_mask);
         b.need = std::max(b.need, need);
     }
     if (cudaSetDevice(c0->device) != cudaSuccess) return fail(c0, "cudaSetDevice failed", KB_ERR_CUDA);
@@ -86,7 +100,8 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
         if (s != KB_OK) return s;
     }
     bool any_mixed = false;
-    for (int i = 0; i < n; ++i) any_mixed |= d[i].op == KB_OP_BUBBLE && d[i].precision == KB_PREC_MIXED;
+    for (int i = 0; i < n; ++i)
+        any_mixed |= (d[i].op == KB_OP_BUBBLE && d[i].precision == KB_PREC_MIXED) || d[i].op == KB_OP_T_SU2;
     if (any_mixed && !kb_tc_prepare(c0->device))
         return fail(c0, "kb_graph_create: tensor-core kernel setup failed", KB_ERR_CUDA);
     if (any_mixed && !kb_mixed_prepare(c0->device))
@@ -95,6 +110,11 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
     // inside a capture); the replays use the tuned split-K factors
     for (int i = 0; i < n; ++i) {
         const kb_bubble_desc& x = d[i];
+        if (x.op == KB_OP_T_SU2 && x.ctx->autotune) {
+            kb_status s = kb_mixed_tune(x.ctx, KB_CH_T, x.slot_left, x.slot_left, x.class_mask, 0.0, nullptr, true);
+            if (s != KB_OK) return s;
+            continue;
+        }
         if (x.op != KB_OP_BUBBLE || x.precision != KB_PREC_MIXED || !x.ctx->autotune) continue;
         kb_status s = kb_mixed_tune(x.ctx, x.channel, x.slot_left, x.slot_right, x.class_mask, x.beta, nullptr);
         if (s != KB_OK) return s;
@@ -104,6 +124,9 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
     cudaStream_t s0 = nullptr;
     cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> join_ev((size_t)joins * br.size(), nullptr);
+    int finishes = 0;
+    for (int i = 0; i < n; ++i) finishes += d[i].op == KB_OP_T_SU2_FINISH;
+    join_ev.resize(join_ev.size() + (size_t)finishes, nullptr);      // one event per finish entry at the end
     kb_status st = KB_OK;
     auto cleanup = [&]() {
         for (auto& b : br) {
@@ -143,10 +166,21 @@ kb_status kb_graph_create(kb_graph** out, const kb_bubble_desc* d, int n) {
     } else {
         cudaEventRecord(fork, s0);
         for (auto& b : br) cudaStreamWaitEvent(b.st, fork, 0);
-        int jn = 0;
+        int jn = 0, fn = 0;
         for (int i = 0; i < n && st == KB_OK; ++i) {
             const kb_bubble_desc& x = d[i];
-            if (x.op == KB_OP_JOIN) {
+            if (x.op == KB_OP_T_SU2_FINISH) {
+                // ctx's branch waits for everything ctx2's branch has so far, then finishes K3
+                cudaEvent_t ev = join_ev[(size_t)joins * br.size() + fn++];
+                cudaEventRecord(ev, br[index[x.ctx2]].st);
+                cudaStreamWaitEvent(br[index[x.ctx]].st, ev, 0);
+                const kb::VertexDev& src = x.ctx2->slots[x.slot2];
+                st = kb_t_su2_finish(x.ctx, x.out_slot, src.cls[KB_CH_A][KB_K3], src.dt[KB_CH_A][KB_K3], x.alpha,
+                                     br[index[x.ctx]].st);
+            } else if (x.op == KB_OP_T_SU2) {
+                st = kb_bubble_t_su2(x.ctx, x.slot_left, x.out_slot, x.pi_kind, x.class_mask, x.alpha,
+                                     br[index[x.ctx]].st);
+            } else if (x.op == KB_OP_JOIN) {
                 cudaEvent_t* ev = &join_ev[(size_t)jn++ * br.size()];
                 for (size_t b = 0; b < br.size(); ++b) cudaEventRecord(ev[b], br[b].st);
                 for (size_t b = 0; b < br.size(); ++b)

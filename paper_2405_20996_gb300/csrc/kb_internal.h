@@ -160,7 +160,12 @@ kb_status kb_scale_classes(kb_ctx* ctx, int r, int so, unsigned classes, double 
 // bubble's K3 contraction tuned ahead of a graph capture (kb_mixed.cu)
 bool kb_tc_tune(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
                 void* scratch, size_t scratch_bytes, bool tri, cudaStream_t st);
-kb_status kb_mixed_tune(kb_ctx* ctx, int r, int sl, int sr, unsigned mask, double beta, cudaStream_t st);
+kb_status kb_mixed_tune(kb_ctx* ctx, int r, int sl, int sr, unsigned mask, double beta, cudaStream_t st,
+                        bool tsu2 = false);
+// the t bubble in its SU(2) form and its completion (kb_mixed.cu)
+kb_status kb_bubble_mixed_t_su2(kb_ctx* ctx, int sl, int so, int pi_kind, unsigned mask, double alpha,
+                                cudaStream_t st);
+kb_status kb_t_su2_finish_impl(kb_ctx* ctx, int so, const void* a_k3, int a_dt, double alpha, cudaStream_t st);
 // symmetry image of a channel's classes into another slot (kb_ops.cu)
 kb_status kb_vertex_image_impl(kb_ctx* ctx, int channel, int src, int dst, unsigned mask, cudaStream_t st);
 // slot arithmetic (kb_ops.cu)

@@ -876,7 +876,7 @@ __device__ __forceinline__ void write_planes(float* base, size_t plane, size_t r
 template <int MODE, int R>
 __global__ void __launch_bounds__(128, 6) k_mx_tile3(VertexF V, DfGrids G, MixedJob J, int w0, int wt0, int vh,
                                                   int rowsL, int rowsR, const float2* __restrict__ Pt,
-                                                  float* __restrict__ tile, float* __restrict__ tileR) {
+                                                  float* __restrict__ tile, float* __restrict__ tileR, int dform = 0) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     constexpr int NS = (R == KB_CH_T) ? 2 : 1;
     constexpr bool RIGHT = (MODE == 1);
@@ -884,7 +884,8 @@ __global__ void __launch_bounds__(128, 6) k_mx_tile3(VertexF V, DfGrids G, Mixed
     if (j >= J.nq) return;
     const df* qn = G.n3v + G.N3v;
     df w = G.n3w[w0 + wl], ve = G.n3v[vi];
-    const size_t K = (size_t)4 * NS * J.nq;
+    // dform (t): one record per side, the density combination up-up + up-down
+    const size_t K = (size_t)4 * (dform ? 1 : NS) * J.nq;
     const size_t planeL = (size_t)rowsL * K, planeR = (size_t)rowsR * K;
     const float2* P = Pt + ((size_t)(w0 + wl) * J.nq + j) * 16;
     const int vm = G.N3v - 1 - vi;                 // mirrored row of the crossing image
@@ -900,8 +901,14 @@ __global__ void __launch_bounds__(128, 6) k_mx_tile3(VertexF V, DfGrids G, Mixed
         const int parts = pass == 0 ? PARTS_UD : PARTS_X;
         if (RIGHT) vertex_part_f32<R, true>(V, G, parts, true, 8 | 16 | 32, w, qn[j], ve, g, pass > 0);
         else vertex_part_f32<R, true>(V, G, parts, false, 8 | 16 | 32, w, ve, qn[j], g, pass > 0);
+        if (dform && pass == 0) {
+            // density record up-up + up-down = 2 up-down + exchanged term
+#pragma unroll
+            for (int c = 0; c < 16; ++c) g[c] = make_float2(2.f * g[c].x, 2.f * g[c].y);
+            continue;
+        }
         const bool uu = pass > 0;
-        const int s = (NS == 1) ? 0 : (RIGHT ? (uu ? 1 : 0) : (uu ? 0 : 1));
+        const int s = (NS == 1 || dform) ? 0 : (RIGHT ? (uu ? 1 : 0) : (uu ? 0 : 1));
         if (MODE != 1) {
             float* base = tile + (size_t)(wt0 + wl) * 4 * planeL;
             size_t col = ((size_t)s * J.nq + j) * 4;
@@ -922,7 +929,7 @@ __global__ void __launch_bounds__(128, 6) k_mx_tile3(VertexF V, DfGrids G, Mixed
                     float sg = sign_c(c);
                     h[c] = make_float2(sg * g[pc].x, -sg * g[pc].y);
                 }
-                if (R == KB_CH_T) sr = 1 - s;      // left up-up (0) <-> right up-up (1)
+                if (R == KB_CH_T && !dform) sr = 1 - s;      // left up-up (0) <-> right up-up (1)
             } else {
 #pragma unroll
                 for (int c = 0; c < 16; ++c) h[c] = g[c];
@@ -1241,7 +1248,7 @@ void kb::kb_mixed_tables(kb_ctx* ctx, df* tab, DfGrids& G, cudaStream_t st) {
 
 template <int r>
 static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, unsigned mask, double alpha, double beta,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool tsu2 = false) {
     const Grids& g = ctx->g;
     bool ok1, ok2;
     VertexF VL = to_vf(ctx->slots[sl], ctx, ok1), VR = to_vf(ctx->slots[sr], ctx, ok2);
@@ -1388,6 +1395,12 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
         // a, t (symmetric): the points v > v' of each w are the images of (w, v', v) at the
         // same w, so the contraction skips the blocks that hold only such points
         const bool tri3 = sym && r != KB_CH_P;
+        // t in its SU(2) form (tsu2, symmetric only): the density contraction with K = 4 Nq,
+        // scattered with alpha / 2; kb_t_su2_finish adds the crossed a bubble and the images
+        const bool td = tsu2 && r == KB_CH_T && sym;
+        const size_t K3K = td ? (size_t)4 * g.nq : K;
+        MixedJob J3 = J;
+        if (td) J3.alpha = 0.5 * J.alpha;
         for (int w0 = w3_lo; w0 < g.n3w; w0 += chunk) {
             int nwc = std::min(chunk, g.n3w - w0);
             float* TAc = TA;
@@ -1395,7 +1408,7 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
             if (sym) {
                 KB_LAUNCH(ctx, st, "k_mx_tile3_both");
                 k_mx_tile3<2, r><<<dim3((g.nq + 127) / 128, g.n3v - vh3, nwc), 128, 0, st>>>(VL, G, J, w0, 0, vh3, rowsL,
-                                                                                           rowsR, P3, TA, TB);
+                                                                                           rowsR, P3, TA, TB, td ? 1 : 0);
             } else {
                 if (cacheL3) {
                     TAc = const_cast<float*>(cacheL3) + (size_t)w0 * 4 * rowsL * K;      // cached left tile
@@ -1413,21 +1426,21 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
                 }
             }
             bool done = false;
-            if (use_tc) done = kb_tc_k3(ctx, TAc, TBc, Cm, rowsL, rowsR, (int)K, nwc, scratch, tc_scratch, tri3, st);
+            if (use_tc) done = kb_tc_k3(ctx, TAc, TBc, Cm, rowsL, rowsR, (int)K3K, nwc, scratch, tc_scratch, tri3, st);
             if (!done) {
                 KB_LAUNCH(ctx, st, "k_mx_cgemm");
                 k_mx_cgemm<<<dim3((unsigned)((rowsR + 63) / 64), (unsigned)((rowsL + 63) / 64), nwc), 256, 0, st>>>(
-                    TAc, TBc, Cm, rowsL, rowsR, (int)K);
+                    TAc, TBc, Cm, rowsL, rowsR, (int)K3K);
             }
             {
                 KB_LAUNCH(ctx, st, "k_mx_scatter3");
                 size_t tot = (size_t)nwc * (g.n3v - vh3) * g.n3v * 16;
-                k_mx_scatter3<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(J, w0, nwc, g.n3v, vh3, Cm,
+                k_mx_scatter3<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(J3, w0, nwc, g.n3v, vh3, Cm,
                                                                             const_cast<void*>(VO.cls[r][KB_K3]),
                                                                             VO.dt[r][KB_K3], tri3 ? 1 : 0);
             }
         }
-        if (tri3 && g.n3v > 1) {
+        if (tri3 && g.n3v > 1 && !td) {
             KB_LAUNCH(ctx, st, "k_mx_trifill");
             const size_t tot = (size_t)(g.n3w - w3_lo) * g.n3v * (g.n3v - 1) / 2 * 16;
             k_mx_trifill<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(const_cast<void*>(VO.cls[r][KB_K3]),
@@ -1447,7 +1460,7 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
         int kw = (r == KB_CH_A) ? 0 : 1;                 // w -> -w image: a conj-after-crossing, t conj
         if (r != KB_CH_P) {
             if ((mask >> KB_K1) & 1) fill(KB_K1, KB_K1, kw, g.n1, 1, 1, g.n1 / 2, 1);
-            if ((mask >> KB_K3) & 1) fill(KB_K3, KB_K3, kw, g.n3w, g.n3v, g.n3v, g.n3w / 2, g.n3v);
+            if (((mask >> KB_K3) & 1) && !(tsu2 && r == KB_CH_T)) fill(KB_K3, KB_K3, kw, g.n3w, g.n3v, g.n3v, g.n3w / 2, g.n3v);
         }
         if (r == KB_CH_P && ((mask >> KB_K3) & 1)) fill(KB_K3, KB_K3, 2, g.n3w, g.n3v, g.n3v, g.n3w, g.n3v / 2);
         if ((mask >> KB_K2) & 1) {
@@ -1458,6 +1471,83 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) { ctx->err = std::string("mixed launch: ") + cudaGetErrorString(e); return KB_ERR_CUDA; }
+    return KB_OK;
+}
+
+// The t bubble of a symmetric slot with itself in its SU(2) form (kb_bubble_t_su2): K1, K2
+// and K2' as kb_bubble computes them, K3 = alpha/2 times the density contraction for the
+// independent points (w >= 0, v <= v'), completed by kb_t_su2_finish_impl.
+kb_status kb_bubble_mixed_t_su2(kb_ctx* ctx, int sl, int so, int pi_kind, unsigned mask, double alpha,
+                                cudaStream_t st) {
+    if (!ctx->slots[sl].symmetric) {
+        ctx->err = "kb_bubble_t_su2: the slot must be declared symmetric";
+        return KB_ERR_ARG;
+    }
+    // the identity needs the density contraction itself: K3 must not be one of the classes
+    // the ordinary bubble skips as identically zero
+    if ((mask >> KB_K3) & 1 & (kb_zero_classes(ctx, KB_CH_T, sl, sl, mask) >> KB_K3)) {
+        ctx->err = "kb_bubble_t_su2: the slot needs its bare part or channel t";
+        return KB_ERR_ARG;
+    }
+    return mixed_impl<KB_CH_T>(ctx, sl, sl, so, pi_kind, mask, alpha, 0.0, st, true);
+}
+
+// K3 of the t output += alpha/2 X[B_a]: the crossed a bubble at t-variables (w, v, v') is
+// B_a(-w, v, v') with the Keldysh indices a1, a2 exchanged (component kswap12(c)); for the
+// independent points w >= 0 (index >= n3w / 2), v <= v'.
+__global__ void k_mx_t_su2_add(void* outp, int odt, const void* ap, int adt, double half_alpha, int nw, int nv) {
+    const int w0 = nw / 2;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t total = (size_t)(nw - w0) * nv * nv * 16;
+    if (idx >= total) return;
+    const int c = idx % 16;
+    size_t rest = idx / 16;
+    const int vp = rest % nv;
+    rest /= nv;
+    const int v = rest % nv;
+    const int w = w0 + (int)(rest / nv);
+    if (v > vp) return;
+    const size_t de = (((size_t)w * nv + v) * nv + vp) * 16 + c;
+    const size_t se = (((size_t)(nw - 1 - w) * nv + v) * nv + vp) * 16 + kswap12(c);
+    double2 x;
+    if (adt == KB_DT_C128) x = reinterpret_cast<const double2*>(ap)[se];
+    else {
+        const float2 y = reinterpret_cast<const float2*>(ap)[se];
+        x = make_double2(y.x, y.y);
+    }
+    if (odt == KB_DT_C128) {
+        double2* o = reinterpret_cast<double2*>(outp) + de;
+        *o = make_double2(o->x + half_alpha * x.x, o->y + half_alpha * x.y);
+    } else {
+        float2* o = reinterpret_cast<float2*>(outp) + de;
+        *o = make_float2((float)(o->x + half_alpha * x.x), (float)(o->y + half_alpha * x.y));
+    }
+}
+
+kb_status kb_t_su2_finish_impl(kb_ctx* ctx, int so, const void* a_k3, int a_dt, double alpha, cudaStream_t st) {
+    const Grids& g = ctx->g;
+    void* out = const_cast<void*>(ctx->slots[so].cls[KB_CH_T][KB_K3]);
+    const int odt = ctx->slots[so].dt[KB_CH_T][KB_K3];
+    {
+        KB_LAUNCH(ctx, st, "k_mx_t_su2_add");
+        const size_t tot = (size_t)(g.n3w - g.n3w / 2) * g.n3v * g.n3v * 16;
+        k_mx_t_su2_add<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(out, odt, a_k3, a_dt, 0.5 * alpha, g.n3w, g.n3v);
+    }
+    if (g.n3v > 1) {
+        KB_LAUNCH(ctx, st, "k_mx_trifill");
+        const size_t tot = (size_t)(g.n3w - g.n3w / 2) * g.n3v * (g.n3v - 1) / 2 * 16;
+        k_mx_trifill<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(out, odt, 1, g.n3w / 2, g.n3w, g.n3v);
+    }
+    {
+        // w < 0 through conjugation (the t channel's image)
+        KB_LAUNCH(ctx, st, "k_mx_symfill");
+        const size_t tot = (size_t)(g.n3w / 2) * g.n3v * g.n3v * 16;
+        if (tot)
+            k_mx_symfill<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(out, out, odt, 1, g.n3w, g.n3v, g.n3v,
+                                                                        g.n3w / 2, g.n3v);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { ctx->err = std::string("kb_t_su2_finish launch: ") + cudaGetErrorString(e); return KB_ERR_CUDA; }
     return KB_OK;
 }
 
@@ -1605,7 +1695,7 @@ extern "C" kb_status kb_vertex_uncache(kb_ctx* ctx, int slot) {
 // Tune the split-K factor of the tensor-core contraction for the K3 shapes this bubble will
 // use (the full chunks of bosonic frequencies and the last partial one), on the context's
 // workspace as operands (any values do for timing); for step graphs, before the capture.
-kb_status kb_mixed_tune(kb_ctx* ctx, int r, int sl, int sr, unsigned mask, double beta, cudaStream_t st) {
+kb_status kb_mixed_tune(kb_ctx* ctx, int r, int sl, int sr, unsigned mask, double beta, cudaStream_t st, bool tsu2) {
     mask &= ~kb_zero_classes(ctx, r, sl, sr, mask);
     if (!((mask >> KB_K3) & 1) || std::getenv("KB_K3_SIMT")) return KB_OK;
     const Grids& g = ctx->g;
@@ -1623,9 +1713,9 @@ kb_status kb_mixed_tune(kb_ctx* ctx, int r, int sl, int sr, unsigned mask, doubl
     const int vh3 = (sym && r == KB_CH_P) ? g.n3v / 2 : 0;
     const int rowsL = 4 * (g.n3v - vh3), rowsR = (int)Lo.rows, nw = g.n3w - w3_lo;
     const bool tri3 = sym && r != KB_CH_P;
+    const int K3K = (tsu2 && sym && r == KB_CH_T) ? 4 * g.nq : (int)Lo.K;
     const int full = std::min(Lo.chunk, nw), last = nw % Lo.chunk;
-    kb_tc_tune(ctx, TA, TB, Cm, rowsL, rowsR, (int)Lo.K, full, scratch, Lo.tc_scratch, tri3, st);
-    if (last && last != full)
-        kb_tc_tune(ctx, TA, TB, Cm, rowsL, rowsR, (int)Lo.K, last, scratch, Lo.tc_scratch, tri3, st);
+    kb_tc_tune(ctx, TA, TB, Cm, rowsL, rowsR, K3K, full, scratch, Lo.tc_scratch, tri3, st);
+    if (last && last != full) kb_tc_tune(ctx, TA, TB, Cm, rowsL, rowsR, K3K, last, scratch, Lo.tc_scratch, tri3, st);
     return cudaGetLastError() == cudaSuccess ? KB_OK : KB_ERR_CUDA;
 }

@@ -114,6 +114,27 @@ class Engine:
         return kb.kb_bubble_desc(self.ctx, channel, left, right, out, pi_kind, class_mask, alpha, beta,
                                  PREC[precision])
 
+    def bubble_t_su2(self, slot, out, pi_kind=kb.KB_PI_GG, class_mask=kb.KB_MASK_ALL, alpha=1.0, stream=None):
+        """The t bubble of a symmetric slot with itself in its SU(2) form (kb_bubble_t_su2);
+        its K3 class is complete after t_su2_finish with the a bubble's K3."""
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        kb.kb_bubble_t_su2(self.ctx, slot, out, pi_kind, class_mask, alpha, st)
+
+    def t_su2_finish(self, out, a_k3, alpha=1.0, stream=None):
+        """kb_t_su2_finish: a_k3 the K3 class (device tensor) of B_a of the same vertex."""
+        assert a_k3.is_cuda and a_k3.is_contiguous() and a_k3.dtype in DT
+        st = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        kb.kb_t_su2_finish(self.ctx, out, a_k3.data_ptr(), DT[a_k3.dtype], alpha, st)
+
+    def desc_t_su2(self, slot, out, pi_kind=kb.KB_PI_GG, class_mask=kb.KB_MASK_ALL, alpha=1.0):
+        """Step-graph entry of bubble_t_su2."""
+        return kb.kb_t_su2_desc(self.ctx, slot, out, pi_kind, class_mask, alpha)
+
+    def desc_t_su2_finish(self, out, a_engine, a_slot, alpha=1.0):
+        """Step-graph entry of t_su2_finish with the K3 class of channel a of slot a_slot of
+        the engine a_engine (which has earlier entries in the same graph)."""
+        return kb.kb_t_su2_finish_desc(self.ctx, out, a_engine.ctx, a_slot, alpha)
+
     def share_slot(self, slot, other, other_slot, U=0.0, has_R=False, include=(0, 1, 2), symmetric=False):
         """Attach the device tensors of another engine's slot to a slot of this engine
         (no copy), e.g. one vertex read by several contexts."""

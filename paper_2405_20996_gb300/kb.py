@@ -40,10 +40,11 @@ class kb_vertex_desc(C.Structure):
 class kb_bubble_desc(C.Structure):
     _fields_ = [("ctx", C.c_void_p), ("channel", C.c_int), ("slot_left", C.c_int), ("slot_right", C.c_int),
                 ("out_slot", C.c_int), ("pi_kind", C.c_int), ("class_mask", C.c_uint), ("alpha", C.c_double),
-                ("beta", C.c_double), ("precision", C.c_int), ("op", C.c_int)]
+                ("beta", C.c_double), ("precision", C.c_int), ("op", C.c_int), ("ctx2", C.c_void_p),
+                ("slot2", C.c_int)]
 
 
-KB_OP_BUBBLE, KB_OP_ADD, KB_OP_JOIN, KB_OP_CACHE, KB_OP_IMAGE = 0, 1, 2, 3, 4
+KB_OP_BUBBLE, KB_OP_ADD, KB_OP_JOIN, KB_OP_CACHE, KB_OP_IMAGE, KB_OP_T_SU2, KB_OP_T_SU2_FINISH = 0, 1, 2, 3, 4, 5, 6
 KB_ERR_TOO_LARGE = 7
 KB_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -62,6 +63,8 @@ _SIGS = {
     "kb_set_vertex_class": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int],
     "kb_bubble": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_double, C.c_double,
                   C.c_int, C.c_void_p],
+    "kb_bubble_t_su2": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_double, C.c_void_p],
+    "kb_t_su2_finish": [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_void_p],
     "kb_bubble_vjp": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_double, C.c_int,
                       C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
     "kb_vertex_add": [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_uint, C.c_double, C.c_void_p],
@@ -197,6 +200,27 @@ def kb_bubble(ctx, channel, slot_left, slot_right, out_slot, pi_kind=KB_PI_GG, c
               alpha=1.0, beta=0.0, precision=KB_PREC_FP64, stream=0):
     _check(ctx, lib().kb_bubble(ctx, channel, slot_left, slot_right, out_slot, pi_kind, class_mask, alpha, beta,
                                 precision, stream))
+
+
+def kb_bubble_t_su2(ctx, slot, out_slot, pi_kind=KB_PI_GG, class_mask=KB_MASK_ALL, alpha=1.0, stream=0):
+    _check(ctx, lib().kb_bubble_t_su2(ctx, slot, out_slot, pi_kind, class_mask, alpha, stream))
+
+
+def kb_t_su2_finish(ctx, out_slot, a_k3_ptr, a_dtype, alpha=1.0, stream=0):
+    _check(ctx, lib().kb_t_su2_finish(ctx, out_slot, a_k3_ptr, a_dtype, alpha, stream))
+
+
+def kb_t_su2_desc(ctx, slot, out_slot, pi_kind=KB_PI_GG, class_mask=KB_MASK_ALL, alpha=1.0):
+    """Step-graph entry: kb_bubble_t_su2."""
+    return kb_bubble_desc(ctx, KB_CH_T, slot, slot, out_slot, pi_kind, class_mask, alpha, 0.0, KB_PREC_MIXED,
+                          KB_OP_T_SU2)
+
+
+def kb_t_su2_finish_desc(ctx, out_slot, ctx_a, slot_a, alpha=1.0):
+    """Step-graph entry: kb_t_su2_finish with the K3 class of channel a of slot slot_a of
+    context ctx_a, after ctx_a's earlier entries."""
+    return kb_bubble_desc(ctx, KB_CH_T, -1, -1, out_slot, 0, KB_MASK_ALL, alpha, 0.0, 0, KB_OP_T_SU2_FINISH, ctx_a,
+                          slot_a)
 
 
 def kb_bubble_vjp(ctx, channel, slot_left, slot_right, gout_slot, pi_kind=KB_PI_GG, class_mask=KB_MASK_ALL,
