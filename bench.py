@@ -350,22 +350,33 @@ def run_points32(args):
         sizes.append(n)
         points += 3 * sum(class_points(g).values())
     stream = torch.cuda.current_stream(dev)
-    graph = StepGraph([e.desc(r, 0, 0, 1, precision="mixed") for e in pts for r in range(3)], device=dev)
+    su2 = not args.no_t_su2          # each point's t bubble in its SU(2) form (its own a bubble's K3)
+    descs = []
+    for e in pts:
+        descs += [e.desc(0, 0, 0, 1, precision="mixed"), e.desc(1, 0, 0, 1, precision="mixed")]
+        descs += [e.desc_t_su2(0, 1), e.desc_t_su2_finish(1, e, 1)] if su2 else [e.desc(2, 0, 0, 1, precision="mixed")]
+    graph = StepGraph(descs, device=dev)
     n0 = sum(e.launches() for e in pts)
     ms_graph = _timed(lambda: graph.launch(stream), args.steps, args.warmup, stream)
     launches = (sum(e.launches() for e in pts) - n0) // (args.steps + args.warmup)
 
     def eager():
         for e in pts:
-            for r in range(3):
-                e.bubble(r, 0, 0, 1, precision="mixed", stream=stream)
+            e.bubble(0, 0, 0, 1, precision="mixed", stream=stream)
+            e.bubble(1, 0, 0, 1, precision="mixed", stream=stream)
+            if su2:
+                e.bubble_t_su2(0, 1, stream=stream)
+                e.t_su2_finish(1, e.out(1, 0)["K3"], stream=stream)
+            else:
+                e.bubble(2, 0, 0, 1, precision="mixed", stream=stream)
 
     ms_eager = _timed(eager, args.steps, args.warmup, stream)
     line = {"metric": METRIC, "value": points / (ms_graph / 1e3), "unit": "points/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "32 parameter points, K3 n^3 n in {21..61}, K2 (2n-1)^2, K1 5n-4, Nq 4001, a,p,t",
-                       "n3": sizes, "points_per_step": points, "launch": "one CUDA graph, one branch per point"},
+                       "n3": sizes, "points_per_step": points, "launch": "one CUDA graph, one branch per point",
+                       "t_channel": "SU(2) form" if su2 else "both spin terms contracted"},
             "eager": {"value": points / (ms_eager / 1e3), "ms_per_step": ms_eager}, "gpu_launches": launches}
     print(json.dumps(line))
     return 0
