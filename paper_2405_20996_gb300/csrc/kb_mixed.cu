@@ -223,6 +223,7 @@ __global__ void k_mx_k1_fin(MixedJob J, const double2* __restrict__ part, void* 
 }
 
 // Column sums over j of the K2-grid tables: S[t][w][s][16], t = 0 (N) or 1 (M).
+// Column sums over j of the K2-grid tables: S[t][w][s][16], t = 0 (N) or 1 (M).
 __global__ void k_mx_sumj(const float2* __restrict__ Nt, const float2* __restrict__ Mt, int nq, int ns,
                           double2* __restrict__ S) {
     __shared__ double sh[4 * 32];
@@ -270,10 +271,11 @@ __global__ void k_mx_nstencil(DfGrids G, int nq, int2* __restrict__ out) {
 
 __global__ void k_mx_ntilde(const float2* __restrict__ Nt, const float2* __restrict__ Mt, DfGrids G, int nq, int ns,
                             int t0, const int2* __restrict__ nst, double2* __restrict__ out) {
-    // one thread per (grid node m, Keldysh component o) of one (w, s, table)
+    // four threads per (grid node m, Keldysh component o) of one (w, s, table), each taking
+    // every fourth node of m's range; their sums are added by shuffles (a warp holds one m)
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     const int wi = blockIdx.y, s = blockIdx.z % ns, t = t0 + blockIdx.z / ns;
-    const int m = idx >> 4, o = idx & 15;
+    const int m = idx >> 6, o = (idx >> 2) & 15, q = idx & 3;
     if (m >= G.N3v) return;
     const float2* T = (t == 0 ? Nt : Mt) + ((size_t)wi * ns + s) * nq * 16 + o;
     const df* qn = G.n3v + G.N3v;
@@ -283,17 +285,20 @@ __global__ void k_mx_ntilde(const float2* __restrict__ Nt, const float2* __restr
     jl = max(jl, 1);
     jh = min(jh, nq - 2);
     double ax = 0.0, ay = 0.0;
-    for (int j = jl; j <= jh; ++j) {
+    for (int j = jl + q; j <= jh; j += 4) {
         const int2 st = __ldg(nst + j);
         const int k = st.x;
         const float tt = __int_as_float(st.y);
         const float ph = (k == m) ? 1.f - tt : ((k + 1 == m) ? tt : 0.f);
-        if (ph == 0.f) continue;
         const float2 x = __ldg(T + (size_t)j * 16);
         ax = fma((double)ph, (double)x.x, ax);
         ay = fma((double)ph, (double)x.y, ay);
     }
-    out[((((size_t)t * G.N2w + wi) * ns + s) * G.N3v + m) * 16 + o] = make_double2(ax, ay);
+    ax += __shfl_xor_sync(0xffffffffu, ax, 1);
+    ay += __shfl_xor_sync(0xffffffffu, ay, 1);
+    ax += __shfl_xor_sync(0xffffffffu, ax, 2);
+    ay += __shfl_xor_sync(0xffffffffu, ay, 2);
+    if (q == 0) out[((((size_t)t * G.N2w + wi) * ns + s) * G.N3v + m) * 16 + o] = make_double2(ax, ay);
 }
 
 // Loads of the propagator-vertex tables in the contraction: each element is used by one
@@ -1329,7 +1334,7 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
             KB_LAUNCH(ctx, st, "k_mx_ntilde");
             const int nt = (!sym && ((mask >> KB_K2P) & 1)) ? 2 : 1;
             const int t0 = ((mask >> KB_K2) & 1) ? 0 : 1;
-            k_mx_ntilde<<<dim3((g.n3v * 16 + 127) / 128, g.n2w, ns * (t0 == 1 ? 1 : nt)), 128, 0, st>>>(
+            k_mx_ntilde<<<dim3((g.n3v * 64 + 127) / 128, g.n2w, ns * (t0 == 1 ? 1 : nt)), 128, 0, st>>>(
                 Nt, Mt, G, g.nq, ns, t0, nst, Ntl);
         }
         const float2* cacheL = valid_cache(ctx, sl, r, 0);
