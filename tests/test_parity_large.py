@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 CFG4 = dict(grids=dict(n1=801, n2w=201, n2v=201, n3w=101, n3v=101), nq=8001, U=3.0, Delta=1.0, T=0.01)
 TOL = 1e-6
-NSAMPLE = {"K1": 24, "K2": 24, "K2p": 24, "K3": 48}
+NSAMPLE = {"K1": 64, "K2": 48, "K2p": 48, "K3": 96}
 
 
 @pytest.fixture(scope="module")

@@ -80,8 +80,9 @@ def test_mixed_pi_dot_sigma_loop_part(r):
 
 def test_mixed_full_size_vs_fp64_gpu_and_oracle_samples():
     """The mixed-precision workload (K1 401, K2 101^2, K3 51^3, 4001 nodes, complex64
-    vertex): every class of every channel within 1e-6 of the plain FP64 GPU path, and
-    sampled points within 1e-6 of the oracle."""
+    vertex): every class of every channel within 1e-6 of the plain FP64 GPU path, and per
+    class 64 random points plus the grid's corner points (first and last index on every
+    axis) within 1e-6 (mixed) and 1e-10 (FP64) of the oracle."""
     cfg = CFG1
     ch = seeded_inputs(cfg, seed=1)
     rng = np.random.default_rng(0)
@@ -93,7 +94,9 @@ def test_mixed_full_size_vs_fp64_gpu_and_oracle_samples():
         fp = gpu_bubble(cfg, ch, r, "fp64")
         for k in CLS:
             assert rel_err(mx[k], fp[k]) <= TOL, (r, k, rel_err(mx[k], fp[k]))
-            idx = [tuple(int(rng.integers(0, n)) for n in shapes[k]) for _ in range(6)]
+            corners = [tuple((n - 1) * ((c >> d) & 1) for d, n in enumerate(shapes[k]))
+                       for c in range(1 << len(shapes[k]))]
+            idx = corners + [tuple(int(rng.integers(0, n)) for n in shapes[k]) for _ in range(64)]
             ref = O.bubble_class(V, V, P, r, k, cfg["nq"], idx=idx)
             got = np.array([mx[k][i] for i in idx])
             scale = np.abs(fp[k]).max()
