@@ -650,23 +650,27 @@ __global__ void __launch_bounds__(K2_THREADS, 3) k_mx_k2(VertexF V, DfGrids G, M
                     // t: group 3, the exchanged partner of group 1 (p at the legs with 1 and 2
                     // exchanged: the same w_p and v_p, v'_p negated), has group 1's K1 and K2
                     // corners with weights of opposite sign, so they are read once: group 1's
-                    // K1 + K2 sum s enters the exchanged term as -s[kswap12(c)]; kswap12
-                    // exchanges components 4m + 1 and 4m + 2, held by lanes l and l ^ 1
-                    float2 s0 = make_float2(0.f, 0.f), s1 = s0;
+                    // K1 + K2 sum s is added to d and subtracted from the exchanged groups'
+                    // sum y.  The exchanged groups are read like the direct ones (lane l holds
+                    // components 2l, 2l+1 of the sum), and the exchanged term x = kswap12(y - s)
+                    // (components 4m + 1 and 4m + 2 exchanged) is formed by one lane-pair
+                    // shuffle: lanes l and l ^ 1 hold 4m, 4m+1 and 4m+2, 4m+3
+                    float2 s0 = make_float2(0.f, 0.f), s1 = s0, y0 = s0, y1 = s0;
                     gather_list<group_channel<R, 1>(), true>(V, G, cb + CH + n, cw + 9 * CH + n, CH, l, d0, d1,
                                                              &s0, &s1);
                     d0 = make_float2(d0.x + s0.x, d0.y + s0.y);
                     d1 = make_float2(d1.x + s1.x, d1.y + s1.y);
-                    gather_list_x<group_channel<R, 2>()>(V, G, cb + 2 * CH + n, cw + 2 * 9 * CH + n, CH, l, x0, x1);
-                    gather_list_x<group_channel<R, 3>(), true>(V, G, cb + 3 * CH + n, cw + 3 * 9 * CH + n, CH, l,
-                                                               x0, x1);
+                    gather_list<group_channel<R, 2>()>(V, G, cb + 2 * CH + n, cw + 2 * 9 * CH + n, CH, l, y0, y1);
+                    gather_list<group_channel<R, 3>(), false, true>(V, G, cb + 3 * CH + n, cw + 3 * 9 * CH + n, CH,
+                                                                    l, y0, y1);
+                    y0 = make_float2(y0.x - s0.x, y0.y - s0.y);
+                    y1 = make_float2(y1.x - s1.x, y1.y - s1.y);
                     const bool odd = l & 1;
-                    const float2 send = odd ? s0 : s1;
+                    const float2 send = odd ? y0 : y1;
                     const float2 recv = make_float2(__shfl_xor_sync(0xffffffffu, send.x, 1),
                                                     __shfl_xor_sync(0xffffffffu, send.y, 1));
-                    const float2 e0 = odd ? recv : s0, e1 = odd ? s1 : recv;
-                    x0 = make_float2(x0.x - e0.x, x0.y - e0.y);
-                    x1 = make_float2(x1.x - e1.x, x1.y - e1.y);
+                    x0 = odd ? recv : y0;
+                    x1 = odd ? y1 : recv;
                 } else {
                     gather_list<group_channel<R, 1>()>(V, G, cb + CH + n, cw + 9 * CH + n, CH, l, d0, d1);
                 }

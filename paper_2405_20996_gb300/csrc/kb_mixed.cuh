@@ -544,27 +544,13 @@ __device__ __forceinline__ void corner_pair(const float4* p, float2 w, float2& a
     }
 }
 
-// The same for an exchanged group: components s0, s1 of records p and p + 1 (float2 units).
-__device__ __forceinline__ void corner_pair_x(const float2* p, int s0, int s1, float2 w, float2& a0, float2& a1,
-                                              long long i0, long long n) {
-    if (w.x != 0.f && kb_rec_ok(i0, n, KB_SITE_K2_GATHER)) {
-        const float2 u0 = __ldg(p + s0), u1 = __ldg(p + s1);
-        a0 = __ffma2_rn(make_float2(w.x, w.x), u0, a0);
-        a1 = __ffma2_rn(make_float2(w.x, w.x), u1, a1);
-    }
-    if (w.y != 0.f && kb_rec_ok(i0 + 1, n, KB_SITE_K2_GATHER)) {
-        const float2 u0 = __ldg(p + 16 + s0), u1 = __ldg(p + 16 + s1);
-        a0 = __ffma2_rn(make_float2(w.y, w.y), u0, a0);
-        a1 = __ffma2_rn(make_float2(w.y, w.y), u1, a1);
-    }
-}
-
 // Gather of one compact corner list by a group of 8 lanes: lane l accumulates components
 // 2l, 2l+1 (one 16-byte piece of every corner record), acc += sum_k w_k rec_k[2l .. 2l+1],
 // so that one warp-wide load delivers the full records of the 4 nodes its lane groups hold.
 // With SPLIT the K1 and K2 corners accumulate into s0, s1 instead (the t channel reuses
-// them for the exchanged p group, which has the same K1 and K2 corners).
-template <int ch, bool SPLIT = false>
+// them for the exchanged p group, which has the same K1 and K2 corners); with SKIP12 they
+// are left out (that exchanged group, whose caller adds them from the direct group).
+template <int ch, bool SPLIT = false, bool SKIP12 = false>
 __device__ __forceinline__ void gather_list(const VertexF& V, const DfGrids& G, const int4* __restrict__ base,
                                             const float2* __restrict__ wt, int stride, int l, float2& a0,
                                             float2& a1, float2* s0 = nullptr, float2* s1 = nullptr) {
@@ -583,7 +569,7 @@ __device__ __forceinline__ void gather_list(const VertexF& V, const DfGrids& G, 
         corner_pair(c1 + (size_t)b.x * 8, w[0], *s0, *s1, b.x, n1);
         corner_pair(c2 + (size_t)b.y * 8, w[1], *s0, *s1, b.y, n2);
         corner_pair(c2 + (size_t)b.y * 8 + s2, w[2], *s0, *s1, b.y + v2, n2);
-    } else {
+    } else if (!SKIP12) {
         corner_pair(c1 + (size_t)b.x * 8, w[0], a0, a1, b.x, n1);
         corner_pair(c2 + (size_t)b.y * 8, w[1], a0, a1, b.y, n2);
         corner_pair(c2 + (size_t)b.y * 8 + s2, w[2], a0, a1, b.y + v2, n2);
@@ -595,34 +581,6 @@ __device__ __forceinline__ void gather_list(const VertexF& V, const DfGrids& G, 
     corner_pair(p3 + s3, w[6], a0, a1, b.w + v3, n3);
     corner_pair(p3 + s33, w[7], a0, a1, b.w + v33, n3);
     corner_pair(p3 + s33 + s3, w[8], a0, a1, b.w + v33 + v3, n3);
-}
-
-// The same for an exchanged group: lane l takes components kswap12(2l), kswap12(2l+1).
-// With SKIP12 the K1 and K2 corners are left out (the caller adds them from the direct group).
-template <int ch, bool SKIP12 = false>
-__device__ __forceinline__ void gather_list_x(const VertexF& V, const DfGrids& G, const int4* __restrict__ base,
-                                              const float2* __restrict__ wt, int stride, int l, float2& a0,
-                                              float2& a1) {
-    const int s0 = kswap12(2 * l), s1 = kswap12(2 * l + 1);
-    const int4 b = *base;
-    float2 w[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) w[i] = wt[i * stride];
-    const size_t s2 = (size_t)G.N2v * 16, s3 = (size_t)G.N3v * 16, s33 = (size_t)G.N3v * G.N3v * 16;
-    const long long n1 = G.N1, n2 = (long long)G.N2w * G.N2v, n3 = (long long)G.N3w * G.N3v * G.N3v;
-    const long long v2 = G.N2v, v3 = G.N3v, v33 = (long long)G.N3v * G.N3v;
-    if (!SKIP12) {
-        corner_pair_x(V.cls[ch][0] + (size_t)b.x * 16, s0, s1, w[0], a0, a1, b.x, n1);
-        corner_pair_x(V.cls[ch][1] + (size_t)b.y * 16, s0, s1, w[1], a0, a1, b.y, n2);
-        corner_pair_x(V.cls[ch][1] + (size_t)b.y * 16 + s2, s0, s1, w[2], a0, a1, b.y + v2, n2);
-    }
-    corner_pair_x(V.cls[ch][2] + (size_t)b.z * 16, s0, s1, w[3], a0, a1, b.z, n2);
-    corner_pair_x(V.cls[ch][2] + (size_t)b.z * 16 + s2, s0, s1, w[4], a0, a1, b.z + v2, n2);
-    const float2* p3 = V.cls[ch][3] + (size_t)b.w * 16;
-    corner_pair_x(p3, s0, s1, w[5], a0, a1, b.w, n3);
-    corner_pair_x(p3 + s3, s0, s1, w[6], a0, a1, b.w + v3, n3);
-    corner_pair_x(p3 + s33, s0, s1, w[7], a0, a1, b.w + v33, n3);
-    corner_pair_x(p3 + s33 + s3, s0, s1, w[8], a0, a1, b.w + v33 + v3, n3);
 }
 
 // Host helpers of the mixed path (kb_mixed.cu) shared with its adjoint (kb_vjp.cu): the

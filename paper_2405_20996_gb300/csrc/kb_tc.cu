@@ -2,21 +2,25 @@
 // split: each FP32 operand x = hi + lo (hi = TF32 rounding of x, lo = x - hi), and
 //   Re C = Ar Br - Ai Bi,  Im C = Ar Bi + Ai Br,
 // every real product X Y taken as Xhi Yhi + Xhi Ylo + Xlo Yhi (the lo*lo term, ~2^-22
-// relative, is dropped).  The minus sign of Ai Bi is the negate-A bit of the instruction
-// descriptor.  A CTA computes either the real or the imaginary part of a 128 x 128 output
-// tile (6 MMAs of N = 128 per k-step): the register file holds the compensated running
-// sums of 128 x 128 real values, and N = 128 halves the shared-memory operand reads per MMA
-// flop against complex 128 x 64 tiles.  Every CTA loads all of its operand planes itself
-// (plain TMA into its own shared memory; no thread-block clusters).  Accumulation in FP32
-// in tensor memory restarted every SEG K chunks; finished segments are added into compensated FP32 sums in registers,
-// the K dimension is split over CTAs and the split partials are added in FP64.
+// relative, is dropped).  Two tile shapes (see TcShape):
+//   one CTA for the real or the imaginary part of a 128 x 128 complex tile: 6 MMAs of
+//   N = 128 per k-step, the minus sign of Ai Bi through the negate-A bit of the instruction
+//   descriptor;
+//   one CTA for both parts of a 128 x 64 complex tile: the B planes of the real and the
+//   imaginary part sit side by side in shared memory as one 128-row operand [Br | Bi], so
+//   P = Ar [Br | Bi] and Q = Ai [Br | Bi] are 6 MMAs of N = 128 per k-step into two
+//   accumulators, and the epilogue forms Re = P_r - Q_i, Im = P_i + Q_r column by column.
+// Every CTA loads all of its operand planes itself (plain TMA into its own shared memory;
+// no thread-block clusters).  Accumulation in FP32 in tensor memory restarted every SEG K
+// chunks; finished segments are added into compensated FP32 sums in registers, the K
+// dimension is split over CTAs and the split partials are added in FP64.
 //
 // Operands (written by k_mx_tile3): A = [batch][plane][M][K], B = [batch][plane][N][K],
 // planes (re hi, re lo, im hi, im lo), K-contiguous FP32.  One CTA = one (batch, 128-row
-// M tile, 128-column N tile, part Re or Im, K range).  Warp roles: warp 0 issues the TMA loads, warp 1
-// allocates tensor memory and issues the MMAs, warps 2-17 drain the accumulators.  All waits are bounded; a wait that gives up sets a device flag
-// (read by kb_check_device), the CTA drains its copies in flight and frees its tensor
-// memory before returning.
+// M tile, N tile, part or both parts, K range).  Warp roles: warp 0 issues the TMA loads,
+// warp 1 allocates tensor memory and issues the MMAs, warps 2-17 drain the accumulators.
+// All waits are bounded; a wait that gives up sets a device flag (read by kb_check_device),
+// the CTA drains its copies in flight and frees its tensor memory before returning.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -133,6 +137,25 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Two 8-column loads (columns ta .. ta+7 and tb .. tb+7 of this warp's 32 lanes) and one
+// wait, in one statement so that no use of the values can be placed before the wait.
+__device__ __forceinline__ void tmem_ld8x2(uint32_t ta, uint32_t tb, float a[8], float b[8]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%17];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(ta), "r"(tb)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        a[i] = __uint_as_float(r[i]);
+        b[i] = __uint_as_float(r[8 + i]);
+    }
+}
+
 struct TcJob {
     int M, N, K, batch, mtiles, ntiles, ksplit, chunks_per_split, nchunks;
     int tiles;   // output tiles per batch entry that are computed
@@ -154,16 +177,19 @@ __host__ __device__ inline int tc_tiles(int mtiles, int ntiles, int cols, bool t
     return n;
 }
 
-// Segmented accumulation: tensor memory holds two buffers of the CTA's 128 x 128 FP32
-// accumulators; the MMA warp restarts a buffer every SEG K chunks and the epilogue warps add
-// each finished segment into compensated (Kahan) FP32 running sums held in registers, so no
-// plain FP32 accumulator ever sums more than SEG * KC * 6 / 8 products.
+// Segmented accumulation: tensor memory holds two buffers of the CTA's FP32 accumulators
+// (128 x 128, or for both parts the two 128 x 128 products P and Q); the MMA warp restarts a
+// buffer every SEG K chunks and the epilogue warps add each finished segment into
+// compensated (Kahan) FP32 running sums held in registers, so no plain FP32 accumulator ever
+// sums more than SEG * KC * 6 / 8 products.
 // Two tile shapes (template BOTH):
 //   BOTH = false  one CTA per real or imaginary part of a 128 x 128 complex tile, N = 128
 //                 MMAs (6 per k-step); the Re and Im CTAs of a tile each load all 8 planes;
-//   BOTH = true   one CTA for both parts of a 128 x 64 complex tile, N = 64 MMAs (12 per
-//                 k-step) into a real and an imaginary accumulator, so every operand byte
-//                 is loaded once per tile.
+//   BOTH = true   one CTA for both parts of a 128 x 64 complex tile: the B planes stored as
+//                 [re hi, im hi, re lo, im lo], so that [Br | Bi] (hi or lo) is one 128-row
+//                 operand, and 6 MMAs of N = 128 per k-step give P = Ar [Br | Bi] and
+//                 Q = Ai [Br | Bi] (512 tensor-memory columns: two buffers of P and Q);
+//                 every operand byte is loaded once per tile.
 // Both hold 128 x 128 running sums per CTA (the register budget of the Kahan epilogue).
 constexpr int SEG = 2;
 constexpr int EPI_WARPS = 16;                 // 4 per TMEM lane quarter, 32 columns each
@@ -193,7 +219,8 @@ __device__ __forceinline__ void kahan2(float2& s, float2& n, float2 x) {
     s = t;
 }
 
-// partial sums P[ks][b][M][N] double2
+// partial sums P[ks][b][M][N] double2.  Register cap: the 18 warps of a CTA sit 5, 5, 4, 4
+// on the SM's four sub-partitions of 16384 registers each, so at most 102 per thread.
 template <bool BOTH>
 __global__ void __maxnreg__(96)
     k_tc_k3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcJob J,
@@ -201,7 +228,8 @@ __global__ void __maxnreg__(96)
     using S = TcShape<BOTH>;
     constexpr int NT = S::NT, STAGES_S = S::STAGES;
     constexpr uint32_t A_PLANE = S::A_PLANE, B_PLANE = S::B_PLANE, STAGE = S::STAGE;
-    constexpr uint32_t TMEM_COLS = 256;            // 2 buffers x 128 columns
+    constexpr uint32_t BUF_COLS = BOTH ? 256 : 128;  // one accumulator buffer (BOTH: P, Q)
+    constexpr uint32_t TMEM_COLS = 2 * BUF_COLS;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES_S * STAGE);
@@ -261,8 +289,10 @@ __global__ void __maxnreg__(96)
                 mbar_expect_tx(&full[s], STAGE);
                 int kx = (c0 + i) * KC;
                 for (int p = 0; p < 4; ++p) {
+                    // B planes: BOTH stores them as re hi, im hi, re lo, im lo
+                    const int bslot = BOTH ? ((p & 1) * 2 + (p >> 1)) : p;
                     tma_load_3d(st + p * A_PLANE, &tmA, &full[s], kx, mt * MT, 4 * b + p);
-                    tma_load_3d(st + 4 * A_PLANE + p * B_PLANE, &tmB, &full[s], kx, nt * NT, 4 * b + p);
+                    tma_load_3d(st + 4 * A_PLANE + bslot * B_PLANE, &tmB, &full[s], kx, nt * NT, 4 * b + p);
                 }
                 issued |= 1u << s;
                 phases = (phases & ~(1u << s)) | (ph << s);
@@ -278,6 +308,7 @@ __global__ void __maxnreg__(96)
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t id_pos = idesc_tf32(MT, NT, false), id_neg = idesc_tf32(MT, NT, true);
+            const uint32_t id_cat = idesc_tf32(MT, 2 * NT, false);   // BOTH: B = [Br | Bi]
             for (int i = 0; i < nck; ++i) {
                 int s = i % STAGES_S;
                 uint32_t ph = (uint32_t)((i / STAGES_S) & 1);
@@ -289,7 +320,7 @@ __global__ void __maxnreg__(96)
                 }
                 if (!mbar_wait(&full[s], ph)) { atomicOr(&g_tc_status, 2); s_fail = 1; break; }
                 fence_after();
-                const uint32_t dacc = tbase + buf * 128;
+                const uint32_t dacc = tbase + buf * BUF_COLS;
                 uint32_t sa = smem_u32(smem + s * STAGE);
                 uint32_t sb = sa + 4 * A_PLANE;
 #pragma unroll
@@ -297,10 +328,21 @@ __global__ void __maxnreg__(96)
                     uint32_t off = kk * 32;
                     uint64_t arh = sdesc_sw64(sa + 0 * A_PLANE + off), arl = sdesc_sw64(sa + 1 * A_PLANE + off);
                     uint64_t aih = sdesc_sw64(sa + 2 * A_PLANE + off), ail = sdesc_sw64(sa + 3 * A_PLANE + off);
+                    uint32_t first = (seg_start && kk == 0) ? 0u : 1u;
+                    if (BOTH) {
+                        // P = Ar [Br | Bi] (columns 0-127), Q = Ai [Br | Bi] (128-255)
+                        const uint64_t bch = sdesc_sw64(sb + off), bcl = sdesc_sw64(sb + 2 * B_PLANE + off);
+                        mma_tf32(dacc, arh, bch, id_cat, first);
+                        mma_tf32(dacc, arh, bcl, id_cat, 1);
+                        mma_tf32(dacc, arl, bch, id_cat, 1);
+                        mma_tf32(dacc + 128, aih, bch, id_cat, first);
+                        mma_tf32(dacc + 128, aih, bcl, id_cat, 1);
+                        mma_tf32(dacc + 128, ail, bch, id_cat, 1);
+                        continue;
+                    }
                     uint64_t brh = sdesc_sw64(sb + 0 * B_PLANE + off), brl = sdesc_sw64(sb + 1 * B_PLANE + off);
                     uint64_t bih = sdesc_sw64(sb + 2 * B_PLANE + off), bil = sdesc_sw64(sb + 3 * B_PLANE + off);
-                    uint32_t first = (seg_start && kk == 0) ? 0u : 1u;
-                    if (BOTH || part == 0) {   // Re = Ar Br - Ai Bi
+                    if (part == 0) {           // Re = Ar Br - Ai Bi
                         mma_tf32(dacc, arh, brh, id_pos, first);
                         mma_tf32(dacc, arh, brl, id_pos, 1);
                         mma_tf32(dacc, arl, brh, id_pos, 1);
@@ -308,14 +350,13 @@ __global__ void __maxnreg__(96)
                         mma_tf32(dacc, aih, bil, id_neg, 1);
                         mma_tf32(dacc, ail, bih, id_neg, 1);
                     }
-                    if (BOTH || part == 1) {   // Im = Ar Bi + Ai Br
-                        const uint32_t di = BOTH ? dacc + 64 : dacc;
-                        mma_tf32(di, arh, bih, id_pos, first);
-                        mma_tf32(di, arh, bil, id_pos, 1);
-                        mma_tf32(di, arl, bih, id_pos, 1);
-                        mma_tf32(di, aih, brh, id_pos, 1);
-                        mma_tf32(di, aih, brl, id_pos, 1);
-                        mma_tf32(di, ail, brh, id_pos, 1);
+                    if (part == 1) {           // Im = Ar Bi + Ai Br
+                        mma_tf32(dacc, arh, bih, id_pos, first);
+                        mma_tf32(dacc, arh, bil, id_pos, 1);
+                        mma_tf32(dacc, arl, bih, id_pos, 1);
+                        mma_tf32(dacc, aih, brh, id_pos, 1);
+                        mma_tf32(dacc, aih, brl, id_pos, 1);
+                        mma_tf32(dacc, ail, brh, id_pos, 1);
                     }
                 }
                 mma_commit(&empty[s]);                   // the stage is free once its MMAs are done
@@ -328,7 +369,8 @@ __global__ void __maxnreg__(96)
         }
     } else {
         // epilogue warps 2 .. 2+EPI_WARPS-1: lane quarter q, 32-column group cg of the 128
-        // accumulator columns (BOTH: cg 0, 1 real, 2, 3 imaginary part of 64 columns)
+        // output columns (BOTH: cg 0, 1 real, 2, 3 imaginary part of the 64 complex columns,
+        // each formed from the products P and Q)
         int e = warp - 2;
         int q = warp & 3, cg = e >> 2;
         float2 sm[16], ng[16];       // columns (2i, 2i+1): running sums and negated compensations
@@ -341,14 +383,32 @@ __global__ void __maxnreg__(96)
                 atomicOr(&g_tc_status, 4); ok = false; break;
             }
             fence_after();
-            uint32_t ta = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 128 + cg * 32);
-            // two 16-column loads, one wait each
+            const uint32_t lb = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BUF_COLS);
+            if (BOTH) {
+                // Re = Ar Br - Ai Bi = P[c] - Q[64 + c], Im = Ar Bi + Ai Br = P[64 + c] + Q[c]
+                const int pp = cg >> 1, h = cg & 1;
+                const uint32_t tp = lb + (uint32_t)(pp * 64 + h * 32), tq = lb + (uint32_t)(128 + (1 - pp) * 64 + h * 32);
+                const float2 sg = pp ? make_float2(1.f, 1.f) : make_float2(-1.f, -1.f);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                float v[16];
-                tmem_ld16(ta + 16 * h, v);
+                for (int hh = 0; hh < 4; ++hh) {
+                    float x[8], y[8];
+                    tmem_ld8x2(tp + 8 * hh, tq + 8 * hh, x, y);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) kahan2(sm[8 * h + c], ng[8 * h + c], make_float2(v[2 * c], v[2 * c + 1]));
+                    for (int c = 0; c < 4; ++c)
+                        kahan2(sm[4 * hh + c], ng[4 * hh + c],
+                               __ffma2_rn(sg, make_float2(y[2 * c], y[2 * c + 1]), make_float2(x[2 * c], x[2 * c + 1])));
+                }
+            } else {
+                // two 16-column loads, one wait each
+                const uint32_t ta = lb + (uint32_t)(cg * 32);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float v[16];
+                    tmem_ld16(ta + 16 * h, v);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        kahan2(sm[8 * h + c], ng[8 * h + c], make_float2(v[2 * c], v[2 * c + 1]));
+                }
             }
             fence_before();
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&segempty[buf])) : "memory");
