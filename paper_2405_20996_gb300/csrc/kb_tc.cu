@@ -11,9 +11,9 @@
 //   P = Ar [Br | Bi] and Q = Ai [Br | Bi] are 6 MMAs of N = 128 per k-step into two
 //   accumulators, and the epilogue forms Re = P_r - Q_i, Im = P_i + Q_r column by column.
 // Every CTA loads all of its operand planes itself (plain TMA into its own shared memory;
-// no thread-block clusters).  Accumulation in FP32 in tensor memory restarted every SEG K
-// chunks; finished segments are added into compensated FP32 sums in registers, the K
-// dimension is split over CTAs and the split partials are added in FP64.
+// no thread-block clusters).  Accumulation in FP32 in tensor memory restarted every 32
+// elements of K; finished segments are added into compensated FP32 sums in registers, the
+// K dimension is split over CTAs and the split partials are added in FP64.
 //
 // Operands (written by k_mx_tile3): A = [batch][plane][M][K], B = [batch][plane][N][K],
 // planes (re hi, re lo, im hi, im lo), K-contiguous FP32.  One CTA = one (batch, 128-row
@@ -40,7 +40,7 @@
 namespace kb {
 namespace tc {
 
-constexpr int KC = 16;            // K elements (FP32) per stage and plane row: 64 bytes
+constexpr int SEGK = 32;          // K elements per accumulation segment
 constexpr int MT = 128;           // rows per M tile
 constexpr long long WAIT_BUDGET = 4000000000LL;   // clock cycles (~2 s) per wait
 
@@ -81,15 +81,17 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
-// Shared-memory matrix descriptor (tcgen05): K-major operand, 64-byte swizzle, 8-row
-// groups 512 bytes apart.
-__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+// Shared-memory matrix descriptor (tcgen05): K-major operand with rows of ROWB bytes
+// (64: 64-byte swizzle, 128: 128-byte swizzle), 8-row groups 8 * ROWB bytes apart.
+template <int ROWB>
+__device__ __forceinline__ uint64_t sdesc_kmajor(uint32_t saddr) {
+    static_assert(ROWB == 64 || ROWB == 128, "row bytes");
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);     // start address
     d |= (uint64_t)1 << 16;                         // leading byte offset (unused here)
-    d |= (uint64_t)(512 >> 4) << 32;                // stride byte offset
+    d |= (uint64_t)((8 * ROWB) >> 4) << 32;         // stride byte offset
     d |= (uint64_t)1 << 46;                         // descriptor version
-    d |= (uint64_t)4 << 61;                         // 64-byte swizzle
+    d |= (uint64_t)(ROWB == 128 ? 2 : 4) << 61;     // 128- or 64-byte swizzle
     return d;
 }
 
@@ -179,28 +181,33 @@ __host__ __device__ inline int tc_tiles(int mtiles, int ntiles, int cols, bool t
 
 // Segmented accumulation: tensor memory holds two buffers of the CTA's FP32 accumulators
 // (128 x 128, or for both parts the two 128 x 128 products P and Q); the MMA warp restarts a
-// buffer every SEG K chunks and the epilogue warps add each finished segment into
-// compensated (Kahan) FP32 running sums held in registers, so no plain FP32 accumulator ever
-// sums more than SEG * KC * 6 / 8 products.
+// buffer every SEGK = 32 elements of K and the epilogue warps add each finished segment
+// into compensated (Kahan) FP32 running sums held in registers, so no plain FP32 accumulator
+// ever sums more than SEGK * 6 / 8 products.
 // Two tile shapes (template BOTH):
 //   BOTH = false  one CTA per real or imaginary part of a 128 x 128 complex tile, N = 128
 //                 MMAs (6 per k-step); the Re and Im CTAs of a tile each load all 8 planes;
+//                 stages of 16 K elements (64-byte plane rows, 64-byte swizzle);
 //   BOTH = true   one CTA for both parts of a 128 x 64 complex tile: the B planes stored as
 //                 [re hi, im hi, re lo, im lo], so that [Br | Bi] (hi or lo) is one 128-row
 //                 operand, and 6 MMAs of N = 128 per k-step give P = Ar [Br | Bi] and
 //                 Q = Ai [Br | Bi] (512 tensor-memory columns: two buffers of P and Q);
-//                 every operand byte is loaded once per tile.
+//                 every operand byte is loaded once per tile; stages of 32 K elements
+//                 (128-byte plane rows, 128-byte swizzle), so that each TMA row read is a
+//                 whole 128-byte line.
 // Both hold 128 x 128 running sums per CTA (the register budget of the Kahan epilogue).
-constexpr int SEG = 2;
 constexpr int EPI_WARPS = 16;                 // 4 per TMEM lane quarter, 32 columns each
 constexpr int NTHREADS_S = 64 + 32 * EPI_WARPS;
 
 template <bool BOTH>
 struct TcShape {
     static constexpr int NT = BOTH ? 64 : 128;            // B rows (complex columns) per CTA
-    static constexpr int STAGES = BOTH ? 4 : 3;
-    static constexpr uint32_t A_PLANE = MT * KC * 4;      // 8 KB
-    static constexpr uint32_t B_PLANE = NT * KC * 4;      // 4 or 8 KB
+    static constexpr int KC = BOTH ? 32 : 16;             // K elements per stage (plane row)
+    static constexpr int ROWB = KC * 4;                   // plane row bytes = swizzle width
+    static constexpr int SEG = SEGK / KC;                 // stages per accumulation segment
+    static constexpr int STAGES = BOTH ? 2 : 3;
+    static constexpr uint32_t A_PLANE = MT * KC * 4;      // 16 or 8 KB
+    static constexpr uint32_t B_PLANE = NT * KC * 4;      // 8 KB
     static constexpr uint32_t STAGE = 4 * A_PLANE + 4 * B_PLANE;
     static constexpr int PARTS = BOTH ? 1 : 2;            // CTAs per tile
     static constexpr size_t smem() { return (size_t)STAGES * STAGE + 128 + 1024; }
@@ -226,7 +233,7 @@ __global__ void __maxnreg__(96)
     k_tc_k3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcJob J,
             double2* __restrict__ P) {
     using S = TcShape<BOTH>;
-    constexpr int NT = S::NT, STAGES_S = S::STAGES;
+    constexpr int NT = S::NT, STAGES_S = S::STAGES, KC = S::KC, ROWB = S::ROWB, SEG = S::SEG;
     constexpr uint32_t A_PLANE = S::A_PLANE, B_PLANE = S::B_PLANE, STAGE = S::STAGE;
     constexpr uint32_t BUF_COLS = BOTH ? 256 : 128;  // one accumulator buffer (BOTH: P, Q)
     constexpr uint32_t TMEM_COLS = 2 * BUF_COLS;
@@ -326,12 +333,12 @@ __global__ void __maxnreg__(96)
 #pragma unroll
                 for (int kk = 0; kk < KC / 8; ++kk) {
                     uint32_t off = kk * 32;
-                    uint64_t arh = sdesc_sw64(sa + 0 * A_PLANE + off), arl = sdesc_sw64(sa + 1 * A_PLANE + off);
-                    uint64_t aih = sdesc_sw64(sa + 2 * A_PLANE + off), ail = sdesc_sw64(sa + 3 * A_PLANE + off);
+                    uint64_t arh = sdesc_kmajor<ROWB>(sa + 0 * A_PLANE + off), arl = sdesc_kmajor<ROWB>(sa + 1 * A_PLANE + off);
+                    uint64_t aih = sdesc_kmajor<ROWB>(sa + 2 * A_PLANE + off), ail = sdesc_kmajor<ROWB>(sa + 3 * A_PLANE + off);
                     uint32_t first = (seg_start && kk == 0) ? 0u : 1u;
                     if (BOTH) {
                         // P = Ar [Br | Bi] (columns 0-127), Q = Ai [Br | Bi] (128-255)
-                        const uint64_t bch = sdesc_sw64(sb + off), bcl = sdesc_sw64(sb + 2 * B_PLANE + off);
+                        const uint64_t bch = sdesc_kmajor<ROWB>(sb + off), bcl = sdesc_kmajor<ROWB>(sb + 2 * B_PLANE + off);
                         mma_tf32(dacc, arh, bch, id_cat, first);
                         mma_tf32(dacc, arh, bcl, id_cat, 1);
                         mma_tf32(dacc, arl, bch, id_cat, 1);
@@ -340,8 +347,8 @@ __global__ void __maxnreg__(96)
                         mma_tf32(dacc + 128, ail, bch, id_cat, 1);
                         continue;
                     }
-                    uint64_t brh = sdesc_sw64(sb + 0 * B_PLANE + off), brl = sdesc_sw64(sb + 1 * B_PLANE + off);
-                    uint64_t bih = sdesc_sw64(sb + 2 * B_PLANE + off), bil = sdesc_sw64(sb + 3 * B_PLANE + off);
+                    uint64_t brh = sdesc_kmajor<ROWB>(sb + 0 * B_PLANE + off), brl = sdesc_kmajor<ROWB>(sb + 1 * B_PLANE + off);
+                    uint64_t bih = sdesc_kmajor<ROWB>(sb + 2 * B_PLANE + off), bil = sdesc_kmajor<ROWB>(sb + 3 * B_PLANE + off);
                     if (part == 0) {           // Re = Ar Br - Ai Bi
                         mma_tf32(dacc, arh, brh, id_pos, first);
                         mma_tf32(dacc, arh, brl, id_pos, 1);
@@ -481,15 +488,16 @@ static EncodeTiled encoder() {
     return fn;
 }
 
-static bool make_map(CUtensorMap* m, const float* base, int K, int rows, int planes, int box_rows) {
+static bool make_map(CUtensorMap* m, const float* base, int K, int rows, int planes, int box_rows, int kc) {
     EncodeTiled enc = encoder();
     if (!enc) return false;
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)planes};
     cuuint64_t strides[2] = {(cuuint64_t)K * 4, (cuuint64_t)K * 4 * rows};
-    cuuint32_t box[3] = {(cuuint32_t)KC, (cuuint32_t)box_rows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)box_rows, 1};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, es,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, kc == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
@@ -517,6 +525,7 @@ struct TcPlan {
 };
 
 static int tc_cols(int both) { return both ? TcShape<true>::NT : TcShape<false>::NT; }
+static int tc_kc(int both) { return both ? TcShape<true>::KC : TcShape<false>::KC; }
 static int tc_parts(int both) { return both ? TcShape<true>::PARTS : TcShape<false>::PARTS; }
 
 // Split-K candidates for one contraction shape and tile shape, best first by the wave
@@ -527,11 +536,12 @@ static std::vector<std::pair<double, int>> split_candidates(int device, int both
                                                             size_t scratch_bytes, bool tri) {
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    const int mtiles = (M + MT - 1) / MT, ntiles = (N + tc_cols(both) - 1) / tc_cols(both), nchunks = (K + KC - 1) / KC;
+    const int mtiles = (M + MT - 1) / MT, ntiles = (N + tc_cols(both) - 1) / tc_cols(both),
+              nseg = (K + SEGK - 1) / SEGK;
     const long base = (long)batch * tc_tiles(mtiles, ntiles, tc_cols(both), tri) * tc_parts(both);
     std::vector<std::pair<double, int>> c;
     for (int s = 1; s <= 64; ++s) {
-        if ((nchunks + s - 1) / s < 8 * SEG) break;
+        if ((nseg + s - 1) / s < 8) break;
         if ((size_t)s * batch * M * N * sizeof(double2) > scratch_bytes) break;
         const long units = base * s, waves = (units + sms - 1) / sms;
         c.push_back({(double)units / (waves * sms) * (1.0 - 0.002 * s), s});
@@ -568,13 +578,13 @@ static bool launch_plan(kb_ctx* ctx, const float* At, const float* Bt, double2* 
 
 static bool launch(kb_ctx* ctx, const float* At, const float* Bt, double2* Cm, int M, int N, int K, int batch,
                    void* scratch, size_t scratch_bytes, bool tri, cudaStream_t st) {
-    const int nchunks = (K + KC - 1) / KC;
     TcPlan plan;
     if (!tuned_plan(ctx->device, M, N, K, batch, tri, plan) ||
         (size_t)plan.split * batch * M * N * sizeof(double2) > scratch_bytes)
         plan = default_plan(ctx->device, M, N, K, batch, scratch_bytes, tri);
     const char* cps_env = std::getenv("KB_TC_CPS");   // developer override: K chunks per split
     if (cps_env && std::atoi(cps_env) > 0) {
+        const int nchunks = (K + tc_kc(plan.both) - 1) / tc_kc(plan.both);
         int cps = std::atoi(cps_env);
         int s = (nchunks + cps - 1) / cps;
         if ((size_t)s * batch * M * N * sizeof(double2) <= scratch_bytes) plan.split = s;
@@ -633,7 +643,7 @@ static bool launch_plan(kb_ctx* ctx, const float* At, const float* Bt, double2* 
     const int cols = tc_cols(plan.both);
     J.mtiles = (M + MT - 1) / MT;
     J.ntiles = (N + cols - 1) / cols;
-    J.nchunks = (K + KC - 1) / KC;
+    J.nchunks = (K + tc_kc(plan.both) - 1) / tc_kc(plan.both);
     J.tri = (tri && M == N) ? 1 : 0;
     J.tiles = tc_tiles(J.mtiles, J.ntiles, cols, J.tri != 0);
     const int base = batch * J.tiles * tc_parts(plan.both);
@@ -644,7 +654,9 @@ static bool launch_plan(kb_ctx* ctx, const float* At, const float* Bt, double2* 
                      M, N, K, batch, J.mtiles, J.ntiles, J.tiles, plan.both ? "re+im" : "part", J.ksplit,
                      J.chunks_per_split);
     CUtensorMap ma, mb;
-    if (!make_map(&ma, At, K, M, 4 * batch, MT) || !make_map(&mb, Bt, K, N, 4 * batch, cols)) return false;
+    if (!make_map(&ma, At, K, M, 4 * batch, MT, tc_kc(plan.both)) ||
+        !make_map(&mb, Bt, K, N, 4 * batch, cols, tc_kc(plan.both)))
+        return false;
     if (!tc_prepare(ctx->device)) return false;
     double2* P = reinterpret_cast<double2*>(scratch);
     {

@@ -105,12 +105,18 @@ def test_mixed_full_size_vs_fp64_gpu_and_oracle_samples():
             assert np.abs(gotf - ref).max() <= 1e-10 * scale, (r, k)
 
 
-def test_tensor_core_contraction_matches_simt_reference():
+@pytest.mark.parametrize("shape", ["1", "0"], ids=["both-parts", "one-part"])
+def test_tensor_core_contraction_matches_simt_reference(shape):
     """K3 through tcgen05 (3xTF32, segmented FP32 accumulation) vs the SIMT FP32
-    reference contraction of the same tiles."""
+    reference contraction of the same tiles, in each tile shape of the tensor-core kernel
+    (both parts of a 128 x 64 complex tile per CTA, or one part of a 128 x 128 tile)."""
     cfg = RAGGED
     ch = seeded_inputs(cfg, seed=47)
-    tc = gpu_bubble(cfg, ch, 2, "mixed", mask=8)
+    os.environ["KB_TC_SHAPE"] = shape
+    try:
+        tc = gpu_bubble(cfg, ch, 2, "mixed", mask=8)
+    finally:
+        os.environ.pop("KB_TC_SHAPE", None)
     os.environ["KB_K3_SIMT"] = "1"
     try:
         simt = gpu_bubble(cfg, ch, 2, "mixed", mask=8)
