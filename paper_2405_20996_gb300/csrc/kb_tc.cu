@@ -129,32 +129,26 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Two 8-column loads (columns ta .. ta+7 and tb .. tb+7 of this warp's 32 lanes) and one
-// wait, in one statement so that no use of the values can be placed before the wait.
-__device__ __forceinline__ void tmem_ld8x2(uint32_t ta, uint32_t tb, float a[8], float b[8]) {
+// Four 4-column loads (this warp's 32 lanes) and one wait, in one statement.
+__device__ __forceinline__ void tmem_ld4x4(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3, float a[4], float b[4],
+                                           float c[4], float d[4]) {
     uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%17];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%16];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4, %5, %6, %7}, [%17];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8, %9, %10, %11}, [%18];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12, %13, %14, %15}, [%19];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
           "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(ta), "r"(tb)
+        : "r"(t0), "r"(t1), "r"(t2), "r"(t3)
         : "memory");
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < 4; ++i) {
         a[i] = __uint_as_float(r[i]);
-        b[i] = __uint_as_float(r[8 + i]);
+        b[i] = __uint_as_float(r[4 + i]);
+        c[i] = __uint_as_float(r[8 + i]);
+        d[i] = __uint_as_float(r[12 + i]);
     }
 }
 
@@ -375,12 +369,12 @@ __global__ void __maxnreg__(96)
             if (!mbar_wait(drain, 0)) atomicOr(&g_tc_status, 2);
         }
     } else {
-        // epilogue warps 2 .. 2+EPI_WARPS-1: lane quarter q, 32-column group cg of the 128
-        // output columns (BOTH: cg 0, 1 real, 2, 3 imaginary part of the 64 complex columns,
-        // each formed from the products P and Q)
+        // epilogue warps 2 .. 2+EPI_WARPS-1: lane quarter q, column group cg: one part, 32
+        // real columns 2i, 2i+1 per sm[i]; BOTH: 16 complex columns, the real and imaginary
+        // part of column i in sm[i], each formed from the products P and Q
         int e = warp - 2;
         int q = warp & 3, cg = e >> 2;
-        float2 sm[16], ng[16];       // columns (2i, 2i+1): running sums and negated compensations
+        float2 sm[16], ng[16];       // running sums and negated compensations
 #pragma unroll
         for (int i = 0; i < 16; ++i) { sm[i] = make_float2(0.f, 0.f); ng[i] = make_float2(0.f, 0.f); }
         bool ok = true;
@@ -392,18 +386,17 @@ __global__ void __maxnreg__(96)
             fence_after();
             const uint32_t lb = tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BUF_COLS);
             if (BOTH) {
-                // Re = Ar Br - Ai Bi = P[c] - Q[64 + c], Im = Ar Bi + Ai Br = P[64 + c] + Q[c]
-                const int pp = cg >> 1, h = cg & 1;
-                const uint32_t tp = lb + (uint32_t)(pp * 64 + h * 32), tq = lb + (uint32_t)(128 + (1 - pp) * 64 + h * 32);
-                const float2 sg = pp ? make_float2(1.f, 1.f) : make_float2(-1.f, -1.f);
+                // column c = 16 cg + i: Re = Ar Br - Ai Bi = P[c] - Q[64 + c],
+                // Im = Ar Bi + Ai Br = P[64 + c] + Q[c]
+                const uint32_t t0 = lb + (uint32_t)(16 * cg);
 #pragma unroll
                 for (int hh = 0; hh < 4; ++hh) {
-                    float x[8], y[8];
-                    tmem_ld8x2(tp + 8 * hh, tq + 8 * hh, x, y);
+                    float pr[4], qi[4], pim[4], qr[4];
+                    tmem_ld4x4(t0 + 4 * hh, t0 + 192 + 4 * hh, t0 + 64 + 4 * hh, t0 + 128 + 4 * hh, pr, qi, pim, qr);
 #pragma unroll
                     for (int c = 0; c < 4; ++c)
                         kahan2(sm[4 * hh + c], ng[4 * hh + c],
-                               __ffma2_rn(sg, make_float2(y[2 * c], y[2 * c + 1]), make_float2(x[2 * c], x[2 * c + 1])));
+                               make_float2(__fsub_rn(pr[c], qi[c]), __fadd_rn(pim[c], qr[c])));
                 }
             } else {
                 // two 16-column loads, one wait each
@@ -421,11 +414,18 @@ __global__ void __maxnreg__(96)
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&segempty[buf])) : "memory");
         }
         int row = mt * MT + q * 32 + lane;
-        if (ok && row < J.M) {
+        if (ok && row < J.M && BOTH) {
+            // the FP64 partial of 16 complex columns, one 16-byte store each
+            double2* out = P + (((size_t)ks * J.batch + b) * J.M + row) * J.N;
+            const int col0 = nt * NT + 16 * cg;
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                if (col0 + i < J.N)
+                    out[col0 + i] = make_double2((double)sm[i].x + (double)ng[i].x, (double)sm[i].y + (double)ng[i].y);
+        } else if (ok && row < J.M) {
             // the FP64 partial: .x real / .y imaginary part of this CTA's columns
-            const int pp = BOTH ? (cg >> 1) : part;
-            double* out = reinterpret_cast<double*>(P + (((size_t)ks * J.batch + b) * J.M + row) * J.N) + pp;
-            int col0 = nt * NT + (BOTH ? (cg & 1) : cg) * 32;
+            double* out = reinterpret_cast<double*>(P + (((size_t)ks * J.batch + b) * J.M + row) * J.N) + part;
+            int col0 = nt * NT + cg * 32;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 if (col0 + 2 * i < J.N) out[2 * (col0 + 2 * i)] = (double)sm[i].x + (double)ng[i].x;
