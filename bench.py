@@ -117,7 +117,7 @@ def mixed_kernel_work(channels=(0, 1, 2), t_su2=False):
 # a-channel bubble of this workload (dram__bytes_read.sum + dram__bytes_write.sum; the
 # commands are in profiles/).  The K3 kernels' traffic grows with the bosonic frequencies of
 # a launch; these are the figures of the captured launches (26 frequencies).
-NCU_TRAFFIC = {"k_mx_k2": 79.61e6, "k_mx_tile3_both": 2.830e9, "k_tc_k3": 3.505e9}
+NCU_TRAFFIC = {"k_mx_k2": 79.61e6, "k_mx_tile3_both": 2.830e9, "k_tc_k3": 3.463e9}
 
 
 def roofline_entry(name, ms_total, steps, work, bf16_peak, traffic=None):
