@@ -803,6 +803,7 @@ def main():
             prof[k] = (p0[0] + t, p0[1] + c)
         kb.kb_profile_enable(e.ctx, False)
     ms = sum(a.elapsed_time(b) for a, b in evs)
+    ms_median = float(np.median([a.elapsed_time(b) for a, b in evs]))
     value, ms_step = weak_scaling_value(points, ms / args.steps, dist, dev)
 
     # ---- end to end through the public API: pinned host inputs -> device -> bubbles -> host ----
@@ -915,6 +916,7 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "points/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "ms_per_step_median": ms_median,
                 "vs_baseline": None, "dtype": "f32" if prec == "mixed" else "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD if len(chans) == 3 else WORKLOAD.replace("a,p,t", args.channels),
                            "precision": prec, "points_per_step": points,
