@@ -264,6 +264,12 @@ typedef struct {
     int n_dsig;                   /* > 0: Katanin substitution with the table dSigma/dLambda */
     double A_dsig;
     const cplx *dsigR, *dsigK;
+    int n_gt;                     /* > 0: G^R, G^K given as tables (the G-table propagator input) */
+    double A_gt;
+    const cplx *gtR, *gtK;
+    int n_st;                     /* > 0: S^R, S^K given as tables */
+    double A_st;
+    const cplx *stR, *stK;
 } oprop;
 
 /* retarded and Keldysh parts of a self-energy table at v (linear in x, zero at x = +-1) */
@@ -286,6 +292,45 @@ static double tanh_ft(double v, double T) {
  * 2 = G dSigma G alone (the line with one insertion of the dSigma tables, the multiloop
  * self-energy flow's t term) */
 static void prop_matrix(const oprop *P, int which, double v, cplx M[2][2]) {
+    /* Tabulated lines (Sec. II.C.2-II.C.5 with the propagators given instead of computed):
+     * retarded and Keldysh parts read from the tables like a self-energy (linear in x, zero at
+     * x = +-1), the advanced part their conjugate; a tabulated S uses the tabulated G (or the
+     * model's) only in the Katanin term. */
+    if ((P->n_gt > 0 && which != 1) || (which == 1 && P->n_st > 0)) {
+        cplx GR, GK, GA, XR, XK;
+        if (P->n_gt > 0) {
+            sigma_at(P->n_gt, P->A_gt, P->gtR, P->gtK, v, &GR, &GK);
+        } else {
+            cplx Gm[2][2];
+            oprop Q = *P;
+            Q.n_st = 0;
+            prop_matrix(&Q, 0, v, Gm);
+            GR = Gm[0][1];
+            GK = Gm[0][0];
+        }
+        GA = conj(GR);
+        M[1][1] = 0;
+        if (which == 0) {
+            M[0][0] = GK;
+            M[0][1] = GR;
+            M[1][0] = GA;
+            return;
+        }
+        cplx dR = 0, dK = 0;
+        if (P->n_dsig > 0) sigma_at(P->n_dsig, P->A_dsig, P->dsigR, P->dsigK, v, &dR, &dK);
+        cplx dA = conj(dR);
+        if (which == 2) {
+            M[0][1] = GR * dR * GR;
+            M[1][0] = GA * dA * GA;
+            M[0][0] = GR * dR * GK + GK * dA * GA + GR * dK * GA;
+            return;
+        }
+        sigma_at(P->n_st, P->A_st, P->stR, P->stK, v, &XR, &XK);
+        M[0][0] = XK + GR * dR * GK + GK * dA * GA + GR * dK * GA;
+        M[0][1] = XR + GR * dR * GR;
+        M[1][0] = conj(XR) + GA * dA * GA;
+        return;
+    }
     cplx sR, sK;
     sigma_at(P->n_sig, P->A_sig, P->sigR, P->sigK, v, &sR, &sK);
     const double lam = (P->reg == 1) ? P->lam : 1.0;

@@ -65,7 +65,9 @@ class _OProp(C.Structure):
     _fields_ = [("Delta", C.c_double), ("T", C.c_double), ("eps", C.c_double), ("A_sig", C.c_double),
                 ("n_sig", C.c_int), ("sigR", C.c_void_p), ("sigK", C.c_void_p), ("reg", C.c_int),
                 ("lam", C.c_double), ("n_dsig", C.c_int), ("A_dsig", C.c_double), ("dsigR", C.c_void_p),
-                ("dsigK", C.c_void_p)]
+                ("dsigK", C.c_void_p), ("n_gt", C.c_int), ("A_gt", C.c_double), ("gtR", C.c_void_p),
+                ("gtK", C.c_void_p), ("n_st", C.c_int), ("A_st", C.c_double), ("stR", C.c_void_p),
+                ("stK", C.c_void_p)]
 
 
 REG_DELTA, REG_U, REG_T, REG_NONE = 0, 1, 2, 3
@@ -109,10 +111,13 @@ class Prop:
     the single-scale propagator of the flow scheme reg (REG_DELTA, REG_U with parameter lam:
     G^R = lam / (v - eps + i Delta - lam Sigma^R), REG_T, or REG_NONE: S = 0), with the
     Katanin substitution S + G dSigma G when dSigma/dLambda tables are given (with REG_NONE
-    the change of G along dSigma)."""
+    the change of G along dSigma).  Tabulated lines: gtR, gtK (G) and stR, stK (S) on tan
+    grids of scales A_gt, A_st replace the computed G and S (the Keldysh parts default to 0;
+    a tabulated G needs a tabulated S wherever S is used)."""
 
     def __init__(self, Delta=1.0, T=0.1, eps=0.0, sigR=None, sigK=None, A_sig=5.0, reg=REG_DELTA, lam=1.0,
-                 dsigR=None, dsigK=None, A_dsig=5.0):
+                 dsigR=None, dsigK=None, A_dsig=5.0, gtR=None, gtK=None, A_gt=5.0, stR=None, stK=None,
+                 A_st=5.0):
         self.sigR = None if sigR is None else np.ascontiguousarray(sigR, dtype=np.complex128)
         self.sigK = None if sigK is None else np.ascontiguousarray(sigK, dtype=np.complex128)
         self.dsigR = None if dsigR is None else np.ascontiguousarray(dsigR, dtype=np.complex128)
@@ -127,6 +132,20 @@ class Prop:
         s.n_sig = 0 if self.sigR is None else len(self.sigR)
         s.sigR = None if self.sigR is None else self.sigR.ctypes.data
         s.sigK = None if self.sigK is None else self.sigK.ctypes.data
+        self.tabs = {}
+        for name, R, K, A in (("g", gtR, gtK, A_gt), ("s", stR, stK, A_st)):
+            n = 0
+            if R is not None:
+                R = np.ascontiguousarray(R, dtype=np.complex128)
+                K = np.zeros_like(R) if K is None else np.ascontiguousarray(K, dtype=np.complex128)
+                assert K.shape == R.shape
+                self.tabs[name] = (R, K)
+                n = len(R)
+            setattr(s, "n_%st" % name, n)
+            setattr(s, "A_%st" % name, float(A))
+            setattr(s, "%stR" % name, None if n == 0 else R.ctypes.data)
+            setattr(s, "%stK" % name, None if n == 0 else K.ctypes.data)
+        self.has_g_table, self.has_s_table = "g" in self.tabs, "s" in self.tabs
         self._s = s
         self.Delta, self.T, self.eps = Delta, T, eps
 
