@@ -114,6 +114,27 @@ kb_status kb_set_regulator(kb_ctx *ctx, int kind, double lambda);
 kb_status kb_set_self_energy_derivative(kb_ctx *ctx, int n_dsig, double A_dsig, const double *dsigR,
                                         const double *dsigK);
 
+/* Tabulated lines (the propagator pair of the bubble, Sec. II.C.5, and the line of the loop,
+ * Sec. II.D.2, built from given propagators instead of from the model and Σ, Sec. II.C.2):
+ * which = KB_PROP_G: G^R and G^K; which = KB_PROP_S: the single-scale propagator S^R and S^K.
+ * n points on the tan grid v_i = A_tab tan(π x_i / 2), x_i = -1 + 2(i+1)/(n+1), interleaved
+ * complex double HOST arrays (copied before the call returns), read linearly in x with zero at
+ * x = ±1; the advanced part is the conjugate of the retarded one and the quantum-quantum
+ * component is 0.  tabR == NULL removes that table (back to the model's line); tabK may be
+ * NULL (zero Keldysh part).  A tabulated line replaces the model and the Σ tables for that
+ * line; the Katanin tables still add G dΣ G to S, with the tabulated G.  While G is tabulated,
+ * the S line (KB_PI_GS_SG, kb_loop line 1) needs an S table (KB_ERR_STATE otherwise), and the
+ * G^R gradient of kb_bubble_vjp is not available with either table (KB_ERR_UNSUPPORTED).  The
+ * endpoint terms at x = ±1 keep the asymptotics of the model and the flow scheme
+ * (v G^R -> λ, v G^K -> 0, v S per scheme), so the tables should hold lines with those
+ * asymptotics, e.g. of a self-energy that vanishes as |v| -> ∞.  Errors: KB_ERR_ARG (which,
+ * n < 1, A_tab <= 0, a non-finite entry), KB_ERR_CUDA (device copy).  Step graphs captured
+ * before the call refuse to launch afterwards. */
+#define KB_PROP_G 0
+#define KB_PROP_S 1
+kb_status kb_set_propagator_table(kb_ctx *ctx, int which, int n, double A_tab, const double *tabR,
+                                  const double *tabK);
+
 /* Vertex slot `slot` (0 .. KB_MAX_SLOTS-1): the bare part R = Γ0 of the parquet
  * approximation (Sec. I.B: -U/2 on components with an odd number of quantum indices)
  * when has_R != 0, and no classes.  Classes are attached with kb_set_vertex_class. */

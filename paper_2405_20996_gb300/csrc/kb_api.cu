@@ -161,6 +161,8 @@ kb_status kb_destroy(kb_ctx* ctx) {
     cudaFree(ctx->d_wq);
     cudaFree(ctx->d_sig);
     cudaFree(ctx->d_dsig);
+    cudaFree(ctx->d_gt);
+    cudaFree(ctx->d_st);
     if (ctx->ws.ptr) {
         cudaFreeAsync(ctx->ws.ptr, nullptr);
         cudaDeviceSynchronize();
@@ -275,6 +277,47 @@ kb_status kb_set_self_energy(kb_ctx* ctx, int n_sig, double A_sig, const double*
     return KB_OK;
 }
 
+kb_status kb_set_propagator_table(kb_ctx* ctx, int which, int n, double A_tab, const double* tabR,
+                                  const double* tabK) {
+    if (!ctx) return KB_ERR_ARG;
+    if (which != KB_PROP_G && which != KB_PROP_S) {
+        ctx->err = "kb_set_propagator_table: which must be KB_PROP_G or KB_PROP_S";
+        return KB_ERR_ARG;
+    }
+    if (tabR && (n < 1 || !(A_tab > 0) || !std::isfinite(A_tab))) {
+        ctx->err = "kb_set_propagator_table: n >= 1, A_tab > 0";
+        return KB_ERR_ARG;
+    }
+    if (tabR)
+        for (int i = 0; i < 2 * n; ++i)
+            if (!std::isfinite(tabR[i]) || (tabK && !std::isfinite(tabK[i]))) {
+                ctx->err = "kb_set_propagator_table: table entries must be finite";
+                return KB_ERR_ARG;
+            }
+    cudaSetDevice(ctx->device);
+    double2*& buf = (which == KB_PROP_G) ? ctx->d_gt : ctx->d_st;
+    if (buf) ++ctx->mem_gen;                   // step graphs that captured the old table
+    cudaFree(buf);
+    buf = nullptr;
+    if (which == KB_PROP_G) { ctx->m.n_gt = 0; ctx->m.gtR = ctx->m.gtK = nullptr; }
+    else { ctx->m.n_st = 0; ctx->m.stR = ctx->m.stK = nullptr; }
+    for (int s = 0; s < KB_MAX_SLOTS; ++s) ++ctx->slot_gen[s];     // cached K3 right tiles hold Π
+    if (!tabR) return KB_OK;
+    std::vector<double2> h(2 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        h[i] = make_double2(tabR[2 * i], tabR[2 * i + 1]);
+        h[n + i] = tabK ? make_double2(tabK[2 * i], tabK[2 * i + 1]) : make_double2(0, 0);
+    }
+    KB_CUDA_TRY(ctx, cudaMalloc(&buf, sizeof(double2) * h.size()));
+    KB_CUDA_TRY(ctx, cudaMemcpy(buf, h.data(), sizeof(double2) * h.size(), cudaMemcpyHostToDevice));
+    if (which == KB_PROP_G) { ctx->m.n_gt = n; ctx->m.A_gt = A_tab; ctx->m.gtR = buf; ctx->m.gtK = buf + n; }
+    else { ctx->m.n_st = n; ctx->m.A_st = A_tab; ctx->m.stR = buf; ctx->m.stK = buf + n; }
+    return KB_OK;
+}
+
+// A tabulated G leaves the single-scale line S undefined unless S is tabulated too.
+static bool s_line_defined(const kb_ctx* ctx) { return ctx->m.n_gt == 0 || ctx->m.n_st > 0; }
+
 kb_status kb_set_vertex(kb_ctx* ctx, int slot, int has_R, double U) {
     if (!ctx || slot < 0 || slot >= KB_MAX_SLOTS || !std::isfinite(U)) {
         if (ctx) ctx->err = "kb_set_vertex: bad slot or U";
@@ -339,6 +382,10 @@ kb_status kb_bubble_t_su2(kb_ctx* ctx, int slot, int so, int pi_kind, unsigned m
         return KB_ERR_ARG;
     }
     if (!ctx->slot_set[slot] || !ctx->slot_set[so]) { ctx->err = "kb_bubble_t_su2: slot not set"; return KB_ERR_STATE; }
+    if (pi_kind == KB_PI_GS_SG && !s_line_defined(ctx)) {
+        ctx->err = "kb_bubble_t_su2: G is tabulated, so KB_PI_GS_SG needs an S table";
+        return KB_ERR_STATE;
+    }
     for (int k = 0; k < 4; ++k)
         if ((mask >> k) & 1) {
             const void* o = ctx->slots[so].cls[KB_CH_T][k];
@@ -387,6 +434,10 @@ kb_status kb_bubble(kb_ctx* ctx, int channel, int sl, int sr, int so, int pi_kin
     }
     if (!ctx->slot_set[sl] || !ctx->slot_set[sr] || !ctx->slot_set[so]) {
         ctx->err = "kb_bubble: slot not set";
+        return KB_ERR_STATE;
+    }
+    if (pi_kind == KB_PI_GS_SG && !s_line_defined(ctx)) {
+        ctx->err = "kb_bubble: G is tabulated, so KB_PI_GS_SG needs an S table";
         return KB_ERR_STATE;
     }
     for (int k = 0; k < 4; ++k)
@@ -452,9 +503,15 @@ kb_status kb_bubble_vjp(kb_ctx* ctx, int channel, int sl, int sr, int sgo, int p
     }
     void* tabs[3] = {grad_GR_K1, grad_GR_K2, grad_GR_K3};
     bool any_gr = grad_GR_K1 || grad_GR_K2 || grad_GR_K3;
-    if (any_gr && (pi_kind != KB_PI_GG || ctx->m.n_sig > 0 || ctx->m.n_dsig > 0)) {
-        ctx->err = "kb_bubble_vjp: the G^R gradient needs pi_kind GG and no self-energy table (FDR form of G^K)";
+    if (any_gr && (pi_kind != KB_PI_GG || ctx->m.n_sig > 0 || ctx->m.n_dsig > 0 || ctx->m.n_gt > 0 ||
+                   ctx->m.n_st > 0)) {
+        ctx->err = "kb_bubble_vjp: the G^R gradient needs pi_kind GG and no self-energy or line table (FDR form "
+                   "of G^K)";
         return KB_ERR_UNSUPPORTED;
+    }
+    if (pi_kind == KB_PI_GS_SG && !s_line_defined(ctx)) {
+        ctx->err = "kb_bubble_vjp: G is tabulated, so KB_PI_GS_SG needs an S table";
+        return KB_ERR_STATE;
     }
     if (precision != KB_PREC_FP64 && precision != KB_PREC_MIXED) {
         ctx->err = "kb_bubble_vjp: precision must be KB_PREC_FP64 or KB_PREC_MIXED";

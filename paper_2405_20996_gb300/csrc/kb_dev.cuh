@@ -95,11 +95,60 @@ __device__ __forceinline__ double tanh_T(double v, double T) {
     return tanh(v * (0.5 / T));
 }
 
+// Retarded and Keldysh parts of a line table at v (n points on the tan grid of scale A,
+// linear in x, zero at x = +-1).
+__device__ __forceinline__ void line_table(const double2* tR, const double2* tK, int n, double A, double v,
+                                           double2& R, double2& K) {
+    R = make_double2(0, 0);
+    K = make_double2(0, 0);
+    double t;
+    int k = xstencil(v, n, A, t);
+    if (k >= 0) { R = cadd(R, cscale(tR[k], 1.0 - t)); K = cadd(K, cscale(tK[k], 1.0 - t)); }
+    if (k >= -1 && k + 1 <= n - 1) { R = cadd(R, cscale(tR[k + 1], t)); K = cadd(K, cscale(tK[k + 1], t)); }
+}
+
+// Katanin substitution S -> S + G dSigma G: the contour product with
+// dSigma = [[0, dS^A], [dS^R, dS^K]] in the [[K, R], [A, 0]] layout of G
+__device__ inline void add_katanin(const Model& m, double v, double2 GR, double2 GA, double2 GK, double2 P[2][2]) {
+    double2 dR = make_double2(0, 0), dK = make_double2(0, 0);
+    double t;
+    int k = xstencil(v, m.n_dsig, m.A_dsig, t);
+    if (k >= 0) { dR = cadd(dR, cscale(m.dsigR[k], 1.0 - t)); dK = cadd(dK, cscale(m.dsigK[k], 1.0 - t)); }
+    if (k >= -1 && k + 1 <= m.n_dsig - 1) {
+        dR = cadd(dR, cscale(m.dsigR[k + 1], t));
+        dK = cadd(dK, cscale(m.dsigK[k + 1], t));
+    }
+    const double2 dA = cconj(dR);
+    P[0][1] = cadd(P[0][1], cmul(cmul(GR, dR), GR));
+    P[1][0] = cadd(P[1][0], cmul(cmul(GA, dA), GA));
+    P[0][0] = cadd(P[0][0], cadd(cadd(cmul(cmul(GR, dR), GK), cmul(cmul(GK, dA), GA)), cmul(cmul(GR, dK), GA)));
+}
+
 // 2x2 Keldysh matrix of G (which = 0) or of the single-scale propagator S = dG/dΛ at fixed
 // Σ of the flow scheme m.reg (which = 1) at frequency v; index [a][a'], 0 = classical,
 // 1 = quantum: [[K, R], [A, 0]].  The interaction flow divides the bare inverse propagator
 // by λ = m.lam: G^R = 1 / ((v - eps + iΔ) / λ - Σ^R), G^K = G^R [Σ^K - 2iΔ th / λ] G^A.
+// With line tables (m.n_gt, m.n_st > 0) G and S are read from them instead (G^A = (G^R)*).
 __device__ inline void prop2x2(const Model& m, int which, double v, double2 P[2][2]) {
+    if (m.n_gt > 0 && (which == 0 || m.n_st > 0)) {
+        double2 GR, GK;
+        line_table(m.gtR, m.gtK, m.n_gt, m.A_gt, v, GR, GK);
+        const double2 GA = cconj(GR);
+        if (which == 0) {
+            P[0][0] = GK;
+            P[0][1] = GR;
+            P[1][0] = GA;
+        } else {
+            double2 SR, SK;
+            line_table(m.stR, m.stK, m.n_st, m.A_st, v, SR, SK);
+            P[0][0] = SK;
+            P[0][1] = SR;
+            P[1][0] = cconj(SR);
+            if (m.n_dsig > 0) add_katanin(m, v, GR, GA, GK, P);
+        }
+        P[1][1] = make_double2(0, 0);
+        return;
+    }
     double2 sR = make_double2(0, 0), sK = make_double2(0, 0);
     if (m.n_sig > 0) {
         double t;
@@ -121,6 +170,14 @@ __device__ inline void prop2x2(const Model& m, int which, double v, double2 P[2]
         P[0][0] = cmul(cmul(GR, mid), GA);
         P[0][1] = GR;
         P[1][0] = GA;
+    } else if (m.n_st > 0) {
+        // tabulated S with the model's G
+        double2 SR, SK;
+        line_table(m.stR, m.stK, m.n_st, m.A_st, v, SR, SK);
+        P[0][0] = SK;
+        P[0][1] = SR;
+        P[1][0] = cconj(SR);
+        if (m.n_dsig > 0) add_katanin(m, v, GR, GA, cmul(cmul(GR, mid), GA), P);
     } else {
         // S^R = -(G^R)^2 d[(G^R)^-1]/dΛ and dmid = d(mid)/dΛ per scheme
         double2 SR, dmid;
@@ -146,22 +203,7 @@ __device__ inline void prop2x2(const Model& m, int which, double v, double2 P[2]
         P[0][0] = cadd(cadd(t1, t2), t3);
         P[0][1] = SR;
         P[1][0] = SA;
-        if (m.n_dsig > 0) {
-            // Katanin substitution S -> S + G dSigma G: the contour product with
-            // dSigma = [[0, dS^A], [dS^R, dS^K]] in the [[K, R], [A, 0]] layout of G
-            double2 dR = make_double2(0, 0), dK = make_double2(0, 0);
-            double t;
-            int k = xstencil(v, m.n_dsig, m.A_dsig, t);
-            if (k >= 0) { dR = cadd(dR, cscale(m.dsigR[k], 1.0 - t)); dK = cadd(dK, cscale(m.dsigK[k], 1.0 - t)); }
-            if (k >= -1 && k + 1 <= m.n_dsig - 1) {
-                dR = cadd(dR, cscale(m.dsigR[k + 1], t));
-                dK = cadd(dK, cscale(m.dsigK[k + 1], t));
-            }
-            const double2 dA = cconj(dR), GK = cmul(cmul(GR, mid), GA);
-            P[0][1] = cadd(P[0][1], cmul(cmul(GR, dR), GR));
-            P[1][0] = cadd(P[1][0], cmul(cmul(GA, dA), GA));
-            P[0][0] = cadd(P[0][0], cadd(cadd(cmul(cmul(GR, dR), GK), cmul(cmul(GK, dA), GA)), cmul(cmul(GR, dK), GA)));
-        }
+        if (m.n_dsig > 0) add_katanin(m, v, GR, GA, cmul(cmul(GR, mid), GA), P);
     }
     P[1][1] = make_double2(0, 0);
 }

@@ -298,6 +298,10 @@ extern "C" kb_status kb_loop(kb_ctx* ctx, int slot, int which, int n, const doub
         ctx->err = "kb_loop: set the grids, the model and the vertex first";
         return KB_ERR_STATE;
     }
+    if (line == 1 && ctx->m.n_gt > 0 && ctx->m.n_st == 0) {
+        ctx->err = "kb_loop: G is tabulated, so the S line needs an S table";
+        return KB_ERR_STATE;
+    }
     if (n == 0) return KB_OK;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return KB_ERR_CUDA;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -41,6 +41,14 @@ struct Model {
     double A_dsig = 5.0;
     const double2* dsigR = nullptr;
     const double2* dsigK = nullptr;
+    int n_gt = 0;            // > 0: G^R, G^K read from these tables (kb_set_propagator_table)
+    double A_gt = 5.0;
+    const double2* gtR = nullptr;
+    const double2* gtK = nullptr;
+    int n_st = 0;            // > 0: S^R, S^K read from these tables
+    double A_st = 5.0;
+    const double2* stR = nullptr;
+    const double2* stK = nullptr;
 };
 
 // Keldysh index maps of channel r (matrix form of the 16-component contraction):
@@ -75,6 +83,8 @@ struct kb_ctx {
     double* d_wq = nullptr;   // weights w_j (device, nq)
     double2* d_sig = nullptr; // Sigma tables (2 * n_sig)
     double2* d_dsig = nullptr; // dSigma/dLambda tables (2 * n_dsig), Katanin substitution
+    double2* d_gt = nullptr;   // tabulated G (2 * n_gt), kb_set_propagator_table
+    double2* d_st = nullptr;   // tabulated S (2 * n_st)
     kb::VertexDev slots[KB_MAX_SLOTS];
     bool slot_set[KB_MAX_SLOTS];
     kb::Workspace ws;

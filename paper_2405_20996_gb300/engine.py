@@ -50,6 +50,12 @@ class Engine:
     def set_self_energy(self, sigR=None, sigK=None, A_sig=5.0):
         kb.kb_set_self_energy(self.ctx, sigR, sigK, A_sig)
 
+    def set_propagator_table(self, which, tabR=None, tabK=None, A_tab=5.0):
+        """Tabulated line (which: "G" or "S"): retarded and Keldysh parts on the tan grid of
+        scale A_tab; tabR None removes it (kb_set_propagator_table)."""
+        w = {"G": kb.KB_PROP_G, "S": kb.KB_PROP_S}[which]
+        kb.kb_set_propagator_table(self.ctx, w, tabR, tabK, A_tab)
+
     def set_vertex(self, slot, U=0.0, has_R=False, channels=None, dtype=torch.complex128, include=(0, 1, 2),
                    symmetric=False):
         """channels: {channel: (K1, K2, K2p, K3)} arrays (numpy or torch; None = absent);

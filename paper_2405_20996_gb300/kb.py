@@ -57,6 +57,7 @@ _SIGS = {
     "kb_set_self_energy": [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p],
     "kb_set_regulator": [C.c_void_p, C.c_int, C.c_double],
     "kb_set_self_energy_derivative": [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p],
+    "kb_set_propagator_table": [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_void_p, C.c_void_p],
     "kb_set_vertex": [C.c_void_p, C.c_int, C.c_int, C.c_double],
     "kb_set_vertex_channels": [C.c_void_p, C.c_int, C.c_uint],
     "kb_set_vertex_symmetric": [C.c_void_p, C.c_int, C.c_int],
@@ -168,6 +169,20 @@ def kb_set_self_energy_derivative(ctx, dsigR=None, dsigK=None, A_dsig=5.0):
     k = None if dsigK is None else np.ascontiguousarray(np.asarray(dsigK, dtype=np.complex128))
     _check(ctx, lib().kb_set_self_energy_derivative(ctx, len(r), A_dsig, r.ctypes.data,
                                                     None if k is None else k.ctypes.data))
+
+
+KB_PROP_G, KB_PROP_S = 0, 1
+
+
+def kb_set_propagator_table(ctx, which, tabR=None, tabK=None, A_tab=5.0):
+    import numpy as np
+    if tabR is None:
+        _check(ctx, lib().kb_set_propagator_table(ctx, which, 0, A_tab, None, None))
+        return
+    r = np.ascontiguousarray(np.asarray(tabR, dtype=np.complex128))
+    k = None if tabK is None else np.ascontiguousarray(np.asarray(tabK, dtype=np.complex128))
+    _check(ctx, lib().kb_set_propagator_table(ctx, which, len(r), A_tab, r.ctypes.data,
+                                              None if k is None else k.ctypes.data))
 
 
 def kb_set_self_energy(ctx, sigR=None, sigK=None, A_sig=5.0):

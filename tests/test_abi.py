@@ -80,6 +80,10 @@ def test_self_energy_derivative_call_rejected_without_context():
     assert kb.lib().kb_set_self_energy_derivative(None, 0, 5.0, None, None) == kb.KB_ERR_ARG
 
 
+def test_propagator_table_call_rejected_without_context():
+    assert kb.lib().kb_set_propagator_table(None, kb.KB_PROP_G, 0, 5.0, None, None) == kb.KB_ERR_ARG
+
+
 def test_vertex_eval_rejected_without_context():
     assert kb.lib().kb_vertex_eval(None, 0, 0, 0, 1, None, None, None) == kb.KB_ERR_ARG
 
