@@ -162,18 +162,24 @@ __device__ __forceinline__ void store_out(void* out, int dt, size_t e, double2 v
 // K1(w) = sum_j sum_s L0_s Pi R0_s.  Grid (w of the K1 grid, node slice): each CTA of 128
 // threads sums its slice of the nodes and writes an FP64 partial; k_mx_k1_fin adds the
 // slices in order and stores.
+// half (p channel, a crossing-symmetric vertex bubbled with itself): the summand at -v'' is
+// the one at v'' with both Keldysh pairs of the output exchanged (crossing exchanges the
+// pairs of L0 and R0, and Pi_p(w, -v'') is Pi_p(w, v'') with its two lines exchanged), so
+// only the nodes v'' >= 0 are summed, the centre node v'' = 0 at half weight, and
+// k_mx_k1_fin adds the sum to its pair-exchanged image.
 constexpr int K1_SLICES = 8;
 
 template <int R>
 __global__ void __launch_bounds__(128) k_mx_k1(VertexF VL, VertexF VR, DfGrids G, Model m, MixedJob J,
                                                const double* __restrict__ xq, const double* __restrict__ wq,
-                                               double2* __restrict__ part, int w_off) {
+                                               double2* __restrict__ part, int w_off, int half) {
     __shared__ double sh[4 * 32];
     int wi = w_off + blockIdx.x, sl = blockIdx.y;
     const df* qn = G.n3v + G.N3v;
     df w = G.n1[wi];
-    const int per = (J.nq + K1_SLICES - 1) / K1_SLICES;
-    const int jb = sl * per, je = min(J.nq, jb + per);
+    const int jlo = half ? (J.nq - 1) / 2 : 0;
+    const int per = (J.nq - jlo + K1_SLICES - 1) / K1_SLICES;
+    const int jb = jlo + sl * per, je = min(J.nq, jb + per);
     float2 acc[16];
     for (int o = 0; o < 16; ++o) acc[o] = make_float2(0, 0);
     for (int j = jb + threadIdx.x; j < je; j += blockDim.x) {
@@ -182,8 +188,9 @@ __global__ void __launch_bounds__(128) k_mx_k1(VertexF VL, VertexF VR, DfGrids G
             double2 Pi[16];
             pi_entry_t<R>(m, J.pi_kind, G.A, (double)w.h + (double)w.l, xq[j], wq[j], Pi,
                      (double)G.n3v[G.N3v + j].h + (double)G.n3v[G.N3v + j].l, true);
+            const double hw = (half && j == jlo) ? 0.5 : 1.0;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) Pf[i] = make_float2((float)Pi[i].x, (float)Pi[i].y);
+            for (int i = 0; i < 16; ++i) Pf[i] = make_float2((float)(hw * Pi[i].x), (float)(hw * Pi[i].y));
         }
         constexpr int NS = (R == KB_CH_T) ? 2 : 1;
 #pragma unroll
@@ -209,7 +216,8 @@ __global__ void __launch_bounds__(128) k_mx_k1(VertexF VL, VertexF VR, DfGrids G
         for (int o = 0; o < 16; ++o) part[((size_t)blockIdx.x * K1_SLICES + sl) * 16 + o] = res[o];
 }
 
-__global__ void k_mx_k1_fin(MixedJob J, const double2* __restrict__ part, void* out, int odt, int w_off, int nw) {
+__global__ void k_mx_k1_fin(MixedJob J, const double2* __restrict__ part, void* out, int odt, int w_off, int nw,
+                            int half) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nw * 16) return;
     int wl = i / 16, o = i % 16, A = o / 4, C = o % 4;
@@ -218,6 +226,15 @@ __global__ void k_mx_k1_fin(MixedJob J, const double2* __restrict__ part, void* 
         double2 p = part[((size_t)wl * K1_SLICES + sl) * 16 + o];
         x += p.x;
         y += p.y;
+    }
+    if (half) {
+        // the image at -v'': rows and columns with the two indices of their pair exchanged
+        const int oi = 4 * (((A & 1) << 1) | (A >> 1)) + (((C & 1) << 1) | (C >> 1));
+        for (int sl = 0; sl < K1_SLICES; ++sl) {
+            double2 p = part[((size_t)wl * K1_SLICES + sl) * 16 + oi];
+            x += p.x;
+            y += p.y;
+        }
     }
     store_out(out, odt, (size_t)(w_off + wl) * 16 + J.M.cO[A][C], make_double2(x, y), J.alpha, J.beta);
 }
@@ -1305,17 +1322,18 @@ static kb_status mixed_impl(kb_ctx* ctx, int sl, int sr, int so, int pi_kind, un
     }
     if ((mask >> KB_K1) & 1) {
         int w_off = (sym && r != KB_CH_P) ? g.n1 / 2 : 0;
+        const int half = (sym && r == KB_CH_P) ? 1 : 0;
         double2* part = reinterpret_cast<double2*>(ws + Lo.off_K1);
         {
             KB_LAUNCH(ctx, st, "k_mx_k1");
             k_mx_k1<r><<<dim3(g.n1 - w_off, K1_SLICES), 128, 0, st>>>(VL, VR, G, ctx->m, J, ctx->d_xq, ctx->d_wq,
-                                                                     part, w_off);
+                                                                     part, w_off, half);
         }
         {
             KB_LAUNCH(ctx, st, "k_mx_k1_fin");
             int tot = (g.n1 - w_off) * 16;
             k_mx_k1_fin<<<(tot + 127) / 128, 128, 0, st>>>(J, part, const_cast<void*>(VO.cls[r][KB_K1]),
-                                                          VO.dt[r][KB_K1], w_off, g.n1 - w_off);
+                                                          VO.dt[r][KB_K1], w_off, g.n1 - w_off, half);
         }
     }
     if (mask & ((1u << KB_K2) | (1u << KB_K2P))) {
