@@ -177,7 +177,8 @@ __host__ __device__ inline int tc_tiles(int mtiles, int ntiles, int cols, bool t
 // (128 x 128, or for both parts the two 128 x 128 products P and Q); the MMA warp restarts a
 // buffer every SEGK = 32 elements of K and the epilogue warps add each finished segment
 // into compensated (Kahan) FP32 running sums held in registers, so no plain FP32 accumulator
-// ever sums more than SEGK * 6 / 8 products.
+// ever sums more than 6 * SEGK products (one part per CTA; both parts: 3 * SEGK into each of
+// P and Q).
 // Two tile shapes (template BOTH):
 //   BOTH = false  one CTA per real or imaginary part of a 128 x 128 complex tile, N = 128
 //                 MMAs (6 per k-step); the Re and Im CTAs of a tile each load all 8 planes;
